@@ -1,0 +1,61 @@
+"""Pins of the oracle's vector-Jacobian products (CPU only): FD, dot-product, mass invariant."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import adjoint, hydro
+from paper_2512_13403_b300 import inputs
+
+G = 5.0 / 3.0
+
+
+def _setup(n=8, steps=4, seed=2, mach=0.8):
+    U0 = torch.from_numpy(inputs.decaying_turbulence((n, n, n), seed=seed, sigma=0.3, mach=mach))
+    dx = (1.0 / n,) * 3
+    dts = []
+    U = U0.clone()
+    for _ in range(steps):
+        dt = hydro.cfl_dt(U, G, dx, 0.4)
+        dts.append(dt)
+        U = hydro.rk2_step(U, dt, G, dx)
+    return U0, dx, dts
+
+
+def test_central_finite_differences():
+    U0, dx, dts = _setup()
+    gen = torch.Generator().manual_seed(0)
+    w = torch.randn(U0.shape, generator=gen, dtype=torch.float64)
+    loss = lambda U: float((w * adjoint.advance(U, dts, G, dx)).sum())
+    g = adjoint.advance_vjp(U0, dts, w, G, dx)
+    idx = [(0, 1, 2, 3), (1, 4, 4, 4), (2, 7, 0, 5), (3, 2, 6, 1), (4, 5, 5, 0), (4, 0, 3, 7)]
+    for i in idx:
+        eps = 1e-6 * max(1.0, abs(float(U0[i])))
+        Up = U0.clone(); Up[i] += eps
+        Um = U0.clone(); Um[i] -= eps
+        fd = (loss(Up) - loss(Um)) / (2 * eps)
+        assert fd == pytest.approx(float(g[i]), rel=1e-5, abs=1e-8), i
+
+
+def test_dot_product_identity():
+    U0, dx, dts = _setup(seed=5)
+    gen = torch.Generator().manual_seed(1)
+    lam = torch.randn(U0.shape, generator=gen, dtype=torch.float64)
+    v = torch.randn(U0.shape, generator=gen, dtype=torch.float64)
+    # J v by forward-mode AD, J^T lambda by the oracle's reverse product
+    _, Jv = torch.func.jvp(lambda U: adjoint.advance(U, dts, G, dx), (U0,), (v,))
+    JTl = adjoint.advance_vjp(U0, dts, lam, G, dx)
+    a = float((lam * Jv).sum())
+    b = float((JTl * v).sum())
+    assert a == pytest.approx(b, rel=1e-12)
+
+
+def test_mass_invariant():
+    U0, dx, dts = _setup(seed=7)
+    N3 = U0[0].numel()
+    lam = torch.zeros_like(U0)
+    lam[0] = 1.0 / N3  # L = mean(rho_final)
+    g = adjoint.advance_vjp(U0, dts, lam, G, dx)
+    assert float((g[0] - 1.0 / N3).abs().max()) < 1e-15
+    assert float(g[1:].abs().max()) < 1e-15

@@ -1,0 +1,96 @@
+"""Pins of the oracle's multigrid Poisson solver and gravity source (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import multigrid as mg
+from paper_2512_13403_b300 import inputs
+
+
+def _coords(shape):
+    nz, ny, nx = shape
+    return [(torch.arange(n, dtype=torch.float64) + 0.5) / n for n in (nx, ny, nz)]
+
+
+def test_single_fourier_mode_exact_discrete_solution():
+    n = 32
+    h = 1.0 / n
+    x, y, z = _coords((n, n, n))
+    m = (1, 2, 3)
+    F = torch.sin(2 * math.pi * (m[0] * x[None, None, :] + m[1] * y[None, :, None] + m[2] * z[:, None, None]))
+    lam = -(4.0 / h ** 2) * sum(math.sin(math.pi * mi * h) ** 2 for mi in m)
+    phi, cycles, res, ok = mg.solve(F, h, tol=1e-11, max_cycles=40)
+    assert ok
+    assert float((phi - F / lam).abs().max()) < 1e-9 * float((F / lam).abs().max())
+
+
+def test_matches_fft_solve_of_same_operator():
+    n = 32
+    h = 1.0 / n
+    rho = torch.from_numpy(inputs.lognormal_density((n, n, n), 1.0, 5))
+    F = mg.poisson_source(rho, 1.0)
+    k = torch.fft.fftfreq(n, d=1.0 / n, dtype=torch.float64)
+    s = lambda kk: torch.sin(math.pi * kk * h) ** 2
+    lam = -(4.0 / h ** 2) * (s(k)[:, None, None] + s(k)[None, :, None] + s(k)[None, None, :])
+    lam[0, 0, 0] = 1.0
+    Fh = torch.fft.fftn(F)
+    Fh[0, 0, 0] = 0.0
+    phi_fft = torch.fft.ifftn(Fh / lam).real
+    phi, cycles, res, ok = mg.solve(F, h, tol=1e-12, max_cycles=60)
+    assert ok
+    assert float((phi - phi_fft).abs().max()) < 1e-10 * float(phi_fft.abs().max())
+
+
+def test_vcycle_reduces_residual():
+    n = 32
+    h = 1.0 / n
+    F = mg.poisson_source(torch.from_numpy(inputs.lognormal_density((n, n, n), 1.0, 6)), 1.0)
+    shapes = mg.level_shapes(F.shape)
+    assert shapes[-1] == (4, 4, 4)
+    phi = torch.zeros_like(F)
+    r0 = mg.relative_residual(phi, F, h)
+    factors = []
+    for _ in range(5):
+        phi = mg.vcycle(phi, F, h, shapes)
+        phi = phi - phi.mean()
+        r1 = mg.relative_residual(phi, F, h)
+        factors.append(r1 / r0)
+        r0 = r1
+    assert max(factors) < 0.2, factors
+
+
+def test_coarse_pseudo_inverse_projects_mean():
+    shape = (4, 4, 4)
+    F = torch.randn(shape, dtype=torch.float64)
+    phi = mg.coarse_solve(F, 0.25)
+    assert float(phi.mean().abs()) < 1e-13
+    assert torch.allclose(mg.apply_A(phi, 0.25), F - F.mean(), atol=1e-12)
+
+
+def test_transfer_operators_on_constants_and_linear_fields():
+    c = torch.full((4, 6, 8), 2.5, dtype=torch.float64)
+    assert torch.allclose(mg.restrict(torch.full((8, 12, 16), 2.5, dtype=torch.float64)), c)
+    assert torch.allclose(mg.prolong(c), torch.full((8, 12, 16), 2.5, dtype=torch.float64))
+    # a field linear in x (cell-centre coordinates) is reproduced away from the periodic seam
+    xc = (torch.arange(8, dtype=torch.float64) + 0.5) / 8
+    e = xc[None, None, :].expand(4, 4, 8).contiguous()
+    xf = (torch.arange(16, dtype=torch.float64) + 0.5) / 16
+    p = mg.prolong(e)
+    assert torch.allclose(p[..., 1:-1], xf[None, None, 1:-1].expand(8, 8, 14))
+    # restriction after prolongation reproduces a linear field away from the seam
+    assert torch.allclose(mg.restrict(p)[..., 1:-1], e[..., 1:-1])
+
+
+def test_gravity_source_on_linear_potential():
+    n = 8
+    h = 1.0 / n
+    U = torch.from_numpy(inputs.uniform_state((n, n, n), rho=2.0, P=1.0, v=(0.1, 0.0, 0.0)))
+    x = (torch.arange(n, dtype=torch.float64) + 0.5) * h
+    phi = torch.sin(2 * math.pi * x)[None, None, :].expand(n, n, n).contiguous()
+    out = mg.gravity_source(U, phi, 0.01, h)
+    gx = -(torch.sin(2 * math.pi * (x + h)) - torch.sin(2 * math.pi * (x - h))) / (2 * h)
+    assert torch.allclose(out[1], U[1] + 2.0 * gx[None, None, :] * 0.01, rtol=1e-14)
+    assert torch.allclose(out[4], U[4] + U[1] * gx[None, None, :] * 0.01, rtol=1e-14)
+    assert torch.equal(out[2], U[2]) and torch.equal(out[0], U[0])
