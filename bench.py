@@ -1,0 +1,301 @@
+"""Benchmark of the periodic finite-volume Euler step on B300 (one JSON line on stdout).
+
+Workload (default): driven cooling turbulence on a 256^3 periodic unit box in float32 — OU forcing
+of the solenoidal modes 1 <= |n| <= 2 (tau = 0.5, a_rms = 1), cooling Lambda = n^2 T^(1/2) above
+T_floor = 0.05 with per-cell subcycling, initial rho = 1, P = 0.6, v = 0.  A step is one full
+update: dt reduction, OU update, both RK2 stages with the fused sources.
+
+Timing: W untimed warm-up steps, then K steps between CUDA events on the solver's stream, with a
+barrier + synchronize on both sides; state buffers (3 x 336 MB) exceed the 126 MB L2, so no flush
+is needed.  value = cell-updates/s (N^3 * K / device time, summed over ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--grid 256]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s at 256^3 (fwd, adjoint); corrector error vs fine at equal time"
+UNIT = "cell-updates/s"
+FWD_BYTES_STAGE1 = 40   # float32: read U^n (20 B), write U1 (20 B) per cell
+FWD_BYTES_STAGE2 = 60   # float32: read U^n and U1 (40 B), write U^{n+1} (20 B) per cell
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_run(nsteps=None, grid=64, budget_s=20.0):
+    """Times the CPU oracle (as it stands) on a bounded sample of the same workload."""
+    import numpy as np
+    import torch
+    from oracle import driver as odrv
+    from paper_2512_13403_b300 import inputs
+    shape = (grid,) * 3
+    U0 = inputs.cooling_box(shape)
+    sim = odrv.Simulation(odrv.Config(shape=shape, forcing=True, cooling=True, ou_seed=1), U0)
+    sim.step()  # warm-up
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        sim.step()
+        n += 1
+        el = time.perf_counter() - t0
+        if (nsteps is not None and n >= nsteps) or (nsteps is None and el > budget_s):
+            break
+    return {"value": grid ** 3 * n / el, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"{grid}^3 driven cooling turbulence (same recipe), float64 oracle, {n} steps "
+                      f"after 1 warm-up, {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    per_step = []
+    import torch
+    from oracle import driver as odrv
+    from paper_2512_13403_b300 import inputs
+    grid = args.ref_grid
+    shape = (grid,) * 3
+    sim = odrv.Simulation(odrv.Config(shape=shape, forcing=True, cooling=True, ou_seed=1),
+                          inputs.cooling_box(shape))
+    for _ in range(args.warmup):
+        sim.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.step()
+    el = time.perf_counter() - t0
+    v = grid ** 3 * steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"driven cooling turbulence {args.grid}^3 (sampled at {grid}^3 on the host)",
+                       "grid": grid, "forcing": "OU 1<=|k|<=2 tau=0.5 a_rms=1",
+                       "cooling": "n^2 T^0.5, T_floor=0.05", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle",
+                             "cores": torch.get_num_threads(),
+                             "sample": f"{grid}^3, {steps} steps after {args.warmup} warm-up"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2512_13403_b300 import build as _build
+    from paper_2512_13403_b300 import inputs
+    from paper_2512_13403_b300.solver import Config, Solver
+
+    if rank == 0 or not os.path.exists(_build.LIB):
+        _build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+
+    n = args.grid
+    shape = (n, n, n)
+    cfg = Config(shape=shape, precision="f32", forcing=True, ou_seed=1 + rank, cooling=True,
+                 t_floor=0.05)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = Solver(cfg, stream=stream)
+        U0 = torch.from_numpy(inputs.cooling_box(shape)).float()
+        Ud = U0.cuda().contiguous()
+        s.init_state(Ud)
+        s.advance(args.warmup)
+        stream.synchronize()
+
+        launches0 = s.launch_count()
+        s.profile(True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            s.advance(args.steps)
+            ev1.record(stream)
+            ev1.synchronize()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        gpu_launches = s.launch_count() - launches0
+        prof = {k: s.profile_read(k) for k in ("stage1", "stage2", "prologue")}
+        s.profile(False)
+        t_sim, nstep = s.time()
+
+        # end to end through the public API with host buffers: upload the initial state from
+        # pinned memory, K steps each followed by a host read of the conserved totals (the
+        # step's reported result), download the final state to pinned memory.
+        host_in = U0.pin_memory()
+        host_out = torch.empty_like(U0).pin_memory()
+        s2 = Solver(cfg, stream=stream)
+        s2.init_state(Ud)
+        s2.advance(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2.init_state(host_in)
+        for _ in range(args.steps):
+            s2.step(0.0, sync=False)
+            s2.conserved_totals()
+        s2.get_state(host_out)
+        e2e_s = time.perf_counter() - t0
+        s2.close()
+
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t)
+    cells = n ** 3
+    value = ws * cells * args.steps / (ms_max * 1e-3)
+
+    peak, peak_kind = _peaks()
+    n2, t2 = prof["stage2"]
+    n1, t1 = prof["stage1"]
+    stage2_ms = t2 / max(n2, 1)
+    stage1_ms = t1 / max(n1, 1)
+    ach2 = FWD_BYTES_STAGE2 * cells / (stage2_ms * 1e-3) / 1e9
+    ach1 = FWD_BYTES_STAGE1 * cells / (stage1_ms * 1e-3) / 1e9
+    state_bytes = 5 * 4 * cells
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"driven cooling turbulence {n}^3 periodic (OU 1<=|k|<=2 tau=0.5 "
+                               f"a_rms=1; cooling n^2 T^0.5 T_floor=0.05; rho=1 P=0.6 v=0)",
+                   "grid": n, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (3 x 336 MB state buffers)",
+                   "sim_time_after": t_sim, "steps_done": nstep},
+        "roofline": {"bound": "hbm", "kernel": "stage2 (RK2 stage 2 + OU forcing + cooling + CFL)",
+                     "achieved": ach2, "peak": peak, "unit": "GB/s", "frac": ach2 / peak,
+                     "peak_source": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": FWD_BYTES_STAGE2 * cells,
+                     "avg_launch_ms": stage2_ms},
+        "kernels": {"stage1": {"launches": n1, "avg_ms": stage1_ms, "achieved_GBps": ach1,
+                               "frac": ach1 / peak},
+                    "stage2": {"launches": n2, "avg_ms": stage2_ms, "achieved_GBps": ach2,
+                               "frac": ach2 / peak},
+                    "prologue": {"launches": prof["prologue"][0],
+                                 "avg_ms": prof["prologue"][1] / max(prof["prologue"][0], 1)}},
+        "e2e": {"value": cells * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": state_bytes / args.steps,
+                "d2h_bytes_per_step": 40 + state_bytes / args.steps},
+        "gpu_launches": gpu_launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_run(budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--grid", type=int, default=256)
+    ap.add_argument("--ref-grid", type=int, default=64)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

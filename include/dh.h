@@ -1,0 +1,164 @@
+/*
+ * dh.h — C ABI of the B300 (sm_103a) finite-volume Euler library.
+ *
+ * The library advances the compressible Euler equations (arXiv:2512.13403, Sec. 3, Eq. 2) on a
+ * periodic uniform Cartesian grid with the pure update (U^{n+1}, theta^{n+1}) = H(U^n, theta^n)
+ * of Sec. 2.1: primitive recovery and MUSCL reconstruction with the MC limiter (App. A.1), HLLC
+ * fluxes with Davis wave speeds (App. A.2), the unsplit divergence integrated by SSP-RK2
+ * (App. A.3), the CFL time step (App. A.4), and the operator-split sources — Ornstein-Uhlenbeck
+ * forcing (Sec. 3.1.1), optically thin cooling (Sec. 4.3) and multigrid self-gravity (Sec. 5.2).
+ *
+ * Data layout.  A state is five structure-of-arrays planes (rho, m_x, m_y, m_z, E), each
+ * nx*ny*nz contiguous values with x fastest, then y, then z: element (f, k, j, i) sits at
+ * offset f*nx*ny*nz + (k*ny + j)*nx + i.  Values are float (DH_F32) or double (DH_F64) as
+ * chosen at dh_create; every pointer argument that carries a state uses that type.
+ *
+ * Ownership.  A context owns every device buffer it needs (allocated once in dh_create and
+ * released in dh_destroy) and the CUDA stream passed to dh_create (not owned: the caller keeps
+ * it alive).  Caller buffers are only read or written during the call that receives them, and
+ * all device work of a call is ordered on the context's stream.  Pointers flagged `on_device`
+ * are device pointers (for example torch CUDA tensors on the same device); otherwise host
+ * pointers (pinned or pageable).
+ *
+ * Errors.  Every entry point returns a dh_status; none aborts, traps or waits without bound.
+ * DH_ERR_ARG leaves the context unchanged.  After DH_ERR_NONFINITE or DH_ERR_POSITIVITY the
+ * context's state, time, step count and forcing state are those of the last good step.
+ * dh_last_error() returns a message for the most recent failure on that context.
+ */
+#ifndef DH_H
+#define DH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DH_API_VERSION 1
+
+typedef enum {
+  DH_OK = 0,
+  DH_ERR_ARG = 1,          /* invalid argument or unsupported configuration               */
+  DH_ERR_CUDA = 2,         /* a CUDA runtime call failed (message in dh_last_error)       */
+  DH_ERR_NONFINITE = 3,    /* a non-finite value appeared in the state                    */
+  DH_ERR_POSITIVITY = 4,   /* rho <= 0 or P <= 0 after a step                             */
+  DH_ERR_MG_NOCONV = 5,    /* multigrid did not reach its tolerance within mg_max_cycles  */
+  DH_ERR_STATE = 6         /* call out of order (e.g. step before init_state)             */
+} dh_status;
+
+typedef enum { DH_F32 = 0, DH_F64 = 1 } dh_precision;
+
+typedef struct dh_ctx dh_ctx;
+
+/* Run configuration.  Fill with dh_config_default, then override fields. */
+typedef struct dh_config {
+  int nx, ny, nz;            /* cells per axis; each >= 4                                  */
+  int precision;             /* DH_F32 (production) or DH_F64 (parity checks)              */
+  double dx, dy, dz;         /* cell widths (default 1/n: unit periodic box)               */
+  double gamma;              /* adiabatic index (default 5/3)                              */
+  double cfl;                /* Courant number C of App. A.4 (default 0.4)                 */
+  double dt_max;             /* upper bound on dt (default +inf)                           */
+  /* Ornstein-Uhlenbeck forcing, Sec. 3.1.1: modes 1 <= |n| <= 2, solenoidal.
+     Needs nx, ny, nz >= 5 so that the forced modes do not alias on the grid. */
+  int forcing;               /* 0/1                                                        */
+  double ou_tau;             /* autocorrelation time (default 0.5)                         */
+  double ou_arms;            /* rms acceleration a_rms (default 1.0)                       */
+  unsigned long long ou_seed;/* seed of the counter-based SplitMix64 draws (default 1)      */
+  /* Optically thin cooling, Sec. 4.3, Lambda = n^2 T^(1/2), code units T = P / rho. */
+  int cooling;               /* 0/1                                                        */
+  double t_floor;            /* temperature floor (default 0.05)                           */
+  double cool_frac;          /* first-substep fractional change limit f (default 0.1)      */
+  int nsub_max;              /* substep cap (default 1024)                                 */
+  /* Multigrid self-gravity, Sec. 5.2: A phi = 4 pi G (rho - <rho>), red-black Gauss-Seidel
+     V-cycles.  Needs dx == dy == dz; halving stops at dims < 8 or odd, coarsest <= 1024 cells. */
+  int gravity;               /* 0/1                                                        */
+  double four_pi_G;          /* 4 pi G (default 1)                                         */
+  double mg_tol;             /* ||F - A phi||_2 / ||F||_2 stop tolerance (default 1e-6)   */
+  int mg_max_cycles;         /* cycle cap (default 30)                                     */
+  int mg_pre, mg_post;       /* smoothing sweeps before / after the coarse correction (2,2)*/
+} dh_config;
+
+/* Fills *cfg with the defaults above for an nx*ny*nz grid. */
+void dh_config_default(dh_config* cfg, int nx, int ny, int nz);
+
+/* Creates a context: validates *cfg (copied), allocates all device buffers on the current
+   device and records `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+   DH_ERR_ARG on an invalid configuration, DH_ERR_CUDA if allocation fails. */
+dh_status dh_create(const dh_config* cfg, void* cuda_stream, dh_ctx** out);
+
+/* Releases every buffer of the context.  NULL is ignored. */
+void dh_destroy(dh_ctx* ctx);
+
+/* Copies a state (layout above, context precision) into the context and resets time, step
+   count, forcing state (draw 0 of Sec. 3.1.1) and the gravitational potential (zero). */
+dh_status dh_init_state(dh_ctx* ctx, const void* U, int on_device);
+
+/* Copies the current state out (layout above, context precision). */
+dh_status dh_get_state(dh_ctx* ctx, void* U_out, int on_device);
+
+/* One step (Sec. 2.1 update H): dt > 0 imposes the time step, dt <= 0 uses the CFL value of
+   App. A.4 computed on the device from the current state.  *dt_used (nullable) receives the dt
+   taken; reading it synchronises the stream. */
+dh_status dh_step(dh_ctx* ctx, double dt, double* dt_used);
+
+/* n_steps CFL steps with no host synchronisation between them; *t_out (nullable) receives the
+   simulation time afterwards.  Synchronises once at the end to report errors. */
+dh_status dh_advance(dh_ctx* ctx, int n_steps, double* t_out);
+
+/* Time and completed step count of the current state. */
+dh_status dh_get_time(dh_ctx* ctx, double* t, long long* nstep);
+
+/* CFL time step C * min_cells,axes dx_a / (|v_a| + c_s) of the current state (App. A.4). */
+dh_status dh_compute_dt(dh_ctx* ctx, double* dt);
+
+/* Sum over cells of each conserved field, accumulated in float64 on the device
+   (deterministic order).  out[5] is a host array. */
+dh_status dh_conserved_totals(dh_ctx* ctx, double out[5]);
+
+/* Normalised forcing acceleration a(x) of the most recent forcing update (Sec. 3.1.1), three
+   planes (a_x, a_y, a_z) in the state layout and context precision.  DH_ERR_STATE if forcing
+   is off. */
+dh_status dh_forcing_field(dh_ctx* ctx, void* a_out, int on_device);
+
+/* Forcing mode table a_hat[m][c] (16 modes x 3 components, unnormalised) as interleaved
+   (re, im) float64 pairs: out[2*(3*m + c) + {0,1}].  Modes are the half-space
+   {1 <= |n|^2 <= 4, first nonzero component of n positive} in lexicographic (n_x, n_y, n_z)
+   order. */
+dh_status dh_forcing_modes(dh_ctx* ctx, double out[96]);
+
+/* Gravitational potential phi of the last solve (one plane, float64, state index order),
+   and the cycles / final relative residual of that solve (nullable outputs). */
+dh_status dh_get_potential(dh_ctx* ctx, double* phi_out, int on_device, int* cycles,
+                           double* rel_residual);
+
+/* Reverse-mode product through n_steps steps (hand adjoint, App. A.3 stages transposed; dt of
+   every step frozen at the value the forward took, App. A.4): given the current state U^0,
+   runs the forward n_steps CFL steps (storing U every `ckpt_every` steps, Sec. 2.3
+   checkpointing), then returns dL/dU^0 in dLdU0 for dL/dU^{n} = dLdU_final.  Both buffers use
+   the state layout and precision; the context state is left at U^{n}.  Hydrodynamics only:
+   DH_ERR_ARG if forcing, cooling or gravity is on. */
+dh_status dh_adjoint_advance(dh_ctx* ctx, int n_steps, int ckpt_every, const void* dLdU_final,
+                             void* dLdU0, int on_device);
+
+/* Profiling: when enabled, device time of every kernel launch is accumulated per kernel kind
+   with CUDA events on the context stream.  dh_profile_read returns, for kernel kind `kind`
+   (see DH_KERNEL_*), the number of launches and their total milliseconds since the last
+   enable.  dh_launch_count returns the number of library kernels launched since creation. */
+enum {
+  DH_KERNEL_STAGE1 = 0, DH_KERNEL_STAGE2 = 1, DH_KERNEL_PROLOGUE = 2, DH_KERNEL_REDUCE = 3,
+  DH_KERNEL_SOURCES = 4, DH_KERNEL_MG = 5, DH_KERNEL_ADJOINT = 6, DH_KERNEL_CONV = 7,
+  DH_KERNEL_KINDS = 8
+};
+dh_status dh_profile_enable(dh_ctx* ctx, int enable);
+dh_status dh_profile_read(dh_ctx* ctx, int kind, long long* launches, double* total_ms);
+dh_status dh_launch_count(dh_ctx* ctx, long long* launches);
+
+/* Message of the most recent failure on ctx (or of the last failed dh_create when ctx is
+   NULL); owned by the library, valid until the next call on the same context. */
+const char* dh_last_error(const dh_ctx* ctx);
+
+/* Name of a status code. */
+const char* dh_status_string(dh_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DH_H */

@@ -1,0 +1,94 @@
+"""ctypes binding of libdh.so (include/dh.h): argument marshalling only.
+
+Every function keeps the C name and signature; all numerical work happens in the CUDA library.
+Loading fails loudly if the library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdh.so")
+
+DH_OK, DH_ERR_ARG, DH_ERR_CUDA, DH_ERR_NONFINITE, DH_ERR_POSITIVITY, DH_ERR_MG_NOCONV, DH_ERR_STATE = range(7)
+DH_F32, DH_F64 = 0, 1
+KERNEL_KINDS = {"stage1": 0, "stage2": 1, "prologue": 2, "reduce": 3, "sources": 4, "mg": 5,
+                "adjoint": 6, "conv": 7}
+
+
+class DhConfig(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("precision", C.c_int),
+        ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+        ("gamma", C.c_double), ("cfl", C.c_double), ("dt_max", C.c_double),
+        ("forcing", C.c_int), ("ou_tau", C.c_double), ("ou_arms", C.c_double),
+        ("ou_seed", C.c_ulonglong),
+        ("cooling", C.c_int), ("t_floor", C.c_double), ("cool_frac", C.c_double),
+        ("nsub_max", C.c_int),
+        ("gravity", C.c_int), ("four_pi_G", C.c_double), ("mg_tol", C.c_double),
+        ("mg_max_cycles", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
+    ]
+
+
+_P = C.c_void_p
+_SIGNATURES = {
+    "dh_config_default": (None, [C.POINTER(DhConfig), C.c_int, C.c_int, C.c_int]),
+    "dh_create": (C.c_int, [C.POINTER(DhConfig), _P, C.POINTER(_P)]),
+    "dh_destroy": (None, [_P]),
+    "dh_init_state": (C.c_int, [_P, _P, C.c_int]),
+    "dh_get_state": (C.c_int, [_P, _P, C.c_int]),
+    "dh_step": (C.c_int, [_P, C.c_double, C.POINTER(C.c_double)]),
+    "dh_advance": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double)]),
+    "dh_get_time": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "dh_compute_dt": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "dh_conserved_totals": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "dh_forcing_field": (C.c_int, [_P, _P, C.c_int]),
+    "dh_forcing_modes": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "dh_get_potential": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "dh_adjoint_advance": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
+    "dh_profile_enable": (C.c_int, [_P, C.c_int]),
+    "dh_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
+    "dh_launch_count": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
+    "dh_last_error": (C.c_char_p, [_P]),
+    "dh_status_string": (C.c_char_p, [C.c_int]),
+}
+
+_lib = None
+
+
+def exported_names():
+    return list(_SIGNATURES)
+
+
+def load(path: str = LIB_PATH):
+    """Loads libdh.so (raises if it is absent) and declares every exported signature."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class DhError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+
+
+def status_name(s: int) -> str:
+    return load().dh_status_string(s).decode()
+
+
+def check(status: int, ctx=None):
+    if status != DH_OK:
+        msg = load().dh_last_error(ctx).decode(errors="replace")
+        raise DhError(status, msg)

@@ -1,0 +1,59 @@
+// Context layout and internal hooks shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/dh.h"
+#include "dh_kernels.h"
+
+struct dh_ctx {
+  dh_config cfg;
+  int prec = DH_F32;
+  cudaStream_t stream = nullptr;
+  long long n3 = 0;
+  size_t state_bytes = 0;
+  void* U[2] = {nullptr, nullptr};   // ping-pong state buffers
+  int cur = 0;                       // index of the current state
+  void* U1 = nullptr;                // RK2 intermediate stage
+  dh::StepRecord* rec = nullptr;     // device step record
+  dh::StepRecord host_rec{};         // host copy after the last synchronisation
+  int pending_steps = 0;             // steps enqueued since the last synchronisation
+  double* ahat = nullptr;            // OU mode table (96 doubles), unnormalised
+  double* ahat_prev = nullptr;       // table before the last update (rollback)
+  void* ahat_norm = nullptr;         // normalised table in the working precision
+  void* tw[3] = {nullptr, nullptr, nullptr};  // per-axis forcing twiddles
+  double* partials = nullptr;        // totals: per-block partial sums
+  double* totals = nullptr;          // totals: 5 doubles
+  bool initialized = false;
+  std::string err;
+  // profiling
+  bool prof_on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  std::vector<int> prof_kinds;
+  double prof_ms[DH_KERNEL_KINDS] = {0};
+  long long prof_count[DH_KERNEL_KINDS] = {0};
+  long long launches = 0;
+  // multigrid (gravity)
+  struct MG* mg = nullptr;
+  // adjoint work space
+  struct AdjointSpace* adj = nullptr;
+};
+
+namespace dh {
+void prof_begin(dh_ctx* c, int kind);
+void prof_end(dh_ctx* c, int launches);
+void prof_fold(dh_ctx* c);
+
+// multigrid.cu
+std::string mg_validate(const dh_config& c);
+cudaError_t mg_allocate(dh_ctx* c);
+void mg_setup_host(dh_ctx* c);
+cudaError_t mg_reset(dh_ctx* c);
+void mg_free(dh_ctx* c);
+template <typename real> cudaError_t gravity_sources(dh_ctx* c, void* Ustar);
+
+// adjoint.cu
+void adjoint_free(dh_ctx* c);
+}  // namespace dh

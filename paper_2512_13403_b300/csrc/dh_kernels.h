@@ -1,0 +1,58 @@
+// Host-side launchers of the library's kernels (implemented in hydro.cu and friends).
+#pragma once
+#include <cuda_runtime.h>
+#include "dh_device.cuh"
+
+namespace dh {
+
+// Everything a stage launch needs; pointers are device pointers of the working precision.
+template <typename real> struct StageArgs {
+  const real* U;        // stage input: U^n (stage 1) or U1 (stage 2)
+  const real* U0;       // U^n (stage 2 only)
+  real* out;            // U1 (stage 1) or U^{n+1} (stage 2)
+  int nx, ny, nz;
+  real gamma, gm1;
+  real idx, idy, idz;   // inverse cell widths
+  real dx, dy, dz;      // cell widths (CFL reduction)
+  StepRecord* rec;
+  // fused sources (stage 2 only)
+  int forcing, cooling;
+  const real* ahat_norm;  // 16 modes x 3 comps x (re, im), normalised
+  const real* tw[3];      // per-axis twiddles: for cell i, (cos t, sin t, cos 2t, sin 2t), t = 2 pi (i+1/2)/n
+  real t_floor, cool_frac;
+  int nsub_max;
+  int reduce_cfl;         // accumulate the CFL minimum of the output state
+};
+
+template <typename real>
+cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s);
+
+struct BeginArgs {
+  StepRecord* rec;
+  double dt_fixed, cfl, dt_max;
+  int precision;            // 0 float, 1 double
+  int forcing;
+  double* ahat;             // 96 doubles (re, im) — unnormalised OU state
+  double* ahat_prev;        // copy before this step's update
+  void* ahat_norm;          // 96 reals of the working precision
+  unsigned long long seed;
+  double tau, arms;
+};
+cudaError_t launch_step_begin(const BeginArgs& a, cudaStream_t s);
+cudaError_t launch_forcing_init(double* ahat, unsigned long long seed, cudaStream_t s);
+
+template <typename real>
+cudaError_t launch_cfl_reduce(const real* U, int nx, int ny, int nz, real gamma, real dx, real dy,
+                              real dz, StepRecord* rec, cudaStream_t s);
+
+template <typename real>
+cudaError_t launch_totals(const real* U, long long n3, double* partials, int nblocks,
+                          double* out5, cudaStream_t s);
+
+template <typename real>
+cudaError_t launch_forcing_field(const real* ahat_norm, const real* const tw[3], int nx, int ny,
+                                 int nz, real* a_out, cudaStream_t s);
+
+int totals_blocks();
+
+}  // namespace dh

@@ -1,0 +1,677 @@
+// Fused finite-volume stage kernel and its small companions (step prologue, reductions).
+//
+// One launch of stage_kernel computes a full SSP-RK2 stage (App. A.3) for a block of cells:
+// primitive recovery (Eq. 2), MC-limited MUSCL face states (App. A.1), HLLC fluxes (App. A.2)
+// on every face of the block, the unsplit divergence and the stage combination.  The second
+// stage also applies the operator-split sources in place — OU forcing (Sec. 3.1.1) then cooling
+// (Sec. 4.3) — and reduces the CFL minimum of the new state for the next step (App. A.4).
+//
+// Blocking: a CTA owns a BX x BY column of cells and marches along z through a chunk of
+// planes.  Primitive planes (with a two-cell x/y halo) sit in a three-plane shared-memory ring
+// (k, k+1, k+2); every x and y face of plane k is evaluated exactly once per CTA by a linear
+// face loop, and the z faces come from a per-thread register pipeline (each z face once).
+#include <math.h>
+#include "dh_kernels.h"
+
+namespace dh {
+
+constexpr int BX = 32, BY = 8, HX = BX + 4, HY = BY + 4;
+constexpr int NTHREADS = BX * BY;
+constexpr int NXF = (BX + 1) * BY;   // x faces of a plane tile
+constexpr int NYF = BX * (BY + 1);   // y faces of a plane tile
+
+template <typename real> struct StageSmem {
+  real w[3][5][HY][HX];     // primitive planes ring
+  real fx[5][BY][BX + 1];   // x-face fluxes of the current plane
+  real fy[5][BY + 1][BX];   // y-face fluxes of the current plane
+  int xs[HX];               // wrapped global x of each smem column
+  int ys[HY];               // wrapped global y of each smem row
+  real red[NTHREADS / 32];  // CFL reduction scratch
+};
+
+// ---------------------------------------------------------------------------------------------
+// Forced-mode table of Sec. 3.1.1 as compile-time data: the half-space of integer n with
+// 1 <= |n|^2 <= 4 whose first nonzero component is positive, lexicographic in (n_x, n_y, n_z).
+__host__ __device__ constexpr int forced_mode_component(int m, int axis) {
+  int count = 0;
+  for (int a = -2; a <= 2; ++a)
+    for (int b = -2; b <= 2; ++b)
+      for (int c = -2; c <= 2; ++c) {
+        const int k2 = a * a + b * b + c * c;
+        const int first = a != 0 ? a : (b != 0 ? b : c);
+        if (k2 >= 1 && k2 <= 4 && first > 0) {
+          if (count == m) return axis == 0 ? a : (axis == 1 ? b : c);
+          ++count;
+        }
+      }
+  return 0;
+}
+static_assert(forced_mode_component(15, 0) == 2 && forced_mode_component(0, 2) == 1,
+              "forced mode enumeration");
+
+template <typename real> struct C2 { real re, im; };
+
+template <typename real>
+__device__ __forceinline__ C2<real> cmul(C2<real> a, C2<real> b) {
+  return C2<real>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// exp(2 pi i n x~) for one axis from its twiddles (n in -2..2, n != 0).
+template <typename real, int N>
+__device__ __forceinline__ C2<real> axis_factor(const real* t) {
+  static_assert(N != 0, "");
+  constexpr int A = N > 0 ? N : -N;
+  const real c = A == 1 ? t[0] : t[2];
+  const real s = A == 1 ? t[1] : t[3];
+  return C2<real>{c, N > 0 ? s : -s};
+}
+
+template <typename real, int M>
+__device__ __forceinline__ void add_mode(const real* __restrict__ ah, const real* tx,
+                                         const real* ty, const real* tz, real acc[3]) {
+  constexpr int NX = forced_mode_component(M, 0);
+  constexpr int NY = forced_mode_component(M, 1);
+  constexpr int NZ = forced_mode_component(M, 2);
+  C2<real> e{real(1), real(0)};
+  bool first = true;
+  if constexpr (NX != 0) { e = axis_factor<real, NX>(tx); first = false; }
+  if constexpr (NY != 0) {
+    const C2<real> f = axis_factor<real, NY>(ty);
+    e = first ? f : cmul(e, f);
+    first = false;
+  }
+  if constexpr (NZ != 0) {
+    const C2<real> f = axis_factor<real, NZ>(tz);
+    e = first ? f : cmul(e, f);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const real are = __ldg(ah + 2 * (3 * M + c));
+    const real aim = __ldg(ah + 2 * (3 * M + c) + 1);
+    acc[c] += are * e.re - aim * e.im;
+  }
+}
+
+template <typename real, int M>
+__device__ __forceinline__ void add_modes(const real* ah, const real* tx, const real* ty,
+                                          const real* tz, real acc[3]) {
+  if constexpr (M < 16) {
+    add_mode<real, M>(ah, tx, ty, tz, acc);
+    add_modes<real, M + 1>(ah, tx, ty, tz, acc);
+  }
+}
+
+// a(x) = 2 Re sum_H a_hat_n exp(2 pi i n . x~), with the normalised table (Sec. 3.1.1).
+template <typename real>
+__device__ __forceinline__ void forcing_accel(const real* ah, const real* const tw[3], int i,
+                                              int j, int k, real a[3]) {
+  real tx[4], ty[4], tz[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    tx[q] = __ldg(tw[0] + 4 * i + q);
+    ty[q] = __ldg(tw[1] + 4 * j + q);
+    tz[q] = __ldg(tw[2] + 4 * k + q);
+  }
+  real acc[3] = {real(0), real(0), real(0)};
+  add_modes<real, 0>(ah, tx, ty, tz, acc);
+  a[0] = real(2) * acc[0];
+  a[1] = real(2) * acc[1];
+  a[2] = real(2) * acc[2];
+}
+
+// Cooling of one cell (Sec. 4.3; Lambda = n^2 T^(1/2), T = P / rho, floor rho T_floor/(gamma-1)).
+template <typename real>
+__device__ __forceinline__ real cooling_energy(real r, real mx, real my, real mz, real E, real dt,
+                                               real gm1, real T_floor, real frac, int nsub_max,
+                                               unsigned& flags) {
+  const real kin = real(0.5) * (mx * mx + my * my + mz * mz) / r;
+  const real Eth = E - kin;
+  const real T = gm1 * Eth / r;
+  if (!(T > T_floor)) return E;
+  const real Efl = r * T_floor / gm1;
+  const real r2 = r * r;
+  const real Ed0 = -r2 * sqrt(T);
+  const real tcool = Eth / (-Ed0);
+  const real raw = ceil(dt / (frac * tcool));
+  // clamp to [1, nsub_max]; a NaN count also takes the cap, so the loop below is always bounded
+  real nsub = raw;
+  if (!(raw <= real(nsub_max))) {
+    if (raw > real(nsub_max)) flags |= FLAG_COOL_CAP;
+    nsub = real(nsub_max);
+  }
+  if (!(nsub >= real(1))) nsub = real(1);
+  real Enew;
+  if (nsub == real(1)) {
+    const real Ep = fmax(Efl, Eth + dt * Ed0);
+    const real Tp = gm1 * Ep / r;
+    const real Edp = Tp > T_floor ? -r2 * sqrt(Tp) : real(0);
+    Enew = fmax(Efl, Eth + real(0.5) * dt * (Ed0 + Edp));
+  } else {
+    const real dts = dt / nsub;
+    const int n = (int)nsub;
+    real Es = Eth;
+    for (int q = 0; q < n; ++q) {
+      const real Tq = gm1 * Es / r;
+      const real ed = Tq > T_floor ? -r2 * sqrt(Tq) : real(0);
+      Es = fmax(Efl, Es + ed * dts);
+    }
+    Enew = Es;
+  }
+  return kin + Enew;
+}
+
+template <typename real>
+__device__ __forceinline__ real cfl_time(real r, real mx, real my, real mz, real E, real gamma,
+                                         real gm1, real dx, real dy, real dz) {
+  const Prim<real> w = cons_to_prim(r, mx, my, mz, E, gm1);
+  const real c = sqrt(gamma * w.p / w.r);
+  const real tx = dx / (fabs(w.vx) + c);
+  const real ty = dy / (fabs(w.vy) + c);
+  const real tz = dz / (fabs(w.vz) + c);
+  return fmin(fmin(tx, ty), tz);
+}
+
+template <typename real>
+__device__ __forceinline__ Prim<real> smem_prim(const StageSmem<real>& S, int slot, int sy,
+                                                int sx) {
+  return Prim<real>{S.w[slot][0][sy][sx], S.w[slot][1][sy][sx], S.w[slot][2][sy][sx],
+                    S.w[slot][3][sy][sx], S.w[slot][4][sy][sx]};
+}
+
+template <typename real>
+__device__ __forceinline__ Prim<real> load_prim(const real* __restrict__ U, long long n3,
+                                                long long idx, real gm1) {
+  return cons_to_prim(__ldg(U + idx), __ldg(U + n3 + idx), __ldg(U + 2 * n3 + idx),
+                      __ldg(U + 3 * n3 + idx), __ldg(U + 4 * n3 + idx), gm1);
+}
+
+template <typename real, int STAGE>
+__global__ void __launch_bounds__(NTHREADS)
+stage_kernel(const StageArgs<real> p, const int zchunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StageSmem<real>& S = *reinterpret_cast<StageSmem<real>*>(smem_raw);
+  const int tid = threadIdx.x;
+  // Skip the stage after a fatal failure.  One thread reads the flag and the CTA follows it, so
+  // a flag raised by another CTA mid-launch cannot split this CTA across a barrier.
+  __shared__ unsigned s_skip;
+  if (tid == 0) s_skip = *((volatile unsigned*)&p.rec->flags) & FATAL_FLAGS;
+  __syncthreads();
+  if (s_skip) return;
+
+  const int tx = tid & (BX - 1), ty = tid / BX;
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const long long plane = (long long)nx * ny;
+  const long long n3 = plane * nz;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, nz);
+  const real dt = (real)p.rec->dt;
+  const real gamma = p.gamma, gm1 = p.gm1;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool active = gx < nx && gy < ny;
+  const int gxw = gx % nx, gyw = gy % ny;
+
+  if (tid < HX) S.xs[tid] = ((x0 + tid - 2) % nx + nx) % nx;
+  if (tid >= 64 && tid < 64 + HY) S.ys[tid - 64] = ((y0 + tid - 64 - 2) % ny + ny) % ny;
+  __syncthreads();
+
+  auto load_plane = [&](int k, int slot) {
+    const long long zoff = (long long)wrap(k, nz) * plane;
+    for (int c = tid; c < HX * HY; c += NTHREADS) {
+      const int sy = c / HX, sx = c - sy * HX;
+      const long long idx = zoff + (long long)S.ys[sy] * nx + S.xs[sx];
+      const Prim<real> w = load_prim(p.U, n3, idx, gm1);
+      S.w[slot][0][sy][sx] = w.r;
+      S.w[slot][1][sy][sx] = w.vx;
+      S.w[slot][2][sy][sx] = w.vy;
+      S.w[slot][3][sy][sx] = w.vz;
+      S.w[slot][4][sy][sx] = w.p;
+    }
+  };
+
+  // Prologue: planes z0, z0+1 in the ring; the own column's z0-2, z0-1 in registers.
+  load_plane(z0, 0);
+  load_plane(z0 + 1, 1);
+  const long long col = (long long)gyw * nx + gxw;
+  const Prim<real> wm2 = load_prim(p.U, n3, (long long)wrap(z0 - 2, nz) * plane + col, gm1);
+  const Prim<real> wm1 = load_prim(p.U, n3, (long long)wrap(z0 - 1, nz) * plane + col, gm1);
+  __syncthreads();
+  Prim<real> dk;          // z slope of the own cell at plane k
+  real fz_lo[5];          // z flux on face k - 1/2
+  {
+    const Prim<real> w0 = smem_prim(S, 0, ty + 2, tx + 2);
+    const Prim<real> w1 = smem_prim(S, 1, ty + 2, tx + 2);
+    const Prim<real> dm1 = limited_slope(wm2, wm1, w0);
+    dk = limited_slope(wm1, w0, w1);
+    face_flux(2, add_half(wm1, dm1, real(1)), add_half(w0, dk, real(-1)), gamma, gm1, fz_lo);
+  }
+
+  real tmin = real(INFINITY);
+  unsigned flags = 0;
+
+  for (int k = z0; k < z1; ++k) {
+    const int s0 = (k - z0) % 3, s1 = (k - z0 + 1) % 3, s2 = (k - z0 + 2) % 3;
+    load_plane(k + 2, s2);
+    __syncthreads();
+
+    // z face k+1/2 of the own column
+    real fz_hi[5];
+    Prim<real> dk1;
+    {
+      const Prim<real> w0 = smem_prim(S, s0, ty + 2, tx + 2);
+      const Prim<real> w1 = smem_prim(S, s1, ty + 2, tx + 2);
+      const Prim<real> w2 = smem_prim(S, s2, ty + 2, tx + 2);
+      dk1 = limited_slope(w0, w1, w2);
+      face_flux(2, add_half(w0, dk, real(1)), add_half(w1, dk1, real(-1)), gamma, gm1, fz_hi);
+    }
+
+    // every x and y face of plane k, once
+    for (int f = tid; f < NXF + NYF; f += NTHREADS) {
+      if (f < NXF) {
+        const int ly = f / (BX + 1), a = f - ly * (BX + 1);
+        const int sy = ly + 2;
+        const Prim<real> w0 = smem_prim(S, s0, sy, a);
+        const Prim<real> w1 = smem_prim(S, s0, sy, a + 1);
+        const Prim<real> w2 = smem_prim(S, s0, sy, a + 2);
+        const Prim<real> w3 = smem_prim(S, s0, sy, a + 3);
+        const Prim<real> dL = limited_slope(w0, w1, w2);
+        const Prim<real> dR = limited_slope(w1, w2, w3);
+        real F[5];
+        face_flux(0, add_half(w1, dL, real(1)), add_half(w2, dR, real(-1)), gamma, gm1, F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) S.fx[c][ly][a] = F[c];
+      } else {
+        const int g = f - NXF;
+        const int a = g / BX, lx = g - a * BX;
+        const int sx = lx + 2;
+        const Prim<real> w0 = smem_prim(S, s0, a, sx);
+        const Prim<real> w1 = smem_prim(S, s0, a + 1, sx);
+        const Prim<real> w2 = smem_prim(S, s0, a + 2, sx);
+        const Prim<real> w3 = smem_prim(S, s0, a + 3, sx);
+        const Prim<real> dL = limited_slope(w0, w1, w2);
+        const Prim<real> dR = limited_slope(w1, w2, w3);
+        real F[5];
+        face_flux(1, add_half(w1, dL, real(1)), add_half(w2, dR, real(-1)), gamma, gm1, F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) S.fy[c][a][lx] = F[c];
+      }
+    }
+    __syncthreads();
+
+    if (active) {
+      const long long idx = (long long)k * plane + col;
+      real u[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        real L = -((S.fx[c][ty][tx + 1] - S.fx[c][ty][tx]) * p.idx);
+        L -= (S.fy[c][ty + 1][tx] - S.fy[c][ty][tx]) * p.idy;
+        L -= (fz_hi[c] - fz_lo[c]) * p.idz;
+        const real uin = __ldg(p.U + c * n3 + idx);
+        if (STAGE == 1) {
+          u[c] = uin + dt * L;
+        } else {
+          const real un = __ldg(p.U0 + c * n3 + idx);
+          u[c] = real(0.5) * un + real(0.5) * (uin + dt * L);
+        }
+      }
+      if (STAGE == 2) {
+        if (p.forcing) {
+          real a[3];
+          forcing_accel(p.ahat_norm, p.tw, gx, gy, k, a);
+          const real e = (u[1] * a[0] + u[2] * a[1] + u[3] * a[2]) * dt;
+          u[1] = u[1] + u[0] * a[0] * dt;
+          u[2] = u[2] + u[0] * a[1] * dt;
+          u[3] = u[3] + u[0] * a[2] * dt;
+          u[4] = u[4] + e;
+        }
+        if (p.cooling)
+          u[4] = cooling_energy(u[0], u[1], u[2], u[3], u[4], dt, gm1, p.t_floor, p.cool_frac,
+                                p.nsub_max, flags);
+        bool finite = true;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) finite = finite && isfinite(u[c]);
+        if (!finite) {
+          flags |= FLAG_NONFINITE;
+        } else {
+          const real pr = gm1 * (u[4] - real(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0]);
+          if (!(u[0] > real(0)) || !(pr > real(0))) flags |= FLAG_POSITIVITY;
+          if (p.reduce_cfl)
+            tmin = fmin(tmin, cfl_time(u[0], u[1], u[2], u[3], u[4], gamma, gm1, p.dx, p.dy, p.dz));
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) p.out[c * n3 + idx] = u[c];
+    }
+    dk = dk1;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) fz_lo[c] = fz_hi[c];
+  }
+
+  if (STAGE == 2) {
+    if (flags) {
+      atomicOr(&p.rec->flags, flags);
+      if (flags & FATAL_FLAGS) atomicCAS(&p.rec->fail_step, -1, (int)(p.rec->nstep - 1));
+    }
+    if (p.reduce_cfl) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+      __syncthreads();
+      if ((tid & 31) == 0) S.red[tid >> 5] = tmin;
+      __syncthreads();
+      if (tid == 0) {
+        real m = S.red[0];
+        for (int w = 1; w < NTHREADS / 32; ++w) m = fmin(m, S.red[w]);
+        if (m < real(INFINITY)) atomicMin(&p.rec->cfl_min_bits, ordered_bits(m));
+      }
+    }
+  }
+}
+
+static int stage_zchunk(int nx, int ny, int nz) {
+  const long long tiles = (long long)((nx + BX - 1) / BX) * ((ny + BY - 1) / BY);
+  // aim for >= ~8 CTAs per SM over 148 SMs, with chunks of at least 8 planes
+  int chunks = (int)((148LL * 8 + tiles - 1) / tiles);
+  if (chunks < 1) chunks = 1;
+  int zc = (nz + chunks - 1) / chunks;
+  if (zc < 8) zc = 8;
+  if (zc > nz) zc = nz;
+  return zc;
+}
+
+template <typename real>
+cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s) {
+  const int zc = stage_zchunk(a.nx, a.ny, a.nz);
+  dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + zc - 1) / zc);
+  const size_t smem = sizeof(StageSmem<real>);
+  cudaError_t e;
+  if (stage == 1) {
+    e = cudaFuncSetAttribute(stage_kernel<real, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    stage_kernel<real, 1><<<grid, NTHREADS, smem, s>>>(a, zc);
+  } else {
+    e = cudaFuncSetAttribute(stage_kernel<real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    stage_kernel<real, 2><<<grid, NTHREADS, smem, s>>>(a, zc);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_stage<float>(int, const StageArgs<float>&, cudaStream_t);
+template cudaError_t launch_stage<double>(int, const StageArgs<double>&, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------------
+// OU forcing draws (Sec. 3.1.1): counter-based SplitMix64 stream, Box-Muller pairs.
+// key = splitmix64(seed); word i = splitmix64(key + i * golden); draw d, mode m, component c
+// uses words 2*((16 d + m) * 3 + c) and the next one.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double unit_uniform(unsigned long long w) {
+  return ((double)(w >> 11) + 0.5) * 0x1.0p-53;
+}
+
+// Projected Gaussian draw eta (re, im) for lane (m, c) of draw d.  Every thread of the block
+// calls this (it synchronises); lanes >= 48 only take part in the barrier.
+__device__ void projected_draw(unsigned long long seed, long long d, int lane_in, double* sre,
+                               double* sim, double& ere, double& eim) {
+  const bool writer = lane_in < 48;
+  const int lane = writer ? lane_in : 47;
+  const int m = lane / 3, c = lane - 3 * m;
+  const unsigned long long key = splitmix64(seed);
+  const unsigned long long i0 = 2ull * (unsigned long long)((d * 16 + m) * 3 + c);
+  const double u1 = unit_uniform(splitmix64(key + i0 * 0x9E3779B97F4A7C15ull));
+  const double u2 = unit_uniform(splitmix64(key + (i0 + 1) * 0x9E3779B97F4A7C15ull));
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  if (writer) {
+    sre[lane] = r * cs;
+    sim[lane] = r * sn;
+  }
+  __syncthreads();
+  int nv[3];
+  // mode vector of m (runtime lookup of the compile-time enumeration)
+  nv[0] = nv[1] = nv[2] = 0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    if (q == m) {
+      nv[0] = forced_mode_component(q, 0);
+      nv[1] = forced_mode_component(q, 1);
+      nv[2] = forced_mode_component(q, 2);
+    }
+  const double k2 = (double)(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+  double pre = 0.0, pim = 0.0;
+  for (int j = 0; j < 3; ++j) {
+    const double P = (c == j ? 1.0 : 0.0) - (double)nv[c] * (double)nv[j] / k2;
+    pre += P * sre[3 * m + j];
+    pim += P * sim[3 * m + j];
+  }
+  ere = pre;
+  eim = pim;
+}
+
+__global__ void forcing_init_kernel(double* ahat, unsigned long long seed) {
+  __shared__ double sre[48], sim[48];
+  const int lane = threadIdx.x;
+  double ere, eim;
+  projected_draw(seed, 0, lane, sre, sim, ere, eim);
+  if (lane < 48) {
+    ahat[2 * lane] = ere;
+    ahat[2 * lane + 1] = eim;
+  }
+}
+
+cudaError_t launch_forcing_init(double* ahat, unsigned long long seed, cudaStream_t s) {
+  forcing_init_kernel<<<1, 64, 0, s>>>(ahat, seed);
+  return cudaGetLastError();
+}
+
+template <typename real>
+__device__ void store_norm(void* out, int i, double v) {
+  reinterpret_cast<real*>(out)[i] = (real)v;
+}
+
+// Step prologue: choose dt (App. A.4 or the caller's), reset the CFL accumulator, advance the
+// OU table (Sec. 3.1.1) and its normalisation, then advance t and the step count.
+__global__ void step_begin_kernel(BeginArgs a) {
+  __shared__ double sre[48], sim[48], sq[64];
+  __shared__ double s_dt;
+  __shared__ unsigned s_skip;
+  StepRecord* rec = a.rec;
+  const int lane = threadIdx.x;
+  if (lane == 0) s_skip = *((volatile unsigned*)&rec->flags) & FATAL_FLAGS;
+  __syncthreads();
+  if (s_skip) return;
+  if (lane == 0) {
+    double dt = a.dt_fixed;
+    if (!(dt > 0.0)) {
+      const unsigned long long b = rec->cfl_min_bits;
+      const double m = a.precision == 0 ? (double)__uint_as_float((unsigned)b)
+                                        : __longlong_as_double((long long)b);
+      dt = fmin(a.cfl * m, a.dt_max);
+    }
+    s_dt = dt;
+  }
+  __syncthreads();
+  const double dt = s_dt;
+  if (a.forcing) {
+    double ere, eim;
+    projected_draw(a.seed, rec->nstep + 1, lane, sre, sim, ere, eim);
+    const double f = exp(-dt / a.tau);
+    const double g = sqrt(1.0 - f * f);
+    double nre = 0.0, nim = 0.0;
+    if (lane < 48) {
+      const double ore = a.ahat[2 * lane], oim = a.ahat[2 * lane + 1];
+      a.ahat_prev[2 * lane] = ore;
+      a.ahat_prev[2 * lane + 1] = oim;
+      nre = f * ore + g * ere;
+      nim = f * oim + g * eim;
+      a.ahat[2 * lane] = nre;
+      a.ahat[2 * lane + 1] = nim;
+    }
+    sq[lane] = nre * nre + nim * nim;
+    __syncthreads();
+    if (lane == 0) {
+      double s = 0.0;
+      for (int q = 0; q < 48; ++q) s += sq[q];
+      sq[0] = a.arms / sqrt(2.0 * s);
+      rec->ou_norm = sq[0];
+    }
+    __syncthreads();
+    const double scale = sq[0];
+    if (lane < 48) {
+      if (a.precision == 0) {
+        store_norm<float>(a.ahat_norm, 2 * lane, scale * nre);
+        store_norm<float>(a.ahat_norm, 2 * lane + 1, scale * nim);
+      } else {
+        store_norm<double>(a.ahat_norm, 2 * lane, scale * nre);
+        store_norm<double>(a.ahat_norm, 2 * lane + 1, scale * nim);
+      }
+    }
+  }
+  if (lane == 0) {
+    rec->dt = dt;
+    rec->cfl_min_bits = a.precision == 0 ? (unsigned long long)__float_as_uint(INFINITY)
+                                         : (unsigned long long)__double_as_longlong(INFINITY);
+    rec->t += dt;
+    rec->nstep += 1;
+  }
+}
+
+cudaError_t launch_step_begin(const BeginArgs& a, cudaStream_t s) {
+  step_begin_kernel<<<1, 64, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// CFL minimum of a state (App. A.4), used for the first step after init_state.
+template <typename real>
+__global__ void cfl_reduce_kernel(const real* __restrict__ U, long long n3, int nx, int ny,
+                                  real gamma, real gm1, real dx, real dy, real dz,
+                                  StepRecord* rec) {
+  __shared__ real red[8];
+  real m = real(INFINITY);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x) {
+    m = fmin(m, cfl_time(__ldg(U + i), __ldg(U + n3 + i), __ldg(U + 2 * n3 + i),
+                         __ldg(U + 3 * n3 + i), __ldg(U + 4 * n3 + i), gamma, gm1, dx, dy, dz));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x / 32); ++w) m = fmin(m, red[w]);
+    if (m < real(INFINITY)) atomicMin(&rec->cfl_min_bits, ordered_bits(m));
+  }
+}
+
+template <typename real>
+cudaError_t launch_cfl_reduce(const real* U, int nx, int ny, int nz, real gamma, real dx, real dy,
+                              real dz, StepRecord* rec, cudaStream_t s) {
+  const long long n3 = (long long)nx * ny * nz;
+  long long blocks = (n3 + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  cfl_reduce_kernel<real><<<(int)blocks, 256, 0, s>>>(U, n3, nx, ny, gamma, gamma - real(1), dx,
+                                                      dy, dz, rec);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cfl_reduce<float>(const float*, int, int, int, float, float, float,
+                                              float, StepRecord*, cudaStream_t);
+template cudaError_t launch_cfl_reduce<double>(const double*, int, int, int, double, double,
+                                               double, double, StepRecord*, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------------
+// Conserved totals in float64 with a fixed reduction order (two passes, no atomics).
+constexpr int TOTALS_BLOCKS = 296, TOTALS_THREADS = 256;
+int totals_blocks() { return TOTALS_BLOCKS; }
+
+template <typename real>
+__global__ void totals_partial_kernel(const real* __restrict__ U, long long n3,
+                                      double* __restrict__ partials) {
+  __shared__ double red[5][TOTALS_THREADS];
+  double s[5] = {0, 0, 0, 0, 0};
+  const long long per = (n3 + gridDim.x - 1) / gridDim.x;
+  const long long b0 = blockIdx.x * per;
+  const long long b1 = b0 + per < n3 ? b0 + per : n3;
+  for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) s[f] += (double)__ldg(U + f * n3 + i);
+  }
+#pragma unroll
+  for (int f = 0; f < 5; ++f) red[f][threadIdx.x] = s[f];
+  __syncthreads();
+  for (int w = TOTALS_THREADS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+#pragma unroll
+      for (int f = 0; f < 5; ++f) red[f][threadIdx.x] += red[f][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partials[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void totals_final_kernel(const double* __restrict__ partials, int nblocks,
+                                    double* __restrict__ out) {
+  const int f = threadIdx.x;
+  if (f < 5) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[b * 5 + f];
+    out[f] = s;
+  }
+}
+
+template <typename real>
+cudaError_t launch_totals(const real* U, long long n3, double* partials, int nblocks, double* out5,
+                          cudaStream_t s) {
+  totals_partial_kernel<real><<<nblocks, TOTALS_THREADS, 0, s>>>(U, n3, partials);
+  totals_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out5);
+  return cudaGetLastError();
+}
+template cudaError_t launch_totals<float>(const float*, long long, double*, int, double*,
+                                          cudaStream_t);
+template cudaError_t launch_totals<double>(const double*, long long, double*, int, double*,
+                                           cudaStream_t);
+
+// ---------------------------------------------------------------------------------------------
+template <typename real>
+__global__ void forcing_field_kernel(const real* __restrict__ ah, const real* tw0,
+                                     const real* tw1, const real* tw2, int nx, int ny, int nz,
+                                     real* __restrict__ out) {
+  const long long n3 = (long long)nx * ny * nz;
+  const real* tw[3] = {tw0, tw1, tw2};
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % nx);
+    const int j = (int)((q / nx) % ny);
+    const int k = (int)(q / ((long long)nx * ny));
+    real a[3];
+    forcing_accel(ah, tw, i, j, k, a);
+    out[q] = a[0];
+    out[n3 + q] = a[1];
+    out[2 * n3 + q] = a[2];
+  }
+}
+
+template <typename real>
+cudaError_t launch_forcing_field(const real* ahat_norm, const real* const tw[3], int nx, int ny,
+                                 int nz, real* a_out, cudaStream_t s) {
+  const long long n3 = (long long)nx * ny * nz;
+  long long blocks = (n3 + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  forcing_field_kernel<real><<<(int)blocks, 256, 0, s>>>(ahat_norm, tw[0], tw[1], tw[2], nx, ny,
+                                                         nz, a_out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_forcing_field<float>(const float*, const float* const[3], int, int,
+                                                 int, float*, cudaStream_t);
+template cudaError_t launch_forcing_field<double>(const double*, const double* const[3], int,
+                                                  int, int, double*, cudaStream_t);
+
+}  // namespace dh

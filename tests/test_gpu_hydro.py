@@ -1,0 +1,181 @@
+"""GPU parity of the hydro step through the C ABI against the FP64 CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import cooling as ocool
+from oracle import driver as odrv
+from oracle import forcing as oforce
+from oracle import hydro as ohydro
+from paper_2512_13403_b300 import inputs
+from tests.gpu_util import rel_l1, rel_linf, solver, to_gpu
+
+pytestmark = pytest.mark.gpu
+G = 5.0 / 3.0
+
+
+def _dx(shape):
+    nz, ny, nx = shape
+    return (1.0 / nx, 1.0 / ny, 1.0 / nz)
+
+
+def test_single_step_fp64_kh32():
+    shape = (32, 32, 32)
+    U0 = inputs.kelvin_helmholtz(shape, seed=0)
+    s = solver(shape, "f64")
+    s.init_state(to_gpu(U0, "f64"))
+    dt = ohydro.cfl_dt(torch.from_numpy(U0), G, _dx(shape), 0.4)
+    s.step(dt)
+    ref = ohydro.rk2_step(torch.from_numpy(U0), dt, G, _dx(shape))
+    assert max(rel_linf(s.get_state(), ref)) <= 1e-11
+
+
+@pytest.mark.parametrize("shape", [(20, 12, 40), (9, 17, 33), (8, 8, 70)])
+def test_ragged_tiles_fp64(shape):
+    U0 = inputs.decaying_turbulence(shape, seed=3, sigma=0.4, mach=1.0)
+    s = solver(shape, "f64")
+    s.init_state(to_gpu(U0, "f64"))
+    U = torch.from_numpy(U0)
+    for _ in range(3):
+        dt = s.step(0.0)
+        dto = ohydro.cfl_dt(U, G, _dx(shape), 0.4)
+        assert dt == pytest.approx(dto, rel=1e-13)
+        U = ohydro.rk2_step(U, dto, G, _dx(shape))
+    assert max(rel_linf(s.get_state(), U)) <= 1e-11
+
+
+def test_kh32_50_steps_fp64_and_fp32():
+    shape = (32, 32, 32)
+    U0 = inputs.kelvin_helmholtz(shape, seed=0)
+    sim = odrv.Simulation(odrv.Config(shape=shape), U0)
+    dts = sim.advance(50)
+    ref = sim.U
+    s64 = solver(shape, "f64")
+    s64.init_state(to_gpu(U0, "f64"))
+    t64 = s64.advance(50)
+    assert t64 == pytest.approx(sim.t, rel=1e-12)
+    assert max(rel_linf(s64.get_state(), ref)) <= 1e-11
+    # FP32 production path: dt schedule replayed, then self-computed dt
+    s32 = solver(shape, "f32")
+    s32.init_state(to_gpu(U0, "f32"))
+    for dt in dts:
+        s32.step(dt, sync=False)
+    assert max(rel_l1(s32.get_state(), ref)) <= 1e-5
+    s32b = solver(shape, "f32")
+    s32b.init_state(to_gpu(U0, "f32"))
+    s32b.advance(50)
+    assert max(rel_l1(s32b.get_state(), ref)) <= 1e-5
+
+
+def test_forcing_and_cooling_fp64():
+    shape = (16, 20, 24)
+    U0 = inputs.decaying_turbulence(shape, seed=9, sigma=0.5, mach=0.7, P0=0.6)
+    kw = dict(forcing=True, ou_tau=0.5, ou_arms=1.0, ou_seed=1, cooling=True, t_floor=0.05)
+    sim = odrv.Simulation(odrv.Config(shape=shape, forcing=True, cooling=True, ou_seed=1), U0)
+    s = solver(shape, "f64", **kw)
+    s.init_state(to_gpu(U0, "f64"))
+    # initial mode table: draw 0 of the counter-based stream, projected
+    assert np.abs(s.forcing_modes() - sim.ou.a_hat.numpy()).max() < 1e-14
+    for _ in range(4):
+        dt = s.step(0.0)
+        dto = sim.step()
+        assert dt == pytest.approx(dto, rel=1e-13)
+    assert np.abs(s.forcing_modes() - sim.ou.a_hat.numpy()).max() < 1e-13
+    a = s.forcing_field()
+    assert max(rel_linf(a, sim.ou.field(shape))) < 1e-12
+    assert max(rel_linf(s.get_state(), sim.U)) <= 1e-11
+
+
+def test_cooling_subcycling_branch_fp64():
+    """Dense hot cells force N_sub > 1; compare against the oracle's subcycled update."""
+    shape = (8, 8, 8)
+    rng = np.random.default_rng(4)
+    rho = np.exp(rng.normal(0, 1.0, shape)) * 5.0
+    P = np.full(shape, 3.0)
+    z = np.zeros(shape)
+    U0 = inputs.prim_to_state(rho, z + 0.1, z, z, P, G)
+    sim = odrv.Simulation(odrv.Config(shape=shape, cooling=True, t_floor=0.05), U0)
+    s = solver(shape, "f64", cooling=True, t_floor=0.05)
+    s.init_state(to_gpu(U0, "f64"))
+    dt = 0.01
+    nsub, _ = ocool.substep_count(torch.from_numpy(U0[4] - 0.5 * U0[1] ** 2 / U0[0]),
+                                  torch.from_numpy(U0[0]), dt, G, 0.05)
+    assert float(nsub.max()) > 1.0  # the subcycled branch is exercised
+    s.step(dt)
+    sim.step(dt)
+    assert max(rel_linf(s.get_state(), sim.U)) <= 1e-11
+
+
+def test_conserved_totals_fp64_and_fp32():
+    shape = (12, 16, 20)
+    U0 = inputs.kelvin_helmholtz(shape, seed=1)
+    for prec in ("f64", "f32"):
+        s = solver(shape, prec)
+        Ug = to_gpu(U0, prec)
+        s.init_state(Ug)
+        tot = s.conserved_totals()
+        exact = [math.fsum(Ug[f].double().cpu().reshape(-1).tolist()) for f in range(5)]
+        for f in range(5):
+            assert tot[f] == pytest.approx(exact[f], rel=1e-13, abs=1e-12)
+        s.advance(5)
+        tot2 = s.conserved_totals()
+        tol = 1e-12 if prec == "f64" else 2e-6
+        for f in (0, 4):
+            assert abs(tot2[f] - tot[f]) <= tol * abs(tot[f])
+
+
+def test_argument_and_state_errors():
+    from paper_2512_13403_b300._lib import DH_ERR_ARG, DH_ERR_STATE, DhError
+    with pytest.raises(DhError) as e:
+        solver((2, 8, 8), "f64")
+    assert e.value.status == DH_ERR_ARG
+    with pytest.raises(DhError) as e:
+        solver((8, 8, 8), "f64", forcing=True, ou_tau=-1.0)
+    assert e.value.status == DH_ERR_ARG
+    s = solver((8, 8, 8), "f64")
+    with pytest.raises(DhError) as e:
+        s.step(0.0)
+    assert e.value.status == DH_ERR_STATE
+
+
+def test_nonfinite_and_positivity_keep_last_good_state():
+    from paper_2512_13403_b300._lib import DH_ERR_NONFINITE, DH_ERR_POSITIVITY, DhError
+    shape = (8, 8, 16)
+    U0 = inputs.decaying_turbulence(shape, seed=1, sigma=0.3, mach=0.5)
+    s = solver(shape, "f64")
+    s.init_state(to_gpu(U0, "f64"))
+    s.advance(2)
+    good = s.get_state().clone()
+    t_good, n_good = s.time()
+    # host-side fault injection: a NaN in the uploaded state
+    bad = good.clone()
+    bad[4, 3, 3, 3] = float("nan")
+    s.init_state(bad)
+    with pytest.raises(DhError) as e:
+        s.step(1e-4)
+    assert e.value.status == DH_ERR_NONFINITE
+    assert torch.equal(s.get_state().isnan(), bad.isnan())
+    assert s.time() == (0.0, 0)
+    # negative pressure after a step: a huge dt on a strong rarefaction
+    s.init_state(good)
+    s.step(1e-4)
+    kept = s.get_state().clone()
+    with pytest.raises(DhError) as e:
+        s.step(10.0)
+    assert e.value.status in (DH_ERR_POSITIVITY, DH_ERR_NONFINITE)
+    assert torch.equal(s.get_state(), kept)
+    t, n = s.time()
+    assert n == 1 and t == pytest.approx(1e-4)
+    # the context stays usable
+    s.advance(2)
+
+
+def test_cfl_dt_matches_oracle():
+    shape = (10, 12, 14)
+    U0 = inputs.decaying_turbulence(shape, seed=8, mach=2.0)
+    s = solver(shape, "f64")
+    s.init_state(to_gpu(U0, "f64"))
+    assert s.compute_dt() == pytest.approx(ohydro.cfl_dt(torch.from_numpy(U0), G, _dx(shape), 0.4),
+                                           rel=1e-14)
