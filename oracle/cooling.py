@@ -4,10 +4,12 @@ Test infrastructure only.
 
 Readings (code units; mu m_H / k_B = 1 and R = 1):
   * n = rho, T = P / rho = (gamma - 1) E_th / rho, E_th = E - |m|^2 / (2 rho).
-  * dE_th/dt = -rho^2 sqrt(T) where T > T_floor, else 0; no heating.
-  * E_th floor = rho T_floor / (gamma - 1) (Sec. 4.3).  Cells at or below T_floor at the start of
-    the cooling step are left untouched; elsewhere every update is max(floor, ...), so cooling
-    never crosses the floor and never heats.
+  * E_th floor = rho T_floor / (gamma - 1) (Sec. 4.3).  dE_th/dt = -rho^2 sqrt(T) while
+    E_th > E_floor (T > T_floor), else 0; no heating.  The branch compares E_th with the floor
+    energy, so a state clamped to the floor (the predictor or a substep) stops cooling exactly,
+    independently of how T = (gamma-1) E_th / rho rounds.  Cells at or below the floor at the
+    start of the cooling step are left untouched; elsewhere every update is max(floor, ...), so
+    cooling never crosses the floor and never heats.
   * t_cool = E_th / |dE/dt| (Sec. 4.3).  N_sub = clamp(ceil(dt / (f t_cool)), 1, N_max) with
     f = 0.1, the maximum fractional change taken in the first substep, and N_max = 1024.
     N_sub = 1: trapezoid with predictor E_p = max(floor, E + dt Edot(E)),
@@ -26,10 +28,15 @@ import math
 import torch
 
 
+def floor_energy(rho: torch.Tensor, gamma: float, T_floor: float) -> torch.Tensor:
+    return rho * T_floor / (gamma - 1.0)
+
+
 def edot(Eth: torch.Tensor, rho: torch.Tensor, gamma: float, T_floor: float) -> torch.Tensor:
+    """-rho^2 sqrt(T) above the floor energy, 0 at or below it."""
     T = (gamma - 1.0) * Eth / rho
-    return torch.where(T > T_floor, -rho * rho * torch.sqrt(torch.clamp(T, min=0.0)),
-                       torch.zeros_like(T))
+    return torch.where(Eth > floor_energy(rho, gamma, T_floor),
+                       -rho * rho * torch.sqrt(torch.clamp(T, min=0.0)), torch.zeros_like(T))
 
 
 def substep_count(Eth, rho, dt, gamma, T_floor, frac=0.1, nsub_max=1024):
@@ -48,7 +55,7 @@ def cool(U: torch.Tensor, dt: float, gamma: float, T_floor: float, frac: float =
     rho = U[0]
     kin = 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho
     Eth = U[4] - kin
-    Efloor = rho * T_floor / (gamma - 1.0)
+    Efloor = floor_energy(rho, gamma, T_floor)
     Ed0 = edot(Eth, rho, gamma, T_floor)
     active = Ed0 < 0.0
     nsub, raw = substep_count(Eth, rho, dt, gamma, T_floor, frac, nsub_max)
