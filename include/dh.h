@@ -129,6 +129,13 @@ dh_status dh_forcing_modes(dh_ctx* ctx, double out[96]);
 dh_status dh_get_potential(dh_ctx* ctx, double* phi_out, int on_device, int* cycles,
                            double* rel_residual);
 
+/* Poisson solve of Sec. 5.2 on its own: F = four_pi_G (rho - <rho>) from one density plane
+   `rho` (state index order, context precision), red-black Gauss-Seidel V-cycles warm-started from
+   the context's potential until ||F - A phi||_2 / ||F||_2 <= mg_tol; the potential stays in the
+   context (read it with dh_get_potential).  Needs gravity on.  DH_ERR_MG_NOCONV if mg_max_cycles
+   cycles do not reach the tolerance (the potential is then the last iterate). */
+dh_status dh_solve_poisson(dh_ctx* ctx, const void* rho, int on_device);
+
 /* Reverse-mode product through n_steps steps (hand adjoint, App. A.3 stages transposed; dt of
    every step frozen at the value the forward took, App. A.4): given the current state U^0,
    runs the forward n_steps CFL steps (storing U every `ckpt_every` steps, Sec. 2.3

@@ -47,6 +47,7 @@ _SIGNATURES = {
     "dh_forcing_field": (C.c_int, [_P, _P, C.c_int]),
     "dh_forcing_modes": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "dh_get_potential": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "dh_solve_poisson": (C.c_int, [_P, _P, C.c_int]),
     "dh_adjoint_advance": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dh_profile_enable": (C.c_int, [_P, C.c_int]),
     "dh_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),

@@ -1,15 +1,456 @@
-// Hand adjoint of the RK2 step: placeholder until the adjoint stage kernels land.
+// Hand-written adjoint of the RK2 step (reverse of App. A.1-A.3, dt frozen per App. A.4) and
+// the checkpointed driver behind dh_adjoint_advance (Sec. 2.3: sparse stored states, segments
+// recomputed during the backward sweep).
+//
+// stage_adjoint_kernel computes, for one RK2 stage out = alpha U0 + beta (U + dt L(U)),
+//   lam_in = c1 lam_out + c2 extra + (dL/dU)^T mu,   mu = beta dt lam_out,
+// as a gather per cell: every face VJP of HLLC o reconstruction is evaluated once per CTA tile
+// (x and y faces in shared memory, z faces in a per-thread register pipeline), the limiter's
+// transposed stencil is gathered from the neighbouring cells, and the primitive-recovery
+// Jacobian is applied last.  No atomics; each output cell is written by one thread.
+//
+// Kink convention: the derivative of the branch the forward took; exact ties of min/max split
+// the derivative evenly between the tied arguments (the MC limiter and the Davis speeds).
+#include <math.h>
+#include <vector>
+
 #include "dh_internal.h"
+#include "dh_adjoint.cuh"
 
 namespace dh {
-void adjoint_free(dh_ctx*) {}
+
+constexpr int ABX = 32, ABY = 8;
+constexpr int ANT = ABX * ABY;
+constexpr int WX = ABX + 6, WY = ABY + 6;   // primitive planes, halo 3
+constexpr int MXH = ABX + 4, MYH = ABY + 4; // mu plane, halo 2
+constexpr int NFXA = ABX + 3;               // x faces per row: -3/2 .. BX+1/2
+constexpr int NFYA = ABY + 3;               // y faces per column
+constexpr int NCXA = ABX + 2;               // x cells per row for the slope terms: -1 .. BX
+constexpr int NCYA = ABY + 2;
+constexpr int FACE_SLOTS = (NFXA * ABY > NFYA * ABX) ? NFXA * ABY : NFYA * ABX;
+constexpr int CELL_SLOTS = (NCXA * ABY > NCYA * ABX) ? NCXA * ABY : NCYA * ABX;
+
+template <typename real> struct AdjSmem {
+  real w[4][5][WY][WX];
+  real mu[5][MYH][MXH];
+  real face[10][FACE_SLOTS];   // (gL[5], gR[5]) per face
+  real cell[10][CELL_SLOTS];   // (A[5], B[5]) per cell
+  int xs[WX], ys[WY];
+};
+
+template <typename real>
+__device__ __forceinline__ Prim<real> ring_prim(const AdjSmem<real>& S, int slot, int sy, int sx) {
+  return Prim<real>{S.w[slot][0][sy][sx], S.w[slot][1][sy][sx], S.w[slot][2][sy][sx],
+                    S.w[slot][3][sy][sx], S.w[slot][4][sy][sx]};
+}
+
+template <typename real>
+__device__ __forceinline__ Prim<real> gload_prim(const real* __restrict__ U, long long n3,
+                                                 long long idx, real gm1) {
+  return cons_to_prim(__ldg(U + idx), __ldg(U + n3 + idx), __ldg(U + 2 * n3 + idx),
+                      __ldg(U + 3 * n3 + idx), __ldg(U + 4 * n3 + idx), gm1);
+}
+
+template <typename real>
+__device__ __forceinline__ void gload5(const real* __restrict__ p, long long n3, long long idx,
+                                       real s, real out[5]) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) out[c] = s * __ldg(p + c * n3 + idx);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(ANT)
+stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AdjSmem<real>& S = *reinterpret_cast<AdjSmem<real>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int tx = tid & (ABX - 1), ty = tid / ABX;
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const long long plane = (long long)nx * ny;
+  const long long n3 = plane * nz;
+  const int x0 = blockIdx.x * ABX, y0 = blockIdx.y * ABY;
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, nz);
+  const real gamma = p.gamma, gm1 = p.gm1;
+  const real dt = (real)*p.dtp;
+  const real sdt = p.beta * dt;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool active = gx < nx && gy < ny;
+  const long long col = (long long)(gy % ny) * nx + (gx % nx);
+
+  if (tid < WX) S.xs[tid] = ((x0 + tid - 3) % nx + nx) % nx;
+  if (tid >= 64 && tid < 64 + WY) S.ys[tid - 64] = ((y0 + tid - 64 - 3) % ny + ny) % ny;
+  __syncthreads();
+
+  auto load_w = [&](int k, int slot) {
+    const long long zoff = (long long)wrap(k, nz) * plane;
+    for (int c = tid; c < WX * WY; c += ANT) {
+      const int sy = c / WX, sx = c - sy * WX;
+      const Prim<real> w = gload_prim(p.U, n3, zoff + (long long)S.ys[sy] * nx + S.xs[sx], gm1);
+      S.w[slot][0][sy][sx] = w.r;
+      S.w[slot][1][sy][sx] = w.vx;
+      S.w[slot][2][sy][sx] = w.vy;
+      S.w[slot][3][sy][sx] = w.vz;
+      S.w[slot][4][sy][sx] = w.p;
+    }
+  };
+  auto load_mu = [&](int k) {
+    const long long zoff = (long long)wrap(k, nz) * plane;
+    for (int c = tid; c < MXH * MYH; c += ANT) {
+      const int sy = c / MXH, sx = c - sy * MXH;
+      const long long idx = zoff + (long long)S.ys[sy + 1] * nx + S.xs[sx + 1];
+#pragma unroll
+      for (int f = 0; f < 5; ++f) S.mu[f][sy][sx] = sdt * __ldg(p.lam_out + f * n3 + idx);
+    }
+  };
+
+  // ---- prologue: ring planes z0..z0+2, own-column history below z0 -------------------------
+  load_w(z0, 0);
+  load_w(z0 + 1, 1);
+  load_w(z0 + 2, 2);
+  const Prim<real> wm3 = gload_prim(p.U, n3, (long long)wrap(z0 - 3, nz) * plane + col, gm1);
+  const Prim<real> wm2 = gload_prim(p.U, n3, (long long)wrap(z0 - 2, nz) * plane + col, gm1);
+  const Prim<real> wm1 = gload_prim(p.U, n3, (long long)wrap(z0 - 1, nz) * plane + col, gm1);
+  real mum2[5], mum1[5], mu0[5], mun[5];
+  gload5(p.lam_out, n3, (long long)wrap(z0 - 2, nz) * plane + col, sdt, mum2);
+  gload5(p.lam_out, n3, (long long)wrap(z0 - 1, nz) * plane + col, sdt, mum1);
+  gload5(p.lam_out, n3, (long long)wrap(z0, nz) * plane + col, sdt, mu0);
+  gload5(p.lam_out, n3, (long long)wrap(z0 + 1, nz) * plane + col, sdt, mun);
+  __syncthreads();
+
+  real gLn[5], gRc[5], gRn[5], Ap[5], Ac[5], Bc[5];
+  {
+    const Prim<real> w0 = ring_prim(S, 0, ty + 3, tx + 3);
+    const Prim<real> w1 = ring_prim(S, 1, ty + 3, tx + 3);
+    const Prim<real> w2 = ring_prim(S, 2, ty + 3, tx + 3);
+    real g[5], gLa[5], gRa[5], gLb[5], gRb[5], D[5], Bt[5];
+    // face z0-3/2
+    for (int c = 0; c < 5; ++c) g[c] = (mum1[c] - mum2[c]) * p.idz;
+    face_vjp(2, wm3, wm2, wm1, w0, g, gamma, gm1, gLa, gRa);
+    // face z0-1/2
+    for (int c = 0; c < 5; ++c) g[c] = (mu0[c] - mum1[c]) * p.idz;
+    face_vjp(2, wm2, wm1, w0, w1, g, gamma, gm1, gLb, gRb);
+    // A_{z0-1} from D = gL(z0-1/2)/2 - gR(z0-3/2)/2
+    for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gLb[c] - real(0.5) * gRa[c];
+    slope_vjp(wm2, wm1, w0, D, Ap, Bt);
+    // face z0+1/2
+    for (int c = 0; c < 5; ++c) g[c] = (mun[c] - mu0[c]) * p.idz;
+    face_vjp(2, wm1, w0, w1, w2, g, gamma, gm1, gLn, gRn);
+    for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gLn[c] - real(0.5) * gRb[c];
+    slope_vjp(wm1, w0, w1, D, Ac, Bc);
+    for (int c = 0; c < 5; ++c) gRc[c] = gRb[c];
+  }
+
+  for (int k = z0; k < z1; ++k) {
+    const int s0 = (k - z0) & 3, s1 = (k - z0 + 1) & 3, s2 = (k - z0 + 2) & 3, s3 = (k - z0 + 3) & 3;
+    load_w(k + 3, s3);
+    load_mu(k);
+    real mun2[5];
+    gload5(p.lam_out, n3, (long long)wrap(k + 2, nz) * plane + col, sdt, mun2);
+    __syncthreads();
+
+    real gW[5];
+    // ---- z: face k+3/2, slope terms of k+1, gather for k ------------------------------------
+    {
+      const Prim<real> w0 = ring_prim(S, s0, ty + 3, tx + 3);
+      const Prim<real> w1 = ring_prim(S, s1, ty + 3, tx + 3);
+      const Prim<real> w2 = ring_prim(S, s2, ty + 3, tx + 3);
+      const Prim<real> w3 = ring_prim(S, s3, ty + 3, tx + 3);
+      real g[5], gL2[5], gR2[5], D[5], An[5], Bn[5];
+      for (int c = 0; c < 5; ++c) g[c] = (mun2[c] - mun[c]) * p.idz;
+      face_vjp(2, w0, w1, w2, w3, g, gamma, gm1, gL2, gR2);
+      for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gL2[c] - real(0.5) * gRn[c];
+      slope_vjp(w0, w1, w2, D, An, Bn);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        gW[c] = (gLn[c] + gRc[c]) + Ap[c] - Ac[c] + Bc[c] - Bn[c];
+        gRc[c] = gRn[c];
+        gLn[c] = gL2[c];
+        gRn[c] = gR2[c];
+        Ap[c] = Ac[c];
+        Ac[c] = An[c];
+        Bc[c] = Bn[c];
+        mun[c] = mun2[c];
+      }
+    }
+
+    // ---- x: faces, slope terms, gather ------------------------------------------------------
+    for (int f = tid; f < NFXA * ABY; f += ANT) {
+      const int ly = f / NFXA, q = f - ly * NFXA;
+      const int sy = ly + 3;
+      real g[5], gL[5], gR[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][ly + 2][q + 1] - S.mu[c][ly + 2][q]) * p.idx;
+      face_vjp(0, ring_prim(S, s0, sy, q), ring_prim(S, s0, sy, q + 1), ring_prim(S, s0, sy, q + 2),
+               ring_prim(S, s0, sy, q + 3), g, gamma, gm1, gL, gR);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) { S.face[c][f] = gL[c]; S.face[5 + c][f] = gR[c]; }
+    }
+    __syncthreads();
+    for (int e = tid; e < NCXA * ABY; e += ANT) {
+      const int ly = e / NCXA, r = e - ly * NCXA;
+      const int sy = ly + 3;
+      real D[5], A[5], B[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        D[c] = real(0.5) * S.face[c][ly * NFXA + r + 1] - real(0.5) * S.face[5 + c][ly * NFXA + r];
+      slope_vjp(ring_prim(S, s0, sy, r + 1), ring_prim(S, s0, sy, r + 2), ring_prim(S, s0, sy, r + 3),
+                D, A, B);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) { S.cell[c][e] = A[c]; S.cell[5 + c][e] = B[c]; }
+    }
+    __syncthreads();
+    {
+      const int fb = ty * NFXA, cb = ty * NCXA;
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        gW[c] += (S.face[c][fb + tx + 2] + S.face[5 + c][fb + tx + 1]) + S.cell[c][cb + tx] -
+                 S.cell[c][cb + tx + 1] + S.cell[5 + c][cb + tx + 1] - S.cell[5 + c][cb + tx + 2];
+    }
+    __syncthreads();
+
+    // ---- y ------------------------------------------------------------------------------------
+    for (int f = tid; f < NFYA * ABX; f += ANT) {
+      const int q = f / ABX, lx = f - q * ABX;
+      const int sx = lx + 3;
+      real g[5], gL[5], gR[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][q + 1][lx + 2] - S.mu[c][q][lx + 2]) * p.idy;
+      face_vjp(1, ring_prim(S, s0, q, sx), ring_prim(S, s0, q + 1, sx), ring_prim(S, s0, q + 2, sx),
+               ring_prim(S, s0, q + 3, sx), g, gamma, gm1, gL, gR);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) { S.face[c][f] = gL[c]; S.face[5 + c][f] = gR[c]; }
+    }
+    __syncthreads();
+    for (int e = tid; e < NCYA * ABX; e += ANT) {
+      const int r = e / ABX, lx = e - r * ABX;
+      const int sx = lx + 3;
+      real D[5], A[5], B[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        D[c] = real(0.5) * S.face[c][(r + 1) * ABX + lx] - real(0.5) * S.face[5 + c][r * ABX + lx];
+      slope_vjp(ring_prim(S, s0, r + 1, sx), ring_prim(S, s0, r + 2, sx), ring_prim(S, s0, r + 3, sx),
+                D, A, B);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) { S.cell[c][e] = A[c]; S.cell[5 + c][e] = B[c]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      gW[c] += (S.face[c][(ty + 2) * ABX + tx] + S.face[5 + c][(ty + 1) * ABX + tx]) +
+               S.cell[c][ty * ABX + tx] - S.cell[c][(ty + 1) * ABX + tx] +
+               S.cell[5 + c][(ty + 1) * ABX + tx] - S.cell[5 + c][(ty + 2) * ABX + tx];
+
+    // ---- primitive recovery transposed, stage combination, store ------------------------------
+    if (active) {
+      const Prim<real> w = ring_prim(S, s0, ty + 3, tx + 3);
+      const real ir = real(1) / w.r;
+      const real v2 = w.vx * w.vx + w.vy * w.vy + w.vz * w.vz;
+      real gU[5];
+      gU[0] = gW[0] - (gW[1] * w.vx + gW[2] * w.vy + gW[3] * w.vz) * ir + gW[4] * gm1 * real(0.5) * v2;
+      gU[1] = gW[1] * ir - gW[4] * gm1 * w.vx;
+      gU[2] = gW[2] * ir - gW[4] * gm1 * w.vy;
+      gU[3] = gW[3] * ir - gW[4] * gm1 * w.vz;
+      gU[4] = gW[4] * gm1;
+      const long long idx = (long long)k * plane + col;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        real v = p.c1 * __ldg(p.lam_out + c * n3 + idx) + gU[c];
+        if (p.extra) v += p.c2 * __ldg(p.extra + c * n3 + idx);
+        p.lam_in[c * n3 + idx] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static int adj_zchunk(int nx, int ny, int nz) {
+  const long long tiles = (long long)((nx + ABX - 1) / ABX) * ((ny + ABY - 1) / ABY);
+  int chunks = (int)((148LL * 4 + tiles - 1) / tiles);
+  if (chunks < 1) chunks = 1;
+  int zc = (nz + chunks - 1) / chunks;
+  if (zc < 8) zc = 8;
+  if (zc > nz) zc = nz;
+  return zc;
+}
+
+template <typename real>
+cudaError_t launch_stage_adjoint(const AdjointArgs<real>& a, cudaStream_t s) {
+  const int zc = adj_zchunk(a.nx, a.ny, a.nz);
+  dim3 grid((a.nx + ABX - 1) / ABX, (a.ny + ABY - 1) / ABY, (a.nz + zc - 1) / zc);
+  const size_t smem = sizeof(AdjSmem<real>);
+  cudaError_t e = cudaFuncSetAttribute(stage_adjoint_kernel<real>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  stage_adjoint_kernel<real><<<grid, ANT, smem, s>>>(a, zc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_stage_adjoint<float>(const AdjointArgs<float>&, cudaStream_t);
+template cudaError_t launch_stage_adjoint<double>(const AdjointArgs<double>&, cudaStream_t);
+
 }  // namespace dh
 
-extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int, int, const void*, void*, int) {
-  if (c) c->err = "adjoint not available in this build";
-  return DH_ERR_ARG;
+// =============================================================================================
+// Checkpointed driver.
+struct AdjointSpace {
+  std::vector<void*> ckpt;   // U at steps 0, k, 2k, ...
+  std::vector<void*> seg;    // segment inputs U^{m0+1..m0+k-1}
+  std::vector<void*> seg1;   // segment stage-1 outputs U1^{m0..m0+k-1}
+  void* lam[3] = {nullptr, nullptr, nullptr};
+  double* dts = nullptr;
+  int nck = 0, k = 0, nsteps = 0;
+};
+
+namespace dh {
+void adjoint_free(dh_ctx* c) {
+  if (!c->adj) return;
+  AdjointSpace* a = c->adj;
+  for (void* p : a->ckpt) cudaFree(p);
+  for (void* p : a->seg) cudaFree(p);
+  for (void* p : a->seg1) cudaFree(p);
+  for (void* p : a->lam) cudaFree(p);
+  cudaFree(a->dts);
+  delete a;
+  c->adj = nullptr;
 }
-extern "C" dh_status dh_get_potential(dh_ctx* c, double*, int, int*, double*) {
-  if (c) c->err = "gravity not available in this build";
-  return DH_ERR_STATE;
+}  // namespace dh
+
+using namespace dh;
+
+static cudaError_t adjoint_reserve(dh_ctx* c, int n, int k) {
+  const int nck = (n + k - 1) / k;
+  AdjointSpace* a = c->adj;
+  if (a && a->nck >= nck && a->k == k && a->nsteps >= n) return cudaSuccess;
+  adjoint_free(c);
+  a = new AdjointSpace();
+  c->adj = a;
+  a->nck = nck;
+  a->k = k;
+  a->nsteps = n;
+  cudaError_t e = cudaSuccess;
+  a->ckpt.assign(nck, nullptr);
+  a->seg.assign(k > 1 ? k - 1 : 0, nullptr);
+  a->seg1.assign(k, nullptr);
+  for (auto& p : a->ckpt) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
+  for (auto& p : a->seg) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
+  for (auto& p : a->seg1) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
+  for (auto& p : a->lam) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&a->dts, (size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (e != cudaSuccess) adjoint_free(c);
+  return e;
+}
+
+template <typename real>
+static cudaError_t replay_stage(dh_ctx* c, int stage, const void* U, const void* U0, void* out,
+                                const double* dtp) {
+  const dh_config& g = c->cfg;
+  StageArgs<real> a;
+  memset(&a, 0, sizeof(a));
+  a.U = (const real*)U; a.U0 = (const real*)U0; a.out = (real*)out;
+  a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
+  a.gamma = (real)g.gamma; a.gm1 = (real)(g.gamma - 1.0);
+  a.idx = (real)(1.0 / g.dx); a.idy = (real)(1.0 / g.dy); a.idz = (real)(1.0 / g.dz);
+  a.dx = (real)g.dx; a.dy = (real)g.dy; a.dz = (real)g.dz;
+  a.rec = c->rec; a.dtp = dtp;
+  prof_begin(c, stage == 1 ? DH_KERNEL_STAGE1 : DH_KERNEL_STAGE2);
+  cudaError_t e = launch_stage<real>(stage, a, c->stream);
+  prof_end(c, 1);
+  return e;
+}
+
+template <typename real>
+static cudaError_t adjoint_stage(dh_ctx* c, const void* U, const void* lam_out, const void* extra,
+                                 void* lam_in, real c1, real c2, real beta, const double* dtp) {
+  const dh_config& g = c->cfg;
+  AdjointArgs<real> a;
+  a.U = (const real*)U; a.lam_out = (const real*)lam_out; a.extra = (const real*)extra;
+  a.lam_in = (real*)lam_in;
+  a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
+  a.gamma = (real)g.gamma; a.gm1 = (real)(g.gamma - 1.0);
+  a.idx = (real)(1.0 / g.dx); a.idy = (real)(1.0 / g.dy); a.idz = (real)(1.0 / g.dz);
+  a.c1 = c1; a.c2 = c2; a.beta = beta; a.dtp = dtp;
+  prof_begin(c, DH_KERNEL_ADJOINT);
+  cudaError_t e = launch_stage_adjoint<real>(a, c->stream);
+  prof_end(c, 1);
+  return e;
+}
+
+template <typename real>
+static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev) {
+  AdjointSpace* a = c->adj;
+  cudaError_t e;
+  void* lam = a->lam[0];
+  void* lam_new = a->lam[1];
+  void* lam_u1 = a->lam[2];
+  e = cudaMemcpyAsync(lam, lam_final_dev, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return e;
+  for (int sgi = (n + k - 1) / k - 1; sgi >= 0; --sgi) {
+    const int m0 = sgi * k;
+    const int len = (m0 + k <= n ? k : n - m0);
+    // recompute the segment: inputs U^{m0+j} and stage-1 outputs U1^{m0+j}
+    auto in = [&](int j) -> void* { return j == 0 ? a->ckpt[sgi] : a->seg[j - 1]; };
+    for (int j = 0; j < len; ++j) {
+      e = replay_stage<real>(c, 1, in(j), nullptr, a->seg1[j], a->dts + m0 + j);
+      if (e != cudaSuccess) return e;
+      if (j + 1 < len) {
+        e = replay_stage<real>(c, 2, a->seg1[j], in(j), in(j + 1), a->dts + m0 + j);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    for (int j = len - 1; j >= 0; --j) {
+      const double* dtp = a->dts + m0 + j;
+      // stage 2: U^{n+1} = U^n/2 + (U1 + dt L(U1))/2
+      e = adjoint_stage<real>(c, a->seg1[j], lam, nullptr, lam_u1, real(0.5), real(0), real(0.5), dtp);
+      if (e != cudaSuccess) return e;
+      // stage 1: U1 = U^n + dt L(U^n); lambda^n also receives lambda^{n+1}/2 from stage 2
+      e = adjoint_stage<real>(c, in(j), lam_u1, lam, lam_new, real(1), real(0.5), real(1), dtp);
+      if (e != cudaSuccess) return e;
+      void* t = lam; lam = lam_new; lam_new = t;
+    }
+  }
+  a->lam[0] = lam;
+  a->lam[1] = lam_new;
+  return cudaSuccess;
+}
+
+extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLdU_final,
+                                        void* dLdU0, int on_device) {
+  if (!c || !dLdU_final || !dLdU0) return DH_ERR_ARG;
+  if (!c->initialized) { c->err = "state not initialised"; return DH_ERR_STATE; }
+  if (n < 0 || k < 1) { c->err = "need n_steps >= 0 and ckpt_every >= 1"; return DH_ERR_ARG; }
+  if (c->cfg.forcing || c->cfg.cooling || c->cfg.gravity) {
+    c->err = "the hand adjoint covers the hydrodynamic step only (forcing, cooling, gravity off)";
+    return DH_ERR_ARG;
+  }
+  const cudaMemcpyKind h2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind d2h = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (n == 0) {
+    cudaError_t e = cudaMemcpyAsync(dLdU0, dLdU_final, c->state_bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return DH_ERR_CUDA; }
+    return DH_OK;
+  }
+  cudaError_t e = adjoint_reserve(c, n, k);
+  if (e != cudaSuccess) { c->err = std::string("adjoint allocation: ") + cudaGetErrorString(e); return DH_ERR_CUDA; }
+  AdjointSpace* a = c->adj;
+  // forward sweep with checkpoints; the dt of every step is recorded on the device
+  for (int m = 0; m < n && e == cudaSuccess; ++m) {
+    if (m % k == 0)
+      e = cudaMemcpyAsync(a->ckpt[m / k], c->U[c->cur], c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = c->prec == DH_F64 ? dh_enqueue_step_f64(c) : dh_enqueue_step_f32(c);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(a->dts + m, &c->rec->dt, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  }
+  if (e != cudaSuccess) { c->err = std::string("adjoint forward: ") + cudaGetErrorString(e); return DH_ERR_CUDA; }
+  dh_status st = dh_finish_steps(c);
+  if (st != DH_OK) return st;
+  // backward sweep
+  e = cudaMemcpyAsync(a->lam[1], dLdU_final, c->state_bytes, h2d, c->stream);
+  if (e == cudaSuccess)
+    e = c->prec == DH_F64 ? adjoint_backward<double>(c, n, k, a->lam[1])
+                          : adjoint_backward<float>(c, n, k, a->lam[1]);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dLdU0, a->lam[0], c->state_bytes, d2h, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) { c->err = std::string("adjoint backward: ") + cudaGetErrorString(e); return DH_ERR_CUDA; }
+  return DH_OK;
 }

@@ -1,0 +1,194 @@
+// Per-face reverse-mode building blocks of the hand adjoint: the MC slope, the limited slope
+// with its positivity fallback, HLLC and the face VJP of reconstruction o HLLC (App. A.1-A.2
+// transposed).  Host and device: the same code is checked on the CPU against finite
+// differences of the forward face flux.
+#pragma once
+#include "dh_device.cuh"
+
+namespace dh {
+
+// Reverse of mc_slope for one component: D = dL/d(slope) -> (dL/da, dL/db).
+template <typename real>
+__host__ __device__ __forceinline__ void mc_slope_vjp(real a, real b, real D, real& ga, real& gb) {
+  ga = real(0);
+  gb = real(0);
+  if (!(a * b > real(0))) return;
+  const real X = real(2) * fabs(a), Y = real(2) * fabs(b), Z = real(0.5) * fabs(a + b);
+  const real m1 = fmin(X, Y);
+  const real mg = D * copysign(real(1), a);  // d(sign(a) m)/dm
+  real m1g, Zg;
+  if (m1 < Z) { m1g = mg; Zg = real(0); }
+  else if (Z < m1) { m1g = real(0); Zg = mg; }
+  else { m1g = real(0.5) * mg; Zg = real(0.5) * mg; }
+  real Xg, Yg;
+  if (X < Y) { Xg = m1g; Yg = real(0); }
+  else if (Y < X) { Xg = real(0); Yg = m1g; }
+  else { Xg = real(0.5) * m1g; Yg = real(0.5) * m1g; }
+  ga = real(2) * copysign(real(1), a) * Xg + real(0.5) * copysign(real(1), a + b) * Zg;
+  gb = real(2) * copysign(real(1), b) * Yg + real(0.5) * copysign(real(1), a + b) * Zg;
+}
+
+// A_i = dL/da_i, B_i = dL/db_i of a cell from D = dL/d(dW_i); zero when the positivity fallback
+// zeroed the cell's slopes.
+template <typename real>
+__host__ __device__ __forceinline__ void slope_vjp(const Prim<real>& wm, const Prim<real>& w0,
+                                          const Prim<real>& wp, const real D[5], real A[5],
+                                          real B[5]) {
+  const Prim<real> d = limited_slope(wm, w0, wp);
+  const bool zeroed = (d.r == real(0) && d.vx == real(0) && d.vy == real(0) && d.vz == real(0) &&
+                       d.p == real(0));
+  // recompute the unguarded slopes to tell the fallback apart from slopes that are all zero
+  const real hr = real(0.5) * mc_slope(wp.r - w0.r, w0.r - wm.r);
+  const real hp = real(0.5) * mc_slope(wp.p - w0.p, w0.p - wm.p);
+  const bool fallback = zeroed && ((w0.r + hr <= real(0)) || (w0.p + hp <= real(0)) ||
+                                   (w0.r - hr <= real(0)) || (w0.p - hp <= real(0)));
+  if (fallback) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) { A[c] = real(0); B[c] = real(0); }
+    return;
+  }
+  mc_slope_vjp(wp.r - w0.r, w0.r - wm.r, D[0], A[0], B[0]);
+  mc_slope_vjp(wp.vx - w0.vx, w0.vx - wm.vx, D[1], A[1], B[1]);
+  mc_slope_vjp(wp.vy - w0.vy, w0.vy - wm.vy, D[2], A[2], B[2]);
+  mc_slope_vjp(wp.vz - w0.vz, w0.vz - wm.vz, D[3], A[3], B[3]);
+  mc_slope_vjp(wp.p - w0.p, w0.p - wm.p, D[4], A[4], B[4]);
+}
+
+// Reverse of hllc() in the face frame (r, u, a, b, p) for both sides.
+template <typename real>
+__host__ __device__ __forceinline__ void hllc_vjp(real rL, real uL, real aL, real bL, real pL, real rR,
+                                         real uR, real aR, real bR, real pR, real gamma,
+                                         real gm1, real g0, real gn, real gt1, real gt2, real ge,
+                                         real gL[5], real gR[5]) {
+  const real cL = q_sqrt(q_div(gamma * pL, rL));
+  const real cR = q_sqrt(q_div(gamma * pR, rR));
+  const real xL = uL - cL, xR = uR - cR;
+  const real yL = uL + cL, yR = uR + cR;
+  const real SL = fmin(xL, xR);
+  const real SR = fmax(yL, yR);
+  const real dL = SL - uL, dR = SR - uR;
+  const real num = pR - pL + rL * uL * dL - rR * uR * dR;
+  const real den = rL * dL - rR * dR;
+  const real Ss = q_div(num, den);
+  const bool left = (SL >= real(0)) || (Ss >= real(0));
+  const bool star = !(SL >= real(0)) && (Ss >= real(0) || SR > real(0));
+  const real r = left ? rL : rR, u = left ? uL : uR, a = left ? aL : aR, b = left ? bL : bR;
+  const real p = left ? pL : pR, S = left ? SL : SR, d = left ? dL : dR;
+  const real E = q_div(p, gm1) + real(0.5) * r * (u * u + a * a + b * b);
+  const real mass = r * u;
+
+  real r_ = 0, u_ = 0, a_ = 0, b_ = 0, p_ = 0, S_ = 0, Ss_ = 0, d_ = 0;
+  real mass_ = g0 + gn * u + gt1 * a + gt2 * b;
+  u_ += gn * mass + ge * (E + p);
+  a_ += gt1 * mass;
+  b_ += gt2 * mass;
+  p_ += gn + ge * u;
+  real E_ = ge * u;
+  if (star) {
+    const real den2 = S - Ss;
+    const real coef = q_div(r * d, den2);
+    const real w = q_div(p, r * d);
+    const real Z = Ss + w;
+    const real Q = q_div(E, r) + (Ss - u) * Z;
+    const real Es = coef * Q;
+    S_ += g0 * (coef - r) + gn * (coef * Ss - mass) + gt1 * (coef * a - r * a) +
+          gt2 * (coef * b - r * b) + ge * (Es - E);
+    real coef_ = S * (g0 + gn * Ss + gt1 * a + gt2 * b);
+    Ss_ += S * gn * coef;
+    r_ -= S * (g0 + gt1 * a + gt2 * b);
+    mass_ -= S * gn;
+    a_ += S * gt1 * (coef - r);
+    b_ += S * gt2 * (coef - r);
+    E_ -= S * ge;
+    const real Es_ = S * ge;
+    coef_ += Es_ * Q;
+    const real Q_ = Es_ * coef;
+    E_ += Q_ / r;
+    r_ -= Q_ * E / (r * r);
+    Ss_ += Q_ * (Z + (Ss - u));
+    u_ -= Q_ * Z;
+    const real w_ = Q_ * (Ss - u);
+    p_ += w_ / (r * d);
+    r_ -= w_ * p / (r * r * d);
+    d_ -= w_ * p / (r * d * d);
+    r_ += coef_ * d / den2;
+    d_ += coef_ * r / den2;
+    const real dc = coef_ * r * d / (den2 * den2);
+    S_ -= dc;
+    Ss_ += dc;
+  }
+  p_ += E_ / gm1;
+  r_ += E_ * real(0.5) * (u * u + a * a + b * b);
+  u_ += E_ * r * u;
+  a_ += E_ * r * a;
+  b_ += E_ * r * b;
+  r_ += mass_ * u;
+  u_ += mass_ * r;
+  S_ += d_;
+  u_ -= d_;
+
+  real rL_ = 0, uL_ = 0, aL_ = 0, bL_ = 0, pL_ = 0, SL_ = 0, dL_ = 0;
+  real rR_ = 0, uR_ = 0, aR_ = 0, bR_ = 0, pR_ = 0, SR_ = 0, dR_ = 0;
+  if (left) { rL_ = r_; uL_ = u_; aL_ = a_; bL_ = b_; pL_ = p_; SL_ = S_; }
+  else      { rR_ = r_; uR_ = u_; aR_ = a_; bR_ = b_; pR_ = p_; SR_ = S_; }
+  if (star) {
+    const real num_ = Ss_ / den;
+    const real den_ = -Ss_ * Ss / den;
+    pR_ += num_;
+    pL_ -= num_;
+    rL_ += num_ * uL * dL + den_ * dL;
+    uL_ += num_ * rL * dL;
+    dL_ += num_ * rL * uL + den_ * rL;
+    rR_ -= num_ * uR * dR + den_ * dR;
+    uR_ -= num_ * rR * dR;
+    dR_ -= num_ * rR * uR + den_ * rR;
+  }
+  SL_ += dL_;
+  uL_ -= dL_;
+  SR_ += dR_;
+  uR_ -= dR_;
+  real cL_ = 0, cR_ = 0;
+  if (xL < xR) { uL_ += SL_; cL_ -= SL_; }
+  else if (xR < xL) { uR_ += SL_; cR_ -= SL_; }
+  else { uL_ += real(0.5) * SL_; cL_ -= real(0.5) * SL_; uR_ += real(0.5) * SL_; cR_ -= real(0.5) * SL_; }
+  if (yL > yR) { uL_ += SR_; cL_ += SR_; }
+  else if (yR > yL) { uR_ += SR_; cR_ += SR_; }
+  else { uL_ += real(0.5) * SR_; cL_ += real(0.5) * SR_; uR_ += real(0.5) * SR_; cR_ += real(0.5) * SR_; }
+  pL_ += cL_ * gamma / (real(2) * cL * rL);
+  rL_ -= cL_ * cL / (real(2) * rL);
+  pR_ += cR_ * gamma / (real(2) * cR * rR);
+  rR_ -= cR_ * cR / (real(2) * rR);
+  gL[0] = rL_; gL[1] = uL_; gL[2] = aL_; gL[3] = bL_; gL[4] = pL_;
+  gR[0] = rR_; gR[1] = uR_; gR[2] = aR_; gR[3] = bR_; gR[4] = pR_;
+}
+
+// Face VJP along `axis` from the four primitive cells around the face and the flux gradient
+// g[5] in (rho, m_x, m_y, m_z, E) order; returns gradients of the two reconstructed states in
+// (rho, v_x, v_y, v_z, P) order.
+template <typename real>
+__host__ __device__ __forceinline__ void face_vjp(int axis, const Prim<real>& w0, const Prim<real>& w1,
+                                         const Prim<real>& w2, const Prim<real>& w3,
+                                         const real g[5], real gamma, real gm1, real gL[5],
+                                         real gR[5]) {
+  const Prim<real> L = add_half(w1, limited_slope(w0, w1, w2), real(1));
+  const Prim<real> R = add_half(w2, limited_slope(w1, w2, w3), real(-1));
+  real fL[5], fR[5];
+  if (axis == 0) {
+    hllc_vjp(L.r, L.vx, L.vy, L.vz, L.p, R.r, R.vx, R.vy, R.vz, R.p, gamma, gm1, g[0], g[1], g[2],
+             g[3], g[4], fL, fR);
+    gL[0] = fL[0]; gL[1] = fL[1]; gL[2] = fL[2]; gL[3] = fL[3]; gL[4] = fL[4];
+    gR[0] = fR[0]; gR[1] = fR[1]; gR[2] = fR[2]; gR[3] = fR[3]; gR[4] = fR[4];
+  } else if (axis == 1) {
+    hllc_vjp(L.r, L.vy, L.vx, L.vz, L.p, R.r, R.vy, R.vx, R.vz, R.p, gamma, gm1, g[0], g[2], g[1],
+             g[3], g[4], fL, fR);
+    gL[0] = fL[0]; gL[1] = fL[2]; gL[2] = fL[1]; gL[3] = fL[3]; gL[4] = fL[4];
+    gR[0] = fR[0]; gR[1] = fR[2]; gR[2] = fR[1]; gR[3] = fR[3]; gR[4] = fR[4];
+  } else {
+    hllc_vjp(L.r, L.vz, L.vx, L.vy, L.p, R.r, R.vz, R.vx, R.vy, R.p, gamma, gm1, g[0], g[3], g[1],
+             g[2], g[4], fL, fR);
+    gL[0] = fL[0]; gL[1] = fL[2]; gL[2] = fL[3]; gL[3] = fL[1]; gL[4] = fL[4];
+    gR[0] = fR[0]; gR[1] = fR[2]; gR[2] = fR[3]; gR[3] = fR[1]; gR[4] = fR[4];
+  }
+}
+
+}  // namespace dh

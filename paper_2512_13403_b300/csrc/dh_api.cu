@@ -121,6 +121,15 @@ extern "C" dh_status dh_create(const dh_config* cfg, void* stream, dh_ctx** out)
     return fail(nullptr, DH_ERR_CUDA, m);
   }
   if (c->prec == DH_F64) upload_twiddles<double>(c); else upload_twiddles<float>(c);
+  {
+    // a defined step record from the start: no flags, no failure, CFL minimum +inf
+    StepRecord r;
+    std::memset(&r, 0, sizeof(r));
+    r.fail_step = -1;
+    r.cfl_min_bits = c->prec == DH_F32 ? (unsigned long long)0x7f800000u : 0x7ff0000000000000ull;
+    c->host_rec = r;
+    cudaMemcpy(c->rec, &r, sizeof(r), cudaMemcpyHostToDevice);
+  }
   if (cfg->gravity) mg_setup_host(c);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -249,6 +258,7 @@ static StageArgs<real> stage_args(dh_ctx* c) {
   a.idx = (real)(1.0 / g.dx); a.idy = (real)(1.0 / g.dy); a.idz = (real)(1.0 / g.dz);
   a.dx = (real)g.dx; a.dy = (real)g.dy; a.dz = (real)g.dz;
   a.rec = c->rec;
+  a.dtp = &c->rec->dt;
   a.ahat_norm = (const real*)c->ahat_norm;
   for (int q = 0; q < 3; ++q) a.tw[q] = (const real*)c->tw[q];
   a.t_floor = (real)g.t_floor; a.cool_frac = (real)g.cool_frac; a.nsub_max = g.nsub_max;
@@ -333,6 +343,10 @@ static dh_status finish_steps(dh_ctx* c, long long nstep_before) {
   }
   return DH_OK;
 }
+
+cudaError_t dh_enqueue_step_f32(dh_ctx* c) { return enqueue_step<float>(c, 0.0); }
+cudaError_t dh_enqueue_step_f64(dh_ctx* c) { return enqueue_step<double>(c, 0.0); }
+dh_status dh_finish_steps(dh_ctx* c) { return finish_steps(c, c->host_rec.nstep - c->pending_steps); }
 
 extern "C" dh_status dh_step(dh_ctx* c, double dt, double* dt_used) {
   if (!c) return fail(c, DH_ERR_ARG, "null context");

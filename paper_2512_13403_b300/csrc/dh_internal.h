@@ -57,3 +57,8 @@ template <typename real> cudaError_t gravity_sources(dh_ctx* c, void* Ustar);
 // adjoint.cu
 void adjoint_free(dh_ctx* c);
 }  // namespace dh
+
+// dh_api.cu: step machinery shared with the adjoint driver
+cudaError_t dh_enqueue_step_f32(dh_ctx* c);
+cudaError_t dh_enqueue_step_f64(dh_ctx* c);
+dh_status dh_finish_steps(dh_ctx* c);

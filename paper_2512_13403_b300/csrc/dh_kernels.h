@@ -15,6 +15,7 @@ template <typename real> struct StageArgs {
   real idx, idy, idz;   // inverse cell widths
   real dx, dy, dz;      // cell widths (CFL reduction)
   StepRecord* rec;
+  const double* dtp;      // time step of this stage (device scalar)
   // fused sources (stage 2 only)
   int forcing, cooling;
   const real* ahat_norm;  // 16 modes x 3 comps x (re, im), normalised
@@ -54,5 +55,20 @@ cudaError_t launch_forcing_field(const real* ahat_norm, const real* const tw[3],
                                  int nz, real* a_out, cudaStream_t s);
 
 int totals_blocks();
+
+// Adjoint of one RK2 stage (adjoint.cu):
+//   lam_in = c1 * lam_out + c2 * extra + (dL/dU)^T (beta * dt * lam_out),  L the unsplit RHS at U.
+template <typename real> struct AdjointArgs {
+  const real* U;         // stage input state
+  const real* lam_out;   // gradient with respect to the stage output
+  const real* extra;     // added with weight c2 (nullable)
+  real* lam_in;          // result
+  int nx, ny, nz;
+  real gamma, gm1, idx, idy, idz;
+  real c1, c2, beta;
+  const double* dtp;
+};
+template <typename real>
+cudaError_t launch_stage_adjoint(const AdjointArgs<real>& a, cudaStream_t s);
 
 }  // namespace dh

@@ -1,0 +1,150 @@
+// Per-cell source terms shared by the fused stage-2 epilogue and the gravity-path source kernel:
+// OU forcing synthesis (Sec. 3.1.1), optically thin cooling (Sec. 4.3) and the CFL time of a
+// cell (App. A.4).
+#pragma once
+#include "dh_device.cuh"
+
+namespace dh {
+
+// Forced-mode table of Sec. 3.1.1 as compile-time data: the half-space of integer n with
+// 1 <= |n|^2 <= 4 whose first nonzero component is positive, lexicographic in (n_x, n_y, n_z).
+__host__ __device__ constexpr int forced_mode_component(int m, int axis) {
+  int count = 0;
+  for (int a = -2; a <= 2; ++a)
+    for (int b = -2; b <= 2; ++b)
+      for (int c = -2; c <= 2; ++c) {
+        const int k2 = a * a + b * b + c * c;
+        const int first = a != 0 ? a : (b != 0 ? b : c);
+        if (k2 >= 1 && k2 <= 4 && first > 0) {
+          if (count == m) return axis == 0 ? a : (axis == 1 ? b : c);
+          ++count;
+        }
+      }
+  return 0;
+}
+static_assert(forced_mode_component(15, 0) == 2 && forced_mode_component(0, 2) == 1,
+              "forced mode enumeration");
+
+template <typename real> struct C2 { real re, im; };
+
+template <typename real>
+__device__ __forceinline__ C2<real> cmul(C2<real> a, C2<real> b) {
+  return C2<real>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// exp(2 pi i n x~) for one axis from its twiddles (n in -2..2, n != 0).
+template <typename real, int N>
+__device__ __forceinline__ C2<real> axis_factor(const real* t) {
+  static_assert(N != 0, "");
+  constexpr int A = N > 0 ? N : -N;
+  const real c = A == 1 ? t[0] : t[2];
+  const real s = A == 1 ? t[1] : t[3];
+  return C2<real>{c, N > 0 ? s : -s};
+}
+
+template <typename real, int M>
+__device__ __forceinline__ void add_mode(const real* __restrict__ ah, const real* tx,
+                                         const real* ty, const real* tz, real acc[3]) {
+  constexpr int NX = forced_mode_component(M, 0);
+  constexpr int NY = forced_mode_component(M, 1);
+  constexpr int NZ = forced_mode_component(M, 2);
+  C2<real> e{real(1), real(0)};
+  bool first = true;
+  if constexpr (NX != 0) { e = axis_factor<real, NX>(tx); first = false; }
+  if constexpr (NY != 0) {
+    const C2<real> f = axis_factor<real, NY>(ty);
+    e = first ? f : cmul(e, f);
+    first = false;
+  }
+  if constexpr (NZ != 0) {
+    const C2<real> f = axis_factor<real, NZ>(tz);
+    e = first ? f : cmul(e, f);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const real are = __ldg(ah + 2 * (3 * M + c));
+    const real aim = __ldg(ah + 2 * (3 * M + c) + 1);
+    acc[c] += are * e.re - aim * e.im;
+  }
+}
+
+template <typename real, int M>
+__device__ __forceinline__ void add_modes(const real* ah, const real* tx, const real* ty,
+                                          const real* tz, real acc[3]) {
+  if constexpr (M < 16) {
+    add_mode<real, M>(ah, tx, ty, tz, acc);
+    add_modes<real, M + 1>(ah, tx, ty, tz, acc);
+  }
+}
+
+// a(x) = 2 Re sum_H a_hat_n exp(2 pi i n . x~), with the normalised table (Sec. 3.1.1).
+template <typename real>
+__device__ __forceinline__ void forcing_accel(const real* ah, const real* const tw[3], int i,
+                                              int j, int k, real a[3]) {
+  real tx[4], ty[4], tz[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    tx[q] = __ldg(tw[0] + 4 * i + q);
+    ty[q] = __ldg(tw[1] + 4 * j + q);
+    tz[q] = __ldg(tw[2] + 4 * k + q);
+  }
+  real acc[3] = {real(0), real(0), real(0)};
+  add_modes<real, 0>(ah, tx, ty, tz, acc);
+  a[0] = real(2) * acc[0];
+  a[1] = real(2) * acc[1];
+  a[2] = real(2) * acc[2];
+}
+
+// Cooling of one cell (Sec. 4.3; Lambda = n^2 T^(1/2), T = P / rho, floor rho T_floor/(gamma-1)).
+// A cell cools only while its thermal energy is above the floor energy; the test compares
+// energies, so a state clamped to the floor is recognised exactly whatever the rounding of T.
+template <typename real>
+__device__ __forceinline__ real cooling_energy(real r, real mx, real my, real mz, real E, real dt,
+                                               real gm1, real T_floor, real frac, int nsub_max,
+                                               unsigned& flags) {
+  const real ir = q_div(real(1), r);
+  const real kin = real(0.5) * (mx * mx + my * my + mz * mz) * ir;
+  const real Eth = E - kin;
+  const real Efl = q_div(r * T_floor, gm1);
+  if (!(Eth > Efl)) return E;
+  const real r2 = r * r;
+  const real Ed0 = -r2 * q_sqrt(gm1 * Eth * ir);
+  const real tcool = q_div(Eth, -Ed0);
+  const real raw = ceil(q_div(dt, frac * tcool));
+  // clamp to [1, nsub_max]; a NaN count also takes the cap, so the loop below is always bounded
+  real nsub = raw;
+  if (!(raw <= real(nsub_max))) {
+    if (raw > real(nsub_max)) flags |= FLAG_COOL_CAP;
+    nsub = real(nsub_max);
+  }
+  if (!(nsub >= real(1))) nsub = real(1);
+  real Enew;
+  if (nsub == real(1)) {
+    const real Ep = fmax(Efl, Eth + dt * Ed0);
+    const real Edp = Ep > Efl ? -r2 * q_sqrt(gm1 * Ep * ir) : real(0);
+    Enew = fmax(Efl, Eth + real(0.5) * dt * (Ed0 + Edp));
+  } else {
+    const real dts = q_div(dt, nsub);
+    const int n = (int)nsub;
+    real Es = Eth;
+    for (int q = 0; q < n; ++q) {
+      const real ed = Es > Efl ? -r2 * q_sqrt(gm1 * Es * ir) : real(0);
+      Es = fmax(Efl, Es + ed * dts);
+    }
+    Enew = Es;
+  }
+  return kin + Enew;
+}
+
+template <typename real>
+__device__ __forceinline__ real cfl_time(real r, real mx, real my, real mz, real E, real gamma,
+                                         real gm1, real dx, real dy, real dz) {
+  const Prim<real> w = cons_to_prim(r, mx, my, mz, E, gm1);
+  const real c = q_sqrt(q_div(gamma * w.p, w.r));
+  const real tx = q_div(dx, fabs(w.vx) + c);
+  const real ty = q_div(dy, fabs(w.vy) + c);
+  const real tz = q_div(dz, fabs(w.vz) + c);
+  return fmin(fmin(tx, ty), tz);
+}
+
+}  // namespace dh

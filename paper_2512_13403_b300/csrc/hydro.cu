@@ -12,164 +12,31 @@
 // face loop, and the z faces come from a per-thread register pipeline (each z face once).
 #include <math.h>
 #include "dh_kernels.h"
+#include "dh_sources.cuh"
 
 namespace dh {
 
 constexpr int BX = 32, BY = 8, HX = BX + 4, HY = BY + 4;
 constexpr int NTHREADS = BX * BY;
+constexpr int NXS = (BX + 2) * BY;   // cells with an x slope in a plane tile: lx = -1 .. BX
+constexpr int NYS = BX * (BY + 2);   // cells with a y slope: ly = -1 .. BY
 constexpr int NXF = (BX + 1) * BY;   // x faces of a plane tile
 constexpr int NYF = BX * (BY + 1);   // y faces of a plane tile
+constexpr int NFORCE = BY * 9;       // forcing row factors: row x (n_x = 0, 1, 2) x component
 
 template <typename real> struct StageSmem {
-  real w[3][5][HY][HX];     // primitive planes ring
-  real fx[5][BY][BX + 1];   // x-face fluxes of the current plane
-  real fy[5][BY + 1][BX];   // y-face fluxes of the current plane
-  int xs[HX];               // wrapped global x of each smem column
-  int ys[HY];               // wrapped global y of each smem row
-  real red[NTHREADS / 32];  // CFL reduction scratch
+  real w[3][5][HY][HX];      // primitive planes ring (k, k+1, k+2), two-cell x/y halo
+  real xm[5][BY][BX + 2];    // x face states W - dW/2 of cells lx = -1..BX (index lx + 1)
+  real xp[5][BY][BX + 2];    //                W + dW/2
+  real ym[5][BY + 2][BX];    // y face states of cells ly = -1..BY (index ly + 1)
+  real yp[5][BY + 2][BX];
+  real fx[5][BY][BX + 1];    // x-face fluxes of the current plane
+  real fy[5][BY + 1][BX];    // y-face fluxes of the current plane
+  real fB[BY][3][3][2];      // forcing: B[row][n_x][component] = sum over modes with that n_x
+  int xs[HX];                // wrapped global x of each smem column
+  int ys[HY];                // wrapped global y of each smem row
+  real red[NTHREADS / 32];   // CFL reduction scratch
 };
-
-// ---------------------------------------------------------------------------------------------
-// Forced-mode table of Sec. 3.1.1 as compile-time data: the half-space of integer n with
-// 1 <= |n|^2 <= 4 whose first nonzero component is positive, lexicographic in (n_x, n_y, n_z).
-__host__ __device__ constexpr int forced_mode_component(int m, int axis) {
-  int count = 0;
-  for (int a = -2; a <= 2; ++a)
-    for (int b = -2; b <= 2; ++b)
-      for (int c = -2; c <= 2; ++c) {
-        const int k2 = a * a + b * b + c * c;
-        const int first = a != 0 ? a : (b != 0 ? b : c);
-        if (k2 >= 1 && k2 <= 4 && first > 0) {
-          if (count == m) return axis == 0 ? a : (axis == 1 ? b : c);
-          ++count;
-        }
-      }
-  return 0;
-}
-static_assert(forced_mode_component(15, 0) == 2 && forced_mode_component(0, 2) == 1,
-              "forced mode enumeration");
-
-template <typename real> struct C2 { real re, im; };
-
-template <typename real>
-__device__ __forceinline__ C2<real> cmul(C2<real> a, C2<real> b) {
-  return C2<real>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
-}
-
-// exp(2 pi i n x~) for one axis from its twiddles (n in -2..2, n != 0).
-template <typename real, int N>
-__device__ __forceinline__ C2<real> axis_factor(const real* t) {
-  static_assert(N != 0, "");
-  constexpr int A = N > 0 ? N : -N;
-  const real c = A == 1 ? t[0] : t[2];
-  const real s = A == 1 ? t[1] : t[3];
-  return C2<real>{c, N > 0 ? s : -s};
-}
-
-template <typename real, int M>
-__device__ __forceinline__ void add_mode(const real* __restrict__ ah, const real* tx,
-                                         const real* ty, const real* tz, real acc[3]) {
-  constexpr int NX = forced_mode_component(M, 0);
-  constexpr int NY = forced_mode_component(M, 1);
-  constexpr int NZ = forced_mode_component(M, 2);
-  C2<real> e{real(1), real(0)};
-  bool first = true;
-  if constexpr (NX != 0) { e = axis_factor<real, NX>(tx); first = false; }
-  if constexpr (NY != 0) {
-    const C2<real> f = axis_factor<real, NY>(ty);
-    e = first ? f : cmul(e, f);
-    first = false;
-  }
-  if constexpr (NZ != 0) {
-    const C2<real> f = axis_factor<real, NZ>(tz);
-    e = first ? f : cmul(e, f);
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const real are = __ldg(ah + 2 * (3 * M + c));
-    const real aim = __ldg(ah + 2 * (3 * M + c) + 1);
-    acc[c] += are * e.re - aim * e.im;
-  }
-}
-
-template <typename real, int M>
-__device__ __forceinline__ void add_modes(const real* ah, const real* tx, const real* ty,
-                                          const real* tz, real acc[3]) {
-  if constexpr (M < 16) {
-    add_mode<real, M>(ah, tx, ty, tz, acc);
-    add_modes<real, M + 1>(ah, tx, ty, tz, acc);
-  }
-}
-
-// a(x) = 2 Re sum_H a_hat_n exp(2 pi i n . x~), with the normalised table (Sec. 3.1.1).
-template <typename real>
-__device__ __forceinline__ void forcing_accel(const real* ah, const real* const tw[3], int i,
-                                              int j, int k, real a[3]) {
-  real tx[4], ty[4], tz[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    tx[q] = __ldg(tw[0] + 4 * i + q);
-    ty[q] = __ldg(tw[1] + 4 * j + q);
-    tz[q] = __ldg(tw[2] + 4 * k + q);
-  }
-  real acc[3] = {real(0), real(0), real(0)};
-  add_modes<real, 0>(ah, tx, ty, tz, acc);
-  a[0] = real(2) * acc[0];
-  a[1] = real(2) * acc[1];
-  a[2] = real(2) * acc[2];
-}
-
-// Cooling of one cell (Sec. 4.3; Lambda = n^2 T^(1/2), T = P / rho, floor rho T_floor/(gamma-1)).
-template <typename real>
-__device__ __forceinline__ real cooling_energy(real r, real mx, real my, real mz, real E, real dt,
-                                               real gm1, real T_floor, real frac, int nsub_max,
-                                               unsigned& flags) {
-  const real kin = real(0.5) * (mx * mx + my * my + mz * mz) / r;
-  const real Eth = E - kin;
-  const real T = gm1 * Eth / r;
-  if (!(T > T_floor)) return E;
-  const real Efl = r * T_floor / gm1;
-  const real r2 = r * r;
-  const real Ed0 = -r2 * sqrt(T);
-  const real tcool = Eth / (-Ed0);
-  const real raw = ceil(dt / (frac * tcool));
-  // clamp to [1, nsub_max]; a NaN count also takes the cap, so the loop below is always bounded
-  real nsub = raw;
-  if (!(raw <= real(nsub_max))) {
-    if (raw > real(nsub_max)) flags |= FLAG_COOL_CAP;
-    nsub = real(nsub_max);
-  }
-  if (!(nsub >= real(1))) nsub = real(1);
-  real Enew;
-  if (nsub == real(1)) {
-    const real Ep = fmax(Efl, Eth + dt * Ed0);
-    const real Tp = gm1 * Ep / r;
-    const real Edp = Tp > T_floor ? -r2 * sqrt(Tp) : real(0);
-    Enew = fmax(Efl, Eth + real(0.5) * dt * (Ed0 + Edp));
-  } else {
-    const real dts = dt / nsub;
-    const int n = (int)nsub;
-    real Es = Eth;
-    for (int q = 0; q < n; ++q) {
-      const real Tq = gm1 * Es / r;
-      const real ed = Tq > T_floor ? -r2 * sqrt(Tq) : real(0);
-      Es = fmax(Efl, Es + ed * dts);
-    }
-    Enew = Es;
-  }
-  return kin + Enew;
-}
-
-template <typename real>
-__device__ __forceinline__ real cfl_time(real r, real mx, real my, real mz, real E, real gamma,
-                                         real gm1, real dx, real dy, real dz) {
-  const Prim<real> w = cons_to_prim(r, mx, my, mz, E, gm1);
-  const real c = sqrt(gamma * w.p / w.r);
-  const real tx = dx / (fabs(w.vx) + c);
-  const real ty = dy / (fabs(w.vy) + c);
-  const real tz = dz / (fabs(w.vz) + c);
-  return fmin(fmin(tx, ty), tz);
-}
 
 template <typename real>
 __device__ __forceinline__ Prim<real> smem_prim(const StageSmem<real>& S, int slot, int sy,
@@ -183,6 +50,40 @@ __device__ __forceinline__ Prim<real> load_prim(const real* __restrict__ U, long
                                                 long long idx, real gm1) {
   return cons_to_prim(__ldg(U + idx), __ldg(U + n3 + idx), __ldg(U + 2 * n3 + idx),
                       __ldg(U + 3 * n3 + idx), __ldg(U + 4 * n3 + idx), gm1);
+}
+
+#define DH_STORE_PRIM(arr, i0, i1, v)                                                   \
+  do {                                                                                  \
+    arr[0][i0][i1] = (v).r; arr[1][i0][i1] = (v).vx; arr[2][i0][i1] = (v).vy;           \
+    arr[3][i0][i1] = (v).vz; arr[4][i0][i1] = (v).p;                                    \
+  } while (0)
+#define DH_LOAD_PRIM(arr, i0, i1)                                                       \
+  Prim<real>{arr[0][i0][i1], arr[1][i0][i1], arr[2][i0][i1], arr[3][i0][i1], arr[4][i0][i1]}
+
+// One task of the per-row forcing factors: for row (y, z) and n_x in {0,1,2}, component c:
+// B = sum over forced modes with that n_x of a_hat_{m,c} exp(2 pi i (n_y y~ + n_z z~)).
+template <typename real, int M>
+__device__ __forceinline__ void row_factor(const real* __restrict__ ah, int nxsel, int c,
+                                           const real* ty, const real* tz, real& bre, real& bim) {
+  if constexpr (M < 16) {
+    constexpr int NX = forced_mode_component(M, 0);
+    constexpr int NY = forced_mode_component(M, 1);
+    constexpr int NZ = forced_mode_component(M, 2);
+    if (NX == nxsel) {
+      C2<real> e{real(1), real(0)};
+      bool first = true;
+      if constexpr (NY != 0) { e = axis_factor<real, NY>(ty); first = false; }
+      if constexpr (NZ != 0) {
+        const C2<real> f = axis_factor<real, NZ>(tz);
+        e = first ? f : cmul(e, f);
+      }
+      const real are = __ldg(ah + 2 * (3 * M + c));
+      const real aim = __ldg(ah + 2 * (3 * M + c) + 1);
+      bre += are * e.re - aim * e.im;
+      bim += are * e.im + aim * e.re;
+    }
+    row_factor<real, M + 1>(ah, nxsel, c, ty, tz, bre, bim);
+  }
 }
 
 template <typename real, int STAGE>
@@ -205,11 +106,12 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
   const int z0 = blockIdx.z * zchunk;
   const int z1 = min(z0 + zchunk, nz);
-  const real dt = (real)p.rec->dt;
+  const real dt = (real)*p.dtp;
   const real gamma = p.gamma, gm1 = p.gm1;
   const int gx = x0 + tx, gy = y0 + ty;
   const bool active = gx < nx && gy < ny;
   const int gxw = gx % nx, gyw = gy % ny;
+  const bool forcing = STAGE == 2 && p.forcing;
 
   if (tid < HX) S.xs[tid] = ((x0 + tid - 2) % nx + nx) % nx;
   if (tid >= 64 && tid < 64 + HY) S.ys[tid - 64] = ((y0 + tid - 64 - 2) % ny + ny) % ny;
@@ -228,6 +130,13 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
       S.w[slot][4][sy][sx] = w.p;
     }
   };
+
+  // x twiddles of the own column (forcing synthesis), fixed for the whole march
+  real twx[4] = {real(0), real(0), real(0), real(0)};
+  if (forcing) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) twx[q] = __ldg(p.tw[0] + 4 * gxw + q);
+  }
 
   // Prologue: planes z0, z0+1 in the ring; the own column's z0-2, z0-1 in registers.
   load_plane(z0, 0);
@@ -252,8 +161,43 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
   for (int k = z0; k < z1; ++k) {
     const int s0 = (k - z0) % 3, s1 = (k - z0 + 1) % 3, s2 = (k - z0 + 2) % 3;
     load_plane(k + 2, s2);
-    __syncthreads();
+    __syncthreads();  // ---- plane k+2 in the ring
 
+    // limited slopes and face states of plane k, once per cell and axis
+    for (int t = tid; t < NXS + NYS; t += NTHREADS) {
+      if (t < NXS) {
+        const int ly = t / (BX + 2), r = t - ly * (BX + 2);
+        const int sy = ly + 2;
+        const Prim<real> w1 = smem_prim(S, s0, sy, r + 1);
+        const Prim<real> d = limited_slope(smem_prim(S, s0, sy, r), w1, smem_prim(S, s0, sy, r + 2));
+        DH_STORE_PRIM(S.xm, ly, r, add_half(w1, d, real(-1)));
+        DH_STORE_PRIM(S.xp, ly, r, add_half(w1, d, real(1)));
+      } else {
+        const int u = t - NXS;
+        const int r = u / BX, lx = u - r * BX;
+        const int sx = lx + 2;
+        const Prim<real> w1 = smem_prim(S, s0, r + 1, sx);
+        const Prim<real> d = limited_slope(smem_prim(S, s0, r, sx), w1, smem_prim(S, s0, r + 2, sx));
+        DH_STORE_PRIM(S.ym, r, lx, add_half(w1, d, real(-1)));
+        DH_STORE_PRIM(S.yp, r, lx, add_half(w1, d, real(1)));
+      }
+    }
+    if (forcing && tid >= NTHREADS - NFORCE) {
+      const int q = tid - (NTHREADS - NFORCE);
+      const int ly = q / 9, rem = q - 9 * ly;
+      const int nxsel = rem / 3, c = rem - 3 * nxsel;
+      const int yrow = (y0 + ly) % ny;
+      real tyv[4], tzv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        tyv[i] = __ldg(p.tw[1] + 4 * yrow + i);
+        tzv[i] = __ldg(p.tw[2] + 4 * k + i);
+      }
+      real bre = real(0), bim = real(0);
+      row_factor<real, 0>(p.ahat_norm, nxsel, c, tyv, tzv, bre, bim);
+      S.fB[ly][nxsel][c][0] = bre;
+      S.fB[ly][nxsel][c][1] = bim;
+    }
     // z face k+1/2 of the own column
     real fz_hi[5];
     Prim<real> dk1;
@@ -264,39 +208,25 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
       dk1 = limited_slope(w0, w1, w2);
       face_flux(2, add_half(w0, dk, real(1)), add_half(w1, dk1, real(-1)), gamma, gm1, fz_hi);
     }
+    __syncthreads();  // ---- face states ready
 
     // every x and y face of plane k, once
     for (int f = tid; f < NXF + NYF; f += NTHREADS) {
+      real F[5];
       if (f < NXF) {
         const int ly = f / (BX + 1), a = f - ly * (BX + 1);
-        const int sy = ly + 2;
-        const Prim<real> w0 = smem_prim(S, s0, sy, a);
-        const Prim<real> w1 = smem_prim(S, s0, sy, a + 1);
-        const Prim<real> w2 = smem_prim(S, s0, sy, a + 2);
-        const Prim<real> w3 = smem_prim(S, s0, sy, a + 3);
-        const Prim<real> dL = limited_slope(w0, w1, w2);
-        const Prim<real> dR = limited_slope(w1, w2, w3);
-        real F[5];
-        face_flux(0, add_half(w1, dL, real(1)), add_half(w2, dR, real(-1)), gamma, gm1, F);
+        face_flux(0, DH_LOAD_PRIM(S.xp, ly, a), DH_LOAD_PRIM(S.xm, ly, a + 1), gamma, gm1, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) S.fx[c][ly][a] = F[c];
       } else {
         const int g = f - NXF;
         const int a = g / BX, lx = g - a * BX;
-        const int sx = lx + 2;
-        const Prim<real> w0 = smem_prim(S, s0, a, sx);
-        const Prim<real> w1 = smem_prim(S, s0, a + 1, sx);
-        const Prim<real> w2 = smem_prim(S, s0, a + 2, sx);
-        const Prim<real> w3 = smem_prim(S, s0, a + 3, sx);
-        const Prim<real> dL = limited_slope(w0, w1, w2);
-        const Prim<real> dR = limited_slope(w1, w2, w3);
-        real F[5];
-        face_flux(1, add_half(w1, dL, real(1)), add_half(w2, dR, real(-1)), gamma, gm1, F);
+        face_flux(1, DH_LOAD_PRIM(S.yp, a, lx), DH_LOAD_PRIM(S.ym, a + 1, lx), gamma, gm1, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) S.fy[c][a][lx] = F[c];
       }
     }
-    __syncthreads();
+    __syncthreads();  // ---- fluxes ready
 
     if (active) {
       const long long idx = (long long)k * plane + col;
@@ -315,9 +245,14 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
         }
       }
       if (STAGE == 2) {
-        if (p.forcing) {
+        if (forcing) {
+          // a = 2 Re sum_{n_x} B_{n_x} exp(2 pi i n_x x~)  (Sec. 3.1.1)
           real a[3];
-          forcing_accel(p.ahat_norm, p.tw, gx, gy, k, a);
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            a[c] = real(2) * (S.fB[ty][0][c][0] +
+                              (S.fB[ty][1][c][0] * twx[0] - S.fB[ty][1][c][1] * twx[1]) +
+                              (S.fB[ty][2][c][0] * twx[2] - S.fB[ty][2][c][1] * twx[3]));
           const real e = (u[1] * a[0] + u[2] * a[1] + u[3] * a[2]) * dt;
           u[1] = u[1] + u[0] * a[0] * dt;
           u[2] = u[2] + u[0] * a[1] * dt;
@@ -333,7 +268,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
         if (!finite) {
           flags |= FLAG_NONFINITE;
         } else {
-          const real pr = gm1 * (u[4] - real(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0]);
+          const real pr = gm1 * (u[4] - real(0.5) * q_div(u[1] * u[1] + u[2] * u[2] + u[3] * u[3], u[0]));
           if (!(u[0] > real(0)) || !(pr > real(0))) flags |= FLAG_POSITIVITY;
           if (p.reduce_cfl)
             tmin = fmin(tmin, cfl_time(u[0], u[1], u[2], u[3], u[4], gamma, gm1, p.dx, p.dy, p.dz));

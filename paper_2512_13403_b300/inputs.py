@@ -104,9 +104,11 @@ def turbulent_velocity(shape, seed, mach, rho, P, gamma, p=-4.0):
     return alpha * u
 
 
-def decaying_turbulence(shape, seed=2, sigma=0.5, mach=2.0, P0=0.6, gamma=5.0 / 3.0):
+def decaying_turbulence(shape, seed=2, sigma=0.5, mach=2.0, P0=0.6, gamma=5.0 / 3.0, p_sigma=0.0):
+    """Lognormal density, k^-4 velocities at rms Mach `mach`, pressure P0.  p_sigma > 0 adds
+    lognormal pressure fluctuations (a generic state: no exactly uniform field)."""
     rho = lognormal_density(shape, sigma, seed)
-    P = np.full(shape, P0)
+    P = np.full(shape, P0) if p_sigma == 0.0 else P0 * lognormal_density(shape, p_sigma, seed + 977)
     u = turbulent_velocity(shape, seed, mach, rho, P, gamma)
     return prim_to_state(rho, u[0], u[1], u[2], P, gamma)
 

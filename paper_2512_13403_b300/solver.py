@@ -161,6 +161,18 @@ class Solver:
                                               C.byref(cyc), C.byref(res)))
         return out, cyc.value, res.value
 
+    def solve_poisson(self, rho):
+        """Standalone multigrid solve for one density plane; returns (phi, cycles, rel_res)."""
+        if isinstance(rho, torch.Tensor):
+            if rho.dtype != self.dtype or tuple(rho.shape) != self.shape or not rho.is_contiguous():
+                raise ValueError("rho must be a contiguous plane of the solver dtype")
+            ptr, dev, keep = rho.data_ptr(), int(rho.is_cuda), rho
+        else:
+            keep = np.ascontiguousarray(rho, dtype=np.float64 if self.dtype == torch.float64 else np.float32)
+            ptr, dev = keep.ctypes.data, 0
+        self._check(self.lib.dh_solve_poisson(self.ctx, C.c_void_p(ptr), dev))
+        return self.potential()
+
     def adjoint_advance(self, n_steps: int, ckpt_every: int, dLdU_final):
         ptr, dev, keep = self._as_buffer(dLdU_final)
         out = torch.empty((5,) + self.shape, dtype=self.dtype, device="cuda" if dev else "cpu")

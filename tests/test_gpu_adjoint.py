@@ -1,0 +1,179 @@
+"""GPU hand adjoint (dh_adjoint_advance) against the oracle's reverse-mode product, finite
+differences of the GPU forward, the dot-product identity and the exact mass invariant.
+
+Derivative checks use generic states (every primitive field fluctuates).  A field that is
+exactly uniform puts every slope of that field on the MC limiter's kink (a = b = 0 up to
+round-off), where the step has no Jacobian: the branch is then picked by round-off, which the
+GPU (fused multiply-adds) and the CPU oracle resolve differently, and finite differences see a
+direction-dependent slope.  Uniform fields are exercised by the mass invariant, which holds on
+any branch."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import adjoint as oadj
+from oracle import hydro as ohydro
+from paper_2512_13403_b300 import inputs
+from tests.gpu_util import solver, to_gpu
+
+pytestmark = pytest.mark.gpu
+G = 5.0 / 3.0
+
+
+def _dx(shape):
+    nz, ny, nx = shape
+    return (1.0 / nx, 1.0 / ny, 1.0 / nz)
+
+
+def _oracle_dts(U0, shape, n):
+    U = torch.from_numpy(U0)
+    dts = []
+    for _ in range(n):
+        dt = ohydro.cfl_dt(U, G, _dx(shape), 0.4)
+        dts.append(dt)
+        U = ohydro.rk2_step(U, dt, G, _dx(shape))
+    return dts
+
+
+def _rel(a, b):
+    a = torch.as_tensor(a).double().cpu()
+    b = torch.as_tensor(b).double().cpu()
+    return float((a - b).norm() / b.norm())
+
+
+@pytest.mark.parametrize("shape,n,k", [((16, 16, 16), 6, 4), ((12, 10, 20), 5, 2), ((9, 12, 40), 3, 3)])
+def test_fp64_matches_oracle_vjp_smooth(shape, n, k):
+    U0 = inputs.decaying_turbulence(shape, seed=5, sigma=0.3, mach=0.8, p_sigma=0.3)
+    lam = np.random.default_rng(1).standard_normal((5,) + shape)
+    s = solver(shape, "f64")
+    s.init_state(to_gpu(U0, "f64"))
+    g = s.adjoint_advance(n, k, to_gpu(lam, "f64"))
+    dts = _oracle_dts(U0, shape, n)
+    ref = oadj.advance_vjp(torch.from_numpy(U0), dts, torch.from_numpy(lam), G, _dx(shape))
+    assert _rel(g, ref) < 1e-10
+    assert float((g.cpu() - ref).abs().max() / ref.abs().max()) < 1e-9
+
+
+def test_kelvin_helmholtz_mass_invariant():
+    """Piecewise-constant shear layer (on the limiter's kink almost everywhere): the gradient of
+    the mean final density is exact on every branch."""
+    shape = (16, 16, 16)
+    U0 = inputs.kelvin_helmholtz(shape, seed=0)
+    lam = np.zeros((5,) + shape)
+    lam[0] = 1.0 / 16 ** 3
+    s = solver(shape, "f64")
+    s.init_state(to_gpu(U0, "f64"))
+    g = s.adjoint_advance(4, 2, to_gpu(lam, "f64")).cpu()
+    assert float((g[0] - 1.0 / 16 ** 3).abs().max()) < 1e-15
+    assert float(g[1:].abs().max()) < 1e-15
+
+
+def test_central_finite_differences_fp64_16cubed():
+    shape = (16, 16, 16)
+    n = 10
+    U0 = inputs.decaying_turbulence(shape, seed=2, sigma=0.5, mach=1.0, p_sigma=0.3)
+    w = np.random.default_rng(3).standard_normal((5,) + shape)
+    s = solver(shape, "f64")
+    s.init_state(to_gpu(U0, "f64"))
+    g = s.adjoint_advance(n, 3, to_gpu(w, "f64")).cpu()
+    dts = _oracle_dts(U0, shape, n)
+    wt = torch.from_numpy(w).cuda()
+
+    def loss(U):
+        f = solver(shape, "f64")
+        f.init_state(to_gpu(U, "f64"))
+        for dt in dts:
+            f.step(dt, sync=False)
+        return float((wt * f.get_state()).sum())
+
+    rng = np.random.default_rng(4)
+    for _ in range(8):
+        i = tuple(int(rng.integers(0, d)) for d in (5,) + shape)
+        eps = 1e-6 * max(1.0, abs(U0[i]))
+        Up = U0.copy(); Up[i] += eps
+        Um = U0.copy(); Um[i] -= eps
+        fd = (loss(Up) - loss(Um)) / (2 * eps)
+        assert fd == pytest.approx(float(g[i]), rel=1e-3, abs=1e-6), i
+
+
+def test_dot_product_identity_fp64():
+    shape = (12, 12, 12)
+    n = 4
+    U0 = inputs.decaying_turbulence(shape, seed=6, sigma=0.3, mach=0.6, p_sigma=0.3)
+    rng = np.random.default_rng(5)
+    lam = rng.standard_normal((5,) + shape)
+    v = rng.standard_normal((5,) + shape) * np.abs(U0).mean(axis=(1, 2, 3), keepdims=True)
+    s = solver(shape, "f64")
+    s.init_state(to_gpu(U0, "f64"))
+    JTl = s.adjoint_advance(n, 2, to_gpu(lam, "f64")).cpu().numpy()
+    dts = _oracle_dts(U0, shape, n)
+
+    def fwd(U):
+        f = solver(shape, "f64")
+        f.init_state(to_gpu(U, "f64"))
+        for dt in dts:
+            f.step(dt, sync=False)
+        return f.get_state().cpu().numpy()
+
+    # a small step keeps the finite difference off the limiter's kinks (|a|, |b| ~ eps |U|)
+    eps = 1e-8
+    Jv = (fwd(U0 + eps * v) - fwd(U0 - eps * v)) / (2 * eps)
+    a = float((lam * Jv).sum())
+    b = float((JTl * v).sum())
+    assert a == pytest.approx(b, rel=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_mass_invariant(prec):
+    shape = (16, 16, 16)
+    U0 = inputs.decaying_turbulence(shape, seed=7, sigma=0.5, mach=1.5)
+    N3 = 16 ** 3
+    lam = np.zeros((5,) + shape)
+    lam[0] = 1.0 / N3
+    s = solver(shape, prec)
+    s.init_state(to_gpu(U0, prec))
+    g = s.adjoint_advance(8, 3, to_gpu(lam, prec)).double().cpu()
+    tol = 1e-15 if prec == "f64" else 1e-9
+    assert float((g[0] - 1.0 / N3).abs().max()) < tol
+    assert float(g[1:].abs().max()) < tol
+
+
+def test_fp32_matches_fp64_oracle_to_1e_3():
+    shape = (32, 32, 32)
+    n = 10
+    U0 = inputs.decaying_turbulence(shape, seed=2, sigma=0.5, mach=2.0, p_sigma=0.3)
+    lam = np.zeros((5,) + shape)
+    rho_t = inputs.decaying_turbulence(shape, seed=3, sigma=0.5, mach=2.0, p_sigma=0.3)[0]
+    # MSE on the final density against a target (the reconstruction loss)
+    dts = _oracle_dts(U0, shape, n)
+    Uf = oadj.advance(torch.from_numpy(U0), dts, G, _dx(shape))
+    lam[0] = 2.0 * (Uf[0].numpy() - rho_t) / rho_t.size
+    s = solver(shape, "f32")
+    s.init_state(to_gpu(U0, "f32"))
+    g = s.adjoint_advance(n, 4, to_gpu(lam, "f32"))
+    ref = oadj.advance_vjp(torch.from_numpy(U0), dts, torch.from_numpy(lam), G, _dx(shape))
+    assert _rel(g, ref) < 1e-3
+
+
+def test_autograd_function_backward():
+    from paper_2512_13403_b300 import autograd as dag
+    shape = (16, 16, 16)
+    U0 = to_gpu(inputs.decaying_turbulence(shape, seed=9, sigma=0.3, mach=0.7, p_sigma=0.3), "f64").requires_grad_(True)
+    s = solver(shape, "f64")
+    Un = dag.advance(U0, s, 5, 2)
+    w = torch.randn_like(Un)
+    (w * Un).sum().backward()
+    s2 = solver(shape, "f64")
+    s2.init_state(U0.detach())
+    ref = s2.adjoint_advance(5, 5, w)
+    assert torch.allclose(U0.grad, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_adjoint_rejects_sources():
+    from paper_2512_13403_b300._lib import DH_ERR_ARG, DhError
+    shape = (8, 8, 8)
+    s = solver(shape, "f64", cooling=True)
+    s.init_state(to_gpu(inputs.cooling_box(shape), "f64"))
+    with pytest.raises(DhError) as e:
+        s.adjoint_advance(2, 1, to_gpu(np.zeros((5,) + shape), "f64"))
+    assert e.value.status == DH_ERR_ARG

@@ -12,7 +12,7 @@ G = 5.0 / 3.0
 
 
 def _setup(n=8, steps=4, seed=2, mach=0.8):
-    U0 = torch.from_numpy(inputs.decaying_turbulence((n, n, n), seed=seed, sigma=0.3, mach=mach))
+    U0 = torch.from_numpy(inputs.decaying_turbulence((n, n, n), seed=seed, sigma=0.3, mach=mach, p_sigma=0.3))
     dx = (1.0 / n,) * 3
     dts = []
     U = U0.clone()
