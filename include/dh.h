@@ -145,6 +145,26 @@ dh_status dh_solve_poisson(dh_ctx* ctx, const void* rho, int on_device);
 dh_status dh_adjoint_advance(dh_ctx* ctx, int n_steps, int ckpt_every, const void* dLdU_final,
                              void* dLdU0, int on_device);
 
+/* Conserved totals (as dh_conserved_totals) for callers that cannot allocate device memory,
+   such as a host framework whose allocator owns the whole device-memory budget, or a
+   time-critical loop that must not pay for the implicit device synchronisation of cudaMalloc.
+   The paper has no counterpart; this entry point exists for such integrations only.
+   Needs no context and allocates nothing: the per-block partial sums live in a fixed
+   file-scope device array of 160 KiB (4096 blocks x 5 doubles) that every device which loads
+   the library keeps until the process exits.
+     U          device pointer to a state (layout above) of `precision` (DH_F32 or DH_F64)
+     n_cells    nx*ny*nz, at most 268435456 (4096 blocks of 65536 cells); larger or < 1 is
+                DH_ERR_ARG with the limit in dh_last_error(NULL)
+     totals_out device pointer to 5 doubles (rho, m_x, m_y, m_z, E), caller-owned
+     cuda_stream cudaStream_t on which the work is ordered (NULL = legacy default stream)
+   Asynchronous: the result is ready when the stream reaches this point.  The first call on a
+   device looks the array's device address up once (cudaGetSymbolAddress) and caches it; make
+   that first call before capturing the stream into a graph.  All calls share the array, which
+   keeps the last call's contents (every slot a call reads is written earlier in the same call);
+   calls whose kernels overlap on the GPU race on it and may return wrong sums. */
+dh_status dh_conserved_totals_static(const void* U, int precision, long long n_cells,
+                                     double* totals_out, void* cuda_stream);
+
 /* Profiling: when enabled, device time of every kernel launch is accumulated per kernel kind
    with CUDA events on the context stream.  dh_profile_read returns, for kernel kind `kind`
    (see DH_KERNEL_*), the number of launches and their total milliseconds since the last

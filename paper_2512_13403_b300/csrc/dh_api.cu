@@ -15,6 +15,8 @@ using namespace dh;
 
 static thread_local std::string g_create_error;
 
+void dh_set_global_error(const std::string& msg) { g_create_error = msg; }
+
 static dh_status fail(dh_ctx* c, dh_status s, const std::string& msg) {
   if (c) c->err = msg; else g_create_error = msg;
   return s;
