@@ -145,6 +145,32 @@ dh_status dh_solve_poisson(dh_ctx* ctx, const void* rho, int on_device);
 dh_status dh_adjoint_advance(dh_ctx* ctx, int n_steps, int ckpt_every, const void* dLdU_final,
                              void* dLdU0, int on_device);
 
+/* ---- Corrector building blocks (residual 3D CNN, BF16 tensor cores, FP32 accumulation) ----
+   A 3x3x3 periodic convolution over an nx*ny*nz grid as an implicit GEMM on tcgen05:
+   out[cell, n] = sum_{tap, c} act[cell + offset(tap), c] * W[n, c, tap] (+ bias[n]), the
+   closure network of Sec. 7 in 3D.  Activations are bf16, channel-last [cell][cin_pad] with
+   cin_pad 8 (up to 8 real channels, the rest zero) or 32; nx*ny*nz must be a multiple of 128
+   and every dimension >= 3.  All pointers are device pointers; work is ordered on `stream`.
+
+   dh_pack_conv_weights: converts fp32 weights W[cout][cin][3][3][3] (cross-correlation order,
+   kernel index (kz, ky, kx) = offset + 1) into the packed bf16 operand `packed` of
+   n_pad * k_pad elements (n_pad = 32 if the packed output count is 32, else 16; k_pad = 864
+   for 9..32 input channels, 224 for <= 8).  transpose_flip = 0 packs the forward
+   convolution (outputs = cout); 1 packs its data gradient (outputs = cin, taps mirrored), so
+   that the same kernel maps an output gradient to an input gradient.
+
+   dh_conv3d_bf16 modes: 0 = GELU (out bf16 [cell][32] = bf16(gelu(z)), z_out fp32
+   [cell][32] = acc + bias, nullable); 1 = linear (out fp32 planar [n_real][cell] = acc + bias);
+   2 = GELU gradient (out bf16 [cell][32] = bf16(acc * gelu'(z_in))).  Supported
+   (cin_pad, nout_pad, mode): (8,32,0), (8,32,2), (32,32,0), (32,32,2), (32,16,1), (32,32,1).
+   *err_flag (device unsigned) becomes nonzero if a bounded wait inside the kernel gave up. */
+dh_status dh_pack_conv_weights(const float* W, int cout, int cin, int transpose_flip,
+                               void* packed, void* stream);
+dh_status dh_conv3d_bf16(const void* act, int cin_pad, const void* packed, int nout_pad,
+                         const float* bias, int mode, const float* z_in, void* out,
+                         float* z_out, int n_real, int nx, int ny, int nz, unsigned* err_flag,
+                         void* stream);
+
 /* Conserved totals (as dh_conserved_totals) for callers that cannot allocate device memory,
    such as a host framework whose allocator owns the whole device-memory budget, or a
    time-critical loop that must not pay for the implicit device synchronisation of cudaMalloc.

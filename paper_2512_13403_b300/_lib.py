@@ -50,6 +50,9 @@ _SIGNATURES = {
     "dh_solve_poisson": (C.c_int, [_P, _P, C.c_int]),
     "dh_adjoint_advance": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dh_conserved_totals_static": (C.c_int, [_P, C.c_int, C.c_longlong, _P, _P]),
+    "dh_pack_conv_weights": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "dh_conv3d_bf16": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int, _P, _P, _P, C.c_int,
+                                 C.c_int, C.c_int, C.c_int, _P, _P]),
     "dh_profile_enable": (C.c_int, [_P, C.c_int]),
     "dh_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
     "dh_launch_count": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
