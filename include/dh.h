@@ -171,6 +171,49 @@ dh_status dh_conv3d_bf16(const void* act, int cin_pad, const void* packed, int n
                          float* z_out, int n_real, int nx, int ny, int nz, unsigned* err_flag,
                          void* stream);
 
+/* dh_conv3d_wgrad_bf16: weight gradient of such a convolution,
+   dW[n][c][tap] = sum_cells grad[cell][n] * act[cell + offset(tap)][c], written in the fp32
+   master layout W[cout][cin][27].  act: bf16 [cell][cin_pad] (cin real channels); grad: bf16
+   [cell][grad_stride] (cout real channels, the rest zero), grad_stride 8 or 32.  `partial` is
+   caller-owned fp32 scratch of nctas * ceil(27*cin_pad/128) * 128 * (cout > 16 ? 32 : 16)
+   values; the per-CTA partial sums are added in a fixed order. */
+dh_status dh_conv3d_wgrad_bf16(const void* act, int cin_pad, int cin, const void* grad,
+                               int grad_stride, int cout, int nx, int ny, int nz, float* partial,
+                               int nctas, float* dW, unsigned* err_flag, void* stream);
+
+/* The corrector network (Sec. 7 closure, BASELINE's 3D CNN): x0 = bf16((U - mu)/sigma),
+   z1 = conv(x0, W1) + b1, h1 = bf16(gelu(z1)), z2 = conv(h1, W2) + b2, h2 = bf16(gelu(z2)),
+   y = conv(h2, W3) + b3, all 3x3x3 periodic, channels 5 -> 32 -> 32 -> 5.  Parameters are one
+   flat fp32 device array of dh_cnn_param_count() = 36357 values: W1[32][5][27], b1[32],
+   W2[32][32][27], b2[32], W3[5][32][27], b3[5]; norm10 = mu[5], sigma[5] (host, sigma > 0).
+   A dh_cnn owns the activations of one grid (nx*ny*nz divisible by 128). */
+typedef struct dh_cnn dh_cnn;
+long long dh_cnn_param_count(void);
+dh_status dh_cnn_create(int nx, int ny, int nz, void* cuda_stream, dh_cnn** out);
+void dh_cnn_destroy(dh_cnn* cnn);
+/* Copies the parameters and packs the tensor-core operands (synchronises). */
+dh_status dh_cnn_set_params(dh_cnn* cnn, const float* params, const float* norm10);
+/* y = network(U) for a float32 state U (device, state layout); y_out (nullable, device) gets
+   y as 5 planes.  Keeps the activations for dh_cnn_backward. */
+dh_status dh_cnn_forward(dh_cnn* cnn, const float* U, float* y_out);
+/* Loss = mean over 5 channels and cells of (y - target)^2 for the last forward (target: 5 planes
+   float32, device); writes d loss / d params into grads (device, 36357 floats) and the loss into
+   *loss (host, nullable).  Synchronises. */
+dh_status dh_cnn_backward(dh_cnn* cnn, const float* target, float* grads, double* loss);
+/* U <- U + sigma * network(U) in place (float32 state, device), then rho >= rho_floor and
+   E >= |m|^2/(2 rho) + rho T_floor/(gamma - 1).  Synchronises. */
+dh_status dh_cnn_correct_state(dh_cnn* cnn, float* U, double rho_floor, double T_floor,
+                               double gamma);
+/* Adam (Kingma & Ba) on n parameters: m, v are caller-owned moment buffers (device), step >= 1
+   the 1-based step count for the bias corrections. */
+dh_status dh_adam_step(float* params, const float* grads, float* m, float* v, long long n,
+                       double lr, double beta1, double beta2, double eps, int step, void* stream);
+/* Corrector of a float32 context: dh_set_corrector copies the parameters (as dh_cnn_set_params);
+   dh_correct applies U <- U + sigma * network(U) to the current state with the floors above
+   (rho_floor = 1e-6 <rho>, the context's T_floor and gamma).  DH_ERR_STATE without a corrector. */
+dh_status dh_set_corrector(dh_ctx* ctx, const float* params, const float* norm10);
+dh_status dh_correct(dh_ctx* ctx);
+
 /* Conserved totals (as dh_conserved_totals) for callers that cannot allocate device memory,
    such as a host framework whose allocator owns the whole device-memory budget, or a
    time-critical loop that must not pay for the implicit device synchronisation of cudaMalloc.

@@ -53,6 +53,19 @@ _SIGNATURES = {
     "dh_pack_conv_weights": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
     "dh_conv3d_bf16": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int, _P, _P, _P, C.c_int,
                                  C.c_int, C.c_int, C.c_int, _P, _P]),
+    "dh_conv3d_wgrad_bf16": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_int, C.c_int,
+                                       C.c_int, C.c_int, _P, C.c_int, _P, _P, _P]),
+    "dh_cnn_param_count": (C.c_longlong, []),
+    "dh_cnn_create": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, C.POINTER(_P)]),
+    "dh_cnn_destroy": (None, [_P]),
+    "dh_cnn_set_params": (C.c_int, [_P, _P, C.POINTER(C.c_float)]),
+    "dh_cnn_forward": (C.c_int, [_P, _P, _P]),
+    "dh_cnn_backward": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double)]),
+    "dh_cnn_correct_state": (C.c_int, [_P, _P, C.c_double, C.c_double, C.c_double]),
+    "dh_adam_step": (C.c_int, [_P, _P, _P, _P, C.c_longlong, C.c_double, C.c_double, C.c_double,
+                               C.c_double, C.c_int, _P]),
+    "dh_set_corrector": (C.c_int, [_P, _P, C.POINTER(C.c_float)]),
+    "dh_correct": (C.c_int, [_P]),
     "dh_profile_enable": (C.c_int, [_P, C.c_int]),
     "dh_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
     "dh_launch_count": (C.c_int, [_P, C.POINTER(C.c_longlong)]),

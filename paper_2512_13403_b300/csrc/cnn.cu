@@ -1,0 +1,351 @@
+// The corrector network around the tensor-core convolutions: normalisation, the three layers,
+// the residual correction with its floors, the mean-squared-error gradient, back-propagation
+// (data and weight gradients on the tensor cores, bias gradients by reduction) and Adam.
+//
+// Network: x0 = bf16((U - mu)/sigma) (5 channels, padded to 8); z1 = conv(x0, W1) + b1,
+// h1 = bf16(gelu(z1)); z2 = conv(h1, W2) + b2, h2 = bf16(gelu(z2)); y = conv(h2, W3) + b3.
+// Correction: U <- U + sigma * y, rho >= rho_floor, E raised so that the thermal energy is at
+// least rho T_floor / (gamma - 1).  Parameters, flat fp32: W1[32][5][27], b1[32],
+// W2[32][32][27], b2[32], W3[5][32][27], b3[5] (36357 values).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <string>
+
+#include "dh_internal.h"
+
+namespace {
+constexpr int NPARAM = 32 * 5 * 27 + 32 + 32 * 32 * 27 + 32 + 5 * 32 * 27 + 5;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + 32 * 5 * 27, OFF_W2 = OFF_B1 + 32,
+              OFF_B2 = OFF_W2 + 32 * 32 * 27, OFF_W3 = OFF_B2 + 32, OFF_B3 = OFF_W3 + 5 * 32 * 27;
+static_assert(OFF_B3 + 5 == NPARAM, "parameter layout");
+constexpr int RBLOCKS = 256;
+}  // namespace
+
+extern "C" dh_status dh_pack_conv_weights(const float*, int, int, int, void*, void*);
+extern "C" dh_status dh_conv3d_bf16(const void*, int, const void*, int, const float*, int,
+                                    const float*, void*, float*, int, int, int, int, unsigned*,
+                                    void*);
+extern "C" dh_status dh_conv3d_wgrad_bf16(const void*, int, int, const void*, int, int, int, int,
+                                          int, float*, int, float*, unsigned*, void*);
+
+struct dh_cnn {
+  int nx = 0, ny = 0, nz = 0;
+  long long ncell = 0;
+  cudaStream_t stream = nullptr;
+  float* params = nullptr;                  // device copy of the parameters
+  float norm[10] = {0};                     // mu[5], sigma[5]
+  float* norm_dev = nullptr;
+  __nv_bfloat16 *pk_w1 = nullptr, *pk_w2 = nullptr, *pk_w3 = nullptr;   // forward operands
+  __nv_bfloat16 *pk_w2t = nullptr, *pk_w3t = nullptr;                  // data-gradient operands
+  __nv_bfloat16 *x0 = nullptr, *h1 = nullptr, *h2 = nullptr;            // activations
+  float *z1 = nullptr, *z2 = nullptr, *y = nullptr;
+  __nv_bfloat16 *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr;          // gradients
+  float* partial = nullptr;                 // weight-gradient partials
+  int nctas = 148;
+  double* red = nullptr;                    // reduction scratch
+  unsigned* err = nullptr;
+  bool have_params = false;
+  bool have_forward = false;
+  std::string msg;
+};
+
+namespace dh {
+
+__global__ void normalize_kernel(const float* __restrict__ U, long long n, const float* __restrict__ norm,
+                                 __nv_bfloat16* __restrict__ x0) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v[c] = __float2bfloat16_rn((U[c * n + q] - norm[c]) / norm[5 + c]);
+    v[5] = v[6] = v[7] = __float2bfloat16_rn(0.0f);
+    reinterpret_cast<uint4*>(x0)[q] = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+// loss = mean over 5 channels and cells of (y - t)^2; dy = d loss / d y as bf16 [cell][8]
+__global__ void mse_grad_kernel(const float* __restrict__ y, const float* __restrict__ t, long long n,
+                                __nv_bfloat16* __restrict__ dy, double* __restrict__ partial) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const double scale = 2.0 / (5.0 * (double)n);
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long b0 = blockIdx.x * per, b1 = b0 + per < n ? b0 + per : n;
+  for (long long q = b0 + threadIdx.x; q < b1; q += blockDim.x) {
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const double d = (double)y[c * n + q] - (double)t[c * n + q];
+      s += d * d;
+      v[c] = __float2bfloat16_rn((float)(scale * d));
+    }
+    v[5] = v[6] = v[7] = __float2bfloat16_rn(0.0f);
+    reinterpret_cast<uint4*>(dy)[q] = *reinterpret_cast<const uint4*>(v);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sum_blocks_kernel(const double* partial, int nb, double scale, double* out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partial[b];
+    *out = scale * s;
+  }
+}
+
+// db[c] = sum over cells of g[cell][c] (bf16 [cell][stride]) for c < nch; one block per channel
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ g, int stride, long long n,
+                                 float* __restrict__ db) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (long long q = threadIdx.x; q < n; q += blockDim.x) s += (double)__bfloat162float(g[q * stride + c]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[c] = (float)red[0];
+}
+
+__global__ void correct_kernel(float* __restrict__ U, const float* __restrict__ y, long long n,
+                               const float* __restrict__ norm, float rho_floor, float T_floor,
+                               float gm1) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    float v[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v[c] = U[c * n + q] + norm[5 + c] * y[c * n + q];
+    const float rho = fmaxf(v[0], rho_floor);
+    const float kin = 0.5f * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / rho;
+    const float Emin = kin + rho * T_floor / gm1;
+    U[q] = rho;
+    U[n + q] = v[1];
+    U[2 * n + q] = v[2];
+    U[3 * n + q] = v[3];
+    U[4 * n + q] = fmaxf(v[4], Emin);
+  }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+static int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 148 * 8) b = 148 * 8;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace dh
+
+using namespace dh;
+
+#define CNN_TRY(call)                                   \
+  do {                                                  \
+    dh_status s__ = (call);                             \
+    if (s__ != DH_OK) return s__;                       \
+  } while (0)
+
+static dh_status cnn_cuda(dh_cnn* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return DH_OK;
+  c->msg = std::string(where) + ": " + cudaGetErrorString(e);
+  dh_set_global_error(c->msg);
+  return DH_ERR_CUDA;
+}
+
+extern "C" void dh_cnn_destroy(dh_cnn* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+  void* ps[] = {c->params, c->norm_dev, c->pk_w1, c->pk_w2, c->pk_w3, c->pk_w2t, c->pk_w3t,
+                c->x0, c->h1, c->h2, c->z1, c->z2, c->y, c->dy, c->dz2, c->dz1, c->partial,
+                c->red, c->err};
+  for (void* p : ps) cudaFree(p);
+  delete c;
+}
+
+extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn** out) {
+  if (!out) return DH_ERR_ARG;
+  *out = nullptr;
+  const long long n = (long long)nx * ny * nz;
+  if (nx < 3 || ny < 3 || nz < 3 || n % 128 != 0) {
+    dh_set_global_error("dh_cnn_create: every dimension >= 3 and nx*ny*nz divisible by 128");
+    return DH_ERR_ARG;
+  }
+  dh_cnn* c = new dh_cnn();
+  c->nx = nx; c->ny = ny; c->nz = nz; c->ncell = n;
+  c->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->nctas, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t b) { if (e == cudaSuccess) e = cudaMalloc(p, b); };
+  A((void**)&c->params, NPARAM * sizeof(float));
+  A((void**)&c->norm_dev, 10 * sizeof(float));
+  A((void**)&c->pk_w1, 32 * 224 * 2);
+  A((void**)&c->pk_w2, 32 * 864 * 2);
+  A((void**)&c->pk_w3, 16 * 864 * 2);
+  A((void**)&c->pk_w2t, 32 * 864 * 2);
+  A((void**)&c->pk_w3t, 32 * 224 * 2);
+  A((void**)&c->x0, n * 8 * 2);
+  A((void**)&c->h1, n * 32 * 2);
+  A((void**)&c->h2, n * 32 * 2);
+  A((void**)&c->z1, n * 32 * 4);
+  A((void**)&c->z2, n * 32 * 4);
+  A((void**)&c->y, n * 5 * 4);
+  A((void**)&c->dy, n * 8 * 2);
+  A((void**)&c->dz2, n * 32 * 2);
+  A((void**)&c->dz1, n * 32 * 2);
+  A((void**)&c->partial, (size_t)c->nctas * 7 * 128 * 32 * sizeof(float));
+  A((void**)&c->red, (RBLOCKS + 8) * sizeof(double));
+  A((void**)&c->err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    dh_set_global_error(std::string("dh_cnn_create: ") + cudaGetErrorString(e));
+    dh_cnn_destroy(c);
+    return DH_ERR_CUDA;
+  }
+  *out = c;
+  return DH_OK;
+}
+
+extern "C" dh_status dh_cnn_set_params(dh_cnn* c, const float* params_dev, const float* norm10) {
+  if (!c || !params_dev || !norm10) return DH_ERR_ARG;
+  for (int k = 0; k < 5; ++k)
+    if (!(norm10[5 + k] > 0.0f)) { dh_set_global_error("dh_cnn_set_params: sigma must be > 0"); return DH_ERR_ARG; }
+  for (int k = 0; k < 10; ++k) c->norm[k] = norm10[k];
+  cudaStream_t s = c->stream;
+  CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(c->params, params_dev, NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, s), "params"));
+  CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(c->norm_dev, c->norm, 10 * sizeof(float), cudaMemcpyHostToDevice, s), "norm"));
+  CNN_TRY(dh_pack_conv_weights(c->params + OFF_W1, 32, 5, 0, c->pk_w1, s));
+  CNN_TRY(dh_pack_conv_weights(c->params + OFF_W2, 32, 32, 0, c->pk_w2, s));
+  CNN_TRY(dh_pack_conv_weights(c->params + OFF_W3, 5, 32, 0, c->pk_w3, s));
+  CNN_TRY(dh_pack_conv_weights(c->params + OFF_W2, 32, 32, 1, c->pk_w2t, s));
+  CNN_TRY(dh_pack_conv_weights(c->params + OFF_W3, 5, 32, 1, c->pk_w3t, s));
+  CNN_TRY(cnn_cuda(c, cudaStreamSynchronize(s), "set_params"));
+  c->have_params = true;
+  return DH_OK;
+}
+
+static dh_status check_err(dh_cnn* c) {
+  unsigned h = 0;
+  CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(&h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "err"));
+  CNN_TRY(cnn_cuda(c, cudaStreamSynchronize(c->stream), "sync"));
+  if (h) {
+    cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream);
+    dh_set_global_error("corrector: a bounded tensor-core wait gave up");
+    return DH_ERR_CUDA;
+  }
+  return DH_OK;
+}
+
+extern "C" dh_status dh_cnn_forward(dh_cnn* c, const float* U, float* y_out) {
+  if (!c || !U) return DH_ERR_ARG;
+  if (!c->have_params) { dh_set_global_error("dh_cnn_forward: parameters not set"); return DH_ERR_STATE; }
+  const long long n = c->ncell;
+  cudaStream_t s = c->stream;
+  normalize_kernel<<<grid_for(n), 256, 0, s>>>(U, n, c->norm_dev, c->x0);
+  CNN_TRY(cnn_cuda(c, cudaGetLastError(), "normalize"));
+  CNN_TRY(dh_conv3d_bf16(c->x0, 8, c->pk_w1, 32, c->params + OFF_B1, 0, nullptr, c->h1, c->z1, 32, c->nx, c->ny, c->nz, c->err, s));
+  CNN_TRY(dh_conv3d_bf16(c->h1, 32, c->pk_w2, 32, c->params + OFF_B2, 0, nullptr, c->h2, c->z2, 32, c->nx, c->ny, c->nz, c->err, s));
+  CNN_TRY(dh_conv3d_bf16(c->h2, 32, c->pk_w3, 16, c->params + OFF_B3, 1, nullptr, c->y, nullptr, 5, c->nx, c->ny, c->nz, c->err, s));
+  if (y_out) CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(y_out, c->y, n * 5 * sizeof(float), cudaMemcpyDeviceToDevice, s), "y"));
+  c->have_forward = true;
+  return DH_OK;
+}
+
+extern "C" dh_status dh_cnn_backward(dh_cnn* c, const float* target, float* grads, double* loss) {
+  if (!c || !target || !grads) return DH_ERR_ARG;
+  if (!c->have_forward) { dh_set_global_error("dh_cnn_backward: run dh_cnn_forward first"); return DH_ERR_STATE; }
+  const long long n = c->ncell;
+  cudaStream_t s = c->stream;
+  mse_grad_kernel<<<RBLOCKS, 256, 0, s>>>(c->y, target, n, c->dy, c->red);
+  sum_blocks_kernel<<<1, 32, 0, s>>>(c->red, RBLOCKS, 1.0 / (5.0 * (double)n), c->red + RBLOCKS);
+  // output layer
+  CNN_TRY(dh_conv3d_wgrad_bf16(c->h2, 32, 32, c->dy, 8, 5, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W3, c->err, s));
+  bias_grad_kernel<<<5, 256, 0, s>>>(c->dy, 8, n, grads + OFF_B3);
+  CNN_TRY(dh_conv3d_bf16(c->dy, 8, c->pk_w3t, 32, nullptr, 2, c->z2, c->dz2, nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
+  // hidden layer
+  CNN_TRY(dh_conv3d_wgrad_bf16(c->h1, 32, 32, c->dz2, 32, 32, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W2, c->err, s));
+  bias_grad_kernel<<<32, 256, 0, s>>>(c->dz2, 32, n, grads + OFF_B2);
+  CNN_TRY(dh_conv3d_bf16(c->dz2, 32, c->pk_w2t, 32, nullptr, 2, c->z1, c->dz1, nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
+  // first layer
+  CNN_TRY(dh_conv3d_wgrad_bf16(c->x0, 8, 5, c->dz1, 32, 32, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W1, c->err, s));
+  bias_grad_kernel<<<32, 256, 0, s>>>(c->dz1, 32, n, grads + OFF_B1);
+  CNN_TRY(cnn_cuda(c, cudaGetLastError(), "backward"));
+  if (loss) CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(loss, c->red + RBLOCKS, sizeof(double), cudaMemcpyDeviceToHost, s), "loss"));
+  return check_err(c);
+}
+
+extern "C" dh_status dh_cnn_correct_state(dh_cnn* c, float* U, double rho_floor, double T_floor,
+                                          double gamma) {
+  if (!c || !U) return DH_ERR_ARG;
+  CNN_TRY(dh_cnn_forward(c, U, nullptr));
+  correct_kernel<<<grid_for(c->ncell), 256, 0, c->stream>>>(U, c->y, c->ncell, c->norm_dev,
+                                                            (float)rho_floor, (float)T_floor,
+                                                            (float)(gamma - 1.0));
+  CNN_TRY(cnn_cuda(c, cudaGetLastError(), "correct"));
+  return check_err(c);
+}
+
+extern "C" dh_status dh_adam_step(float* params, const float* grads, float* m, float* v, long long n,
+                                  double lr, double beta1, double beta2, double eps, int step,
+                                  void* stream) {
+  if (!params || !grads || !m || !v || n < 1 || step < 1) return DH_ERR_ARG;
+  const float c1 = (float)(1.0 - pow(beta1, step)), c2 = (float)(1.0 - pow(beta2, step));
+  adam_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, n, (float)lr,
+                                                             (float)beta1, (float)beta2,
+                                                             (float)eps, c1, c2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
+  return DH_OK;
+}
+
+extern "C" long long dh_cnn_param_count(void) { return NPARAM; }
+
+// ---- the context's corrector -------------------------------------------------------------------
+extern "C" dh_status dh_set_corrector(dh_ctx* ctx, const float* params_dev, const float* norm10) {
+  if (!ctx || !params_dev || !norm10) return DH_ERR_ARG;
+  if (ctx->prec != DH_F32) { ctx->err = "the corrector runs on float32 states"; return DH_ERR_ARG; }
+  if (!ctx->cnn) {
+    dh_status st = dh_cnn_create(ctx->cfg.nx, ctx->cfg.ny, ctx->cfg.nz, ctx->stream, &ctx->cnn);
+    if (st != DH_OK) { ctx->err = dh_last_error(nullptr); return st; }
+  }
+  dh_status st = dh_cnn_set_params(ctx->cnn, params_dev, norm10);
+  if (st != DH_OK) ctx->err = dh_last_error(nullptr);
+  return st;
+}
+
+extern "C" dh_status dh_correct(dh_ctx* ctx) {
+  if (!ctx) return DH_ERR_ARG;
+  if (!ctx->cnn || !ctx->cnn->have_params) { ctx->err = "no corrector set"; return DH_ERR_STATE; }
+  if (!ctx->initialized) { ctx->err = "state not initialised"; return DH_ERR_STATE; }
+  // rho floor: 1e-6 of the mean density
+  double tot[5];
+  dh_status st = dh_conserved_totals(ctx, tot);
+  if (st != DH_OK) return st;
+  const double rho_floor = 1e-6 * tot[0] / (double)ctx->n3;
+  st = dh_cnn_correct_state(ctx->cnn, (float*)ctx->U[ctx->cur], rho_floor, ctx->cfg.t_floor,
+                            ctx->cfg.gamma);
+  if (st != DH_OK) { ctx->err = dh_last_error(nullptr); return st; }
+  // the state changed: the next CFL step must see it
+  return dh_refresh_cfl(ctx);
+}

@@ -316,3 +316,230 @@ extern "C" dh_status dh_conv3d_bf16(const void* act, int cin_pad, const void* pa
   if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
   return DH_OK;
 }
+
+// =============================================================================================
+// Weight gradient: dW[n][c][tap] = sum_cells g[cell][n] * act[cell + offset(tap)][c], a GEMM
+// with M = (tap, c) rows (27 * CIN, in tiles of 128), N = n, K = cells.  Each CTA reduces a
+// contiguous range of cells in 16-cell K steps: the threads gather, for every tap, the 16
+// neighbour rows and transpose them into K-major core matrices (a row holds one (tap, c) over
+// 16 consecutive cells), the gradient rows likewise; one thread issues one MMA per M tile into
+// its own TMEM accumulator.  Per-CTA partial sums go to global memory and a second kernel adds
+// them in a fixed order.
+namespace dh {
+
+constexpr int WG_THREADS = 128;
+constexpr int WG_STAGES = 2;
+
+template <int CIN, int NOUT>
+__global__ void __launch_bounds__(WG_THREADS)
+conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat16* __restrict__ g,
+                       int g_stride, int nx, int ny, int nz, long long cells_per_cta,
+                       float* __restrict__ partial, unsigned* err) {
+  constexpr int MROWS = 27 * CIN;
+  constexpr int MT = (MROWS + 127) / 128;           // M tiles
+  constexpr int A_TILE = 128 * 16 * 2;              // bytes per M tile per stage
+  constexpr int B_TILE = NOUT * 16 * 2;
+  constexpr int STAGE = MT * A_TILE + B_TILE;
+  constexpr uint32_t TMEM_COLS = MT * NOUT <= 32 ? 32 : (MT * NOUT <= 64 ? 64 : (MT * NOUT <= 128 ? 128 : 256));
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + WG_STAGES * STAGE);
+  uint64_t* bar_done = bars + WG_STAGES;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar_done + 1);
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long long ncell = (long long)nx * ny * nz;
+  const long long c0 = (long long)blockIdx.x * cells_per_cta;
+  const long long c1 = c0 + cells_per_cta < ncell ? c0 + cells_per_cta : ncell;
+  const int ksteps = c1 > c0 ? (int)((c1 - c0 + 15) / 16) : 0;
+
+  // zero both stages once: padding rows (beyond 27 * CIN) and tail cells stay zero
+  for (int i = tid; i < WG_STAGES * STAGE / 16; i += WG_THREADS)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) {
+    for (int b = 0; b < WG_STAGES; ++b) tc::mbar_init(&bars[b], 1);
+    tc::mbar_init(bar_done, 1);
+    tc::mbar_fence_init();
+    s_abort = 0;
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(s_tmem, TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t idesc = tc::idesc_bf16_f32(128, NOUT);
+  const uint32_t s_addr = tc::smem_u32(smem);
+  uint32_t phase_bits = 0;
+
+  for (int s = 0; s < ksteps; ++s) {
+    const int b = s % WG_STAGES;
+    if (s >= WG_STAGES) {
+      if (!tc::mbar_wait(&bars[b], (phase_bits >> b) & 1u, CV_WAIT_ITERS)) s_abort = 1;
+      phase_bits ^= 1u << b;
+    }
+    unsigned char* st = smem + b * STAGE;
+    const long long x0 = c0 + 16LL * s;
+    // A: items (tap, channel group of 8, cell k); each loads 8 channels and scatters them
+    for (int it = tid; it < 27 * (CIN / 8) * 16; it += WG_THREADS) {
+      const int k = it & 15;
+      const int rest = it >> 4;
+      const int cg = rest % (CIN / 8), tap = rest / (CIN / 8);
+      const long long x = x0 + k;
+      __align__(16) __nv_bfloat16 v[8];
+      if (x < c1) {
+        const int i = (int)(x % nx);
+        const long long t1 = x / nx;
+        const int j = (int)(t1 % ny), kz = (int)(t1 / ny);
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        const long long nq = ((long long)wrap(kz + dz, nz) * ny + wrap(j + dy, ny)) * nx + wrap(i + dx, nx);
+        *reinterpret_cast<uint4*>(v) = __ldg(reinterpret_cast<const uint4*>(act + nq * CIN + cg * 8));
+      } else {
+        *reinterpret_cast<uint4*>(v) = make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int m = tap * CIN + cg * 8 + e;       // A row
+        const int t = m >> 7, mr = m & 127;
+        const int off = t * A_TILE + (((mr >> 3) * 2 + (k >> 3)) * 8 + (mr & 7)) * 16 + (k & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16*>(st + off) = v[e];
+      }
+    }
+    // B: items (channel group of 8, cell k)
+    for (int it = tid; it < (NOUT / 8) * 16; it += WG_THREADS) {
+      const int k = it & 15, ng = it >> 4;
+      const long long x = x0 + k;
+      __align__(16) __nv_bfloat16 v[8];
+      if (x < c1 && ng * 8 < g_stride)
+        *reinterpret_cast<uint4*>(v) = __ldg(reinterpret_cast<const uint4*>(g + x * g_stride + ng * 8));
+      else
+        *reinterpret_cast<uint4*>(v) = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int n = ng * 8 + e;
+        const int off = MT * A_TILE + (((n >> 3) * 2 + (k >> 3)) * 8 + (n & 7)) * 16 + (k & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16*>(st + off) = v[e];
+      }
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (s_abort) break;
+    if (tid == 0) {
+      tc::tc_fence_after();
+      const uint32_t base = s_addr + b * STAGE;
+      const uint64_t bdesc = tc::smem_desc(base + MT * A_TILE, 128, 256);
+#pragma unroll
+      for (int t = 0; t < MT; ++t) {
+        const uint64_t adesc = tc::smem_desc(base + t * A_TILE, 128, 256);
+        tc::mma_bf16(tmem + t * NOUT, adesc, bdesc, idesc, s > 0 ? 1u : 0u);
+      }
+      tc::mma_commit(&bars[b]);
+      if (s == ksteps - 1) tc::mma_commit(bar_done);
+    }
+  }
+  bool have = ksteps > 0 && !s_abort;
+  if (have) {
+    if (!tc::mbar_wait(bar_done, 0, CV_WAIT_ITERS)) { s_abort = 1; have = false; }
+  }
+  __syncthreads();
+  if (s_abort) have = false;
+  tc::tc_fence_after();
+  // epilogue: partial[cta][m][n]
+  float* out = partial + (long long)blockIdx.x * MT * 128 * NOUT;
+  for (int t = 0; t < MT; ++t) {
+    const int m = t * 128 + warp * 32 + (tid & 31);
+    if (have) {
+      const uint32_t taddr = tmem + t * NOUT + ((uint32_t)(warp * 32) << 16);
+      if (NOUT == 32) {
+        float acc[32];
+        tc::tmem_ld_32x32b_x32(taddr, acc);
+        tc::tmem_ld_wait();
+        for (int n = 0; n < 32; ++n) out[(long long)m * NOUT + n] = acc[n];
+      } else {
+        float acc[16];
+        tc::tmem_ld_32x32b_x16(taddr, acc);
+        tc::tmem_ld_wait();
+        for (int n = 0; n < 16; ++n) out[(long long)m * NOUT + n] = acc[n];
+      }
+    } else {
+      for (int n = 0; n < NOUT; ++n) out[(long long)m * NOUT + n] = 0.0f;
+    }
+  }
+  if (s_abort) {
+    if (tid == 0) {
+      atomicOr(err, 1u);
+      tc::mma_commit(bar_done);
+    }
+    tc::mbar_wait(bar_done, ksteps > 0 ? 1u : 0u, CV_WAIT_ITERS);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// dW[n][c][tap] (master layout) = sum over CTAs of partial[cta][tap * cin_pad + c][n]
+__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int nctas, int mt, int nout_pad,
+                                    int cin_pad, int cout, int cin, float* __restrict__ dW) {
+  const int total = cout * cin * 27;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int tap = idx % 27, c = (idx / 27) % cin, n = idx / (27 * cin);
+    const int m = tap * cin_pad + c;
+    double s = 0.0;
+    for (int b = 0; b < nctas; ++b) s += (double)partial[((long long)b * mt * 128 + m) * nout_pad + n];
+    dW[idx] = (float)s;
+  }
+}
+
+template <int CIN, int NOUT>
+static cudaError_t launch_wgrad(const __nv_bfloat16* act, const __nv_bfloat16* g, int g_stride,
+                                int nx, int ny, int nz, int nctas, float* partial, unsigned* err,
+                                cudaStream_t s) {
+  constexpr int MT = (27 * CIN + 127) / 128;
+  constexpr int STAGE = MT * 128 * 16 * 2 + NOUT * 16 * 2;
+  const size_t smem = (size_t)WG_STAGES * STAGE + 8 * (WG_STAGES + 1) + 16;
+  cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad_tc_kernel<CIN, NOUT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long ncell = (long long)nx * ny * nz;
+  long long per = (ncell + nctas - 1) / nctas;
+  per = (per + 15) / 16 * 16;
+  conv3d_wgrad_tc_kernel<CIN, NOUT><<<nctas, WG_THREADS, smem, s>>>(act, g, g_stride, nx, ny, nz,
+                                                                   per, partial, err);
+  return cudaGetLastError();
+}
+
+}  // namespace dh
+
+extern "C" dh_status dh_conv3d_wgrad_bf16(const void* act, int cin_pad, int cin, const void* grad,
+                                          int grad_stride, int cout, int nx, int ny, int nz,
+                                          float* partial, int nctas, float* dW, unsigned* err_flag,
+                                          void* stream) {
+  if (!act || !grad || !partial || !dW || !err_flag || nctas < 1) return DH_ERR_ARG;
+  if ((cin_pad != 8 && cin_pad != 32) || cin > cin_pad || cout > 32 || cout < 1 ||
+      (grad_stride != 8 && grad_stride != 32) || cout > grad_stride) {
+    dh_set_global_error("dh_conv3d_wgrad_bf16: cin_pad 8 or 32, cout <= grad_stride in {8, 32}");
+    return DH_ERR_ARG;
+  }
+  const int nout_pad = cout > 16 ? 32 : 16;
+  const int mt = (27 * cin_pad + 127) / 128;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  const __nv_bfloat16* a = (const __nv_bfloat16*)act;
+  const __nv_bfloat16* gg = (const __nv_bfloat16*)grad;
+  if (cin_pad == 8 && nout_pad == 32) e = launch_wgrad<8, 32>(a, gg, grad_stride, nx, ny, nz, nctas, partial, err_flag, s);
+  else if (cin_pad == 32 && nout_pad == 32) e = launch_wgrad<32, 32>(a, gg, grad_stride, nx, ny, nz, nctas, partial, err_flag, s);
+  else if (cin_pad == 32 && nout_pad == 16) e = launch_wgrad<32, 16>(a, gg, grad_stride, nx, ny, nz, nctas, partial, err_flag, s);
+  else if (cin_pad == 8 && nout_pad == 16) e = launch_wgrad<8, 16>(a, gg, grad_stride, nx, ny, nz, nctas, partial, err_flag, s);
+  else return DH_ERR_ARG;
+  if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
+  wgrad_reduce_kernel<<<64, 256, 0, s>>>(partial, nctas, mt, nout_pad, cin_pad, cout, cin, dW);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
+  return DH_OK;
+}

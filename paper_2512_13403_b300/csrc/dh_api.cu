@@ -157,6 +157,7 @@ extern "C" void dh_destroy(dh_ctx* c) {
   for (int a = 0; a < 3; ++a) cudaFree(c->tw[a]);
   mg_free(c);
   adjoint_free(c);
+  if (c->cnn) dh_cnn_destroy(c->cnn);
   for (auto& ev : c->prof_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   delete c;
 }
@@ -343,6 +344,13 @@ static dh_status finish_steps(dh_ctx* c, long long nstep_before) {
       return fail(c, DH_ERR_NONFINITE, "non-finite state in step " + std::to_string(failed));
     return fail(c, DH_ERR_POSITIVITY, "rho or P not positive after step " + std::to_string(failed));
   }
+  return DH_OK;
+}
+
+dh_status dh_refresh_cfl(dh_ctx* c) {
+  DH_CUDA(c, reset_cfl_bits(c));
+  DH_CUDA(c, c->prec == DH_F64 ? cfl_reduce_current<double>(c) : cfl_reduce_current<float>(c));
+  DH_CUDA(c, cudaStreamSynchronize(c->stream));
   return DH_OK;
 }
 

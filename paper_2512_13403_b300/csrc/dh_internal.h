@@ -39,6 +39,8 @@ struct dh_ctx {
   struct MG* mg = nullptr;
   // adjoint work space
   struct AdjointSpace* adj = nullptr;
+  // corrector network (dh_set_corrector)
+  struct dh_cnn* cnn = nullptr;
 };
 
 namespace dh {
@@ -64,3 +66,6 @@ cudaError_t dh_enqueue_step_f64(dh_ctx* c);
 dh_status dh_finish_steps(dh_ctx* c);
 // message returned by dh_last_error(NULL)
 void dh_set_global_error(const std::string& msg);
+// recompute the CFL minimum of the current state (after an external change of the state)
+dh_status dh_refresh_cfl(dh_ctx* c);
+extern "C" void dh_cnn_destroy(struct dh_cnn* c);

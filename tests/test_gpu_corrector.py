@@ -133,3 +133,115 @@ def test_data_gradient_of_output_layer():
     ref = oc.conv3d_data_grad(dy, oc.bf16(W)) * oc.gelu_grad(zp)
     got = _planar(out, 32, shape)
     assert float((got - ref).norm() / ref.norm()) < 4e-3
+
+
+def _wgrad(x, gr, cin_pad, g_stride, cout, shape):
+    lib = _lib.load()
+    nz, ny, nx = shape
+    nctas = 148
+    mt = (27 * cin_pad + 127) // 128
+    nout_pad = 32 if cout > 16 else 16
+    partial = torch.empty(nctas * mt * 128 * nout_pad, dtype=torch.float32, device="cuda")
+    dW = torch.empty(cout * x.shape[0] * 27, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    a_dev = _act(x, cin_pad)      # keep the device buffers alive until the kernel has run
+    g_dev = _act(gr, g_stride)
+    st = lib.dh_conv3d_wgrad_bf16(_ptr(a_dev), cin_pad, x.shape[0], _ptr(g_dev),
+                                  g_stride, cout, nx, ny, nz, _ptr(partial), nctas, _ptr(dW), _ptr(err), None)
+    assert st == 0, lib.dh_last_error(None)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    return dW.double().cpu().reshape(cout, x.shape[0], 3, 3, 3)
+
+
+@pytest.mark.parametrize("cin,cout,shape", [(5, 32, (8, 16, 16)), (32, 32, (8, 16, 16)),
+                                            (32, 5, (16, 8, 32)), (32, 32, (64, 64, 64))])
+def test_weight_gradient(cin, cout, shape):
+    g = torch.Generator().manual_seed(5)
+    x = oc.bf16(torch.randn((cin,) + shape, generator=g, dtype=torch.float64))
+    gr = oc.bf16(torch.randn((cout,) + shape, generator=g, dtype=torch.float64))
+    got = _wgrad(x, gr, 8 if cin <= 8 else 32, 8 if cout <= 8 else 32, cout, shape)
+    ref = oc.conv3d_weight_grad(x, gr, cout)
+    assert float((got - ref).norm() / ref.norm()) < 1e-5
+
+
+def _net_params(seed):
+    from paper_2512_13403_b300 import corrector as cr
+    p = cr.init_params(seed, out_scale=1.0)
+    g = torch.Generator().manual_seed(seed)
+    p = p + 0.01 * torch.randn(p.shape, generator=g)   # nonzero biases too
+    return p, cr.unflatten(p.double())
+
+
+def test_network_forward_and_backward_against_oracle():
+    from paper_2512_13403_b300 import corrector as cr
+    shape = (8, 16, 16)
+    params, pd = _net_params(3)
+    U = torch.from_numpy(__import__("paper_2512_13403_b300").inputs.decaying_turbulence(shape, seed=1, sigma=0.5, mach=1.0, p_sigma=0.3))
+    mu = [float(U[c].mean()) for c in range(5)]
+    sigma = [float(U[c].std()) for c in range(5)]
+    net = cr.Network(shape)
+    net.set_params(params, mu, sigma)
+    Ug = U.float().cuda().contiguous()
+    y = net.forward(Ug)
+    yr, cache = oc.forward(U.float().double(), pd, mu, sigma)
+    assert float((y.double().cpu() - yr).norm() / yr.norm()) < 1e-2
+    # backward of the mean-squared error against a target, vs reverse-mode AD of the oracle with
+    # the BF16 roundings passed straight through
+    tgt = yr + 0.1 * torch.randn(yr.shape, generator=torch.Generator().manual_seed(9), dtype=torch.float64)
+    grads = torch.zeros(cr.NPARAM, dtype=torch.float32, device="cuda")
+    loss = net.backward(tgt.float().cuda().contiguous(), grads)
+    q = {k: v.clone().requires_grad_(True) for k, v in pd.items()}
+    st = lambda t: t + (oc.bf16(t) - t).detach()
+    mu_t = torch.tensor(mu, dtype=torch.float64).reshape(5, 1, 1, 1)
+    sg_t = torch.tensor(sigma, dtype=torch.float64).reshape(5, 1, 1, 1)
+    x0 = oc.bf16((U.float().double() - mu_t) / sg_t)
+    h1 = st(oc.gelu(oc.conv3d_periodic(x0, st(q["W1"]), q["b1"])))
+    h2 = st(oc.gelu(oc.conv3d_periodic(h1, st(q["W2"]), q["b2"])))
+    yy = oc.conv3d_periodic(h2, st(q["W3"]), q["b3"])
+    L = ((yy - tgt) ** 2).mean()
+    L.backward()
+    assert loss == pytest.approx(float(L.detach()), rel=2e-2)
+    gg = cr.unflatten(grads.double().cpu())
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        ref = q[k].grad
+        assert float((gg[k] - ref).norm() / ref.norm()) < 3e-2, k
+
+
+def test_zero_network_is_identity_and_floors():
+    from paper_2512_13403_b300 import corrector as cr
+    shape = (8, 16, 16)
+    net = cr.Network(shape)
+    net.set_params(torch.zeros(cr.NPARAM), [0.0] * 5, [1.0] * 5)
+    U = torch.from_numpy(__import__("paper_2512_13403_b300").inputs.decaying_turbulence(shape, seed=2, sigma=0.5, mach=1.0)).float().cuda().contiguous()
+    V = U.clone()
+    net.correct_state(V, 1e-6, 0.05, 5 / 3)
+    assert torch.equal(V, U)
+    # a state below the floors is lifted onto them
+    W = U.clone()
+    W[0, 0, 0, 0] = -1.0
+    W[4, 1, 1, 1] = 0.0
+    net.correct_state(W, 1e-3, 0.05, 5 / 3)
+    assert float(W[0, 0, 0, 0]) == pytest.approx(1e-3)
+    kin = 0.5 * float(W[1, 1, 1, 1] ** 2 + W[2, 1, 1, 1] ** 2 + W[3, 1, 1, 1] ** 2) / float(W[0, 1, 1, 1])
+    assert float(W[4, 1, 1, 1]) >= kin + float(W[0, 1, 1, 1]) * 0.05 * 1.5 * (1 - 1e-6)
+
+
+def test_adam_matches_definition():
+    from paper_2512_13403_b300 import corrector as cr
+    g = torch.Generator().manual_seed(7)
+    p0 = torch.randn(1000, generator=g)
+    p = p0.clone().cuda()
+    opt = cr.Adam(p, lr=1e-2)
+    m = torch.zeros(1000, dtype=torch.float64)
+    v = torch.zeros(1000, dtype=torch.float64)
+    pr = p0.double().clone()
+    for t in range(1, 4):
+        grad = torch.randn(1000, generator=g)
+        opt.step(grad.cuda())
+        gd = grad.double()
+        m = 0.9 * m + 0.1 * gd
+        v = 0.999 * v + 0.001 * gd * gd
+        pr = pr - 1e-2 * (m / (1 - 0.9 ** t)) / (torch.sqrt(v / (1 - 0.999 ** t)) + 1e-8)
+    torch.cuda.synchronize()
+    assert torch.allclose(p.double().cpu(), pr, rtol=1e-5, atol=1e-6)
