@@ -6,7 +6,8 @@ Network (channel counts 5 -> 32 -> 32 -> 5, 3x3x3 kernels, periodic padding as i
   z1 = conv(x0, bf16(W1)) + b1,  h1 = bf16(gelu(z1))
   z2 = conv(h1, bf16(W2)) + b2,  h2 = bf16(gelu(z2))
   y  = conv(h2, bf16(W3)) + b3
-  U' = U + sigma * y, then rho >= rho_floor and E raised where needed so that
+  U' = U + s * y (s a per-channel output scale, by default sigma), then rho >= rho_floor and
+       E raised where needed so that
        E - |m|^2 / (2 rho) >= rho T_floor / (gamma - 1).
 BF16 rounding is round-to-nearest-even of the float64 value; products and sums are float64
 (the tensor cores accumulate in float32, so the two agree to float32 rounding before each
@@ -70,10 +71,12 @@ def forward(U: torch.Tensor, p: dict, mu, sigma):
     return y, dict(x0=x0, z1=z1, h1=h1, z2=z2, h2=h2)
 
 
-def correct(U: torch.Tensor, p: dict, mu, sigma, rho_floor: float, T_floor: float, gamma: float):
-    sig = torch.as_tensor(sigma, dtype=torch.float64).reshape(5, 1, 1, 1)
+def correct(U: torch.Tensor, p: dict, mu, sigma, rho_floor: float, T_floor: float, gamma: float,
+            out_scale=None):
+    """U + s * y with s = out_scale (per channel; sigma when not given), then the floors."""
+    s = torch.as_tensor(sigma if out_scale is None else out_scale, dtype=torch.float64).reshape(5, 1, 1, 1)
     y, _ = forward(U, p, mu, sigma)
-    V = U + sig * y
+    V = U + s * y
     rho = torch.clamp(V[0], min=rho_floor)
     kin = 0.5 * (V[1] ** 2 + V[2] ** 2 + V[3] ** 2) / rho
     Emin = kin + rho * T_floor / (gamma - 1.0)
