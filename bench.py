@@ -30,6 +30,13 @@ METRIC = "cell-updates/s at 256^3 (fwd, adjoint); corrector error vs fine at equ
 UNIT = "cell-updates/s"
 FWD_BYTES_STAGE1 = 40   # float32: read U^n (20 B), write U1 (20 B) per cell
 FWD_BYTES_STAGE2 = 60   # float32: read U^n and U1 (40 B), write U^{n+1} (20 B) per cell
+ADJ_BYTES_STAGE = 70    # float32 per adjoint stage launch, average of stage-2^T (read U1, lambda;
+                        # write lambda_U1: 60 B) and stage-1^T (read U^n, lambda_U1, lambda;
+                        # write lambda^n: 80 B)
+# DRAM bytes of one stage-2 launch at 256^3 and its warp instructions, from the ncu capture
+# summarised in profiles/stage_kernels_driven_cooling_turbulence_256cubed.md (same kernel source)
+STAGE2_DRAM_BYTES_256 = 695152128 + 312060416
+STAGE2_WARP_INSTR_256 = 794812160
 
 
 def _peaks():
@@ -270,12 +277,93 @@ def run_ours(args):
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
     }
+    # instruction-issue roofline of the same kernel: warp instructions per launch (ncu) over the
+    # live launch time, against 4 issue slots per SM per cycle at the sampled SM clock
+    clk = line["clocks"].get("sm_mhz") or 2032.0
+    if n == 256:
+        line["roofline"]["traffic"] = STAGE2_DRAM_BYTES_256
+        issue_peak = 148 * 4 * clk * 1e6
+        issue = STAGE2_WARP_INSTR_256 / (stage2_ms * 1e-3)
+        line["roofline_alu"] = {"bound": "alu", "kernel": "stage2", "achieved": issue,
+                                "peak": issue_peak, "unit": "warp-instr/s",
+                                "frac": issue / issue_peak,
+                                "note": "warp instructions per launch from ncu; peak = 148 SMs x 4 "
+                                        "issue slots x median SM clock sampled during the run"}
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_leg(args, stream)
+    if not args.no_corrector:
+        line["corrector"] = corrector_leg(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(budget_s=args.cpu_budget)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def adjoint_leg(args, stream):
+    """Hand adjoint through n steps of 256^3 decaying turbulence (hydro only), checkpoints every k:
+    cell-updates/s = N^3 n / wall time of dh_adjoint_advance (forward, recompute and backward)."""
+    import torch
+    from paper_2512_13403_b300 import inputs
+    from paper_2512_13403_b300.solver import Config, Solver
+    n = args.grid
+    shape = (n, n, n)
+    steps, k = args.adj_steps, args.adj_ckpt
+    with torch.cuda.stream(stream):
+        s = Solver(Config(shape=shape, precision="f32"), stream=stream)
+        U0 = torch.from_numpy(inputs.decaying_turbulence(shape, seed=2, sigma=0.5, mach=2.0)).float().cuda()
+        lam = torch.zeros_like(U0)
+        lam[0] = 2.0 / n ** 3  # gradient of a mean-squared density misfit (scale only)
+        s.init_state(U0)
+        s.adjoint_advance(2, 1, lam)  # warm-up: allocations and first launches
+        s.init_state(U0)
+        s.profile(True)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.adjoint_advance(steps, k, lam)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        na, ta = s.profile_read("adjoint")
+        s.profile(False)
+        s.close()
+    peak, kind = _peaks()
+    adj_ms = ta / max(na, 1)
+    ach = ADJ_BYTES_STAGE * n ** 3 / (adj_ms * 1e-3) / 1e9
+    return {"value": n ** 3 * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "ckpt_every": k,
+            "ms_per_step": ms / steps,
+            "workload": f"decaying turbulence {n}^3 (lognormal rho sigma=0.5, k^-4 velocity, rms Mach 2), "
+                        "hydro only, float32",
+            "roofline": {"bound": "hbm", "kernel": "stage_adjoint_kernel<float>", "achieved": ach,
+                         "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": kind,
+                         "traffic": None, "avg_launch_ms": adj_ms, "launches": na}}
+
+
+def corrector_leg(args):
+    """Config-4 style closure: solver-made pairs at 256^3 -> 64^3, BF16 tensor-core training,
+    relative L2 error against the downsampled fine run over 100 coarse steps."""
+    import torch
+    from paper_2512_13403_b300 import closure
+    setup = closure.ClosureSetup(fine=args.grid, factor=4, runs=args.corr_runs,
+                                 snapshots=args.corr_snapshots, spinup_steps=200)
+    t0 = time.time()
+    X, Y = closure.make_pairs(setup)
+    t1 = time.time()
+    params, norm, losses = closure.train(X, Y, epochs=args.corr_epochs)
+    t2 = time.time()
+    err, ms = closure.evaluate(setup, params, norm, steps=100, equal_time_substeps=2)
+    t3 = time.time()
+    mean = {k: sum(v) / len(v) for k, v in err.items()}
+    return {"metric": "relative L2 vs 4x-downsampled fine run, mean over 100 coarse steps",
+            "uncorrected": mean["uncorrected"], "corrected": mean["corrected"],
+            "uncorrected_equal_gpu_time": mean.get("uncorrected_equal_gpu_time"),
+            "final_step": {k: v[-1] for k, v in err.items()},
+            "gpu_ms_per_coarse_step": ms, "pairs": int(X.shape[0]), "epochs": args.corr_epochs,
+            "train_loss": losses, "seconds": {"pairs": t1 - t0, "train": t2 - t1, "eval": t3 - t2},
+            "reading": "equal GPU time as matched physical time (primary) and, second, the "
+                       "uncorrected run with 2 substeps per coarse step"}
 
 
 def main():
@@ -288,6 +376,13 @@ def main():
     ap.add_argument("--ref-grid", type=int, default=64)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adj-steps", type=int, default=20)
+    ap.add_argument("--adj-ckpt", type=int, default=10)
+    ap.add_argument("--no-corrector", action="store_true")
+    ap.add_argument("--corr-runs", type=int, default=20)
+    ap.add_argument("--corr-snapshots", type=int, default=100)
+    ap.add_argument("--corr-epochs", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

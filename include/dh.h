@@ -124,6 +124,18 @@ dh_status dh_forcing_field(dh_ctx* ctx, void* a_out, int on_device);
    order. */
 dh_status dh_forcing_modes(dh_ctx* ctx, double out[96]);
 
+/* Sets the forcing mode table (same layout as dh_forcing_modes).  hold = 1 keeps it: later
+   steps skip the OU update of Sec. 3.1.1 and force with this table (renormalised to a_rms) until
+   the next call with hold = 0.  Used to drive several runs (a coarse and a fine grid) with one
+   acceleration history.  DH_ERR_STATE if forcing is off. */
+dh_status dh_set_forcing_modes(dh_ctx* ctx, const double modes[96], int hold);
+
+/* Block mean of a float32 state (device, state layout, nx*ny*nz) over factor^3 cells into
+   U_coarse (device, (nx/factor)*(ny/factor)*(nz/factor)): the conservative restriction of the
+   conserved fields onto a coarser grid.  Dimensions must be divisible by factor. */
+dh_status dh_downsample(const float* U_fine, int nx, int ny, int nz, int factor, float* U_coarse,
+                        void* cuda_stream);
+
 /* Gravitational potential phi of the last solve (one plane, float64, state index order),
    and the cycles / final relative residual of that solve (nullable outputs). */
 dh_status dh_get_potential(dh_ctx* ctx, double* phi_out, int on_device, int* cycles,
@@ -185,22 +197,25 @@ dh_status dh_conv3d_wgrad_bf16(const void* act, int cin_pad, int cin, const void
    z1 = conv(x0, W1) + b1, h1 = bf16(gelu(z1)), z2 = conv(h1, W2) + b2, h2 = bf16(gelu(z2)),
    y = conv(h2, W3) + b3, all 3x3x3 periodic, channels 5 -> 32 -> 32 -> 5.  Parameters are one
    flat fp32 device array of dh_cnn_param_count() = 36357 values: W1[32][5][27], b1[32],
-   W2[32][32][27], b2[32], W3[5][32][27], b3[5]; norm10 = mu[5], sigma[5] (host, sigma > 0).
+   W2[32][32][27], b2[32], W3[5][32][27], b3[5]; norm15 = mu[5], sigma[5], s[5] (host, sigma > 0):
+   input normalisation (U - mu)/sigma and per-channel output scale s of the correction.
    A dh_cnn owns the activations of one grid (nx*ny*nz divisible by 128). */
 typedef struct dh_cnn dh_cnn;
 long long dh_cnn_param_count(void);
 dh_status dh_cnn_create(int nx, int ny, int nz, void* cuda_stream, dh_cnn** out);
 void dh_cnn_destroy(dh_cnn* cnn);
 /* Copies the parameters and packs the tensor-core operands (synchronises). */
-dh_status dh_cnn_set_params(dh_cnn* cnn, const float* params, const float* norm10);
+dh_status dh_cnn_set_params(dh_cnn* cnn, const float* params, const float* norm15);
 /* y = network(U) for a float32 state U (device, state layout); y_out (nullable, device) gets
    y as 5 planes.  Keeps the activations for dh_cnn_backward. */
 dh_status dh_cnn_forward(dh_cnn* cnn, const float* U, float* y_out);
-/* Loss = mean over 5 channels and cells of (y - target)^2 for the last forward (target: 5 planes
-   float32, device); writes d loss / d params into grads (device, 36357 floats) and the loss into
-   *loss (host, nullable).  Synchronises. */
-dh_status dh_cnn_backward(dh_cnn* cnn, const float* target, float* grads, double* loss);
-/* U <- U + sigma * network(U) in place (float32 state, device), then rho >= rho_floor and
+/* For the last forward (on U_in): residual target t = (U_target - U_in) / s per channel,
+   loss = mean over 5 channels and cells of (y - t)^2; writes d loss / d params into grads
+   (device, 36357 floats) and the loss into *loss (host, nullable).  U_in, U_target: float32
+   states (device).  Synchronises. */
+dh_status dh_cnn_backward(dh_cnn* cnn, const float* U_in, const float* U_target, float* grads,
+                          double* loss);
+/* U <- U + s * network(U) in place (float32 state, device), then rho >= rho_floor and
    E >= |m|^2/(2 rho) + rho T_floor/(gamma - 1).  Synchronises. */
 dh_status dh_cnn_correct_state(dh_cnn* cnn, float* U, double rho_floor, double T_floor,
                                double gamma);
@@ -209,9 +224,9 @@ dh_status dh_cnn_correct_state(dh_cnn* cnn, float* U, double rho_floor, double T
 dh_status dh_adam_step(float* params, const float* grads, float* m, float* v, long long n,
                        double lr, double beta1, double beta2, double eps, int step, void* stream);
 /* Corrector of a float32 context: dh_set_corrector copies the parameters (as dh_cnn_set_params);
-   dh_correct applies U <- U + sigma * network(U) to the current state with the floors above
+   dh_correct applies U <- U + s * network(U) to the current state with the floors above
    (rho_floor = 1e-6 <rho>, the context's T_floor and gamma).  DH_ERR_STATE without a corrector. */
-dh_status dh_set_corrector(dh_ctx* ctx, const float* params, const float* norm10);
+dh_status dh_set_corrector(dh_ctx* ctx, const float* params, const float* norm15);
 dh_status dh_correct(dh_ctx* ctx);
 
 /* Conserved totals (as dh_conserved_totals) for callers that cannot allocate device memory,

@@ -46,6 +46,8 @@ _SIGNATURES = {
     "dh_conserved_totals": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "dh_forcing_field": (C.c_int, [_P, _P, C.c_int]),
     "dh_forcing_modes": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "dh_set_forcing_modes": (C.c_int, [_P, C.POINTER(C.c_double), C.c_int]),
+    "dh_downsample": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "dh_get_potential": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "dh_solve_poisson": (C.c_int, [_P, _P, C.c_int]),
     "dh_adjoint_advance": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
@@ -60,7 +62,7 @@ _SIGNATURES = {
     "dh_cnn_destroy": (None, [_P]),
     "dh_cnn_set_params": (C.c_int, [_P, _P, C.POINTER(C.c_float)]),
     "dh_cnn_forward": (C.c_int, [_P, _P, _P]),
-    "dh_cnn_backward": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double)]),
+    "dh_cnn_backward": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_double)]),
     "dh_cnn_correct_state": (C.c_int, [_P, _P, C.c_double, C.c_double, C.c_double]),
     "dh_adam_step": (C.c_int, [_P, _P, _P, _P, C.c_longlong, C.c_double, C.c_double, C.c_double,
                                C.c_double, C.c_int, _P]),

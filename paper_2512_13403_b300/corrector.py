@@ -72,9 +72,12 @@ class Network:
         except Exception:
             pass
 
-    def set_params(self, params: torch.Tensor, mu, sigma):
+    def set_params(self, params: torch.Tensor, mu, sigma, out_scale=None):
+        """mu, sigma: input normalisation; out_scale: per-channel scale of the correction
+        (defaults to sigma)."""
         p = params.detach().float().cuda().contiguous()
-        norm = (C.c_float * 10)(*[float(x) for x in list(mu) + list(sigma)])
+        out_scale = list(sigma) if out_scale is None else list(out_scale)
+        norm = (C.c_float * 15)(*[float(x) for x in list(mu) + list(sigma) + out_scale])
         check(self.lib.dh_cnn_set_params(self.h, C.c_void_p(p.data_ptr()), norm))
 
     def forward(self, U: torch.Tensor) -> torch.Tensor:
@@ -83,9 +86,11 @@ class Network:
         check(self.lib.dh_cnn_forward(self.h, C.c_void_p(U.data_ptr()), C.c_void_p(y.data_ptr())))
         return y
 
-    def backward(self, target: torch.Tensor, grads: torch.Tensor) -> float:
+    def backward(self, U_in: torch.Tensor, U_target: torch.Tensor, grads: torch.Tensor) -> float:
+        """Gradient of mean((y - (U_target - U_in)/s)^2) for the last forward (on U_in)."""
         loss = C.c_double()
-        check(self.lib.dh_cnn_backward(self.h, C.c_void_p(target.data_ptr()),
+        check(self.lib.dh_cnn_backward(self.h, C.c_void_p(U_in.data_ptr()),
+                                       C.c_void_p(U_target.data_ptr()),
                                        C.c_void_p(grads.data_ptr()), C.byref(loss)))
         return loss.value
 

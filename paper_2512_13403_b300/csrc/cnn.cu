@@ -4,7 +4,7 @@
 //
 // Network: x0 = bf16((U - mu)/sigma) (5 channels, padded to 8); z1 = conv(x0, W1) + b1,
 // h1 = bf16(gelu(z1)); z2 = conv(h1, W2) + b2, h2 = bf16(gelu(z2)); y = conv(h2, W3) + b3.
-// Correction: U <- U + sigma * y, rho >= rho_floor, E raised so that the thermal energy is at
+// Correction: U <- U + s * y (s the per-channel output scale), rho >= rho_floor, E raised so that the thermal energy is at
 // least rho T_floor / (gamma - 1).  Parameters, flat fp32: W1[32][5][27], b1[32],
 // W2[32][32][27], b2[32], W3[5][32][27], b3[5] (36357 values).
 #include <cuda_bf16.h>
@@ -34,7 +34,7 @@ struct dh_cnn {
   long long ncell = 0;
   cudaStream_t stream = nullptr;
   float* params = nullptr;                  // device copy of the parameters
-  float norm[10] = {0};                     // mu[5], sigma[5]
+  float norm[15] = {0};                     // mu[5], sigma[5], output scale[5]
   float* norm_dev = nullptr;
   __nv_bfloat16 *pk_w1 = nullptr, *pk_w2 = nullptr, *pk_w3 = nullptr;   // forward operands
   __nv_bfloat16 *pk_w2t = nullptr, *pk_w3t = nullptr;                  // data-gradient operands
@@ -64,9 +64,12 @@ __global__ void normalize_kernel(const float* __restrict__ U, long long n, const
   }
 }
 
-// loss = mean over 5 channels and cells of (y - t)^2; dy = d loss / d y as bf16 [cell][8]
-__global__ void mse_grad_kernel(const float* __restrict__ y, const float* __restrict__ t, long long n,
-                                __nv_bfloat16* __restrict__ dy, double* __restrict__ partial) {
+// Residual target t = (U_target - U_in) / s per channel; loss = mean over 5 channels and cells of
+// (y - t)^2; dy = d loss / d y as bf16 [cell][8].
+__global__ void mse_grad_kernel(const float* __restrict__ y, const float* __restrict__ Uin,
+                                const float* __restrict__ Utgt, const float* __restrict__ norm,
+                                long long n, __nv_bfloat16* __restrict__ dy,
+                                double* __restrict__ partial) {
   __shared__ double red[256];
   double s = 0.0;
   const double scale = 2.0 / (5.0 * (double)n);
@@ -76,7 +79,8 @@ __global__ void mse_grad_kernel(const float* __restrict__ y, const float* __rest
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      const double d = (double)y[c * n + q] - (double)t[c * n + q];
+      const double t = ((double)Utgt[c * n + q] - (double)Uin[c * n + q]) / (double)norm[10 + c];
+      const double d = (double)y[c * n + q] - t;
       s += d * d;
       v[c] = __float2bfloat16_rn((float)(scale * d));
     }
@@ -123,7 +127,7 @@ __global__ void correct_kernel(float* __restrict__ U, const float* __restrict__ 
        q += (long long)gridDim.x * blockDim.x) {
     float v[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) v[c] = U[c * n + q] + norm[5 + c] * y[c * n + q];
+    for (int c = 0; c < 5; ++c) v[c] = U[c * n + q] + norm[10 + c] * y[c * n + q];
     const float rho = fmaxf(v[0], rho_floor);
     const float kin = 0.5f * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / rho;
     const float Emin = kin + rho * T_floor / gm1;
@@ -199,7 +203,7 @@ extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn*
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t b) { if (e == cudaSuccess) e = cudaMalloc(p, b); };
   A((void**)&c->params, NPARAM * sizeof(float));
-  A((void**)&c->norm_dev, 10 * sizeof(float));
+  A((void**)&c->norm_dev, 15 * sizeof(float));
   A((void**)&c->pk_w1, 32 * 224 * 2);
   A((void**)&c->pk_w2, 32 * 864 * 2);
   A((void**)&c->pk_w3, 16 * 864 * 2);
@@ -227,14 +231,14 @@ extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn*
   return DH_OK;
 }
 
-extern "C" dh_status dh_cnn_set_params(dh_cnn* c, const float* params_dev, const float* norm10) {
-  if (!c || !params_dev || !norm10) return DH_ERR_ARG;
+extern "C" dh_status dh_cnn_set_params(dh_cnn* c, const float* params_dev, const float* norm15) {
+  if (!c || !params_dev || !norm15) return DH_ERR_ARG;
   for (int k = 0; k < 5; ++k)
-    if (!(norm10[5 + k] > 0.0f)) { dh_set_global_error("dh_cnn_set_params: sigma must be > 0"); return DH_ERR_ARG; }
-  for (int k = 0; k < 10; ++k) c->norm[k] = norm10[k];
+    if (!(norm15[5 + k] > 0.0f)) { dh_set_global_error("dh_cnn_set_params: sigma must be > 0"); return DH_ERR_ARG; }
+  for (int k = 0; k < 15; ++k) c->norm[k] = norm15[k];
   cudaStream_t s = c->stream;
   CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(c->params, params_dev, NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, s), "params"));
-  CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(c->norm_dev, c->norm, 10 * sizeof(float), cudaMemcpyHostToDevice, s), "norm"));
+  CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(c->norm_dev, c->norm, 15 * sizeof(float), cudaMemcpyHostToDevice, s), "norm"));
   CNN_TRY(dh_pack_conv_weights(c->params + OFF_W1, 32, 5, 0, c->pk_w1, s));
   CNN_TRY(dh_pack_conv_weights(c->params + OFF_W2, 32, 32, 0, c->pk_w2, s));
   CNN_TRY(dh_pack_conv_weights(c->params + OFF_W3, 5, 32, 0, c->pk_w3, s));
@@ -272,12 +276,13 @@ extern "C" dh_status dh_cnn_forward(dh_cnn* c, const float* U, float* y_out) {
   return DH_OK;
 }
 
-extern "C" dh_status dh_cnn_backward(dh_cnn* c, const float* target, float* grads, double* loss) {
-  if (!c || !target || !grads) return DH_ERR_ARG;
+extern "C" dh_status dh_cnn_backward(dh_cnn* c, const float* U_in, const float* U_target,
+                                     float* grads, double* loss) {
+  if (!c || !U_in || !U_target || !grads) return DH_ERR_ARG;
   if (!c->have_forward) { dh_set_global_error("dh_cnn_backward: run dh_cnn_forward first"); return DH_ERR_STATE; }
   const long long n = c->ncell;
   cudaStream_t s = c->stream;
-  mse_grad_kernel<<<RBLOCKS, 256, 0, s>>>(c->y, target, n, c->dy, c->red);
+  mse_grad_kernel<<<RBLOCKS, 256, 0, s>>>(c->y, U_in, U_target, c->norm_dev, n, c->dy, c->red);
   sum_blocks_kernel<<<1, 32, 0, s>>>(c->red, RBLOCKS, 1.0 / (5.0 * (double)n), c->red + RBLOCKS);
   // output layer
   CNN_TRY(dh_conv3d_wgrad_bf16(c->h2, 32, 32, c->dy, 8, 5, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W3, c->err, s));
@@ -322,14 +327,14 @@ extern "C" dh_status dh_adam_step(float* params, const float* grads, float* m, f
 extern "C" long long dh_cnn_param_count(void) { return NPARAM; }
 
 // ---- the context's corrector -------------------------------------------------------------------
-extern "C" dh_status dh_set_corrector(dh_ctx* ctx, const float* params_dev, const float* norm10) {
-  if (!ctx || !params_dev || !norm10) return DH_ERR_ARG;
+extern "C" dh_status dh_set_corrector(dh_ctx* ctx, const float* params_dev, const float* norm15) {
+  if (!ctx || !params_dev || !norm15) return DH_ERR_ARG;
   if (ctx->prec != DH_F32) { ctx->err = "the corrector runs on float32 states"; return DH_ERR_ARG; }
   if (!ctx->cnn) {
     dh_status st = dh_cnn_create(ctx->cfg.nx, ctx->cfg.ny, ctx->cfg.nz, ctx->stream, &ctx->cnn);
     if (st != DH_OK) { ctx->err = dh_last_error(nullptr); return st; }
   }
-  dh_status st = dh_cnn_set_params(ctx->cnn, params_dev, norm10);
+  dh_status st = dh_cnn_set_params(ctx->cnn, params_dev, norm15);
   if (st != DH_OK) ctx->err = dh_last_error(nullptr);
   return st;
 }

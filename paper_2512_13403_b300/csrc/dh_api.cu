@@ -277,6 +277,7 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed) {
   b.precision = c->prec == DH_F64 ? 1 : 0;
   b.forcing = g.forcing; b.ahat = c->ahat; b.ahat_prev = c->ahat_prev; b.ahat_norm = c->ahat_norm;
   b.seed = g.ou_seed; b.tau = g.ou_tau; b.arms = g.ou_arms;
+  b.hold = c->ou_hold;
   prof_begin(c, DH_KERNEL_PROLOGUE);
   cudaError_t e = launch_step_begin(b, c->stream);
   prof_end(c, 1);
@@ -464,6 +465,15 @@ extern "C" dh_status dh_forcing_modes(dh_ctx* c, double out[96]) {
   if (!c->cfg.forcing) return fail(c, DH_ERR_STATE, "forcing is off");
   DH_CUDA(c, cudaMemcpyAsync(out, c->ahat, 96 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   DH_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DH_OK;
+}
+
+extern "C" dh_status dh_set_forcing_modes(dh_ctx* c, const double in[96], int hold) {
+  if (!c || !in) return fail(c, DH_ERR_ARG, "null argument");
+  if (!c->cfg.forcing) return fail(c, DH_ERR_STATE, "forcing is off");
+  DH_CUDA(c, cudaMemcpyAsync(c->ahat, in, 96 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  DH_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->ou_hold = hold != 0;
   return DH_OK;
 }
 

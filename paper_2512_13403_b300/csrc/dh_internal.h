@@ -24,6 +24,7 @@ struct dh_ctx {
   double* ahat_prev = nullptr;       // table before the last update (rollback)
   void* ahat_norm = nullptr;         // normalised table in the working precision
   void* tw[3] = {nullptr, nullptr, nullptr};  // per-axis forcing twiddles
+  int ou_hold = 0;                   // 1: steps keep the forcing table as set (no OU update)
   double* partials = nullptr;        // totals: per-block partial sums
   double* totals = nullptr;          // totals: 5 doubles
   bool initialized = false;

@@ -38,6 +38,7 @@ struct BeginArgs {
   void* ahat_norm;          // 96 reals of the working precision
   unsigned long long seed;
   double tau, arms;
+  int hold;                 // keep the table (no draw, no update), only renormalise it
 };
 cudaError_t launch_step_begin(const BeginArgs& a, cudaStream_t s);
 cudaError_t launch_forcing_init(double* ahat, unsigned long long seed, cudaStream_t s);

@@ -13,6 +13,7 @@
 #include <math.h>
 #include "dh_kernels.h"
 #include "dh_sources.cuh"
+#include "../../include/dh.h"
 
 namespace dh {
 
@@ -436,17 +437,17 @@ __global__ void step_begin_kernel(BeginArgs a) {
   __syncthreads();
   const double dt = s_dt;
   if (a.forcing) {
-    double ere, eim;
-    projected_draw(a.seed, rec->nstep + 1, lane, sre, sim, ere, eim);
-    const double f = exp(-dt / a.tau);
-    const double g = sqrt(1.0 - f * f);
+    double ere = 0.0, eim = 0.0;
+    if (!a.hold) projected_draw(a.seed, rec->nstep + 1, lane, sre, sim, ere, eim);
+    const double f = a.hold ? 1.0 : exp(-dt / a.tau);
+    const double g = a.hold ? 0.0 : sqrt(1.0 - f * f);
     double nre = 0.0, nim = 0.0;
     if (lane < 48) {
       const double ore = a.ahat[2 * lane], oim = a.ahat[2 * lane + 1];
       a.ahat_prev[2 * lane] = ore;
       a.ahat_prev[2 * lane + 1] = oim;
-      nre = f * ore + g * ere;
-      nim = f * oim + g * eim;
+      nre = a.hold ? ore : f * ore + g * ere;
+      nim = a.hold ? oim : f * oim + g * eim;
       a.ahat[2 * lane] = nre;
       a.ahat[2 * lane + 1] = nim;
     }
@@ -609,4 +610,37 @@ template cudaError_t launch_forcing_field<float>(const float*, const float* cons
 template cudaError_t launch_forcing_field<double>(const double*, const double* const[3], int,
                                                   int, int, double*, cudaStream_t);
 
+// ---------------------------------------------------------------------------------------------
+// Block mean of a float32 state over factor^3 fine cells (conservative restriction of the
+// conserved fields onto a coarser grid).
+__global__ void downsample_kernel(const float* __restrict__ Uf, int nx, int ny, int nz, int r,
+                                  float* __restrict__ Uc) {
+  const int cx = nx / r, cy = ny / r, cz = nz / r;
+  const long long nc = (long long)cx * cy * cz, nf = (long long)nx * ny * nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nc * 5;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(q / nc);
+    const long long c = q - (long long)f * nc;
+    const int I = (int)(c % cx);
+    const long long t = c / cx;
+    const int J = (int)(t % cy), K = (int)(t / cy);
+    double s = 0.0;
+    for (int dk = 0; dk < r; ++dk)
+      for (int dj = 0; dj < r; ++dj)
+        for (int di = 0; di < r; ++di)
+          s += (double)Uf[(long long)f * nf + ((long long)(K * r + dk) * ny + (J * r + dj)) * nx + (I * r + di)];
+    Uc[q] = (float)(s / (double)(r * r * r));
+  }
+}
+
 }  // namespace dh
+
+extern "C" dh_status dh_downsample(const float* Uf, int nx, int ny, int nz, int factor, float* Uc,
+                                   void* stream) {
+  if (!Uf || !Uc || factor < 1 || nx % factor || ny % factor || nz % factor) return DH_ERR_ARG;
+  const long long nc = (long long)(nx / factor) * (ny / factor) * (nz / factor) * 5;
+  long long b = (nc + 255) / 256;
+  if (b > 148 * 8) b = 148 * 8;
+  dh::downsample_kernel<<<(int)b, 256, 0, (cudaStream_t)stream>>>(Uf, nx, ny, nz, factor, Uc);
+  return cudaGetLastError() == cudaSuccess ? DH_OK : DH_ERR_CUDA;
+}

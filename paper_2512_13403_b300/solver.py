@@ -153,6 +153,13 @@ class Solver:
         a = np.frombuffer(out, dtype=np.float64).reshape(16, 3, 2)
         return a[..., 0] + 1j * a[..., 1]
 
+    def set_forcing_modes(self, modes: np.ndarray, hold: bool):
+        a = np.zeros((16, 3, 2), dtype=np.float64)
+        a[..., 0] = np.real(modes)
+        a[..., 1] = np.imag(modes)
+        buf = (C.c_double * 96)(*a.reshape(-1).tolist())
+        self._check(self.lib.dh_set_forcing_modes(self.ctx, buf, int(hold)))
+
     def potential(self):
         out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
         cyc = C.c_int()

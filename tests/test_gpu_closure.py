@@ -1,0 +1,78 @@
+"""The closure workflow's library pieces on the GPU: 4^3 block mean, held forcing tables, the
+context corrector, and a small end-to-end pair/train/evaluate cycle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import corrector as oc
+from paper_2512_13403_b300 import closure, inputs
+from paper_2512_13403_b300.corrector import NPARAM, init_params, unflatten
+from tests.gpu_util import solver, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_downsample_is_block_mean():
+    U = torch.rand(5, 16, 24, 32, dtype=torch.float32, device="cuda")
+    D = closure.downsample(U, 4)
+    ref = U.double().reshape(5, 4, 4, 6, 4, 8, 4).mean(dim=(2, 4, 6))
+    assert torch.allclose(D.double(), ref, rtol=1e-6, atol=1e-7)
+
+
+def test_held_forcing_table_is_kept():
+    shape = (16, 16, 16)
+    s = solver(shape, "f32", forcing=True)
+    s.init_state(to_gpu(inputs.cooling_box(shape), "f32"))
+    rng = np.random.default_rng(0)
+    modes = rng.standard_normal((16, 3)) + 1j * rng.standard_normal((16, 3))
+    s.set_forcing_modes(modes, hold=True)
+    s.advance(3)
+    assert np.array_equal(s.forcing_modes(), modes)
+    s.set_forcing_modes(modes, hold=False)
+    s.advance(1)
+    assert not np.array_equal(s.forcing_modes(), modes)
+
+
+def test_context_corrector_matches_oracle_and_zero_is_identity():
+    import ctypes as C
+    from paper_2512_13403_b300 import _lib
+    shape = (8, 16, 16)
+    U0 = inputs.decaying_turbulence(shape, seed=3, sigma=0.5, mach=1.0, p_sigma=0.2)
+    s = solver(shape, "f32")
+    s.init_state(to_gpu(U0, "f32"))
+    lib = _lib.load()
+    with pytest.raises(_lib.DhError):
+        _lib.check(lib.dh_correct(s.ctx), s.ctx)
+    mu = [float(U0[c].mean()) for c in range(5)]
+    sg = [float(U0[c].std()) for c in range(5)]
+    out = [0.01 * v for v in sg]
+    p = init_params(1, out_scale=1.0).cuda()
+    norm = (C.c_float * 15)(*(mu + sg + out))
+    _lib.check(lib.dh_set_corrector(s.ctx, C.c_void_p(p.data_ptr()), norm), s.ctx)
+    _lib.check(lib.dh_correct(s.ctx), s.ctx)
+    got = s.get_state().double().cpu()
+    Uf = torch.from_numpy(U0).float().double()
+    ref = oc.correct(Uf, unflatten(p.double().cpu()), mu, sg, 1e-6 * float(Uf[0].mean()), 0.05, 5 / 3,
+                     out_scale=out)
+    # the corrections agree to the BF16 activation rounding; the state itself to float32
+    assert float((got - ref).abs().max() / (ref - Uf).abs().max()) < 2e-2
+    # zero network: identity
+    s.init_state(to_gpu(U0, "f32"))
+    z = torch.zeros(NPARAM, dtype=torch.float32, device="cuda")
+    _lib.check(lib.dh_set_corrector(s.ctx, C.c_void_p(z.data_ptr()), norm), s.ctx)
+    _lib.check(lib.dh_correct(s.ctx), s.ctx)
+    assert torch.equal(s.get_state().cpu(), torch.from_numpy(U0).float())
+
+
+def test_small_pair_train_evaluate_cycle():
+    setup = closure.ClosureSetup(fine=32, factor=4, runs=2, snapshots=6, spinup_steps=10)
+    X, Y = closure.make_pairs(setup)
+    assert X.shape == (12, 5, 8, 8, 8) and torch.isfinite(X).all() and torch.isfinite(Y).all()
+    # the coarse step and the downsampled fine run differ, but not by much
+    rel = float((Y - X).norm() / Y.norm())
+    assert 0.0 < rel < 0.1
+    params, norm, losses = closure.train(X, Y, epochs=3, lr0=3e-3, lr1=1e-3)
+    assert losses[-1] < losses[0]
+    err, ms = closure.evaluate(setup, params, norm, steps=4, equal_time_substeps=2)
+    for k in ("uncorrected", "corrected", "uncorrected_equal_gpu_time"):
+        assert len(err[k]) == 4 and all(np.isfinite(err[k]))

@@ -190,7 +190,10 @@ def test_network_forward_and_backward_against_oracle():
     # the BF16 roundings passed straight through
     tgt = yr + 0.1 * torch.randn(yr.shape, generator=torch.Generator().manual_seed(9), dtype=torch.float64)
     grads = torch.zeros(cr.NPARAM, dtype=torch.float32, device="cuda")
-    loss = net.backward(tgt.float().cuda().contiguous(), grads)
+    # residual target (U_target - U_in)/s with U_in = 0 and s = sigma gives tgt itself
+    zero = torch.zeros_like(Ug)
+    sg = torch.tensor(sigma, dtype=torch.float64).reshape(5, 1, 1, 1)
+    loss = net.backward(zero, (tgt * sg).float().cuda().contiguous(), grads)
     q = {k: v.clone().requires_grad_(True) for k, v in pd.items()}
     st = lambda t: t + (oc.bf16(t) - t).detach()
     mu_t = torch.tensor(mu, dtype=torch.float64).reshape(5, 1, 1, 1)
@@ -212,7 +215,7 @@ def test_zero_network_is_identity_and_floors():
     from paper_2512_13403_b300 import corrector as cr
     shape = (8, 16, 16)
     net = cr.Network(shape)
-    net.set_params(torch.zeros(cr.NPARAM), [0.0] * 5, [1.0] * 5)
+    net.set_params(torch.zeros(cr.NPARAM), [0.0] * 5, [1.0] * 5, [1.0] * 5)
     U = torch.from_numpy(__import__("paper_2512_13403_b300").inputs.decaying_turbulence(shape, seed=2, sigma=0.5, mach=1.0)).float().cuda().contiguous()
     V = U.clone()
     net.correct_state(V, 1e-6, 0.05, 5 / 3)
