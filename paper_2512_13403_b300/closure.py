@@ -6,9 +6,11 @@ and its training step, Adam); this module sequences the calls and reports error 
 
 Pairs (one per coarse step of a fine run): input = one coarse step H_c applied to D4 U_f(t),
 target = D4 U_f(t + dt_c), with D4 the 4^3 block mean of the conserved fields and the fine run
-landing exactly on t + dt_c (its last step clipped).  The coarse step is driven with the fine
-run's forcing mode table at time t (held for the step), so both grids see one acceleration
-history and the pair isolates the coarse discretisation error.
+landing exactly on t + dt_c (its last step clipped).  Forcing: over each coarse interval the
+fine run draws and applies one OU update in its first substep and then holds that table for its
+remaining substeps, and the coarse step is driven with the same table; both grids thus see one
+acceleration history, and the pair isolates the coarse discretisation error instead of the
+difference between two noise realisations.
 """
 from __future__ import annotations
 
@@ -66,6 +68,21 @@ def advance_to(solver: Solver, dt_total: float):
         t += dt
 
 
+def fine_interval(fine: Solver, dt_c: float, forcing: bool):
+    """Advance the fine run by dt_c: the first substep takes a fresh OU update, the rest hold the
+    table.  Returns the table of the interval (None without forcing)."""
+    if forcing:
+        fine.set_forcing_modes(fine.forcing_modes(), hold=False)
+    dt1 = min(fine.compute_dt(), dt_c)
+    fine.step(dt1)
+    modes = None
+    if forcing:
+        modes = fine.forcing_modes()
+        fine.set_forcing_modes(modes, hold=True)
+    advance_to(fine, dt_c - dt1)
+    return modes
+
+
 def make_pairs(setup: ClosureSetup, log=None):
     """Returns (inputs, targets): float32 CUDA tensors of shape (P, 5, n, n, n)."""
     n, nc = setup.fine, setup.coarse
@@ -81,11 +98,12 @@ def make_pairs(setup: ClosureSetup, log=None):
         for s in range(setup.snapshots):
             Uc0 = downsample(fine.get_state(), setup.factor)
             coarse.init_state(Uc0)
-            if setup.forcing:
-                coarse.set_forcing_modes(fine.forcing_modes(), hold=True)
-            dt_c = coarse.step(0.0)
+            dt_c = coarse.compute_dt()
+            modes = fine_interval(fine, dt_c, setup.forcing)
+            if modes is not None:
+                coarse.set_forcing_modes(modes, hold=True)
+            coarse.step(dt_c)
             X[k] = coarse.get_state()
-            advance_to(fine, dt_c)
             Y[k] = downsample(fine.get_state(), setup.factor)
             k += 1
         if log:
@@ -173,11 +191,11 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seed: int = 20
     gpu_ms = {k: 0.0 for k in runs}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for k in range(steps):
-        modes = fine.forcing_modes() if setup.forcing else None
+        dt_c = plain.compute_dt()
+        modes = fine_interval(fine, dt_c, setup.forcing)
         for s in runs.values():
             if modes is not None:
                 s.set_forcing_modes(modes, hold=True)
-        dt_c = plain.compute_dt()
         for name, s in runs.items():
             ev0.record()
             if name == "uncorrected_equal_gpu_time":
@@ -190,7 +208,6 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seed: int = 20
             ev1.record()
             ev1.synchronize()
             gpu_ms[name] += ev0.elapsed_time(ev1)
-        advance_to(fine, dt_c)
         ref = downsample(fine.get_state(), setup.factor)
         for name, s in runs.items():
             err[name].append(_rel_l2(s.get_state(), ref))
