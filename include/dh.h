@@ -160,9 +160,22 @@ dh_status dh_adjoint_advance(dh_ctx* ctx, int n_steps, int ckpt_every, const voi
 /* ---- Corrector building blocks (residual 3D CNN, BF16 tensor cores, FP32 accumulation) ----
    A 3x3x3 periodic convolution over an nx*ny*nz grid as an implicit GEMM on tcgen05:
    out[cell, n] = sum_{tap, c} act[cell + offset(tap), c] * W[n, c, tap] (+ bias[n]), the
-   closure network of Sec. 7 in 3D.  Activations are bf16, channel-last [cell][cin_pad] with
-   cin_pad 8 (up to 8 real channels, the rest zero) or 32; nx*ny*nz must be a multiple of 128
-   and every dimension >= 3.  All pointers are device pointers; work is ordered on `stream`.
+   closure network of Sec. 7 in 3D.  Every dimension must be >= 3.  All pointers are device
+   pointers; work is ordered on `stream`.
+
+   Padded activation layout (bf16): C channels (C = 8, up to 8 real with the rest zero, or 32)
+   are stored as C/8 channel groups of R = dh_conv_padded_rows(nx, ny, nz) rows of 8 bf16
+   (16 bytes), group after group, C/8 * R * 16 bytes in all.  In group g, row
+   guard + ((z+1)(ny+2) + (y+1))(nx+2) + (x+1) holds channels 8g..8g+7 of cell (x, y, z) for
+   x, y, z in [-1, n]: coordinates -1 and n are periodic images (x = -1 is cell nx-1, and so on
+   for faces, edges and corners).  The guard rows before and after the padded volume must be
+   zero: allocate the buffer zeroed once; the kernels below write only cell rows and their
+   images.  A tap is then a fixed row offset, which is what lets the tensor-core operand of
+   every tap be a shifted view of one shared-memory window.
+
+   dh_conv_padded_rows: R above (-1 if a dimension is < 3).
+   dh_conv_pad: channel-last bf16 [cell][channels] -> padded layout (cell rows and images).
+   dh_conv_unpad: padded layout -> channel-last bf16 [cell][channels].  channels is 8 or 32.
 
    dh_pack_conv_weights: converts fp32 weights W[cout][cin][3][3][3] (cross-correlation order,
    kernel index (kz, ky, kx) = offset + 1) into the packed bf16 operand `packed` of
@@ -171,11 +184,19 @@ dh_status dh_adjoint_advance(dh_ctx* ctx, int n_steps, int ckpt_every, const voi
    convolution (outputs = cout); 1 packs its data gradient (outputs = cin, taps mirrored), so
    that the same kernel maps an output gradient to an input gradient.
 
-   dh_conv3d_bf16 modes: 0 = GELU (out bf16 [cell][32] = bf16(gelu(z)), z_out fp32
-   [cell][32] = acc + bias, nullable); 1 = linear (out fp32 planar [n_real][cell] = acc + bias);
-   2 = GELU gradient (out bf16 [cell][32] = bf16(acc * gelu'(z_in))).  Supported
+   dh_conv3d_bf16: act in the padded layout with cin_pad channels.  Modes: 0 = GELU (out bf16
+   padded, 32 channels, = bf16(gelu(z)); z_out fp32 [cell][32] = acc + bias, nullable);
+   1 = linear (out fp32 planar [n_real][cell] = acc + bias); 2 = GELU gradient (out bf16
+   padded, 32 channels, = bf16(acc * gelu'(z_in)), z_in fp32 [cell][32]).  Supported
    (cin_pad, nout_pad, mode): (8,32,0), (8,32,2), (32,32,0), (32,32,2), (32,16,1), (32,32,1).
-   *err_flag (device unsigned) becomes nonzero if a bounded wait inside the kernel gave up. */
+   Two shared-memory windows of (130 + 2 (nx+2)) rows per tap plane must fit next to the
+   weights: DH_ERR_ARG for nx beyond about 150 with 32 input channels.  *err_flag (device
+   unsigned) becomes nonzero if a bounded wait inside the kernel gave up. */
+long long dh_conv_padded_rows(int nx, int ny, int nz);
+dh_status dh_conv_pad(const void* src, int channels, int nx, int ny, int nz, void* dst,
+                      void* stream);
+dh_status dh_conv_unpad(const void* src, int channels, int nx, int ny, int nz, void* dst,
+                        void* stream);
 dh_status dh_pack_conv_weights(const float* W, int cout, int cin, int transpose_flip,
                                void* packed, void* stream);
 dh_status dh_conv3d_bf16(const void* act, int cin_pad, const void* packed, int nout_pad,
@@ -185,8 +206,8 @@ dh_status dh_conv3d_bf16(const void* act, int cin_pad, const void* packed, int n
 
 /* dh_conv3d_wgrad_bf16: weight gradient of such a convolution,
    dW[n][c][tap] = sum_cells grad[cell][n] * act[cell + offset(tap)][c], written in the fp32
-   master layout W[cout][cin][27].  act: bf16 [cell][cin_pad] (cin real channels); grad: bf16
-   [cell][grad_stride] (cout real channels, the rest zero), grad_stride 8 or 32.  `partial` is
+   master layout W[cout][cin][27].  act: padded layout with cin_pad channels (cin real); grad:
+   padded layout with grad_stride channels (8 or 32; cout real, the rest zero).  `partial` is
    caller-owned fp32 scratch of nctas * ceil(27*cin_pad/128) * 128 * (cout > 16 ? 32 : 16)
    values; the per-CTA partial sums are added in a fixed order. */
 dh_status dh_conv3d_wgrad_bf16(const void* act, int cin_pad, int cin, const void* grad,
@@ -199,7 +220,7 @@ dh_status dh_conv3d_wgrad_bf16(const void* act, int cin_pad, int cin, const void
    flat fp32 device array of dh_cnn_param_count() = 36357 values: W1[32][5][27], b1[32],
    W2[32][32][27], b2[32], W3[5][32][27], b3[5]; norm15 = mu[5], sigma[5], s[5] (host, sigma > 0):
    input normalisation (U - mu)/sigma and per-channel output scale s of the correction.
-   A dh_cnn owns the activations of one grid (nx*ny*nz divisible by 128). */
+   A dh_cnn owns the activations of one grid (every dimension >= 3). */
 typedef struct dh_cnn dh_cnn;
 long long dh_cnn_param_count(void);
 dh_status dh_cnn_create(int nx, int ny, int nz, void* cuda_stream, dh_cnn** out);
@@ -216,7 +237,8 @@ dh_status dh_cnn_forward(dh_cnn* cnn, const float* U, float* y_out);
 dh_status dh_cnn_backward(dh_cnn* cnn, const float* U_in, const float* U_target, float* grads,
                           double* loss);
 /* U <- U + s * network(U) in place (float32 state, device), then rho >= rho_floor and
-   E >= |m|^2/(2 rho) + rho T_floor/(gamma - 1).  Synchronises. */
+   E >= |m|^2/(2 rho) + rho T_floor/(gamma - 1).  An inference pass: it keeps no activations
+   for dh_cnn_backward (call dh_cnn_forward again before the next backward).  Synchronises. */
 dh_status dh_cnn_correct_state(dh_cnn* cnn, float* U, double rho_floor, double T_floor,
                                double gamma);
 /* Adam (Kingma & Ba) on n parameters: m, v are caller-owned moment buffers (device), step >= 1

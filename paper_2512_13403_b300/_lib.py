@@ -52,6 +52,9 @@ _SIGNATURES = {
     "dh_solve_poisson": (C.c_int, [_P, _P, C.c_int]),
     "dh_adjoint_advance": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dh_conserved_totals_static": (C.c_int, [_P, C.c_int, C.c_longlong, _P, _P]),
+    "dh_conv_padded_rows": (C.c_longlong, [C.c_int, C.c_int, C.c_int]),
+    "dh_conv_pad": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "dh_conv_unpad": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "dh_pack_conv_weights": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
     "dh_conv3d_bf16": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int, _P, _P, _P, C.c_int,
                                  C.c_int, C.c_int, C.c_int, _P, _P]),

@@ -12,6 +12,7 @@
 
 #include <string>
 
+#include "conv_layout.cuh"
 #include "dh_internal.h"
 
 namespace {
@@ -38,12 +39,14 @@ struct dh_cnn {
   float* norm_dev = nullptr;
   __nv_bfloat16 *pk_w1 = nullptr, *pk_w2 = nullptr, *pk_w3 = nullptr;   // forward operands
   __nv_bfloat16 *pk_w2t = nullptr, *pk_w3t = nullptr;                  // data-gradient operands
-  __nv_bfloat16 *x0 = nullptr, *h1 = nullptr, *h2 = nullptr;            // activations
-  float *z1 = nullptr, *z2 = nullptr, *y = nullptr;
-  __nv_bfloat16 *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr;          // gradients
+  // activations and their gradients, padded layout (conv_layout.cuh): 1 or 4 channel groups
+  __nv_bfloat16 *x0 = nullptr, *h1 = nullptr, *h2 = nullptr;
+  float *z1 = nullptr, *z2 = nullptr, *y = nullptr;                     // [cell][32], [5][cell]
+  __nv_bfloat16 *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr;
   float* partial = nullptr;                 // weight-gradient partials
   int nctas = 148;
   double* red = nullptr;                    // reduction scratch
+  double* bpart = nullptr;                  // bias-gradient partial sums [32][BG_BLOCKS]
   unsigned* err = nullptr;
   bool have_params = false;
   bool have_forward = false;
@@ -52,15 +55,25 @@ struct dh_cnn {
 
 namespace dh {
 
-__global__ void normalize_kernel(const float* __restrict__ U, long long n, const float* __restrict__ norm,
-                                 __nv_bfloat16* __restrict__ x0) {
+__device__ __forceinline__ void cell_xyz(long long q, const ConvGeom& g, int& x, int& y, int& z) {
+  x = (int)(q % g.nx);
+  const long long t = q / g.nx;
+  y = (int)(t % g.ny);
+  z = (int)(t / g.ny);
+}
+
+__global__ void normalize_kernel(const float* __restrict__ U, ConvGeom g,
+                                 const float* __restrict__ norm, __nv_bfloat16* __restrict__ x0) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c] = __float2bfloat16_rn((U[c * n + q] - norm[c]) / norm[5 + c]);
     v[5] = v[6] = v[7] = __float2bfloat16_rn(0.0f);
-    reinterpret_cast<uint4*>(x0)[q] = *reinterpret_cast<const uint4*>(v);
+    int x, y, z;
+    cell_xyz(q, g, x, y, z);
+    store_with_images(reinterpret_cast<uint4*>(x0), g, x, y, z, *reinterpret_cast<const uint4*>(v));
   }
 }
 
@@ -68,8 +81,9 @@ __global__ void normalize_kernel(const float* __restrict__ U, long long n, const
 // (y - t)^2; dy = d loss / d y as bf16 [cell][8].
 __global__ void mse_grad_kernel(const float* __restrict__ y, const float* __restrict__ Uin,
                                 const float* __restrict__ Utgt, const float* __restrict__ norm,
-                                long long n, __nv_bfloat16* __restrict__ dy,
+                                ConvGeom g, __nv_bfloat16* __restrict__ dy,
                                 double* __restrict__ partial) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
   __shared__ double red[256];
   double s = 0.0;
   const double scale = 2.0 / (5.0 * (double)n);
@@ -79,13 +93,15 @@ __global__ void mse_grad_kernel(const float* __restrict__ y, const float* __rest
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      const double t = ((double)Utgt[c * n + q] - (double)Uin[c * n + q]) / (double)norm[10 + c];
-      const double d = (double)y[c * n + q] - t;
-      s += d * d;
-      v[c] = __float2bfloat16_rn((float)(scale * d));
+      const float t = (Utgt[c * n + q] - Uin[c * n + q]) / norm[10 + c];
+      const float d = y[c * n + q] - t;
+      s += (double)d * (double)d;
+      v[c] = __float2bfloat16_rn((float)scale * d);
     }
     v[5] = v[6] = v[7] = __float2bfloat16_rn(0.0f);
-    reinterpret_cast<uint4*>(dy)[q] = *reinterpret_cast<const uint4*>(v);
+    int x, yy, z;
+    cell_xyz(q, g, x, yy, z);
+    store_with_images(reinterpret_cast<uint4*>(dy), g, x, yy, z, *reinterpret_cast<const uint4*>(v));
   }
   red[threadIdx.x] = s;
   __syncthreads();
@@ -104,20 +120,53 @@ __global__ void sum_blocks_kernel(const double* partial, int nb, double scale, d
   }
 }
 
-// db[c] = sum over cells of g[cell][c] (bf16 [cell][stride]) for c < nch; one block per channel
-__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ g, int stride, long long n,
-                                 float* __restrict__ db) {
-  __shared__ double red[256];
-  const int c = blockIdx.x;
-  double s = 0.0;
-  for (long long q = threadIdx.x; q < n; q += blockDim.x) s += (double)__bfloat162float(g[q * stride + c]);
-  red[threadIdx.x] = s;
+// Bias gradient db[c] = sum over cells of channel c of a padded gradient.  Block (b, group)
+// sums a contiguous cell range of one 8-channel group (each thread reads whole 16-byte rows);
+// part[c][b] is then added in block order by bias_grad_final_kernel.
+constexpr int BG_BLOCKS = 64;
+__global__ void bias_grad_partial_kernel(const __nv_bfloat16* __restrict__ grad, ConvGeom g,
+                                         double* __restrict__ part) {
+  __shared__ double red[8][256];
+  const int grp = blockIdx.y;
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long q0 = blockIdx.x * per, q1 = q0 + per < n ? q0 + per : n;
+  const uint4* rows = reinterpret_cast<const uint4*>(grad) + (long long)grp * g.rows;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    int x, y, z;
+    cell_xyz(q, g, x, y, z);
+    const uint4 v = __ldg(rows + pad_row(g, x, y, z));
+    const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += __bfloat162float(h[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) red[e][threadIdx.x] = (double)acc[e];
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) red[e][threadIdx.x] += red[e][threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) db[c] = (float)red[0];
+  if (threadIdx.x < 8) part[(long long)(grp * 8 + threadIdx.x) * gridDim.x + blockIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void bias_grad_final_kernel(const double* __restrict__ part, int nb, int nch,
+                                       float* __restrict__ db) {
+  const int c = threadIdx.x;
+  if (c < nch) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(long long)c * nb + b];
+    db[c] = (float)s;
+  }
+}
+
+static void bias_grad(const __nv_bfloat16* grad, int groups, int nch, const ConvGeom& g,
+                      double* part, float* db, cudaStream_t s) {
+  bias_grad_partial_kernel<<<dim3(BG_BLOCKS, groups), 256, 0, s>>>(grad, g, part);
+  bias_grad_final_kernel<<<1, 32, 0, s>>>(part, BG_BLOCKS, nch, db);
 }
 
 __global__ void correct_kernel(float* __restrict__ U, const float* __restrict__ y, long long n,
@@ -181,7 +230,7 @@ extern "C" void dh_cnn_destroy(dh_cnn* c) {
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   void* ps[] = {c->params, c->norm_dev, c->pk_w1, c->pk_w2, c->pk_w3, c->pk_w2t, c->pk_w3t,
                 c->x0, c->h1, c->h2, c->z1, c->z2, c->y, c->dy, c->dz2, c->dz1, c->partial,
-                c->red, c->err};
+                c->red, c->bpart, c->err};
   for (void* p : ps) cudaFree(p);
   delete c;
 }
@@ -190,10 +239,11 @@ extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn*
   if (!out) return DH_ERR_ARG;
   *out = nullptr;
   const long long n = (long long)nx * ny * nz;
-  if (nx < 3 || ny < 3 || nz < 3 || n % 128 != 0) {
-    dh_set_global_error("dh_cnn_create: every dimension >= 3 and nx*ny*nz divisible by 128");
+  if (nx < 3 || ny < 3 || nz < 3) {
+    dh_set_global_error("dh_cnn_create: every dimension must be >= 3");
     return DH_ERR_ARG;
   }
+  const long long prow = conv_geom(nx, ny, nz).rows;   // 16-byte rows per channel group
   dh_cnn* c = new dh_cnn();
   c->nx = nx; c->ny = ny; c->nz = nz; c->ncell = n;
   c->stream = (cudaStream_t)stream;
@@ -209,19 +259,26 @@ extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn*
   A((void**)&c->pk_w3, 16 * 864 * 2);
   A((void**)&c->pk_w2t, 32 * 864 * 2);
   A((void**)&c->pk_w3t, 32 * 224 * 2);
-  A((void**)&c->x0, n * 8 * 2);
-  A((void**)&c->h1, n * 32 * 2);
-  A((void**)&c->h2, n * 32 * 2);
+  A((void**)&c->x0, prow * 16);
+  A((void**)&c->h1, prow * 4 * 16);
+  A((void**)&c->h2, prow * 4 * 16);
   A((void**)&c->z1, n * 32 * 4);
   A((void**)&c->z2, n * 32 * 4);
   A((void**)&c->y, n * 5 * 4);
-  A((void**)&c->dy, n * 8 * 2);
-  A((void**)&c->dz2, n * 32 * 2);
-  A((void**)&c->dz1, n * 32 * 2);
+  A((void**)&c->dy, prow * 16);
+  A((void**)&c->dz2, prow * 4 * 16);
+  A((void**)&c->dz1, prow * 4 * 16);
   A((void**)&c->partial, (size_t)c->nctas * 7 * 128 * 32 * sizeof(float));
   A((void**)&c->red, (RBLOCKS + 8) * sizeof(double));
+  A((void**)&c->bpart, 32 * BG_BLOCKS * sizeof(double));
   A((void**)&c->err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(unsigned));
+  // the guard rows of the padded buffers must read as zero; every other row is rewritten by
+  // the producer of the buffer (cell rows and their halo images)
+  for (__nv_bfloat16* b : {c->x0, c->dy})
+    if (e == cudaSuccess) e = cudaMemset(b, 0, prow * 16);
+  for (__nv_bfloat16* b : {c->h1, c->h2, c->dz2, c->dz1})
+    if (e == cudaSuccess) e = cudaMemset(b, 0, prow * 4 * 16);
   if (e != cudaSuccess) {
     dh_set_global_error(std::string("dh_cnn_create: ") + cudaGetErrorString(e));
     dh_cnn_destroy(c);
@@ -261,19 +318,26 @@ static dh_status check_err(dh_cnn* c) {
   return DH_OK;
 }
 
-extern "C" dh_status dh_cnn_forward(dh_cnn* c, const float* U, float* y_out) {
+// The forward pass; keep_z stores the pre-activations z1, z2 that back-propagation needs
+// (an inference pass skips those 256 bytes per cell of writes).
+static dh_status cnn_forward(dh_cnn* c, const float* U, float* y_out, bool keep_z) {
   if (!c || !U) return DH_ERR_ARG;
   if (!c->have_params) { dh_set_global_error("dh_cnn_forward: parameters not set"); return DH_ERR_STATE; }
   const long long n = c->ncell;
   cudaStream_t s = c->stream;
-  normalize_kernel<<<grid_for(n), 256, 0, s>>>(U, n, c->norm_dev, c->x0);
+  c->have_forward = false;
+  normalize_kernel<<<grid_for(n), 256, 0, s>>>(U, conv_geom(c->nx, c->ny, c->nz), c->norm_dev, c->x0);
   CNN_TRY(cnn_cuda(c, cudaGetLastError(), "normalize"));
-  CNN_TRY(dh_conv3d_bf16(c->x0, 8, c->pk_w1, 32, c->params + OFF_B1, 0, nullptr, c->h1, c->z1, 32, c->nx, c->ny, c->nz, c->err, s));
-  CNN_TRY(dh_conv3d_bf16(c->h1, 32, c->pk_w2, 32, c->params + OFF_B2, 0, nullptr, c->h2, c->z2, 32, c->nx, c->ny, c->nz, c->err, s));
+  CNN_TRY(dh_conv3d_bf16(c->x0, 8, c->pk_w1, 32, c->params + OFF_B1, 0, nullptr, c->h1, keep_z ? c->z1 : nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
+  CNN_TRY(dh_conv3d_bf16(c->h1, 32, c->pk_w2, 32, c->params + OFF_B2, 0, nullptr, c->h2, keep_z ? c->z2 : nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
   CNN_TRY(dh_conv3d_bf16(c->h2, 32, c->pk_w3, 16, c->params + OFF_B3, 1, nullptr, c->y, nullptr, 5, c->nx, c->ny, c->nz, c->err, s));
   if (y_out) CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(y_out, c->y, n * 5 * sizeof(float), cudaMemcpyDeviceToDevice, s), "y"));
-  c->have_forward = true;
+  c->have_forward = keep_z;
   return DH_OK;
+}
+
+extern "C" dh_status dh_cnn_forward(dh_cnn* c, const float* U, float* y_out) {
+  return cnn_forward(c, U, y_out, true);
 }
 
 extern "C" dh_status dh_cnn_backward(dh_cnn* c, const float* U_in, const float* U_target,
@@ -282,19 +346,20 @@ extern "C" dh_status dh_cnn_backward(dh_cnn* c, const float* U_in, const float* 
   if (!c->have_forward) { dh_set_global_error("dh_cnn_backward: run dh_cnn_forward first"); return DH_ERR_STATE; }
   const long long n = c->ncell;
   cudaStream_t s = c->stream;
-  mse_grad_kernel<<<RBLOCKS, 256, 0, s>>>(c->y, U_in, U_target, c->norm_dev, n, c->dy, c->red);
+  const ConvGeom geo = conv_geom(c->nx, c->ny, c->nz);
+  mse_grad_kernel<<<RBLOCKS, 256, 0, s>>>(c->y, U_in, U_target, c->norm_dev, geo, c->dy, c->red);
   sum_blocks_kernel<<<1, 32, 0, s>>>(c->red, RBLOCKS, 1.0 / (5.0 * (double)n), c->red + RBLOCKS);
   // output layer
   CNN_TRY(dh_conv3d_wgrad_bf16(c->h2, 32, 32, c->dy, 8, 5, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W3, c->err, s));
-  bias_grad_kernel<<<5, 256, 0, s>>>(c->dy, 8, n, grads + OFF_B3);
+  bias_grad(c->dy, 1, 5, geo, c->bpart, grads + OFF_B3, s);
   CNN_TRY(dh_conv3d_bf16(c->dy, 8, c->pk_w3t, 32, nullptr, 2, c->z2, c->dz2, nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
   // hidden layer
   CNN_TRY(dh_conv3d_wgrad_bf16(c->h1, 32, 32, c->dz2, 32, 32, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W2, c->err, s));
-  bias_grad_kernel<<<32, 256, 0, s>>>(c->dz2, 32, n, grads + OFF_B2);
+  bias_grad(c->dz2, 4, 32, geo, c->bpart, grads + OFF_B2, s);
   CNN_TRY(dh_conv3d_bf16(c->dz2, 32, c->pk_w2t, 32, nullptr, 2, c->z1, c->dz1, nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
   // first layer
   CNN_TRY(dh_conv3d_wgrad_bf16(c->x0, 8, 5, c->dz1, 32, 32, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W1, c->err, s));
-  bias_grad_kernel<<<32, 256, 0, s>>>(c->dz1, 32, n, grads + OFF_B1);
+  bias_grad(c->dz1, 4, 32, geo, c->bpart, grads + OFF_B1, s);
   CNN_TRY(cnn_cuda(c, cudaGetLastError(), "backward"));
   if (loss) CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(loss, c->red + RBLOCKS, sizeof(double), cudaMemcpyDeviceToHost, s), "loss"));
   return check_err(c);
@@ -303,7 +368,7 @@ extern "C" dh_status dh_cnn_backward(dh_cnn* c, const float* U_in, const float* 
 extern "C" dh_status dh_cnn_correct_state(dh_cnn* c, float* U, double rho_floor, double T_floor,
                                           double gamma) {
   if (!c || !U) return DH_ERR_ARG;
-  CNN_TRY(dh_cnn_forward(c, U, nullptr));
+  CNN_TRY(cnn_forward(c, U, nullptr, false));
   correct_kernel<<<grid_for(c->ncell), 256, 0, c->stream>>>(U, c->y, c->ncell, c->norm_dev,
                                                             (float)rho_floor, (float)T_floor,
                                                             (float)(gamma - 1.0));

@@ -1,35 +1,40 @@
 // Residual 3D convolutional corrector on the tensor cores (BF16 operands, FP32 accumulation).
 //
 // Every 3x3x3 periodic convolution is an implicit GEMM: D[cell, n] = sum_k A[cell, k] B[n, k]
-// with k = (tap, input channel), A gathered from the 27 neighbours of each cell and B the packed
-// weights.  A persistent CTA of 128 threads walks 128-cell tiles (M = 128); for each 16-wide
-// K step the threads gather A into a 4-stage shared-memory ring (no-swizzle K-major core
-// matrices), one elected thread issues tcgen05.mma into a TMEM accumulator (128 lanes x N FP32
-// columns) and commits to the stage's mbarrier; B (all taps) stays resident in shared memory.
-// The epilogue reads TMEM with tcgen05.ld (one row per thread) and fuses bias + GELU, the
-// GELU derivative (backward), or the linear output.  The same kernel computes the backward
-// data gradient with tap-flipped, channel-transposed weights.
+// with k = (tap, input channel), A the 27 neighbours of each cell and B the packed weights.
+// Activations are kept in the padded channel-group-major layout of conv_layout.cuh, in which a
+// tap is a constant row shift.  A persistent CTA walks 128-row tiles of the padded volume
+// (M = 128); for each tile one thread copies three windows (the tile's rows in planes dz = -1,
+// 0, +1, widened by the in-plane reach of the taps) into a shared-memory ring with 1D bulk
+// copies (TMA engine, mbarrier transaction counts), then issues one tcgen05.mma per 16-wide K
+// step whose A descriptor is the window shifted by the tap's row offset — no gather, no
+// per-step barrier.  B (all taps) stays resident in shared memory.  Two TMEM accumulators
+// alternate, so the epilogue of tile j-1 (tcgen05.ld, bias + GELU, the GELU derivative, or the
+// linear output; padded writes with halo images) runs while the tensor cores work on tile j.
+// Rows of a tile that are halo positions are computed and dropped.  The same kernel computes
+// the backward data gradient with tap-flipped, channel-transposed weights.
 //
-// Channel-last activations: bf16 [cell][C], C = 8 (5 state channels padded) or 32.
-// K layout: k = tap * C + c, tap = (dz+1)*9 + (dy+1)*3 + (dx+1); for C = 8 a 16-wide K step
-// holds two taps (tap 27 is a zero pad), for C = 32 half a tap.
+// K layout: k = tap * C + c, tap = (dz+1)*9 + (dy+1)*3 + (dx+1).  C = 32: a K step is half a
+// tap (two channel groups, LBO = one window).  C = 8: a K step holds taps 2s and 2s+1 (LBO =
+// the distance between their two shifted windows; tap 27 points at a zero block).
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include "conv_layout.cuh"
 #include "dh_internal.h"
 #include "tc_ptx.cuh"
 
 namespace dh {
 
-constexpr int CV_THREADS = 128;
-constexpr int CV_STAGES = 4;
-constexpr int CV_STAGE_BYTES = 128 * 16 * 2;   // 128 rows x 16 bf16
+constexpr int CV_THREADS = 320;   // 10 warps: TMA, MMA, 8 x epilogue
+constexpr int CV_MAX_STAGES = 3;
 constexpr uint32_t CV_WAIT_ITERS = 1u << 22;   // bounded mbarrier waits
+constexpr int CV_SMEM_MAX = 226 * 1024;   // dynamic; the kernel's static part is below 1 KB
 
 enum ConvMode : int {
-  CONV_GELU = 0,        // out_bf16 = bf16(gelu(acc + bias)); z_out = acc + bias (fp32)
+  CONV_GELU = 0,        // out_bf16 = bf16(gelu(acc + bias)) (padded); z_out = acc + bias (fp32)
   CONV_LINEAR = 1,      // out_f32 planar [c][cell] = acc + bias for c < n_real
-  CONV_GELU_GRAD = 2,   // out_bf16 = bf16(acc * gelu'(z_in))
+  CONV_GELU_GRAD = 2,   // out_bf16 = bf16(acc * gelu'(z_in)) (padded)
 };
 
 __device__ __forceinline__ float gelu_exact(float z) {
@@ -42,53 +47,88 @@ __device__ __forceinline__ float gelu_grad(float z) {
   return Phi + z * phi;
 }
 
+// Two floats rounded to bf16 (nearest even), element 0 in the low half (lower address).
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  uint32_t u;
+  memcpy(&u, &h, sizeof(u));
+  return u;
+}
+
 struct ConvArgs {
-  const __nv_bfloat16* act;   // [cells][CIN]
+  const __nv_bfloat16* act;   // padded layout, CIN / 8 groups
   const __nv_bfloat16* wpk;   // packed B, [NOUT/8][K/8][8][8] bf16
   const float* bias;          // [NOUT] (nullable: zero)
   const float* z_in;          // [cells][32] fp32, CONV_GELU_GRAD
-  __nv_bfloat16* out_bf16;    // [cells][NOUT] for GELU modes
+  __nv_bfloat16* out_bf16;    // padded layout, 4 groups, for the GELU modes
   float* out_f32;             // planar [n_real][cells] for CONV_LINEAR
   float* z_out;               // [cells][NOUT] fp32 (nullable) for CONV_GELU
   int n_real;                 // real output channels (CONV_LINEAR)
-  int nx, ny, nz;
   unsigned* err;              // set to 1 if a bounded wait gave up
 };
 
+template <int CIN, int NOUT>
+struct ConvShape {
+  static constexpr int G = CIN / 8;
+  static constexpr int K = CIN == 32 ? 27 * 32 : 28 * 8;   // padded reduction length
+  static constexpr int KSTEPS = K / 16;
+  static constexpr int B_BYTES = NOUT * K * 2;
+  static constexpr int ZERO_BYTES = CIN == 8 ? 128 * 16 : 0;
+  static constexpr uint32_t TMEM_COLS = 2 * NOUT <= 32 ? 32 : 64;   // two accumulators
+  static size_t stage_bytes(const ConvGeom& g) { return (size_t)3 * G * g.win * 16; }
+  static size_t smem_bytes(const ConvGeom& g, int stages) {
+    return (size_t)B_BYTES + stages * stage_bytes(g) + ZERO_BYTES + 12 * 8 + 16;
+  }
+};
+
+// Bounded wait on an mbarrier phase that also gives up when another role has aborted.
+__device__ __forceinline__ bool cv_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t i = 0; i < CV_WAIT_ITERS; ++i) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+// Warp roles: warp 0 lane 0 copies windows (TMA), warp 1 issues the MMAs (converged, one
+// elected lane), warps 2..9 run the epilogue (warp w reads TMEM lanes 32 (w % 4) .. and 16
+// of the accumulator's columns).
 template <int CIN, int NOUT, int MODE>
 __global__ void __launch_bounds__(CV_THREADS)
-conv3d_tc_kernel(const ConvArgs p) {
-  constexpr int K = CIN == 32 ? 27 * 32 : 28 * 8;      // padded reduction length
-  constexpr int KSTEPS = K / 16;
-  constexpr int B_BYTES = NOUT * K * 2;
-  constexpr uint32_t TMEM_COLS = 32;
+conv3d_tc_kernel(const ConvArgs p, const ConvGeom g, const int stages) {
+  using S = ConvShape<CIN, NOUT>;
+  constexpr int G = S::G, KSTEPS = S::KSTEPS, K = S::K;
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sB = smem;                              // resident weights
-  unsigned char* sA = smem + B_BYTES;                    // stage ring
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + CV_STAGES * CV_STAGE_BYTES);
-  uint64_t* bar_done = bars + CV_STAGES;
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar_done + 1);
+  const uint32_t win_bytes = (uint32_t)g.win * 16;
+  const uint32_t stage_bytes = 3u * G * win_bytes;
+  unsigned char* sB = smem;                                        // resident weights
+  unsigned char* sA = smem + S::B_BYTES;                           // window ring
+  unsigned char* sZero = sA + (size_t)stages * stage_bytes;        // zero tap (C = 8)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sZero + S::ZERO_BYTES);
+  uint64_t* full = bars;          // [3] windows of a tile landed (TMA -> MMA)
+  uint64_t* empty = bars + 3;     // [3] MMAs reading a slot completed (MMA -> TMA)
+  uint64_t* accf = bars + 6;      // [2] accumulator holds a finished tile (MMA -> epilogue)
+  uint64_t* acce = bars + 8;      // [2] accumulator read out (epilogue -> MMA), 8 arrivals
+  uint64_t* bbar = bars + 10;     // weights landed
+  uint64_t* drain = bars + 11;    // abort path: all issued MMAs completed
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 12);
   __shared__ int s_abort;
 
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5;
-  const long long ncell = (long long)p.nx * p.ny * p.nz;
-  const int ntiles = (int)(ncell / 128);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long ncell = (long long)g.nx * g.ny * g.nz;
+  const int nt = (int)((g.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);   // own tiles
 
-  // weights -> shared memory (same packed layout)
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(p.wpk);
-    uint4* dst = reinterpret_cast<uint4*>(sB);
-    for (int i = tid; i < B_BYTES / 16; i += CV_THREADS) dst[i] = __ldg(src + i);
-  }
+  if (S::ZERO_BYTES)
+    for (int i = tid; i < S::ZERO_BYTES / 16; i += CV_THREADS)
+      reinterpret_cast<uint4*>(sZero)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
-    for (int b = 0; b < CV_STAGES; ++b) tc::mbar_init(&bars[b], 1);
-    tc::mbar_init(bar_done, 1);
+    for (int b = 0; b < 12; ++b) tc::mbar_init(&bars[b], (b == 8 || b == 9) ? 8u : 1u);
     tc::mbar_fence_init();
     s_abort = 0;
   }
-  if (warp == 0) {
-    tc::tmem_alloc(s_tmem, TMEM_COLS);
+  if (warp == 1) {
+    tc::tmem_alloc(s_tmem, S::TMEM_COLS);
     tc::tmem_relinquish();
   }
   tc::fence_async_smem();
@@ -96,133 +136,204 @@ conv3d_tc_kernel(const ConvArgs p) {
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *s_tmem;
-  const uint32_t idesc = tc::idesc_bf16_f32(128, NOUT);
-  const uint32_t sA_addr = tc::smem_u32(sA);
-  const uint32_t sB_addr = tc::smem_u32(sB);
+  volatile int* abort_flag = &s_abort;
+  int tma_issued = 0;            // warp 0 lane 0
+  bool b_waited = false;         // warp 1
 
-  uint32_t phase_bits = 0;   // parity of the next wait, per stage
-  uint32_t done_phase = 0;
-  long long it = 0;          // running K-step counter across tiles
-
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    // the cell of this thread's A row
-    const long long q = (long long)tile * 128 + tid;
-    const int i = (int)(q % p.nx);
-    const long long t1 = q / p.nx;
-    const int j = (int)(t1 % p.ny);
-    const int k = (int)(t1 / p.ny);
-
-    for (int s = 0; s < KSTEPS; ++s, ++it) {
-      const int b = (int)(it % CV_STAGES);
-      if (it >= CV_STAGES) {
-        if (!tc::mbar_wait(&bars[b], (phase_bits >> b) & 1u, CV_WAIT_ITERS)) s_abort = 1;
-        phase_bits ^= 1u << b;
-      }
-      // gather the two 16-byte core-matrix rows of this thread (kg = 0, 1)
-      unsigned char* stage = sA + b * CV_STAGE_BYTES;
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint32_t sA_addr = tc::smem_u32(sA);
+      tc::mbar_arrive_expect_tx(bbar, S::B_BYTES);
+      tc::bulk_g2s(tc::smem_u32(sB), p.wpk, S::B_BYTES, bbar);
+      for (int j = 0; j < nt; ++j) {
+        const int slot = j % stages;
+        if (j >= stages && !cv_wait(&empty[slot], (uint32_t)(j / stages - 1) & 1u, abort_flag)) break;
+        const long long R0 = g.PXY + 128 * (blockIdx.x + (long long)j * gridDim.x);
+        tc::mbar_arrive_expect_tx(&full[slot], stage_bytes);
+        for (int dzi = 0; dzi < 3; ++dzi) {
+          const long long row = g.guard + R0 + (long long)(dzi - 1) * g.PXY - (g.PX + 1);
 #pragma unroll
-      for (int kg = 0; kg < 2; ++kg) {
-        int tap, c0;
-        if (CIN == 32) { tap = s >> 1; c0 = (s & 1) * 16 + kg * 8; }
-        else { tap = 2 * s + kg; c0 = 0; }
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (tap < 27) {
-          const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-          const int ii = wrap(i + dx, p.nx), jj = wrap(j + dy, p.ny), kk = wrap(k + dz, p.nz);
-          const long long nq = ((long long)kk * p.ny + jj) * p.nx + ii;
-          v = __ldg(reinterpret_cast<const uint4*>(p.act + nq * CIN + c0));
+          for (int cg = 0; cg < G; ++cg)
+            tc::bulk_g2s(sA_addr + slot * stage_bytes + (dzi * G + cg) * win_bytes,
+                         p.act + ((long long)cg * g.rows + row) * 8, win_bytes, &full[slot]);
         }
-        const int off = (((tid >> 3) * 2 + kg) * 8 + (tid & 7)) * 16;
-        *reinterpret_cast<uint4*>(stage + off) = v;
-      }
-      tc::fence_async_smem();
-      __syncthreads();
-      if (s_abort) break;
-      if (tid == 0) {
-        tc::tc_fence_after();
-        const uint64_t adesc = tc::smem_desc(sA_addr + b * CV_STAGE_BYTES, 128, 256);
-        const uint64_t bdesc = tc::smem_desc(sB_addr + s * 256, 128, (K / 8) * 128);
-        tc::mma_bf16(tmem, adesc, bdesc, idesc, s > 0 ? 1u : 0u);
-        tc::mma_commit(&bars[b]);
-        if (s == KSTEPS - 1) tc::mma_commit(bar_done);
+        ++tma_issued;
       }
     }
-    if (s_abort) break;
-    if (!tc::mbar_wait(bar_done, done_phase, CV_WAIT_ITERS)) s_abort = 1;
-    done_phase ^= 1u;
-    __syncthreads();
-    if (s_abort) break;
-    tc::tc_fence_after();
-
-    // epilogue: this thread owns TMEM lane `tid` (warp w reads lanes 32w..32w+31)
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    if (NOUT == 32) {
-      float acc[32];
-      tc::tmem_ld_32x32b_x32(taddr, acc);
-      tc::tmem_ld_wait();
-      if (MODE == CONV_GELU) {
-        __align__(16) __nv_bfloat16 hv[32];
+  } else if (warp == 1) {
+    // converged warp: every lane waits and computes the (uniform) descriptors; one lane issues
+    const uint32_t idesc = tc::idesc_bf16_f32(128, NOUT);
+    const uint32_t sA_addr = tc::smem_u32(sA), sB_addr = tc::smem_u32(sB);
+    const uint32_t win16 = (uint32_t)g.win;          // window length in 16-byte units
+    const int px16 = g.PX;                           // one padded row of a plane, in 16-byte units
+    const uint64_t bdesc0 = tc::smem_desc(sB_addr, 128, (K / 8) * 128);
+    // zero block relative to a slot's window origin (C = 8 pairs tap 26 with it), 16-byte units
+    uint32_t zero16_slot[CV_MAX_STAGES];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const float z = acc[c] + (p.bias ? __ldg(p.bias + c) : 0.0f);
-          if (p.z_out) p.z_out[q * 32 + c] = z;
-          hv[c] = __float2bfloat16_rn(gelu_exact(z));
+    for (int sl = 0; sl < CV_MAX_STAGES; ++sl)
+      zero16_slot[sl] = (tc::smem_u32(sZero) - (sA_addr + sl * stage_bytes + (uint32_t)(g.PX + 1) * 16u)) >> 4;
+    bool ok = __all_sync(0xffffffffu, cv_wait(bbar, 0, abort_flag));
+    b_waited = ok;
+    for (int j = 0; ok && j < nt; ++j) {
+      const int slot = j % stages, a = j & 1;
+      ok = __all_sync(0xffffffffu, cv_wait(&full[slot], (uint32_t)(j / stages) & 1u, abort_flag));
+      if (ok && j >= 2)
+        ok = __all_sync(0xffffffffu, cv_wait(&acce[a], (uint32_t)((j >> 1) - 1) & 1u, abort_flag));
+      if (!ok) break;
+      __syncwarp();
+      tc::tc_fence_after();
+      const uint32_t acc = tmem + (uint32_t)a * NOUT;
+      const uint32_t zero16 = zero16_slot[slot == 0 ? 0 : (slot == 1 ? 1 : 2)];
+      // Descriptor of the slot's window origin (output row 0 of plane dz = 0, PX + 1 rows in);
+      // every K step adds its tap's offset (and, for C = 8, its LBO) to the low word, in 16-byte
+      // units: start-address field bits 0..13, LBO field bits 16..29, both without carry.
+      const uint64_t d0 = tc::smem_desc(sA_addr + slot * stage_bytes + (uint32_t)(g.PX + 1) * 16u,
+                                        CIN == 32 ? win_bytes : 0u, 128);
+      const uint32_t d0_lo = (uint32_t)d0, d0_hi = (uint32_t)(d0 >> 32);
+      const uint32_t b0_lo = (uint32_t)bdesc0, b0_hi = (uint32_t)(bdesc0 >> 32);
+#pragma unroll
+      for (int s = 0; s < KSTEPS; ++s) {
+        const int t = CIN == 32 ? (s >> 1) : 2 * s;
+        uint32_t off = (uint32_t)((t / 9) * G) * win16 + (uint32_t)(((t / 3) % 3 - 1) * px16 + (t % 3 - 1));
+        if (CIN == 32) {
+          off += (uint32_t)((s & 1) * 2) * win16;
+        } else {
+          const int t1 = t + 1;
+          uint32_t lbo16;
+          if (t1 < 27) {
+            lbo16 = (uint32_t)((t1 / 9) * G) * win16 +
+                    (uint32_t)(((t1 / 3) % 3 - 1) * px16 + (t1 % 3 - 1)) - off;
+          } else {
+            lbo16 = zero16 - off;
+          }
+          off += lbo16 << 16;
         }
-        uint4* dst = reinterpret_cast<uint4*>(p.out_bf16 + q * 32);
-#pragma unroll
-        for (int v4 = 0; v4 < 4; ++v4) dst[v4] = reinterpret_cast<const uint4*>(hv)[v4];
-      } else if (MODE == CONV_GELU_GRAD) {
-        __align__(16) __nv_bfloat16 hv[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) hv[c] = __float2bfloat16_rn(acc[c] * gelu_grad(__ldg(p.z_in + q * 32 + c)));
-        uint4* dst = reinterpret_cast<uint4*>(p.out_bf16 + q * 32);
-#pragma unroll
-        for (int v4 = 0; v4 < 4; ++v4) dst[v4] = reinterpret_cast<const uint4*>(hv)[v4];
-      } else {
-        for (int c = 0; c < p.n_real; ++c)
-          p.out_f32[(long long)c * ncell + q] = acc[c] + (p.bias ? __ldg(p.bias + c) : 0.0f);
+        const uint64_t adesc = ((uint64_t)d0_hi << 32) | (uint64_t)(d0_lo + off);
+        const uint64_t bdesc = ((uint64_t)b0_hi << 32) | (uint64_t)(b0_lo + (uint32_t)(s * 16));
+        tc::mma_bf16_elect(acc, adesc, bdesc, idesc, s > 0 ? 1u : 0u);
       }
-    } else {
+      tc::mma_commit_elect(&empty[slot]);
+      tc::mma_commit_elect(&accf[a]);
+    }
+  } else {
+    // epilogue: warp w reads TMEM lane quarter w % 4 and output columns [16 h, 16 h + 16)
+    const int q = warp & 3;
+    const int hcol = (warp - 2) >> 2;
+    const int trow = q * 32 + lane;        // tile row = TMEM lane
+    const bool cols = 16 * hcol < NOUT;    // this warp has columns to read
+    for (int j = 0; j < nt; ++j) {
+      const int a = j & 1;
+      if (!__all_sync(0xffffffffu, cv_wait(&accf[a], (uint32_t)(j >> 1) & 1u, abort_flag))) break;
+      __syncwarp();   // tcgen05.ld below is warp-collective
+      tc::tc_fence_after();
       float acc[16];
-      tc::tmem_ld_32x32b_x16(taddr, acc);
-      tc::tmem_ld_wait();
-      for (int c = 0; c < p.n_real && c < 16; ++c)
-        p.out_f32[(long long)c * ncell + q] = acc[c] + (p.bias ? __ldg(p.bias + c) : 0.0f);
+      if (cols) {
+        tc::tmem_ld_32x32b_x16(tmem + (uint32_t)(a * NOUT + 16 * hcol) + ((uint32_t)(q * 32) << 16), acc);
+        tc::tmem_ld_wait();
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce[a]);   // the accumulator may be overwritten now
+      if (!cols) continue;
+
+      // padded row of this thread (fits 32 bits: the launcher rejects larger volumes)
+      const uint32_t rho = (uint32_t)g.PXY + 128u * (blockIdx.x + (uint32_t)j * gridDim.x) + trow;
+      const uint32_t pz = rho / (uint32_t)g.PXY;
+      const uint32_t rem = rho - pz * (uint32_t)g.PXY;
+      const int py = (int)(rem / (uint32_t)g.PX), px = (int)(rem - (uint32_t)py * (uint32_t)g.PX);
+      if (!(px >= 1 && px <= g.nx && py >= 1 && py <= g.ny && (int)pz <= g.nz)) continue;   // halo row
+      const int x = px - 1, y = py - 1, z = (int)pz - 1;
+      const long long qc = ((long long)z * g.ny + y) * g.nx + x;
+      const int c0 = 16 * hcol;
+      if (MODE == CONV_LINEAR) {
+        for (int c = 0; c < 16 && c0 + c < p.n_real; ++c)
+          p.out_f32[(long long)(c0 + c) * ncell + qc] = acc[c] + (p.bias ? __ldg(p.bias + c0 + c) : 0.0f);
+      } else {
+        float hv[16];   // values to round to bf16
+        if (MODE == CONV_GELU) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const float zv = acc[c] + (p.bias ? __ldg(p.bias + c0 + c) : 0.0f);
+            acc[c] = zv;
+            hv[c] = gelu_exact(zv);
+          }
+          if (p.z_out) {
+            float4* zo = reinterpret_cast<float4*>(p.z_out + qc * 32 + c0);
+#pragma unroll
+            for (int v4 = 0; v4 < 4; ++v4)
+              zo[v4] = make_float4(acc[4 * v4], acc[4 * v4 + 1], acc[4 * v4 + 2], acc[4 * v4 + 3]);
+          }
+        } else {
+          const float4* zi = reinterpret_cast<const float4*>(p.z_in + qc * 32 + c0);
+#pragma unroll
+          for (int v4 = 0; v4 < 4; ++v4) {
+            const float4 zz = __ldg(zi + v4);
+            hv[4 * v4] = acc[4 * v4] * gelu_grad(zz.x);
+            hv[4 * v4 + 1] = acc[4 * v4 + 1] * gelu_grad(zz.y);
+            hv[4 * v4 + 2] = acc[4 * v4 + 2] * gelu_grad(zz.z);
+            hv[4 * v4 + 3] = acc[4 * v4 + 3] * gelu_grad(zz.w);
+          }
+        }
+        uint4* out = reinterpret_cast<uint4*>(p.out_bf16);
+#pragma unroll
+        for (int cg = 0; cg < 2; ++cg)
+          store_with_images(out + (long long)(2 * hcol + cg) * g.rows, g, x, y, z,
+                            make_uint4(pack_bf16x2(hv[8 * cg], hv[8 * cg + 1]),
+                                       pack_bf16x2(hv[8 * cg + 2], hv[8 * cg + 3]),
+                                       pack_bf16x2(hv[8 * cg + 4], hv[8 * cg + 5]),
+                                       pack_bf16x2(hv[8 * cg + 6], hv[8 * cg + 7])));
+      }
     }
-    tc::tc_fence_before();
-    __syncthreads();
   }
 
-  // drain: every MMA issued must be complete before the accumulator is released.  Normally
-  // the last tile's completion was awaited above; after an abort, commit once more and give the
-  // tensor cores a bounded wait before freeing TMEM.
-  if (s_abort) {
-    if (tid == 0) {
-      atomicOr(p.err, 1u);
-      tc::mma_commit(bar_done);
-    }
-    tc::mbar_wait(bar_done, done_phase, CV_WAIT_ITERS);
-  }
+  // All roles are done.  After an abort, every MMA issued and every copy in flight must land
+  // before TMEM and shared memory are released; the waits stay bounded.
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  const bool aborted = s_abort != 0;
+  if (aborted) {
+    if (tid == 0) atomicOr(p.err, 1u);
+    if (warp == 1) {
+      tc::mma_commit_elect(drain);
+      tc::mbar_wait(drain, 0, CV_WAIT_ITERS);
+    }
+    if (warp == 0 && lane == 0) {
+      const int first = tma_issued > stages ? tma_issued - stages : 0;
+      for (int jj = first; jj < tma_issued; ++jj)
+        tc::mbar_wait(&full[jj % stages], (uint32_t)(jj / stages) & 1u, CV_WAIT_ITERS);
+      tc::mbar_wait(bbar, 0, CV_WAIT_ITERS);
+    }
+  }
+  (void)b_waited;
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, TMEM_COLS);
+    tc::tmem_dealloc(tmem, S::TMEM_COLS);
   }
 }
 
 template <int CIN, int NOUT, int MODE>
-static cudaError_t launch_conv(const ConvArgs& a, int max_ctas, cudaStream_t s) {
-  constexpr int K = CIN == 32 ? 27 * 32 : 28 * 8;
-  const size_t smem = (size_t)NOUT * K * 2 + CV_STAGES * CV_STAGE_BYTES + 8 * (CV_STAGES + 1) + 16;
-  cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<CIN, NOUT, MODE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static cudaError_t launch_conv(const ConvArgs& a, const ConvGeom& g, cudaStream_t s) {
+  using S = ConvShape<CIN, NOUT>;
+  if (g.rows >= (1LL << 31)) return cudaErrorInvalidValue;   // padded rows are 32-bit indices
+  int stages = CV_MAX_STAGES;
+  while (stages >= 2 && S::smem_bytes(g, stages) > (size_t)CV_SMEM_MAX) --stages;
+  if (stages < 2) return cudaErrorInvalidValue;
+  const size_t smem = S::smem_bytes(g, stages);
+  auto kern = conv3d_tc_kernel<CIN, NOUT, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long ncell = (long long)a.nx * a.ny * a.nz;
-  int ntiles = (int)(ncell / 128);
-  int grid = ntiles < max_ctas ? ntiles : max_ctas;
-  if (grid < 1) grid = 1;
-  conv3d_tc_kernel<CIN, NOUT, MODE><<<grid, CV_THREADS, smem, s>>>(a);
+  int dev = 0, sms = 148, occ = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, CV_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  if (occ * (int)S::TMEM_COLS > 512) occ = 512 / (int)S::TMEM_COLS;   // TMEM per SM
+  long long grid = (long long)sms * occ;
+  if (grid > g.ntiles) grid = g.ntiles;
+  kern<<<(unsigned)grid, CV_THREADS, smem, s>>>(a, g, stages);
   return cudaGetLastError();
 }
 
@@ -276,16 +387,84 @@ extern "C" dh_status dh_pack_conv_weights(const float* W, int cout, int cin, int
   return DH_OK;
 }
 
+namespace dh {
+
+// ---------------------------------------------------------------------------------------------
+// Layout conversion between channel-last [cell][C] bf16 and the padded layout.
+__global__ void pad_kernel(const __nv_bfloat16* __restrict__ src, int C, ConvGeom g,
+                           __nv_bfloat16* __restrict__ dst) {
+  const long long ncell = (long long)g.nx * g.ny * g.nz;
+  const int G = C / 8;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell * G;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long q = i / G;
+    const int cg = (int)(i - q * G);
+    const int x = (int)(q % g.nx);
+    const long long t = q / g.nx;
+    const int y = (int)(t % g.ny), z = (int)(t / g.ny);
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + q * C + cg * 8));
+    store_with_images(reinterpret_cast<uint4*>(dst) + (long long)cg * g.rows, g, x, y, z, v);
+  }
+}
+
+__global__ void unpad_kernel(const __nv_bfloat16* __restrict__ src, int C, ConvGeom g,
+                             __nv_bfloat16* __restrict__ dst) {
+  const long long ncell = (long long)g.nx * g.ny * g.nz;
+  const int G = C / 8;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell * G;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long q = i / G;
+    const int cg = (int)(i - q * G);
+    const int x = (int)(q % g.nx);
+    const long long t = q / g.nx;
+    const int y = (int)(t % g.ny), z = (int)(t / g.ny);
+    reinterpret_cast<uint4*>(dst + q * C)[cg] =
+        __ldg(reinterpret_cast<const uint4*>(src) + (long long)cg * g.rows + pad_row(g, x, y, z));
+  }
+}
+
+static bool conv_dims_ok(int nx, int ny, int nz) { return nx >= 3 && ny >= 3 && nz >= 3; }
+
+}  // namespace dh
+
+using namespace dh;
+
+extern "C" long long dh_conv_padded_rows(int nx, int ny, int nz) {
+  if (!conv_dims_ok(nx, ny, nz)) return -1;
+  return conv_geom(nx, ny, nz).rows;
+}
+
+extern "C" dh_status dh_conv_pad(const void* src, int channels, int nx, int ny, int nz, void* dst,
+                                 void* stream) {
+  if (!src || !dst || (channels != 8 && channels != 32) || !conv_dims_ok(nx, ny, nz)) return DH_ERR_ARG;
+  pad_kernel<<<148 * 4, 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)src, channels,
+                                                       conv_geom(nx, ny, nz), (__nv_bfloat16*)dst);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
+  return DH_OK;
+}
+
+extern "C" dh_status dh_conv_unpad(const void* src, int channels, int nx, int ny, int nz, void* dst,
+                                   void* stream) {
+  if (!src || !dst || (channels != 8 && channels != 32) || !conv_dims_ok(nx, ny, nz)) return DH_ERR_ARG;
+  unpad_kernel<<<148 * 4, 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)src, channels,
+                                                         conv_geom(nx, ny, nz), (__nv_bfloat16*)dst);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
+  return DH_OK;
+}
+
 extern "C" dh_status dh_conv3d_bf16(const void* act, int cin_pad, const void* packed, int nout_pad,
                                     const float* bias, int mode, const float* z_in, void* out,
                                     float* z_out, int n_real, int nx, int ny, int nz,
                                     unsigned* err_flag, void* stream) {
   if (!act || !packed || !out || !err_flag) return DH_ERR_ARG;
-  const long long ncell = (long long)nx * ny * nz;
-  if (nx < 3 || ny < 3 || nz < 3 || ncell % 128 != 0) {
-    dh_set_global_error("dh_conv3d_bf16: needs every dimension >= 3 and nx*ny*nz divisible by 128");
+  if (!conv_dims_ok(nx, ny, nz)) {
+    dh_set_global_error("dh_conv3d_bf16: every dimension must be >= 3");
     return DH_ERR_ARG;
   }
+  if (mode == CONV_GELU_GRAD && !z_in) return DH_ERR_ARG;
+  const ConvGeom g = conv_geom(nx, ny, nz);
   ConvArgs a;
   a.act = (const __nv_bfloat16*)act;
   a.wpk = (const __nv_bfloat16*)packed;
@@ -295,22 +474,21 @@ extern "C" dh_status dh_conv3d_bf16(const void* act, int cin_pad, const void* pa
   a.out_f32 = (float*)out;
   a.z_out = z_out;
   a.n_real = n_real;
-  a.nx = nx; a.ny = ny; a.nz = nz;
   a.err = err_flag;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int max_ctas = 2 * sms;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaErrorInvalidValue;
-  if (cin_pad == 8 && nout_pad == 32 && mode == CONV_GELU) e = launch_conv<8, 32, CONV_GELU>(a, max_ctas, s);
-  else if (cin_pad == 8 && nout_pad == 32 && mode == CONV_GELU_GRAD) e = launch_conv<8, 32, CONV_GELU_GRAD>(a, max_ctas, s);
-  else if (cin_pad == 32 && nout_pad == 32 && mode == CONV_GELU) e = launch_conv<32, 32, CONV_GELU>(a, max_ctas, s);
-  else if (cin_pad == 32 && nout_pad == 32 && mode == CONV_GELU_GRAD) e = launch_conv<32, 32, CONV_GELU_GRAD>(a, max_ctas, s);
-  else if (cin_pad == 32 && nout_pad == 16 && mode == CONV_LINEAR) e = launch_conv<32, 16, CONV_LINEAR>(a, max_ctas, s);
-  else if (cin_pad == 32 && nout_pad == 32 && mode == CONV_LINEAR) e = launch_conv<32, 32, CONV_LINEAR>(a, max_ctas, s);
+  cudaError_t e = cudaErrorNotSupported;
+  if (cin_pad == 8 && nout_pad == 32 && mode == CONV_GELU) e = launch_conv<8, 32, CONV_GELU>(a, g, s);
+  else if (cin_pad == 8 && nout_pad == 32 && mode == CONV_GELU_GRAD) e = launch_conv<8, 32, CONV_GELU_GRAD>(a, g, s);
+  else if (cin_pad == 32 && nout_pad == 32 && mode == CONV_GELU) e = launch_conv<32, 32, CONV_GELU>(a, g, s);
+  else if (cin_pad == 32 && nout_pad == 32 && mode == CONV_GELU_GRAD) e = launch_conv<32, 32, CONV_GELU_GRAD>(a, g, s);
+  else if (cin_pad == 32 && nout_pad == 16 && mode == CONV_LINEAR && n_real >= 1 && n_real <= 16) e = launch_conv<32, 16, CONV_LINEAR>(a, g, s);
+  else if (cin_pad == 32 && nout_pad == 32 && mode == CONV_LINEAR && n_real >= 1 && n_real <= 32) e = launch_conv<32, 32, CONV_LINEAR>(a, g, s);
   else {
-    dh_set_global_error("dh_conv3d_bf16: unsupported (cin_pad, nout_pad, mode) combination");
+    dh_set_global_error("dh_conv3d_bf16: unsupported (cin_pad, nout_pad, mode, n_real) combination");
+    return DH_ERR_ARG;
+  }
+  if (e == cudaErrorInvalidValue) {
+    dh_set_global_error("dh_conv3d_bf16: the x extent is too large for two shared-memory windows");
     return DH_ERR_ARG;
   }
   if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
@@ -321,7 +499,8 @@ extern "C" dh_status dh_conv3d_bf16(const void* act, int cin_pad, const void* pa
 // Weight gradient: dW[n][c][tap] = sum_cells g[cell][n] * act[cell + offset(tap)][c], a GEMM
 // with M = (tap, c) rows (27 * CIN, in tiles of 128), N = n, K = cells.  Each CTA reduces a
 // contiguous range of cells in 16-cell K steps: the threads gather, for every tap, the 16
-// neighbour rows and transpose them into K-major core matrices (a row holds one (tap, c) over
+// neighbour rows (read from the padded layout, where a tap is a row offset) and transpose them
+// into K-major core matrices (a row holds one (tap, c) over
 // 16 consecutive cells), the gradient rows likewise; one thread issues one MMA per M tile into
 // its own TMEM accumulator.  Per-CTA partial sums go to global memory and a second kernel adds
 // them in a fixed order.
@@ -345,9 +524,9 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + WG_STAGES * STAGE);
   uint64_t* bar_done = bars + WG_STAGES;
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar_done + 1);
-  __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5;
+  const ConvGeom geo = conv_geom(nx, ny, nz);
   const long long ncell = (long long)nx * ny * nz;
   const long long c0 = (long long)blockIdx.x * cells_per_cta;
   const long long c1 = c0 + cells_per_cta < ncell ? c0 + cells_per_cta : ncell;
@@ -360,7 +539,6 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
     for (int b = 0; b < WG_STAGES; ++b) tc::mbar_init(&bars[b], 1);
     tc::mbar_init(bar_done, 1);
     tc::mbar_fence_init();
-    s_abort = 0;
   }
   if (warp == 0) {
     tc::tmem_alloc(s_tmem, TMEM_COLS);
@@ -374,11 +552,13 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
   const uint32_t idesc = tc::idesc_bf16_f32(128, NOUT);
   const uint32_t s_addr = tc::smem_u32(smem);
   uint32_t phase_bits = 0;
+  int my_abort = 0;      // this thread saw a bounded wait give up
+  bool aborted = false;  // some thread did (agreed at a barrier)
 
   for (int s = 0; s < ksteps; ++s) {
     const int b = s % WG_STAGES;
     if (s >= WG_STAGES) {
-      if (!tc::mbar_wait(&bars[b], (phase_bits >> b) & 1u, CV_WAIT_ITERS)) s_abort = 1;
+      if (!tc::mbar_wait(&bars[b], (phase_bits >> b) & 1u, CV_WAIT_ITERS)) my_abort = 1;
       phase_bits ^= 1u << b;
     }
     unsigned char* st = smem + b * STAGE;
@@ -395,8 +575,8 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
         const long long t1 = x / nx;
         const int j = (int)(t1 % ny), kz = (int)(t1 / ny);
         const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const long long nq = ((long long)wrap(kz + dz, nz) * ny + wrap(j + dy, ny)) * nx + wrap(i + dx, nx);
-        *reinterpret_cast<uint4*>(v) = __ldg(reinterpret_cast<const uint4*>(act + nq * CIN + cg * 8));
+        *reinterpret_cast<uint4*>(v) = __ldg(reinterpret_cast<const uint4*>(act) + cg * geo.rows +
+                                             pad_row(geo, i + dx, j + dy, kz + dz));
       } else {
         *reinterpret_cast<uint4*>(v) = make_uint4(0u, 0u, 0u, 0u);
       }
@@ -413,8 +593,13 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
       const int k = it & 15, ng = it >> 4;
       const long long x = x0 + k;
       __align__(16) __nv_bfloat16 v[8];
-      if (x < c1 && ng * 8 < g_stride)
-        *reinterpret_cast<uint4*>(v) = __ldg(reinterpret_cast<const uint4*>(g + x * g_stride + ng * 8));
+      if (x < c1 && ng * 8 < g_stride) {
+        const int i = (int)(x % nx);
+        const long long t1 = x / nx;
+        const int j = (int)(t1 % ny), kz = (int)(t1 / ny);
+        *reinterpret_cast<uint4*>(v) =
+            __ldg(reinterpret_cast<const uint4*>(g) + ng * geo.rows + pad_row(geo, i, j, kz));
+      }
       else
         *reinterpret_cast<uint4*>(v) = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
@@ -425,8 +610,7 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
       }
     }
     tc::fence_async_smem();
-    __syncthreads();
-    if (s_abort) break;
+    if (__syncthreads_or(my_abort)) { aborted = true; break; }
     if (tid == 0) {
       tc::tc_fence_after();
       const uint32_t base = s_addr + b * STAGE;
@@ -440,12 +624,10 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
       if (s == ksteps - 1) tc::mma_commit(bar_done);
     }
   }
-  bool have = ksteps > 0 && !s_abort;
-  if (have) {
-    if (!tc::mbar_wait(bar_done, 0, CV_WAIT_ITERS)) { s_abort = 1; have = false; }
-  }
-  __syncthreads();
-  if (s_abort) have = false;
+  int done_fail = 0;
+  if (ksteps > 0 && !aborted && !tc::mbar_wait(bar_done, 0, CV_WAIT_ITERS)) done_fail = 1;
+  if (__syncthreads_or(done_fail)) aborted = true;
+  const bool have = ksteps > 0 && !aborted;
   tc::tc_fence_after();
   // epilogue: partial[cta][m][n]
   float* out = partial + (long long)blockIdx.x * MT * 128 * NOUT;
@@ -468,12 +650,13 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
       for (int n = 0; n < NOUT; ++n) out[(long long)m * NOUT + n] = 0.0f;
     }
   }
-  if (s_abort) {
+  if (aborted) {
+    // phase 0 of bar_done completes once every MMA issued so far has completed
     if (tid == 0) {
       atomicOr(err, 1u);
       tc::mma_commit(bar_done);
     }
-    tc::mbar_wait(bar_done, ksteps > 0 ? 1u : 0u, CV_WAIT_ITERS);
+    tc::mbar_wait(bar_done, 0, CV_WAIT_ITERS);
   }
   tc::tc_fence_before();
   __syncthreads();

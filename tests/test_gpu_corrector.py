@@ -29,41 +29,71 @@ def _pack(W, transpose_flip):
     return packed
 
 
-def _conv(act, cin_pad, packed, nout_pad, bias, mode, shape, z_in=None, n_real=32):
+def _rows(shape):
+    nz, ny, nx = shape
+    return int(_lib.load().dh_conv_padded_rows(nx, ny, nz))
+
+
+def _padded_empty(cpad, shape):
+    """Zeroed bf16 buffer of the padded layout (guard rows must read zero)."""
+    return torch.zeros(cpad // 8 * _rows(shape) * 8, dtype=torch.bfloat16, device="cuda")
+
+
+def _unpad(buf, cpad, shape):
+    nz, ny, nx = shape
+    out = torch.empty(nx * ny * nz, cpad, dtype=torch.bfloat16, device="cuda")
+    assert _lib.load().dh_conv_unpad(_ptr(buf), cpad, nx, ny, nz, _ptr(out), None) == 0
+    torch.cuda.synchronize()
+    return out
+
+
+def _conv(act, cin_pad, packed, nout_pad, bias, mode, shape, z_in=None, n_real=32, keep=None):
+    """act: padded layout.  Returns (out, z_out) with bf16 outputs unpadded to [cell][32];
+    keep (a list) receives the padded output buffer."""
     lib = _lib.load()
     nz, ny, nx = shape
     ncell = nx * ny * nz
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     z_out = None
     if mode == 0:
-        out = torch.empty(ncell, 32, dtype=torch.bfloat16, device="cuda")
+        out = _padded_empty(32, shape)
         z_out = torch.empty(ncell, 32, dtype=torch.float32, device="cuda")
     elif mode == 1:
         out = torch.empty(n_real, ncell, dtype=torch.float32, device="cuda")
     else:
-        out = torch.empty(ncell, 32, dtype=torch.bfloat16, device="cuda")
+        out = _padded_empty(32, shape)
     b = bias.float().contiguous().cuda() if bias is not None else None
     st = lib.dh_conv3d_bf16(_ptr(act), cin_pad, _ptr(packed), nout_pad, _ptr(b), mode, _ptr(z_in),
                             _ptr(out), _ptr(z_out), n_real, nx, ny, nz, _ptr(err), None)
     assert st == 0, lib.dh_last_error(None)
     torch.cuda.synchronize()
     assert int(err.item()) == 0, "bounded wait gave up"
+    if keep is not None:
+        keep.append(out)
+    if mode != 1:
+        out = _unpad(out, 32, shape)
     return out, z_out
 
 
 def _act(x, cpad):
-    """(c, nz, ny, nx) float64 -> bf16 channel-last [cell][cpad] on the GPU."""
+    """(c, nz, ny, nx) float64 -> bf16 padded layout with cpad channels on the GPU."""
     c = x.shape[0]
+    shape = tuple(x.shape[1:])
+    nz, ny, nx = shape
     flat = torch.zeros(x[0].numel(), cpad, dtype=torch.float64)
     flat[:, :c] = x.reshape(c, -1).t()
-    return flat.to(torch.bfloat16).cuda().contiguous()
+    cl = flat.to(torch.bfloat16).cuda().contiguous()
+    buf = _padded_empty(cpad, shape)
+    assert _lib.load().dh_conv_pad(_ptr(cl), cpad, nx, ny, nz, _ptr(buf), None) == 0
+    torch.cuda.synchronize()
+    return buf
 
 
 def _planar(a, c, shape):
     return a.float().cpu().double()[:, :c].t().reshape((c,) + shape)
 
 
-SHAPES = [(8, 16, 16), (16, 8, 32), (64, 64, 64)]
+SHAPES = [(8, 16, 16), (16, 8, 32), (5, 7, 9), (64, 64, 64)]   # (5, 7, 9): 315 cells, ragged tiles
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -93,7 +123,46 @@ def test_hidden_layer_32_to_32_gelu(shape):
     assert float((zg - zr).abs().max() / zr.abs().max()) < 1e-5
 
 
-@pytest.mark.parametrize("shape", SHAPES[:2])
+def test_padded_output_layout_images_and_guards():
+    """The GELU output in the padded layout: every halo row equals the periodic image it
+    stands for, and the guard rows stay zero."""
+    shape = (5, 7, 9)
+    nz, ny, nx = shape
+    g = torch.Generator().manual_seed(11)
+    x = oc.bf16(torch.randn((32,) + shape, generator=g, dtype=torch.float64))
+    W = torch.randn(32, 32, 3, 3, 3, generator=g, dtype=torch.float64) * 0.05
+    keep = []
+    out, _ = _conv(_act(x, 32), 32, _pack(W, 0), 32, None, 0, shape, keep=keep)
+    R = _rows(shape)
+    buf = keep[0].float().cpu().reshape(4, R, 8)
+    PX, PY, PZ = nx + 2, ny + 2, nz + 2
+    guard = (R - PX * PY * PZ) // 2
+    assert torch.count_nonzero(buf[:, :guard]) == 0 and torch.count_nonzero(buf[:, guard + PX * PY * PZ:]) == 0
+    vol = buf[:, guard:guard + PX * PY * PZ].reshape(4, PZ, PY, PX, 8)
+    cells = out.float().cpu().reshape(nz, ny, nx, 4, 8).permute(3, 0, 1, 2, 4)
+    idx = lambda n: torch.tensor([(i - 1) % n for i in range(n + 2)])
+    expect = cells[:, idx(nz)][:, :, idx(ny)][:, :, :, idx(nx)]
+    assert torch.equal(vol, expect)
+
+
+def test_periodic_shift_equivariance_is_bitwise():
+    """Each output row is computed by the same sequence of MMAs wherever its tile falls, so a
+    periodic shift of the input shifts the output bit for bit."""
+    shape = (8, 16, 16)
+    g = torch.Generator().manual_seed(12)
+    x = oc.bf16(torch.randn((32,) + shape, generator=g, dtype=torch.float64))
+    W = torch.randn(32, 32, 3, 3, 3, generator=g, dtype=torch.float64) * 0.05
+    b = torch.randn(32, generator=g, dtype=torch.float64) * 0.1
+    pk = _pack(W, 0)
+    _, z0 = _conv(_act(x, 32), 32, pk, 32, b, 0, shape)
+    shift = (3, 5, 7)
+    _, z1 = _conv(_act(torch.roll(x, shift, dims=(1, 2, 3)), 32), 32, pk, 32, b, 0, shape)
+    a = _planar(z0, 32, shape)
+    c = _planar(z1, 32, shape)
+    assert torch.equal(torch.roll(a, shift, dims=(1, 2, 3)), c)
+
+
+@pytest.mark.parametrize("shape", SHAPES[:3])
 def test_output_layer_32_to_5_linear(shape):
     g = torch.Generator().manual_seed(2)
     x = oc.bf16(torch.randn((32,) + shape, generator=g, dtype=torch.float64))
@@ -105,7 +174,7 @@ def test_output_layer_32_to_5_linear(shape):
     assert float((yg - yr).abs().max() / yr.abs().max()) < 1e-5
 
 
-@pytest.mark.parametrize("shape", SHAPES[:2])
+@pytest.mark.parametrize("shape", SHAPES[:3])
 def test_data_gradient_through_gelu(shape):
     """dz_prev = conv^T(dz, W) * gelu'(z_prev), the backward step between hidden layers."""
     g = torch.Generator().manual_seed(3)
@@ -155,7 +224,8 @@ def _wgrad(x, gr, cin_pad, g_stride, cout, shape):
 
 
 @pytest.mark.parametrize("cin,cout,shape", [(5, 32, (8, 16, 16)), (32, 32, (8, 16, 16)),
-                                            (32, 5, (16, 8, 32)), (32, 32, (64, 64, 64))])
+                                            (32, 5, (16, 8, 32)), (32, 32, (5, 7, 9)),
+                                            (32, 32, (64, 64, 64))])
 def test_weight_gradient(cin, cout, shape):
     g = torch.Generator().manual_seed(5)
     x = oc.bf16(torch.randn((cin,) + shape, generator=g, dtype=torch.float64))
