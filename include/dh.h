@@ -106,6 +106,17 @@ dh_status dh_advance(dh_ctx* ctx, int n_steps, double* t_out);
 /* Time and completed step count of the current state. */
 dh_status dh_get_time(dh_ctx* ctx, double* t, long long* nstep);
 
+/* File checkpoint of the context (the restart the paper's pure update H(U^n, theta^n) of
+   Sec. 2.1 implies: theta = time, step count, OU table, gravity warm start).  dh_save writes
+   the current state, t, dt, the step count (which also numbers the OU draws), the OU tables
+   and hold flag, and with gravity the float64 potential that warm-starts the next solve, with a
+   checksum; it settles pending steps first.  dh_load reads such a file into a context created
+   with the same grid, precision, physics switches, OU seed, gamma and cell widths (else
+   DH_ERR_ARG, context unchanged), after which stepping continues bit for bit as in the saved
+   context.  DH_ERR_ARG for unreadable, truncated or corrupted files.  Both synchronise. */
+dh_status dh_save(dh_ctx* ctx, const char* path);
+dh_status dh_load(dh_ctx* ctx, const char* path);
+
 /* CFL time step C * min_cells,axes dx_a / (|v_a| + c_s) of the current state (App. A.4). */
 dh_status dh_compute_dt(dh_ctx* ctx, double* dt);
 

@@ -52,6 +52,8 @@ _SIGNATURES = {
     "dh_solve_poisson": (C.c_int, [_P, _P, C.c_int]),
     "dh_adjoint_advance": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dh_conserved_totals_static": (C.c_int, [_P, C.c_int, C.c_longlong, _P, _P]),
+    "dh_save": (C.c_int, [_P, C.c_char_p]),
+    "dh_load": (C.c_int, [_P, C.c_char_p]),
     "dh_conv_padded_rows": (C.c_longlong, [C.c_int, C.c_int, C.c_int]),
     "dh_conv_pad": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "dh_conv_unpad": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),

@@ -160,57 +160,97 @@ def _rel_l2(U: torch.Tensor, R: torch.Tensor) -> float:
                      for c in range(5)) / 5.0)
 
 
-def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seed: int = 200,
-             equal_time_substeps: int = 0):
-    """Corrected and uncorrected coarse runs against the downsampled fine run, same forcing.
-
-    Returns per-step relative L2 errors and the GPU time per coarse step of each run.  With
-    equal_time_substeps > 1 a third run, uncorrected, takes that many substeps per coarse step
-    (the uncorrected solver given the corrected run's GPU time as a smaller time step).
-    """
-    n, nc = setup.fine, setup.coarse
-    fine = Solver(_cfg(n, setup, seed))
-    fine.init_state(torch.from_numpy(inputs.cooling_box((n, n, n))).float().cuda().contiguous())
-    fine.advance(setup.spinup_steps)
-    U0 = downsample(fine.get_state(), setup.factor)
-    plain = Solver(_cfg(nc, setup, seed))
-    corr = Solver(_cfg(nc, setup, seed))
-    plain.init_state(U0)
-    corr.init_state(U0)
-    mu, sigma, out = norm
+def _set_corrector(solver: Solver, params, norm):
     import ctypes as C
+    mu, sigma, out = norm
     normbuf = (C.c_float * 15)(*[float(v) for v in list(mu) + list(sigma) + list(out)])
     p = params.detach().float().cuda().contiguous()
-    _lib.check(_lib.load().dh_set_corrector(corr.ctx, C.c_void_p(p.data_ptr()), normbuf), corr.ctx)
-    runs = {"uncorrected": plain, "corrected": corr}
-    if equal_time_substeps > 1:
-        eq = Solver(_cfg(nc, setup, seed))
-        eq.init_state(U0)
-        runs["uncorrected_equal_gpu_time"] = eq
-    err = {k: [] for k in runs}
-    gpu_ms = {k: 0.0 for k in runs}
+    _lib.check(_lib.load().dh_set_corrector(solver.ctx, C.c_void_p(p.data_ptr()), normbuf), solver.ctx)
+
+
+def _timed(fn) -> float:
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for k in range(steps):
-        dt_c = plain.compute_dt()
-        modes = fine_interval(fine, dt_c, setup.forcing)
-        for s in runs.values():
-            if modes is not None:
-                s.set_forcing_modes(modes, hold=True)
-        for name, s in runs.items():
-            ev0.record()
-            if name == "uncorrected_equal_gpu_time":
-                for _ in range(equal_time_substeps):
-                    s.step(dt_c / equal_time_substeps, sync=False)
-            else:
-                s.step(dt_c, sync=False)
-            if name == "corrected":
-                _lib.check(_lib.load().dh_correct(s.ctx), s.ctx)
-            ev1.record()
-            ev1.synchronize()
-            gpu_ms[name] += ev0.elapsed_time(ev1)
-        ref = downsample(fine.get_state(), setup.factor)
-        for name, s in runs.items():
-            err[name].append(_rel_l2(s.get_state(), ref))
-    for s in list(runs.values()) + [fine]:
-        s.close()
-    return err, {k: v / steps for k, v in gpu_ms.items()}
+    ev0.record()
+    fn()
+    ev1.record()
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def equal_time_substeps(setup: ClosureSetup, params, norm, U0: torch.Tensor, probes: int = 10) -> int:
+    """Substeps that give the uncorrected coarse run the GPU time of one corrected coarse step:
+    round(t_corrected / t_uncorrected), measured on scratch runs from U0."""
+    nc = setup.coarse
+    plain = Solver(_cfg(nc, setup, 0))
+    corr = Solver(_cfg(nc, setup, 0))
+    plain.init_state(U0)
+    corr.init_state(U0)
+    _set_corrector(corr, params, norm)
+    lib = _lib.load()
+    tp = tc = 0.0
+    for k in range(probes + 2):
+        dt = plain.compute_dt()
+        a = _timed(lambda: plain.step(dt, sync=False))
+        b = _timed(lambda: (corr.step(dt, sync=False), _lib.check(lib.dh_correct(corr.ctx), corr.ctx)))
+        if k >= 2:            # the first steps warm up the kernels
+            tp += a
+            tc += b
+    plain.close()
+    corr.close()
+    return max(1, int(round(tc / tp)))
+
+
+def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
+             equal_time_substeps_n="auto"):
+    """Corrected and uncorrected coarse runs against the downsampled fine run, same forcing.
+
+    For every held-out seed, a fine run is spun up and downsampled; coarse runs start from that
+    state and advance one coarse step per fine interval (the table of the interval held, as in
+    make_pairs).  A third run, uncorrected, takes `equal_time_substeps_n` substeps per coarse
+    step: the uncorrected solver given the corrected run's GPU time as a smaller time step
+    ("auto": from the measured cost ratio).  Returns (per-step relative L2 errors averaged over
+    the seeds, GPU ms per coarse step of each run, the substep count).
+    """
+    n, nc = setup.fine, setup.coarse
+    lib = _lib.load()
+    err = {"uncorrected": np.zeros(steps), "corrected": np.zeros(steps),
+           "uncorrected_equal_gpu_time": np.zeros(steps)}
+    gpu_ms = {k: 0.0 for k in err}
+    sub = equal_time_substeps_n
+    for seed in seeds:
+        fine = Solver(_cfg(n, setup, seed))
+        fine.init_state(torch.from_numpy(inputs.cooling_box((n, n, n))).float().cuda().contiguous())
+        fine.advance(setup.spinup_steps)
+        U0 = downsample(fine.get_state(), setup.factor)
+        if sub == "auto":
+            sub = equal_time_substeps(setup, params, norm, U0)
+        runs = {}
+        for name in err:
+            runs[name] = Solver(_cfg(nc, setup, seed))
+            runs[name].init_state(U0)
+        _set_corrector(runs["corrected"], params, norm)
+        for k in range(steps):
+            dt_c = runs["uncorrected"].compute_dt()
+            modes = fine_interval(fine, dt_c, setup.forcing)
+            for name, s in runs.items():
+                if modes is not None:
+                    s.set_forcing_modes(modes, hold=True)
+                if name == "uncorrected_equal_gpu_time":
+                    def adv(s=s):
+                        for _ in range(sub):
+                            s.step(dt_c / sub, sync=False)
+                elif name == "corrected":
+                    def adv(s=s):
+                        s.step(dt_c, sync=False)
+                        _lib.check(lib.dh_correct(s.ctx), s.ctx)
+                else:
+                    def adv(s=s):
+                        s.step(dt_c, sync=False)
+                gpu_ms[name] += _timed(adv)
+            ref = downsample(fine.get_state(), setup.factor)
+            for name, s in runs.items():
+                err[name][k] += _rel_l2(s.get_state(), ref) / len(seeds)
+        for s in list(runs.values()) + [fine]:
+            s.close()
+    nrun = steps * len(seeds)
+    return ({k: v.tolist() for k, v in err.items()}, {k: v / nrun for k, v in gpu_ms.items()}, sub)

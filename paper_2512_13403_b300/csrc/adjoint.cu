@@ -27,14 +27,14 @@ constexpr int NFXA = ABX + 3;               // x faces per row: -3/2 .. BX+1/2
 constexpr int NFYA = ABY + 3;               // y faces per column
 constexpr int NCXA = ABX + 2;               // x cells per row for the slope terms: -1 .. BX
 constexpr int NCYA = ABY + 2;
-constexpr int FACE_SLOTS = (NFXA * ABY > NFYA * ABX) ? NFXA * ABY : NFYA * ABX;
-constexpr int CELL_SLOTS = (NCXA * ABY > NCYA * ABX) ? NCXA * ABY : NCYA * ABX;
+constexpr int NFX = NFXA * ABY, NFY = NFYA * ABX;   // x and y faces of a plane tile
+constexpr int NCX = NCXA * ABY, NCY = NCYA * ABX;   // cells with x and y slope terms
 
 template <typename real> struct AdjSmem {
   real w[4][5][WY][WX];
   real mu[5][MYH][MXH];
-  real face[10][FACE_SLOTS];   // (gL[5], gR[5]) per face
-  real cell[10][CELL_SLOTS];   // (A[5], B[5]) per cell
+  real face[10][NFX + NFY];    // (gL[5], gR[5]) per face: x faces, then y faces
+  real cell[10][NCX + NCY];    // (A[5], B[5]) per cell: x terms, then y terms
   int xs[WX], ys[WY];
 };
 
@@ -174,28 +174,50 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       }
     }
 
-    // ---- x: faces, slope terms, gather ------------------------------------------------------
-    for (int f = tid; f < NFXA * ABY; f += ANT) {
-      const int ly = f / NFXA, q = f - ly * NFXA;
-      const int sy = ly + 3;
+    // ---- x and y faces of plane k (one linear loop), then their slope terms, then the gather
+    for (int f = tid; f < NFX + NFY; f += ANT) {
       real g[5], gL[5], gR[5];
+      if (f < NFX) {
+        const int ly = f / NFXA, q = f - ly * NFXA;
+        const int sy = ly + 3;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][ly + 2][q + 1] - S.mu[c][ly + 2][q]) * p.idx;
-      face_vjp(0, ring_prim(S, s0, sy, q), ring_prim(S, s0, sy, q + 1), ring_prim(S, s0, sy, q + 2),
-               ring_prim(S, s0, sy, q + 3), g, gamma, gm1, gL, gR);
+        for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][ly + 2][q + 1] - S.mu[c][ly + 2][q]) * p.idx;
+        face_vjp(0, ring_prim(S, s0, sy, q), ring_prim(S, s0, sy, q + 1), ring_prim(S, s0, sy, q + 2),
+                 ring_prim(S, s0, sy, q + 3), g, gamma, gm1, gL, gR);
+      } else {
+        const int fy = f - NFX;
+        const int q = fy / ABX, lx = fy - q * ABX;
+        const int sx = lx + 3;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][q + 1][lx + 2] - S.mu[c][q][lx + 2]) * p.idy;
+        face_vjp(1, ring_prim(S, s0, q, sx), ring_prim(S, s0, q + 1, sx), ring_prim(S, s0, q + 2, sx),
+                 ring_prim(S, s0, q + 3, sx), g, gamma, gm1, gL, gR);
+      }
 #pragma unroll
       for (int c = 0; c < 5; ++c) { S.face[c][f] = gL[c]; S.face[5 + c][f] = gR[c]; }
     }
     __syncthreads();
-    for (int e = tid; e < NCXA * ABY; e += ANT) {
-      const int ly = e / NCXA, r = e - ly * NCXA;
-      const int sy = ly + 3;
+    for (int e = tid; e < NCX + NCY; e += ANT) {
       real D[5], A[5], B[5];
+      if (e < NCX) {
+        const int ly = e / NCXA, r = e - ly * NCXA;
+        const int sy = ly + 3;
 #pragma unroll
-      for (int c = 0; c < 5; ++c)
-        D[c] = real(0.5) * S.face[c][ly * NFXA + r + 1] - real(0.5) * S.face[5 + c][ly * NFXA + r];
-      slope_vjp(ring_prim(S, s0, sy, r + 1), ring_prim(S, s0, sy, r + 2), ring_prim(S, s0, sy, r + 3),
-                D, A, B);
+        for (int c = 0; c < 5; ++c)
+          D[c] = real(0.5) * S.face[c][ly * NFXA + r + 1] - real(0.5) * S.face[5 + c][ly * NFXA + r];
+        slope_vjp(ring_prim(S, s0, sy, r + 1), ring_prim(S, s0, sy, r + 2),
+                  ring_prim(S, s0, sy, r + 3), D, A, B);
+      } else {
+        const int ey = e - NCX;
+        const int r = ey / ABX, lx = ey - r * ABX;
+        const int sx = lx + 3;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          D[c] = real(0.5) * S.face[c][NFX + (r + 1) * ABX + lx] -
+                 real(0.5) * S.face[5 + c][NFX + r * ABX + lx];
+        slope_vjp(ring_prim(S, s0, r + 1, sx), ring_prim(S, s0, r + 2, sx),
+                  ring_prim(S, s0, r + 3, sx), D, A, B);
+      }
 #pragma unroll
       for (int c = 0; c < 5; ++c) { S.cell[c][e] = A[c]; S.cell[5 + c][e] = B[c]; }
     }
@@ -203,43 +225,14 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
     {
       const int fb = ty * NFXA, cb = ty * NCXA;
 #pragma unroll
-      for (int c = 0; c < 5; ++c)
+      for (int c = 0; c < 5; ++c) {
         gW[c] += (S.face[c][fb + tx + 2] + S.face[5 + c][fb + tx + 1]) + S.cell[c][cb + tx] -
                  S.cell[c][cb + tx + 1] + S.cell[5 + c][cb + tx + 1] - S.cell[5 + c][cb + tx + 2];
+        gW[c] += (S.face[c][NFX + (ty + 2) * ABX + tx] + S.face[5 + c][NFX + (ty + 1) * ABX + tx]) +
+                 S.cell[c][NCX + ty * ABX + tx] - S.cell[c][NCX + (ty + 1) * ABX + tx] +
+                 S.cell[5 + c][NCX + (ty + 1) * ABX + tx] - S.cell[5 + c][NCX + (ty + 2) * ABX + tx];
+      }
     }
-    __syncthreads();
-
-    // ---- y ------------------------------------------------------------------------------------
-    for (int f = tid; f < NFYA * ABX; f += ANT) {
-      const int q = f / ABX, lx = f - q * ABX;
-      const int sx = lx + 3;
-      real g[5], gL[5], gR[5];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][q + 1][lx + 2] - S.mu[c][q][lx + 2]) * p.idy;
-      face_vjp(1, ring_prim(S, s0, q, sx), ring_prim(S, s0, q + 1, sx), ring_prim(S, s0, q + 2, sx),
-               ring_prim(S, s0, q + 3, sx), g, gamma, gm1, gL, gR);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) { S.face[c][f] = gL[c]; S.face[5 + c][f] = gR[c]; }
-    }
-    __syncthreads();
-    for (int e = tid; e < NCYA * ABX; e += ANT) {
-      const int r = e / ABX, lx = e - r * ABX;
-      const int sx = lx + 3;
-      real D[5], A[5], B[5];
-#pragma unroll
-      for (int c = 0; c < 5; ++c)
-        D[c] = real(0.5) * S.face[c][(r + 1) * ABX + lx] - real(0.5) * S.face[5 + c][r * ABX + lx];
-      slope_vjp(ring_prim(S, s0, r + 1, sx), ring_prim(S, s0, r + 2, sx), ring_prim(S, s0, r + 3, sx),
-                D, A, B);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) { S.cell[c][e] = A[c]; S.cell[5 + c][e] = B[c]; }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < 5; ++c)
-      gW[c] += (S.face[c][(ty + 2) * ABX + tx] + S.face[5 + c][(ty + 1) * ABX + tx]) +
-               S.cell[c][ty * ABX + tx] - S.cell[c][(ty + 1) * ABX + tx] +
-               S.cell[5 + c][(ty + 1) * ABX + tx] - S.cell[5 + c][(ty + 2) * ABX + tx];
 
     // ---- primitive recovery transposed, stage combination, store ------------------------------
     if (active) {

@@ -169,9 +169,13 @@ static void bias_grad(const __nv_bfloat16* grad, int groups, int nch, const Conv
   bias_grad_final_kernel<<<1, 32, 0, s>>>(part, BG_BLOCKS, nch, db);
 }
 
+// rho_floor is rho_floor_c, or floor_per_mass * totals[0] when `totals` (the FP64 conserved
+// totals of U, on the device) is given.
 __global__ void correct_kernel(float* __restrict__ U, const float* __restrict__ y, long long n,
-                               const float* __restrict__ norm, float rho_floor, float T_floor,
-                               float gm1) {
+                               const float* __restrict__ norm, float rho_floor_c,
+                               const double* __restrict__ totals, double floor_per_mass,
+                               float T_floor, float gm1) {
+  const float rho_floor = totals ? (float)(floor_per_mass * totals[0]) : rho_floor_c;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     float v[5];
@@ -365,15 +369,21 @@ extern "C" dh_status dh_cnn_backward(dh_cnn* c, const float* U_in, const float* 
   return check_err(c);
 }
 
-extern "C" dh_status dh_cnn_correct_state(dh_cnn* c, float* U, double rho_floor, double T_floor,
-                                          double gamma) {
+static dh_status cnn_correct(dh_cnn* c, float* U, double rho_floor, const double* totals,
+                             double floor_per_mass, double T_floor, double gamma) {
   if (!c || !U) return DH_ERR_ARG;
   CNN_TRY(cnn_forward(c, U, nullptr, false));
   correct_kernel<<<grid_for(c->ncell), 256, 0, c->stream>>>(U, c->y, c->ncell, c->norm_dev,
-                                                            (float)rho_floor, (float)T_floor,
+                                                            (float)rho_floor, totals,
+                                                            floor_per_mass, (float)T_floor,
                                                             (float)(gamma - 1.0));
   CNN_TRY(cnn_cuda(c, cudaGetLastError(), "correct"));
   return check_err(c);
+}
+
+extern "C" dh_status dh_cnn_correct_state(dh_cnn* c, float* U, double rho_floor, double T_floor,
+                                          double gamma) {
+  return cnn_correct(c, U, rho_floor, nullptr, 0.0, T_floor, gamma);
 }
 
 extern "C" dh_status dh_adam_step(float* params, const float* grads, float* m, float* v, long long n,
@@ -408,13 +418,13 @@ extern "C" dh_status dh_correct(dh_ctx* ctx) {
   if (!ctx) return DH_ERR_ARG;
   if (!ctx->cnn || !ctx->cnn->have_params) { ctx->err = "no corrector set"; return DH_ERR_STATE; }
   if (!ctx->initialized) { ctx->err = "state not initialised"; return DH_ERR_STATE; }
-  // rho floor: 1e-6 of the mean density
-  double tot[5];
-  dh_status st = dh_conserved_totals(ctx, tot);
-  if (st != DH_OK) return st;
-  const double rho_floor = 1e-6 * tot[0] / (double)ctx->n3;
-  st = dh_cnn_correct_state(ctx->cnn, (float*)ctx->U[ctx->cur], rho_floor, ctx->cfg.t_floor,
-                            ctx->cfg.gamma);
+  // rho floor: 1e-6 of the mean density, from FP64 totals that stay on the device
+  float* U = (float*)ctx->U[ctx->cur];
+  cudaError_t e = launch_totals<float>(U, ctx->n3, ctx->partials, totals_blocks(), ctx->totals,
+                                       ctx->stream);
+  if (e != cudaSuccess) { ctx->err = cudaGetErrorString(e); return DH_ERR_CUDA; }
+  dh_status st = cnn_correct(ctx->cnn, U, 0.0, ctx->totals, 1e-6 / (double)ctx->n3,
+                             ctx->cfg.t_floor, ctx->cfg.gamma);
   if (st != DH_OK) { ctx->err = dh_last_error(nullptr); return st; }
   // the state changed: the next CFL step must see it
   return dh_refresh_cfl(ctx);

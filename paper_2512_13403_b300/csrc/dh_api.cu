@@ -349,9 +349,9 @@ static dh_status finish_steps(dh_ctx* c, long long nstep_before) {
 }
 
 dh_status dh_refresh_cfl(dh_ctx* c) {
+  // stream-ordered: the next step reads the minimum on the device
   DH_CUDA(c, reset_cfl_bits(c));
   DH_CUDA(c, c->prec == DH_F64 ? cfl_reduce_current<double>(c) : cfl_reduce_current<float>(c));
-  DH_CUDA(c, cudaStreamSynchronize(c->stream));
   return DH_OK;
 }
 

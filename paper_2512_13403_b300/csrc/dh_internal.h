@@ -55,6 +55,7 @@ cudaError_t mg_allocate(dh_ctx* c);
 void mg_setup_host(dh_ctx* c);
 cudaError_t mg_reset(dh_ctx* c);
 void mg_free(dh_ctx* c);
+double* mg_phi64(dh_ctx* c);   // the float64 potential (warm start of the next solve)
 template <typename real> cudaError_t gravity_sources(dh_ctx* c, void* Ustar);
 
 // adjoint.cu

@@ -124,6 +124,8 @@ cudaError_t mg_reset(dh_ctx* c) {
   return cudaMemsetAsync(m->phi64, 0, m->cells[0] * sizeof(double), c->stream);
 }
 
+double* mg_phi64(dh_ctx* c) { return c->mg ? c->mg->phi64 : nullptr; }
+
 void mg_free(dh_ctx* c) {
   MG* m = c->mg;
   if (!m) return;

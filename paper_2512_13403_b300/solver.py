@@ -188,6 +188,14 @@ class Solver:
                                                 C.c_void_p(ptr), C.c_void_p(optr), dev))
         return out
 
+    def save(self, path: str):
+        """File checkpoint (state, time, step count, OU tables, gravity warm start)."""
+        self._check(self.lib.dh_save(self.ctx, str(path).encode()))
+
+    def load(self, path: str):
+        """Restore a checkpoint written by a context of the same configuration."""
+        self._check(self.lib.dh_load(self.ctx, str(path).encode()))
+
     def profile(self, enable: bool):
         self._check(self.lib.dh_profile_enable(self.ctx, int(enable)))
 

@@ -73,6 +73,11 @@ def test_small_pair_train_evaluate_cycle():
     assert 0.0 < rel < 0.1
     params, norm, losses = closure.train(X, Y, epochs=3, lr0=3e-3, lr1=1e-3)
     assert losses[-1] < losses[0]
-    err, ms = closure.evaluate(setup, params, norm, steps=4, equal_time_substeps=2)
+    err, ms, sub = closure.evaluate(setup, params, norm, steps=4, seeds=(200, 201))
+    assert sub >= 1
     for k in ("uncorrected", "corrected", "uncorrected_equal_gpu_time"):
-        assert len(err[k]) == 4 and all(np.isfinite(err[k]))
+        assert len(err[k]) == 4 and all(np.isfinite(err[k])) and ms[k] > 0.0
+    # the same evaluation with a fixed substep count reproduces the shared runs exactly
+    err2, _, _ = closure.evaluate(setup, params, norm, steps=4, seeds=(200, 201),
+                                  equal_time_substeps_n=sub)
+    assert err2["uncorrected"] == err["uncorrected"] and err2["corrected"] == err["corrected"]
