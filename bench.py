@@ -361,6 +361,7 @@ def corrector_leg(args):
             "uncorrected": mean["uncorrected"], "corrected": mean["corrected"],
             "uncorrected_equal_gpu_time": mean["uncorrected_equal_gpu_time"],
             "equal_time_substeps": sub,
+            "diverged": {k: list(v) for k, v in getattr(closure.evaluate, "diverged", {}).items()},
             "final_step": {k: v[-1] for k, v in err.items()},
             "gpu_ms_per_coarse_step": ms, "pairs": int(X.shape[0]), "epochs": args.corr_epochs,
             "train_loss": losses, "seconds": {"pairs": t1 - t0, "train": t2 - t1, "eval": t3 - t2},

@@ -249,7 +249,8 @@ dh_status dh_cnn_backward(dh_cnn* cnn, const float* U_in, const float* U_target,
                           double* loss);
 /* U <- U + s * network(U) in place (float32 state, device), then rho >= rho_floor and
    E >= |m|^2/(2 rho) + rho T_floor/(gamma - 1).  An inference pass: it keeps no activations
-   for dh_cnn_backward (call dh_cnn_forward again before the next backward).  Synchronises. */
+   for dh_cnn_backward (call dh_cnn_forward again before the next backward).  Synchronises.
+   DH_ERR_NONFINITE if a corrected value is not finite (U then holds the corrected values). */
 dh_status dh_cnn_correct_state(dh_cnn* cnn, float* U, double rho_floor, double T_floor,
                                double gamma);
 /* Adam (Kingma & Ba) on n parameters: m, v are caller-owned moment buffers (device), step >= 1
@@ -258,7 +259,9 @@ dh_status dh_adam_step(float* params, const float* grads, float* m, float* v, lo
                        double lr, double beta1, double beta2, double eps, int step, void* stream);
 /* Corrector of a float32 context: dh_set_corrector copies the parameters (as dh_cnn_set_params);
    dh_correct applies U <- U + s * network(U) to the current state with the floors above
-   (rho_floor = 1e-6 <rho>, the context's T_floor and gamma).  DH_ERR_STATE without a corrector. */
+   (rho_floor = 1e-6 <rho>, the context's T_floor and gamma); it settles enqueued steps first.
+   DH_ERR_STATE without a corrector; DH_ERR_NONFINITE if the corrected state is not finite, in
+   which case the context keeps the uncorrected state. */
 dh_status dh_set_corrector(dh_ctx* ctx, const float* params, const float* norm15);
 dh_status dh_correct(dh_ctx* ctx);
 

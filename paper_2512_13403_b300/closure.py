@@ -209,13 +209,16 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
     make_pairs).  A third run, uncorrected, takes `equal_time_substeps_n` substeps per coarse
     step: the uncorrected solver given the corrected run's GPU time as a smaller time step
     ("auto": from the measured cost ratio).  Returns (per-step relative L2 errors averaged over
-    the seeds, GPU ms per coarse step of each run, the substep count).
+    the seeds, GPU ms per coarse step of each run, the substep count).  A run whose state stops
+    being finite ends there and counts as an infinite error afterwards; `evaluate.diverged`
+    maps such runs to (seed, coarse step).
     """
     n, nc = setup.fine, setup.coarse
     lib = _lib.load()
     err = {"uncorrected": np.zeros(steps), "corrected": np.zeros(steps),
            "uncorrected_equal_gpu_time": np.zeros(steps)}
     gpu_ms = {k: 0.0 for k in err}
+    diverged = {}          # run name -> (seed, coarse step) of a non-finite state
     sub = equal_time_substeps_n
     for seed in seeds:
         fine = Solver(_cfg(n, setup, seed))
@@ -229,10 +232,11 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
             runs[name] = Solver(_cfg(nc, setup, seed))
             runs[name].init_state(U0)
         _set_corrector(runs["corrected"], params, norm)
+        live = dict(runs)
         for k in range(steps):
             dt_c = runs["uncorrected"].compute_dt()
             modes = fine_interval(fine, dt_c, setup.forcing)
-            for name, s in runs.items():
+            for name, s in list(live.items()):
                 if modes is not None:
                     s.set_forcing_modes(modes, hold=True)
                 if name == "uncorrected_equal_gpu_time":
@@ -246,11 +250,18 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
                 else:
                     def adv(s=s):
                         s.step(dt_c, sync=False)
-                gpu_ms[name] += _timed(adv)
+                try:
+                    gpu_ms[name] += _timed(adv)
+                except _lib.DhError:
+                    # a non-finite state: the run stops and its error is infinite from here
+                    diverged.setdefault(name, (seed, k))
+                    del live[name]
             ref = downsample(fine.get_state(), setup.factor)
-            for name, s in runs.items():
-                err[name][k] += _rel_l2(s.get_state(), ref) / len(seeds)
+            for name in runs:
+                e = _rel_l2(live[name].get_state(), ref) if name in live else float("inf")
+                err[name][k] += e / len(seeds)
         for s in list(runs.values()) + [fine]:
             s.close()
     nrun = steps * len(seeds)
+    evaluate.diverged = diverged
     return ({k: v.tolist() for k, v in err.items()}, {k: v / nrun for k, v in gpu_ms.items()}, sub)

@@ -55,11 +55,13 @@ struct dh_cnn {
 
 namespace dh {
 
+// Cell coordinates of linear index q (grids below 2^31 cells: 32-bit arithmetic).
 __device__ __forceinline__ void cell_xyz(long long q, const ConvGeom& g, int& x, int& y, int& z) {
-  x = (int)(q % g.nx);
-  const long long t = q / g.nx;
-  y = (int)(t % g.ny);
-  z = (int)(t / g.ny);
+  const unsigned t = (unsigned)q / (unsigned)g.nx;
+  x = (int)((unsigned)q - t * (unsigned)g.nx);
+  const unsigned w = t / (unsigned)g.ny;
+  y = (int)(t - w * (unsigned)g.ny);
+  z = (int)w;
 }
 
 __global__ void normalize_kernel(const float* __restrict__ U, ConvGeom g,
@@ -112,12 +114,15 @@ __global__ void mse_grad_kernel(const float* __restrict__ y, const float* __rest
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// *out = scale * sum of partial[0..nb) in a fixed order: lane l sums entries l, l+32, ...,
+// then a fixed shuffle tree (one warp).
 __global__ void sum_blocks_kernel(const double* partial, int nb, double scale, double* out) {
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += partial[b];
-    *out = scale * s;
-  }
+  const int l = threadIdx.x;
+  double s = 0.0;
+  for (int b = l; b < nb; b += 32) s += partial[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (l == 0) *out = scale * s;
 }
 
 // Bias gradient db[c] = sum over cells of channel c of a padded gradient.  Block (b, group)
@@ -169,27 +174,34 @@ static void bias_grad(const __nv_bfloat16* grad, int groups, int nch, const Conv
   bias_grad_final_kernel<<<1, 32, 0, s>>>(part, BG_BLOCKS, nch, db);
 }
 
-// rho_floor is rho_floor_c, or floor_per_mass * totals[0] when `totals` (the FP64 conserved
-// totals of U, on the device) is given.
-__global__ void correct_kernel(float* __restrict__ U, const float* __restrict__ y, long long n,
-                               const float* __restrict__ norm, float rho_floor_c,
+// Uout = floors(Uin + s * y) (Uout may be Uin).  rho_floor is rho_floor_c, or
+// floor_per_mass * totals[0] when `totals` (the FP64 conserved totals of Uin, on the device) is
+// given.  A non-finite result sets bit 2 of *err.
+constexpr unsigned CNN_ERR_WAIT = 1u, CNN_ERR_NONFINITE = 2u;
+__global__ void correct_kernel(const float* Uin, float* Uout, const float* __restrict__ y,
+                               long long n, const float* __restrict__ norm, float rho_floor_c,
                                const double* __restrict__ totals, double floor_per_mass,
-                               float T_floor, float gm1) {
+                               float T_floor, float gm1, unsigned* err) {
   const float rho_floor = totals ? (float)(floor_per_mass * totals[0]) : rho_floor_c;
+  bool finite = true;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     float v[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) v[c] = U[c * n + q] + norm[10 + c] * y[c * n + q];
+    for (int c = 0; c < 5; ++c) v[c] = Uin[c * n + q] + norm[10 + c] * y[c * n + q];
     const float rho = fmaxf(v[0], rho_floor);
     const float kin = 0.5f * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / rho;
     const float Emin = kin + rho * T_floor / gm1;
-    U[q] = rho;
-    U[n + q] = v[1];
-    U[2 * n + q] = v[2];
-    U[3 * n + q] = v[3];
-    U[4 * n + q] = fmaxf(v[4], Emin);
+    const float E = fmaxf(v[4], Emin);
+    finite = finite && isfinite(rho) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]) &&
+             isfinite(E) && isfinite(kin);
+    Uout[q] = rho;
+    Uout[n + q] = v[1];
+    Uout[2 * n + q] = v[2];
+    Uout[3 * n + q] = v[3];
+    Uout[4 * n + q] = E;
   }
+  if (!__all_sync(0xffffffffu, finite) && (threadIdx.x & 31) == 0) atomicOr(err, CNN_ERR_NONFINITE);
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -243,8 +255,8 @@ extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn*
   if (!out) return DH_ERR_ARG;
   *out = nullptr;
   const long long n = (long long)nx * ny * nz;
-  if (nx < 3 || ny < 3 || nz < 3) {
-    dh_set_global_error("dh_cnn_create: every dimension must be >= 3");
+  if (nx < 3 || ny < 3 || nz < 3 || n >= (1LL << 31)) {
+    dh_set_global_error("dh_cnn_create: every dimension must be >= 3 and the grid below 2^31 cells");
     return DH_ERR_ARG;
   }
   const long long prow = conv_geom(nx, ny, nz).rows;   // 16-byte rows per channel group
@@ -316,8 +328,12 @@ static dh_status check_err(dh_cnn* c) {
   CNN_TRY(cnn_cuda(c, cudaStreamSynchronize(c->stream), "sync"));
   if (h) {
     cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream);
-    dh_set_global_error("corrector: a bounded tensor-core wait gave up");
-    return DH_ERR_CUDA;
+    if (h & CNN_ERR_WAIT) {
+      dh_set_global_error("corrector: a bounded tensor-core wait gave up");
+      return DH_ERR_CUDA;
+    }
+    dh_set_global_error("corrector: the corrected state is not finite");
+    return DH_ERR_NONFINITE;
   }
   return DH_OK;
 }
@@ -369,21 +385,22 @@ extern "C" dh_status dh_cnn_backward(dh_cnn* c, const float* U_in, const float* 
   return check_err(c);
 }
 
-static dh_status cnn_correct(dh_cnn* c, float* U, double rho_floor, const double* totals,
-                             double floor_per_mass, double T_floor, double gamma) {
-  if (!c || !U) return DH_ERR_ARG;
-  CNN_TRY(cnn_forward(c, U, nullptr, false));
-  correct_kernel<<<grid_for(c->ncell), 256, 0, c->stream>>>(U, c->y, c->ncell, c->norm_dev,
+static dh_status cnn_correct(dh_cnn* c, const float* Uin, float* Uout, double rho_floor,
+                             const double* totals, double floor_per_mass, double T_floor,
+                             double gamma) {
+  if (!c || !Uin || !Uout) return DH_ERR_ARG;
+  CNN_TRY(cnn_forward(c, Uin, nullptr, false));
+  correct_kernel<<<grid_for(c->ncell), 256, 0, c->stream>>>(Uin, Uout, c->y, c->ncell, c->norm_dev,
                                                             (float)rho_floor, totals,
                                                             floor_per_mass, (float)T_floor,
-                                                            (float)(gamma - 1.0));
+                                                            (float)(gamma - 1.0), c->err);
   CNN_TRY(cnn_cuda(c, cudaGetLastError(), "correct"));
   return check_err(c);
 }
 
 extern "C" dh_status dh_cnn_correct_state(dh_cnn* c, float* U, double rho_floor, double T_floor,
                                           double gamma) {
-  return cnn_correct(c, U, rho_floor, nullptr, 0.0, T_floor, gamma);
+  return cnn_correct(c, U, U, rho_floor, nullptr, 0.0, T_floor, gamma);
 }
 
 extern "C" dh_status dh_adam_step(float* params, const float* grads, float* m, float* v, long long n,
@@ -418,14 +435,22 @@ extern "C" dh_status dh_correct(dh_ctx* ctx) {
   if (!ctx) return DH_ERR_ARG;
   if (!ctx->cnn || !ctx->cnn->have_params) { ctx->err = "no corrector set"; return DH_ERR_STATE; }
   if (!ctx->initialized) { ctx->err = "state not initialised"; return DH_ERR_STATE; }
+  // settle enqueued steps: their rollback bookkeeping assumes no other buffer swap
+  if (ctx->pending_steps > 0) {
+    dh_status s0 = dh_finish_steps(ctx);
+    if (s0 != DH_OK) return s0;
+  }
   // rho floor: 1e-6 of the mean density, from FP64 totals that stay on the device
-  float* U = (float*)ctx->U[ctx->cur];
+  const float* U = (const float*)ctx->U[ctx->cur];
+  float* V = (float*)ctx->U[1 - ctx->cur];
   cudaError_t e = launch_totals<float>(U, ctx->n3, ctx->partials, totals_blocks(), ctx->totals,
                                        ctx->stream);
   if (e != cudaSuccess) { ctx->err = cudaGetErrorString(e); return DH_ERR_CUDA; }
-  dh_status st = cnn_correct(ctx->cnn, U, 0.0, ctx->totals, 1e-6 / (double)ctx->n3,
+  // the corrected state goes to the other buffer and becomes current only if it is finite
+  dh_status st = cnn_correct(ctx->cnn, U, V, 0.0, ctx->totals, 1e-6 / (double)ctx->n3,
                              ctx->cfg.t_floor, ctx->cfg.gamma);
   if (st != DH_OK) { ctx->err = dh_last_error(nullptr); return st; }
+  ctx->cur = 1 - ctx->cur;
   // the state changed: the next CFL step must see it
   return dh_refresh_cfl(ctx);
 }

@@ -399,9 +399,9 @@ __global__ void pad_kernel(const __nv_bfloat16* __restrict__ src, int C, ConvGeo
        i += (long long)gridDim.x * blockDim.x) {
     const long long q = i / G;
     const int cg = (int)(i - q * G);
-    const int x = (int)(q % g.nx);
-    const long long t = q / g.nx;
-    const int y = (int)(t % g.ny), z = (int)(t / g.ny);
+    const unsigned t = (unsigned)q / (unsigned)g.nx;
+    const int x = (int)((unsigned)q - t * (unsigned)g.nx);
+    const int y = (int)(t % (unsigned)g.ny), z = (int)(t / (unsigned)g.ny);
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + q * C + cg * 8));
     store_with_images(reinterpret_cast<uint4*>(dst) + (long long)cg * g.rows, g, x, y, z, v);
   }
@@ -415,15 +415,17 @@ __global__ void unpad_kernel(const __nv_bfloat16* __restrict__ src, int C, ConvG
        i += (long long)gridDim.x * blockDim.x) {
     const long long q = i / G;
     const int cg = (int)(i - q * G);
-    const int x = (int)(q % g.nx);
-    const long long t = q / g.nx;
-    const int y = (int)(t % g.ny), z = (int)(t / g.ny);
+    const unsigned t = (unsigned)q / (unsigned)g.nx;
+    const int x = (int)((unsigned)q - t * (unsigned)g.nx);
+    const int y = (int)(t % (unsigned)g.ny), z = (int)(t / (unsigned)g.ny);
     reinterpret_cast<uint4*>(dst + q * C)[cg] =
         __ldg(reinterpret_cast<const uint4*>(src) + (long long)cg * g.rows + pad_row(g, x, y, z));
   }
 }
 
-static bool conv_dims_ok(int nx, int ny, int nz) { return nx >= 3 && ny >= 3 && nz >= 3; }
+static bool conv_dims_ok(int nx, int ny, int nz) {
+  return nx >= 3 && ny >= 3 && nz >= 3 && (long long)nx * ny * nz < (1LL << 31);
+}
 
 }  // namespace dh
 
@@ -498,50 +500,66 @@ extern "C" dh_status dh_conv3d_bf16(const void* act, int cin_pad, const void* pa
 // =============================================================================================
 // Weight gradient: dW[n][c][tap] = sum_cells g[cell][n] * act[cell + offset(tap)][c], a GEMM
 // with M = (tap, c) rows (27 * CIN, in tiles of 128), N = n, K = cells.  Each CTA reduces a
-// contiguous range of cells in 16-cell K steps: the threads gather, for every tap, the 16
-// neighbour rows (read from the padded layout, where a tap is a row offset) and transpose them
-// into K-major core matrices (a row holds one (tap, c) over
-// 16 consecutive cells), the gradient rows likewise; one thread issues one MMA per M tile into
-// its own TMEM accumulator.  Per-CTA partial sums go to global memory and a second kernel adds
-// them in a fixed order.
+// contiguous range of cells in 32-cell K steps.  An 8-cell x 8-channel block of either operand
+// (act shifted by a tap, or the gradient) is transposed into a K-major core matrix (a row = one
+// channel over 8 consecutive cells) by one quarter of an stmatrix.trans: lane t loads the 4
+// bytes of cell t/4, channels 2(t%4)..+1 of the padded layout (where a tap is a row offset).
+// A converged warp issues the MMAs of a step (one per M tile and 16-cell half) into per-tile TMEM
+// accumulators while the threads build the next step.  Per-CTA partial sums go to global memory
+// and a second kernel adds them in a fixed order.
 namespace dh {
 
-constexpr int WG_THREADS = 128;
+constexpr int WG_THREADS = 256;
 constexpr int WG_STAGES = 2;
+constexpr int WG_KG = 4;                 // 8-cell groups per K step
+constexpr int WG_KCELLS = 8 * WG_KG;     // cells per K step
+
+template <int CIN, int NOUT>
+struct WgShape {
+  static constexpr int G = CIN / 8;                    // activation channel groups
+  static constexpr int GN = NOUT / 8;                  // gradient channel groups (B rows / 8)
+  static constexpr int MT = (27 * CIN + 127) / 128;    // M tiles
+  static constexpr int A_TILE = 16 * WG_KG * 128;      // 16 M groups x WG_KG K groups x 128 B
+  static constexpr int B_BYTES = GN * WG_KG * 128;
+  static constexpr int STAGE = MT * A_TILE + B_BYTES;
+  static constexpr uint32_t TMEM_COLS =
+      MT * NOUT <= 32 ? 32 : (MT * NOUT <= 64 ? 64 : (MT * NOUT <= 128 ? 128 : 256));
+  static constexpr size_t SMEM = (size_t)WG_STAGES * STAGE + 8 * 4 + 16;
+};
 
 template <int CIN, int NOUT>
 __global__ void __launch_bounds__(WG_THREADS)
 conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat16* __restrict__ g,
                        int g_stride, int nx, int ny, int nz, long long cells_per_cta,
                        float* __restrict__ partial, unsigned* err) {
-  constexpr int MROWS = 27 * CIN;
-  constexpr int MT = (MROWS + 127) / 128;           // M tiles
-  constexpr int A_TILE = 128 * 16 * 2;              // bytes per M tile per stage
-  constexpr int B_TILE = NOUT * 16 * 2;
-  constexpr int STAGE = MT * A_TILE + B_TILE;
-  constexpr uint32_t TMEM_COLS = MT * NOUT <= 32 ? 32 : (MT * NOUT <= 64 ? 64 : (MT * NOUT <= 128 ? 128 : 256));
+  using W = WgShape<CIN, NOUT>;
+  constexpr int G = W::G, GN = W::GN, MT = W::MT;
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + WG_STAGES * STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + WG_STAGES * W::STAGE);
   uint64_t* bar_done = bars + WG_STAGES;
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar_done + 1);
 
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const ConvGeom geo = conv_geom(nx, ny, nz);
   const long long ncell = (long long)nx * ny * nz;
   const long long c0 = (long long)blockIdx.x * cells_per_cta;
   const long long c1 = c0 + cells_per_cta < ncell ? c0 + cells_per_cta : ncell;
-  const int ksteps = c1 > c0 ? (int)((c1 - c0 + 15) / 16) : 0;
+  const int ksteps = c1 > c0 ? (int)((c1 - c0 + WG_KCELLS - 1) / WG_KCELLS) : 0;
 
-  // zero both stages once: padding rows (beyond 27 * CIN) and tail cells stay zero
-  for (int i = tid; i < WG_STAGES * STAGE / 16; i += WG_THREADS)
+  // zero both stages once: M rows past 27 * CIN stay zero
+  for (int i = tid; i < WG_STAGES * W::STAGE / 16; i += WG_THREADS)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  // row offset of each tap in the padded layout
+  __shared__ long long s_shift[27];
+  if (tid < 27)
+    s_shift[tid] = (long long)(tid / 9 - 1) * geo.PXY + (long long)((tid / 3) % 3 - 1) * geo.PX + (tid % 3 - 1);
   if (tid == 0) {
     for (int b = 0; b < WG_STAGES; ++b) tc::mbar_init(&bars[b], 1);
     tc::mbar_init(bar_done, 1);
     tc::mbar_fence_init();
   }
   if (warp == 0) {
-    tc::tmem_alloc(s_tmem, TMEM_COLS);
+    tc::tmem_alloc(s_tmem, W::TMEM_COLS);
     tc::tmem_relinquish();
   }
   tc::fence_async_smem();
@@ -551,9 +569,12 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
   const uint32_t tmem = *s_tmem;
   const uint32_t idesc = tc::idesc_bf16_f32(128, NOUT);
   const uint32_t s_addr = tc::smem_u32(smem);
+  const unsigned char* act_b = reinterpret_cast<const unsigned char*>(act);
+  const unsigned char* g_b = reinterpret_cast<const unsigned char*>(g);
+  const int g_groups = g_stride / 8;
   uint32_t phase_bits = 0;
-  int my_abort = 0;      // this thread saw a bounded wait give up
-  bool aborted = false;  // some thread did (agreed at a barrier)
+  int my_abort = 0;
+  bool aborted = false;
 
   for (int s = 0; s < ksteps; ++s) {
     const int b = s % WG_STAGES;
@@ -561,67 +582,79 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
       if (!tc::mbar_wait(&bars[b], (phase_bits >> b) & 1u, CV_WAIT_ITERS)) my_abort = 1;
       phase_bits ^= 1u << b;
     }
-    unsigned char* st = smem + b * STAGE;
-    const long long x0 = c0 + 16LL * s;
-    // A: items (tap, channel group of 8, cell k); each loads 8 channels and scatters them
-    for (int it = tid; it < 27 * (CIN / 8) * 16; it += WG_THREADS) {
-      const int k = it & 15;
-      const int rest = it >> 4;
-      const int cg = rest % (CIN / 8), tap = rest / (CIN / 8);
-      const long long x = x0 + k;
-      __align__(16) __nv_bfloat16 v[8];
-      if (x < c1) {
-        const int i = (int)(x % nx);
-        const long long t1 = x / nx;
-        const int j = (int)(t1 % ny), kz = (int)(t1 / ny);
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        *reinterpret_cast<uint4*>(v) = __ldg(reinterpret_cast<const uint4*>(act) + cg * geo.rows +
-                                             pad_row(geo, i + dx, j + dy, kz + dz));
-      } else {
-        *reinterpret_cast<uint4*>(v) = make_uint4(0u, 0u, 0u, 0u);
-      }
+    const uint32_t st = s_addr + b * W::STAGE;
+    const long long k0 = c0 + (long long)WG_KCELLS * s;
+    // padded rows of this lane's cells (cell k0 + 8 kg + lane/4), -1 past the range
+    // (32-bit index arithmetic: the launcher rejects grids of 2^31 cells or more)
+    long long prow[WG_KG];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int m = tap * CIN + cg * 8 + e;       // A row
-        const int t = m >> 7, mr = m & 127;
-        const int off = t * A_TILE + (((mr >> 3) * 2 + (k >> 3)) * 8 + (mr & 7)) * 16 + (k & 7) * 2;
-        *reinterpret_cast<__nv_bfloat16*>(st + off) = v[e];
+    for (int kg = 0; kg < WG_KG; ++kg) {
+      const long long q = k0 + 8 * kg + (lane >> 2);
+      if (q < c1) {
+        const unsigned uq = (unsigned)q;
+        const unsigned t1 = uq / (unsigned)nx;
+        const int x = (int)(uq - t1 * (unsigned)nx);
+        const unsigned z = t1 / (unsigned)ny;
+        prow[kg] = pad_row(geo, x, (int)(t1 - z * (unsigned)ny), (int)z);
+      } else {
+        prow[kg] = -1;
       }
     }
-    // B: items (channel group of 8, cell k)
-    for (int it = tid; it < (NOUT / 8) * 16; it += WG_THREADS) {
-      const int k = it & 15, ng = it >> 4;
-      const long long x = x0 + k;
-      __align__(16) __nv_bfloat16 v[8];
-      if (x < c1 && ng * 8 < g_stride) {
-        const int i = (int)(x % nx);
-        const long long t1 = x / nx;
-        const int j = (int)(t1 % ny), kz = (int)(t1 / ny);
-        *reinterpret_cast<uint4*>(v) =
-            __ldg(reinterpret_cast<const uint4*>(g) + ng * geo.rows + pad_row(geo, i, j, kz));
-      }
-      else
-        *reinterpret_cast<uint4*>(v) = make_uint4(0u, 0u, 0u, 0u);
+    // Quad q transposes the four K groups of one operand row group: q < 27 G is activation
+    // group (tap, cg) = (q / G, q % G), then the GN gradient groups.  All of this warp's loads
+    // are issued first (their latencies overlap), then the transposing stores.
+    constexpr int NWARP = WG_THREADS / 32;
+    constexpr int NQA = 27 * G, NQ = NQA + GN;
+    constexpr int QPW = (NQ + NWARP - 1) / NWARP;   // quads per warp
+    uint32_t r[QPW][4];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int n = ng * 8 + e;
-        const int off = MT * A_TILE + (((n >> 3) * 2 + (k >> 3)) * 8 + (n & 7)) * 16 + (k & 7) * 2;
-        *reinterpret_cast<__nv_bfloat16*>(st + off) = v[e];
+    for (int j = 0; j < QPW; ++j) {
+      const int quad = warp + NWARP * j;
+      // row offset of this quad's operand row group (a tap shift may be negative)
+      long long base = 0;
+      bool valid = false;
+      if (quad < NQA) {
+        base = (long long)(quad % G) * geo.rows + s_shift[quad / G];
+        valid = true;
+      } else if (quad < NQ && quad - NQA < g_groups) {
+        base = (long long)(quad - NQA) * geo.rows;
+        valid = true;
       }
+      const unsigned char* src = quad < NQA ? act_b : g_b;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        uint32_t v = 0u;
+        if (valid && prow[i] >= 0)
+          v = __ldg(reinterpret_cast<const uint32_t*>(src + (base + prow[i]) * 16 + (lane & 3) * 4));
+        r[j][i] = v;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < QPW; ++j) {
+      const int quad = warp + NWARP * j;
+      if (quad >= NQ) break;   // warp-uniform
+      // lane 8i + jj gives the address of row jj of K group i of this quad's row group
+      const uint32_t grp = quad < NQA ? (uint32_t)((quad >> 4) * W::A_TILE + (quad & 15) * WG_KG * 128)
+                                      : (uint32_t)(MT * W::A_TILE + (quad - NQA) * WG_KG * 128);
+      const uint32_t dst = st + grp + (uint32_t)(lane >> 3) * 128u + (uint32_t)(lane & 7) * 16u;
+      tc::stmatrix_x4_trans(dst, r[j][0], r[j][1], r[j][2], r[j][3]);
     }
     tc::fence_async_smem();
     if (__syncthreads_or(my_abort)) { aborted = true; break; }
-    if (tid == 0) {
+    if (warp == 0) {
+      __syncwarp();
       tc::tc_fence_after();
-      const uint32_t base = s_addr + b * STAGE;
-      const uint64_t bdesc = tc::smem_desc(base + MT * A_TILE, 128, 256);
 #pragma unroll
       for (int t = 0; t < MT; ++t) {
-        const uint64_t adesc = tc::smem_desc(base + t * A_TILE, 128, 256);
-        tc::mma_bf16(tmem + t * NOUT, adesc, bdesc, idesc, s > 0 ? 1u : 0u);
+#pragma unroll
+        for (int h = 0; h < WG_KG / 2; ++h) {
+          const uint64_t adesc = tc::smem_desc(st + t * W::A_TILE + h * 256, 128, WG_KG * 128);
+          const uint64_t bdesc = tc::smem_desc(st + MT * W::A_TILE + h * 256, 128, WG_KG * 128);
+          tc::mma_bf16_elect(tmem + t * NOUT, adesc, bdesc, idesc, (s > 0 || h > 0) ? 1u : 0u);
+        }
       }
-      tc::mma_commit(&bars[b]);
-      if (s == ksteps - 1) tc::mma_commit(bar_done);
+      tc::mma_commit_elect(&bars[b]);
+      if (s == ksteps - 1) tc::mma_commit_elect(bar_done);
     }
   }
   int done_fail = 0;
@@ -629,53 +662,72 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
   if (__syncthreads_or(done_fail)) aborted = true;
   const bool have = ksteps > 0 && !aborted;
   tc::tc_fence_after();
-  // epilogue: partial[cta][m][n]
+  // epilogue (warps 0..3, one TMEM lane quarter each): partial[cta][m][n]
   float* out = partial + (long long)blockIdx.x * MT * 128 * NOUT;
-  for (int t = 0; t < MT; ++t) {
-    const int m = t * 128 + warp * 32 + (tid & 31);
-    if (have) {
-      const uint32_t taddr = tmem + t * NOUT + ((uint32_t)(warp * 32) << 16);
-      if (NOUT == 32) {
-        float acc[32];
-        tc::tmem_ld_32x32b_x32(taddr, acc);
-        tc::tmem_ld_wait();
-        for (int n = 0; n < 32; ++n) out[(long long)m * NOUT + n] = acc[n];
+  if (warp < 4) {
+    for (int t = 0; t < MT; ++t) {
+      const int m = t * 128 + warp * 32 + lane;
+      if (have) {
+        const uint32_t taddr = tmem + t * NOUT + ((uint32_t)(warp * 32) << 16);
+        if (NOUT == 32) {
+          float acc[32];
+          tc::tmem_ld_32x32b_x32(taddr, acc);
+          tc::tmem_ld_wait();
+          float4* o4 = reinterpret_cast<float4*>(out + (long long)m * NOUT);
+#pragma unroll
+          for (int v = 0; v < 8; ++v) o4[v] = make_float4(acc[4 * v], acc[4 * v + 1], acc[4 * v + 2], acc[4 * v + 3]);
+        } else {
+          float acc[16];
+          tc::tmem_ld_32x32b_x16(taddr, acc);
+          tc::tmem_ld_wait();
+          float4* o4 = reinterpret_cast<float4*>(out + (long long)m * NOUT);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) o4[v] = make_float4(acc[4 * v], acc[4 * v + 1], acc[4 * v + 2], acc[4 * v + 3]);
+        }
       } else {
-        float acc[16];
-        tc::tmem_ld_32x32b_x16(taddr, acc);
-        tc::tmem_ld_wait();
-        for (int n = 0; n < 16; ++n) out[(long long)m * NOUT + n] = acc[n];
+        for (int n = 0; n < NOUT; ++n) out[(long long)m * NOUT + n] = 0.0f;
       }
-    } else {
-      for (int n = 0; n < NOUT; ++n) out[(long long)m * NOUT + n] = 0.0f;
     }
   }
   if (aborted) {
     // phase 0 of bar_done completes once every MMA issued so far has completed
-    if (tid == 0) {
-      atomicOr(err, 1u);
-      tc::mma_commit(bar_done);
+    if (tid == 0) atomicOr(err, 1u);
+    if (warp == 0) {
+      tc::mma_commit_elect(bar_done);
+      tc::mbar_wait(bar_done, 0, CV_WAIT_ITERS);
     }
-    tc::mbar_wait(bar_done, 0, CV_WAIT_ITERS);
   }
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, TMEM_COLS);
+    tc::tmem_dealloc(tmem, W::TMEM_COLS);
   }
 }
 
-// dW[n][c][tap] (master layout) = sum over CTAs of partial[cta][tap * cin_pad + c][n]
+// dW[n][c][tap] (master layout) = sum over CTAs, in CTA order, of
+// partial[cta][tap * cin_pad + c][n].  Consecutive threads take consecutive n, so the reads of
+// one CTA's partials are contiguous.
 __global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int nctas, int mt, int nout_pad,
                                     int cin_pad, int cout, int cin, float* __restrict__ dW) {
   const int total = cout * cin * 27;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const int tap = idx % 27, c = (idx / 27) % cin, n = idx / (27 * cin);
+    const int n = idx % cout, mm = idx / cout;
+    const int c = mm % cin, tap = mm / cin;
     const int m = tap * cin_pad + c;
-    double s = 0.0;
-    for (int b = 0; b < nctas; ++b) s += (double)partial[((long long)b * mt * 128 + m) * nout_pad + n];
-    dW[idx] = (float)s;
+    const long long stride = (long long)mt * 128 * nout_pad;
+    const float* p = partial + (long long)m * nout_pad + n;
+    // four interleaved accumulators (CTA b into b % 4), combined in a fixed order
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int b = 0;
+    for (; b + 3 < nctas; b += 4) {
+      s0 += (double)p[b * stride];
+      s1 += (double)p[(b + 1) * stride];
+      s2 += (double)p[(b + 2) * stride];
+      s3 += (double)p[(b + 3) * stride];
+    }
+    for (; b < nctas; ++b) s0 += (double)p[b * stride];
+    dW[((long long)n * cin + c) * 27 + tap] = (float)((s0 + s1) + (s2 + s3));
   }
 }
 
@@ -683,17 +735,16 @@ template <int CIN, int NOUT>
 static cudaError_t launch_wgrad(const __nv_bfloat16* act, const __nv_bfloat16* g, int g_stride,
                                 int nx, int ny, int nz, int nctas, float* partial, unsigned* err,
                                 cudaStream_t s) {
-  constexpr int MT = (27 * CIN + 127) / 128;
-  constexpr int STAGE = MT * 128 * 16 * 2 + NOUT * 16 * 2;
-  const size_t smem = (size_t)WG_STAGES * STAGE + 8 * (WG_STAGES + 1) + 16;
+  using W = WgShape<CIN, NOUT>;
+  if ((long long)nx * ny * nz >= (1LL << 31)) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad_tc_kernel<CIN, NOUT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W::SMEM);
   if (e != cudaSuccess) return e;
   const long long ncell = (long long)nx * ny * nz;
   long long per = (ncell + nctas - 1) / nctas;
-  per = (per + 15) / 16 * 16;
-  conv3d_wgrad_tc_kernel<CIN, NOUT><<<nctas, WG_THREADS, smem, s>>>(act, g, g_stride, nx, ny, nz,
-                                                                   per, partial, err);
+  per = (per + WG_KCELLS - 1) / WG_KCELLS * WG_KCELLS;
+  conv3d_wgrad_tc_kernel<CIN, NOUT><<<nctas, WG_THREADS, W::SMEM, s>>>(act, g, g_stride, nx, ny, nz,
+                                                                       per, partial, err);
   return cudaGetLastError();
 }
 
@@ -721,7 +772,8 @@ extern "C" dh_status dh_conv3d_wgrad_bf16(const void* act, int cin_pad, int cin,
   else if (cin_pad == 8 && nout_pad == 16) e = launch_wgrad<8, 16>(a, gg, grad_stride, nx, ny, nz, nctas, partial, err_flag, s);
   else return DH_ERR_ARG;
   if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
-  wgrad_reduce_kernel<<<64, 256, 0, s>>>(partial, nctas, mt, nout_pad, cin_pad, cout, cin, dW);
+  wgrad_reduce_kernel<<<(cout * cin * 27 + 255) / 256, 256, 0, s>>>(partial, nctas, mt, nout_pad,
+                                                                    cin_pad, cout, cin, dW);
   e = cudaGetLastError();
   if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
   return DH_OK;

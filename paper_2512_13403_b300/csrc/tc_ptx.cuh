@@ -56,6 +56,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void* src, uin
       : "memory");
 }
 
+// ---- warp-wide 8x8 transposes into shared memory ---------------------------------------------
+// Four 8x8 b16 matrices, transposed on the way out: lane t holds in r[i] elements
+// (row t/4, columns 2(t%4), 2(t%4)+1) of matrix i; lane 8i+j gives the shared-memory address of
+// row j of the stored (transposed) matrix i, i.e. of column j of the held matrix.
+__device__ __forceinline__ void stmatrix_x4_trans(uint32_t row_addr, uint32_t r0, uint32_t r1,
+                                                  uint32_t r2, uint32_t r3) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(
+                   row_addr),
+               "r"(r0), "r"(r1), "r"(r2), "r"(r3)
+               : "memory");
+}
+
 // ---- proxy / tcgen05 ordering ---------------------------------------------------------------
 // Generic-proxy shared-memory writes become visible to the async proxy (tensor cores).
 __device__ __forceinline__ void fence_async_smem() {

@@ -81,3 +81,23 @@ def test_small_pair_train_evaluate_cycle():
     err2, _, _ = closure.evaluate(setup, params, norm, steps=4, seeds=(200, 201),
                                   equal_time_substeps_n=sub)
     assert err2["uncorrected"] == err["uncorrected"] and err2["corrected"] == err["corrected"]
+
+
+def test_non_finite_correction_is_reported_and_state_kept():
+    import ctypes as C
+    from paper_2512_13403_b300 import _lib
+    shape = (8, 16, 16)
+    U0 = inputs.decaying_turbulence(shape, seed=3, sigma=0.5, mach=1.0, p_sigma=0.2)
+    s = solver(shape, "f32")
+    s.init_state(to_gpu(U0, "f32"))
+    s.step(s.compute_dt())
+    before = s.get_state().clone()
+    p = torch.zeros(NPARAM, dtype=torch.float32)
+    p[-5:] = 3.0e38            # output bias b3: s * y overflows to infinity
+    p = p.cuda()               # kept alive across the call
+    norm = (C.c_float * 15)(*([0.0] * 5 + [1.0] * 5 + [10.0] * 5))
+    lib = _lib.load()
+    _lib.check(lib.dh_set_corrector(s.ctx, C.c_void_p(p.data_ptr()), norm), s.ctx)
+    assert lib.dh_correct(s.ctx) == 3   # DH_ERR_NONFINITE
+    assert torch.equal(s.get_state(), before)
+    s.step(s.compute_dt())              # the context stays usable
