@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace dh {
 
 // Status bits of the device step record.
@@ -52,10 +54,33 @@ __host__ __device__ __forceinline__ float q_sqrt(float x) {
 #endif
 }
 
+// ---- packed float32 pairs (FADD2 / FMUL2 / FFMA2 of sm_100+) ---------------------------------
+// Each lane is an IEEE round-to-nearest float32 operation, so a packed expression gives the
+// bits of the same scalar expression; packing halves the instruction count of paired work
+// (the two sides of a face, two state components).  Float32 device code only.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b in one packed instruction: fma(b, -1, a) rounds the exact difference once.
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, f2s(-1.0f), a); }
+
 // W = (rho, v, P) from U (Eq. 2).
 template <typename real>
 __host__ __device__ __forceinline__ Prim<real> cons_to_prim(real r, real mx, real my, real mz, real E,
                                                    real gm1) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (std::is_same<real, float>::value) {
+    // one reciprocal for the three velocities, paired products
+    const float ir = q_div(1.0f, r);
+    const float2 vxy = p_mul(f2(mx, my), f2s(ir));
+    const float vz = mz * ir;
+    const float2 sq = p_mul(vxy, vxy);
+    const float v2 = sq.x + sq.y + vz * vz;
+    return Prim<float>{r, vxy.x, vxy.y, vz, gm1 * (E - 0.5f * r * v2)};
+  }
+#endif
   Prim<real> w;
   w.r = r;
   w.vx = q_div(mx, r);
@@ -72,11 +97,36 @@ __host__ __device__ __forceinline__ real mc_slope(real a, real b) {
   return (a * b > real(0)) ? copysign(m, a) : real(0);
 }
 
+// mc_slope on two lanes.  2 min(|a|, |b|, |a+b|/4) equals min(2|a|, 2|b|, |a+b|/2) bit for bit:
+// scaling by powers of two is exact and commutes with min and |.|.
+__device__ __forceinline__ float2 mc_slope2(float2 a, float2 b) {
+  const float2 q = p_mul(p_add(a, b), f2s(0.25f));
+  const float2 ab = p_mul(a, b);
+  const float2 m = p_mul(f2(fminf(fminf(fabsf(a.x), fabsf(b.x)), fabsf(q.x)),
+                            fminf(fminf(fabsf(a.y), fabsf(b.y)), fabsf(q.y))),
+                         f2s(2.0f));
+  return f2(ab.x > 0.0f ? copysignf(m.x, a.x) : 0.0f, ab.y > 0.0f ? copysignf(m.y, a.y) : 0.0f);
+}
+
 // Limited slope of a cell from its two neighbours along one axis, with the positivity fallback:
 // if W +- dW/2 has rho <= 0 or P <= 0 every slope of the cell on that axis is zero.
 template <typename real>
 __host__ __device__ __forceinline__ Prim<real> limited_slope(const Prim<real>& wm, const Prim<real>& w0,
                                                     const Prim<real>& wp) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (std::is_same<real, float>::value) {
+    const float2 c01 = f2(w0.r, w0.vx), c23 = f2(w0.vy, w0.vz);
+    const float2 d01 = mc_slope2(p_sub(f2(wp.r, wp.vx), c01), p_sub(c01, f2(wm.r, wm.vx)));
+    const float2 d23 = mc_slope2(p_sub(f2(wp.vy, wp.vz), c23), p_sub(c23, f2(wm.vy, wm.vz)));
+    const float dp = mc_slope(wp.p - w0.p, w0.p - wm.p);
+    const float2 h = p_mul(f2(d01.x, dp), f2s(0.5f));        // half slopes of rho and P
+    const float2 rp = f2(w0.r, w0.p);
+    const float2 up = p_add(rp, h), dn = p_sub(rp, h);
+    const bool bad = (up.x <= 0.0f) || (up.y <= 0.0f) || (dn.x <= 0.0f) || (dn.y <= 0.0f);
+    if (bad) return Prim<float>{0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    return Prim<float>{d01.x, d01.y, d23.x, d23.y, dp};
+  }
+#endif
   Prim<real> d;
   d.r = mc_slope(wp.r - w0.r, w0.r - wm.r);
   d.vx = mc_slope(wp.vx - w0.vx, w0.vx - wm.vx);
@@ -94,6 +144,13 @@ template <typename real>
 __host__ __device__ __forceinline__ Prim<real> add_half(const Prim<real>& w, const Prim<real>& d, real s) {
   // w + s * d / 2 with s = +1 (left state of the upper face) or -1 (right state of the lower face)
   const real h = real(0.5) * s;
+#if defined(__CUDA_ARCH__)
+  if constexpr (std::is_same<real, float>::value) {
+    const float2 a = p_fma(f2(d.r, d.vx), f2s(h), f2(w.r, w.vx));
+    const float2 b = p_fma(f2(d.vy, d.vz), f2s(h), f2(w.vy, w.vz));
+    return Prim<float>{a.x, a.y, b.x, b.y, w.p + h * d.p};
+  }
+#endif
   return Prim<real>{w.r + h * d.r, w.vx + h * d.vx, w.vy + h * d.vy, w.vz + h * d.vz,
                     w.p + h * d.p};
 }
@@ -135,11 +192,68 @@ __host__ __device__ __forceinline__ Flux<real> hllc(real rL, real uL, real aL, r
   return F;
 }
 
+// hllc() for float32 with the left and right states in the two lanes of packed operations.
+__device__ __forceinline__ Flux<float> hllc_packed(float rL, float uL, float aL, float bL, float pL,
+                                                   float rR, float uR, float aR, float bR, float pR,
+                                                   float gamma, float gm1) {
+  const float2 r = f2(rL, rR), u = f2(uL, uR), pp = f2(pL, pR);
+  const float2 gp = p_mul(pp, f2s(gamma));
+  const float2 c = f2(q_sqrt(q_div(gp.x, rL)), q_sqrt(q_div(gp.y, rR)));
+  const float2 um = p_sub(u, c), upc = p_add(u, c);
+  const float SL = fminf(um.x, um.y);
+  const float SR = fmaxf(upc.x, upc.y);
+  const float2 d = p_sub(f2(SL, SR), u);            // (S_L - u_L, S_R - u_R)
+  const float2 rd = p_mul(r, d);
+  // numerator p_R - p_L + rho_L u_L d_L - rho_R u_R d_R as (rd_L u_L - p_L) - (rd_R u_R - p_R)
+  const float2 t = p_sub(p_mul(rd, u), pp);
+  const float Sstar = q_div(t.x - t.y, rd.x - rd.y);
+
+  const bool left = (SL >= 0.0f) || (Sstar >= 0.0f);
+  const bool star = !(SL >= 0.0f) && (Sstar >= 0.0f || SR > 0.0f);
+  const float rk = left ? rL : rR, uk = left ? uL : uR, ak = left ? aL : aR, bk = left ? bL : bR;
+  const float pk = left ? pL : pR, S = left ? SL : SR, dk = left ? d.x : d.y;
+
+  const float2 ua2 = p_mul(f2(uk, ak), f2(uk, ak));
+  const float E = q_div(pk, gm1) + 0.5f * rk * (ua2.x + ua2.y + bk * bk);
+  const float mass = rk * uk;
+  const float2 fna = p_fma(f2s(mass), f2(uk, ak), f2(pk, 0.0f));   // (mass u + p, mass a)
+  Flux<float> F{mass, fna.x, fna.y, mass * bk, uk * (E + pk)};
+  if (star) {
+    const float rdk = rk * dk;
+    const float coef = q_div(rdk, S - Sstar);
+    const float Es = coef * (q_div(E, rk) + (Sstar - uk) * (Sstar + q_div(pk, rdk)));
+    const float w = coef - rk;
+    const float2 f0n = p_fma(f2s(S), f2(w, coef * Sstar - mass), f2(F.f0, F.fn));
+    const float2 ft = p_fma(f2s(S * w), f2(ak, bk), f2(F.ft1, F.ft2));
+    F.f0 = f0n.x;
+    F.fn = f0n.y;
+    F.ft1 = ft.x;
+    F.ft2 = ft.y;
+    F.fe += S * (Es - E);
+  }
+  return F;
+}
+
 // HLLC flux across a face normal to `axis` (0 = x, 1 = y, 2 = z) from reconstructed
 // primitive states; returns fluxes in (rho, m_x, m_y, m_z, E) order.
 template <typename real>
 __host__ __device__ __forceinline__ void face_flux(int axis, const Prim<real>& L, const Prim<real>& R,
                                           real gamma, real gm1, real out[5]) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (std::is_same<real, float>::value) {
+    if (axis == 0) {
+      Flux<float> F = hllc_packed(L.r, L.vx, L.vy, L.vz, L.p, R.r, R.vx, R.vy, R.vz, R.p, gamma, gm1);
+      out[0] = F.f0; out[1] = F.fn; out[2] = F.ft1; out[3] = F.ft2; out[4] = F.fe;
+    } else if (axis == 1) {
+      Flux<float> F = hllc_packed(L.r, L.vy, L.vx, L.vz, L.p, R.r, R.vy, R.vx, R.vz, R.p, gamma, gm1);
+      out[0] = F.f0; out[1] = F.ft1; out[2] = F.fn; out[3] = F.ft2; out[4] = F.fe;
+    } else {
+      Flux<float> F = hllc_packed(L.r, L.vz, L.vx, L.vy, L.p, R.r, R.vz, R.vx, R.vy, R.p, gamma, gm1);
+      out[0] = F.f0; out[1] = F.ft1; out[2] = F.ft2; out[3] = F.fn; out[4] = F.fe;
+    }
+    return;
+  }
+#endif
   if (axis == 0) {
     Flux<real> F = hllc(L.r, L.vx, L.vy, L.vz, L.p, R.r, R.vx, R.vy, R.vz, R.p, gamma, gm1);
     out[0] = F.f0; out[1] = F.fn; out[2] = F.ft1; out[3] = F.ft2; out[4] = F.fe;

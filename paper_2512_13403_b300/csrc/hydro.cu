@@ -232,17 +232,48 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
     if (active) {
       const long long idx = (long long)k * plane + col;
       real u[5];
+      if constexpr (std::is_same<real, float>::value) {
+        // components (0,1) and (2,3) as packed pairs, 4 alone
+        float uin[5], un[5];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        real L = -((S.fx[c][ty][tx + 1] - S.fx[c][ty][tx]) * p.idx);
-        L -= (S.fy[c][ty + 1][tx] - S.fy[c][ty][tx]) * p.idy;
-        L -= (fz_hi[c] - fz_lo[c]) * p.idz;
-        const real uin = __ldg(p.U + c * n3 + idx);
-        if (STAGE == 1) {
-          u[c] = uin + dt * L;
-        } else {
-          const real un = __ldg(p.U0 + c * n3 + idx);
-          u[c] = real(0.5) * un + real(0.5) * (uin + dt * L);
+        for (int c = 0; c < 5; ++c) {
+          uin[c] = __ldg(p.U + c * n3 + idx);
+          if (STAGE == 2) un[c] = __ldg(p.U0 + c * n3 + idx);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c += 2) {
+          const float2 dfx = p_sub(f2(S.fx[c][ty][tx + 1], S.fx[c + 1][ty][tx + 1]),
+                                   f2(S.fx[c][ty][tx], S.fx[c + 1][ty][tx]));
+          const float2 dfy = p_sub(f2(S.fy[c][ty + 1][tx], S.fy[c + 1][ty + 1][tx]),
+                                   f2(S.fy[c][ty][tx], S.fy[c + 1][ty][tx]));
+          const float2 dfz = p_sub(f2(fz_hi[c], fz_hi[c + 1]), f2(fz_lo[c], fz_lo[c + 1]));
+          float2 L = p_mul(dfx, f2s(-p.idx));
+          L = p_fma(dfy, f2s(-p.idy), L);
+          L = p_fma(dfz, f2s(-p.idz), L);
+          float2 v = p_fma(f2s(dt), L, f2(uin[c], uin[c + 1]));
+          if (STAGE == 2) v = p_fma(f2s(0.5f), f2(un[c], un[c + 1]), p_mul(f2s(0.5f), v));
+          u[c] = v.x;
+          u[c + 1] = v.y;
+        }
+        {
+          float L = -((S.fx[4][ty][tx + 1] - S.fx[4][ty][tx]) * p.idx);
+          L -= (S.fy[4][ty + 1][tx] - S.fy[4][ty][tx]) * p.idy;
+          L -= (fz_hi[4] - fz_lo[4]) * p.idz;
+          u[4] = STAGE == 1 ? uin[4] + dt * L : 0.5f * un[4] + 0.5f * (uin[4] + dt * L);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          real L = -((S.fx[c][ty][tx + 1] - S.fx[c][ty][tx]) * p.idx);
+          L -= (S.fy[c][ty + 1][tx] - S.fy[c][ty][tx]) * p.idy;
+          L -= (fz_hi[c] - fz_lo[c]) * p.idz;
+          const real uin = __ldg(p.U + c * n3 + idx);
+          if (STAGE == 1) {
+            u[c] = uin + dt * L;
+          } else {
+            const real un = __ldg(p.U0 + c * n3 + idx);
+            u[c] = real(0.5) * un + real(0.5) * (uin + dt * L);
+          }
         }
       }
       if (STAGE == 2) {
