@@ -33,10 +33,11 @@ FWD_BYTES_STAGE2 = 60   # float32: read U^n and U1 (40 B), write U^{n+1} (20 B) 
 ADJ_BYTES_STAGE = 70    # float32 per adjoint stage launch, average of stage-2^T (read U1, lambda;
                         # write lambda_U1: 60 B) and stage-1^T (read U^n, lambda_U1, lambda;
                         # write lambda^n: 80 B)
-# DRAM bytes of one stage-2 launch at 256^3 and its warp instructions, from the ncu capture
-# summarised in profiles/stage_kernels_driven_cooling_turbulence_256cubed.md (same kernel source)
-STAGE2_DRAM_BYTES_256 = 695152128 + 312060416
-STAGE2_WARP_INSTR_256 = 794812160
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp instructions
+# (smsp__inst_executed.sum) of one stage-2 launch at 256^3, from one ncu capture of the current
+# kernel source
+STAGE2_DRAM_BYTES_256 = 693882624 + 307771392
+STAGE2_WARP_INSTR_256 = 750485248
 
 
 def _peaks():

@@ -7,43 +7,72 @@ kink the derivative is that of the branch the forward took (torch's one-sided ru
 limiter's a*b <= 0 branch has zero derivative).  Long integrations recompute each step from the
 stored states (checkpointing in its simplest form, Sec. 2.3).
 
+With sources the step is RK2, then the forcing kick with the step's field held fixed (it depends
+on the random draws only), then cooling, differentiated through the oracle's own cooling
+routine (the branch the forward took; the integer substep count carries no derivative).
+
 Pins: tests/test_oracle_adjoint.py (central finite differences, the dot-product identity with
-forward-mode products, and the exact mass invariant dL/drho_0 = 1/N^3 for L = mean(rho_final)).
+forward-mode products, and the exact mass invariant dL/drho_0 = 1/N^3 for L = mean(rho_final),
+with and without forcing and cooling).
 """
 from __future__ import annotations
 
 import torch
 
+from . import cooling as _cool
+from . import forcing as _force
 from . import hydro as _hydro
 
 
-def step_vjp(U: torch.Tensor, dt: float, lam: torch.Tensor, gamma: float, dx, a=None):
-    """lambda^n = (dU^{n+1}/dU^n)^T lambda^{n+1} for one RK2 step (+ optional fixed forcing a)."""
-    Ud = U.detach().clone().requires_grad_(True)
-    out = _hydro.rk2_step(Ud, dt, gamma, dx)
+def full_step(U: torch.Tensor, dt: float, gamma: float, dx, a=None, cooling=None) -> torch.Tensor:
+    """One step as the driver takes it without gravity: RK2 (App. A.3), then the Lie-split
+    sources in their order, the forcing kick with the fixed field a (Sec. 3.1.1) and cooling
+    (Sec. 4.3; `cooling` = dict(T_floor=, frac=, nsub_max=) or None)."""
+    U = _hydro.rk2_step(U, dt, gamma, dx)
     if a is not None:
-        kick = out.clone()
-        kick[1:4] = out[1:4] + out[0] * a * dt
-        kick[4] = out[4] + (out[1] * a[0] + out[2] * a[1] + out[3] * a[2]) * dt
-        out = kick
+        U = _force.apply_forcing(U, a, dt)
+    if cooling is not None:
+        U, _ = _cool.cool(U, dt, gamma, cooling["T_floor"], cooling.get("frac", 0.1),
+                          cooling.get("nsub_max", 1024))
+    return U
+
+
+def step_vjp(U: torch.Tensor, dt: float, lam: torch.Tensor, gamma: float, dx, a=None,
+             cooling=None):
+    """lambda^n = (dU^{n+1}/dU^n)^T lambda^{n+1} for one step (sources optional)."""
+    Ud = U.detach().clone().requires_grad_(True)
+    out = full_step(Ud, dt, gamma, dx, a, cooling)
     (g,) = torch.autograd.grad(out, Ud, grad_outputs=lam)
     return g
 
 
-def advance_vjp(U0: torch.Tensor, dts, lam_final: torch.Tensor, gamma: float, dx):
-    """lambda^0 for U^n = H_{dt_{n-1}} o ... o H_{dt_0}(U^0); states recomputed forward first."""
+def advance_vjp(U0: torch.Tensor, dts, lam_final: torch.Tensor, gamma: float, dx, fields=None,
+                cooling=None):
+    """lambda^0 for U^n = H_{n-1} o ... o H_0(U^0) (fields[n]: forcing of step n, or None);
+    states recomputed forward first."""
+    fields = fields if fields is not None else [None] * len(dts)
     states = [U0.detach().clone()]
     with torch.no_grad():
-        for dt in dts[:-1]:
-            states.append(_hydro.rk2_step(states[-1], dt, gamma, dx))
+        for n in range(len(dts) - 1):
+            states.append(full_step(states[-1], dts[n], gamma, dx, fields[n], cooling))
     lam = lam_final.clone()
     for n in reversed(range(len(dts))):
-        lam = step_vjp(states[n], dts[n], lam, gamma, dx)
+        lam = step_vjp(states[n], dts[n], lam, gamma, dx, fields[n], cooling)
     return lam
 
 
-def advance(U0: torch.Tensor, dts, gamma: float, dx) -> torch.Tensor:
+def advance(U0: torch.Tensor, dts, gamma: float, dx, fields=None, cooling=None) -> torch.Tensor:
+    fields = fields if fields is not None else [None] * len(dts)
     U = U0.clone()
-    for dt in dts:
-        U = _hydro.rk2_step(U, dt, gamma, dx)
+    for n, dt in enumerate(dts):
+        U = full_step(U, dt, gamma, dx, fields[n], cooling)
     return U
+
+
+def record(sim, nsteps: int):
+    """Runs an oracle Simulation for nsteps CFL steps; returns (dts, forcing fields per step)."""
+    dts, fields = [], []
+    for _ in range(nsteps):
+        dts.append(sim.step())
+        fields.append(sim.last_field)
+    return dts, fields

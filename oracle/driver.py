@@ -82,6 +82,7 @@ class Simulation:
         if self.ou is not None:
             self.ou.update(dt, self.nstep)
             a = self.ou.field(c.shape)
+        self.last_field = a
         U = _hydro.rk2_step(self.U, dt, c.gamma, c.dx)
         if a is not None:
             U = _force.apply_forcing(U, a, dt)

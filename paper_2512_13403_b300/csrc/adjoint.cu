@@ -16,6 +16,7 @@
 
 #include "dh_internal.h"
 #include "dh_adjoint.cuh"
+#include "dh_sources.cuh"
 
 namespace dh {
 
@@ -281,6 +282,72 @@ cudaError_t launch_stage_adjoint(const AdjointArgs<real>& a, cudaStream_t s) {
 template cudaError_t launch_stage_adjoint<float>(const AdjointArgs<float>&, cudaStream_t);
 template cudaError_t launch_stage_adjoint<double>(const AdjointArgs<double>&, cudaStream_t);
 
+// Pointwise adjoint of the sources of one step (Sec. 3.1.1 kick, then Sec. 4.3 cooling): the
+// forward is recomputed from UH (kick with the step's field a(x), then the cooling tangents), and
+//   cooling^T:  lam_rho += lam_E (cR - (1 - cE) K / rho),  lam_m += lam_E (1 - cE) v,
+//               lam_E *= cE    (K = |m|^2 / (2 rho), v = m / rho of the kicked state),
+//   kick^T:     lam_rho += dt a . lam_m,  lam_m += dt a lam_E.
+template <typename real>
+__global__ void source_adjoint_kernel(const SourceAdjArgs<real> p) {
+  const long long n3 = (long long)p.nx * p.ny * p.nz;
+  const real dt = (real)*p.dtp;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3;
+       q += (long long)gridDim.x * blockDim.x) {
+    const unsigned t1 = (unsigned)q / (unsigned)p.nx;
+    const int i = (int)((unsigned)q - t1 * (unsigned)p.nx);
+    const int j = (int)(t1 % (unsigned)p.ny), k = (int)(t1 / (unsigned)p.ny);
+    real u[5], l[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      u[c] = p.UH[c * n3 + q];
+      l[c] = p.lam[c * n3 + q];
+    }
+    real a[3] = {real(0), real(0), real(0)};
+    if (p.tab) {
+      forcing_accel(p.tab, p.tw, i, j, k, a);
+      // the kick as the stage-2 epilogue applies it (momentum before the kick in the energy)
+      const real e = (u[1] * a[0] + u[2] * a[1] + u[3] * a[2]) * dt;
+      u[1] = u[1] + u[0] * a[0] * dt;
+      u[2] = u[2] + u[0] * a[1] * dt;
+      u[3] = u[3] + u[0] * a[2] * dt;
+      u[4] = u[4] + e;
+    }
+    if (p.cooling) {
+      real cR, cE;
+      cooling_tangents(u[0], u[1], u[2], u[3], u[4], dt, p.gm1, p.t_floor, p.cool_frac,
+                       p.nsub_max, cR, cE);
+      const real ir = real(1) / u[0];
+      const real v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
+      const real K = real(0.5) * (u[1] * v0 + u[2] * v1 + u[3] * v2);
+      const real w = (real(1) - cE) * l[4];
+      l[0] += l[4] * cR - w * K * ir;
+      l[1] += w * v0;
+      l[2] += w * v1;
+      l[3] += w * v2;
+      l[4] *= cE;
+    }
+    if (p.tab) {
+      l[0] += dt * (a[0] * l[1] + a[1] * l[2] + a[2] * l[3]);
+      l[1] += dt * a[0] * l[4];
+      l[2] += dt * a[1] * l[4];
+      l[3] += dt * a[2] * l[4];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) p.lamH[c * n3 + q] = l[c];
+  }
+}
+
+template <typename real>
+cudaError_t launch_source_adjoint(const SourceAdjArgs<real>& a, cudaStream_t s) {
+  const long long n3 = (long long)a.nx * a.ny * a.nz;
+  long long blocks = (n3 + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  source_adjoint_kernel<real><<<(int)blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_source_adjoint<float>(const SourceAdjArgs<float>&, cudaStream_t);
+template cudaError_t launch_source_adjoint<double>(const SourceAdjArgs<double>&, cudaStream_t);
+
 }  // namespace dh
 
 // =============================================================================================
@@ -289,9 +356,13 @@ struct AdjointSpace {
   std::vector<void*> ckpt;   // U at steps 0, k, 2k, ...
   std::vector<void*> seg;    // segment inputs U^{m0+1..m0+k-1}
   std::vector<void*> seg1;   // segment stage-1 outputs U1^{m0..m0+k-1}
-  void* lam[3] = {nullptr, nullptr, nullptr};
+  std::vector<void*> segH;   // segment stage-2 states before the sources (forcing / cooling on)
+  void* scratch = nullptr;   // replayed output nobody reads
+  void* lam[4] = {nullptr, nullptr, nullptr, nullptr};
   double* dts = nullptr;
+  void* tabs = nullptr;      // normalised OU table of every step (96 reals each)
   int nck = 0, k = 0, nsteps = 0;
+  bool sources = false;
 };
 
 namespace dh {
@@ -301,8 +372,11 @@ void adjoint_free(dh_ctx* c) {
   for (void* p : a->ckpt) cudaFree(p);
   for (void* p : a->seg) cudaFree(p);
   for (void* p : a->seg1) cudaFree(p);
+  for (void* p : a->segH) cudaFree(p);
   for (void* p : a->lam) cudaFree(p);
+  cudaFree(a->scratch);
   cudaFree(a->dts);
+  cudaFree(a->tabs);
   delete a;
   c->adj = nullptr;
 }
@@ -312,30 +386,41 @@ using namespace dh;
 
 static cudaError_t adjoint_reserve(dh_ctx* c, int n, int k) {
   const int nck = (n + k - 1) / k;
+  const bool sources = c->cfg.forcing || c->cfg.cooling;
   AdjointSpace* a = c->adj;
-  if (a && a->nck >= nck && a->k == k && a->nsteps >= n) return cudaSuccess;
+  if (a && a->nck >= nck && a->k == k && a->nsteps >= n && a->sources == sources) return cudaSuccess;
   adjoint_free(c);
   a = new AdjointSpace();
   c->adj = a;
   a->nck = nck;
   a->k = k;
   a->nsteps = n;
+  a->sources = sources;
   cudaError_t e = cudaSuccess;
   a->ckpt.assign(nck, nullptr);
   a->seg.assign(k > 1 ? k - 1 : 0, nullptr);
   a->seg1.assign(k, nullptr);
+  a->segH.assign(sources ? k : 0, nullptr);
   for (auto& p : a->ckpt) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
   for (auto& p : a->seg) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
   for (auto& p : a->seg1) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
+  for (auto& p : a->segH) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
   for (auto& p : a->lam) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
+  if (e == cudaSuccess && sources) e = cudaMalloc(&a->scratch, c->state_bytes);
+  if (e == cudaSuccess && sources)
+    e = cudaMalloc(&a->tabs, (size_t)(n > 0 ? n : 1) * 96 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&a->dts, (size_t)(n > 0 ? n : 1) * sizeof(double));
   if (e != cudaSuccess) adjoint_free(c);
   return e;
 }
 
+// Re-runs one stage as the forward ran it.  Stage 2 with sources applies the step's forcing
+// table `tab` and cooling exactly as the fused forward kernel did, and stores the state before
+// the sources into pre_src.
 template <typename real>
 static cudaError_t replay_stage(dh_ctx* c, int stage, const void* U, const void* U0, void* out,
-                                const double* dtp) {
+                                const double* dtp, const void* tab = nullptr,
+                                void* pre_src = nullptr) {
   const dh_config& g = c->cfg;
   StageArgs<real> a;
   memset(&a, 0, sizeof(a));
@@ -345,6 +430,14 @@ static cudaError_t replay_stage(dh_ctx* c, int stage, const void* U, const void*
   a.idx = (real)(1.0 / g.dx); a.idy = (real)(1.0 / g.dy); a.idz = (real)(1.0 / g.dz);
   a.dx = (real)g.dx; a.dy = (real)g.dy; a.dz = (real)g.dz;
   a.rec = c->rec; a.dtp = dtp;
+  if (stage == 2 && pre_src) {
+    a.pre_src = (real*)pre_src;
+    a.forcing = g.forcing && tab;
+    a.ahat_norm = (const real*)tab;
+    for (int q = 0; q < 3; ++q) a.tw[q] = (const real*)c->tw[q];
+    a.cooling = g.cooling;
+    a.t_floor = (real)g.t_floor; a.cool_frac = (real)g.cool_frac; a.nsub_max = g.nsub_max;
+  }
   prof_begin(c, stage == 1 ? DH_KERNEL_STAGE1 : DH_KERNEL_STAGE2);
   cudaError_t e = launch_stage<real>(stage, a, c->stream);
   prof_end(c, 1);
@@ -382,21 +475,46 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
     const int len = (m0 + k <= n ? k : n - m0);
     // recompute the segment: inputs U^{m0+j} and stage-1 outputs U1^{m0+j}
     auto in = [&](int j) -> void* { return j == 0 ? a->ckpt[sgi] : a->seg[j - 1]; };
+    const bool src = a->sources;
+    auto tab = [&](int m) -> const void* {
+      return c->cfg.forcing ? (const void*)((const real*)a->tabs + (size_t)m * 96) : nullptr;
+    };
     for (int j = 0; j < len; ++j) {
       e = replay_stage<real>(c, 1, in(j), nullptr, a->seg1[j], a->dts + m0 + j);
       if (e != cudaSuccess) return e;
-      if (j + 1 < len) {
+      if (src) {
+        // with sources the last stage 2 is replayed too: its pre-source state is needed
+        e = replay_stage<real>(c, 2, a->seg1[j], in(j), j + 1 < len ? in(j + 1) : a->scratch,
+                               a->dts + m0 + j, tab(m0 + j), a->segH[j]);
+        if (e != cudaSuccess) return e;
+      } else if (j + 1 < len) {
         e = replay_stage<real>(c, 2, a->seg1[j], in(j), in(j + 1), a->dts + m0 + j);
         if (e != cudaSuccess) return e;
       }
     }
     for (int j = len - 1; j >= 0; --j) {
       const double* dtp = a->dts + m0 + j;
-      // stage 2: U^{n+1} = U^n/2 + (U1 + dt L(U1))/2
-      e = adjoint_stage<real>(c, a->seg1[j], lam, nullptr, lam_u1, real(0.5), real(0), real(0.5), dtp);
+      // sources: U^{n+1} = C(F(U_H)) -> lambda of U_H
+      void* lam_h = lam;
+      if (src) {
+        SourceAdjArgs<real> sa;
+        sa.lam = (const real*)lam; sa.UH = (const real*)a->segH[j]; sa.lamH = (real*)a->lam[3];
+        sa.tab = (const real*)tab(m0 + j);
+        for (int q = 0; q < 3; ++q) sa.tw[q] = (const real*)c->tw[q];
+        sa.nx = c->cfg.nx; sa.ny = c->cfg.ny; sa.nz = c->cfg.nz;
+        sa.cooling = c->cfg.cooling;
+        sa.gm1 = (real)(c->cfg.gamma - 1.0); sa.t_floor = (real)c->cfg.t_floor;
+        sa.cool_frac = (real)c->cfg.cool_frac; sa.nsub_max = c->cfg.nsub_max;
+        sa.dtp = dtp;
+        e = launch_source_adjoint<real>(sa, c->stream);
+        if (e != cudaSuccess) return e;
+        lam_h = a->lam[3];
+      }
+      // stage 2: U_H = U^n/2 + (U1 + dt L(U1))/2
+      e = adjoint_stage<real>(c, a->seg1[j], lam_h, nullptr, lam_u1, real(0.5), real(0), real(0.5), dtp);
       if (e != cudaSuccess) return e;
-      // stage 1: U1 = U^n + dt L(U^n); lambda^n also receives lambda^{n+1}/2 from stage 2
-      e = adjoint_stage<real>(c, in(j), lam_u1, lam, lam_new, real(1), real(0.5), real(1), dtp);
+      // stage 1: U1 = U^n + dt L(U^n); lambda^n also receives lambda_H/2 from stage 2
+      e = adjoint_stage<real>(c, in(j), lam_u1, lam_h, lam_new, real(1), real(0.5), real(1), dtp);
       if (e != cudaSuccess) return e;
       void* t = lam; lam = lam_new; lam_new = t;
     }
@@ -411,8 +529,8 @@ extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLd
   if (!c || !dLdU_final || !dLdU0) return DH_ERR_ARG;
   if (!c->initialized) { c->err = "state not initialised"; return DH_ERR_STATE; }
   if (n < 0 || k < 1) { c->err = "need n_steps >= 0 and ckpt_every >= 1"; return DH_ERR_ARG; }
-  if (c->cfg.forcing || c->cfg.cooling || c->cfg.gravity) {
-    c->err = "the hand adjoint covers the hydrodynamic step only (forcing, cooling, gravity off)";
+  if (c->cfg.gravity) {
+    c->err = "the hand adjoint covers hydrodynamics, forcing and cooling (gravity off)";
     return DH_ERR_ARG;
   }
   const cudaMemcpyKind h2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -433,6 +551,11 @@ extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLd
     if (e == cudaSuccess) e = c->prec == DH_F64 ? dh_enqueue_step_f64(c) : dh_enqueue_step_f32(c);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(a->dts + m, &c->rec->dt, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && c->cfg.forcing) {
+      const size_t tb = 96 * (c->prec == DH_F64 ? sizeof(double) : sizeof(float));
+      e = cudaMemcpyAsync((char*)a->tabs + (size_t)m * tb, c->ahat_norm, tb, cudaMemcpyDeviceToDevice,
+                          c->stream);
+    }
   }
   if (e != cudaSuccess) { c->err = std::string("adjoint forward: ") + cudaGetErrorString(e); return DH_ERR_CUDA; }
   dh_status st = dh_finish_steps(c);

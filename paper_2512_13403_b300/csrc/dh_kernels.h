@@ -23,6 +23,7 @@ template <typename real> struct StageArgs {
   real t_floor, cool_frac;
   int nsub_max;
   int reduce_cfl;         // accumulate the CFL minimum of the output state
+  real* pre_src;          // stage 2 (nullable): also store the state before the sources
 };
 
 template <typename real>
@@ -69,6 +70,23 @@ template <typename real> struct AdjointArgs {
   real c1, c2, beta;
   const double* dtp;
 };
+// Adjoint of the operator-split sources of one step (forcing kick, then cooling), pointwise:
+//   lamH = (dF/dU)^T (dC/dU)^T lam  at the state UH the sources were applied to.
+template <typename real> struct SourceAdjArgs {
+  const real* lam;        // lambda of the state after the sources
+  const real* UH;         // state after the RK2 step, before the sources
+  real* lamH;             // lambda of UH
+  const real* tab;        // normalised OU table of the step (nullable: no forcing)
+  const real* tw[3];      // forcing twiddles
+  int nx, ny, nz;
+  int cooling;
+  real gm1, t_floor, cool_frac;
+  int nsub_max;
+  const double* dtp;
+};
+template <typename real>
+cudaError_t launch_source_adjoint(const SourceAdjArgs<real>& a, cudaStream_t s);
+
 template <typename real>
 cudaError_t launch_stage_adjoint(const AdjointArgs<real>& a, cudaStream_t s);
 

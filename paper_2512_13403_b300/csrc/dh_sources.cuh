@@ -136,6 +136,76 @@ __device__ __forceinline__ real cooling_energy(real r, real mx, real my, real mz
   return kin + Enew;
 }
 
+// Tangents of the cooling map of one cell, (rho, E_th) -> E_th', as cooling_energy computes it:
+// cR = dE_th'/drho at fixed E_th, cE = dE_th'/dE_th.  Forward-mode along the same branches and
+// substeps; the substep count is a frozen integer.  Rules: a clamp max(E_floor, X) takes the
+// tangent of the larger argument (half of each on an exact tie); the rate -rho^2 sqrt(T),
+// T = (gamma-1) E / rho, has d(rate) = 1.5 rate/rho drho + 0.5 rate/E dE above the floor and is
+// zero at or below it.  A cell that does not cool is the identity (cR = 0, cE = 1).
+template <typename real>
+__device__ __forceinline__ void cooling_tangents(real r, real mx, real my, real mz, real E, real dt,
+                                                 real gm1, real T_floor, real frac, int nsub_max,
+                                                 real& cR, real& cE) {
+  const real ir = q_div(real(1), r);
+  const real kin = real(0.5) * (mx * mx + my * my + mz * mz) * ir;
+  const real Eth = E - kin;
+  const real Efl = q_div(r * T_floor, gm1);
+  cR = real(0);
+  cE = real(1);
+  if (!(Eth > Efl)) return;
+  const real dfl = q_div(T_floor, gm1);   // dE_floor/drho
+  const real r2 = r * r;
+  // clamp rule for max(E_floor, X) with tangent (xr, xe)
+  auto clamp_t = [&](real X, real xr, real xe, real& tr, real& te) {
+    if (X > Efl) { tr = xr; te = xe; }
+    else if (X < Efl) { tr = dfl; te = real(0); }
+    else { tr = real(0.5) * (xr + dfl); te = real(0.5) * xe; }
+  };
+  const real Ed0 = -r2 * q_sqrt(gm1 * Eth * ir);
+  const real tcool = q_div(Eth, -Ed0);
+  const real raw = ceil(q_div(dt, frac * tcool));
+  real nsub = raw;
+  if (!(raw <= real(nsub_max))) nsub = real(nsub_max);
+  if (!(nsub >= real(1))) nsub = real(1);
+  if (nsub == real(1)) {
+    const real d0r = real(1.5) * Ed0 * ir, d0e = real(0.5) * q_div(Ed0, Eth);
+    const real X = Eth + dt * Ed0;
+    real pr, pe;
+    clamp_t(X, dt * d0r, real(1) + dt * d0e, pr, pe);
+    const real Ep = fmax(Efl, X);
+    real Edp = real(0), dpr = real(0), dpe = real(0);
+    if (Ep > Efl) {
+      Edp = -r2 * q_sqrt(gm1 * Ep * ir);
+      const real g = real(0.5) * q_div(Edp, Ep);
+      dpr = real(1.5) * Edp * ir + g * pr;
+      dpe = g * pe;
+    }
+    const real Y = Eth + real(0.5) * dt * (Ed0 + Edp);
+    clamp_t(Y, real(0.5) * dt * (d0r + dpr), real(1) + real(0.5) * dt * (d0e + dpe), cR, cE);
+  } else {
+    const real dts = q_div(dt, nsub);
+    const int n = (int)nsub;
+    real Es = Eth, sr = real(0), se = real(1);
+    for (int q = 0; q < n; ++q) {
+      real ed = real(0), er = real(0), ee = real(0);
+      if (Es > Efl) {
+        ed = -r2 * q_sqrt(gm1 * Es * ir);
+        const real g = real(0.5) * q_div(ed, Es);
+        er = real(1.5) * ed * ir + g * sr;
+        ee = g * se;
+      }
+      const real X = Es + ed * dts;
+      real tr, te;
+      clamp_t(X, sr + dts * er, se + dts * ee, tr, te);
+      Es = fmax(Efl, X);
+      sr = tr;
+      se = te;
+    }
+    cR = sr;
+    cE = se;
+  }
+}
+
 template <typename real>
 __device__ __forceinline__ real cfl_time(real r, real mx, real my, real mz, real E, real gamma,
                                          real gm1, real dx, real dy, real dz) {

@@ -277,6 +277,10 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
         }
       }
       if (STAGE == 2) {
+        if (p.pre_src) {
+#pragma unroll
+          for (int c = 0; c < 5; ++c) p.pre_src[c * n3 + idx] = u[c];
+        }
         if (forcing) {
           // a = 2 Re sum_{n_x} B_{n_x} exp(2 pi i n_x x~)  (Sec. 3.1.1)
           real a[3];

@@ -169,11 +169,56 @@ def test_autograd_function_backward():
     assert torch.allclose(U0.grad, ref, rtol=1e-12, atol=1e-14)
 
 
-def test_adjoint_rejects_sources():
+def test_adjoint_rejects_gravity():
     from paper_2512_13403_b300._lib import DH_ERR_ARG, DhError
     shape = (8, 8, 8)
-    s = solver(shape, "f64", cooling=True)
-    s.init_state(to_gpu(inputs.cooling_box(shape), "f64"))
+    s = solver(shape, "f64", gravity=True)
+    s.init_state(to_gpu(inputs.self_gravitating_box(shape, seed=5, sigma=0.5), "f64"))
     with pytest.raises(DhError) as e:
         s.adjoint_advance(2, 1, to_gpu(np.zeros((5,) + shape), "f64"))
     assert e.value.status == DH_ERR_ARG
+
+
+def _source_case(shape, steps, seed=3):
+    from oracle import driver
+    U0 = inputs.decaying_turbulence(shape, seed=seed, sigma=0.5, mach=0.8, p_sigma=0.3)
+    nz, ny, nx = shape
+    cfg = driver.Config(shape=shape, gamma=G, forcing=True, ou_seed=11, cooling=True,
+                        t_floor=0.05, cool_frac=0.02)
+    sim = driver.Simulation(cfg, torch.from_numpy(U0))
+    dts, fields = oadj.record(sim, steps)
+    return U0, dts, fields, dict(T_floor=0.05, frac=0.02, nsub_max=1024)
+
+
+@pytest.mark.parametrize("shape,n,k", [((16, 16, 16), 5, 2), ((12, 10, 20), 4, 4)])
+def test_fp64_with_forcing_and_cooling_matches_oracle(shape, n, k):
+    """Adjoint through RK2, the forcing kick (field of each step fixed) and subcycled cooling."""
+    U0, dts, fields, cool = _source_case(shape, n)
+    lam = np.random.default_rng(4).standard_normal((5,) + shape)
+    s = solver(shape, "f64", forcing=True, ou_seed=11, cooling=True, t_floor=0.05, cool_frac=0.02)
+    s.init_state(to_gpu(U0, "f64"))
+    g = s.adjoint_advance(n, k, to_gpu(lam, "f64"))
+    ref = oadj.advance_vjp(torch.from_numpy(U0), dts, torch.from_numpy(lam), G, _dx(shape), fields, cool)
+    assert _rel(g, ref) < 1e-10
+    assert float((g.cpu() - ref).abs().max() / ref.abs().max()) < 1e-9
+
+
+def test_sources_mass_invariant_and_fp32():
+    shape = (16, 16, 16)
+    U0, dts, fields, cool = _source_case(shape, 4, seed=6)
+    kw = dict(forcing=True, ou_seed=11, cooling=True, t_floor=0.05, cool_frac=0.02)
+    N3 = int(np.prod(shape))
+    lam = np.zeros((5,) + shape)
+    lam[0] = 1.0 / N3
+    s = solver(shape, "f64", **kw)
+    s.init_state(to_gpu(U0, "f64"))
+    g = s.adjoint_advance(4, 2, to_gpu(lam, "f64")).cpu()
+    assert float((g[0] - 1.0 / N3).abs().max()) < 1e-15
+    assert float(g[1:].abs().max()) < 1e-15
+    # float32 against the float64 oracle
+    w = np.random.default_rng(7).standard_normal((5,) + shape)
+    s32 = solver(shape, "f32", **kw)
+    s32.init_state(to_gpu(U0, "f32"))
+    g32 = s32.adjoint_advance(4, 2, to_gpu(w, "f32"))
+    ref = oadj.advance_vjp(torch.from_numpy(U0), dts, torch.from_numpy(w), G, _dx(shape), fields, cool)
+    assert _rel(g32, ref) < 1e-3
