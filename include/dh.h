@@ -163,8 +163,13 @@ dh_status dh_solve_poisson(dh_ctx* ctx, const void* rho, int on_device);
    every step frozen at the value the forward took, App. A.4): given the current state U^0,
    runs the forward n_steps CFL steps (storing U every `ckpt_every` steps, Sec. 2.3
    checkpointing), then returns dL/dU^0 in dLdU0 for dL/dU^{n} = dLdU_final.  Both buffers use
-   the state layout and precision; the context state is left at U^{n}.  Hydrodynamics only:
-   DH_ERR_ARG if forcing, cooling or gravity is on. */
+   the state layout and precision; the context is left at U^{n} and steps on as if no adjoint
+   had run.  The operator-split sources are differentiated too: the OU kick with each step's
+   field held fixed (Sec. 3.1.1; the draws do not depend on U), self-gravity (Sec. 5: the kick
+   transposed pointwise, then the potential's share through one more Poisson solve with the
+   symmetric seven-point operator, to mg_tol) and cooling (Sec. 4.3: forward-mode tangents of
+   the trapezoid or subcycled update along the branches the forward took).  DH_ERR_MG_NOCONV if
+   an adjoint Poisson solve misses mg_tol. */
 dh_status dh_adjoint_advance(dh_ctx* ctx, int n_steps, int ckpt_every, const void* dLdU_final,
                              void* dLdU0, int on_device);
 

@@ -8,8 +8,10 @@ limiter's a*b <= 0 branch has zero derivative).  Long integrations recompute eac
 stored states (checkpointing in its simplest form, Sec. 2.3).
 
 With sources the step is RK2, then the forcing kick with the step's field held fixed (it depends
-on the random draws only), then cooling, differentiated through the oracle's own cooling
-routine (the branch the forward took; the integer substep count carries no derivative).
+on the random draws only), then self-gravity with the exact Poisson solution of the seven-point
+operator (the limit of the V-cycles; differentiated through the FFT solve), then cooling,
+differentiated through the oracle's own cooling routine (the branch the forward took; the
+integer substep count carries no derivative).
 
 Pins: tests/test_oracle_adjoint.py (central finite differences, the dot-product identity with
 forward-mode products, and the exact mass invariant dL/drho_0 = 1/N^3 for L = mean(rho_final),
@@ -22,15 +24,22 @@ import torch
 from . import cooling as _cool
 from . import forcing as _force
 from . import hydro as _hydro
+from . import multigrid as _mg
 
 
-def full_step(U: torch.Tensor, dt: float, gamma: float, dx, a=None, cooling=None) -> torch.Tensor:
-    """One step as the driver takes it without gravity: RK2 (App. A.3), then the Lie-split
-    sources in their order, the forcing kick with the fixed field a (Sec. 3.1.1) and cooling
-    (Sec. 4.3; `cooling` = dict(T_floor=, frac=, nsub_max=) or None)."""
+def full_step(U: torch.Tensor, dt: float, gamma: float, dx, a=None, cooling=None,
+              gravity=None) -> torch.Tensor:
+    """One step as the driver takes it: RK2 (App. A.3), then the Lie-split sources in their
+    order, the forcing kick with the fixed field a (Sec. 3.1.1), self-gravity (Sec. 5:
+    `gravity` = dict(four_pi_G=) or None, phi the exact solution of the seven-point Poisson
+    problem, which converged V-cycles reproduce to their tolerance) and cooling (Sec. 4.3;
+    `cooling` = dict(T_floor=, frac=, nsub_max=) or None)."""
     U = _hydro.rk2_step(U, dt, gamma, dx)
     if a is not None:
         U = _force.apply_forcing(U, a, dt)
+    if gravity is not None:
+        phi = _mg.fft_solve(_mg.poisson_source(U[0], gravity["four_pi_G"]), dx[0])
+        U = _mg.gravity_source(U, phi, dt, dx[0])
     if cooling is not None:
         U, _ = _cool.cool(U, dt, gamma, cooling["T_floor"], cooling.get("frac", 0.1),
                           cooling.get("nsub_max", 1024))
@@ -38,34 +47,35 @@ def full_step(U: torch.Tensor, dt: float, gamma: float, dx, a=None, cooling=None
 
 
 def step_vjp(U: torch.Tensor, dt: float, lam: torch.Tensor, gamma: float, dx, a=None,
-             cooling=None):
+             cooling=None, gravity=None):
     """lambda^n = (dU^{n+1}/dU^n)^T lambda^{n+1} for one step (sources optional)."""
     Ud = U.detach().clone().requires_grad_(True)
-    out = full_step(Ud, dt, gamma, dx, a, cooling)
+    out = full_step(Ud, dt, gamma, dx, a, cooling, gravity)
     (g,) = torch.autograd.grad(out, Ud, grad_outputs=lam)
     return g
 
 
 def advance_vjp(U0: torch.Tensor, dts, lam_final: torch.Tensor, gamma: float, dx, fields=None,
-                cooling=None):
+                cooling=None, gravity=None):
     """lambda^0 for U^n = H_{n-1} o ... o H_0(U^0) (fields[n]: forcing of step n, or None);
     states recomputed forward first."""
     fields = fields if fields is not None else [None] * len(dts)
     states = [U0.detach().clone()]
     with torch.no_grad():
         for n in range(len(dts) - 1):
-            states.append(full_step(states[-1], dts[n], gamma, dx, fields[n], cooling))
+            states.append(full_step(states[-1], dts[n], gamma, dx, fields[n], cooling, gravity))
     lam = lam_final.clone()
     for n in reversed(range(len(dts))):
-        lam = step_vjp(states[n], dts[n], lam, gamma, dx, fields[n], cooling)
+        lam = step_vjp(states[n], dts[n], lam, gamma, dx, fields[n], cooling, gravity)
     return lam
 
 
-def advance(U0: torch.Tensor, dts, gamma: float, dx, fields=None, cooling=None) -> torch.Tensor:
+def advance(U0: torch.Tensor, dts, gamma: float, dx, fields=None, cooling=None,
+            gravity=None) -> torch.Tensor:
     fields = fields if fields is not None else [None] * len(dts)
     U = U0.clone()
     for n, dt in enumerate(dts):
-        U = full_step(U, dt, gamma, dx, fields[n], cooling)
+        U = full_step(U, dt, gamma, dx, fields[n], cooling, gravity)
     return U
 
 

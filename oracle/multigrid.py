@@ -23,7 +23,8 @@ Readings:
 
 Pins: tests/test_oracle_multigrid.py (single discrete Fourier mode against its exact discrete
 solution F / lambda, FFT solve of the same operator, pseudo-inverse coarse solve, residual
-reduction per cycle, restriction/prolongation identities on constants and linear fields).
+reduction per cycle, restriction/prolongation identities on constants and linear fields; the
+FFT solve itself against a single mode and against converged V-cycles).
 """
 from __future__ import annotations
 
@@ -144,6 +145,19 @@ def solve(F: torch.Tensor, h: float, phi0=None, tol=1e-6, max_cycles=30, npre=2,
         cycles += 1
         res = relative_residual(phi, F, h)
     return phi, cycles, res, res <= tol
+
+
+def fft_solve(F: torch.Tensor, h: float) -> torch.Tensor:
+    """Exact A phi = F - <F>, <phi> = 0, for the same seven-point operator: on a periodic grid
+    the DFT diagonalises A, with eigenvalue -(4/h^2) sum_a sin^2(pi k_a / n_a) for mode k.  A
+    plain library FFT, differentiable; the reference the multigrid iterates converge to."""
+    nz, ny, nx = F.shape
+    s = lambda n: torch.sin(math.pi * torch.fft.fftfreq(n, d=1.0 / n, dtype=torch.float64) / n) ** 2
+    lam = -(4.0 / h ** 2) * (s(nz)[:, None, None] + s(ny)[None, :, None] + s(nx)[None, None, :])
+    keep = torch.ones_like(lam)
+    keep[0, 0, 0] = 0.0
+    lam = torch.where(keep > 0, lam, torch.ones_like(lam))
+    return torch.fft.ifftn(torch.fft.fftn(F) * keep / lam).real
 
 
 def poisson_source(rho: torch.Tensor, four_pi_G: float) -> torch.Tensor:

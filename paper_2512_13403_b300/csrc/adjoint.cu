@@ -305,11 +305,26 @@ __global__ void source_adjoint_kernel(const SourceAdjArgs<real> p) {
     real a[3] = {real(0), real(0), real(0)};
     if (p.tab) {
       forcing_accel(p.tab, p.tw, i, j, k, a);
-      // the kick as the stage-2 epilogue applies it (momentum before the kick in the energy)
+      // the kick as the forward applies it (momentum before the kick in the energy)
       const real e = (u[1] * a[0] + u[2] * a[1] + u[3] * a[2]) * dt;
       u[1] = u[1] + u[0] * a[0] * dt;
       u[2] = u[2] + u[0] * a[1] * dt;
       u[3] = u[3] + u[0] * a[2] * dt;
+      u[4] = u[4] + e;
+    }
+    real gv[3] = {real(0), real(0), real(0)}, mF[3] = {u[1], u[2], u[3]};
+    if (p.phi) {
+      // g = -grad phi (central differences) and the gravity kick, as gravity_sources_kernel
+      const double* ph = p.phi;
+      const long long row = (long long)k * p.ny;
+      gv[0] = (real)(-(ph[(row + j) * p.nx + wrap(i + 1, p.nx)] - ph[(row + j) * p.nx + wrap(i - 1, p.nx)]) * p.i2h);
+      gv[1] = (real)(-(ph[(row + wrap(j + 1, p.ny)) * p.nx + i] - ph[(row + wrap(j - 1, p.ny)) * p.nx + i]) * p.i2h);
+      gv[2] = (real)(-(ph[((long long)wrap(k + 1, p.nz) * p.ny + j) * p.nx + i] -
+                       ph[((long long)wrap(k - 1, p.nz) * p.ny + j) * p.nx + i]) * p.i2h);
+      const real e = (u[1] * gv[0] + u[2] * gv[1] + u[3] * gv[2]) * dt;
+      u[1] = u[1] + u[0] * gv[0] * dt;
+      u[2] = u[2] + u[0] * gv[1] * dt;
+      u[3] = u[3] + u[0] * gv[2] * dt;
       u[4] = u[4] + e;
     }
     if (p.cooling) {
@@ -325,6 +340,16 @@ __global__ void source_adjoint_kernel(const SourceAdjArgs<real> p) {
       l[2] += w * v1;
       l[3] += w * v2;
       l[4] *= cE;
+    }
+    if (p.phi) {
+      // gravity kick^T, and dL/dg = dt (rho lam_m + m lam_E) with m before the kick
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        p.h[d * n3 + q] = (double)dt * ((double)u[0] * (double)l[1 + d] + (double)mF[d] * (double)l[4]);
+      l[0] += dt * (gv[0] * l[1] + gv[1] * l[2] + gv[2] * l[3]);
+      l[1] += dt * gv[0] * l[4];
+      l[2] += dt * gv[1] * l[4];
+      l[3] += dt * gv[2] * l[4];
     }
     if (p.tab) {
       l[0] += dt * (a[0] * l[1] + a[1] * l[2] + a[2] * l[3]);
@@ -348,6 +373,34 @@ cudaError_t launch_source_adjoint(const SourceAdjArgs<real>& a, cudaStream_t s) 
 template cudaError_t launch_source_adjoint<float>(const SourceAdjArgs<float>&, cudaStream_t);
 template cudaError_t launch_source_adjoint<double>(const SourceAdjArgs<double>&, cudaStream_t);
 
+// psi = dL/dphi = sum_a (h_a(i + e_a) - h_a(i - e_a)) / (2 dx): the transpose of g = -grad phi.
+__global__ void gravity_psi_kernel(const double* __restrict__ h, int nx, int ny, int nz, double i2h,
+                                   double* __restrict__ psi) {
+  const long long n3 = (long long)nx * ny * nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3;
+       q += (long long)gridDim.x * blockDim.x) {
+    const unsigned t1 = (unsigned)q / (unsigned)nx;
+    const int i = (int)((unsigned)q - t1 * (unsigned)nx);
+    const int j = (int)(t1 % (unsigned)ny), k = (int)(t1 / (unsigned)ny);
+    const long long row = (long long)k * ny;
+    const double hx = h[(row + j) * nx + wrap(i + 1, nx)] - h[(row + j) * nx + wrap(i - 1, nx)];
+    const double hy = h[n3 + (row + wrap(j + 1, ny)) * nx + i] - h[n3 + (row + wrap(j - 1, ny)) * nx + i];
+    const double hz = h[2 * n3 + ((long long)wrap(k + 1, nz) * ny + j) * nx + i] -
+                      h[2 * n3 + ((long long)wrap(k - 1, nz) * ny + j) * nx + i];
+    psi[q] = (hx + hy + hz) * i2h;
+  }
+}
+
+// lam_rho += 4 pi G w: the density's share through the Poisson source F = 4 pi G (rho - <rho>)
+// (w = dL/dF has zero mean, so the mean subtraction adds nothing).
+template <typename real>
+__global__ void add_density_adjoint_kernel(real* __restrict__ lam, const double* __restrict__ w,
+                                           long long n3, double four_pi_G) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3;
+       q += (long long)gridDim.x * blockDim.x)
+    lam[q] = (real)((double)lam[q] + four_pi_G * w[q]);
+}
+
 }  // namespace dh
 
 // =============================================================================================
@@ -361,8 +414,12 @@ struct AdjointSpace {
   void* lam[4] = {nullptr, nullptr, nullptr, nullptr};
   double* dts = nullptr;
   void* tabs = nullptr;      // normalised OU table of every step (96 reals each)
+  // gravity: the potential at every checkpoint (warm start of the replay), of every segment
+  // step, dL/dg, dL/dphi, dL/dF, and the forward's final potential
+  std::vector<double*> ckPhi, segPhi;
+  double *hbuf = nullptr, *psi = nullptr, *wsol = nullptr, *phi_keep = nullptr;
   int nck = 0, k = 0, nsteps = 0;
-  bool sources = false;
+  bool sources = false, gravity = false;
 };
 
 namespace dh {
@@ -377,6 +434,12 @@ void adjoint_free(dh_ctx* c) {
   cudaFree(a->scratch);
   cudaFree(a->dts);
   cudaFree(a->tabs);
+  for (double* p : a->ckPhi) cudaFree(p);
+  for (double* p : a->segPhi) cudaFree(p);
+  cudaFree(a->hbuf);
+  cudaFree(a->psi);
+  cudaFree(a->wsol);
+  cudaFree(a->phi_keep);
   delete a;
   c->adj = nullptr;
 }
@@ -386,9 +449,12 @@ using namespace dh;
 
 static cudaError_t adjoint_reserve(dh_ctx* c, int n, int k) {
   const int nck = (n + k - 1) / k;
-  const bool sources = c->cfg.forcing || c->cfg.cooling;
+  const bool gravity = c->cfg.gravity;
+  const bool sources = c->cfg.forcing || c->cfg.cooling || gravity;
   AdjointSpace* a = c->adj;
-  if (a && a->nck >= nck && a->k == k && a->nsteps >= n && a->sources == sources) return cudaSuccess;
+  if (a && a->nck >= nck && a->k == k && a->nsteps >= n && a->sources == sources &&
+      a->gravity == gravity)
+    return cudaSuccess;
   adjoint_free(c);
   a = new AdjointSpace();
   c->adj = a;
@@ -396,7 +462,19 @@ static cudaError_t adjoint_reserve(dh_ctx* c, int n, int k) {
   a->k = k;
   a->nsteps = n;
   a->sources = sources;
+  a->gravity = gravity;
   cudaError_t e = cudaSuccess;
+  if (gravity) {
+    const size_t pb = (size_t)c->n3 * sizeof(double);
+    a->ckPhi.assign(nck, nullptr);
+    a->segPhi.assign(k, nullptr);
+    for (auto& p : a->ckPhi) if (e == cudaSuccess) e = cudaMalloc((void**)&p, pb);
+    for (auto& p : a->segPhi) if (e == cudaSuccess) e = cudaMalloc((void**)&p, pb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&a->hbuf, 3 * pb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&a->psi, pb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&a->wsol, pb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&a->phi_keep, pb);
+  }
   a->ckpt.assign(nck, nullptr);
   a->seg.assign(k > 1 ? k - 1 : 0, nullptr);
   a->seg1.assign(k, nullptr);
@@ -479,10 +557,27 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
     auto tab = [&](int m) -> const void* {
       return c->cfg.forcing ? (const void*)((const real*)a->tabs + (size_t)m * 96) : nullptr;
     };
+    const size_t pb = (size_t)c->n3 * sizeof(double);
+    if (a->gravity) {
+      // the potential the forward started this segment from (warm start of its first solve)
+      e = cudaMemcpyAsync(mg_phi64(c), a->ckPhi[sgi], pb, cudaMemcpyDeviceToDevice, c->stream);
+      if (e != cudaSuccess) return e;
+    }
     for (int j = 0; j < len; ++j) {
       e = replay_stage<real>(c, 1, in(j), nullptr, a->seg1[j], a->dts + m0 + j);
       if (e != cudaSuccess) return e;
-      if (src) {
+      if (a->gravity) {
+        // stage 2 without fused sources, then the Poisson solve and forcing -> gravity ->
+        // cooling exactly as the forward step took them
+        void* out = j + 1 < len ? in(j + 1) : a->scratch;
+        e = replay_stage<real>(c, 2, a->seg1[j], in(j), out, a->dts + m0 + j);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(a->segH[j], out, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = gravity_sources<real>(c, out, tab(m0 + j), a->dts + m0 + j, false);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(a->segPhi[j], mg_phi64(c), pb, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+      } else if (src) {
         // with sources the last stage 2 is replayed too: its pre-source state is needed
         e = replay_stage<real>(c, 2, a->seg1[j], in(j), j + 1 < len ? in(j + 1) : a->scratch,
                                a->dts + m0 + j, tab(m0 + j), a->segH[j]);
@@ -498,6 +593,7 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
       void* lam_h = lam;
       if (src) {
         SourceAdjArgs<real> sa;
+        memset(&sa, 0, sizeof(sa));
         sa.lam = (const real*)lam; sa.UH = (const real*)a->segH[j]; sa.lamH = (real*)a->lam[3];
         sa.tab = (const real*)tab(m0 + j);
         for (int q = 0; q < 3; ++q) sa.tw[q] = (const real*)c->tw[q];
@@ -506,9 +602,26 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
         sa.gm1 = (real)(c->cfg.gamma - 1.0); sa.t_floor = (real)c->cfg.t_floor;
         sa.cool_frac = (real)c->cfg.cool_frac; sa.nsub_max = c->cfg.nsub_max;
         sa.dtp = dtp;
+        sa.phi = a->gravity ? a->segPhi[j] : nullptr;
+        sa.h = a->hbuf;
+        sa.i2h = 1.0 / (2.0 * c->cfg.dx);
         e = launch_source_adjoint<real>(sa, c->stream);
         if (e != cudaSuccess) return e;
         lam_h = a->lam[3];
+        if (a->gravity) {
+          // the potential's share: psi = dL/dphi, A w = psi - <psi>, lam_rho += 4 pi G w
+          const long long n3 = c->n3;
+          const int blocks = (int)((n3 + 255) / 256 < 148 * 8 ? (n3 + 255) / 256 : 148 * 8);
+          gravity_psi_kernel<<<blocks, 256, 0, c->stream>>>(a->hbuf, c->cfg.nx, c->cfg.ny, c->cfg.nz,
+                                                            1.0 / (2.0 * c->cfg.dx), a->psi);
+          e = cudaGetLastError();
+          if (e == cudaSuccess) e = mg_solve_rhs(c, a->psi, a->wsol);
+          if (e != cudaSuccess) return e;
+          add_density_adjoint_kernel<real><<<blocks, 256, 0, c->stream>>>((real*)lam_h, a->wsol, n3,
+                                                                          c->cfg.four_pi_G);
+          e = cudaGetLastError();
+          if (e != cudaSuccess) return e;
+        }
       }
       // stage 2: U_H = U^n/2 + (U1 + dt L(U1))/2
       e = adjoint_stage<real>(c, a->seg1[j], lam_h, nullptr, lam_u1, real(0.5), real(0), real(0.5), dtp);
@@ -529,10 +642,6 @@ extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLd
   if (!c || !dLdU_final || !dLdU0) return DH_ERR_ARG;
   if (!c->initialized) { c->err = "state not initialised"; return DH_ERR_STATE; }
   if (n < 0 || k < 1) { c->err = "need n_steps >= 0 and ckpt_every >= 1"; return DH_ERR_ARG; }
-  if (c->cfg.gravity) {
-    c->err = "the hand adjoint covers hydrodynamics, forcing and cooling (gravity off)";
-    return DH_ERR_ARG;
-  }
   const cudaMemcpyKind h2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind d2h = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (n == 0) {
@@ -546,8 +655,12 @@ extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLd
   AdjointSpace* a = c->adj;
   // forward sweep with checkpoints; the dt of every step is recorded on the device
   for (int m = 0; m < n && e == cudaSuccess; ++m) {
-    if (m % k == 0)
+    if (m % k == 0) {
       e = cudaMemcpyAsync(a->ckpt[m / k], c->U[c->cur], c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess && a->gravity)
+        e = cudaMemcpyAsync(a->ckPhi[m / k], mg_phi64(c), (size_t)c->n3 * sizeof(double),
+                            cudaMemcpyDeviceToDevice, c->stream);
+    }
     if (e == cudaSuccess) e = c->prec == DH_F64 ? dh_enqueue_step_f64(c) : dh_enqueue_step_f32(c);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(a->dts + m, &c->rec->dt, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
@@ -560,13 +673,34 @@ extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLd
   if (e != cudaSuccess) { c->err = std::string("adjoint forward: ") + cudaGetErrorString(e); return DH_ERR_CUDA; }
   dh_status st = dh_finish_steps(c);
   if (st != DH_OK) return st;
+  const size_t pb = (size_t)c->n3 * sizeof(double);
+  if (a->gravity) {
+    // keep the forward's final potential (the next step's warm start); start dL/dF at zero
+    e = cudaMemcpyAsync(a->phi_keep, mg_phi64(c), pb, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a->wsol, 0, pb, c->stream);
+  }
   // backward sweep
-  e = cudaMemcpyAsync(a->lam[1], dLdU_final, c->state_bytes, h2d, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(a->lam[1], dLdU_final, c->state_bytes, h2d, c->stream);
   if (e == cudaSuccess)
     e = c->prec == DH_F64 ? adjoint_backward<double>(c, n, k, a->lam[1])
                           : adjoint_backward<float>(c, n, k, a->lam[1]);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dLdU0, a->lam[0], c->state_bytes, d2h, c->stream);
+  if (e == cudaSuccess && a->gravity)
+    e = cudaMemcpyAsync(mg_phi64(c), a->phi_keep, pb, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) { c->err = std::string("adjoint backward: ") + cudaGetErrorString(e); return DH_ERR_CUDA; }
+  if (a->gravity) {
+    // an adjoint Poisson solve that missed mg_tol raised the flag in the step record
+    StepRecord r;
+    e = cudaMemcpy(&r, c->rec, sizeof(r), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return DH_ERR_CUDA; }
+    if (r.flags & FLAG_MG_NOCONV) {
+      r.flags &= ~FLAG_MG_NOCONV;
+      r.fail_step = -1;
+      cudaMemcpy(c->rec, &r, sizeof(r), cudaMemcpyHostToDevice);
+      c->err = "a multigrid solve of the adjoint did not reach mg_tol within mg_max_cycles";
+      return DH_ERR_MG_NOCONV;
+    }
+  }
   return DH_OK;
 }

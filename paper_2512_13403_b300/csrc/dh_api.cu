@@ -302,7 +302,7 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed) {
   prof_end(c, 1);
   if (e != cudaSuccess) return e;
   if (!fuse) {
-    e = gravity_sources<real>(c, Unew);
+    e = gravity_sources<real>(c, Unew, nullptr, &c->rec->dt, true);
     if (e != cudaSuccess) return e;
   }
   c->cur = 1 - c->cur;

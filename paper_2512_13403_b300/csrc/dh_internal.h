@@ -56,7 +56,14 @@ void mg_setup_host(dh_ctx* c);
 cudaError_t mg_reset(dh_ctx* c);
 void mg_free(dh_ctx* c);
 double* mg_phi64(dh_ctx* c);   // the float64 potential (warm start of the next solve)
-template <typename real> cudaError_t gravity_sources(dh_ctx* c, void* Ustar);
+// Poisson solve on the density of Ustar, then forcing -> gravity -> cooling in place.  tab:
+// normalised OU table (null: the context's current one); dtp: the step's dt on the device;
+// in_step: a step of the context (records flags and the CFL minimum) rather than a replay.
+template <typename real>
+cudaError_t gravity_sources(dh_ctx* c, void* Ustar, const void* tab, const double* dtp,
+                            bool in_step);
+// A x = rhs - <rhs> by V-cycles (x: warm start and result, <x> = 0), for the adjoint.
+cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, double* x);
 
 // adjoint.cu
 void adjoint_free(dh_ctx* c);

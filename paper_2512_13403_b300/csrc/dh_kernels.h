@@ -70,8 +70,9 @@ template <typename real> struct AdjointArgs {
   real c1, c2, beta;
   const double* dtp;
 };
-// Adjoint of the operator-split sources of one step (forcing kick, then cooling), pointwise:
-//   lamH = (dF/dU)^T (dC/dU)^T lam  at the state UH the sources were applied to.
+// Adjoint of the operator-split sources of one step (forcing kick, gravity kick, cooling),
+// pointwise: lamH = (dF/dU)^T (dG/dU)^T (dC/dU)^T lam at the state UH the sources were applied
+// to, and with gravity h = dL/dg (the potential's part is added by a Poisson solve).
 template <typename real> struct SourceAdjArgs {
   const real* lam;        // lambda of the state after the sources
   const real* UH;         // state after the RK2 step, before the sources
@@ -83,6 +84,9 @@ template <typename real> struct SourceAdjArgs {
   real gm1, t_floor, cool_frac;
   int nsub_max;
   const double* dtp;
+  const double* phi;      // potential of the step (nullable: no gravity)
+  double* h;              // gravity: dL/dg, 3 planes (output)
+  double i2h;             // 1 / (2 dx)
 };
 template <typename real>
 cudaError_t launch_source_adjoint(const SourceAdjArgs<real>& a, cudaStream_t s);

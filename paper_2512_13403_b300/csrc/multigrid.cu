@@ -375,29 +375,14 @@ static void vcycle(dh_ctx* c, int l) {
   c->launches += 2 * (g.mg_pre + g.mg_post) + 2;
 }
 
-// Solves for phi64 from the density plane of U (type real); returns false on a CUDA error.
-template <typename real>
-cudaError_t mg_solve(dh_ctx* c, const real* rho, bool in_step) {
+// V-cycles on phi64 for the source in F64 (|F|^2 already in scal[1]) until the relative
+// residual reaches mg_tol, then the gauge <phi> = 0.  Marks FLAG_MG_NOCONV on failure.
+static cudaError_t mg_iterate(dh_ctx* c) {
   MG* m = c->mg;
   const dh_config& g = c->cfg;
   cudaStream_t s = c->stream;
   const long long n = m->cells[0];
   const int nx = m->n[0][0], ny = m->n[0][1], nz = m->n[0][2];
-  if (in_step) {
-    // nothing to solve after a fatal failure earlier in this batch (the stages skipped)
-    unsigned fl = 0;
-    cudaError_t e = cudaMemcpyAsync(&fl, &c->rec->flags, sizeof(fl), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return e;
-    if (fl & FATAL_FLAGS) return cudaSuccess;
-  }
-  prof_begin(c, DH_KERNEL_MG);
-  sum_partial_kernel<real><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rho, n, m->partials);
-  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
-  poisson_source_kernel<real><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rho, n, m->scal + 0, g.four_pi_G,
-                                                                 m->F64, m->partials);
-  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
-  prof_end(c, 4);
   const double ih2 = 1.0 / (m->h[0] * m->h[0]);
   int cycles = 0;
   double rel = 0.0;
@@ -412,7 +397,7 @@ cudaError_t mg_solve(dh_ctx* c, const real* rho, bool in_step) {
     cudaError_t e = cudaMemcpyAsync(h, m->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    if (!(h[1] > 0.0)) {  // uniform density: phi = 0
+    if (!(h[1] > 0.0)) {  // zero source: phi = 0
       zero64_kernel<<<grid_for(n), 256, 0, s>>>(m->phi64, n);
       c->launches += 1;
       ok = true;
@@ -444,13 +429,59 @@ cudaError_t mg_solve(dh_ctx* c, const real* rho, bool in_step) {
   return cudaGetLastError();
 }
 
+// Solves for phi64 from the density plane of U (type real).
+template <typename real>
+cudaError_t mg_solve(dh_ctx* c, const real* rho, bool in_step) {
+  MG* m = c->mg;
+  const dh_config& g = c->cfg;
+  cudaStream_t s = c->stream;
+  const long long n = m->cells[0];
+  if (in_step) {
+    // nothing to solve after a fatal failure earlier in this batch (the stages skipped)
+    unsigned fl = 0;
+    cudaError_t e = cudaMemcpyAsync(&fl, &c->rec->flags, sizeof(fl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (fl & FATAL_FLAGS) return cudaSuccess;
+  }
+  prof_begin(c, DH_KERNEL_MG);
+  sum_partial_kernel<real><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rho, n, m->partials);
+  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
+  poisson_source_kernel<real><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rho, n, m->scal + 0, g.four_pi_G,
+                                                                 m->F64, m->partials);
+  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
+  prof_end(c, 4);
+  return mg_iterate(c);
+}
+
+// A x = rhs - <rhs> for a float64 right-hand side; x (float64, n cells) is the warm start and
+// the result, with <x> = 0.  The solve the adjoint of the gravity step needs (A is symmetric).
+cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, double* x) {
+  MG* m = c->mg;
+  cudaStream_t s = c->stream;
+  const long long n = m->cells[0];
+  prof_begin(c, DH_KERNEL_MG);
+  sum_partial_kernel<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rhs, n, m->partials);
+  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
+  poisson_source_kernel<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rhs, n, m->scal + 0, 1.0,
+                                                                   m->F64, m->partials);
+  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
+  prof_end(c, 4);
+  double* keep = m->phi64;
+  m->phi64 = x;
+  cudaError_t e = mg_iterate(c);
+  m->phi64 = keep;
+  return e;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Sources after the hydro update when gravity is on: forcing -> gravity -> cooling (the Lie
 // splitting order), then the positivity/finite checks and the CFL minimum for the next step.
 template <typename real>
 __global__ void __launch_bounds__(256)
 gravity_sources_kernel(real* __restrict__ U, const double* __restrict__ phi, int nx, int ny,
-                       int nz, double i2h, StepRecord* rec, int forcing,
+                       int nz, double i2h, StepRecord* rec, const double* dtp, int in_step,
+                       int forcing,
                        const real* __restrict__ ah, const real* tw0, const real* tw1,
                        const real* tw2, int cooling, real gamma, real gm1, real t_floor,
                        real frac, int nsub_max, real dx, real dy, real dz) {
@@ -459,7 +490,7 @@ gravity_sources_kernel(real* __restrict__ U, const double* __restrict__ phi, int
   if (threadIdx.x == 0) s_skip = *((volatile unsigned*)&rec->flags) & FATAL_FLAGS;
   __syncthreads();
   if (s_skip) return;
-  const real dt = (real)rec->dt;
+  const real dt = (real)*dtp;
   const long long plane = (long long)nx * ny;
   const long long n3 = plane * nz;
   const real* tw[3] = {tw0, tw1, tw2};
@@ -511,6 +542,7 @@ gravity_sources_kernel(real* __restrict__ U, const double* __restrict__ phi, int
 #pragma unroll
     for (int c = 0; c < 5; ++c) U[c * n3 + q] = u[c];
   }
+  if (!in_step) return;   // a replay (adjoint) leaves the step record alone
   if (flags) {
     atomicOr(&rec->flags, flags);
     if (flags & FATAL_FLAGS) atomicCAS(&rec->fail_step, -1, (int)(rec->nstep - 1));
@@ -527,24 +559,26 @@ gravity_sources_kernel(real* __restrict__ U, const double* __restrict__ phi, int
 }
 
 template <typename real>
-cudaError_t gravity_sources(dh_ctx* c, void* Ustar) {
+cudaError_t gravity_sources(dh_ctx* c, void* Ustar, const void* tab, const double* dtp,
+                            bool in_step) {
   const dh_config& g = c->cfg;
   real* U = (real*)Ustar;
-  // skip when an earlier failure is pending (the stage kernels already skipped)
-  cudaError_t e = mg_solve<real>(c, U, true);
+  // in a step, skip when an earlier failure is pending (the stage kernels already skipped)
+  cudaError_t e = mg_solve<real>(c, U, in_step);
   if (e != cudaSuccess) return e;
   const long long n = c->n3;
   prof_begin(c, DH_KERNEL_SOURCES);
   gravity_sources_kernel<real><<<grid_for(n), 256, 0, c->stream>>>(
-      U, c->mg->phi64, g.nx, g.ny, g.nz, 1.0 / (2.0 * g.dx), c->rec, g.forcing,
-      (const real*)c->ahat_norm, (const real*)c->tw[0], (const real*)c->tw[1],
-      (const real*)c->tw[2], g.cooling, (real)g.gamma, (real)(g.gamma - 1.0), (real)g.t_floor,
-      (real)g.cool_frac, g.nsub_max, (real)g.dx, (real)g.dy, (real)g.dz);
+      U, c->mg->phi64, g.nx, g.ny, g.nz, 1.0 / (2.0 * g.dx), c->rec, dtp, in_step ? 1 : 0,
+      g.forcing, (const real*)(tab ? tab : c->ahat_norm), (const real*)c->tw[0],
+      (const real*)c->tw[1], (const real*)c->tw[2], g.cooling, (real)g.gamma,
+      (real)(g.gamma - 1.0), (real)g.t_floor, (real)g.cool_frac, g.nsub_max, (real)g.dx,
+      (real)g.dy, (real)g.dz);
   prof_end(c, 1);
   return cudaGetLastError();
 }
-template cudaError_t gravity_sources<float>(dh_ctx*, void*);
-template cudaError_t gravity_sources<double>(dh_ctx*, void*);
+template cudaError_t gravity_sources<float>(dh_ctx*, void*, const void*, const double*, bool);
+template cudaError_t gravity_sources<double>(dh_ctx*, void*, const void*, const double*, bool);
 
 }  // namespace dh
 

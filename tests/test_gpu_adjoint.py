@@ -169,14 +169,59 @@ def test_autograd_function_backward():
     assert torch.allclose(U0.grad, ref, rtol=1e-12, atol=1e-14)
 
 
-def test_adjoint_rejects_gravity():
-    from paper_2512_13403_b300._lib import DH_ERR_ARG, DhError
-    shape = (8, 8, 8)
-    s = solver(shape, "f64", gravity=True)
-    s.init_state(to_gpu(inputs.self_gravitating_box(shape, seed=5, sigma=0.5), "f64"))
-    with pytest.raises(DhError) as e:
-        s.adjoint_advance(2, 1, to_gpu(np.zeros((5,) + shape), "f64"))
-    assert e.value.status == DH_ERR_ARG
+def _gravity_case(shape, steps, forcing_cooling, seed=5):
+    from oracle import driver
+    U0 = inputs.decaying_turbulence(shape, seed=seed, sigma=0.5, mach=0.8, p_sigma=0.3)
+    fc = dict(forcing=True, ou_seed=11, cooling=True, t_floor=0.05, cool_frac=0.02) if forcing_cooling else {}
+    kw = dict(gravity=True, four_pi_G=1.0, mg_tol=1e-12, mg_max_cycles=60, **fc)
+    cfg = driver.Config(shape=shape, gamma=G, **kw)
+    sim = driver.Simulation(cfg, torch.from_numpy(U0))
+    dts, fields = oadj.record(sim, steps)
+    cool = dict(T_floor=0.05, frac=0.02, nsub_max=1024) if forcing_cooling else None
+    return U0, dts, fields, cool, dict(four_pi_G=1.0), kw
+
+
+@pytest.mark.parametrize("forcing_cooling", [False, True])
+def test_fp64_with_gravity_matches_oracle(forcing_cooling):
+    """Adjoint through self-gravity: the gravity kick transposed pointwise, then the potential's
+    share through a second Poisson solve (the operator is symmetric)."""
+    shape, n, k = (16, 16, 16), 4, 2
+    U0, dts, fields, cool, grav, kw = _gravity_case(shape, n, forcing_cooling)
+    lam = np.random.default_rng(5).standard_normal((5,) + shape)
+    s = solver(shape, "f64", **kw)
+    s.init_state(to_gpu(U0, "f64"))
+    g = s.adjoint_advance(n, k, to_gpu(lam, "f64"))
+    ref = oadj.advance_vjp(torch.from_numpy(U0), dts, torch.from_numpy(lam), G, _dx(shape),
+                           fields if forcing_cooling else None, cool, grav)
+    assert _rel(g, ref) < 1e-9
+    assert float((g.cpu() - ref).abs().max() / ref.abs().max()) < 1e-8
+
+
+def test_gravity_mass_invariant_fp32_and_state_kept():
+    shape = (16, 16, 16)
+    U0, dts, fields, cool, grav, kw = _gravity_case(shape, 4, True, seed=6)
+    N3 = int(np.prod(shape))
+    lam = np.zeros((5,) + shape)
+    lam[0] = 1.0 / N3
+    s = solver(shape, "f64", **kw)
+    s.init_state(to_gpu(U0, "f64"))
+    g = s.adjoint_advance(4, 2, to_gpu(lam, "f64")).cpu()
+    assert float((g[0] - 1.0 / N3).abs().max()) < 1e-14
+    assert float(g[1:].abs().max()) < 1e-14
+    # the context continues from the forward's final state and potential as if no adjoint ran
+    s.advance(1)
+    ref = solver(shape, "f64", **kw)
+    ref.init_state(to_gpu(U0, "f64"))
+    ref.advance(5)
+    assert torch.equal(s.get_state().cpu(), ref.get_state().cpu())
+    # float32 against the float64 oracle
+    w = np.random.default_rng(8).standard_normal((5,) + shape)
+    kw32 = dict(kw, mg_tol=1e-6, mg_max_cycles=30)
+    s32 = solver(shape, "f32", **kw32)
+    s32.init_state(to_gpu(U0, "f32"))
+    g32 = s32.adjoint_advance(4, 2, to_gpu(w, "f32"))
+    ref32 = oadj.advance_vjp(torch.from_numpy(U0), dts, torch.from_numpy(w), G, _dx(shape), fields, cool, grav)
+    assert _rel(g32, ref32) < 1e-3
 
 
 def _source_case(shape, steps, seed=3):

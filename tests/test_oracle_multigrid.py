@@ -94,3 +94,24 @@ def test_gravity_source_on_linear_potential():
     assert torch.allclose(out[1], U[1] + 2.0 * gx[None, None, :] * 0.01, rtol=1e-14)
     assert torch.allclose(out[4], U[4] + U[1] * gx[None, None, :] * 0.01, rtol=1e-14)
     assert torch.equal(out[2], U[2]) and torch.equal(out[0], U[0])
+
+
+def test_fft_solve_single_mode_and_multigrid():
+    nz, ny, nx = 8, 16, 32
+    h = 1.0 / 32
+    shape = (nz, ny, nx)
+    x = (torch.arange(nx, dtype=torch.float64) + 0.5) / nx
+    y = (torch.arange(ny, dtype=torch.float64) + 0.5) / ny
+    z = (torch.arange(nz, dtype=torch.float64) + 0.5) / nz
+    m = (3, 1, 2)   # (x, y, z) wave numbers
+    F = torch.cos(2 * math.pi * (m[0] * x[None, None, :] + m[1] * y[None, :, None] + m[2] * z[:, None, None]))
+    lam = -(4.0 / h ** 2) * (math.sin(math.pi * m[0] / nx) ** 2 + math.sin(math.pi * m[1] / ny) ** 2 +
+                             math.sin(math.pi * m[2] / nz) ** 2)
+    phi = mg.fft_solve(F, h)
+    assert float((phi - F / lam).abs().max()) < 1e-12 * float((F / lam).abs().max())
+    rho = torch.from_numpy(inputs.lognormal_density((16, 16, 16), 1.0, 8))
+    F2 = mg.poisson_source(rho, 1.0)
+    phi_mg, _, _, ok = mg.solve(F2, 1.0 / 16, tol=1e-12, max_cycles=60)
+    assert ok
+    phi_f = mg.fft_solve(F2, 1.0 / 16)
+    assert float((phi_mg - phi_f).abs().max()) < 1e-10 * float(phi_f.abs().max())
