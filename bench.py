@@ -292,6 +292,8 @@ def run_ours(args):
                                         "issue slots x median SM clock sampled during the run"}
     if not args.no_adjoint:
         line["adjoint"] = adjoint_leg(args, stream)
+    if not args.no_selfgrav:
+        line["self_gravitating"] = selfgrav_leg(args, stream)
     if not args.no_corrector:
         line["corrector"] = corrector_leg(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -302,20 +304,14 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def adjoint_leg(args, stream):
-    """Hand adjoint through n steps of 256^3 decaying turbulence (hydro only), checkpoints every k:
-    cell-updates/s = N^3 n / wall time of dh_adjoint_advance (forward, recompute and backward)."""
+def _adjoint_run(cfg, U0, steps, k, stream, lam_scale):
+    """Times one dh_adjoint_advance (forward, recompute, backward) after a short warm-up."""
     import torch
-    from paper_2512_13403_b300 import inputs
-    from paper_2512_13403_b300.solver import Config, Solver
-    n = args.grid
-    shape = (n, n, n)
-    steps, k = args.adj_steps, args.adj_ckpt
+    from paper_2512_13403_b300.solver import Solver
     with torch.cuda.stream(stream):
-        s = Solver(Config(shape=shape, precision="f32"), stream=stream)
-        U0 = torch.from_numpy(inputs.decaying_turbulence(shape, seed=2, sigma=0.5, mach=2.0)).float().cuda()
+        s = Solver(cfg, stream=stream)
         lam = torch.zeros_like(U0)
-        lam[0] = 2.0 / n ** 3  # gradient of a mean-squared density misfit (scale only)
+        lam[0] = lam_scale  # gradient of a mean-squared density misfit (scale only)
         s.init_state(U0)
         s.adjoint_advance(2, 1, lam)  # warm-up: allocations and first launches
         s.init_state(U0)
@@ -330,16 +326,93 @@ def adjoint_leg(args, stream):
         na, ta = s.profile_read("adjoint")
         s.profile(False)
         s.close()
+    return ms, na, ta
+
+
+def adjoint_leg(args, stream):
+    """Hand adjoint through n steps at 256^3, checkpoints every k: cell-updates/s = N^3 n / wall
+    time of dh_adjoint_advance (forward, recompute and backward).  Main line: decaying turbulence
+    (hydro only); also the driven cooling box (forcing + cooling) and, self-gravitating, the
+    same with multigrid gravity."""
+    import torch
+    from paper_2512_13403_b300 import inputs
+    from paper_2512_13403_b300.solver import Config
+    n = args.grid
+    shape = (n, n, n)
+    steps, k = args.adj_steps, args.adj_ckpt
+    U0 = torch.from_numpy(inputs.decaying_turbulence(shape, seed=2, sigma=0.5, mach=2.0)).float().cuda()
+    ms, na, ta = _adjoint_run(Config(shape=shape, precision="f32"), U0, steps, k, stream, 2.0 / n ** 3)
     peak, kind = _peaks()
     adj_ms = ta / max(na, 1)
     ach = ADJ_BYTES_STAGE * n ** 3 / (adj_ms * 1e-3) / 1e9
-    return {"value": n ** 3 * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "ckpt_every": k,
+    out = {"value": n ** 3 * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "ckpt_every": k,
+           "ms_per_step": ms / steps,
+           "workload": f"decaying turbulence {n}^3 (lognormal rho sigma=0.5, k^-4 velocity, rms Mach 2), "
+                       "hydro only, float32",
+           "roofline": {"bound": "hbm", "kernel": "stage_adjoint_kernel<float>", "achieved": ach,
+                        "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": kind,
+                        "traffic": None, "avg_launch_ms": adj_ms, "launches": na}}
+    if not args.adj_sources:
+        return out
+    Ub = torch.from_numpy(inputs.cooling_box(shape)).float().cuda()
+    src = dict(forcing=True, cooling=True, t_floor=0.05)
+    ms2, _, _ = _adjoint_run(Config(shape=shape, precision="f32", **src), Ub, steps, k, stream, 2.0 / n ** 3)
+    Ug = torch.from_numpy(inputs.self_gravitating_box(shape, seed=5, sigma=1.0)).float().cuda()
+    ms3, _, _ = _adjoint_run(Config(shape=shape, precision="f32", gravity=True, **src), Ug, steps, k,
+                             stream, 2.0 / n ** 3)
+    out["with_sources"] = {
+        "driven_cooling": {"value": n ** 3 * steps / (ms2 * 1e-3), "unit": UNIT, "ms_per_step": ms2 / steps,
+                           "workload": f"driven cooling turbulence {n}^3 (OU forcing + cooling), float32"},
+        "self_gravitating": {"value": n ** 3 * steps / (ms3 * 1e-3), "unit": UNIT, "ms_per_step": ms3 / steps,
+                             "workload": f"self-gravitating driven cooling box {n}^3 (lognormal rho sigma=1, "
+                                         "multigrid gravity tol 1e-6 + OU forcing + cooling), float32"}}
+    return out
+
+
+def selfgrav_leg(args, stream):
+    """Self-gravitating driven cooling turbulence (multigrid gravity, RBGS 2+2 V-cycles to a
+    relative residual of 1e-6, OU forcing, cooling) at 1024^3 float32: cell-updates/s over the
+    timed steps after one warm-up step (which also takes the cold-start Poisson solve)."""
+    import torch
+    from paper_2512_13403_b300 import inputs
+    from paper_2512_13403_b300.solver import Config, Solver
+    n = args.sg_grid
+    shape = (n, n, n)
+    cfg = Config(shape=shape, precision="f32", forcing=True, cooling=True, t_floor=0.05,
+                 gravity=True, four_pi_G=1.0, mg_tol=1e-6, mg_max_cycles=30)
+    with torch.cuda.stream(stream):
+        s = Solver(cfg, stream=stream)
+        U0 = inputs.self_gravitating_box_device(shape, seed=5, sigma=1.0)
+        s.init_state(U0)
+        del U0
+        torch.cuda.empty_cache()
+        s.advance(1)
+        s.profile(True)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.advance(args.sg_steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        nmg, tmg = s.profile_read("mg")
+        n1, t1 = s.profile_read("stage1")
+        n2, t2 = s.profile_read("stage2")
+        nsrc, tsrc = s.profile_read("sources")
+        cycles, res = s.mg_stats()
+        s.profile(False)
+        t_end, _ = s.time()
+        s.close()
+    steps = args.sg_steps
+    return {"value": n ** 3 * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
             "ms_per_step": ms / steps,
-            "workload": f"decaying turbulence {n}^3 (lognormal rho sigma=0.5, k^-4 velocity, rms Mach 2), "
-                        "hydro only, float32",
-            "roofline": {"bound": "hbm", "kernel": "stage_adjoint_kernel<float>", "achieved": ach,
-                         "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": kind,
-                         "traffic": None, "avg_launch_ms": adj_ms, "launches": na}}
+            "device_ms_per_step": {"stage1": t1 / steps, "stage2": t2 / steps, "multigrid": tmg / steps,
+                                   "sources": tsrc / steps},
+            "sim_time_after": t_end,
+            "multigrid_last_solve": {"cycles": cycles, "relative_residual": res},
+            "workload": f"self-gravitating driven cooling turbulence {n}^3 periodic, float32 "
+                        "(lognormal rho sigma=1 k^-2, v=0, P=0.6; 4 pi G=1, multigrid RBGS 2+2 "
+                        "V-cycles to 1e-6 with FP64 norms; OU forcing + cooling)"}
 
 
 def corrector_leg(args):
@@ -384,7 +457,12 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adj-steps", type=int, default=20)
     ap.add_argument("--adj-ckpt", type=int, default=10)
+    ap.add_argument("--no-adj-sources", dest="adj_sources", action="store_false",
+                    help="skip the adjoint timings with forcing, cooling and gravity")
     ap.add_argument("--no-corrector", action="store_true")
+    ap.add_argument("--no-selfgrav", action="store_true", help="skip the 1024^3 self-gravitating leg")
+    ap.add_argument("--sg-grid", type=int, default=1024)
+    ap.add_argument("--sg-steps", type=int, default=20)
     ap.add_argument("--corr-runs", type=int, default=20)
     ap.add_argument("--corr-snapshots", type=int, default=100)
     ap.add_argument("--corr-epochs", type=int, default=4)

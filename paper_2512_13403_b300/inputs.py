@@ -149,3 +149,39 @@ def double_sod(nx, ny=4, nz=4, gamma=1.4, left=(1.0, 0.0, 1.0), right=(0.125, 0.
     P = np.where(inner, left[2], right[2])
     z = np.zeros(shape)
     return prim_to_state(rho, vx, z, z, P, gamma)
+
+
+def lognormal_density_device(shape, sigma, seed, device="cuda"):
+    """lognormal_density's recipe on the GPU in float32 for grids too large for the host
+    (1024^3): white noise from torch's seeded generator (not numpy's stream), the |n|^-1
+    amplitude (power |n|^-2) on 1 <= |n| < min(N)/2 through a real FFT, unit variance,
+    rho = exp(sigma g) / <exp(sigma g)>."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    nz, ny, nx = shape
+    F = torch.fft.rfftn(torch.randn(shape, generator=gen, device=device, dtype=torch.float32))
+    kz = torch.fft.fftfreq(nz, d=1.0 / nz, device=device)
+    ky = torch.fft.fftfreq(ny, d=1.0 / ny, device=device)
+    kx = torch.fft.rfftfreq(nx, d=1.0 / nx, device=device)
+    kmag = torch.sqrt(kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2)
+    band = (kmag >= 1.0) & (kmag < min(shape) / 2.0)
+    F *= torch.where(band, kmag.clamp(min=1.0) ** -1.0, torch.zeros_like(kmag))
+    del kmag, band
+    g = torch.fft.irfftn(F, s=shape)
+    del F
+    g -= g.double().mean().float()
+    g /= g.double().pow(2).mean().sqrt().float()
+    e = torch.exp(sigma * g)
+    del g
+    return e / e.double().mean().float()
+
+
+def self_gravitating_box_device(shape, seed=5, sigma=1.0, P0=0.6, gamma=5.0 / 3.0, device="cuda"):
+    """self_gravitating_box on the GPU (float32 state, 5 planes): lognormal density from
+    lognormal_density_device, fluid at rest, pressure P0."""
+    import torch
+    U = torch.zeros((5,) + tuple(shape), dtype=torch.float32, device=device)
+    U[0] = lognormal_density_device(shape, sigma, seed, device)
+    U[4] = P0 / (gamma - 1.0)
+    return U

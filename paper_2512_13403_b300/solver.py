@@ -168,6 +168,13 @@ class Solver:
                                               C.byref(cyc), C.byref(res)))
         return out, cyc.value, res.value
 
+    def mg_stats(self):
+        """(V-cycles, final relative residual) of the last Poisson solve."""
+        cyc = C.c_int()
+        res = C.c_double()
+        self._check(self.lib.dh_get_potential(self.ctx, None, 1, C.byref(cyc), C.byref(res)))
+        return cyc.value, res.value
+
     def solve_poisson(self, rho):
         """Standalone multigrid solve for one density plane; returns (phi, cycles, rel_res)."""
         if isinstance(rho, torch.Tensor):
