@@ -70,6 +70,7 @@ __host__ __device__ __forceinline__ void hllc_vjp(real rL, real uL, real aL, rea
   const real num = pR - pL + rL * uL * dL - rR * uR * dR;
   const real den = rL * dL - rR * dR;
   const real Ss = q_div(num, den);
+  const real iden = q_div(real(1), den);
   const bool left = (SL >= real(0)) || (Ss >= real(0));
   const bool star = !(SL >= real(0)) && (Ss >= real(0) || SR > real(0));
   const real r = left ? rL : rR, u = left ? uL : uR, a = left ? aL : aR, b = left ? bL : bR;
@@ -84,12 +85,17 @@ __host__ __device__ __forceinline__ void hllc_vjp(real rL, real uL, real aL, rea
   b_ += gt2 * mass;
   p_ += gn + ge * u;
   real E_ = ge * u;
+  // reciprocals shared by the reverse sweep (quotients of the working precision, as forward)
+  const real ir = q_div(real(1), r);
   if (star) {
     const real den2 = S - Ss;
-    const real coef = q_div(r * d, den2);
-    const real w = q_div(p, r * d);
+    const real rd = r * d;
+    const real ird = q_div(real(1), rd);
+    const real iden2 = q_div(real(1), den2);
+    const real coef = rd * iden2;
+    const real w = p * ird;
     const real Z = Ss + w;
-    const real Q = q_div(E, r) + (Ss - u) * Z;
+    const real Q = E * ir + (Ss - u) * Z;
     const real Es = coef * Q;
     S_ += g0 * (coef - r) + gn * (coef * Ss - mass) + gt1 * (coef * a - r * a) +
           gt2 * (coef * b - r * b) + ge * (Es - E);
@@ -103,21 +109,21 @@ __host__ __device__ __forceinline__ void hllc_vjp(real rL, real uL, real aL, rea
     const real Es_ = S * ge;
     coef_ += Es_ * Q;
     const real Q_ = Es_ * coef;
-    E_ += Q_ / r;
-    r_ -= Q_ * E / (r * r);
+    E_ += Q_ * ir;
+    r_ -= Q_ * E * ir * ir;
     Ss_ += Q_ * (Z + (Ss - u));
     u_ -= Q_ * Z;
     const real w_ = Q_ * (Ss - u);
-    p_ += w_ / (r * d);
-    r_ -= w_ * p / (r * r * d);
-    d_ -= w_ * p / (r * d * d);
-    r_ += coef_ * d / den2;
-    d_ += coef_ * r / den2;
-    const real dc = coef_ * r * d / (den2 * den2);
+    p_ += w_ * ird;
+    r_ -= w_ * w * ir;        // d(p / (r d))/dr = -w / r
+    d_ -= w_ * w * r * ird;   // d(p / (r d))/dd = -w / d
+    r_ += coef_ * d * iden2;
+    d_ += coef_ * r * iden2;
+    const real dc = coef_ * coef * iden2;   // coef_ r d / den2^2
     S_ -= dc;
     Ss_ += dc;
   }
-  p_ += E_ / gm1;
+  p_ += E_ * q_div(real(1), gm1);
   r_ += E_ * real(0.5) * (u * u + a * a + b * b);
   u_ += E_ * r * u;
   a_ += E_ * r * a;
@@ -132,8 +138,8 @@ __host__ __device__ __forceinline__ void hllc_vjp(real rL, real uL, real aL, rea
   if (left) { rL_ = r_; uL_ = u_; aL_ = a_; bL_ = b_; pL_ = p_; SL_ = S_; }
   else      { rR_ = r_; uR_ = u_; aR_ = a_; bR_ = b_; pR_ = p_; SR_ = S_; }
   if (star) {
-    const real num_ = Ss_ / den;
-    const real den_ = -Ss_ * Ss / den;
+    const real num_ = Ss_ * iden;
+    const real den_ = -num_ * Ss;
     pR_ += num_;
     pL_ -= num_;
     rL_ += num_ * uL * dL + den_ * dL;
@@ -154,10 +160,12 @@ __host__ __device__ __forceinline__ void hllc_vjp(real rL, real uL, real aL, rea
   if (yL > yR) { uL_ += SR_; cL_ += SR_; }
   else if (yR > yL) { uR_ += SR_; cR_ += SR_; }
   else { uL_ += real(0.5) * SR_; cL_ += real(0.5) * SR_; uR_ += real(0.5) * SR_; cR_ += real(0.5) * SR_; }
-  pL_ += cL_ * gamma / (real(2) * cL * rL);
-  rL_ -= cL_ * cL / (real(2) * rL);
-  pR_ += cR_ * gamma / (real(2) * cR * rR);
-  rR_ -= cR_ * cR / (real(2) * rR);
+  // c = sqrt(gamma p / rho): dc/dp = gamma / (2 c rho), dc/drho = -c / (2 rho)
+  const real hL = real(0.5) * q_div(cL_, rL), hR = real(0.5) * q_div(cR_, rR);
+  pL_ += hL * q_div(gamma, cL);
+  rL_ -= hL * cL;
+  pR_ += hR * q_div(gamma, cR);
+  rR_ -= hR * cR;
   gL[0] = rL_; gL[1] = uL_; gL[2] = aL_; gL[3] = bL_; gL[4] = pL_;
   gR[0] = rR_; gR[1] = uR_; gR[2] = aR_; gR[3] = bR_; gR[4] = pR_;
 }
