@@ -109,8 +109,8 @@ dh_status dh_get_time(dh_ctx* ctx, double* t, long long* nstep);
 /* File checkpoint of the context (the restart the paper's pure update H(U^n, theta^n) of
    Sec. 2.1 implies: theta = time, step count, OU table, gravity warm start).  dh_save writes
    the current state, t, dt, the step count (which also numbers the OU draws), the OU tables
-   and hold flag, and with gravity the float64 potential that warm-starts the next solve, with a
-   checksum; it settles pending steps first.  dh_load reads such a file into a context created
+   and hold flag, and with gravity the potential that warm-starts the next solve (its float-float
+   words: n hi floats then n lo floats), with a checksum; it settles pending steps first.  dh_load reads such a file into a context created
    with the same grid, precision, physics switches, OU seed, gamma and cell widths (else
    DH_ERR_ARG, context unchanged), after which stepping continues bit for bit as in the saved
    context.  DH_ERR_ARG for unreadable, truncated or corrupted files.  Both synchronise. */
@@ -148,7 +148,8 @@ dh_status dh_downsample(const float* U_fine, int nx, int ny, int nz, int factor,
                         void* cuda_stream);
 
 /* Gravitational potential phi of the last solve (one plane, float64, state index order),
-   and the cycles / final relative residual of that solve (nullable outputs). */
+   and the cycles / final relative residual of that solve (nullable outputs).  The context holds
+   phi in float-float (about 48 significant bits); phi_out receives hi + lo rounded to float64. */
 dh_status dh_get_potential(dh_ctx* ctx, double* phi_out, int on_device, int* cycles,
                            double* rel_residual);
 

@@ -238,7 +238,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
     // ---- primitive recovery transposed, stage combination, store ------------------------------
     if (active) {
       const Prim<real> w = ring_prim(S, s0, ty + 3, tx + 3);
-      const real ir = real(1) / w.r;
+      const real ir = q_div(real(1), w.r);
       const real v2 = w.vx * w.vx + w.vy * w.vy + w.vz * w.vz;
       real gU[5];
       gU[0] = gW[0] - (gW[1] * w.vx + gW[2] * w.vy + gW[3] * w.vz) * ir + gW[4] * gm1 * real(0.5) * v2;
@@ -315,12 +315,7 @@ __global__ void source_adjoint_kernel(const SourceAdjArgs<real> p) {
     real gv[3] = {real(0), real(0), real(0)}, mF[3] = {u[1], u[2], u[3]};
     if (p.phi) {
       // g = -grad phi (central differences) and the gravity kick, as gravity_sources_kernel
-      const double* ph = p.phi;
-      const long long row = (long long)k * p.ny;
-      gv[0] = (real)(-(ph[(row + j) * p.nx + wrap(i + 1, p.nx)] - ph[(row + j) * p.nx + wrap(i - 1, p.nx)]) * p.i2h);
-      gv[1] = (real)(-(ph[(row + wrap(j + 1, p.ny)) * p.nx + i] - ph[(row + wrap(j - 1, p.ny)) * p.nx + i]) * p.i2h);
-      gv[2] = (real)(-(ph[((long long)wrap(k + 1, p.nz) * p.ny + j) * p.nx + i] -
-                       ph[((long long)wrap(k - 1, p.nz) * p.ny + j) * p.nx + i]) * p.i2h);
+      potential_gradient(p.phi, p.nx, p.ny, p.nz, i, j, k, (real)p.i2h, gv[0], gv[1], gv[2]);
       const real e = (u[1] * gv[0] + u[2] * gv[1] + u[3] * gv[2]) * dt;
       u[1] = u[1] + u[0] * gv[0] * dt;
       u[2] = u[2] + u[0] * gv[1] * dt;
@@ -331,7 +326,7 @@ __global__ void source_adjoint_kernel(const SourceAdjArgs<real> p) {
       real cR, cE;
       cooling_tangents(u[0], u[1], u[2], u[3], u[4], dt, p.gm1, p.t_floor, p.cool_frac,
                        p.nsub_max, cR, cE);
-      const real ir = real(1) / u[0];
+      const real ir = q_div(real(1), u[0]);
       const real v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
       const real K = real(0.5) * (u[1] * v0 + u[2] * v1 + u[3] * v2);
       const real w = (real(1) - cE) * l[4];
@@ -393,12 +388,13 @@ __global__ void gravity_psi_kernel(const double* __restrict__ h, int nx, int ny,
 
 // lam_rho += 4 pi G w: the density's share through the Poisson source F = 4 pi G (rho - <rho>)
 // (w = dL/dF has zero mean, so the mean subtraction adds nothing).
+// w is float-float (planar).
 template <typename real>
-__global__ void add_density_adjoint_kernel(real* __restrict__ lam, const double* __restrict__ w,
-                                           long long n3, double four_pi_G) {
+__global__ void add_density_adjoint_kernel(real* __restrict__ lam, const float* __restrict__ w,
+                                           long long n3, real four_pi_G) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3;
        q += (long long)gridDim.x * blockDim.x)
-    lam[q] = (real)((double)lam[q] + four_pi_G * w[q]);
+    lam[q] = lam[q] + four_pi_G * ((real)w[q] + (real)w[n3 + q]);
 }
 
 }  // namespace dh
@@ -416,8 +412,9 @@ struct AdjointSpace {
   void* tabs = nullptr;      // normalised OU table of every step (96 reals each)
   // gravity: the potential at every checkpoint (warm start of the replay), of every segment
   // step, dL/dg, dL/dphi, dL/dF, and the forward's final potential
-  std::vector<double*> ckPhi, segPhi;
-  double *hbuf = nullptr, *psi = nullptr, *wsol = nullptr, *phi_keep = nullptr;
+  std::vector<float*> ckPhi, segPhi;   // float-float potentials, 8 B per cell
+  double *hbuf = nullptr, *psi = nullptr;
+  float *wsol = nullptr, *phi_keep = nullptr;   // float-float, planar
   int nck = 0, k = 0, nsteps = 0;
   bool sources = false, gravity = false;
 };
@@ -434,8 +431,8 @@ void adjoint_free(dh_ctx* c) {
   cudaFree(a->scratch);
   cudaFree(a->dts);
   cudaFree(a->tabs);
-  for (double* p : a->ckPhi) cudaFree(p);
-  for (double* p : a->segPhi) cudaFree(p);
+  for (float* p : a->ckPhi) cudaFree(p);
+  for (float* p : a->segPhi) cudaFree(p);
   cudaFree(a->hbuf);
   cudaFree(a->psi);
   cudaFree(a->wsol);
@@ -560,7 +557,7 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
     const size_t pb = (size_t)c->n3 * sizeof(double);
     if (a->gravity) {
       // the potential the forward started this segment from (warm start of its first solve)
-      e = cudaMemcpyAsync(mg_phi64(c), a->ckPhi[sgi], pb, cudaMemcpyDeviceToDevice, c->stream);
+      e = cudaMemcpyAsync(mg_phi(c), a->ckPhi[sgi], pb, cudaMemcpyDeviceToDevice, c->stream);
       if (e != cudaSuccess) return e;
     }
     for (int j = 0; j < len; ++j) {
@@ -575,7 +572,7 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
           e = cudaMemcpyAsync(a->segH[j], out, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess) e = gravity_sources<real>(c, out, tab(m0 + j), a->dts + m0 + j, false);
         if (e == cudaSuccess)
-          e = cudaMemcpyAsync(a->segPhi[j], mg_phi64(c), pb, cudaMemcpyDeviceToDevice, c->stream);
+          e = cudaMemcpyAsync(a->segPhi[j], mg_phi(c), pb, cudaMemcpyDeviceToDevice, c->stream);
         if (e != cudaSuccess) return e;
       } else if (src) {
         // with sources the last stage 2 is replayed too: its pre-source state is needed
@@ -618,7 +615,7 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
           if (e == cudaSuccess) e = mg_solve_rhs(c, a->psi, a->wsol);
           if (e != cudaSuccess) return e;
           add_density_adjoint_kernel<real><<<blocks, 256, 0, c->stream>>>((real*)lam_h, a->wsol, n3,
-                                                                          c->cfg.four_pi_G);
+                                                                          (real)c->cfg.four_pi_G);
           e = cudaGetLastError();
           if (e != cudaSuccess) return e;
         }
@@ -658,7 +655,7 @@ extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLd
     if (m % k == 0) {
       e = cudaMemcpyAsync(a->ckpt[m / k], c->U[c->cur], c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
       if (e == cudaSuccess && a->gravity)
-        e = cudaMemcpyAsync(a->ckPhi[m / k], mg_phi64(c), (size_t)c->n3 * sizeof(double),
+        e = cudaMemcpyAsync(a->ckPhi[m / k], mg_phi(c), (size_t)c->n3 * sizeof(double),
                             cudaMemcpyDeviceToDevice, c->stream);
     }
     if (e == cudaSuccess) e = c->prec == DH_F64 ? dh_enqueue_step_f64(c) : dh_enqueue_step_f32(c);
@@ -676,7 +673,7 @@ extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLd
   const size_t pb = (size_t)c->n3 * sizeof(double);
   if (a->gravity) {
     // keep the forward's final potential (the next step's warm start); start dL/dF at zero
-    e = cudaMemcpyAsync(a->phi_keep, mg_phi64(c), pb, cudaMemcpyDeviceToDevice, c->stream);
+    e = cudaMemcpyAsync(a->phi_keep, mg_phi(c), pb, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(a->wsol, 0, pb, c->stream);
   }
   // backward sweep
@@ -686,7 +683,7 @@ extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLd
                           : adjoint_backward<float>(c, n, k, a->lam[1]);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dLdU0, a->lam[0], c->state_bytes, d2h, c->stream);
   if (e == cudaSuccess && a->gravity)
-    e = cudaMemcpyAsync(mg_phi64(c), a->phi_keep, pb, cudaMemcpyDeviceToDevice, c->stream);
+    e = cudaMemcpyAsync(mg_phi(c), a->phi_keep, pb, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) { c->err = std::string("adjoint backward: ") + cudaGetErrorString(e); return DH_ERR_CUDA; }
   if (a->gravity) {

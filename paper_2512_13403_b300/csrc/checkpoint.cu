@@ -1,11 +1,13 @@
 // File checkpoints of a context (dh_save / dh_load): everything a continuation depends on, so
 // that a loaded context steps bit for bit like the one that was saved.
 //
-// Layout (native byte order): 8-byte magic "DHCKPT01", a fixed header (geometry, precision,
+// Layout (native byte order): 8-byte magic "DHCKPT02", a fixed header (geometry, precision,
 // physics switches, OU seed and hold flag, gamma and cell widths, t, dt, step count, OU
 // normalisation), the OU tables a_hat and its pre-update copy (96 doubles each; forcing only),
-// the state (5 planes of the context precision), the float64 potential that warm-starts the
-// next Poisson solve (gravity only), and a 64-bit FNV-1a checksum of everything before it.
+// the state (5 planes of the context precision), the potential that warm-starts the next
+// Poisson solve as its float-float words (n hi floats, then n lo floats; gravity only), and a
+// 64-bit FNV-1a checksum of everything before it.  Version 02 replaced version 01's float64
+// potential by the float-float words (same size, other meaning): 01 files are refused.
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -16,7 +18,7 @@
 
 namespace {
 
-constexpr char kMagic[8] = {'D', 'H', 'C', 'K', 'P', 'T', '0', '1'};
+constexpr char kMagic[8] = {'D', 'H', 'C', 'K', 'P', 'T', '0', '2'};
 
 struct CkptHeader {
   int32_t nx, ny, nz, precision;
@@ -61,7 +63,7 @@ extern "C" dh_status dh_save(dh_ctx* c, const char* path) {
   h.nstep = c->host_rec.nstep;
   std::vector<double> ahat(96, 0.0), ahat_prev(96, 0.0);
   std::vector<unsigned char> state(c->state_bytes);
-  std::vector<double> phi;
+  std::vector<float> phi;   // float-float words
   cudaError_t e = cudaSuccess;
   if (g.forcing) {
     e = cudaMemcpyAsync(ahat.data(), c->ahat, 96 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -71,8 +73,8 @@ extern "C" dh_status dh_save(dh_ctx* c, const char* path) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(state.data(), c->U[c->cur], c->state_bytes, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && g.gravity) {
-    phi.resize((size_t)c->n3);
-    e = cudaMemcpyAsync(phi.data(), dh::mg_phi64(c), (size_t)c->n3 * sizeof(double),
+    phi.resize(2 * (size_t)c->n3);
+    e = cudaMemcpyAsync(phi.data(), dh::mg_phi(c), phi.size() * sizeof(float),
                         cudaMemcpyDeviceToHost, c->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -94,7 +96,7 @@ extern "C" dh_status dh_save(dh_ctx* c, const char* path) {
     put(ahat_prev.data(), 96 * sizeof(double));
   }
   put(state.data(), state.size());
-  if (g.gravity) put(phi.data(), phi.size() * sizeof(double));
+  if (g.gravity) put(phi.data(), phi.size() * sizeof(float));
   const uint64_t check = sum.h;
   if (ok) ok = std::fwrite(&check, 1, sizeof(check), f) == sizeof(check);
   if (std::fclose(f) != 0) ok = false;
@@ -130,15 +132,15 @@ extern "C" dh_status dh_load(dh_ctx* c, const char* path) {
   }
   std::vector<double> ahat(96), ahat_prev(96);
   std::vector<unsigned char> state(c->state_bytes);
-  std::vector<double> phi;
+  std::vector<float> phi;   // float-float words
   if (g.forcing) {
     get(ahat.data(), 96 * sizeof(double));
     get(ahat_prev.data(), 96 * sizeof(double));
   }
   get(state.data(), state.size());
   if (g.gravity) {
-    phi.resize((size_t)c->n3);
-    get(phi.data(), phi.size() * sizeof(double));
+    phi.resize(2 * (size_t)c->n3);
+    get(phi.data(), phi.size() * sizeof(float));
   }
   uint64_t check = 0;
   const uint64_t expect = sum.h;
@@ -163,7 +165,7 @@ extern "C" dh_status dh_load(dh_ctx* c, const char* path) {
       e = cudaMemcpyAsync(c->ahat_prev, ahat_prev.data(), 96 * sizeof(double), cudaMemcpyHostToDevice, c->stream);
   }
   if (e == cudaSuccess && g.gravity)
-    e = cudaMemcpyAsync(dh::mg_phi64(c), phi.data(), phi.size() * sizeof(double),
+    e = cudaMemcpyAsync(dh::mg_phi(c), phi.data(), phi.size() * sizeof(float),
                         cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host vectors go out of scope
   if (e != cudaSuccess) return fail(c, DH_ERR_CUDA, std::string("dh_load: ") + cudaGetErrorString(e));

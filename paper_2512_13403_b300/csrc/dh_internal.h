@@ -55,7 +55,7 @@ cudaError_t mg_allocate(dh_ctx* c);
 void mg_setup_host(dh_ctx* c);
 cudaError_t mg_reset(dh_ctx* c);
 void mg_free(dh_ctx* c);
-double* mg_phi64(dh_ctx* c);   // the float64 potential (warm start of the next solve)
+void* mg_phi(dh_ctx* c);   // the potential, float-float planar, 8 B per cell (warm start of the next solve)
 // Poisson solve on the density of Ustar, then forcing -> gravity -> cooling in place.  tab:
 // normalised OU table (null: the context's current one); dtp: the step's dt on the device;
 // in_step: a step of the context (records flags and the CFL minimum) rather than a replay.
@@ -63,7 +63,7 @@ template <typename real>
 cudaError_t gravity_sources(dh_ctx* c, void* Ustar, const void* tab, const double* dtp,
                             bool in_step);
 // A x = rhs - <rhs> by V-cycles (x: warm start and result, <x> = 0), for the adjoint.
-cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, double* x);
+cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, float* x);   // x float-float planar
 
 // adjoint.cu
 void adjoint_free(dh_ctx* c);

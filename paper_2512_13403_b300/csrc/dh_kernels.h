@@ -84,7 +84,7 @@ template <typename real> struct SourceAdjArgs {
   real gm1, t_floor, cool_frac;
   int nsub_max;
   const double* dtp;
-  const double* phi;      // potential of the step (nullable: no gravity)
+  const float* phi;       // potential of the step, float-float planar (nullable: no gravity)
   double* h;              // gravity: dL/dg, 3 planes (output)
   double i2h;             // 1 / (2 dx)
 };

@@ -3,8 +3,29 @@
 // cell (App. A.4).
 #pragma once
 #include "dh_device.cuh"
+#include "ff.cuh"
 
 namespace dh {
+
+// g = -grad phi by central differences (Sec. 5) from the float-float potential (planar, n hi
+// words then n lo words).  The difference of the two words is taken in float-float, so the
+// cancellation of neighbouring values costs no accuracy; only the result is rounded to real.
+template <typename real>
+__device__ __forceinline__ void potential_gradient(const float* __restrict__ phi, int nx, int ny,
+                                                   int nz, int i, int j, int k, real i2h, real& g0,
+                                                   real& g1, real& g2) {
+  const long long n = (long long)nx * ny * nz;
+  const long long row = (long long)k * ny;
+  const ff2 dx = ff_sub(ff_load(phi, n, (row + j) * nx + wrap(i + 1, nx)),
+                        ff_load(phi, n, (row + j) * nx + wrap(i - 1, nx)));
+  const ff2 dy = ff_sub(ff_load(phi, n, (row + wrap(j + 1, ny)) * nx + i),
+                        ff_load(phi, n, (row + wrap(j - 1, ny)) * nx + i));
+  const ff2 dz = ff_sub(ff_load(phi, n, ((long long)wrap(k + 1, nz) * ny + j) * nx + i),
+                        ff_load(phi, n, ((long long)wrap(k - 1, nz) * ny + j) * nx + i));
+  g0 = -((real)dx.hi + (real)dx.lo) * i2h;
+  g1 = -((real)dy.hi + (real)dy.lo) * i2h;
+  g2 = -((real)dz.hi + (real)dz.lo) * i2h;
+}
 
 // Forced-mode table of Sec. 3.1.1 as compile-time data: the half-space of integer n with
 // 1 <= |n|^2 <= 4 whose first nonzero component is positive, lexicographic in (n_x, n_y, n_z).

@@ -619,9 +619,10 @@ __global__ void forcing_field_kernel(const real* __restrict__ ah, const real* tw
   const real* tw[3] = {tw0, tw1, tw2};
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3;
        q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % nx);
-    const int j = (int)((q / nx) % ny);
-    const int k = (int)(q / ((long long)nx * ny));
+    const unsigned t = (unsigned)q / (unsigned)nx;   // grids below 2^31 cells
+    const int i = (int)((unsigned)q - t * (unsigned)nx);
+    const int j = (int)(t % (unsigned)ny);
+    const int k = (int)(t / (unsigned)ny);
     real a[3];
     forcing_accel(ah, tw, i, j, k, a);
     out[q] = a[0];

@@ -2,13 +2,17 @@
 // use it.
 //
 // Solve A phi = F, F = 4 pi G (rho - <rho>), A the seven-point periodic Laplacian.  The fine
-// level keeps phi and F in float64 and iterates defect correction: r = F - A phi (float64),
-// then one float32 V-cycle for A e = r (red-black Gauss-Seidel, mg_pre / mg_post sweeps,
-// 8-child mean restriction, cell-centred trilinear prolongation, exact coarsest solve), then
-// phi += e.  For a linear smoother this is the V-cycle applied to phi itself, so the iterates
-// are those of Sec. 5.2's cycle; keeping phi and the residual in float64 lets the relative
-// residual reach 1e-6 at large N, which float32 phi cannot (its rounding alone leaves
-// ~eps_32 * |phi| / h^2 in A phi).  Norms and means are float64 with a fixed reduction order.
+// level keeps phi and F in float-float (a pair of float32 words, ~48 significant bits, ff.cuh)
+// and iterates defect correction: r = F - A phi (float-float), then one float32 V-cycle for
+// A e = r (red-black Gauss-Seidel, mg_pre / mg_post sweeps, 8-child mean restriction,
+// cell-centred trilinear prolongation, exact coarsest solve), then phi += e.  For a linear
+// smoother this is the V-cycle applied to phi itself, so the iterates are those of Sec. 5.2's
+// cycle; keeping phi and the residual in extended precision lets the relative residual reach
+// 1e-6 at large N, which float32 phi cannot (its rounding alone leaves ~eps_32 * |phi| / h^2 in
+// A phi).  Float-float runs on the float32 pipes: on this part float64 arithmetic is scarce
+// enough that a float64 residual is bound by it.  Norms and means are accumulated per thread
+// in compensated float32 and across threads in float64, in a fixed order; the residual norm is
+// taken relative to the RMS of F, so the working range is that of float32.
 //
 // The coarsest grid (<= 1024 cells) is solved with the pseudo-inverse of its operator, a
 // circulant: A^+ e_p = sum_q G[(p - q) mod n] r_q with G[d] = (1/N) sum_{k != 0}
@@ -20,10 +24,13 @@
 
 #include "dh_internal.h"
 #include "dh_sources.cuh"
+#include "ff.cuh"
 
 namespace dh {
 constexpr int MG_LMAX = 16;
-constexpr int RED_BLOCKS = 296, RED_THREADS = 256;
+// reductions: 8 CTAs per SM over 148 SMs (enough warps to cover the stencil loads), then one
+// warp adds the per-block partials in a fixed order
+constexpr int RED_BLOCKS = 148 * 8, RED_THREADS = 256;
 }
 
 struct MG {
@@ -31,8 +38,9 @@ struct MG {
   int n[dh::MG_LMAX][3];
   double h[dh::MG_LMAX];
   long long cells[dh::MG_LMAX];
-  double* phi64 = nullptr;
-  double* F64 = nullptr;
+  // potential and source in float-float, planar: n hi floats then n lo floats (ff.cuh)
+  float* phi = nullptr;
+  float* F = nullptr;
   float* e[dh::MG_LMAX] = {nullptr};
   float* r[dh::MG_LMAX] = {nullptr};
   double* G = nullptr;           // coarsest circulant pseudo-inverse
@@ -76,8 +84,8 @@ cudaError_t mg_allocate(dh_ctx* c) {
   MG* m = new MG();
   c->mg = m;
   level_dims(c->cfg, m);
-  cudaError_t e = cudaMalloc(&m->phi64, m->cells[0] * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&m->F64, m->cells[0] * sizeof(double));
+  cudaError_t e = cudaMalloc(&m->phi, 2 * m->cells[0] * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->F, 2 * m->cells[0] * sizeof(float));
   for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
     e = cudaMalloc(&m->e[l], m->cells[l] * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&m->r[l], m->cells[l] * sizeof(float));
@@ -86,7 +94,7 @@ cudaError_t mg_allocate(dh_ctx* c) {
   if (e == cudaSuccess) e = cudaMalloc(&m->partials, RED_BLOCKS * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&m->scal, 8 * sizeof(double));
   // the potential is the warm start of the first solve: zero, not whatever the allocator held
-  if (e == cudaSuccess) e = cudaMemset(m->phi64, 0, m->cells[0] * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(m->phi, 0, 2 * m->cells[0] * sizeof(float));
   return e;
 }
 
@@ -121,16 +129,16 @@ cudaError_t mg_reset(dh_ctx* c) {
   MG* m = c->mg;
   m->last_cycles = 0;
   m->last_res = 0.0;
-  return cudaMemsetAsync(m->phi64, 0, m->cells[0] * sizeof(double), c->stream);
+  return cudaMemsetAsync(m->phi, 0, 2 * m->cells[0] * sizeof(float), c->stream);
 }
 
-double* mg_phi64(dh_ctx* c) { return c->mg ? c->mg->phi64 : nullptr; }
+void* mg_phi(dh_ctx* c) { return c->mg ? c->mg->phi : nullptr; }
 
 void mg_free(dh_ctx* c) {
   MG* m = c->mg;
   if (!m) return;
-  cudaFree(m->phi64);
-  cudaFree(m->F64);
+  cudaFree(m->phi);
+  cudaFree(m->F);
   for (int l = 0; l < MG_LMAX; ++l) { cudaFree(m->e[l]); cudaFree(m->r[l]); }
   cudaFree(m->G);
   cudaFree(m->partials);
@@ -157,68 +165,107 @@ __device__ __forceinline__ void block_range(long long n, long long& b0, long lon
   b1 = b0 + per < n ? b0 + per : n;
 }
 
+// out = scale * sum(partials): lane l adds entries l, l + 32, ..., then a fixed shuffle tree
+// (one warp; the order, and so the result, does not depend on scheduling)
+__global__ void finalize_kernel(const double* partials, int nb, double* out, double scale) {
+  const int l = threadIdx.x;
+  double s = 0.0;
+  for (int b = l; b < nb; b += 32) s += partials[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (l == 0) *out = scale * s;
+}
+
 template <typename T>
-__global__ void sum_partial_kernel(const T* __restrict__ x, long long n, double* partials) {
+__global__ void sum_partial_kernel(const T* __restrict__ x, long long n, double* partials);
+
+// float32 data: compensated float32 per thread (no float64 arithmetic per cell)
+template <>
+__global__ void sum_partial_kernel<float>(const float* __restrict__ x, long long n, double* partials) {
+  __shared__ double red[RED_THREADS];
+  long long b0, b1;
+  block_range(n, b0, b1);
+  ff2 acc{0.0f, 0.0f};
+  for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) ff_acc(acc, x[i]);
+  const double s = block_sum(ff_to_double(acc), red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <>
+__global__ void sum_partial_kernel<double>(const double* __restrict__ x, long long n, double* partials) {
   __shared__ double red[RED_THREADS];
   long long b0, b1;
   block_range(n, b0, b1);
   double s = 0.0;
-  for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += (double)x[i];
+  for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += x[i];
   s = block_sum(s, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// out = scale * sum(partials)
-__global__ void finalize_kernel(const double* partials, int nb, double* out, double scale) {
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += partials[b];
-    *out = scale * s;
-  }
-}
-
+// F = four_pi_G (rho - <rho>) in float-float, the mean and the factor carried as float-float;
+// partials of |F|^2.
 template <typename T>
 __global__ void poisson_source_kernel(const T* __restrict__ rho, long long n, const double* mean,
-                                      double four_pi_G, double* __restrict__ F, double* partials) {
+                                      double four_pi_G, float* __restrict__ F, double* partials) {
   __shared__ double red[RED_THREADS];
   long long b0, b1;
   block_range(n, b0, b1);
-  const double m = *mean;
-  double s = 0.0;
+  const ff2 mneg = ff_neg(ff_from_double(*mean));
+  const ff2 fpg = ff_from_double(four_pi_G);
+  ff2 acc{0.0f, 0.0f};
   for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-    const double f = four_pi_G * ((double)rho[i] - m);
-    F[i] = f;
-    s += f * f;
+    const ff2 f = ff_mul(ff_add(ff_from_double((double)rho[i]), mneg), fpg);
+    ff_store(F, n, i, f);
+    ff_acc(acc, f.hi * f.hi);
   }
-  s = block_sum(s, red);
+  const double s = block_sum(ff_to_double(acc), red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// r = F - A phi in float64; stores r as the float32 right-hand side of the correction.
-__global__ void residual64_kernel(const double* __restrict__ phi, const double* __restrict__ F,
-                                  float* __restrict__ r32, int nx, int ny, int nz, double ih2,
-                                  double* partials) {
+// r = F - A phi: stores r as the float32 right-hand side of the correction, and partials of
+// |r / rms(F)|^2 with rms(F) = sqrt(fnorm2 / n).  h^2 A phi is the neighbour sum minus 6 phi:
+// the hi words go through a TwoSum chain (exact), the lo words, the chain's rounding errors and
+// the exact error of 6 phi_hi through float32, an absolute error of a few eps32^2 times
+// sum |phi| -- far below what a relative residual of 1e-6 needs at any N this part holds.
+__global__ void residual_ff_kernel(const float* __restrict__ phi, const float* __restrict__ F,
+                                   float* __restrict__ r32, int nx, int ny, int nz, ff2 h2,
+                                   float ih2, const double* fnorm2, double* partials) {
   __shared__ double red[RED_THREADS];
   const long long n = (long long)nx * ny * nz;
   long long b0, b1;
   block_range(n, b0, b1);
-  double s = 0.0;
+  const float sF = (float)(1.0 / sqrt(*fnorm2 / (double)n));
+  ff2 acc{0.0f, 0.0f};
   for (long long q = b0 + threadIdx.x; q < b1; q += blockDim.x) {
-    const int i = (int)(q % nx);
-    const long long t = q / nx;
-    const int j = (int)(t % ny);
-    const int k = (int)(t / ny);
+    const unsigned t = (unsigned)q / (unsigned)nx;   // grids below 2^31 cells
+    const int i = (int)((unsigned)q - t * (unsigned)nx);
+    const int k = (int)(t / (unsigned)ny);
+    const int j = (int)(t - (unsigned)k * (unsigned)ny);
     const long long row = (long long)k * ny;
-    const double c = phi[q];
-    const double nb = phi[((long long)wrap(k - 1, nz) * ny + j) * nx + i] +
-                      phi[((long long)wrap(k + 1, nz) * ny + j) * nx + i] +
-                      phi[(row + wrap(j - 1, ny)) * nx + i] + phi[(row + wrap(j + 1, ny)) * nx + i] +
-                      phi[(row + j) * nx + wrap(i - 1, nx)] + phi[(row + j) * nx + wrap(i + 1, nx)];
-    const double rr = F[q] - (nb - 6.0 * c) * ih2;
-    r32[q] = (float)rr;
-    s += rr * rr;
+    const long long nq[6] = {((long long)wrap(k - 1, nz) * ny + j) * nx + i,
+                             ((long long)wrap(k + 1, nz) * ny + j) * nx + i,
+                             (row + wrap(j - 1, ny)) * nx + i, (row + wrap(j + 1, ny)) * nx + i,
+                             (row + j) * nx + wrap(i - 1, nx), (row + j) * nx + wrap(i + 1, nx)};
+    const ff2 c = ff_load(phi, n, q);
+    // -6 phi_c: exact product of the hi word
+    ff2 sum{__fmul_rn(-6.0f, c.hi), 0.0f};
+    float err = __fmaf_rn(-6.0f, c.hi, -sum.hi);
+    float lo = __fmul_rn(-6.0f, c.lo);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      const ff2 v = ff_load(phi, n, nq[a]);
+      ff_acc(sum, v.hi);
+      lo = __fadd_rn(lo, v.lo);
+    }
+    const ff2 lap = ff_fast_two_sum(sum.hi, __fadd_rn(sum.lo, __fadd_rn(err, lo)));  // h^2 A phi
+    const ff2 fh = ff_mul(ff_load(F, n, q), h2);                                      // h^2 F
+    const ff2 d = ff_two_sum(fh.hi, -lap.hi);
+    const float rr = __fmul_rn(__fadd_rn(d.hi, __fadd_rn(d.lo, __fsub_rn(fh.lo, lap.lo))), ih2);
+    r32[q] = rr;
+    const float rs = rr * sF;
+    ff_acc(acc, rs * rs);
   }
-  s = block_sum(s, red);
+  const double s = block_sum(ff_to_double(acc), red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
@@ -228,10 +275,11 @@ __global__ void rbgs_kernel(float* __restrict__ e, const float* __restrict__ r, 
   const long long half = (long long)(nx / 2) * ny * nz;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < half;
        t += (long long)gridDim.x * blockDim.x) {
-    const int ih = (int)(t % (nx / 2));
-    const long long u = t / (nx / 2);
-    const int j = (int)(u % ny);
-    const int k = (int)(u / ny);
+    const unsigned hx = (unsigned)(nx / 2);
+    const unsigned u = (unsigned)t / hx;
+    const int ih = (int)((unsigned)t - u * hx);
+    const int k = (int)(u / (unsigned)ny);
+    const int j = (int)(u - (unsigned)k * (unsigned)ny);
     const int i = 2 * ih + ((j + k + color) & 1);
     const long long row = (long long)k * ny;
     const long long q = (row + j) * nx + i;
@@ -250,10 +298,10 @@ __global__ void resid_restrict_kernel(const float* __restrict__ e, const float* 
   const long long nc = (long long)cx * cy * cz;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
        t += (long long)gridDim.x * blockDim.x) {
-    const int I = (int)(t % cx);
-    const long long u = t / cx;
-    const int J = (int)(u % cy);
-    const int K = (int)(u / cy);
+    const unsigned u = (unsigned)t / (unsigned)cx;
+    const int I = (int)((unsigned)t - u * (unsigned)cx);
+    const int K = (int)(u / (unsigned)cy);
+    const int J = (int)(u - (unsigned)K * (unsigned)cy);
     float s = 0.f;
     for (int dk = 0; dk < 2; ++dk)
       for (int dj = 0; dj < 2; ++dj)
@@ -279,10 +327,10 @@ __global__ void prolong_add_kernel(float* __restrict__ ef, const float* __restri
   const long long nf = (long long)nx * ny * nz;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nf;
        q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % nx);
-    const long long u = q / nx;
-    const int j = (int)(u % ny);
-    const int k = (int)(u / ny);
+    const unsigned u = (unsigned)q / (unsigned)nx;
+    const int i = (int)((unsigned)q - u * (unsigned)nx);
+    const int k = (int)(u / (unsigned)ny);
+    const int j = (int)(u - (unsigned)k * (unsigned)ny);
     const int I = i >> 1, J = j >> 1, K = k >> 1;
     const int I2 = wrap(I + ((i & 1) ? 1 : -1), cx);
     const int J2 = wrap(J + ((j & 1) ? 1 : -1), cy);
@@ -313,23 +361,35 @@ __global__ void coarse_solve_kernel(const float* __restrict__ r, float* __restri
   }
 }
 
-__global__ void update64_kernel(double* __restrict__ phi, const float* __restrict__ e, long long n) {
+__global__ void update_ff_kernel(float* __restrict__ phi, const float* __restrict__ e, long long n) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x)
-    phi[q] += (double)e[q];
+    ff_store(phi, n, q, ff_add_f(ff_load(phi, n, q), e[q]));
 }
 
-__global__ void sub_mean_kernel(double* __restrict__ phi, long long n, const double* mean) {
-  const double m = *mean;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x)
-    phi[q] -= m;
+// Per-block float-float sums of the potential (the gauge's mean), in float64 partials.
+__global__ void sum_ff_kernel(const float* __restrict__ phi, long long n, double* partials) {
+  __shared__ double red[RED_THREADS];
+  long long b0, b1;
+  block_range(n, b0, b1);
+  ff2 acc{0.0f, 0.0f};
+  for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc = ff_add(acc, ff_load(phi, n, i));
+  const double s = block_sum(ff_to_double(acc), red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-__global__ void zero64_kernel(double* __restrict__ phi, long long n) {
+__global__ void sub_mean_ff_kernel(float* __restrict__ phi, long long n, const double* mean) {
+  const ff2 mneg = ff_neg(ff_from_double(*mean));
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x)
-    phi[q] = 0.0;
+    ff_store(phi, n, q, ff_add(ff_load(phi, n, q), mneg));
+}
+
+// float-float -> float64 (for callers of the potential)
+__global__ void ff_to_double_kernel(const float* __restrict__ phi, long long n, double* __restrict__ out) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    out[q] = ff_to_double(ff_load(phi, n, q));
 }
 
 __global__ void mark_fail_kernel(StepRecord* rec, unsigned flag) {
@@ -375,50 +435,52 @@ static void vcycle(dh_ctx* c, int l) {
   c->launches += 2 * (g.mg_pre + g.mg_post) + 2;
 }
 
-// V-cycles on phi64 for the source in F64 (|F|^2 already in scal[1]) until the relative
-// residual reaches mg_tol, then the gauge <phi> = 0.  Marks FLAG_MG_NOCONV on failure.
+// V-cycles on phi for the source in F (|F|^2 already in scal[1]) until the relative residual
+// reaches mg_tol, then the gauge <phi> = 0.  Marks FLAG_MG_NOCONV on failure.
 static cudaError_t mg_iterate(dh_ctx* c) {
   MG* m = c->mg;
   const dh_config& g = c->cfg;
   cudaStream_t s = c->stream;
   const long long n = m->cells[0];
   const int nx = m->n[0][0], ny = m->n[0][1], nz = m->n[0][2];
-  const double ih2 = 1.0 / (m->h[0] * m->h[0]);
+  const double hh = m->h[0] * m->h[0];
+  const ff2 h2 = ff_from_double(hh);
+  const float ih2 = (float)(1.0 / hh);
   int cycles = 0;
   double rel = 0.0;
   bool ok = false;
   while (true) {
     prof_begin(c, DH_KERNEL_MG);
-    residual64_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->phi64, m->F64, m->r[0], nx, ny, nz,
-                                                         ih2, m->partials);
-    finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 2, 1.0);
+    residual_ff_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->phi, m->F, m->r[0], nx, ny, nz, h2,
+                                                          ih2, m->scal + 1, m->partials);
+    finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 2, 1.0 / (double)n);
     prof_end(c, 2);
     double h[3];
     cudaError_t e = cudaMemcpyAsync(h, m->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
     if (!(h[1] > 0.0)) {  // zero source: phi = 0
-      zero64_kernel<<<grid_for(n), 256, 0, s>>>(m->phi64, n);
-      c->launches += 1;
+      e = cudaMemsetAsync(m->phi, 0, 2 * n * sizeof(float), s);
+      if (e != cudaSuccess) return e;
       ok = true;
       rel = 0.0;
       break;
     }
-    rel = std::sqrt(h[2] / h[1]);
+    rel = std::sqrt(h[2]);   // scal[2] = |r|^2 / |F|^2
     if (rel <= g.mg_tol) { ok = true; break; }
     if (!(rel == rel)) break;                 // non-finite residual
     if (cycles >= g.mg_max_cycles) break;
     prof_begin(c, DH_KERNEL_MG);
     vcycle(c, 0);
-    update64_kernel<<<grid_for(n), 256, 0, s>>>(m->phi64, m->e[0], n);
+    update_ff_kernel<<<grid_for(n), 256, 0, s>>>(m->phi, m->e[0], n);
     prof_end(c, 1);
     ++cycles;
   }
   // gauge <phi> = 0
   prof_begin(c, DH_KERNEL_MG);
-  sum_partial_kernel<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->phi64, n, m->partials);
+  sum_ff_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->phi, n, m->partials);
   finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 3, 1.0 / (double)n);
-  sub_mean_kernel<<<grid_for(n), 256, 0, s>>>(m->phi64, n, m->scal + 3);
+  sub_mean_ff_kernel<<<grid_for(n), 256, 0, s>>>(m->phi, n, m->scal + 3);
   prof_end(c, 3);
   m->last_cycles = cycles;
   m->last_res = rel;
@@ -429,7 +491,7 @@ static cudaError_t mg_iterate(dh_ctx* c) {
   return cudaGetLastError();
 }
 
-// Solves for phi64 from the density plane of U (type real).
+// Solves for phi from the density plane of U (type real).
 template <typename real>
 cudaError_t mg_solve(dh_ctx* c, const real* rho, bool in_step) {
   MG* m = c->mg;
@@ -448,15 +510,16 @@ cudaError_t mg_solve(dh_ctx* c, const real* rho, bool in_step) {
   sum_partial_kernel<real><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rho, n, m->partials);
   finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
   poisson_source_kernel<real><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rho, n, m->scal + 0, g.four_pi_G,
-                                                                 m->F64, m->partials);
+                                                                 m->F, m->partials);
   finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
   prof_end(c, 4);
   return mg_iterate(c);
 }
 
-// A x = rhs - <rhs> for a float64 right-hand side; x (float64, n cells) is the warm start and
-// the result, with <x> = 0.  The solve the adjoint of the gravity step needs (A is symmetric).
-cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, double* x) {
+// A x = rhs - <rhs> for a float64 right-hand side; x (float-float, planar, n cells) is the warm
+// start and the result, with <x> = 0.  The solve the adjoint of the gravity step needs (A is
+// symmetric).
+cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, float* x) {
   MG* m = c->mg;
   cudaStream_t s = c->stream;
   const long long n = m->cells[0];
@@ -464,13 +527,13 @@ cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, double* x) {
   sum_partial_kernel<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rhs, n, m->partials);
   finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
   poisson_source_kernel<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rhs, n, m->scal + 0, 1.0,
-                                                                   m->F64, m->partials);
+                                                                   m->F, m->partials);
   finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
   prof_end(c, 4);
-  double* keep = m->phi64;
-  m->phi64 = x;
+  float* keep = m->phi;
+  m->phi = x;
   cudaError_t e = mg_iterate(c);
-  m->phi64 = keep;
+  m->phi = keep;
   return e;
 }
 
@@ -479,8 +542,8 @@ cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, double* x) {
 // splitting order), then the positivity/finite checks and the CFL minimum for the next step.
 template <typename real>
 __global__ void __launch_bounds__(256)
-gravity_sources_kernel(real* __restrict__ U, const double* __restrict__ phi, int nx, int ny,
-                       int nz, double i2h, StepRecord* rec, const double* dtp, int in_step,
+gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int nx, int ny,
+                       int nz, real i2h, StepRecord* rec, const double* dtp, int in_step,
                        int forcing,
                        const real* __restrict__ ah, const real* tw0, const real* tw1,
                        const real* tw2, int cooling, real gamma, real gm1, real t_floor,
@@ -498,10 +561,10 @@ gravity_sources_kernel(real* __restrict__ U, const double* __restrict__ phi, int
   unsigned flags = 0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3;
        q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % nx);
-    const long long t = q / nx;
-    const int j = (int)(t % ny);
-    const int k = (int)(t / ny);
+    const unsigned t = (unsigned)q / (unsigned)nx;
+    const int i = (int)((unsigned)q - t * (unsigned)nx);
+    const int k = (int)(t / (unsigned)ny);
+    const int j = (int)(t - (unsigned)k * (unsigned)ny);
     real u[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) u[c] = U[c * n3 + q];
@@ -516,11 +579,8 @@ gravity_sources_kernel(real* __restrict__ U, const double* __restrict__ phi, int
     }
     {
       // g = -grad phi by central differences (Sec. 5), momentum taken before the kick
-      const long long row = (long long)k * ny;
-      const real g0 = (real)(-(phi[(row + j) * nx + wrap(i + 1, nx)] - phi[(row + j) * nx + wrap(i - 1, nx)]) * i2h);
-      const real g1 = (real)(-(phi[(row + wrap(j + 1, ny)) * nx + i] - phi[(row + wrap(j - 1, ny)) * nx + i]) * i2h);
-      const real g2 = (real)(-(phi[((long long)wrap(k + 1, nz) * ny + j) * nx + i] -
-                               phi[((long long)wrap(k - 1, nz) * ny + j) * nx + i]) * i2h);
+      real g0, g1, g2;
+      potential_gradient(phi, nx, ny, nz, i, j, k, i2h, g0, g1, g2);
       const real e = (u[1] * g0 + u[2] * g1 + u[3] * g2) * dt;
       u[1] = u[1] + u[0] * g0 * dt;
       u[2] = u[2] + u[0] * g1 * dt;
@@ -535,7 +595,7 @@ gravity_sources_kernel(real* __restrict__ U, const double* __restrict__ phi, int
     if (!finite) {
       flags |= FLAG_NONFINITE;
     } else {
-      const real pr = gm1 * (u[4] - real(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0]);
+      const real pr = gm1 * (u[4] - real(0.5) * q_div(u[1] * u[1] + u[2] * u[2] + u[3] * u[3], u[0]));
       if (!(u[0] > real(0)) || !(pr > real(0))) flags |= FLAG_POSITIVITY;
       tmin = fmin(tmin, cfl_time(u[0], u[1], u[2], u[3], u[4], gamma, gm1, dx, dy, dz));
     }
@@ -569,7 +629,7 @@ cudaError_t gravity_sources(dh_ctx* c, void* Ustar, const void* tab, const doubl
   const long long n = c->n3;
   prof_begin(c, DH_KERNEL_SOURCES);
   gravity_sources_kernel<real><<<grid_for(n), 256, 0, c->stream>>>(
-      U, c->mg->phi64, g.nx, g.ny, g.nz, 1.0 / (2.0 * g.dx), c->rec, dtp, in_step ? 1 : 0,
+      U, c->mg->phi, g.nx, g.ny, g.nz, (real)(1.0 / (2.0 * g.dx)), c->rec, dtp, in_step ? 1 : 0,
       g.forcing, (const real*)(tab ? tab : c->ahat_norm), (const real*)c->tw[0],
       (const real*)c->tw[1], (const real*)c->tw[2], g.cooling, (real)g.gamma,
       (real)(g.gamma - 1.0), (real)g.t_floor, (real)g.cool_frac, g.nsub_max, (real)g.dx,
@@ -587,9 +647,14 @@ extern "C" dh_status dh_get_potential(dh_ctx* c, double* phi_out, int on_device,
   if (!c) return DH_ERR_ARG;
   if (!c->cfg.gravity || !c->mg) { c->err = "gravity is off"; return DH_ERR_STATE; }
   if (phi_out) {
-    cudaError_t e = cudaMemcpyAsync(phi_out, c->mg->phi64, c->mg->cells[0] * sizeof(double),
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                    c->stream);
+    // float-float -> float64 in the source buffer F (free between solves), then copied out
+    MG* m = c->mg;
+    const long long n = m->cells[0];
+    double* tmp = on_device ? phi_out : (double*)m->F;
+    dh::ff_to_double_kernel<<<dh::grid_for(n), 256, 0, c->stream>>>(m->phi, n, tmp);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !on_device)
+      e = cudaMemcpyAsync(phi_out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return DH_ERR_CUDA; }
   }

@@ -4,6 +4,7 @@ seconds and a few hundred MB on the device.
     python -m paper_2512_13403_b300.profile_cases adjoint [n]     # dh_adjoint_advance, 2 steps
     python -m paper_2512_13403_b300.profile_cases corrector [n]   # 3 network forwards + 1 backward
     python -m paper_2512_13403_b300.profile_cases stage [n]       # 3 forward steps, driven cooling box
+    python -m paper_2512_13403_b300.profile_cases selfgrav [n]    # 4 steps, gravity + forcing + cooling
 """
 from __future__ import annotations
 
@@ -53,8 +54,22 @@ def stage(n: int = 128):
     print("stage", n, s.time())
 
 
+def selfgrav(n: int = 1024):
+    from . import inputs as _in
+    cfg = Config(shape=(n, n, n), precision="f32", forcing=True, cooling=True, t_floor=0.05,
+                 gravity=True, four_pi_G=1.0, mg_tol=1e-6, mg_max_cycles=30)
+    s = Solver(cfg)
+    U0 = _in.self_gravitating_box_device((n, n, n), seed=5, sigma=1.0)
+    s.init_state(U0)
+    del U0
+    torch.cuda.empty_cache()
+    s.advance(4)
+    torch.cuda.synchronize()
+    print("selfgrav", n, s.time(), s.mg_stats())
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "stage"
     size = int(sys.argv[2]) if len(sys.argv) > 2 else None
-    fn = {"adjoint": adjoint, "corrector": corrector, "stage": stage}[case]
+    fn = {"adjoint": adjoint, "corrector": corrector, "stage": stage, "selfgrav": selfgrav}[case]
     fn() if size is None else fn(size)
