@@ -149,7 +149,8 @@ dh_status dh_downsample(const float* U_fine, int nx, int ny, int nz, int factor,
 
 /* Gravitational potential phi of the last solve (one plane, float64, state index order),
    and the cycles / final relative residual of that solve (nullable outputs).  The context holds
-   phi in float-float (about 48 significant bits); phi_out receives hi + lo rounded to float64. */
+   phi in float-float (about 48 significant bits) in whatever gauge the solves left it (only
+   differences of phi enter a step); phi_out receives phi - <phi> rounded to float64. */
 dh_status dh_get_potential(dh_ctx* ctx, double* phi_out, int on_device, int* cycles,
                            double* rel_residual);
 

@@ -74,6 +74,9 @@ __host__ __device__ __forceinline__ ff2 ff_from_double(double v) {
   return ff2{hi, (float)(v - (double)hi)};
 }
 
+__device__ __forceinline__ ff2 ff_from(float v) { return ff2{v, 0.0f}; }
+__device__ __forceinline__ ff2 ff_from(double v) { return ff_from_double(v); }
+
 __host__ __device__ __forceinline__ double ff_to_double(ff2 x) { return (double)x.hi + (double)x.lo; }
 
 // planar storage: n hi floats, then n lo floats

@@ -20,6 +20,7 @@
 // eigenvalues; it also removes the mean (the constant null space).
 #include <math.h>
 #include <string.h>
+#include <utility>
 #include <vector>
 
 #include "dh_internal.h"
@@ -31,6 +32,7 @@ constexpr int MG_LMAX = 16;
 // reductions: 8 CTAs per SM over 148 SMs (enough warps to cover the stencil loads), then one
 // warp adds the per-block partials in a fixed order
 constexpr int RED_BLOCKS = 148 * 8, RED_THREADS = 256;
+constexpr int RES_BLOCKS = 148 * 4;   // the residual's grid: one resident wave
 }
 
 struct MG {
@@ -42,6 +44,7 @@ struct MG {
   float* phi = nullptr;
   float* F = nullptr;
   float* e[dh::MG_LMAX] = {nullptr};
+  float* e2[dh::MG_LMAX] = {nullptr};   // the sweep's other buffer (a sweep writes e2, then swaps)
   float* r[dh::MG_LMAX] = {nullptr};
   double* G = nullptr;           // coarsest circulant pseudo-inverse
   double* partials = nullptr;    // RED_BLOCKS doubles
@@ -88,6 +91,7 @@ cudaError_t mg_allocate(dh_ctx* c) {
   if (e == cudaSuccess) e = cudaMalloc(&m->F, 2 * m->cells[0] * sizeof(float));
   for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
     e = cudaMalloc(&m->e[l], m->cells[l] * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&m->e2[l], m->cells[l] * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&m->r[l], m->cells[l] * sizeof(float));
   }
   if (e == cudaSuccess) e = cudaMalloc(&m->G, m->cells[m->L - 1] * sizeof(double));
@@ -139,7 +143,7 @@ void mg_free(dh_ctx* c) {
   if (!m) return;
   cudaFree(m->phi);
   cudaFree(m->F);
-  for (int l = 0; l < MG_LMAX; ++l) { cudaFree(m->e[l]); cudaFree(m->r[l]); }
+  for (int l = 0; l < MG_LMAX; ++l) { cudaFree(m->e[l]); cudaFree(m->e2[l]); cudaFree(m->r[l]); }
   cudaFree(m->G);
   cudaFree(m->partials);
   cudaFree(m->scal);
@@ -208,15 +212,24 @@ template <typename T>
 __global__ void poisson_source_kernel(const T* __restrict__ rho, long long n, const double* mean,
                                       double four_pi_G, float* __restrict__ F, double* partials) {
   __shared__ double red[RED_THREADS];
-  long long b0, b1;
-  block_range(n, b0, b1);
   const ff2 mneg = ff_neg(ff_from_double(*mean));
   const ff2 fpg = ff_from_double(four_pi_G);
   ff2 acc{0.0f, 0.0f};
-  for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-    const ff2 f = ff_mul(ff_add(ff_from_double((double)rho[i]), mneg), fpg);
-    ff_store(F, n, i, f);
-    ff_acc(acc, f.hi * f.hi);
+  // cells q0 + u * stride, u < 4, per pass: four independent loads in flight per thread
+  const long long stride = (long long)gridDim.x * RED_THREADS;
+  for (long long q0 = blockIdx.x * (long long)RED_THREADS + threadIdx.x; q0 < n; q0 += 4 * stride) {
+    T v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = q0 + u * stride < n ? rho[q0 + u * stride] : T(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long q = q0 + u * stride;
+      if (q < n) {
+        const ff2 f = ff_mul(ff_add(ff_from(v[u]), mneg), fpg);
+        ff_store(F, n, q, f);
+        ff_acc(acc, f.hi * f.hi);
+      }
+    }
   }
   const double s = block_sum(ff_to_double(acc), red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -227,68 +240,187 @@ __global__ void poisson_source_kernel(const T* __restrict__ rho, long long n, co
 // the hi words go through a TwoSum chain (exact), the lo words, the chain's rounding errors and
 // the exact error of 6 phi_hi through float32, an absolute error of a few eps32^2 times
 // sum |phi| -- far below what a relative residual of 1e-6 needs at any N this part holds.
-__global__ void residual_ff_kernel(const float* __restrict__ phi, const float* __restrict__ F,
-                                   float* __restrict__ r32, int nx, int ny, int nz, ff2 h2,
-                                   float ih2, const double* fnorm2, double* partials) {
+// The grid strides through the cells together (cell q by thread q mod the grid's threads), so
+// the planes above and below a cell are read while they are still in L2; the grid is one wave.
+// Indices are 32-bit (grids below 2^31 cells) and a thread's (i, j, k) advance by the stride's
+// digits instead of being divided out per cell.
+__global__ void __launch_bounds__(RED_THREADS, 4)
+residual_ff_kernel(const float* __restrict__ phi, const float* __restrict__ F,
+                   float* __restrict__ r32, int nx, int ny, int nz, ff2 h2, float ih2,
+                   const double* fnorm2, double* partials) {
   __shared__ double red[RED_THREADS];
-  const long long n = (long long)nx * ny * nz;
-  long long b0, b1;
-  block_range(n, b0, b1);
+  const unsigned n = (unsigned)nx * (unsigned)ny * (unsigned)nz;
+  const unsigned plane = (unsigned)nx * (unsigned)ny;
+  const float* __restrict__ phl = phi + n;
+  const float* __restrict__ Fl = F + n;
   const float sF = (float)(1.0 / sqrt(*fnorm2 / (double)n));
+  const unsigned stride = gridDim.x * RED_THREADS;
+  const int si = (int)(stride % (unsigned)nx), sj = (int)((stride / (unsigned)nx) % (unsigned)ny),
+            sk = (int)(stride / plane);
+  unsigned q = blockIdx.x * RED_THREADS + threadIdx.x;
+  int i = (int)(q % (unsigned)nx), j = (int)((q / (unsigned)nx) % (unsigned)ny), k = (int)(q / plane);
   ff2 acc{0.0f, 0.0f};
-  for (long long q = b0 + threadIdx.x; q < b1; q += blockDim.x) {
-    const unsigned t = (unsigned)q / (unsigned)nx;   // grids below 2^31 cells
-    const int i = (int)((unsigned)q - t * (unsigned)nx);
-    const int k = (int)(t / (unsigned)ny);
-    const int j = (int)(t - (unsigned)k * (unsigned)ny);
-    const long long row = (long long)k * ny;
-    const long long nq[6] = {((long long)wrap(k - 1, nz) * ny + j) * nx + i,
-                             ((long long)wrap(k + 1, nz) * ny + j) * nx + i,
-                             (row + wrap(j - 1, ny)) * nx + i, (row + wrap(j + 1, ny)) * nx + i,
-                             (row + j) * nx + wrap(i - 1, nx), (row + j) * nx + wrap(i + 1, nx)};
-    const ff2 c = ff_load(phi, n, q);
+  for (; q < n; q += stride) {
+    const unsigned xm = i == 0 ? q + nx - 1 : q - 1, xp = i == nx - 1 ? q + 1 - nx : q + 1;
+    const unsigned ym = j == 0 ? q + plane - nx : q - nx, yp = j == ny - 1 ? q + nx - plane : q + nx;
+    const unsigned zm = k == 0 ? q + n - plane : q - plane, zp = k == nz - 1 ? q + plane - n : q + plane;
+    const unsigned nq[6] = {zm, zp, ym, yp, xm, xp};
+    const ff2 c{phi[q], phl[q]};
     // -6 phi_c: exact product of the hi word
     ff2 sum{__fmul_rn(-6.0f, c.hi), 0.0f};
-    float err = __fmaf_rn(-6.0f, c.hi, -sum.hi);
+    const float err = __fmaf_rn(-6.0f, c.hi, -sum.hi);
     float lo = __fmul_rn(-6.0f, c.lo);
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
-      const ff2 v = ff_load(phi, n, nq[a]);
-      ff_acc(sum, v.hi);
-      lo = __fadd_rn(lo, v.lo);
+      ff_acc(sum, phi[nq[a]]);
+      lo = __fadd_rn(lo, phl[nq[a]]);
     }
     const ff2 lap = ff_fast_two_sum(sum.hi, __fadd_rn(sum.lo, __fadd_rn(err, lo)));  // h^2 A phi
-    const ff2 fh = ff_mul(ff_load(F, n, q), h2);                                      // h^2 F
+    const ff2 fh = ff_mul(ff2{F[q], Fl[q]}, h2);                                      // h^2 F
     const ff2 d = ff_two_sum(fh.hi, -lap.hi);
     const float rr = __fmul_rn(__fadd_rn(d.hi, __fadd_rn(d.lo, __fsub_rn(fh.lo, lap.lo))), ih2);
     r32[q] = rr;
     const float rs = rr * sF;
     ff_acc(acc, rs * rs);
+    // (i, j, k) of q + stride
+    i += si;
+    int cy = i >= nx;
+    if (cy) i -= nx;
+    j += sj + cy;
+    cy = j >= ny;
+    if (cy) j -= ny;
+    k += sk + cy;
   }
   const double s = block_sum(ff_to_double(acc), red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// One colour of red-black Gauss-Seidel on A e = r: e_i = (sum of 6 neighbours - h^2 r_i) / 6.
-__global__ void rbgs_kernel(float* __restrict__ e, const float* __restrict__ r, int nx, int ny,
-                            int nz, float h2, int color) {
-  const long long half = (long long)(nx / 2) * ny * nz;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < half;
-       t += (long long)gridDim.x * blockDim.x) {
-    const unsigned hx = (unsigned)(nx / 2);
-    const unsigned u = (unsigned)t / hx;
-    const int ih = (int)((unsigned)t - u * hx);
-    const int k = (int)(u / (unsigned)ny);
-    const int j = (int)(u - (unsigned)k * (unsigned)ny);
-    const int i = 2 * ih + ((j + k + color) & 1);
-    const long long row = (long long)k * ny;
-    const long long q = (row + j) * nx + i;
-    const float nb = e[((long long)wrap(k - 1, nz) * ny + j) * nx + i] +
-                     e[((long long)wrap(k + 1, nz) * ny + j) * nx + i] +
-                     e[(row + wrap(j - 1, ny)) * nx + i] + e[(row + wrap(j + 1, ny)) * nx + i] +
-                     e[(row + j) * nx + wrap(i - 1, nx)] + e[(row + j) * nx + wrap(i + 1, nx)];
-    e[q] = (nb - h2 * r[q]) * (1.0f / 6.0f);
+// Asynchronous 4-byte global -> shared copies (cp.async), grouped per plane.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// One red-black Gauss-Seidel sweep on A e = r in one pass, from e_old into e_new: first every
+// red cell (i + j + k even), then every black cell, each e_i = (sum of 6 neighbours - h^2 r_i)/6.
+// Every neighbour of a cell has the other colour, so the red update reads only old black values
+// and the black update only new red values: the result is that of two colour passes in place,
+// value for value.  A CTA owns a 32 x 8 column of cells and a run of planes [z0, z1); it marches
+// p = z0-1 .. z1, computing red on plane p over the tile and a one-cell halo (from old values on
+// the tile and a two-cell halo, planes p-1..p+1), then black on plane p-1 over the tile from the
+// red planes p-2..p, and writes plane p-1 (both colours).  The halo's red values are recomputed
+// by each CTA that needs them, so CTAs never wait on one another; the periodic wrap in z is just
+// the march's first and last red planes.  Old e and r arrive by cp.async SW_D planes ahead.
+constexpr int SW_TX = 32, SW_TY = 8;                  // tile (one thread per cell of a plane)
+constexpr int SW_EX = SW_TX + 4, SW_EY = SW_TY + 4;   // old e: tile + 2-cell halo
+constexpr int SW_RX = SW_TX + 2, SW_RY = SW_TY + 2;   // new red e and r: tile + 1-cell halo
+constexpr int SW_E = SW_EX * SW_EY, SW_R = SW_RX * SW_RY;
+constexpr int SW_ZC = 64;                              // planes per CTA
+constexpr int SW_D = 3;                                // copy groups in flight
+constexpr int SW_RING = 6;                             // >= 3 + SW_D old-e and 2 + SW_D r slots
+
+template <bool ZERO>   // ZERO: e_old = 0 (the first sweep of a V-cycle level; e_old unread)
+__global__ void __launch_bounds__(256, 8)
+rbgs_sweep_kernel(const float* __restrict__ eo, float* __restrict__ en, const float* __restrict__ r,
+                  int nx, int ny, int nz, float h2) {
+  __shared__ float s_eo[ZERO ? 1 : SW_RING][SW_E];
+  __shared__ float s_r[SW_RING][SW_R];
+  __shared__ float s_red[3][SW_R];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * SW_TX, y0 = blockIdx.y * SW_TY;   // both even
+  const int z0 = blockIdx.z * SW_ZC;
+  const int z1 = z0 + SW_ZC < nz ? z0 + SW_ZC : nz;
+  const int nit = z1 - z0 + 2;   // iterations ip = 0 .. nit - 1 (p = z0 - 1 + ip)
+  const long long plane = (long long)nx * ny;
+  // Global offsets within a plane of this thread's (up to) two halo positions; positions past
+  // the halo of the grid's last cells (tiles larger than the grid) read cell 0 and are unused.
+  int eoff[2], roff[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int pe = tid + 256 * u;
+    const int ex = x0 - 2 + pe % SW_EX, ey = y0 - 2 + pe / SW_EX;
+    eoff[u] = (pe < SW_E && ex < nx + 2 && ey < ny + 2) ? wrap(ey, ny) * nx + wrap(ex, nx) : 0;
+    const int rx = x0 - 1 + pe % SW_RX, ry = y0 - 1 + pe / SW_RX;
+    roff[u] = (pe < SW_R && rx < nx + 1 && ry < ny + 1) ? wrap(ry, ny) * nx + wrap(rx, nx) : 0;
   }
+  const bool e2nd = tid + 256 < SW_E, r2nd = tid + 256 < SW_R;
+  // Old-e plane z0 - 2 + m lives in s_eo[m % SW_RING]; r plane z0 - 1 + m in s_r[m % SW_RING].
+  auto copy_eo = [&](int m) {
+    const float* b = eo + (long long)wrap(z0 - 2 + m, nz) * plane;
+    float* d = s_eo[ZERO ? 0 : m % SW_RING];
+    cp_async4(d + tid, b + eoff[0]);
+    if (e2nd) cp_async4(d + tid + 256, b + eoff[1]);
+  };
+  // group m (m = 0 .. nit - 1): old-e plane z0 + m and r plane z0 - 1 + m
+  auto issue_group = [&](int m) {
+    if (m < nit) {
+      if (!ZERO) copy_eo(m + 2);
+      const float* b = r + (long long)wrap(z0 - 1 + m, nz) * plane;
+      float* d = s_r[m % SW_RING];
+      cp_async4(d + tid, b + roff[0]);
+      if (r2nd) cp_async4(d + tid + 256, b + roff[1]);
+    }
+    cp_async_commit();   // empty groups keep the count uniform
+  };
+  // Red cells of the tile + 1 halo: SW_RY rows of SW_RX / 2; thread t < SW_R / 2 takes one.  The
+  // cell (x0 - 1 + rx, y0 - 1 + ry, p) is red when rx + ry + p is even (x0, y0 even, n even).
+  const bool has_red = tid < SW_R / 2;
+  const int ry = has_red ? tid / (SW_RX / 2) : 0, kk = has_red ? tid % (SW_RX / 2) : 0;
+  const int rx_even = 2 * kk + (ry & 1), rx_odd = 2 * kk + ((ry + 1) & 1);
+  // this thread's cell of the tile
+  const int tx = tid & (SW_TX - 1), ty = tid / SW_TX;
+  const int cb = (ty + 1) * SW_RX + tx + 1;
+  const bool writes = x0 + tx < nx && y0 + ty < ny;
+  float* out = en + (long long)(y0 + ty) * nx + (x0 + tx);
+
+  if (!ZERO) {
+    copy_eo(0);
+    copy_eo(1);
+  }
+#pragma unroll
+  for (int m = 0; m < SW_D; ++m) issue_group(m);   // the first group also carries e planes 0, 1
+  int s3 = 0;   // ip % 3: slot of the red plane p
+  for (int ip = 0; ip < nit; ++ip) {
+    const int p = z0 - 1 + ip;
+    issue_group(ip + SW_D);
+    cp_async_wait<SW_D>();   // groups 0 .. ip have landed (this thread's copies)
+    __syncthreads();
+    const int s3p = s3 == 2 ? 0 : s3 + 1, s3m = s3 == 0 ? 2 : s3 - 1;
+    // red on plane p over the tile + 1 halo
+    if (has_red) {
+      const int rx = (p & 1) ? rx_odd : rx_even;
+      const int c = ry * SW_RX + rx;
+      float nb = 0.f;
+      if (!ZERO) {
+        const float* em = s_eo[ip % SW_RING];
+        const float* ec = s_eo[(ip + 1) % SW_RING];
+        const float* ep = s_eo[(ip + 2) % SW_RING];
+        const int e = (ry + 1) * SW_EX + rx + 1;
+        nb = em[e] + ep[e] + ec[e - SW_EX] + ec[e + SW_EX] + ec[e - 1] + ec[e + 1];
+      }
+      s_red[s3][c] = (nb - h2 * s_r[ip % SW_RING][c]) * (1.0f / 6.0f);
+    }
+    __syncthreads();
+    // black on plane p - 1 over the tile, and the write of plane p - 1
+    if (ip >= 2) {
+      const float* rm = s_red[s3p];   // plane p - 2 (the slot p + 1 will take)
+      const float* rc = s_red[s3m];   // plane p - 1
+      const float* rp = s_red[s3];    // plane p
+      float v;
+      if ((tx + ty + p - 1) & 1) {
+        const float nb = rm[cb] + rp[cb] + rc[cb - SW_RX] + rc[cb + SW_RX] + rc[cb - 1] + rc[cb + 1];
+        v = (nb - h2 * s_r[(ip - 1) % SW_RING][cb]) * (1.0f / 6.0f);
+      } else {
+        v = rc[cb];
+      }
+      if (writes) out[(long long)(p - 1) * plane] = v;
+    }
+    s3 = s3p;
+  }
+  cp_async_wait<0>();
 }
 
 // rc[I] = mean over the 8 children of (r - A e), coarse dims (cx, cy, cz).
@@ -385,11 +517,13 @@ __global__ void sub_mean_ff_kernel(float* __restrict__ phi, long long n, const d
     ff_store(phi, n, q, ff_add(ff_load(phi, n, q), mneg));
 }
 
-// float-float -> float64 (for callers of the potential)
-__global__ void ff_to_double_kernel(const float* __restrict__ phi, long long n, double* __restrict__ out) {
+// phi - <phi>, float-float -> float64 (for callers of the potential)
+__global__ void ff_to_double_kernel(const float* __restrict__ phi, long long n, const double* mean,
+                                    double* __restrict__ out) {
+  const ff2 mneg = ff_neg(ff_from_double(*mean));
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x)
-    out[q] = ff_to_double(ff_load(phi, n, q));
+    out[q] = ff_to_double(ff_add(ff_load(phi, n, q), mneg));
 }
 
 __global__ void mark_fail_kernel(StepRecord* rec, unsigned flag) {
@@ -418,26 +552,31 @@ static void vcycle(dh_ctx* c, int l) {
     c->launches += 1;
     return;
   }
-  cudaMemsetAsync(m->e[l], 0, m->cells[l] * sizeof(float), s);
-  const int gb = grid_for(m->cells[l] / 2);
-  for (int it = 0; it < g.mg_pre; ++it) {
-    rbgs_kernel<<<gb, 256, 0, s>>>(m->e[l], m->r[l], nx, ny, nz, h2, 0);
-    rbgs_kernel<<<gb, 256, 0, s>>>(m->e[l], m->r[l], nx, ny, nz, h2, 1);
-  }
+  // sweeps: e2 <- sweep(e), then swap (the first from e = 0 reads nothing)
+  const dim3 sg((nx + SW_TX - 1) / SW_TX, (ny + SW_TY - 1) / SW_TY, (nz + SW_ZC - 1) / SW_ZC);
+  auto sweep = [&](bool zero) {
+    if (zero)
+      rbgs_sweep_kernel<true><<<sg, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
+    else
+      rbgs_sweep_kernel<false><<<sg, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
+    std::swap(m->e[l], m->e2[l]);
+  };
+  if (g.mg_pre == 0) cudaMemsetAsync(m->e[l], 0, m->cells[l] * sizeof(float), s);
+  for (int it = 0; it < g.mg_pre; ++it) sweep(it == 0);
   resid_restrict_kernel<<<grid_for(m->cells[l + 1]), 256, 0, s>>>(
       m->e[l], m->r[l], m->r[l + 1], nx / 2, ny / 2, nz / 2, 1.0f / h2);
   vcycle(c, l + 1);
   prolong_add_kernel<<<grid_for(m->cells[l]), 256, 0, s>>>(m->e[l], m->e[l + 1], nx / 2, ny / 2, nz / 2);
-  for (int it = 0; it < g.mg_post; ++it) {
-    rbgs_kernel<<<gb, 256, 0, s>>>(m->e[l], m->r[l], nx, ny, nz, h2, 0);
-    rbgs_kernel<<<gb, 256, 0, s>>>(m->e[l], m->r[l], nx, ny, nz, h2, 1);
-  }
-  c->launches += 2 * (g.mg_pre + g.mg_post) + 2;
+  for (int it = 0; it < g.mg_post; ++it) sweep(false);
+  c->launches += g.mg_pre + g.mg_post + 2;
 }
 
 // V-cycles on phi for the source in F (|F|^2 already in scal[1]) until the relative residual
-// reaches mg_tol, then the gauge <phi> = 0.  Marks FLAG_MG_NOCONV on failure.
-static cudaError_t mg_iterate(dh_ctx* c) {
+// reaches mg_tol, then (gauge) <phi> = 0.  Marks FLAG_MG_NOCONV on failure.  The solves inside
+// a step leave the gauge open: only differences of phi enter the step, and dh_get_potential
+// removes the mean when it hands phi out (a constant is in A's null space, so the warm start and
+// the iterates are unaffected by it).
+static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
   MG* m = c->mg;
   const dh_config& g = c->cfg;
   cudaStream_t s = c->stream;
@@ -451,9 +590,9 @@ static cudaError_t mg_iterate(dh_ctx* c) {
   bool ok = false;
   while (true) {
     prof_begin(c, DH_KERNEL_MG);
-    residual_ff_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->phi, m->F, m->r[0], nx, ny, nz, h2,
+    residual_ff_kernel<<<RES_BLOCKS, RED_THREADS, 0, s>>>(m->phi, m->F, m->r[0], nx, ny, nz, h2,
                                                           ih2, m->scal + 1, m->partials);
-    finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 2, 1.0 / (double)n);
+    finalize_kernel<<<1, 32, 0, s>>>(m->partials, RES_BLOCKS, m->scal + 2, 1.0 / (double)n);
     prof_end(c, 2);
     double h[3];
     cudaError_t e = cudaMemcpyAsync(h, m->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -476,12 +615,13 @@ static cudaError_t mg_iterate(dh_ctx* c) {
     prof_end(c, 1);
     ++cycles;
   }
-  // gauge <phi> = 0
-  prof_begin(c, DH_KERNEL_MG);
-  sum_ff_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->phi, n, m->partials);
-  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 3, 1.0 / (double)n);
-  sub_mean_ff_kernel<<<grid_for(n), 256, 0, s>>>(m->phi, n, m->scal + 3);
-  prof_end(c, 3);
+  if (gauge) {
+    prof_begin(c, DH_KERNEL_MG);
+    sum_ff_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->phi, n, m->partials);
+    finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 3, 1.0 / (double)n);
+    sub_mean_ff_kernel<<<grid_for(n), 256, 0, s>>>(m->phi, n, m->scal + 3);
+    prof_end(c, 3);
+  }
   m->last_cycles = cycles;
   m->last_res = rel;
   if (!ok) {
@@ -513,7 +653,7 @@ cudaError_t mg_solve(dh_ctx* c, const real* rho, bool in_step) {
                                                                  m->F, m->partials);
   finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
   prof_end(c, 4);
-  return mg_iterate(c);
+  return mg_iterate(c, false);
 }
 
 // A x = rhs - <rhs> for a float64 right-hand side; x (float-float, planar, n cells) is the warm
@@ -532,7 +672,7 @@ cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, float* x) {
   prof_end(c, 4);
   float* keep = m->phi;
   m->phi = x;
-  cudaError_t e = mg_iterate(c);
+  cudaError_t e = mg_iterate(c, true);
   m->phi = keep;
   return e;
 }
@@ -651,7 +791,10 @@ extern "C" dh_status dh_get_potential(dh_ctx* c, double* phi_out, int on_device,
     MG* m = c->mg;
     const long long n = m->cells[0];
     double* tmp = on_device ? phi_out : (double*)m->F;
-    dh::ff_to_double_kernel<<<dh::grid_for(n), 256, 0, c->stream>>>(m->phi, n, tmp);
+    dh::sum_ff_kernel<<<dh::RED_BLOCKS, dh::RED_THREADS, 0, c->stream>>>(m->phi, n, m->partials);
+    dh::finalize_kernel<<<1, 32, 0, c->stream>>>(m->partials, dh::RED_BLOCKS, m->scal + 3,
+                                                 1.0 / (double)n);
+    dh::ff_to_double_kernel<<<dh::grid_for(n), 256, 0, c->stream>>>(m->phi, n, m->scal + 3, tmp);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && !on_device)
       e = cudaMemcpyAsync(phi_out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
