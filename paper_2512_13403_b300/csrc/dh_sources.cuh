@@ -2,29 +2,40 @@
 // OU forcing synthesis (Sec. 3.1.1), optically thin cooling (Sec. 4.3) and the CFL time of a
 // cell (App. A.4).
 #pragma once
+#include <type_traits>
+
 #include "dh_device.cuh"
 #include "ff.cuh"
 
 namespace dh {
 
 // g = -grad phi by central differences (Sec. 5) from the float-float potential (planar, n hi
-// words then n lo words).  The difference of the two words is taken in float-float, so the
-// cancellation of neighbouring values costs no accuracy; only the result is rounded to real.
+// words then n lo words; grids below 2^31 cells).  For a float32 result the two words are
+// differenced separately: hi - hi is exact when the two lie within a factor 2 of each other
+// (Sterbenz) and otherwise rounds below an ulp of the result, so the float-float difference is
+// not needed.  For float64 the difference is taken in float-float.
 template <typename real>
 __device__ __forceinline__ void potential_gradient(const float* __restrict__ phi, int nx, int ny,
                                                    int nz, int i, int j, int k, real i2h, real& g0,
                                                    real& g1, real& g2) {
-  const long long n = (long long)nx * ny * nz;
-  const long long row = (long long)k * ny;
-  const ff2 dx = ff_sub(ff_load(phi, n, (row + j) * nx + wrap(i + 1, nx)),
-                        ff_load(phi, n, (row + j) * nx + wrap(i - 1, nx)));
-  const ff2 dy = ff_sub(ff_load(phi, n, (row + wrap(j + 1, ny)) * nx + i),
-                        ff_load(phi, n, (row + wrap(j - 1, ny)) * nx + i));
-  const ff2 dz = ff_sub(ff_load(phi, n, ((long long)wrap(k + 1, nz) * ny + j) * nx + i),
-                        ff_load(phi, n, ((long long)wrap(k - 1, nz) * ny + j) * nx + i));
-  g0 = -((real)dx.hi + (real)dx.lo) * i2h;
-  g1 = -((real)dy.hi + (real)dy.lo) * i2h;
-  g2 = -((real)dz.hi + (real)dz.lo) * i2h;
+  const unsigned plane = (unsigned)nx * (unsigned)ny, n = plane * (unsigned)nz;
+  const unsigned q = ((unsigned)k * (unsigned)ny + (unsigned)j) * (unsigned)nx + (unsigned)i;
+  const unsigned xm = i == 0 ? q + nx - 1 : q - 1, xp = i == nx - 1 ? q + 1 - nx : q + 1;
+  const unsigned ym = j == 0 ? q + plane - nx : q - nx, yp = j == ny - 1 ? q + nx - plane : q + nx;
+  const unsigned zm = k == 0 ? q + n - plane : q - plane, zp = k == nz - 1 ? q + plane - n : q + plane;
+  const float* __restrict__ lo = phi + n;
+  if constexpr (std::is_same<real, float>::value) {
+    g0 = -((phi[xp] - phi[xm]) + (lo[xp] - lo[xm])) * i2h;
+    g1 = -((phi[yp] - phi[ym]) + (lo[yp] - lo[ym])) * i2h;
+    g2 = -((phi[zp] - phi[zm]) + (lo[zp] - lo[zm])) * i2h;
+  } else {
+    const ff2 dx = ff_sub(ff2{phi[xp], lo[xp]}, ff2{phi[xm], lo[xm]});
+    const ff2 dy = ff_sub(ff2{phi[yp], lo[yp]}, ff2{phi[ym], lo[ym]});
+    const ff2 dz = ff_sub(ff2{phi[zp], lo[zp]}, ff2{phi[zm], lo[zm]});
+    g0 = -((real)dx.hi + (real)dx.lo) * i2h;
+    g1 = -((real)dy.hi + (real)dy.lo) * i2h;
+    g2 = -((real)dz.hi + (real)dz.lo) * i2h;
+  }
 }
 
 // Forced-mode table of Sec. 3.1.1 as compile-time data: the half-space of integer n with
@@ -95,6 +106,32 @@ __device__ __forceinline__ void add_modes(const real* ah, const real* tx, const 
   if constexpr (M < 16) {
     add_mode<real, M>(ah, tx, ty, tz, acc);
     add_modes<real, M + 1>(ah, tx, ty, tz, acc);
+  }
+}
+
+// One task of the per-row forcing factors: for row (y, z) and n_x in {0,1,2}, component c:
+// B = sum over forced modes with that n_x of a_hat_{m,c} exp(2 pi i (n_y y~ + n_z z~)).
+template <typename real, int M>
+__device__ __forceinline__ void row_factor(const real* __restrict__ ah, int nxsel, int c,
+                                           const real* ty, const real* tz, real& bre, real& bim) {
+  if constexpr (M < 16) {
+    constexpr int NX = forced_mode_component(M, 0);
+    constexpr int NY = forced_mode_component(M, 1);
+    constexpr int NZ = forced_mode_component(M, 2);
+    if (NX == nxsel) {
+      C2<real> e{real(1), real(0)};
+      bool first = true;
+      if constexpr (NY != 0) { e = axis_factor<real, NY>(ty); first = false; }
+      if constexpr (NZ != 0) {
+        const C2<real> f = axis_factor<real, NZ>(tz);
+        e = first ? f : cmul(e, f);
+      }
+      const real are = __ldg(ah + 2 * (3 * M + c));
+      const real aim = __ldg(ah + 2 * (3 * M + c) + 1);
+      bre += are * e.re - aim * e.im;
+      bim += are * e.im + aim * e.re;
+    }
+    row_factor<real, M + 1>(ah, nxsel, c, ty, tz, bre, bim);
   }
 }
 

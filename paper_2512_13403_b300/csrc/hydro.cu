@@ -61,32 +61,6 @@ __device__ __forceinline__ Prim<real> load_prim(const real* __restrict__ U, long
 #define DH_LOAD_PRIM(arr, i0, i1)                                                       \
   Prim<real>{arr[0][i0][i1], arr[1][i0][i1], arr[2][i0][i1], arr[3][i0][i1], arr[4][i0][i1]}
 
-// One task of the per-row forcing factors: for row (y, z) and n_x in {0,1,2}, component c:
-// B = sum over forced modes with that n_x of a_hat_{m,c} exp(2 pi i (n_y y~ + n_z z~)).
-template <typename real, int M>
-__device__ __forceinline__ void row_factor(const real* __restrict__ ah, int nxsel, int c,
-                                           const real* ty, const real* tz, real& bre, real& bim) {
-  if constexpr (M < 16) {
-    constexpr int NX = forced_mode_component(M, 0);
-    constexpr int NY = forced_mode_component(M, 1);
-    constexpr int NZ = forced_mode_component(M, 2);
-    if (NX == nxsel) {
-      C2<real> e{real(1), real(0)};
-      bool first = true;
-      if constexpr (NY != 0) { e = axis_factor<real, NY>(ty); first = false; }
-      if constexpr (NZ != 0) {
-        const C2<real> f = axis_factor<real, NZ>(tz);
-        e = first ? f : cmul(e, f);
-      }
-      const real are = __ldg(ah + 2 * (3 * M + c));
-      const real aim = __ldg(ah + 2 * (3 * M + c) + 1);
-      bre += are * e.re - aim * e.im;
-      bim += are * e.im + aim * e.re;
-    }
-    row_factor<real, M + 1>(ah, nxsel, c, ty, tz, bre, bim);
-  }
-}
-
 template <typename real, int STAGE>
 __global__ void __launch_bounds__(NTHREADS)
 stage_kernel(const StageArgs<real> p, const int zchunk) {

@@ -423,6 +423,117 @@ rbgs_sweep_kernel(const float* __restrict__ eo, float* __restrict__ en, const fl
   cp_async_wait<0>();
 }
 
+// 16-byte cp.async (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// The same sweep for rows of a multiple of 4 cells, two cells per thread: a CTA owns a 64 x 8
+// column; thread (t, y) takes the pair x0 + 2t, x0 + 2t + 1 of row y, which holds one red and
+// one black cell.  Planes arrive as aligned float4 chunks covering x0 - 4 .. x0 + 67 (the red
+// cells of x0 - 2 .. x0 + 65 and their black neighbours; with n_x a multiple of 4 no chunk
+// straddles the periodic wrap), old e on rows y0 - 2 .. y0 + 9 and r on y0 - 1 .. y0 + 8.
+constexpr int S4_TX = 64, S4_TY = 8, S4_W = 72;       // tile, smem row width (floats)
+constexpr int S4_EROWS = S4_TY + 4, S4_RROWS = S4_TY + 2;
+constexpr int S4_ECH = S4_EROWS * (S4_W / 4), S4_RCH = S4_RROWS * (S4_W / 4);   // float4 chunks
+constexpr int S4_NRED = S4_RROWS * (S4_W / 2 - 2);   // red tasks: pairs x0 - 2 .. x0 + 65
+// rings: old e in use for planes p-1..p+1 plus S4_D in flight; r in use for p-1 (black), p (red),
+// S4_D in flight, and one more so that a copy never lands in the slot a slower thread's black
+// step of the previous plane may still read
+constexpr int S4_D = 2, S4_ERING = 3 + S4_D, S4_RRING = 3 + S4_D;
+
+template <bool ZERO>
+__global__ void __launch_bounds__(256)
+rbgs_sweep4_kernel(const float* __restrict__ eo, float* __restrict__ en, const float* __restrict__ r,
+                   int nx, int ny, int nz, float h2) {
+  __shared__ __align__(16) float s_eo[ZERO ? 1 : S4_ERING][S4_EROWS * S4_W];
+  __shared__ __align__(16) float s_r[S4_RRING][S4_RROWS * S4_W];
+  __shared__ float s_red[3][S4_RROWS * S4_W];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * S4_TX, y0 = blockIdx.y * S4_TY;
+  const int z0 = blockIdx.z * SW_ZC;
+  const int z1 = z0 + SW_ZC < nz ? z0 + SW_ZC : nz;
+  const int nit = z1 - z0 + 2;
+  const long long plane = (long long)nx * ny;
+  // this thread's chunk of each plane: global offset within the plane and smem offset
+  int eg = 0, es = 0, rg = 0, rs = 0;
+  const bool ech = tid < S4_ECH, rch = tid < S4_RCH;
+  {
+    const int row = tid / (S4_W / 4), cc = tid % (S4_W / 4);
+    const int gx = x0 - 4 + 4 * cc;
+    const int wx = gx < nx + 4 ? wrap(gx, nx) : 0;   // chunks past the needed halo: unused
+    const int gye = y0 - 2 + row, gyr = y0 - 1 + row;
+    eg = (gye < ny + 2 ? wrap(gye, ny) : 0) * nx + wx;
+    rg = (gyr < ny + 1 ? wrap(gyr, ny) : 0) * nx + wx;
+    es = row * S4_W + 4 * cc;
+    rs = es;
+  }
+  auto issue_group = [&](int m) {   // old-e plane z0 + m and r plane z0 - 1 + m
+    if (m < nit) {
+      if (!ZERO && ech)
+        cp_async16(&s_eo[ZERO ? 0 : (m + 2) % S4_ERING][es],
+                   eo + (long long)wrap(z0 + m, nz) * plane + eg);
+      if (rch) cp_async16(&s_r[m % S4_RRING][rs], r + (long long)wrap(z0 - 1 + m, nz) * plane + rg);
+    }
+    cp_async_commit();
+  };
+  // this thread's pair
+  const int t2 = tid % (S4_TX / 2), ty = tid / (S4_TX / 2);
+  const bool writes = x0 + 2 * t2 < nx && y0 + ty < ny;
+  float* out = en + (long long)(y0 + ty) * nx + (x0 + 2 * t2);
+
+  if (!ZERO && ech) {
+    for (int m = 0; m < 2; ++m)
+      cp_async16(&s_eo[ZERO ? 0 : m][es], eo + (long long)wrap(z0 - 2 + m, nz) * plane + eg);
+  }
+#pragma unroll
+  for (int m = 0; m < S4_D; ++m) issue_group(m);
+  int s3 = 0;
+  for (int ip = 0; ip < nit; ++ip) {
+    const int p = z0 - 1 + ip;
+    issue_group(ip + S4_D);
+    cp_async_wait<S4_D>();
+    __syncthreads();
+    const int s3p = s3 == 2 ? 0 : s3 + 1, s3m = s3 == 0 ? 2 : s3 - 1;
+    // red on plane p: pairs x0 - 2 + 2 pp (pp = 0 .. 33) of rows y0 - 1 .. y0 + 8
+    {
+      const float* rr = s_r[ip % S4_RRING];
+      float* red = s_red[s3];
+      for (int t = tid; t < S4_NRED; t += 256) {
+        const int ry = t / (S4_W / 2 - 2), pp = t % (S4_W / 2 - 2);
+        const int c = 2 + 2 * pp + ((ry + 1 + p) & 1);   // smem column (origin x0 - 4)
+        float nb = 0.f;
+        if (!ZERO) {
+          const float* em = s_eo[ZERO ? 0 : ip % S4_ERING];
+          const float* ec = s_eo[ZERO ? 0 : (ip + 1) % S4_ERING];
+          const float* ep = s_eo[ZERO ? 0 : (ip + 2) % S4_ERING];
+          const int e = (ry + 1) * S4_W + c;
+          nb = em[e] + ep[e] + ec[e - S4_W] + ec[e + S4_W] + ec[e - 1] + ec[e + 1];
+        }
+        red[ry * S4_W + c] = (nb - h2 * rr[ry * S4_W + c]) * (1.0f / 6.0f);
+      }
+    }
+    __syncthreads();
+    // black on plane p - 1 (one cell of the pair), and the write of the pair
+    if (ip >= 2) {
+      const float* rm = s_red[s3p];
+      const float* rc = s_red[s3m];
+      const float* rp = s_red[s3];
+      const int q = p - 1;
+      const int b = (ty + q + 1) & 1;                     // black cell's offset in the pair
+      const int c = (ty + 1) * S4_W + 4 + 2 * t2 + b;
+      const float nb = rm[c] + rp[c] + rc[c - S4_W] + rc[c + S4_W] + rc[c - 1] + rc[c + 1];
+      const float vb = (nb - h2 * s_r[(ip - 1) % S4_RRING][c]) * (1.0f / 6.0f);
+      const float vr = rc[b ? c - 1 : c + 1];
+      if (writes)
+        *reinterpret_cast<float2*>(out + (long long)q * plane) = b ? make_float2(vr, vb) : make_float2(vb, vr);
+    }
+    s3 = s3p;
+  }
+  cp_async_wait<0>();
+}
+
 // rc[I] = mean over the 8 children of (r - A e), coarse dims (cx, cy, cz).
 __global__ void resid_restrict_kernel(const float* __restrict__ e, const float* __restrict__ r,
                                       float* __restrict__ rc, int cx, int cy, int cz, float ih2) {
@@ -554,8 +665,14 @@ static void vcycle(dh_ctx* c, int l) {
   }
   // sweeps: e2 <- sweep(e), then swap (the first from e = 0 reads nothing)
   const dim3 sg((nx + SW_TX - 1) / SW_TX, (ny + SW_TY - 1) / SW_TY, (nz + SW_ZC - 1) / SW_ZC);
+  const dim3 sg4((nx + S4_TX - 1) / S4_TX, (ny + S4_TY - 1) / S4_TY, (nz + SW_ZC - 1) / SW_ZC);
+  const bool vec = nx % 4 == 0;
   auto sweep = [&](bool zero) {
-    if (zero)
+    if (vec && zero)
+      rbgs_sweep4_kernel<true><<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
+    else if (vec)
+      rbgs_sweep4_kernel<false><<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
+    else if (zero)
       rbgs_sweep_kernel<true><<<sg, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
     else
       rbgs_sweep_kernel<false><<<sg, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
@@ -680,6 +797,12 @@ cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, float* x) {
 // ---------------------------------------------------------------------------------------------
 // Sources after the hydro update when gravity is on: forcing -> gravity -> cooling (the Lie
 // splitting order), then the positivity/finite checks and the CFL minimum for the next step.
+// A CTA owns a 64 x 4 column of cells and marches GS_ZC planes.  The forcing is synthesised as
+// in the stage kernel: per plane, 36 threads form the row factors B[row][n_x][component] (the
+// forced modes summed over n_y, n_z for that row), and each cell adds its x twiddles, so the
+// per-cell cost is a few FMAs instead of a sum over all forced modes.
+constexpr int GS_TX = 64, GS_TY = 4, GS_ZC = 16, GS_NF = GS_TY * 9;
+
 template <typename real>
 __global__ void __launch_bounds__(256)
 gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int nx, int ny,
@@ -690,27 +813,58 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
                        real frac, int nsub_max, real dx, real dy, real dz) {
   __shared__ unsigned s_skip;
   __shared__ real red[8];
-  if (threadIdx.x == 0) s_skip = *((volatile unsigned*)&rec->flags) & FATAL_FLAGS;
+  __shared__ real fB[2][GS_TY][3][3][2];   // double-buffered by plane parity
+  const int tid = threadIdx.x;
+  if (tid == 0) s_skip = *((volatile unsigned*)&rec->flags) & FATAL_FLAGS;
   __syncthreads();
   if (s_skip) return;
   const real dt = (real)*dtp;
   const long long plane = (long long)nx * ny;
   const long long n3 = plane * nz;
-  const real* tw[3] = {tw0, tw1, tw2};
+  const int tx = tid % GS_TX, ty = tid / GS_TX;
+  const int i = blockIdx.x * GS_TX + tx, j = blockIdx.y * GS_TY + ty;
+  const int z0 = blockIdx.z * GS_ZC, z1 = z0 + GS_ZC < nz ? z0 + GS_ZC : nz;
+  const bool active = i < nx && j < ny;
+  real twx[4] = {real(0), real(0), real(0), real(0)};
+  if (forcing && active) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) twx[q] = __ldg(tw0 + 4 * i + q);
+  }
   real tmin = real(INFINITY);
   unsigned flags = 0;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3;
-       q += (long long)gridDim.x * blockDim.x) {
-    const unsigned t = (unsigned)q / (unsigned)nx;
-    const int i = (int)((unsigned)q - t * (unsigned)nx);
-    const int k = (int)(t / (unsigned)ny);
-    const int j = (int)(t - (unsigned)k * (unsigned)ny);
+  for (int k = z0; k < z1; ++k) {
+    const int buf = (k - z0) & 1;
+    if (forcing) {
+      if (tid < GS_NF) {
+        const int ly = tid / 9, rem = tid - 9 * ly;
+        const int nxsel = rem / 3, c = rem - 3 * nxsel;
+        const int yrow = (blockIdx.y * GS_TY + ly) % ny;
+        real tyv[4], tzv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          tyv[q] = __ldg(tw1 + 4 * yrow + q);
+          tzv[q] = __ldg(tw2 + 4 * k + q);
+        }
+        real bre = real(0), bim = real(0);
+        row_factor<real, 0>(ah, nxsel, c, tyv, tzv, bre, bim);
+        fB[buf][ly][nxsel][c][0] = bre;
+        fB[buf][ly][nxsel][c][1] = bim;
+      }
+      __syncthreads();   // one barrier per plane: the other buffer is rewritten a plane later
+    }
+    if (!active) continue;
+    const long long q = (long long)k * plane + (long long)j * nx + i;
     real u[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) u[c] = U[c * n3 + q];
     if (forcing) {
+      // a = 2 Re sum_{n_x} B_{n_x} exp(2 pi i n_x x~)  (Sec. 3.1.1)
       real a[3];
-      forcing_accel(ah, tw, i, j, k, a);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        a[c] = real(2) * (fB[buf][ty][0][c][0] +
+                          (fB[buf][ty][1][c][0] * twx[0] - fB[buf][ty][1][c][1] * twx[1]) +
+                          (fB[buf][ty][2][c][0] * twx[2] - fB[buf][ty][2][c][1] * twx[3]));
       const real e = (u[1] * a[0] + u[2] * a[1] + u[3] * a[2]) * dt;
       u[1] = u[1] + u[0] * a[0] * dt;
       u[2] = u[2] + u[0] * a[1] * dt;
@@ -749,9 +903,9 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tmin;
+  if ((tid & 31) == 0) red[tid >> 5] = tmin;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     real m = red[0];
     for (int w = 1; w < 8; ++w) m = fmin(m, red[w]);
     if (m < real(INFINITY)) atomicMin(&rec->cfl_min_bits, ordered_bits(m));
@@ -766,9 +920,9 @@ cudaError_t gravity_sources(dh_ctx* c, void* Ustar, const void* tab, const doubl
   // in a step, skip when an earlier failure is pending (the stage kernels already skipped)
   cudaError_t e = mg_solve<real>(c, U, in_step);
   if (e != cudaSuccess) return e;
-  const long long n = c->n3;
   prof_begin(c, DH_KERNEL_SOURCES);
-  gravity_sources_kernel<real><<<grid_for(n), 256, 0, c->stream>>>(
+  const dim3 grid((g.nx + GS_TX - 1) / GS_TX, (g.ny + GS_TY - 1) / GS_TY, (g.nz + GS_ZC - 1) / GS_ZC);
+  gravity_sources_kernel<real><<<grid, 256, 0, c->stream>>>(
       U, c->mg->phi, g.nx, g.ny, g.nz, (real)(1.0 / (2.0 * g.dx)), c->rec, dtp, in_step ? 1 : 0,
       g.forcing, (const real*)(tab ? tab : c->ahat_norm), (const real*)c->tw[0],
       (const real*)c->tw[1], (const real*)c->tw[2], g.cooling, (real)g.gamma,
