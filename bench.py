@@ -294,6 +294,8 @@ def run_ours(args):
         line["adjoint"] = adjoint_leg(args, stream)
     if not args.no_selfgrav:
         line["self_gravitating"] = selfgrav_leg(args, stream)
+    if not args.no_poisson_variants:
+        line["poisson_variants"] = poisson_variants_leg(args, stream)
     if not args.no_corrector:
         line["corrector"] = corrector_leg(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -415,6 +417,41 @@ def selfgrav_leg(args, stream):
                         "V-cycles to 1e-6 with FP64 norms; OU forcing + cooling)"}
 
 
+def poisson_variants_leg(args, stream):
+    """Cold-start Poisson solves (zero initial potential) to a relative residual of 1e-6 on a
+    lognormal density (sigma = 1, k^-2), float32 state, for each smoother x cycle of Sec. 5.2 and
+    App. C: cycles, device time per solve and per cycle (one context per variant)."""
+    import torch
+    from paper_2512_13403_b300 import inputs
+    from paper_2512_13403_b300.solver import Config, Solver
+    n = args.pv_grid
+    shape = (n, n, n)
+    out = {"grid": n, "tolerance": 1e-6, "sweeps": "2+2", "omega": 2.0 / 3.0, "variants": {}}
+    with torch.cuda.stream(stream):
+        rho = inputs.self_gravitating_box_device(shape, seed=5, sigma=1.0)[0].contiguous()
+        for smoother, cyc in (("rbgs", "V"), ("rbgs", "W"), ("jacobi", "V"), ("jacobi", "W")):
+            cfg = Config(shape=shape, precision="f32", gravity=True, four_pi_G=1.0, mg_tol=1e-6,
+                         mg_max_cycles=60, mg_smoother=smoother, mg_cycle=cyc)
+            s = Solver(cfg, stream=stream)
+            s.solve_poisson(rho, fetch=False)   # warm-up (kernels loaded, buffers touched)
+            times = []
+            for _ in range(3):
+                s.reset_potential()
+                torch.cuda.synchronize()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                _, cycles, res = s.solve_poisson(rho, fetch=False)
+                ev1.record(stream)
+                ev1.synchronize()
+                times.append(ev0.elapsed_time(ev1))
+            ms = sorted(times)[1]
+            out["variants"][f"{smoother}-{cyc}"] = {"cycles": cycles, "relative_residual": res,
+                                                    "ms_per_solve": ms, "ms_per_cycle": ms / max(cycles, 1)}
+            s.close()
+            torch.cuda.empty_cache()
+    return out
+
+
 def corrector_leg(args):
     """Config-4 style closure: solver-made pairs at 256^3 -> 64^3, BF16 tensor-core training,
     relative L2 error against the downsampled fine run over 100 coarse steps."""
@@ -462,6 +499,9 @@ def main():
     ap.add_argument("--no-corrector", action="store_true")
     ap.add_argument("--no-selfgrav", action="store_true", help="skip the 1024^3 self-gravitating leg")
     ap.add_argument("--sg-grid", type=int, default=1024)
+    ap.add_argument("--no-poisson-variants", action="store_true",
+                    help="skip the cold-start Poisson solves per smoother and cycle")
+    ap.add_argument("--pv-grid", type=int, default=512)
     ap.add_argument("--sg-steps", type=int, default=20)
     ap.add_argument("--corr-runs", type=int, default=20)
     ap.add_argument("--corr-snapshots", type=int, default=100)

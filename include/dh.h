@@ -67,13 +67,18 @@ typedef struct dh_config {
   double t_floor;            /* temperature floor (default 0.05)                           */
   double cool_frac;          /* first-substep fractional change limit f (default 0.1)      */
   int nsub_max;              /* substep cap (default 1024)                                 */
-  /* Multigrid self-gravity, Sec. 5.2: A phi = 4 pi G (rho - <rho>), red-black Gauss-Seidel
-     V-cycles.  Needs dx == dy == dz; halving stops at dims < 8 or odd, coarsest <= 1024 cells. */
+  /* Multigrid self-gravity, Sec. 5.2 and App. C: A phi = 4 pi G (rho - <rho>) by V- or
+     W-cycles smoothed by red-black Gauss-Seidel or weighted Jacobi.  Needs dx == dy == dz;
+     halving stops at dims < 8 or odd, coarsest <= 1024 cells. */
   int gravity;               /* 0/1                                                        */
   double four_pi_G;          /* 4 pi G (default 1)                                         */
   double mg_tol;             /* ||F - A phi||_2 / ||F||_2 stop tolerance (default 1e-6)   */
   int mg_max_cycles;         /* cycle cap (default 30)                                     */
   int mg_pre, mg_post;       /* smoothing sweeps before / after the coarse correction (2,2)*/
+  int mg_smoother;           /* 0: red-black Gauss-Seidel (default); 1: weighted Jacobi     */
+  double mg_omega;           /* Jacobi weight, 0 < omega <= 1 (default 2/3, Sec. 5.2)       */
+  int mg_cycle;              /* 1: V-cycle (default); 2: W-cycle, two visits of each coarser
+                                level above the coarsest (App. C)                          */
 } dh_config;
 
 /* Fills *cfg with the defaults above for an nx*ny*nz grid. */
@@ -153,6 +158,10 @@ dh_status dh_downsample(const float* U_fine, int nx, int ny, int nz, int factor,
    differences of phi enter a step); phi_out receives phi - <phi> rounded to float64. */
 dh_status dh_get_potential(dh_ctx* ctx, double* phi_out, int on_device, int* cycles,
                            double* rel_residual);
+
+/* Sets the potential, the warm start of the next Poisson solve, to zero (the cold start of
+   dh_init_state) without touching the state.  Needs gravity on.  Asynchronous on the stream. */
+dh_status dh_reset_potential(dh_ctx* ctx);
 
 /* Poisson solve of Sec. 5.2 on its own: F = four_pi_G (rho - <rho>) from one density plane
    `rho` (state index order, context precision), red-black Gauss-Seidel V-cycles warm-started from

@@ -47,6 +47,9 @@ class Config:
     mg_max_cycles: int = 30
     mg_pre: int = 2
     mg_post: int = 2
+    mg_smoother: str = "rbgs"
+    mg_omega: float = 2.0 / 3.0
+    mg_cycle: str = "V"
 
     def __post_init__(self):
         if self.dx is None:
@@ -89,7 +92,8 @@ class Simulation:
         if c.gravity:
             F = _mg.poisson_source(U[0], c.four_pi_G)
             self.phi, self.mg_cycles, self.mg_residual, ok = _mg.solve(
-                F, c.dx[0], self.phi, c.mg_tol, c.mg_max_cycles, c.mg_pre, c.mg_post)
+                F, c.dx[0], self.phi, c.mg_tol, c.mg_max_cycles, c.mg_pre, c.mg_post,
+                c.mg_smoother, c.mg_omega, c.mg_cycle)
             U = _mg.gravity_source(U, self.phi, dt, c.dx[0])
         if c.cooling:
             U, cap = _cool.cool(U, dt, c.gamma, c.t_floor, c.cool_frac, c.nsub_max)

@@ -4,9 +4,15 @@ Solves A phi = F on a periodic grid with cubic cells of width h, where A is the 
 Laplacian (Sec. 5.2) and F = 4 pi G (rho - <rho>) (Sec. 5.1, mean-subtracted source).
 
 Readings:
-  * Smoother: red-black Gauss-Seidel (the paper provides it beside weighted Jacobi; the V-cycle
-    with 2 pre- and 2 post-sweeps is the configuration built here).  Red = (i+j+k) even, updated
-    first, then black, each from the latest values: phi_i = (sum of 6 neighbours - h^2 F_i) / 6.
+  * Smoothers: red-black Gauss-Seidel (default here) and weighted Jacobi (the paper's default,
+    Sec. 5.2).  RBGS: red = (i+j+k) even, updated first, then black, each from the latest values:
+    phi_i = (sum of 6 neighbours - h^2 F_i) / 6.  Jacobi: phi + omega D^{-1} (F - A phi) with
+    D = -6/h^2, i.e. (1 - omega) phi + (omega/6)(sum of 6 neighbours - h^2 F), omega = 2/3.  The
+    paper's component form prints the first coefficient as (1 - omega)/6; the matrix form it
+    expands fixes it at (1 - omega), which is what is built.
+  * Cycles (App. C): V visits each coarser level once; W visits the next coarser level twice
+    (the second visit starting from the first's correction), recursively, except a coarsest level
+    solved exactly, which is visited once (a second exact solve changes nothing).
   * Restriction: mean of the 8 children (Sec. 5.2 full-weighting formula with 1/8).
   * Prolongation: cell-centred trilinear interpolation from the 8 nearest coarse cells; per axis
     a fine cell takes 3/4 of its parent and 1/4 of the parent's neighbour on its side, giving the
@@ -60,6 +66,11 @@ def rbgs_sweep(phi: torch.Tensor, F: torch.Tensor, h: float) -> torch.Tensor:
     return phi
 
 
+def jacobi_sweep(phi: torch.Tensor, F: torch.Tensor, h: float, omega: float) -> torch.Tensor:
+    """One weighted Jacobi pass: phi + omega D^{-1} (F - A phi), D = -6/h^2 (Sec. 5.2)."""
+    return phi + omega * (-(h * h) / 6.0) * (F - apply_A(phi, h))
+
+
 def restrict(r: torch.Tensor) -> torch.Tensor:
     nz, ny, nx = r.shape
     return r.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).mean(dim=(1, 3, 5))
@@ -110,18 +121,29 @@ def coarse_solve(F: torch.Tensor, h: float) -> torch.Tensor:
     return (_PINV_CACHE[key] @ F.reshape(-1)).reshape(F.shape)
 
 
-def vcycle(phi, F, h, shapes, level=0, npre=2, npost=2):
+def cycle(phi, F, h, shapes, level=0, npre=2, npost=2, smoother="rbgs", omega=2.0 / 3.0, gamma=1):
+    """One multigrid cycle on A phi = F: gamma = 1 is the V-cycle, gamma = 2 the W-cycle."""
     if level == len(shapes) - 1:
         return coarse_solve(F, h)
+
+    def smooth(p):
+        return rbgs_sweep(p, F, h) if smoother == "rbgs" else jacobi_sweep(p, F, h, omega)
+
     for _ in range(npre):
-        phi = rbgs_sweep(phi, F, h)
-    r = F - apply_A(phi, h)
-    rc = restrict(r)
-    ec = vcycle(torch.zeros_like(rc), rc, 2.0 * h, shapes, level + 1, npre, npost)
+        phi = smooth(phi)
+    rc = restrict(F - apply_A(phi, h))
+    ec = torch.zeros_like(rc)
+    visits = gamma if level + 1 < len(shapes) - 1 else 1
+    for _ in range(visits):
+        ec = cycle(ec, rc, 2.0 * h, shapes, level + 1, npre, npost, smoother, omega, gamma)
     phi = phi + prolong(ec)
     for _ in range(npost):
-        phi = rbgs_sweep(phi, F, h)
+        phi = smooth(phi)
     return phi
+
+
+def vcycle(phi, F, h, shapes, level=0, npre=2, npost=2):
+    return cycle(phi, F, h, shapes, level, npre, npost)
 
 
 def relative_residual(phi, F, h) -> float:
@@ -131,8 +153,9 @@ def relative_residual(phi, F, h) -> float:
     return float(torch.linalg.vector_norm(F - apply_A(phi, h))) / nF
 
 
-def solve(F: torch.Tensor, h: float, phi0=None, tol=1e-6, max_cycles=30, npre=2, npost=2):
-    """V-cycles until the relative residual meets tol; returns (phi, cycles, rel_res, converged)."""
+def solve(F: torch.Tensor, h: float, phi0=None, tol=1e-6, max_cycles=30, npre=2, npost=2,
+          smoother="rbgs", omega=2.0 / 3.0, cycle_type="V"):
+    """Cycles until the relative residual meets tol; returns (phi, cycles, rel_res, converged)."""
     shapes = level_shapes(F.shape)
     phi = torch.zeros_like(F) if phi0 is None else phi0.clone()
     if float(torch.linalg.vector_norm(F)) == 0.0:
@@ -140,7 +163,7 @@ def solve(F: torch.Tensor, h: float, phi0=None, tol=1e-6, max_cycles=30, npre=2,
     res = relative_residual(phi, F, h)
     cycles = 0
     while res > tol and cycles < max_cycles:
-        phi = vcycle(phi, F, h, shapes, 0, npre, npost)
+        phi = cycle(phi, F, h, shapes, 0, npre, npost, smoother, omega, 2 if cycle_type == "W" else 1)
         phi = phi - phi.mean()
         cycles += 1
         res = relative_residual(phi, F, h)

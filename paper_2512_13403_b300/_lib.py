@@ -29,6 +29,7 @@ class DhConfig(C.Structure):
         ("nsub_max", C.c_int),
         ("gravity", C.c_int), ("four_pi_G", C.c_double), ("mg_tol", C.c_double),
         ("mg_max_cycles", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
+        ("mg_smoother", C.c_int), ("mg_omega", C.c_double), ("mg_cycle", C.c_int),
     ]
 
 
@@ -50,6 +51,7 @@ _SIGNATURES = {
     "dh_downsample": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "dh_get_potential": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "dh_solve_poisson": (C.c_int, [_P, _P, C.c_int]),
+    "dh_reset_potential": (C.c_int, [_P]),
     "dh_adjoint_advance": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dh_conserved_totals_static": (C.c_int, [_P, C.c_int, C.c_longlong, _P, _P]),
     "dh_save": (C.c_int, [_P, C.c_char_p]),

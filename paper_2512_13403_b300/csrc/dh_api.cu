@@ -47,6 +47,7 @@ extern "C" void dh_config_default(dh_config* cfg, int nx, int ny, int nz) {
   cfg->cooling = 0; cfg->t_floor = 0.05; cfg->cool_frac = 0.1; cfg->nsub_max = 1024;
   cfg->gravity = 0; cfg->four_pi_G = 1.0; cfg->mg_tol = 1e-6; cfg->mg_max_cycles = 30;
   cfg->mg_pre = 2; cfg->mg_post = 2;
+  cfg->mg_smoother = 0; cfg->mg_omega = 2.0 / 3.0; cfg->mg_cycle = 1;
 }
 
 static std::string validate(const dh_config& c) {

@@ -77,6 +77,9 @@ std::string mg_validate(const dh_config& c) {
     return "gravity needs cubic cells (dx == dy == dz)";
   if (c.mg_max_cycles < 1 || c.mg_pre < 0 || c.mg_post < 0) return "bad multigrid cycle settings";
   if (!(c.mg_tol > 0.0)) return "mg_tol must be positive";
+  if (c.mg_smoother != 0 && c.mg_smoother != 1) return "mg_smoother must be 0 (RBGS) or 1 (Jacobi)";
+  if (!(c.mg_omega > 0.0 && c.mg_omega <= 1.0)) return "mg_omega must lie in (0, 1]";
+  if (c.mg_cycle != 1 && c.mg_cycle != 2) return "mg_cycle must be 1 (V) or 2 (W)";
   MG m;
   level_dims(c, &m);
   if (m.cells[m.L - 1] > 1024) return "coarsest multigrid level exceeds 1024 cells";
@@ -534,6 +537,109 @@ rbgs_sweep4_kernel(const float* __restrict__ eo, float* __restrict__ en, const f
   cp_async_wait<0>();
 }
 
+// Weighted Jacobi (Sec. 5.2) on A e = r from e_old into e_new: e_new = e + omega D^{-1} (r - A e)
+// with D = -6/h^2, i.e. e_new = (1 - omega) e + (omega / 6) (sum of 6 neighbours - h^2 r).
+// Rows of a multiple of 4 cells: a CTA owns a 64 x 8 column and a run of planes; old e arrives
+// by 16-byte cp.async on the tile and a one-row halo (x0 - 4 .. x0 + 67), r on the tile, two
+// planes ahead; each thread updates a pair of cells and stores a float2.
+constexpr int J4_EROWS = S4_TY + 2, J4_ECH = J4_EROWS * (S4_W / 4);
+constexpr int J4_RCH = S4_TY * (S4_TX / 4);
+constexpr int J4_D = 2, J4_ERING = 4 + J4_D, J4_RRING = 2 + J4_D;   // no slot a slower thread
+                                                                    // of the last plane reads
+
+__global__ void __launch_bounds__(256)
+jacobi4_kernel(const float* __restrict__ eo, float* __restrict__ en, const float* __restrict__ r,
+               int nx, int ny, int nz, float h2, float omega) {
+  __shared__ __align__(16) float s_e[J4_ERING][J4_EROWS * S4_W];
+  __shared__ __align__(16) float s_r[J4_RRING][S4_TY * S4_TX];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * S4_TX, y0 = blockIdx.y * S4_TY;
+  const int z0 = blockIdx.z * SW_ZC;
+  const int z1 = z0 + SW_ZC < nz ? z0 + SW_ZC : nz;
+  const int nit = z1 - z0;
+  const long long plane = (long long)nx * ny;
+  int eg = 0, es = 0, rg = 0, rs = 0;
+  const bool ech = tid < J4_ECH, rch = tid < J4_RCH;
+  {
+    const int row = tid / (S4_W / 4), cc = tid % (S4_W / 4);
+    const int gx = x0 - 4 + 4 * cc, gy = y0 - 1 + row;
+    const int wx = gx < nx + 4 ? wrap(gx, nx) : 0;
+    eg = (gy < ny + 1 ? wrap(gy, ny) : 0) * nx + wx;
+    es = row * S4_W + 4 * cc;
+    const int rrow = tid / (S4_TX / 4), rc4 = tid % (S4_TX / 4);
+    const int rgx = x0 + 4 * rc4, rgy = y0 + rrow;
+    rg = (rgx < nx && rgy < ny) ? rgy * nx + rgx : 0;
+    rs = rrow * S4_TX + 4 * rc4;
+  }
+  // e plane z0 - 1 + m in s_e[m % J4_ERING]; r plane z0 + m in s_r[m % J4_RRING]
+  auto copy_e = [&](int m) {
+    if (ech) cp_async16(&s_e[m % J4_ERING][es], eo + (long long)wrap(z0 - 1 + m, nz) * plane + eg);
+  };
+  auto issue_group = [&](int m) {   // e plane z0 + 1 + m and r plane z0 + m
+    if (m < nit) {
+      copy_e(m + 2);
+      if (rch) cp_async16(&s_r[m % J4_RRING][rs], r + (long long)(z0 + m) * plane + rg);
+    }
+    cp_async_commit();
+  };
+  const int t2 = tid % (S4_TX / 2), ty = tid / (S4_TX / 2);
+  const bool writes = x0 + 2 * t2 < nx && y0 + ty < ny;
+  float* out = en + (long long)(y0 + ty) * nx + (x0 + 2 * t2);
+  const float cw = 1.0f - omega, cn = omega * (1.0f / 6.0f);
+  copy_e(0);
+  copy_e(1);
+#pragma unroll
+  for (int m = 0; m < J4_D; ++m) issue_group(m);
+  for (int it = 0; it < nit; ++it) {
+    issue_group(it + J4_D);
+    cp_async_wait<J4_D>();
+    __syncthreads();
+    const float* em = s_e[it % J4_ERING];
+    const float* ec = s_e[(it + 1) % J4_ERING];
+    const float* ep = s_e[(it + 2) % J4_ERING];
+    const float* rr = s_r[it % J4_RRING];
+    const int c = (ty + 1) * S4_W + 4 + 2 * t2;   // the pair's first cell
+    float v[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int cu = c + u;
+      const float nb = em[cu] + ep[cu] + ec[cu - S4_W] + ec[cu + S4_W] + ec[cu - 1] + ec[cu + 1];
+      v[u] = cw * ec[cu] + cn * (nb - h2 * rr[ty * S4_TX + 2 * t2 + u]);
+    }
+    if (writes) *reinterpret_cast<float2*>(out + (long long)(z0 + it) * plane) = make_float2(v[0], v[1]);
+  }
+  cp_async_wait<0>();
+}
+
+// The same for any row length, one cell per thread from global memory.
+__global__ void jacobi_kernel(const float* __restrict__ eo, float* __restrict__ en,
+                              const float* __restrict__ r, int nx, int ny, int nz, float h2,
+                              float omega) {
+  const long long n = (long long)nx * ny * nz;
+  const float cw = 1.0f - omega, cn = omega * (1.0f / 6.0f);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const unsigned t = (unsigned)q / (unsigned)nx;
+    const int i = (int)((unsigned)q - t * (unsigned)nx);
+    const int k = (int)(t / (unsigned)ny);
+    const int j = (int)(t - (unsigned)k * (unsigned)ny);
+    const long long row = (long long)k * ny;
+    const float nb = eo[((long long)wrap(k - 1, nz) * ny + j) * nx + i] +
+                     eo[((long long)wrap(k + 1, nz) * ny + j) * nx + i] +
+                     eo[(row + wrap(j - 1, ny)) * nx + i] + eo[(row + wrap(j + 1, ny)) * nx + i] +
+                     eo[(row + j) * nx + wrap(i - 1, nx)] + eo[(row + j) * nx + wrap(i + 1, nx)];
+    en[q] = cw * eo[q] + cn * (nb - h2 * r[q]);
+  }
+}
+
+// The first Jacobi sweep of a level from e = 0: e_new = -(omega h^2 / 6) r.
+__global__ void jacobi_zero_kernel(float* __restrict__ en, const float* __restrict__ r,
+                                   long long n, float s) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    en[q] = s * r[q];
+}
+
 // rc[I] = mean over the 8 children of (r - A e), coarse dims (cx, cy, cz).
 __global__ void resid_restrict_kernel(const float* __restrict__ e, const float* __restrict__ r,
                                       float* __restrict__ rc, int cx, int cy, int cz, float ih2) {
@@ -651,8 +757,11 @@ static int grid_for(long long n) {
   return (int)b;
 }
 
-// One float32 V-cycle for A e_l = r_l starting from e_l = 0.
-static void vcycle(dh_ctx* c, int l) {
+// One float32 cycle for A e_l = r_l (Sec. 5.2; App. C): pre-smoothing, restriction of the
+// residual, the coarser level visited once (V-cycle) or twice (W-cycle: the second visit starts
+// from the first's result; a coarsest level, solved exactly, is visited once), prolongation and
+// post-smoothing.  zero_init: e_l starts at 0 (the first visit of a level), else from e_l.
+static void cycle(dh_ctx* c, int l, bool zero_init) {
   MG* m = c->mg;
   const dh_config& g = c->cfg;
   cudaStream_t s = c->stream;
@@ -663,29 +772,42 @@ static void vcycle(dh_ctx* c, int l) {
     c->launches += 1;
     return;
   }
-  // sweeps: e2 <- sweep(e), then swap (the first from e = 0 reads nothing)
+  // smoothing sweeps write e2 from e, then swap; a first sweep from e = 0 reads no e
   const dim3 sg((nx + SW_TX - 1) / SW_TX, (ny + SW_TY - 1) / SW_TY, (nz + SW_ZC - 1) / SW_ZC);
   const dim3 sg4((nx + S4_TX - 1) / S4_TX, (ny + S4_TY - 1) / S4_TY, (nz + SW_ZC - 1) / SW_ZC);
   const bool vec = nx % 4 == 0;
-  auto sweep = [&](bool zero) {
-    if (vec && zero)
+  const float omega = (float)g.mg_omega;
+  auto smooth = [&](bool zero) {
+    if (g.mg_smoother == 1) {
+      if (zero)
+        jacobi_zero_kernel<<<grid_for(m->cells[l]), 256, 0, s>>>(m->e2[l], m->r[l], m->cells[l],
+                                                                 -omega * h2 * (1.0f / 6.0f));
+      else if (vec)
+        jacobi4_kernel<<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2, omega);
+      else
+        jacobi_kernel<<<grid_for(m->cells[l]), 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny,
+                                                            nz, h2, omega);
+    } else if (vec && zero) {
       rbgs_sweep4_kernel<true><<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
-    else if (vec)
+    } else if (vec) {
       rbgs_sweep4_kernel<false><<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
-    else if (zero)
+    } else if (zero) {
       rbgs_sweep_kernel<true><<<sg, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
-    else
+    } else {
       rbgs_sweep_kernel<false><<<sg, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
+    }
     std::swap(m->e[l], m->e2[l]);
+    c->launches += 1;
   };
-  if (g.mg_pre == 0) cudaMemsetAsync(m->e[l], 0, m->cells[l] * sizeof(float), s);
-  for (int it = 0; it < g.mg_pre; ++it) sweep(it == 0);
+  if (zero_init && g.mg_pre == 0) cudaMemsetAsync(m->e[l], 0, m->cells[l] * sizeof(float), s);
+  for (int it = 0; it < g.mg_pre; ++it) smooth(zero_init && it == 0);
   resid_restrict_kernel<<<grid_for(m->cells[l + 1]), 256, 0, s>>>(
       m->e[l], m->r[l], m->r[l + 1], nx / 2, ny / 2, nz / 2, 1.0f / h2);
-  vcycle(c, l + 1);
+  const int visits = (g.mg_cycle == 2 && l + 1 < m->L - 1) ? 2 : 1;
+  for (int v = 0; v < visits; ++v) cycle(c, l + 1, v == 0);
   prolong_add_kernel<<<grid_for(m->cells[l]), 256, 0, s>>>(m->e[l], m->e[l + 1], nx / 2, ny / 2, nz / 2);
-  for (int it = 0; it < g.mg_post; ++it) sweep(false);
-  c->launches += g.mg_pre + g.mg_post + 2;
+  for (int it = 0; it < g.mg_post; ++it) smooth(false);
+  c->launches += 2;
 }
 
 // V-cycles on phi for the source in F (|F|^2 already in scal[1]) until the relative residual
@@ -727,7 +849,7 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
     if (!(rel == rel)) break;                 // non-finite residual
     if (cycles >= g.mg_max_cycles) break;
     prof_begin(c, DH_KERNEL_MG);
-    vcycle(c, 0);
+    cycle(c, 0, true);
     update_ff_kernel<<<grid_for(n), 256, 0, s>>>(m->phi, m->e[0], n);
     prof_end(c, 1);
     ++cycles;
@@ -957,6 +1079,14 @@ extern "C" dh_status dh_get_potential(dh_ctx* c, double* phi_out, int on_device,
   }
   if (cycles) *cycles = c->mg->last_cycles;
   if (rel_residual) *rel_residual = c->mg->last_res;
+  return DH_OK;
+}
+
+extern "C" dh_status dh_reset_potential(dh_ctx* c) {
+  if (!c) return DH_ERR_ARG;
+  if (!c->cfg.gravity || !c->mg) { c->err = "gravity is off"; return DH_ERR_STATE; }
+  const cudaError_t e = dh::mg_reset(c);
+  if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return DH_ERR_CUDA; }
   return DH_OK;
 }
 

@@ -39,6 +39,9 @@ class Config:
     mg_max_cycles: int = 30
     mg_pre: int = 2
     mg_post: int = 2
+    mg_smoother: str = "rbgs"     # "rbgs" or "jacobi"
+    mg_omega: float = 2.0 / 3.0
+    mg_cycle: str = "V"           # "V" or "W"
 
     def to_c(self) -> DhConfig:
         nz, ny, nx = self.shape
@@ -53,6 +56,9 @@ class Config:
         for f in ("nsub_max", "mg_max_cycles", "mg_pre", "mg_post"):
             setattr(c, f, int(getattr(self, f)))
         c.forcing, c.cooling, c.gravity = int(self.forcing), int(self.cooling), int(self.gravity)
+        c.mg_smoother = {"rbgs": 0, "jacobi": 1}[self.mg_smoother]
+        c.mg_omega = float(self.mg_omega)
+        c.mg_cycle = {"V": 1, "W": 2}[self.mg_cycle]
         c.ou_seed = int(self.ou_seed)
         return c
 
@@ -175,8 +181,13 @@ class Solver:
         self._check(self.lib.dh_get_potential(self.ctx, None, 1, C.byref(cyc), C.byref(res)))
         return cyc.value, res.value
 
-    def solve_poisson(self, rho):
-        """Standalone multigrid solve for one density plane; returns (phi, cycles, rel_res)."""
+    def reset_potential(self):
+        """Zero potential: the next solve starts cold."""
+        self._check(self.lib.dh_reset_potential(self.ctx))
+
+    def solve_poisson(self, rho, fetch: bool = True):
+        """Standalone multigrid solve for one density plane; returns (phi, cycles, rel_res), or
+        (None, cycles, rel_res) without fetch (phi stays in the context)."""
         if isinstance(rho, torch.Tensor):
             if rho.dtype != self.dtype or tuple(rho.shape) != self.shape or not rho.is_contiguous():
                 raise ValueError("rho must be a contiguous plane of the solver dtype")
@@ -185,6 +196,8 @@ class Solver:
             keep = np.ascontiguousarray(rho, dtype=np.float64 if self.dtype == torch.float64 else np.float32)
             ptr, dev = keep.ctypes.data, 0
         self._check(self.lib.dh_solve_poisson(self.ctx, C.c_void_p(ptr), dev))
+        if not fetch:
+            return (None,) + tuple(self.mg_stats())
         return self.potential()
 
     def adjoint_advance(self, n_steps: int, ckpt_every: int, dLdU_final):

@@ -41,6 +41,8 @@ def test_config_struct_matches_header_layout():
     assert abs(cfg.gamma - 5 / 3) < 1e-15 and cfg.cfl == 0.4
     assert cfg.ou_tau == 0.5 and cfg.t_floor == 0.05 and cfg.mg_tol == 1e-6
     assert cfg.mg_pre == 2 and cfg.mg_post == 2 and cfg.nsub_max == 1024
+    # the fields after the mg sweep counts (offsets follow the header's order)
+    assert cfg.mg_smoother == 0 and abs(cfg.mg_omega - 2 / 3) < 1e-15 and cfg.mg_cycle == 1
 
 
 def test_create_rejects_bad_config_without_gpu_work():
@@ -54,3 +56,10 @@ def test_create_rejects_bad_config_without_gpu_work():
     assert lib.dh_create(C.byref(cfg), None, C.byref(ctx)) == _lib.DH_ERR_ARG
     assert b">= 4" in lib.dh_last_error(None)
     assert lib.dh_status_string(_lib.DH_ERR_POSITIVITY) == b"DH_ERR_POSITIVITY"
+    for field, bad, msg in (("mg_cycle", 3, b"mg_cycle"), ("mg_smoother", 2, b"mg_smoother"),
+                            ("mg_omega", 1.5, b"mg_omega")):
+        lib.dh_config_default(C.byref(cfg), 16, 16, 16)
+        cfg.gravity = 1
+        setattr(cfg, field, bad)
+        assert lib.dh_create(C.byref(cfg), None, C.byref(ctx)) == _lib.DH_ERR_ARG
+        assert msg in lib.dh_last_error(None)

@@ -115,3 +115,56 @@ def test_nonconvergence_is_reported_and_rolled_back():
     assert e.value.status == DH_ERR_MG_NOCONV
     assert torch.equal(s.get_state().cpu(), torch.from_numpy(U0))
     assert s.time() == (0.0, 0)
+
+
+VARIANTS = [("jacobi", "W"), ("jacobi", "V"), ("rbgs", "W")]
+
+
+@pytest.mark.parametrize("smoother,cycle_type", VARIANTS)
+@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 24, 40), (12, 20, 30)])
+def test_variants_match_fft_solution(shape, smoother, cycle_type):
+    """Weighted Jacobi (omega = 2/3) and W-cycles (Sec. 5.2, App. C) reach the exact solution of
+    the same operator.  (12, 20, 30) has rows of 30 cells, not a multiple of 4 (the
+    one-cell-per-thread smoother kernels)."""
+    h = 1.0 / shape[2]
+    rho = inputs.lognormal_density(shape, 1.0, 5)
+    F = omg.poisson_source(torch.from_numpy(rho), 1.0)
+    exact = _fft_solution(F, h)
+    s = solver(shape, "f64", gravity=True, dx=(h, h, h), mg_tol=1e-11, mg_max_cycles=120,
+               mg_smoother=smoother, mg_cycle=cycle_type)
+    phi, cyc, res = s.solve_poisson(to_gpu(rho[None], "f64")[0].contiguous())
+    assert res <= 1e-11
+    assert float((phi.cpu() - exact).abs().max()) < 1e-9 * float(exact.abs().max())
+
+
+@pytest.mark.parametrize("smoother,cycle_type", VARIANTS + [("rbgs", "V")])
+def test_variant_cycle_counts_match_oracle(smoother, cycle_type):
+    """The same cycle on both sides contracts at the same rate: equal cycle counts to 1e-8
+    (the float32 corrections change the iterates only in the rounding)."""
+    shape = (64, 64, 64)
+    h = 1.0 / 64
+    rho = inputs.lognormal_density(shape, 1.0, 7)
+    s = solver(shape, "f64", gravity=True, mg_tol=1e-8, mg_max_cycles=60, mg_smoother=smoother,
+               mg_cycle=cycle_type)
+    phi, cyc, res = s.solve_poisson(to_gpu(rho[None], "f64")[0].contiguous())
+    F = omg.poisson_source(torch.from_numpy(rho), 1.0)
+    _, ocyc, ores, ok = omg.solve(F, h, tol=1e-8, max_cycles=60, smoother=smoother,
+                                  cycle_type=cycle_type)
+    assert ok and res <= 1e-8
+    assert abs(cyc - ocyc) <= 1, (cyc, ocyc)
+
+
+def test_gravity_step_jacobi_wcycle_fp64_vs_oracle():
+    shape = (16, 16, 16)
+    U0 = inputs.self_gravitating_box(shape, seed=4, sigma=1.0)
+    kw = dict(gravity=True, mg_tol=1e-11, mg_max_cycles=120, mg_smoother="jacobi", mg_cycle="W")
+    sim = odrv.Simulation(odrv.Config(shape=shape, **kw), U0)
+    s = solver(shape, "f64", **kw)
+    s.init_state(to_gpu(U0, "f64"))
+    for _ in range(3):
+        dt = s.step(0.0)
+        dto = sim.step()
+        assert dt == pytest.approx(dto, rel=1e-9)
+    phi, cyc, res = s.potential()
+    assert float((phi.cpu() - sim.phi).abs().max()) < 1e-8 * float(sim.phi.abs().max())
+    assert max(rel_linf(s.get_state(), sim.U)) <= 1e-9

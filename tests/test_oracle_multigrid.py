@@ -115,3 +115,85 @@ def test_fft_solve_single_mode_and_multigrid():
     assert ok
     phi_f = mg.fft_solve(F2, 1.0 / 16)
     assert float((phi_mg - phi_f).abs().max()) < 1e-10 * float(phi_f.abs().max())
+
+
+@pytest.mark.parametrize("omega", [2.0 / 3.0, 1.0, 0.5])
+def test_weighted_jacobi_amplifies_a_fourier_mode_by_its_symbol(omega):
+    """Weighted Jacobi phi + omega D^-1 (F - A phi), D = -6/h^2 (Sec. 5.2), on F = 0 multiplies a
+    discrete Fourier mode by 1 - omega + (omega/3) sum_a cos(2 pi m_a / n_a).  (The printed
+    component form's (1 - omega)/6 coefficient would give a different factor.)"""
+    shape = (8, 12, 16)   # (nz, ny, nx)
+    h = 1.0 / 16
+    m = (3, 2, 1)         # (m_x, m_y, m_z)
+    nz, ny, nx = shape
+    i = torch.arange(nx, dtype=torch.float64)[None, None, :]
+    j = torch.arange(ny, dtype=torch.float64)[None, :, None]
+    k = torch.arange(nz, dtype=torch.float64)[:, None, None]
+    phi = torch.cos(2 * math.pi * (m[0] * i / nx + m[1] * j / ny + m[2] * k / nz) + 0.3)
+    out = mg.jacobi_sweep(phi, torch.zeros_like(phi), h, omega)
+    sym = 1 - omega + omega / 3 * (math.cos(2 * math.pi * m[0] / nx) + math.cos(2 * math.pi * m[1] / ny)
+                                   + math.cos(2 * math.pi * m[2] / nz))
+    assert float((out - sym * phi).abs().max()) < 1e-13
+    # and the source enters as -omega h^2 F / 6
+    F = torch.rand(shape, dtype=torch.float64, generator=torch.Generator().manual_seed(1))
+    out = mg.jacobi_sweep(torch.zeros_like(F), F, h, omega)
+    assert float((out + omega * h * h / 6 * F).abs().max()) < 1e-15
+
+
+@pytest.mark.parametrize("smoother", ["rbgs", "jacobi"])
+def test_wcycle_on_two_levels_is_the_vcycle(smoother):
+    """Above an exactly solved coarsest level there is nothing to visit twice (App. C)."""
+    n = 8
+    h = 1.0 / n
+    F = mg.poisson_source(torch.from_numpy(inputs.lognormal_density((n, n, n), 1.0, 3)), 1.0)
+    shapes = mg.level_shapes(F.shape)
+    assert len(shapes) == 2
+    phi = 0.01 * F
+    v = mg.cycle(phi, F, h, shapes, smoother=smoother, gamma=1)
+    w = mg.cycle(phi, F, h, shapes, smoother=smoother, gamma=2)
+    assert torch.equal(v, w)
+
+
+@pytest.mark.parametrize("smoother", ["rbgs", "jacobi"])
+def test_wcycle_contracts_faster_than_vcycle_and_visits_levels_twice(smoother):
+    n = 32
+    h = 1.0 / n
+    F = mg.poisson_source(torch.from_numpy(inputs.lognormal_density((n, n, n), 1.0, 6)), 1.0)
+    shapes = mg.level_shapes(F.shape)
+    assert len(shapes) == 4
+
+    def rate(gamma):
+        phi = torch.zeros_like(F)
+        r = [mg.relative_residual(phi, F, h)]
+        for _ in range(4):
+            phi = mg.cycle(phi, F, h, shapes, smoother=smoother, gamma=gamma)
+            r.append(mg.relative_residual(phi - phi.mean(), F, h))
+        return r[1] / r[4]   # reduction over the last three cycles
+
+    assert rate(2) > 1.2 * rate(1)
+    # the W recursion visits level l 2^l times (the coarsest as often as its parent)
+    calls = []
+    orig = mg.coarse_solve
+
+    def counting(Fc, hc):
+        calls.append(Fc.shape)
+        return orig(Fc, hc)
+
+    mg.coarse_solve = counting
+    try:
+        mg.cycle(torch.zeros_like(F), F, h, shapes, smoother=smoother, gamma=2)
+    finally:
+        mg.coarse_solve = orig
+    assert len(calls) == 4   # levels 0, 1, 2 visited 1, 2, 4 times; level 3 once per visit of 2
+
+
+@pytest.mark.parametrize("smoother,cycle_type", [("jacobi", "W"), ("jacobi", "V"), ("rbgs", "W")])
+def test_smoother_and_cycle_variants_reach_the_fft_solution(smoother, cycle_type):
+    n = 16
+    h = 1.0 / n
+    F = mg.poisson_source(torch.from_numpy(inputs.lognormal_density((n, n, n), 1.0, 2)), 1.0)
+    phi, cycles, res, ok = mg.solve(F, h, tol=1e-12, max_cycles=80, smoother=smoother,
+                                    cycle_type=cycle_type)
+    exact = mg.fft_solve(F, h)
+    assert ok
+    assert float((phi - exact).abs().max()) < 1e-10 * float(exact.abs().max())
