@@ -28,13 +28,14 @@ from . import multigrid as _mg
 
 
 def full_step(U: torch.Tensor, dt: float, gamma: float, dx, a=None, cooling=None,
-              gravity=None) -> torch.Tensor:
+              gravity=None, scheme=None) -> torch.Tensor:
     """One step as the driver takes it: RK2 (App. A.3), then the Lie-split sources in their
     order, the forcing kick with the fixed field a (Sec. 3.1.1), self-gravity (Sec. 5:
     `gravity` = dict(four_pi_G=) or None, phi the exact solution of the seven-point Poisson
     problem, which converged V-cycles reproduce to their tolerance) and cooling (Sec. 4.3;
-    `cooling` = dict(T_floor=, frac=, nsub_max=) or None)."""
-    U = _hydro.rk2_step(U, dt, gamma, dx)
+    `cooling` = dict(T_floor=, frac=, nsub_max=) or None).  `scheme` = dict(integrator=,
+    limiter=) or None (RK2 with MC)."""
+    U = _hydro.step(U, dt, gamma, dx, **(scheme or {}))
     if a is not None:
         U = _force.apply_forcing(U, a, dt)
     if gravity is not None:
@@ -47,35 +48,36 @@ def full_step(U: torch.Tensor, dt: float, gamma: float, dx, a=None, cooling=None
 
 
 def step_vjp(U: torch.Tensor, dt: float, lam: torch.Tensor, gamma: float, dx, a=None,
-             cooling=None, gravity=None):
+             cooling=None, gravity=None, scheme=None):
     """lambda^n = (dU^{n+1}/dU^n)^T lambda^{n+1} for one step (sources optional)."""
     Ud = U.detach().clone().requires_grad_(True)
-    out = full_step(Ud, dt, gamma, dx, a, cooling, gravity)
+    out = full_step(Ud, dt, gamma, dx, a, cooling, gravity, scheme)
     (g,) = torch.autograd.grad(out, Ud, grad_outputs=lam)
     return g
 
 
 def advance_vjp(U0: torch.Tensor, dts, lam_final: torch.Tensor, gamma: float, dx, fields=None,
-                cooling=None, gravity=None):
+                cooling=None, gravity=None, scheme=None):
     """lambda^0 for U^n = H_{n-1} o ... o H_0(U^0) (fields[n]: forcing of step n, or None);
     states recomputed forward first."""
     fields = fields if fields is not None else [None] * len(dts)
     states = [U0.detach().clone()]
     with torch.no_grad():
         for n in range(len(dts) - 1):
-            states.append(full_step(states[-1], dts[n], gamma, dx, fields[n], cooling, gravity))
+            states.append(full_step(states[-1], dts[n], gamma, dx, fields[n], cooling, gravity,
+                                    scheme))
     lam = lam_final.clone()
     for n in reversed(range(len(dts))):
-        lam = step_vjp(states[n], dts[n], lam, gamma, dx, fields[n], cooling, gravity)
+        lam = step_vjp(states[n], dts[n], lam, gamma, dx, fields[n], cooling, gravity, scheme)
     return lam
 
 
 def advance(U0: torch.Tensor, dts, gamma: float, dx, fields=None, cooling=None,
-            gravity=None) -> torch.Tensor:
+            gravity=None, scheme=None) -> torch.Tensor:
     fields = fields if fields is not None else [None] * len(dts)
     U = U0.clone()
     for n, dt in enumerate(dts):
-        U = full_step(U, dt, gamma, dx, fields[n], cooling, gravity)
+        U = full_step(U, dt, gamma, dx, fields[n], cooling, gravity, scheme)
     return U
 
 

@@ -47,6 +47,8 @@ class Config:
     mg_max_cycles: int = 30
     mg_pre: int = 2
     mg_post: int = 2
+    integrator: str = "rk2"       # "rk2" or "ssprk3"
+    limiter: str = "mc"           # "mc" or "vanleer"
     mg_smoother: str = "rbgs"
     mg_omega: float = 2.0 / 3.0
     mg_cycle: str = "V"
@@ -86,7 +88,7 @@ class Simulation:
             self.ou.update(dt, self.nstep)
             a = self.ou.field(c.shape)
         self.last_field = a
-        U = _hydro.rk2_step(self.U, dt, c.gamma, c.dx)
+        U = _hydro.step(self.U, dt, c.gamma, c.dx, c.integrator, c.limiter)
         if a is not None:
             U = _force.apply_forcing(U, a, dt)
         if c.gravity:

@@ -8,6 +8,10 @@ holds the value on face i+1/2.
 Readings where the paper is silent (each also listed in the design notes):
   * MC limiter: 0 if a*b <= 0 else sign(a) * min(2|a|, 2|b|, |a+b|/2), a forward and b backward
     difference (App. A.1 names the limiter only).
+  * Van Leer limiter (App. A.1 lists it; the paper's fiducial runs use it): 0 if a*b <= 0 else
+    2ab/(a+b), the harmonic form of the classic van Leer slope.
+  * SSPRK3 (App. A.3 lists it): the Shu-Osher form U1 = U + dt L(U),
+    U2 = 3/4 U + 1/4 (U1 + dt L(U1)), U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2)).
   * Positivity fallback: if either reconstructed face state of a cell along an axis has
     rho <= 0 or P <= 0, all slopes of that cell along that axis are set to zero.
   * HLLC: Toro-Spruce-Speares star states with the Davis wave speeds of App. A.2; region
@@ -52,21 +56,32 @@ def mc_limiter(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
     return torch.where(a * b > 0.0, slope, torch.zeros_like(slope))
 
 
-def limited_slopes(W: torch.Tensor, axis: int) -> torch.Tensor:
-    """Delta W_i = MC(W_{i+1} - W_i, W_i - W_{i-1}) per primitive, with the positivity fallback."""
+def van_leer_limiter(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """Van Leer slope 2ab/(a+b) where a*b > 0, else 0 (App. A.1).  The denominator of the branch
+    not taken is replaced by 1 so that reverse mode sees no 0/0 there."""
+    pos = a * b > 0.0
+    den = torch.where(pos, a + b, torch.ones_like(a))
+    return torch.where(pos, 2.0 * a * b / den, torch.zeros_like(a))
+
+
+LIMITERS = {"mc": mc_limiter, "vanleer": van_leer_limiter}
+
+
+def limited_slopes(W: torch.Tensor, axis: int, limiter: str = "mc") -> torch.Tensor:
+    """Delta W_i = lim(W_{i+1} - W_i, W_i - W_{i-1}) per primitive, with the positivity fallback."""
     d = _dim(axis)
     Wp = torch.roll(W, -1, dims=d)
     Wm = torch.roll(W, 1, dims=d)
-    dW = mc_limiter(Wp - W, W - Wm)
+    dW = LIMITERS[limiter](Wp - W, W - Wm)
     hi = W + 0.5 * dW
     lo = W - 0.5 * dW
     bad = (hi[0] <= 0.0) | (hi[4] <= 0.0) | (lo[0] <= 0.0) | (lo[4] <= 0.0)
     return torch.where(bad.unsqueeze(0), torch.zeros_like(dW), dW)
 
 
-def face_states(W: torch.Tensor, axis: int):
+def face_states(W: torch.Tensor, axis: int, limiter: str = "mc"):
     """W^L_{i+1/2} = W_i + dW_i / 2 and W^R_{i+1/2} = W_{i+1} - dW_{i+1} / 2 (App. A.1)."""
-    dW = limited_slopes(W, axis)
+    dW = limited_slopes(W, axis, limiter)
     WL = W + 0.5 * dW
     WR = torch.roll(W - 0.5 * dW, -1, dims=_dim(axis))
     return WL, WR
@@ -133,21 +148,42 @@ def hllc_flux(WL: torch.Tensor, WR: torch.Tensor, axis: int, gamma: float) -> to
                                    torch.where(SR > 0.0, FsR, FR)))
 
 
-def rhs(U: torch.Tensor, gamma: float, dx) -> torch.Tensor:
+def rhs(U: torch.Tensor, gamma: float, dx, limiter: str = "mc") -> torch.Tensor:
     """Unsplit method-of-lines RHS dU/dt = -sum_a (F_a,i+1/2 - F_a,i-1/2) / dx_a (App. A.3)."""
     W = cons_to_prim(U, gamma)
     L = torch.zeros_like(U)
     for axis in range(3):
-        WL, WR = face_states(W, axis)
+        WL, WR = face_states(W, axis, limiter)
         F = hllc_flux(WL, WR, axis, gamma)
         L = L - (F - torch.roll(F, 1, dims=_dim(axis))) / dx[axis]
     return L
 
 
-def rk2_step(U: torch.Tensor, dt: float, gamma: float, dx) -> torch.Tensor:
+def rk2_step(U: torch.Tensor, dt: float, gamma: float, dx, limiter: str = "mc") -> torch.Tensor:
     """Heun / SSP-RK2 (App. A.3): U1 = U + dt L(U); U^{n+1} = U/2 + (U1 + dt L(U1))/2."""
-    U1 = U + dt * rhs(U, gamma, dx)
-    return 0.5 * U + 0.5 * (U1 + dt * rhs(U1, gamma, dx))
+    U1 = U + dt * rhs(U, gamma, dx, limiter)
+    return 0.5 * U + 0.5 * (U1 + dt * rhs(U1, gamma, dx, limiter))
+
+
+def ssprk3(L, U: torch.Tensor, dt: float) -> torch.Tensor:
+    """Shu-Osher SSPRK3 for dU/dt = L(U) (App. A.3)."""
+    U1 = U + dt * L(U)
+    U2 = 0.75 * U + 0.25 * (U1 + dt * L(U1))
+    return U / 3.0 + (2.0 / 3.0) * (U2 + dt * L(U2))
+
+
+def ssprk3_step(U: torch.Tensor, dt: float, gamma: float, dx, limiter: str = "mc") -> torch.Tensor:
+    return ssprk3(lambda V: rhs(V, gamma, dx, limiter), U, dt)
+
+
+def step(U: torch.Tensor, dt: float, gamma: float, dx, integrator: str = "rk2",
+         limiter: str = "mc") -> torch.Tensor:
+    """The hydro update of one step with the chosen integrator and limiter."""
+    if integrator == "rk2":
+        return rk2_step(U, dt, gamma, dx, limiter)
+    if integrator == "ssprk3":
+        return ssprk3_step(U, dt, gamma, dx, limiter)
+    raise ValueError(integrator)
 
 
 def rk2_stages(U: torch.Tensor, dt: float, gamma: float, dx):

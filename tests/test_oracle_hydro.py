@@ -165,3 +165,64 @@ def test_conserved_totals_exact_sum():
     assert tot[0] == math.fsum(U[0].reshape(-1).tolist())
     # rho = 2 on half of the y rows, 1 on the other half
     assert tot[0] == 4 * 8 * (4 * 2.0 + 4 * 1.0)
+
+
+@pytest.mark.parametrize("a,b,expected", [
+    (1.0, 3.0, 1.5), (3.0, 1.0, 1.5), (-2.0, -2.0, -2.0), (1.0, -1.0, 0.0), (0.0, 5.0, 0.0),
+    (-4.0, -1.0, -1.6), (2.0, 0.0, 0.0)])
+def test_van_leer_truth_table(a, b, expected):
+    """2ab/(a+b) on same-sign differences, else 0 (the van Leer slope of App. A.1)."""
+    got = hydro.van_leer_limiter(torch.tensor([a], dtype=torch.float64), torch.tensor([b], dtype=torch.float64))
+    assert float(got) == pytest.approx(expected, abs=1e-15)
+
+
+def test_van_leer_is_tvd_bounded_and_between_minmod_and_mc():
+    rng = np.random.default_rng(3)
+    a = torch.from_numpy(rng.normal(size=4000))
+    b = torch.from_numpy(rng.normal(size=4000))
+    vl = hydro.van_leer_limiter(a, b)
+    mc = hydro.mc_limiter(a, b)
+    same = a * b > 0
+    minmod = torch.where(same, torch.sign(a) * torch.minimum(a.abs(), b.abs()), torch.zeros_like(a))
+    assert torch.all(vl.abs() <= 2 * torch.minimum(a.abs(), b.abs()) + 1e-15)
+    assert torch.all(vl.abs() >= minmod.abs() - 1e-15)
+    assert torch.all(vl.abs() <= mc.abs() + 1e-15)
+    # gradients stay finite where a = -b (the branch not taken has a zero denominator)
+    x = torch.tensor([1.0, -2.0], dtype=torch.float64, requires_grad=True)
+    y = torch.tensor([-1.0, 2.0], dtype=torch.float64, requires_grad=True)
+    hydro.van_leer_limiter(x, y).sum().backward()
+    assert torch.all(torch.isfinite(x.grad)) and torch.all(x.grad == 0)
+
+
+@pytest.mark.parametrize("z", [-0.3, -1.0, -2.5, 0.7])
+def test_ssprk3_stability_polynomial(z):
+    """On dU/dt = lambda U the Shu-Osher SSPRK3 step multiplies by 1 + z + z^2/2 + z^3/6,
+    z = lambda dt: the third-order Taylor polynomial (App. A.3 lists SSPRK3)."""
+    lam = torch.tensor([[z, 0.4], [-0.4, z]], dtype=torch.float64)   # a rotation-damping pair
+    U = torch.tensor([1.0, -0.5], dtype=torch.float64)
+    out = hydro.ssprk3(lambda V: lam @ V, U, 1.0)
+    P = torch.eye(2, dtype=torch.float64) + lam + lam @ lam / 2 + lam @ lam @ lam / 6
+    assert torch.allclose(out, P @ U, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("integrator,limiter", [("rk2", "vanleer"), ("ssprk3", "mc"), ("ssprk3", "vanleer")])
+def test_variants_sound_wave_second_order_and_conservative(integrator, limiter):
+    g = 1.4
+    errs = []
+    for nx in (16, 32, 64):
+        U0 = inputs.sound_wave(nx, 2, 2, amp=1e-6, gamma=g)
+        U = torch.from_numpy(U0)
+        dx = (1.0 / nx, 1.0 / 2, 1.0 / 2)
+        nsteps = int(math.ceil(1.0 / (0.4 / nx)))
+        dt = 1.0 / nsteps
+        for _ in range(nsteps):
+            U = hydro.step(U, dt, g, dx, integrator, limiter)
+        errs.append(float((U[0] - torch.from_numpy(U0[0])).abs().mean()) / 1e-6)
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > 1.7, (errs, rates)
+    U0 = torch.from_numpy(inputs.kelvin_helmholtz((8, 12, 16), seed=0))
+    dxk = (1 / 16, 1 / 12, 1 / 8)
+    U1 = hydro.step(U0, 1e-3, 5 / 3, dxk, integrator, limiter)
+    t0, t1 = hydro.conserved_totals(U0), hydro.conserved_totals(U1)
+    for f in range(5):
+        assert abs(t1[f] - t0[f]) <= 1e-13 * (float(U0[f].abs().sum()) + float(U0[4].abs().sum()) * 1e-3)
