@@ -69,8 +69,14 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the sampler takes a moment to start: wait for its first line, then count only the
+            # samples from here on
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
+        self.first = len(self.lines)
         return self
 
     def _read(self):
@@ -79,6 +85,11 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc is not None:
+            # a timed region shorter than the sampling interval still gets the sample that
+            # closes it
+            t0 = time.time()
+            while len(self.lines) <= self.first and time.time() - t0 < 2.0:
+                time.sleep(0.01)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -88,7 +99,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[getattr(self, "first", 0):]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -294,6 +305,8 @@ def run_ours(args):
         line["adjoint"] = adjoint_leg(args, stream)
     if not args.no_selfgrav:
         line["self_gravitating"] = selfgrav_leg(args, stream)
+    if not args.no_scheme_variants:
+        line["scheme_variants"] = scheme_variants_leg(args, stream)
     if not args.no_poisson_variants:
         line["poisson_variants"] = poisson_variants_leg(args, stream)
     if not args.no_corrector:
@@ -417,6 +430,37 @@ def selfgrav_leg(args, stream):
                         "V-cycles to 1e-6 with FP64 norms; OU forcing + cooling)"}
 
 
+def scheme_variants_leg(args, stream):
+    """The default workload's forward step (256^3 driven cooling turbulence, float32) for each
+    limiter x integrator of App. A.1 / A.3: cell-updates/s over 20 steps after 3 warm-up."""
+    import torch
+    from paper_2512_13403_b300 import inputs
+    from paper_2512_13403_b300.solver import Config, Solver
+    n = args.grid
+    shape = (n, n, n)
+    out = {}
+    with torch.cuda.stream(stream):
+        U0 = torch.from_numpy(inputs.cooling_box(shape)).float().cuda().contiguous()
+        for integrator, limiter in (("rk2", "mc"), ("rk2", "vanleer"), ("ssprk3", "mc"),
+                                    ("ssprk3", "vanleer")):
+            cfg = Config(shape=shape, precision="f32", forcing=True, ou_seed=1, cooling=True,
+                         t_floor=0.05, integrator=integrator, limiter=limiter)
+            s = Solver(cfg, stream=stream)
+            s.init_state(U0)
+            s.advance(3)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            s.advance(20)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            out[f"{integrator}-{limiter}"] = {"value": n ** 3 * 20 / (ms * 1e-3), "unit": UNIT,
+                                              "ms_per_step": ms / 20}
+            s.close()
+    return out
+
+
 def poisson_variants_leg(args, stream):
     """Cold-start Poisson solves (zero initial potential) to a relative residual of 1e-6 on a
     lognormal density (sigma = 1, k^-2), float32 state, for each smoother x cycle of Sec. 5.2 and
@@ -499,6 +543,8 @@ def main():
     ap.add_argument("--no-corrector", action="store_true")
     ap.add_argument("--no-selfgrav", action="store_true", help="skip the 1024^3 self-gravitating leg")
     ap.add_argument("--sg-grid", type=int, default=1024)
+    ap.add_argument("--no-scheme-variants", action="store_true",
+                    help="skip the forward step per limiter and integrator")
     ap.add_argument("--no-poisson-variants", action="store_true",
                     help="skip the cold-start Poisson solves per smoother and cycle")
     ap.add_argument("--pv-grid", type=int, default=512)

@@ -79,6 +79,9 @@ typedef struct dh_config {
   double mg_omega;           /* Jacobi weight, 0 < omega <= 1 (default 2/3, Sec. 5.2)       */
   int mg_cycle;              /* 1: V-cycle (default); 2: W-cycle, two visits of each coarser
                                 level above the coarsest (App. C)                          */
+  /* Scheme (App. A.1, A.3). */
+  int limiter;               /* 0: MC (default); 1: van Leer 2ab/(a+b)                     */
+  int integrator;            /* 2: RK2 / Heun (default); 3: SSPRK3 (Shu-Osher form)        */
 } dh_config;
 
 /* Fills *cfg with the defaults above for an nx*ny*nz grid. */

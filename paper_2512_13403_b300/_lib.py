@@ -30,6 +30,7 @@ class DhConfig(C.Structure):
         ("gravity", C.c_int), ("four_pi_G", C.c_double), ("mg_tol", C.c_double),
         ("mg_max_cycles", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
         ("mg_smoother", C.c_int), ("mg_omega", C.c_double), ("mg_cycle", C.c_int),
+        ("limiter", C.c_int), ("integrator", C.c_int),
     ]
 
 

@@ -59,7 +59,7 @@ __device__ __forceinline__ void gload5(const real* __restrict__ p, long long n3,
   for (int c = 0; c < 5; ++c) out[c] = s * __ldg(p + c * n3 + idx);
 }
 
-template <typename real>
+template <typename real, int LIM>
 __global__ void __launch_bounds__(ANT)
 stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -127,18 +127,18 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
     real g[5], gLa[5], gRa[5], gLb[5], gRb[5], D[5], Bt[5];
     // face z0-3/2
     for (int c = 0; c < 5; ++c) g[c] = (mum1[c] - mum2[c]) * p.idz;
-    face_vjp(2, wm3, wm2, wm1, w0, g, gamma, gm1, gLa, gRa);
+    face_vjp<LIM>(2, wm3, wm2, wm1, w0, g, gamma, gm1, gLa, gRa);
     // face z0-1/2
     for (int c = 0; c < 5; ++c) g[c] = (mu0[c] - mum1[c]) * p.idz;
-    face_vjp(2, wm2, wm1, w0, w1, g, gamma, gm1, gLb, gRb);
+    face_vjp<LIM>(2, wm2, wm1, w0, w1, g, gamma, gm1, gLb, gRb);
     // A_{z0-1} from D = gL(z0-1/2)/2 - gR(z0-3/2)/2
     for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gLb[c] - real(0.5) * gRa[c];
-    slope_vjp(wm2, wm1, w0, D, Ap, Bt);
+    slope_vjp<LIM>(wm2, wm1, w0, D, Ap, Bt);
     // face z0+1/2
     for (int c = 0; c < 5; ++c) g[c] = (mun[c] - mu0[c]) * p.idz;
-    face_vjp(2, wm1, w0, w1, w2, g, gamma, gm1, gLn, gRn);
+    face_vjp<LIM>(2, wm1, w0, w1, w2, g, gamma, gm1, gLn, gRn);
     for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gLn[c] - real(0.5) * gRb[c];
-    slope_vjp(wm1, w0, w1, D, Ac, Bc);
+    slope_vjp<LIM>(wm1, w0, w1, D, Ac, Bc);
     for (int c = 0; c < 5; ++c) gRc[c] = gRb[c];
   }
 
@@ -159,9 +159,9 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       const Prim<real> w3 = ring_prim(S, s3, ty + 3, tx + 3);
       real g[5], gL2[5], gR2[5], D[5], An[5], Bn[5];
       for (int c = 0; c < 5; ++c) g[c] = (mun2[c] - mun[c]) * p.idz;
-      face_vjp(2, w0, w1, w2, w3, g, gamma, gm1, gL2, gR2);
+      face_vjp<LIM>(2, w0, w1, w2, w3, g, gamma, gm1, gL2, gR2);
       for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gL2[c] - real(0.5) * gRn[c];
-      slope_vjp(w0, w1, w2, D, An, Bn);
+      slope_vjp<LIM>(w0, w1, w2, D, An, Bn);
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         gW[c] = (gLn[c] + gRc[c]) + Ap[c] - Ac[c] + Bc[c] - Bn[c];
@@ -183,7 +183,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
         const int sy = ly + 3;
 #pragma unroll
         for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][ly + 2][q + 1] - S.mu[c][ly + 2][q]) * p.idx;
-        face_vjp(0, ring_prim(S, s0, sy, q), ring_prim(S, s0, sy, q + 1), ring_prim(S, s0, sy, q + 2),
+        face_vjp<LIM>(0, ring_prim(S, s0, sy, q), ring_prim(S, s0, sy, q + 1), ring_prim(S, s0, sy, q + 2),
                  ring_prim(S, s0, sy, q + 3), g, gamma, gm1, gL, gR);
       } else {
         const int fy = f - NFX;
@@ -191,7 +191,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
         const int sx = lx + 3;
 #pragma unroll
         for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][q + 1][lx + 2] - S.mu[c][q][lx + 2]) * p.idy;
-        face_vjp(1, ring_prim(S, s0, q, sx), ring_prim(S, s0, q + 1, sx), ring_prim(S, s0, q + 2, sx),
+        face_vjp<LIM>(1, ring_prim(S, s0, q, sx), ring_prim(S, s0, q + 1, sx), ring_prim(S, s0, q + 2, sx),
                  ring_prim(S, s0, q + 3, sx), g, gamma, gm1, gL, gR);
       }
 #pragma unroll
@@ -206,7 +206,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
 #pragma unroll
         for (int c = 0; c < 5; ++c)
           D[c] = real(0.5) * S.face[c][ly * NFXA + r + 1] - real(0.5) * S.face[5 + c][ly * NFXA + r];
-        slope_vjp(ring_prim(S, s0, sy, r + 1), ring_prim(S, s0, sy, r + 2),
+        slope_vjp<LIM>(ring_prim(S, s0, sy, r + 1), ring_prim(S, s0, sy, r + 2),
                   ring_prim(S, s0, sy, r + 3), D, A, B);
       } else {
         const int ey = e - NCX;
@@ -216,7 +216,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
         for (int c = 0; c < 5; ++c)
           D[c] = real(0.5) * S.face[c][NFX + (r + 1) * ABX + lx] -
                  real(0.5) * S.face[5 + c][NFX + r * ABX + lx];
-        slope_vjp(ring_prim(S, s0, r + 1, sx), ring_prim(S, s0, r + 2, sx),
+        slope_vjp<LIM>(ring_prim(S, s0, r + 1, sx), ring_prim(S, s0, r + 2, sx),
                   ring_prim(S, s0, r + 3, sx), D, A, B);
       }
 #pragma unroll
@@ -251,6 +251,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       for (int c = 0; c < 5; ++c) {
         real v = p.c1 * __ldg(p.lam_out + c * n3 + idx) + gU[c];
         if (p.extra) v += p.c2 * __ldg(p.extra + c * n3 + idx);
+        if (p.extra2) v += p.c3 * __ldg(p.extra2 + c * n3 + idx);
         p.lam_in[c * n3 + idx] = v;
       }
     }
@@ -273,11 +274,14 @@ cudaError_t launch_stage_adjoint(const AdjointArgs<real>& a, cudaStream_t s) {
   const int zc = adj_zchunk(a.nx, a.ny, a.nz);
   dim3 grid((a.nx + ABX - 1) / ABX, (a.ny + ABY - 1) / ABY, (a.nz + zc - 1) / zc);
   const size_t smem = sizeof(AdjSmem<real>);
-  cudaError_t e = cudaFuncSetAttribute(stage_adjoint_kernel<real>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  stage_adjoint_kernel<real><<<grid, ANT, smem, s>>>(a, zc);
-  return cudaGetLastError();
+  auto run = [&](auto kernel) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, ANT, smem, s>>>(a, zc);
+    return cudaGetLastError();
+  };
+  return a.limiter == LIM_VL ? run(stage_adjoint_kernel<real, LIM_VL>)
+                             : run(stage_adjoint_kernel<real, LIM_MC>);
 }
 template cudaError_t launch_stage_adjoint<float>(const AdjointArgs<float>&, cudaStream_t);
 template cudaError_t launch_stage_adjoint<double>(const AdjointArgs<double>&, cudaStream_t);
@@ -405,9 +409,11 @@ struct AdjointSpace {
   std::vector<void*> ckpt;   // U at steps 0, k, 2k, ...
   std::vector<void*> seg;    // segment inputs U^{m0+1..m0+k-1}
   std::vector<void*> seg1;   // segment stage-1 outputs U1^{m0..m0+k-1}
+  std::vector<void*> seg2;   // SSPRK3: segment stage-2 outputs U2^{m0..m0+k-1}
   std::vector<void*> segH;   // segment stage-2 states before the sources (forcing / cooling on)
   void* scratch = nullptr;   // replayed output nobody reads
-  void* lam[4] = {nullptr, nullptr, nullptr, nullptr};
+  // lambda of: the step output, the step input, U1, the pre-source state, U2 (SSPRK3)
+  void* lam[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double* dts = nullptr;
   void* tabs = nullptr;      // normalised OU table of every step (96 reals each)
   // gravity: the potential at every checkpoint (warm start of the replay), of every segment
@@ -416,7 +422,7 @@ struct AdjointSpace {
   double *hbuf = nullptr, *psi = nullptr;
   float *wsol = nullptr, *phi_keep = nullptr;   // float-float, planar
   int nck = 0, k = 0, nsteps = 0;
-  bool sources = false, gravity = false;
+  bool sources = false, gravity = false, rk3 = false;
 };
 
 namespace dh {
@@ -426,6 +432,7 @@ void adjoint_free(dh_ctx* c) {
   for (void* p : a->ckpt) cudaFree(p);
   for (void* p : a->seg) cudaFree(p);
   for (void* p : a->seg1) cudaFree(p);
+  for (void* p : a->seg2) cudaFree(p);
   for (void* p : a->segH) cudaFree(p);
   for (void* p : a->lam) cudaFree(p);
   cudaFree(a->scratch);
@@ -448,9 +455,10 @@ static cudaError_t adjoint_reserve(dh_ctx* c, int n, int k) {
   const int nck = (n + k - 1) / k;
   const bool gravity = c->cfg.gravity;
   const bool sources = c->cfg.forcing || c->cfg.cooling || gravity;
+  const bool rk3 = c->cfg.integrator == 3;
   AdjointSpace* a = c->adj;
   if (a && a->nck >= nck && a->k == k && a->nsteps >= n && a->sources == sources &&
-      a->gravity == gravity)
+      a->gravity == gravity && a->rk3 == rk3)
     return cudaSuccess;
   adjoint_free(c);
   a = new AdjointSpace();
@@ -460,6 +468,7 @@ static cudaError_t adjoint_reserve(dh_ctx* c, int n, int k) {
   a->nsteps = n;
   a->sources = sources;
   a->gravity = gravity;
+  a->rk3 = rk3;
   cudaError_t e = cudaSuccess;
   if (gravity) {
     const size_t pb = (size_t)c->n3 * sizeof(double);
@@ -475,12 +484,15 @@ static cudaError_t adjoint_reserve(dh_ctx* c, int n, int k) {
   a->ckpt.assign(nck, nullptr);
   a->seg.assign(k > 1 ? k - 1 : 0, nullptr);
   a->seg1.assign(k, nullptr);
+  a->seg2.assign(rk3 ? k : 0, nullptr);
   a->segH.assign(sources ? k : 0, nullptr);
   for (auto& p : a->ckpt) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
   for (auto& p : a->seg) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
   for (auto& p : a->seg1) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
+  for (auto& p : a->seg2) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
   for (auto& p : a->segH) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
-  for (auto& p : a->lam) if (e == cudaSuccess) e = cudaMalloc(&p, c->state_bytes);
+  for (int q = 0; q < (rk3 ? 5 : 4); ++q)
+    if (e == cudaSuccess) e = cudaMalloc(&a->lam[q], c->state_bytes);
   if (e == cudaSuccess && sources) e = cudaMalloc(&a->scratch, c->state_bytes);
   if (e == cudaSuccess && sources)
     e = cudaMalloc(&a->tabs, (size_t)(n > 0 ? n : 1) * 96 * sizeof(double));
@@ -489,13 +501,14 @@ static cudaError_t adjoint_reserve(dh_ctx* c, int n, int k) {
   return e;
 }
 
-// Re-runs one stage as the forward ran it.  Stage 2 with sources applies the step's forcing
-// table `tab` and cooling exactly as the fused forward kernel did, and stores the state before
-// the sources into pre_src.
+// Re-runs one stage as the forward ran it: stage 1, or a combination stage
+// out = w0 U0 + w1 (U + dt L(U)), the step's final one (final) or SSPRK3's middle one.  The final
+// stage with sources applies the step's forcing table `tab` and cooling exactly as the fused
+// forward kernel did, and stores the state before the sources into pre_src.
 template <typename real>
 static cudaError_t replay_stage(dh_ctx* c, int stage, const void* U, const void* U0, void* out,
-                                const double* dtp, const void* tab = nullptr,
-                                void* pre_src = nullptr) {
+                                const double* dtp, real w0, real w1, bool final,
+                                const void* tab = nullptr, void* pre_src = nullptr) {
   const dh_config& g = c->cfg;
   StageArgs<real> a;
   memset(&a, 0, sizeof(a));
@@ -505,7 +518,10 @@ static cudaError_t replay_stage(dh_ctx* c, int stage, const void* U, const void*
   a.idx = (real)(1.0 / g.dx); a.idy = (real)(1.0 / g.dy); a.idz = (real)(1.0 / g.dz);
   a.dx = (real)g.dx; a.dy = (real)g.dy; a.dz = (real)g.dz;
   a.rec = c->rec; a.dtp = dtp;
-  if (stage == 2 && pre_src) {
+  a.limiter = g.limiter;
+  a.w0 = w0; a.w1 = w1;
+  a.final_stage = final ? 1 : 0;
+  if (stage == 2 && final && pre_src) {
     a.pre_src = (real*)pre_src;
     a.forcing = g.forcing && tab;
     a.ahat_norm = (const real*)tab;
@@ -513,15 +529,18 @@ static cudaError_t replay_stage(dh_ctx* c, int stage, const void* U, const void*
     a.cooling = g.cooling;
     a.t_floor = (real)g.t_floor; a.cool_frac = (real)g.cool_frac; a.nsub_max = g.nsub_max;
   }
-  prof_begin(c, stage == 1 ? DH_KERNEL_STAGE1 : DH_KERNEL_STAGE2);
-  cudaError_t e = launch_stage<real>(stage, a, c->stream);
+  prof_begin(c, stage == 2 && final ? DH_KERNEL_STAGE2 : DH_KERNEL_STAGE1);
+  // RK2's final stage is kernel stage 2; SSPRK3's weighted stages are kernel stage 3
+  const bool rk2_final = stage == 2 && final && w0 == real(0.5) && w1 == real(0.5);
+  cudaError_t e = launch_stage<real>(stage == 1 ? 1 : (rk2_final ? 2 : 3), a, c->stream);
   prof_end(c, 1);
   return e;
 }
 
 template <typename real>
 static cudaError_t adjoint_stage(dh_ctx* c, const void* U, const void* lam_out, const void* extra,
-                                 void* lam_in, real c1, real c2, real beta, const double* dtp) {
+                                 void* lam_in, real c1, real c2, real beta, const double* dtp,
+                                 const void* extra2 = nullptr, real c3 = real(0)) {
   const dh_config& g = c->cfg;
   AdjointArgs<real> a;
   a.U = (const real*)U; a.lam_out = (const real*)lam_out; a.extra = (const real*)extra;
@@ -530,6 +549,8 @@ static cudaError_t adjoint_stage(dh_ctx* c, const void* U, const void* lam_out, 
   a.gamma = (real)g.gamma; a.gm1 = (real)(g.gamma - 1.0);
   a.idx = (real)(1.0 / g.dx); a.idy = (real)(1.0 / g.dy); a.idz = (real)(1.0 / g.dz);
   a.c1 = c1; a.c2 = c2; a.beta = beta; a.dtp = dtp;
+  a.extra2 = (const real*)extra2; a.c3 = c3;
+  a.limiter = g.limiter;
   prof_begin(c, DH_KERNEL_ADJOINT);
   cudaError_t e = launch_stage_adjoint<real>(a, c->stream);
   prof_end(c, 1);
@@ -560,27 +581,36 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
       e = cudaMemcpyAsync(mg_phi(c), a->ckPhi[sgi], pb, cudaMemcpyDeviceToDevice, c->stream);
       if (e != cudaSuccess) return e;
     }
+    // final-stage weights: RK2 (1/2, 1/2); SSPRK3 (1/3, 2/3) after the middle stage (3/4, 1/4)
+    const real fw0 = a->rk3 ? real(1.0 / 3.0) : real(0.5), fw1 = a->rk3 ? real(2.0 / 3.0) : real(0.5);
     for (int j = 0; j < len; ++j) {
-      e = replay_stage<real>(c, 1, in(j), nullptr, a->seg1[j], a->dts + m0 + j);
+      const double* dtp = a->dts + m0 + j;
+      e = replay_stage<real>(c, 1, in(j), nullptr, a->seg1[j], dtp, real(1), real(1), false);
       if (e != cudaSuccess) return e;
+      const void* last = a->seg1[j];   // input of the final stage
+      if (a->rk3) {
+        e = replay_stage<real>(c, 2, a->seg1[j], in(j), a->seg2[j], dtp, real(0.75), real(0.25), false);
+        if (e != cudaSuccess) return e;
+        last = a->seg2[j];
+      }
       if (a->gravity) {
-        // stage 2 without fused sources, then the Poisson solve and forcing -> gravity ->
-        // cooling exactly as the forward step took them
+        // the final stage without fused sources, then the Poisson solve and forcing -> gravity
+        // -> cooling exactly as the forward step took them
         void* out = j + 1 < len ? in(j + 1) : a->scratch;
-        e = replay_stage<real>(c, 2, a->seg1[j], in(j), out, a->dts + m0 + j);
+        e = replay_stage<real>(c, 2, last, in(j), out, dtp, fw0, fw1, true);
         if (e == cudaSuccess)
           e = cudaMemcpyAsync(a->segH[j], out, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
-        if (e == cudaSuccess) e = gravity_sources<real>(c, out, tab(m0 + j), a->dts + m0 + j, false);
+        if (e == cudaSuccess) e = gravity_sources<real>(c, out, tab(m0 + j), dtp, false);
         if (e == cudaSuccess)
           e = cudaMemcpyAsync(a->segPhi[j], mg_phi(c), pb, cudaMemcpyDeviceToDevice, c->stream);
         if (e != cudaSuccess) return e;
       } else if (src) {
-        // with sources the last stage 2 is replayed too: its pre-source state is needed
-        e = replay_stage<real>(c, 2, a->seg1[j], in(j), j + 1 < len ? in(j + 1) : a->scratch,
-                               a->dts + m0 + j, tab(m0 + j), a->segH[j]);
+        // with sources the last final stage is replayed too: its pre-source state is needed
+        e = replay_stage<real>(c, 2, last, in(j), j + 1 < len ? in(j + 1) : a->scratch, dtp, fw0,
+                               fw1, true, tab(m0 + j), a->segH[j]);
         if (e != cudaSuccess) return e;
       } else if (j + 1 < len) {
-        e = replay_stage<real>(c, 2, a->seg1[j], in(j), in(j + 1), a->dts + m0 + j);
+        e = replay_stage<real>(c, 2, last, in(j), in(j + 1), dtp, fw0, fw1, true);
         if (e != cudaSuccess) return e;
       }
     }
@@ -620,12 +650,28 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
           if (e != cudaSuccess) return e;
         }
       }
-      // stage 2: U_H = U^n/2 + (U1 + dt L(U1))/2
-      e = adjoint_stage<real>(c, a->seg1[j], lam_h, nullptr, lam_u1, real(0.5), real(0), real(0.5), dtp);
-      if (e != cudaSuccess) return e;
-      // stage 1: U1 = U^n + dt L(U^n); lambda^n also receives lambda_H/2 from stage 2
-      e = adjoint_stage<real>(c, in(j), lam_u1, lam_h, lam_new, real(1), real(0.5), real(1), dtp);
-      if (e != cudaSuccess) return e;
+      if (!a->rk3) {
+        // stage 2: U_H = U^n/2 + (U1 + dt L(U1))/2
+        e = adjoint_stage<real>(c, a->seg1[j], lam_h, nullptr, lam_u1, real(0.5), real(0), real(0.5), dtp);
+        if (e != cudaSuccess) return e;
+        // stage 1: U1 = U^n + dt L(U^n); lambda^n also receives lambda_H/2 from stage 2
+        e = adjoint_stage<real>(c, in(j), lam_u1, lam_h, lam_new, real(1), real(0.5), real(1), dtp);
+        if (e != cudaSuccess) return e;
+      } else {
+        void* lam_u2 = a->lam[4];
+        // stage 3: U_H = U^n/3 + 2/3 (U2 + dt L(U2))
+        e = adjoint_stage<real>(c, a->seg2[j], lam_h, nullptr, lam_u2, real(2.0 / 3.0), real(0),
+                                real(2.0 / 3.0), dtp);
+        if (e != cudaSuccess) return e;
+        // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
+        e = adjoint_stage<real>(c, a->seg1[j], lam_u2, nullptr, lam_u1, real(0.25), real(0),
+                                real(0.25), dtp);
+        if (e != cudaSuccess) return e;
+        // stage 1: U1 = U^n + dt L(U^n); lambda^n also receives lambda_H/3 and 3/4 lambda_U2
+        e = adjoint_stage<real>(c, in(j), lam_u1, lam_h, lam_new, real(1), real(1.0 / 3.0), real(1),
+                                dtp, lam_u2, real(0.75));
+        if (e != cudaSuccess) return e;
+      }
       void* t = lam; lam = lam_new; lam_new = t;
     }
   }

@@ -1,4 +1,4 @@
-// Per-face reverse-mode building blocks of the hand adjoint: the MC slope, the limited slope
+// Per-face reverse-mode building blocks of the hand adjoint: the MC and van Leer slopes, the limited slope
 // with its positivity fallback, HLLC and the face VJP of reconstruction o HLLC (App. A.1-A.2
 // transposed).  Host and device: the same code is checked on the CPU against finite
 // differences of the forward face flux.
@@ -28,18 +28,36 @@ __host__ __device__ __forceinline__ void mc_slope_vjp(real a, real b, real D, re
   gb = real(2) * copysign(real(1), b) * Yg + real(0.5) * copysign(real(1), a + b) * Zg;
 }
 
+// Reverse of vl_slope: d/da 2ab/(a+b) = 2b^2/(a+b)^2, d/db = 2a^2/(a+b)^2 where a*b > 0, else 0.
+template <typename real>
+__host__ __device__ __forceinline__ void vl_slope_vjp(real a, real b, real D, real& ga, real& gb) {
+  ga = real(0);
+  gb = real(0);
+  if (!(a * b > real(0))) return;
+  const real is = q_div(real(1), a + b);
+  const real t = real(2) * D * is * is;
+  ga = t * b * b;
+  gb = t * a * a;
+}
+
+template <int LIM, typename real>
+__host__ __device__ __forceinline__ void lim_slope_vjp(real a, real b, real D, real& ga, real& gb) {
+  if constexpr (LIM == LIM_VL) vl_slope_vjp(a, b, D, ga, gb);
+  else mc_slope_vjp(a, b, D, ga, gb);
+}
+
 // A_i = dL/da_i, B_i = dL/db_i of a cell from D = dL/d(dW_i); zero when the positivity fallback
 // zeroed the cell's slopes.
-template <typename real>
+template <int LIM = LIM_MC, typename real>
 __host__ __device__ __forceinline__ void slope_vjp(const Prim<real>& wm, const Prim<real>& w0,
                                           const Prim<real>& wp, const real D[5], real A[5],
                                           real B[5]) {
-  const Prim<real> d = limited_slope(wm, w0, wp);
+  const Prim<real> d = limited_slope<LIM>(wm, w0, wp);
   const bool zeroed = (d.r == real(0) && d.vx == real(0) && d.vy == real(0) && d.vz == real(0) &&
                        d.p == real(0));
   // recompute the unguarded slopes to tell the fallback apart from slopes that are all zero
-  const real hr = real(0.5) * mc_slope(wp.r - w0.r, w0.r - wm.r);
-  const real hp = real(0.5) * mc_slope(wp.p - w0.p, w0.p - wm.p);
+  const real hr = real(0.5) * lim_slope<LIM>(wp.r - w0.r, w0.r - wm.r);
+  const real hp = real(0.5) * lim_slope<LIM>(wp.p - w0.p, w0.p - wm.p);
   const bool fallback = zeroed && ((w0.r + hr <= real(0)) || (w0.p + hp <= real(0)) ||
                                    (w0.r - hr <= real(0)) || (w0.p - hp <= real(0)));
   if (fallback) {
@@ -47,11 +65,11 @@ __host__ __device__ __forceinline__ void slope_vjp(const Prim<real>& wm, const P
     for (int c = 0; c < 5; ++c) { A[c] = real(0); B[c] = real(0); }
     return;
   }
-  mc_slope_vjp(wp.r - w0.r, w0.r - wm.r, D[0], A[0], B[0]);
-  mc_slope_vjp(wp.vx - w0.vx, w0.vx - wm.vx, D[1], A[1], B[1]);
-  mc_slope_vjp(wp.vy - w0.vy, w0.vy - wm.vy, D[2], A[2], B[2]);
-  mc_slope_vjp(wp.vz - w0.vz, w0.vz - wm.vz, D[3], A[3], B[3]);
-  mc_slope_vjp(wp.p - w0.p, w0.p - wm.p, D[4], A[4], B[4]);
+  lim_slope_vjp<LIM>(wp.r - w0.r, w0.r - wm.r, D[0], A[0], B[0]);
+  lim_slope_vjp<LIM>(wp.vx - w0.vx, w0.vx - wm.vx, D[1], A[1], B[1]);
+  lim_slope_vjp<LIM>(wp.vy - w0.vy, w0.vy - wm.vy, D[2], A[2], B[2]);
+  lim_slope_vjp<LIM>(wp.vz - w0.vz, w0.vz - wm.vz, D[3], A[3], B[3]);
+  lim_slope_vjp<LIM>(wp.p - w0.p, w0.p - wm.p, D[4], A[4], B[4]);
 }
 
 // Reverse of hllc() in the face frame (r, u, a, b, p) for both sides.
@@ -173,13 +191,13 @@ __host__ __device__ __forceinline__ void hllc_vjp(real rL, real uL, real aL, rea
 // Face VJP along `axis` from the four primitive cells around the face and the flux gradient
 // g[5] in (rho, m_x, m_y, m_z, E) order; returns gradients of the two reconstructed states in
 // (rho, v_x, v_y, v_z, P) order.
-template <typename real>
+template <int LIM = LIM_MC, typename real>
 __host__ __device__ __forceinline__ void face_vjp(int axis, const Prim<real>& w0, const Prim<real>& w1,
                                          const Prim<real>& w2, const Prim<real>& w3,
                                          const real g[5], real gamma, real gm1, real gL[5],
                                          real gR[5]) {
-  const Prim<real> L = add_half(w1, limited_slope(w0, w1, w2), real(1));
-  const Prim<real> R = add_half(w2, limited_slope(w1, w2, w3), real(-1));
+  const Prim<real> L = add_half(w1, limited_slope<LIM>(w0, w1, w2), real(1));
+  const Prim<real> R = add_half(w2, limited_slope<LIM>(w1, w2, w3), real(-1));
   real fL[5], fR[5];
   if (axis == 0) {
     hllc_vjp(L.r, L.vx, L.vy, L.vz, L.p, R.r, R.vx, R.vy, R.vz, R.p, gamma, gm1, g[0], g[1], g[2],

@@ -48,6 +48,7 @@ extern "C" void dh_config_default(dh_config* cfg, int nx, int ny, int nz) {
   cfg->gravity = 0; cfg->four_pi_G = 1.0; cfg->mg_tol = 1e-6; cfg->mg_max_cycles = 30;
   cfg->mg_pre = 2; cfg->mg_post = 2;
   cfg->mg_smoother = 0; cfg->mg_omega = 2.0 / 3.0; cfg->mg_cycle = 1;
+  cfg->limiter = 0; cfg->integrator = 2;
 }
 
 static std::string validate(const dh_config& c) {
@@ -58,6 +59,8 @@ static std::string validate(const dh_config& c) {
   if (!(c.gamma > 1.0)) return "gamma must exceed 1";
   if (!(c.cfl > 0.0)) return "cfl must be positive";
   if (!(c.dt_max > 0.0)) return "dt_max must be positive";
+  if (c.limiter != 0 && c.limiter != 1) return "limiter must be 0 (MC) or 1 (van Leer)";
+  if (c.integrator != 2 && c.integrator != 3) return "integrator must be 2 (RK2) or 3 (SSPRK3)";
   if (c.forcing) {
     if (c.nx < 5 || c.ny < 5 || c.nz < 5) return "forcing needs every dimension >= 5";
     if (!(c.ou_tau > 0.0) || !(c.ou_arms >= 0.0)) return "ou_tau must be > 0 and ou_arms >= 0";
@@ -266,6 +269,9 @@ static StageArgs<real> stage_args(dh_ctx* c) {
   a.ahat_norm = (const real*)c->ahat_norm;
   for (int q = 0; q < 3; ++q) a.tw[q] = (const real*)c->tw[q];
   a.t_floor = (real)g.t_floor; a.cool_frac = (real)g.cool_frac; a.nsub_max = g.nsub_max;
+  a.limiter = g.limiter;
+  a.w0 = real(0.5); a.w1 = real(0.5);
+  a.final_stage = 1;
   return a;
 }
 
@@ -287,19 +293,36 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed) {
   StageArgs<real> a = stage_args<real>(c);
   const real* Un = (const real*)c->U[c->cur];
   real* Unew = (real*)c->U[1 - c->cur];
-  a.U = Un; a.U0 = nullptr; a.out = (real*)c->U1;
+  const bool rk3 = g.integrator == 3;
+  // RK2: U^n -> U1 (scratch) -> U^{n+1}.  SSPRK3: U^n -> U1 (in the output buffer) -> U2
+  // (scratch) -> U^{n+1}; U^n is never written, so it stays the last good state.
+  real* Ust1 = rk3 ? Unew : (real*)c->U1;
+  a.U = Un; a.U0 = nullptr; a.out = Ust1;
   prof_begin(c, DH_KERNEL_STAGE1);
   e = launch_stage<real>(1, a, c->stream);
   prof_end(c, 1);
   if (e != cudaSuccess) return e;
+  const real* Ulast = Ust1;
+  if (rk3) {
+    StageArgs<real> m = a;
+    m.U = Ust1; m.U0 = Un; m.out = (real*)c->U1;
+    m.w0 = real(0.75); m.w1 = real(0.25);
+    m.final_stage = 0;
+    prof_begin(c, DH_KERNEL_STAGE1);
+    e = launch_stage<real>(3, m, c->stream);
+    prof_end(c, 1);
+    if (e != cudaSuccess) return e;
+    Ulast = (const real*)c->U1;
+    a.w0 = real(1.0 / 3.0); a.w1 = real(2.0 / 3.0);
+  }
 
-  a.U = (const real*)c->U1; a.U0 = Un; a.out = Unew;
+  a.U = Ulast; a.U0 = Un; a.out = Unew;
   const bool fuse = !g.gravity;
   a.forcing = fuse ? g.forcing : 0;
   a.cooling = fuse ? g.cooling : 0;
   a.reduce_cfl = fuse ? 1 : 0;
   prof_begin(c, DH_KERNEL_STAGE2);
-  e = launch_stage<real>(2, a, c->stream);
+  e = launch_stage<real>(rk3 ? 3 : 2, a, c->stream);
   prof_end(c, 1);
   if (e != cudaSuccess) return e;
   if (!fuse) {

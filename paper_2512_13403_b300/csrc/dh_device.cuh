@@ -108,13 +108,28 @@ __device__ __forceinline__ float2 mc_slope2(float2 a, float2 b) {
   return f2(ab.x > 0.0f ? copysignf(m.x, a.x) : 0.0f, ab.y > 0.0f ? copysignf(m.y, a.y) : 0.0f);
 }
 
+// Van Leer (App. A.1): 0 if a*b <= 0 else 2ab/(a+b), the harmonic form.
+template <typename real>
+__host__ __device__ __forceinline__ real vl_slope(real a, real b) {
+  const real ab = a * b;
+  return ab > real(0) ? q_div(real(2) * ab, a + b) : real(0);
+}
+
+// Slope limiters: LIM_MC (default) or LIM_VL.
+constexpr int LIM_MC = 0, LIM_VL = 1;
+template <int LIM, typename real>
+__host__ __device__ __forceinline__ real lim_slope(real a, real b) {
+  if constexpr (LIM == LIM_VL) return vl_slope(a, b);
+  else return mc_slope(a, b);
+}
+
 // Limited slope of a cell from its two neighbours along one axis, with the positivity fallback:
 // if W +- dW/2 has rho <= 0 or P <= 0 every slope of the cell on that axis is zero.
-template <typename real>
+template <int LIM = LIM_MC, typename real>
 __host__ __device__ __forceinline__ Prim<real> limited_slope(const Prim<real>& wm, const Prim<real>& w0,
                                                     const Prim<real>& wp) {
 #if defined(__CUDA_ARCH__)
-  if constexpr (std::is_same<real, float>::value) {
+  if constexpr (std::is_same<real, float>::value && LIM == LIM_MC) {
     const float2 c01 = f2(w0.r, w0.vx), c23 = f2(w0.vy, w0.vz);
     const float2 d01 = mc_slope2(p_sub(f2(wp.r, wp.vx), c01), p_sub(c01, f2(wm.r, wm.vx)));
     const float2 d23 = mc_slope2(p_sub(f2(wp.vy, wp.vz), c23), p_sub(c23, f2(wm.vy, wm.vz)));
@@ -128,11 +143,11 @@ __host__ __device__ __forceinline__ Prim<real> limited_slope(const Prim<real>& w
   }
 #endif
   Prim<real> d;
-  d.r = mc_slope(wp.r - w0.r, w0.r - wm.r);
-  d.vx = mc_slope(wp.vx - w0.vx, w0.vx - wm.vx);
-  d.vy = mc_slope(wp.vy - w0.vy, w0.vy - wm.vy);
-  d.vz = mc_slope(wp.vz - w0.vz, w0.vz - wm.vz);
-  d.p = mc_slope(wp.p - w0.p, w0.p - wm.p);
+  d.r = lim_slope<LIM>(wp.r - w0.r, w0.r - wm.r);
+  d.vx = lim_slope<LIM>(wp.vx - w0.vx, w0.vx - wm.vx);
+  d.vy = lim_slope<LIM>(wp.vy - w0.vy, w0.vy - wm.vy);
+  d.vz = lim_slope<LIM>(wp.vz - w0.vz, w0.vz - wm.vz);
+  d.p = lim_slope<LIM>(wp.p - w0.p, w0.p - wm.p);
   const real hr = real(0.5) * d.r, hp = real(0.5) * d.p;
   const bool bad = (w0.r + hr <= real(0)) || (w0.p + hp <= real(0)) || (w0.r - hr <= real(0)) ||
                    (w0.p - hp <= real(0));

@@ -24,8 +24,15 @@ template <typename real> struct StageArgs {
   int nsub_max;
   int reduce_cfl;         // accumulate the CFL minimum of the output state
   real* pre_src;          // stage 2 (nullable): also store the state before the sources
+  int limiter;            // LIM_MC or LIM_VL
+  // stage 3 (SSPRK3's combinations): out = w0 U0 + w1 (U + dt L(U)), (3/4, 1/4) then (1/3, 2/3);
+  // final_stage: this one ends the step and takes the epilogue (pre_src, sources, finite and
+  // positivity checks, CFL).  Stage 2 is RK2's final stage with weights (1/2, 1/2).
+  real w0, w1;
+  int final_stage;
 };
 
+// stage 1: U + dt L(U); 2: RK2's final stage; 3: the weighted combination of SSPRK3
 template <typename real>
 cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s);
 
@@ -69,6 +76,9 @@ template <typename real> struct AdjointArgs {
   real gamma, gm1, idx, idy, idz;
   real c1, c2, beta;
   const double* dtp;
+  const real* extra2;    // added with weight c3 (nullable; SSPRK3's first stage)
+  real c3;
+  int limiter;           // LIM_MC or LIM_VL
 };
 // Adjoint of the operator-split sources of one step (forcing kick, gravity kick, cooling),
 // pointwise: lamH = (dF/dU)^T (dG/dU)^T (dC/dU)^T lam at the state UH the sources were applied

@@ -61,7 +61,7 @@ __device__ __forceinline__ Prim<real> load_prim(const real* __restrict__ U, long
 #define DH_LOAD_PRIM(arr, i0, i1)                                                       \
   Prim<real>{arr[0][i0][i1], arr[1][i0][i1], arr[2][i0][i1], arr[3][i0][i1], arr[4][i0][i1]}
 
-template <typename real, int STAGE>
+template <typename real, int STAGE, int LIM>
 __global__ void __launch_bounds__(NTHREADS)
 stage_kernel(const StageArgs<real> p, const int zchunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -86,7 +86,13 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
   const int gx = x0 + tx, gy = y0 + ty;
   const bool active = gx < nx && gy < ny;
   const int gxw = gx % nx, gyw = gy % ny;
-  const bool forcing = STAGE == 2 && p.forcing;
+  // STAGE 1: out = U + dt L(U).  STAGE 2: RK2's final stage, out = (U0 + U + dt L(U)) / 2 with
+  // the epilogue.  STAGE 3: out = w0 U0 + w1 (U + dt L(U)), with the epilogue if final_stage
+  // (SSPRK3's second and third stages).
+  constexpr bool COMB = STAGE >= 2;
+  const bool final = STAGE == 2 || (STAGE == 3 && p.final_stage);
+  const real w0 = STAGE == 2 ? real(0.5) : p.w0, w1 = STAGE == 2 ? real(0.5) : p.w1;
+  const bool forcing = final && p.forcing;
 
   if (tid < HX) S.xs[tid] = ((x0 + tid - 2) % nx + nx) % nx;
   if (tid >= 64 && tid < 64 + HY) S.ys[tid - 64] = ((y0 + tid - 64 - 2) % ny + ny) % ny;
@@ -125,8 +131,8 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
   {
     const Prim<real> w0 = smem_prim(S, 0, ty + 2, tx + 2);
     const Prim<real> w1 = smem_prim(S, 1, ty + 2, tx + 2);
-    const Prim<real> dm1 = limited_slope(wm2, wm1, w0);
-    dk = limited_slope(wm1, w0, w1);
+    const Prim<real> dm1 = limited_slope<LIM>(wm2, wm1, w0);
+    dk = limited_slope<LIM>(wm1, w0, w1);
     face_flux(2, add_half(wm1, dm1, real(1)), add_half(w0, dk, real(-1)), gamma, gm1, fz_lo);
   }
 
@@ -144,7 +150,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
         const int ly = t / (BX + 2), r = t - ly * (BX + 2);
         const int sy = ly + 2;
         const Prim<real> w1 = smem_prim(S, s0, sy, r + 1);
-        const Prim<real> d = limited_slope(smem_prim(S, s0, sy, r), w1, smem_prim(S, s0, sy, r + 2));
+        const Prim<real> d = limited_slope<LIM>(smem_prim(S, s0, sy, r), w1, smem_prim(S, s0, sy, r + 2));
         DH_STORE_PRIM(S.xm, ly, r, add_half(w1, d, real(-1)));
         DH_STORE_PRIM(S.xp, ly, r, add_half(w1, d, real(1)));
       } else {
@@ -152,7 +158,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
         const int r = u / BX, lx = u - r * BX;
         const int sx = lx + 2;
         const Prim<real> w1 = smem_prim(S, s0, r + 1, sx);
-        const Prim<real> d = limited_slope(smem_prim(S, s0, r, sx), w1, smem_prim(S, s0, r + 2, sx));
+        const Prim<real> d = limited_slope<LIM>(smem_prim(S, s0, r, sx), w1, smem_prim(S, s0, r + 2, sx));
         DH_STORE_PRIM(S.ym, r, lx, add_half(w1, d, real(-1)));
         DH_STORE_PRIM(S.yp, r, lx, add_half(w1, d, real(1)));
       }
@@ -180,7 +186,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
       const Prim<real> w0 = smem_prim(S, s0, ty + 2, tx + 2);
       const Prim<real> w1 = smem_prim(S, s1, ty + 2, tx + 2);
       const Prim<real> w2 = smem_prim(S, s2, ty + 2, tx + 2);
-      dk1 = limited_slope(w0, w1, w2);
+      dk1 = limited_slope<LIM>(w0, w1, w2);
       face_flux(2, add_half(w0, dk, real(1)), add_half(w1, dk1, real(-1)), gamma, gm1, fz_hi);
     }
     __syncthreads();  // ---- face states ready
@@ -212,7 +218,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           uin[c] = __ldg(p.U + c * n3 + idx);
-          if (STAGE == 2) un[c] = __ldg(p.U0 + c * n3 + idx);
+          if (COMB) un[c] = __ldg(p.U0 + c * n3 + idx);
         }
 #pragma unroll
         for (int c = 0; c < 4; c += 2) {
@@ -225,7 +231,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
           L = p_fma(dfy, f2s(-p.idy), L);
           L = p_fma(dfz, f2s(-p.idz), L);
           float2 v = p_fma(f2s(dt), L, f2(uin[c], uin[c + 1]));
-          if (STAGE == 2) v = p_fma(f2s(0.5f), f2(un[c], un[c + 1]), p_mul(f2s(0.5f), v));
+          if (COMB) v = p_fma(f2s(w0), f2(un[c], un[c + 1]), p_mul(f2s(w1), v));
           u[c] = v.x;
           u[c + 1] = v.y;
         }
@@ -233,7 +239,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
           float L = -((S.fx[4][ty][tx + 1] - S.fx[4][ty][tx]) * p.idx);
           L -= (S.fy[4][ty + 1][tx] - S.fy[4][ty][tx]) * p.idy;
           L -= (fz_hi[4] - fz_lo[4]) * p.idz;
-          u[4] = STAGE == 1 ? uin[4] + dt * L : 0.5f * un[4] + 0.5f * (uin[4] + dt * L);
+          u[4] = STAGE == 1 ? uin[4] + dt * L : w0 * un[4] + w1 * (uin[4] + dt * L);
         }
       } else {
 #pragma unroll
@@ -246,11 +252,11 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
             u[c] = uin + dt * L;
           } else {
             const real un = __ldg(p.U0 + c * n3 + idx);
-            u[c] = real(0.5) * un + real(0.5) * (uin + dt * L);
+            u[c] = w0 * un + w1 * (uin + dt * L);
           }
         }
       }
-      if (STAGE == 2) {
+      if (COMB && final) {
         if (p.pre_src) {
 #pragma unroll
           for (int c = 0; c < 5; ++c) p.pre_src[c * n3 + idx] = u[c];
@@ -292,7 +298,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
     for (int c = 0; c < 5; ++c) fz_lo[c] = fz_hi[c];
   }
 
-  if (STAGE == 2) {
+  if (COMB) {
     if (flags) {
       atomicOr(&p.rec->flags, flags);
       if (flags & FATAL_FLAGS) atomicCAS(&p.rec->fail_step, -1, (int)(p.rec->nstep - 1));
@@ -323,26 +329,30 @@ static int stage_zchunk(int nx, int ny, int nz) {
   return zc;
 }
 
+template <typename real, int STAGE, int LIM>
+static cudaError_t launch_stage_t(const StageArgs<real>& a, dim3 grid, size_t smem, int zc,
+                                  cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(stage_kernel<real, STAGE, LIM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  stage_kernel<real, STAGE, LIM><<<grid, NTHREADS, smem, s>>>(a, zc);
+  return cudaGetLastError();
+}
+
 template <typename real>
 cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s) {
   const int zc = stage_zchunk(a.nx, a.ny, a.nz);
   dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + zc - 1) / zc);
   const size_t smem = sizeof(StageSmem<real>);
-  cudaError_t e;
-  if (stage == 1) {
-    e = cudaFuncSetAttribute(stage_kernel<real, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    stage_kernel<real, 1><<<grid, NTHREADS, smem, s>>>(a, zc);
-  } else {
-    e = cudaFuncSetAttribute(stage_kernel<real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    stage_kernel<real, 2><<<grid, NTHREADS, smem, s>>>(a, zc);
+  if (a.limiter == LIM_VL) {
+    if (stage == 1) return launch_stage_t<real, 1, LIM_VL>(a, grid, smem, zc, s);
+    if (stage == 2) return launch_stage_t<real, 2, LIM_VL>(a, grid, smem, zc, s);
+    return launch_stage_t<real, 3, LIM_VL>(a, grid, smem, zc, s);
   }
-  return cudaGetLastError();
+  if (stage == 1) return launch_stage_t<real, 1, LIM_MC>(a, grid, smem, zc, s);
+  if (stage == 2) return launch_stage_t<real, 2, LIM_MC>(a, grid, smem, zc, s);
+  return launch_stage_t<real, 3, LIM_MC>(a, grid, smem, zc, s);
 }
-
 template cudaError_t launch_stage<float>(int, const StageArgs<float>&, cudaStream_t);
 template cudaError_t launch_stage<double>(int, const StageArgs<double>&, cudaStream_t);
 

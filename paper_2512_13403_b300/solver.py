@@ -42,6 +42,8 @@ class Config:
     mg_smoother: str = "rbgs"     # "rbgs" or "jacobi"
     mg_omega: float = 2.0 / 3.0
     mg_cycle: str = "V"           # "V" or "W"
+    limiter: str = "mc"           # "mc" or "vanleer"
+    integrator: str = "rk2"       # "rk2" or "ssprk3"
 
     def to_c(self) -> DhConfig:
         nz, ny, nx = self.shape
@@ -59,6 +61,8 @@ class Config:
         c.mg_smoother = {"rbgs": 0, "jacobi": 1}[self.mg_smoother]
         c.mg_omega = float(self.mg_omega)
         c.mg_cycle = {"V": 1, "W": 2}[self.mg_cycle]
+        c.limiter = {"mc": 0, "vanleer": 1}[self.limiter]
+        c.integrator = {"rk2": 2, "ssprk3": 3}[self.integrator]
         c.ou_seed = int(self.ou_seed)
         return c
 

@@ -43,6 +43,7 @@ def test_config_struct_matches_header_layout():
     assert cfg.mg_pre == 2 and cfg.mg_post == 2 and cfg.nsub_max == 1024
     # the fields after the mg sweep counts (offsets follow the header's order)
     assert cfg.mg_smoother == 0 and abs(cfg.mg_omega - 2 / 3) < 1e-15 and cfg.mg_cycle == 1
+    assert cfg.limiter == 0 and cfg.integrator == 2
 
 
 def test_create_rejects_bad_config_without_gpu_work():
@@ -57,7 +58,8 @@ def test_create_rejects_bad_config_without_gpu_work():
     assert b">= 4" in lib.dh_last_error(None)
     assert lib.dh_status_string(_lib.DH_ERR_POSITIVITY) == b"DH_ERR_POSITIVITY"
     for field, bad, msg in (("mg_cycle", 3, b"mg_cycle"), ("mg_smoother", 2, b"mg_smoother"),
-                            ("mg_omega", 1.5, b"mg_omega")):
+                            ("mg_omega", 1.5, b"mg_omega"), ("limiter", 2, b"limiter"),
+                            ("integrator", 4, b"integrator")):
         lib.dh_config_default(C.byref(cfg), 16, 16, 16)
         cfg.gravity = 1
         setattr(cfg, field, bad)

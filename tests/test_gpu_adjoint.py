@@ -267,3 +267,46 @@ def test_sources_mass_invariant_and_fp32():
     g32 = s32.adjoint_advance(4, 2, to_gpu(w, "f32"))
     ref = oadj.advance_vjp(torch.from_numpy(U0), dts, torch.from_numpy(w), G, _dx(shape), fields, cool)
     assert _rel(g32, ref) < 1e-3
+
+
+SCHEMES = [("rk2", "vanleer"), ("ssprk3", "mc"), ("ssprk3", "vanleer")]
+
+
+@pytest.mark.parametrize("integrator,limiter", SCHEMES)
+def test_scheme_variants_match_oracle_vjp(integrator, limiter):
+    """Hand adjoint of SSPRK3 and of the van Leer slope against reverse mode of the oracle."""
+    shape, n, k = (12, 10, 20), 4, 3
+    U0 = inputs.decaying_turbulence(shape, seed=5, sigma=0.3, mach=0.8, p_sigma=0.3)
+    lam = np.random.default_rng(1).standard_normal((5,) + shape)
+    s = solver(shape, "f64", integrator=integrator, limiter=limiter)
+    s.init_state(to_gpu(U0, "f64"))
+    g = s.adjoint_advance(n, k, to_gpu(lam, "f64"))
+    scheme = dict(integrator=integrator, limiter=limiter)
+    U = torch.from_numpy(U0)
+    dts = []
+    for _ in range(n):
+        dts.append(ohydro.cfl_dt(U, G, _dx(shape), 0.4))
+        U = ohydro.step(U, dts[-1], G, _dx(shape), integrator, limiter)
+    ref = oadj.advance_vjp(torch.from_numpy(U0), dts, torch.from_numpy(lam), G, _dx(shape),
+                           scheme=scheme)
+    assert _rel(g, ref) < 1e-10
+    assert float((g.cpu() - ref).abs().max() / ref.abs().max()) < 1e-9
+
+
+@pytest.mark.parametrize("integrator,limiter", [("ssprk3", "vanleer")])
+def test_scheme_variant_with_sources_matches_oracle_vjp(integrator, limiter):
+    shape, n, k = (16, 16, 16), 4, 2
+    from oracle import driver
+    U0 = inputs.decaying_turbulence(shape, seed=8, sigma=0.4, mach=0.6, P0=0.6, p_sigma=0.3)
+    kw = dict(forcing=True, ou_seed=11, cooling=True, t_floor=0.05, cool_frac=0.02,
+              integrator=integrator, limiter=limiter)
+    sim = driver.Simulation(driver.Config(shape=shape, gamma=G, **kw), torch.from_numpy(U0))
+    dts, fields = oadj.record(sim, n)
+    lam = np.random.default_rng(4).standard_normal((5,) + shape)
+    s = solver(shape, "f64", **kw)
+    s.init_state(to_gpu(U0, "f64"))
+    g = s.adjoint_advance(n, k, to_gpu(lam, "f64"))
+    ref = oadj.advance_vjp(torch.from_numpy(U0), dts, torch.from_numpy(lam), G, _dx(shape), fields,
+                           dict(T_floor=0.05, frac=0.02, nsub_max=1024),
+                           scheme=dict(integrator=integrator, limiter=limiter))
+    assert _rel(g, ref) < 1e-10

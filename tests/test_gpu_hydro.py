@@ -198,3 +198,42 @@ def test_cfl_dt_matches_oracle():
     s.init_state(to_gpu(U0, "f64"))
     assert s.compute_dt() == pytest.approx(ohydro.cfl_dt(torch.from_numpy(U0), G, _dx(shape), 0.4),
                                            rel=1e-14)
+
+
+SCHEMES = [("rk2", "vanleer"), ("ssprk3", "mc"), ("ssprk3", "vanleer")]
+
+
+@pytest.mark.parametrize("integrator,limiter", SCHEMES)
+@pytest.mark.parametrize("shape", [(16, 16, 16), (9, 17, 33)])
+def test_scheme_variants_fp64(shape, integrator, limiter):
+    """Van Leer limiter and SSPRK3 (App. A.1, A.3) against the oracle, three CFL steps."""
+    U0 = inputs.decaying_turbulence(shape, seed=3, sigma=0.4, mach=1.0)
+    s = solver(shape, "f64", integrator=integrator, limiter=limiter)
+    s.init_state(to_gpu(U0, "f64"))
+    U = torch.from_numpy(U0)
+    for _ in range(3):
+        dt = s.step(0.0)
+        dto = ohydro.cfl_dt(U, G, _dx(shape), 0.4)
+        assert dt == pytest.approx(dto, rel=1e-13)
+        U = ohydro.step(U, dto, G, _dx(shape), integrator, limiter)
+    assert max(rel_linf(s.get_state(), U)) <= 1e-11
+
+
+@pytest.mark.parametrize("integrator,limiter", SCHEMES)
+def test_scheme_variants_with_sources_fp64_and_fp32(integrator, limiter):
+    shape = (16, 20, 24)
+    U0 = inputs.decaying_turbulence(shape, seed=9, sigma=0.5, mach=0.7, P0=0.6)
+    kw = dict(forcing=True, ou_seed=1, cooling=True, t_floor=0.05, integrator=integrator,
+              limiter=limiter)
+    sim = odrv.Simulation(odrv.Config(shape=shape, **kw), U0)
+    s = solver(shape, "f64", **kw)
+    s32 = solver(shape, "f32", **kw)
+    s.init_state(to_gpu(U0, "f64"))
+    s32.init_state(to_gpu(U0, "f32"))
+    for _ in range(4):
+        dt = s.step(0.0)
+        s32.step(dt)
+        dto = sim.step()
+        assert dt == pytest.approx(dto, rel=1e-13)
+    assert max(rel_linf(s.get_state(), sim.U)) <= 1e-11
+    assert max(rel_linf(s32.get_state(), sim.U)) <= 1e-5
