@@ -14,9 +14,21 @@ BF16 rounding is round-to-nearest-even of the float64 value; products and sums a
 BF16 rounding).  gelu is the exact erf form.  conv is cross-correlation,
 out[o, z, y, x] = sum_{i, a, b, c} W[o, i, a, b, c] in[i, z + a - 1, y + b - 1, x + c - 1].
 
+Flux form (Sec. 7's learned flux, applied after the step): W3 has 15 output channels,
+y[5 a + c] the flux of field c through the face i + 1/2 along axis a (x, y, z), and the
+correction is dU_c(i) = -s_c sum_a (y_{a,c}(i) - y_{a,c}(i - e_a)): a periodic divergence, so
+every conserved total is unchanged.
+
+Solver-in-the-loop rollout loss (Sec. 7): from U_0, each step applies the solver step H_s and
+then the correction, U_s = C(H_s(U_{s-1})) for s = 1..S, and
+L = (1/S) sum_s mean over fields c and cells of ((U_s - T_s) / w_c)^2 against reference states
+T_s, with per-field weights w.  Reverse mode of this function is the gradient the rollout
+training follows.
+
 Pins: tests/test_oracle_corrector.py (brute-force convolution, delta-kernel translation,
 translation equivariance, gelu values and derivative, bf16 rounding of hand values, zero
-network = identity map).
+network = identity map, flux form: exact conservation and a single face moving mass between
+two cells, the transposed divergence, and the rollout gradient against finite differences).
 """
 from __future__ import annotations
 
@@ -71,12 +83,28 @@ def forward(U: torch.Tensor, p: dict, mu, sigma):
     return y, dict(x0=x0, z1=z1, h1=h1, z2=z2, h2=h2)
 
 
-def correct(U: torch.Tensor, p: dict, mu, sigma, rho_floor: float, T_floor: float, gamma: float,
-            out_scale=None):
-    """U + s * y with s = out_scale (per channel; sigma when not given), then the floors."""
+def flux_divergence(y: torch.Tensor) -> torch.Tensor:
+    """-sum_a (y_{a,c}(i) - y_{a,c}(i - e_a)) for the 15-channel flux output, per field c."""
+    out = torch.zeros((5,) + tuple(y.shape[1:]), dtype=y.dtype)
+    for a in range(3):
+        dim = 3 - a                      # x is the last tensor dimension of a (5, nz, ny, nx) field set
+        ya = y[5 * a:5 * a + 5]
+        out = out - (ya - torch.roll(ya, 1, dims=dim))
+    return out
+
+
+def correction(U: torch.Tensor, p: dict, mu, sigma, out_scale=None) -> torch.Tensor:
+    """dU before the floors: s * y (state form, 5 outputs) or s * divergence(y) (flux form,
+    15 outputs), s = out_scale per field (sigma when not given)."""
     s = torch.as_tensor(sigma if out_scale is None else out_scale, dtype=torch.float64).reshape(5, 1, 1, 1)
     y, _ = forward(U, p, mu, sigma)
-    V = U + s * y
+    return s * (flux_divergence(y) if y.shape[0] == 15 else y)
+
+
+def correct(U: torch.Tensor, p: dict, mu, sigma, rho_floor: float, T_floor: float, gamma: float,
+            out_scale=None):
+    """U + dU (either form), then the floors."""
+    V = U + correction(U, p, mu, sigma, out_scale)
     rho = torch.clamp(V[0], min=rho_floor)
     kin = 0.5 * (V[1] ** 2 + V[2] ** 2 + V[3] ** 2) / rho
     Emin = kin + rho * T_floor / (gamma - 1.0)
@@ -84,3 +112,16 @@ def correct(U: torch.Tensor, p: dict, mu, sigma, rho_floor: float, T_floor: floa
     out[0] = rho
     out[4] = torch.maximum(V[4], Emin)
     return out
+
+
+def rollout_loss(U0: torch.Tensor, steps, targets, p: dict, mu, sigma, out_scale, weights,
+                 rho_floor: float, T_floor: float, gamma: float) -> torch.Tensor:
+    """The rollout loss above: steps[s] maps a state to the next (the solver step of interval s),
+    targets[s] is T_{s+1}, weights w (5 values)."""
+    w = torch.as_tensor(weights, dtype=torch.float64).reshape(5, 1, 1, 1)
+    U = U0
+    L = torch.zeros((), dtype=torch.float64)
+    for H, T in zip(steps, targets):
+        U = correct(H(U), p, mu, sigma, rho_floor, T_floor, gamma, out_scale)
+        L = L + (((U - T) / w) ** 2).mean()
+    return L / len(steps)

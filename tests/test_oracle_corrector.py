@@ -92,3 +92,80 @@ def test_data_and_weight_gradients_by_duality():
     lhs = float((dy * oc.conv3d_periodic(x, W)).sum())
     assert lhs == pytest.approx(float((oc.conv3d_data_grad(dy, W) * x).sum()), rel=1e-12)
     assert lhs == pytest.approx(float((oc.conv3d_weight_grad(x, dy, 2) * W).sum()), rel=1e-12)
+
+
+def _params(form, seed=0, scale=0.3):
+    g = torch.Generator().manual_seed(seed)
+    k = 15 if form == "flux" else 5
+    shapes = {"W1": (32, 5, 3, 3, 3), "b1": (32,), "W2": (32, 32, 3, 3, 3), "b2": (32,),
+              "W3": (k, 32, 3, 3, 3), "b3": (k,)}
+    return {n: scale * torch.randn(s, generator=g, dtype=torch.float64) / math.sqrt(27 * (s[1] if len(s) > 1 else 1))
+            for n, s in shapes.items()}
+
+
+def test_flux_divergence_conserves_every_total():
+    g = torch.Generator().manual_seed(3)
+    y = torch.randn(15, 5, 6, 7, generator=g, dtype=torch.float64)
+    d = oc.flux_divergence(y)
+    assert d.shape == (5, 5, 6, 7)
+    for c in range(5):
+        assert abs(float(d[c].sum())) < 1e-12 * float(y.abs().sum())
+
+
+@pytest.mark.parametrize("a,c", [(0, 0), (1, 3), (2, 4)])
+def test_single_face_flux_moves_mass_between_two_cells(a, c):
+    """Flux f through the face i + 1/2 along axis a: cell i loses f, cell i + e_a gains f."""
+    y = torch.zeros(15, 4, 5, 6, dtype=torch.float64)
+    k, j, i = 3, 4, 5                     # a cell on the upper boundary of every axis
+    y[5 * a + c, k, j, i] = 2.5
+    d = oc.flux_divergence(y)
+    nxt = [k, j, i]
+    nxt[2 - a] = (nxt[2 - a] + 1) % (4, 5, 6)[2 - a]
+    expect = torch.zeros_like(d)
+    expect[c, k, j, i] = -2.5
+    expect[c, nxt[0], nxt[1], nxt[2]] = 2.5
+    assert torch.equal(d, expect)
+
+
+def test_transposed_flux_divergence_is_forward_difference():
+    """(d D / d y)^T g at (a, c, i) = g_c(i + e_a) - g_c(i): the rule the GPU output gradient
+    follows."""
+    gen = torch.Generator().manual_seed(5)
+    y = torch.randn(15, 4, 5, 6, generator=gen, dtype=torch.float64, requires_grad=True)
+    gg = torch.randn(5, 4, 5, 6, generator=gen, dtype=torch.float64)
+    (gy,) = torch.autograd.grad((oc.flux_divergence(y) * gg).sum(), y)
+    for a in range(3):
+        dim = 3 - a
+        expect = torch.roll(gg, -1, dims=dim) - gg
+        assert torch.allclose(gy[5 * a:5 * a + 5], expect, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("form", ["state", "flux"])
+def test_rollout_gradient_matches_finite_differences(form, monkeypatch):
+    """Reverse mode of the rollout loss (two solver steps, each followed by the correction)
+    against central differences along a random parameter direction, BF16 rounding off."""
+    from oracle import hydro
+    from paper_2512_13403_b300 import inputs
+    monkeypatch.setattr(oc, "bf16", lambda t: t)
+    shape = (6, 6, 6)
+    U0 = torch.from_numpy(inputs.decaying_turbulence(shape, seed=4, sigma=0.3, mach=0.5, p_sigma=0.2))
+    dx = (1 / 6, 1 / 6, 1 / 6)
+    steps = [lambda U: hydro.rk2_step(U, 2e-3, 5 / 3, dx)] * 2
+    T = [U0 + 0.01 * torch.randn(U0.shape, generator=torch.Generator().manual_seed(s), dtype=torch.float64)
+         for s in (1, 2)]
+    mu = [float(U0[c].mean()) for c in range(5)]
+    sg = [float(U0[c].std()) + 0.1 for c in range(5)]
+    out = [0.01] * 5
+    w = [0.1, 0.2, 0.2, 0.2, 0.3]
+    p = _params(form, seed=1)
+    q = {k: v.clone().requires_grad_(True) for k, v in p.items()}
+    L = oc.rollout_loss(U0, steps, T, q, mu, sg, out, w, 1e-9, 1e-6, 5 / 3)
+    L.backward()
+    gen = torch.Generator().manual_seed(7)
+    dirn = {k: torch.randn(v.shape, generator=gen, dtype=torch.float64) for k, v in p.items()}
+    ad = sum(float((q[k].grad * dirn[k]).sum()) for k in p)
+    eps = 1e-5
+    f = lambda t: float(oc.rollout_loss(U0, steps, T, {k: p[k] + t * dirn[k] for k in p}, mu, sg, out,
+                                        w, 1e-9, 1e-6, 5 / 3))
+    fd = (f(eps) - f(-eps)) / (2 * eps)
+    assert ad == pytest.approx(fd, rel=1e-6)
