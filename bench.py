@@ -509,17 +509,58 @@ def corrector_leg(args):
     params, norm, losses = closure.train(X, Y, epochs=args.corr_epochs)
     t2 = time.time()
     err, ms, sub = closure.evaluate(setup, params, norm, steps=100, seeds=args.corr_eval_seeds)
+    diverged = {k: list(v) for k, v in getattr(closure.evaluate, "diverged", {}).items()}
     t3 = time.time()
     mean = {k: sum(v) / len(v) for k, v in err.items()}
+    # flux form (Sec. 7's learned flux in divergence form), one-step trained on the same pairs
+    pf, nf, lf = closure.train(X, Y, epochs=args.corr_epochs, form="flux")
+    ef, _, _ = closure.evaluate(setup, pf, nf, steps=100, seeds=args.corr_eval_seeds,
+                                equal_time_substeps_n=sub, form="flux")
+    div_f = {k: list(v) for k, v in getattr(closure.evaluate, "diverged", {}).items()}
+    t4 = time.time()
+    # rollout (solver-in-the-loop) training from each one-step corrector
+    trajs = closure.make_trajectories(setup, count=args.rollout_trajs, length=args.rollout_unroll)
+    pr, lr_hist, it_ms = closure.train_rollout(trajs, setup, params, norm, iters=args.rollout_iters,
+                                               lr=args.rollout_lr)
+    er, _, _ = closure.evaluate(setup, pr, norm, steps=100, seeds=args.corr_eval_seeds,
+                                equal_time_substeps_n=sub)
+    div_r = {k: list(v) for k, v in getattr(closure.evaluate, "diverged", {}).items()}
+    prf, lrf_hist, itf_ms = closure.train_rollout(trajs, setup, pf, nf, iters=args.rollout_iters,
+                                                  lr=args.rollout_lr, form="flux")
+    erf, _, _ = closure.evaluate(setup, prf, nf, steps=100, seeds=args.corr_eval_seeds,
+                                 equal_time_substeps_n=sub, form="flux")
+    div_rf = {k: list(v) for k, v in getattr(closure.evaluate, "diverged", {}).items()}
+    t5 = time.time()
     return {"metric": "relative L2 vs 4x-downsampled fine run, mean over 100 coarse steps and "
                       f"held-out seeds {list(args.corr_eval_seeds)}",
             "uncorrected": mean["uncorrected"], "corrected": mean["corrected"],
             "uncorrected_equal_gpu_time": mean["uncorrected_equal_gpu_time"],
             "equal_time_substeps": sub,
-            "diverged": {k: list(v) for k, v in getattr(closure.evaluate, "diverged", {}).items()},
+            "diverged": diverged,
+            "flux_form": {"corrected": sum(ef["corrected"]) / len(ef["corrected"]),
+                          "final_step": ef["corrected"][-1], "train_loss": lf,
+                          "diverged": div_f.get("corrected"),
+                          "rollout_trained": {"corrected": sum(erf["corrected"]) / len(erf["corrected"]),
+                                              "final_step": erf["corrected"][-1],
+                                              "diverged": div_rf.get("corrected"),
+                                              "ms_per_iteration": itf_ms,
+                                              "loss_first": lrf_hist[:len(trajs)],
+                                              "loss_last": lrf_hist[-len(trajs):]},
+                          "note": "15-output network, correction = divergence of learned face "
+                                  "fluxes (conserves every total); one-step training, then "
+                                  "rollout training"},
+            "rollout_training": {"unroll": args.rollout_unroll, "trajectories": args.rollout_trajs,
+                                 "iterations": args.rollout_iters, "lr": args.rollout_lr,
+                                 "ms_per_iteration": it_ms,
+                                 "loss_first": lr_hist[:len(trajs)], "loss_last": lr_hist[-len(trajs):],
+                                 "corrected": sum(er["corrected"]) / len(er["corrected"]),
+                                 "final_step": er["corrected"][-1], "diverged": div_r.get("corrected"),
+                                 "note": "state form, from the one-step corrector: rollout loss "
+                                         "through the solver's hand adjoint and the network VJP"},
             "final_step": {k: v[-1] for k, v in err.items()},
             "gpu_ms_per_coarse_step": ms, "pairs": int(X.shape[0]), "epochs": args.corr_epochs,
-            "train_loss": losses, "seconds": {"pairs": t1 - t0, "train": t2 - t1, "eval": t3 - t2},
+            "train_loss": losses, "seconds": {"pairs": t1 - t0, "train": t2 - t1, "eval": t3 - t2,
+                                               "flux_form": t4 - t3, "rollout": t5 - t4},
             "reading": "equal GPU time as matched physical time (primary) and, second, the "
                        "uncorrected run given the corrected run's GPU time as "
                        f"{sub} substeps per coarse step (measured cost ratio)"}
@@ -543,6 +584,10 @@ def main():
     ap.add_argument("--no-corrector", action="store_true")
     ap.add_argument("--no-selfgrav", action="store_true", help="skip the 1024^3 self-gravitating leg")
     ap.add_argument("--sg-grid", type=int, default=1024)
+    ap.add_argument("--rollout-trajs", type=int, default=4)
+    ap.add_argument("--rollout-unroll", type=int, default=8)
+    ap.add_argument("--rollout-iters", type=int, default=64)
+    ap.add_argument("--rollout-lr", type=float, default=3e-4)
     ap.add_argument("--no-scheme-variants", action="store_true",
                     help="skip the forward step per limiter and integrator")
     ap.add_argument("--no-poisson-variants", action="store_true",

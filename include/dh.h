@@ -186,6 +186,11 @@ dh_status dh_solve_poisson(dh_ctx* ctx, const void* rho, int on_device);
    an adjoint Poisson solve misses mg_tol. */
 dh_status dh_adjoint_advance(dh_ctx* ctx, int n_steps, int ckpt_every, const void* dLdU_final,
                              void* dLdU0, int on_device);
+/* dh_adjoint_advance with every step of the forward sweep taken at the imposed dt > 0 (as
+   dh_step(dt)); dt = 0 is the CFL step of dh_adjoint_advance.  The form a rollout whose steps
+   must land on fixed times (solver-in-the-loop training against a reference trajectory) needs. */
+dh_status dh_adjoint_advance_dt(dh_ctx* ctx, int n_steps, int ckpt_every, double dt,
+                                const void* dLdU_final, void* dLdU0, int on_device);
 
 /* ---- Corrector building blocks (residual 3D CNN, BF16 tensor cores, FP32 accumulation) ----
    A 3x3x3 periodic convolution over an nx*ny*nz grid as an implicit GEMM on tcgen05:
@@ -254,6 +259,15 @@ dh_status dh_conv3d_wgrad_bf16(const void* act, int cin_pad, int cin, const void
 typedef struct dh_cnn dh_cnn;
 long long dh_cnn_param_count(void);
 dh_status dh_cnn_create(int nx, int ny, int nz, void* cuda_stream, dh_cnn** out);
+/* The same network in either correction form (Sec. 7: a learned correction of the state, or a
+   learned flux added in divergence form).  form 0 = state form above (5 outputs).  form 1 =
+   flux form: W3[15][32][27], b3[15] (dh_cnn_param_count_form(1) = 45007 values), y[5 a + c] is
+   the flux of field c through the face i + 1/2 along axis a (x, y, z), and the correction is
+   dU_c(i) = -s_c sum_a (y_{a,c}(i) - y_{a,c}(i - e_a)), periodic: it changes no conserved total.
+   Every call below takes either form; dh_cnn_backward then compares the divergence with the
+   residual target.  DH_ERR_ARG for another form. */
+long long dh_cnn_param_count_form(int form);
+dh_status dh_cnn_create_form(int nx, int ny, int nz, int form, void* cuda_stream, dh_cnn** out);
 void dh_cnn_destroy(dh_cnn* cnn);
 /* Copies the parameters and packs the tensor-core operands (synchronises). */
 dh_status dh_cnn_set_params(dh_cnn* cnn, const float* params, const float* norm15);
@@ -266,8 +280,16 @@ dh_status dh_cnn_forward(dh_cnn* cnn, const float* U, float* y_out);
    states (device).  Synchronises. */
 dh_status dh_cnn_backward(dh_cnn* cnn, const float* U_in, const float* U_target, float* grads,
                           double* loss);
-/* U <- U + s * network(U) in place (float32 state, device), then rho >= rho_floor and
-   E >= |m|^2/(2 rho) + rho T_floor/(gamma - 1).  An inference pass: it keeps no activations
+/* Vector-Jacobian product of the correction dU(U) (before the floors) for the last
+   dh_cnn_forward (on U): given dL_dcorr = dL/d(dU) (device, 5 planes float32), writes
+   dL/d(params) into grads (device, param count floats) and, if dL_dU is not NULL,
+   dL/dU = (d dU / dU)^T dL_dcorr into dL_dU (device, 5 planes float32).  The identity part of
+   U + dU is the caller's.  The bf16 roundings of the forward are taken as the identity.  The
+   building block of solver-in-the-loop training (Sec. 7), where the loss of a rollout is
+   carried back through the corrector and the solver's adjoint.  Synchronises. */
+dh_status dh_cnn_vjp(dh_cnn* cnn, const float* dL_dcorr, float* grads, float* dL_dU);
+/* U <- U + dU(U) in place (float32 state, device; dU = s * network(U) in the state form),
+   then rho >= rho_floor and E >= |m|^2/(2 rho) + rho T_floor/(gamma - 1).  An inference pass: it keeps no activations
    for dh_cnn_backward (call dh_cnn_forward again before the next backward).  Synchronises.
    DH_ERR_NONFINITE if a corrected value is not finite (U then holds the corrected values). */
 dh_status dh_cnn_correct_state(dh_cnn* cnn, float* U, double rho_floor, double T_floor,
@@ -282,6 +304,9 @@ dh_status dh_adam_step(float* params, const float* grads, float* m, float* v, lo
    DH_ERR_STATE without a corrector; DH_ERR_NONFINITE if the corrected state is not finite, in
    which case the context keeps the uncorrected state. */
 dh_status dh_set_corrector(dh_ctx* ctx, const float* params, const float* norm15);
+/* dh_set_corrector for either form (see dh_cnn_create_form); replaces a corrector of the
+   other form. */
+dh_status dh_set_corrector_form(dh_ctx* ctx, int form, const float* params, const float* norm15);
 dh_status dh_correct(dh_ctx* ctx);
 
 /* Conserved totals (as dh_conserved_totals) for callers that cannot allocate device memory,

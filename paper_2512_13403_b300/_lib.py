@@ -54,6 +54,7 @@ _SIGNATURES = {
     "dh_solve_poisson": (C.c_int, [_P, _P, C.c_int]),
     "dh_reset_potential": (C.c_int, [_P]),
     "dh_adjoint_advance": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
+    "dh_adjoint_advance_dt": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, _P, _P, C.c_int]),
     "dh_conserved_totals_static": (C.c_int, [_P, C.c_int, C.c_longlong, _P, _P]),
     "dh_save": (C.c_int, [_P, C.c_char_p]),
     "dh_load": (C.c_int, [_P, C.c_char_p]),
@@ -67,6 +68,9 @@ _SIGNATURES = {
                                        C.c_int, C.c_int, _P, C.c_int, _P, _P, _P]),
     "dh_cnn_param_count": (C.c_longlong, []),
     "dh_cnn_create": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, C.POINTER(_P)]),
+    "dh_cnn_param_count_form": (C.c_longlong, [C.c_int]),
+    "dh_cnn_create_form": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _P, C.POINTER(_P)]),
+    "dh_cnn_vjp": (C.c_int, [_P, _P, _P, _P]),
     "dh_cnn_destroy": (None, [_P]),
     "dh_cnn_set_params": (C.c_int, [_P, _P, C.POINTER(C.c_float)]),
     "dh_cnn_forward": (C.c_int, [_P, _P, _P]),
@@ -75,6 +79,7 @@ _SIGNATURES = {
     "dh_adam_step": (C.c_int, [_P, _P, _P, _P, C.c_longlong, C.c_double, C.c_double, C.c_double,
                                C.c_double, C.c_int, _P]),
     "dh_set_corrector": (C.c_int, [_P, _P, C.POINTER(C.c_float)]),
+    "dh_set_corrector_form": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_float)]),
     "dh_correct": (C.c_int, [_P]),
     "dh_profile_enable": (C.c_int, [_P, C.c_int]),
     "dh_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),

@@ -23,7 +23,7 @@ import numpy as np
 import torch
 
 from . import _lib, inputs
-from .corrector import Adam, Network, NPARAM, init_params
+from .corrector import FORMS, Adam, Network, NPARAM, init_params, nparam
 from .solver import Config, Solver
 
 
@@ -123,15 +123,15 @@ def normalisation(X: torch.Tensor, Y: torch.Tensor):
 
 
 def train(X: torch.Tensor, Y: torch.Tensor, epochs: int = 4, lr0: float = 1e-3, lr1: float = 1e-4,
-          seed: int = 0, log=None):
+          seed: int = 0, log=None, form: str = "state"):
     """Adam on the pair set, one pair per step, learning rate decayed geometrically from lr0 to
     lr1.  Returns (params, (mu, sigma, out_scale), losses)."""
     shape = tuple(X.shape[2:])
-    net = Network(shape)
+    net = Network(shape, form=form)
     mu, sigma, out = normalisation(X, Y)
-    params = init_params(seed, out_scale=0.01).cuda()
+    params = init_params(seed, out_scale=0.01, form=form).cuda()
     opt = Adam(params, lr=lr0)
-    grads = torch.zeros(NPARAM, dtype=torch.float32, device="cuda")
+    grads = torch.zeros(nparam(form), dtype=torch.float32, device="cuda")
     g = np.random.default_rng(seed)
     P = X.shape[0]
     total = epochs * P
@@ -160,12 +160,13 @@ def _rel_l2(U: torch.Tensor, R: torch.Tensor) -> float:
                      for c in range(5)) / 5.0)
 
 
-def _set_corrector(solver: Solver, params, norm):
+def _set_corrector(solver: Solver, params, norm, form: str = "state"):
     import ctypes as C
     mu, sigma, out = norm
     normbuf = (C.c_float * 15)(*[float(v) for v in list(mu) + list(sigma) + list(out)])
     p = params.detach().float().cuda().contiguous()
-    _lib.check(_lib.load().dh_set_corrector(solver.ctx, C.c_void_p(p.data_ptr()), normbuf), solver.ctx)
+    _lib.check(_lib.load().dh_set_corrector_form(solver.ctx, FORMS[form], C.c_void_p(p.data_ptr()),
+                                                 normbuf), solver.ctx)
 
 
 def _timed(fn) -> float:
@@ -201,7 +202,7 @@ def equal_time_substeps(setup: ClosureSetup, params, norm, U0: torch.Tensor, pro
 
 
 def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
-             equal_time_substeps_n="auto"):
+             equal_time_substeps_n="auto", form: str = "state"):
     """Corrected and uncorrected coarse runs against the downsampled fine run, same forcing.
 
     For every held-out seed, a fine run is spun up and downsampled; coarse runs start from that
@@ -231,7 +232,7 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
         for name in err:
             runs[name] = Solver(_cfg(nc, setup, seed))
             runs[name].init_state(U0)
-        _set_corrector(runs["corrected"], params, norm)
+        _set_corrector(runs["corrected"], params, norm, form)
         live = dict(runs)
         for k in range(steps):
             dt_c = runs["uncorrected"].compute_dt()
@@ -265,3 +266,121 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
     nrun = steps * len(seeds)
     evaluate.diverged = diverged
     return ({k: v.tolist() for k, v in err.items()}, {k: v / nrun for k, v in gpu_ms.items()}, sub)
+
+
+# ---- solver-in-the-loop training (Sec. 7) ------------------------------------------------------
+@dataclasses.dataclass
+class Trajectory:
+    """A reference rollout on the coarse grid: the start state, the time step, OU table and
+    downsampled fine state after each coarse interval."""
+    U0: torch.Tensor
+    dts: List[float]
+    modes: list
+    targets: List[torch.Tensor]
+
+
+def make_trajectories(setup: ClosureSetup, count: int, length: int, seed0: int = 300, log=None):
+    """`count` reference rollouts of `length` coarse intervals, each from a spun-up fine run
+    (intervals, time steps and OU tables as in make_pairs)."""
+    n, nc = setup.fine, setup.coarse
+    coarse = Solver(_cfg(nc, setup, seed0))
+    out = []
+    for r in range(count):
+        fine = Solver(_cfg(n, setup, seed0 + r))
+        fine.init_state(torch.from_numpy(inputs.cooling_box((n, n, n))).float().cuda().contiguous())
+        fine.advance(setup.spinup_steps)
+        U0 = downsample(fine.get_state(), setup.factor)
+        dts, modes, targets = [], [], []
+        for _ in range(length):
+            coarse.init_state(downsample(fine.get_state(), setup.factor))
+            dt_c = coarse.compute_dt()
+            modes.append(fine_interval(fine, dt_c, setup.forcing))
+            dts.append(dt_c)
+            targets.append(downsample(fine.get_state(), setup.factor))
+        out.append(Trajectory(U0, dts, modes, targets))
+        fine.close()
+        if log:
+            log(f"trajectories: {r + 1}/{count}")
+    coarse.close()
+    return out
+
+
+class RolloutTrainer:
+    """Loss and gradient of the rollout loss through the solver's hand adjoint and the network's
+    VJP, for a coarse solver configuration and a network form."""
+
+    def __init__(self, shape, cfg: Config, form: str = "state", rho_floor_frac: float = 1e-6):
+        self.shape = tuple(shape)
+        self.cfg = cfg
+        self.form = form
+        self.net = Network(self.shape, form=form)
+        self.solver = Solver(cfg)
+        self.grads = torch.zeros(nparam(form), dtype=torch.float32, device="cuda")
+        self.rho_floor_frac = rho_floor_frac
+
+    def close(self):
+        self.net.close()
+        self.solver.close()
+
+    def _start(self, U, modes):
+        self.solver.init_state(U)
+        if modes is not None:
+            self.solver.set_forcing_modes(modes, hold=True)
+
+    def loss_and_grad(self, traj: Trajectory, params, norm, weights):
+        """L = (1/S) sum_s mean(((U_s - T_s) / w)^2), U_s = C(H_s(U_{s-1})); returns (L, dL/dparams).
+        The floors of the correction are taken as inactive in the gradient."""
+        mu, sigma, out = norm
+        self.net.set_params(params, mu, sigma, out)
+        S = len(traj.dts)
+        n5 = 5 * traj.U0[0].numel()
+        w2 = torch.tensor([float(v) ** 2 for v in weights], dtype=torch.float32, device="cuda").reshape(5, 1, 1, 1)
+        rho_floor = self.rho_floor_frac * float(traj.U0[0].mean())
+        Us, Vs = [traj.U0], []
+        loss = 0.0
+        for k in range(S):
+            self._start(Us[-1], traj.modes[k])
+            self.solver.step(traj.dts[k])
+            V = self.solver.get_state()
+            Vs.append(V)
+            Un = V.clone()
+            self.net.correct_state(Un, rho_floor, self.cfg.t_floor, self.cfg.gamma)
+            Us.append(Un)
+            loss += float((((Un - traj.targets[k]) ** 2) / w2).sum()) / (n5 * S)
+        total = torch.zeros_like(self.grads)
+        lam = 2.0 * (Us[S] - traj.targets[S - 1]) / (w2 * n5 * S)
+        for k in reversed(range(S)):
+            self.net.forward(Vs[k])
+            gU = self.net.vjp(lam.contiguous(), self.grads)
+            total += self.grads
+            lam_V = (lam + gU).contiguous()
+            self._start(Us[k], traj.modes[k])
+            lam = self.solver.adjoint_advance(1, 1, lam_V, dt=traj.dts[k])
+            if k > 0:
+                lam = lam + 2.0 * (Us[k] - traj.targets[k - 1]) / (w2 * n5 * S)
+        return loss, total
+
+
+def train_rollout(trajs: List[Trajectory], setup: ClosureSetup, params, norm, iters: int,
+                  lr: float = 1e-4, form: str = "state", weights=None, log=None):
+    """Adam on the rollout loss, one trajectory per iteration (cycling).  Returns
+    (params, losses, ms per iteration)."""
+    nc = setup.coarse
+    if weights is None:
+        weights = [max(float(torch.stack([t[c] for tr in trajs for t in tr.targets]).std()), 1e-12)
+                   for c in range(5)]
+    tr = RolloutTrainer((nc, nc, nc), _cfg(nc, setup, 0), form)
+    params = params.clone()
+    opt = Adam(params, lr=lr)
+    losses = []
+    t0 = time.perf_counter()
+    for it in range(iters):
+        L, g = tr.loss_and_grad(trajs[it % len(trajs)], params, norm, weights)
+        opt.step(g)
+        losses.append(L)
+        if log and (it + 1) % max(1, iters // 10) == 0:
+            log(f"rollout training: iteration {it + 1}/{iters} loss {L:.4e}")
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0) / max(iters, 1)
+    tr.close()
+    return params, losses, ms

@@ -14,17 +14,30 @@ import torch
 from . import _lib
 from ._lib import check
 
-NPARAM = 36357
-LAYOUT = [("W1", (32, 5, 3, 3, 3)), ("b1", (32,)), ("W2", (32, 32, 3, 3, 3)), ("b2", (32,)),
-          ("W3", (5, 32, 3, 3, 3)), ("b3", (5,))]
+FORMS = {"state": 0, "flux": 1}
+NOUT = {"state": 5, "flux": 15}
 
 
-def init_params(seed: int = 0, out_scale: float = 0.1) -> torch.Tensor:
+def layout(form: str = "state"):
+    k = NOUT[form]
+    return [("W1", (32, 5, 3, 3, 3)), ("b1", (32,)), ("W2", (32, 32, 3, 3, 3)), ("b2", (32,)),
+            ("W3", (k, 32, 3, 3, 3)), ("b3", (k,))]
+
+
+def nparam(form: str = "state") -> int:
+    return int(sum(np.prod(s) for _, s in layout(form)))
+
+
+NPARAM = nparam("state")
+LAYOUT = layout("state")
+
+
+def init_params(seed: int = 0, out_scale: float = 0.1, form: str = "state") -> torch.Tensor:
     """Seeded fan-in uniform initialisation (float32, CPU); the output layer is scaled down so the
     untrained correction starts small."""
     g = np.random.default_rng(seed)
     parts = []
-    for name, shape in LAYOUT:
+    for name, shape in layout(form):
         if name.startswith("W"):
             fan_in = shape[1] * 27
             bound = 1.0 / math.sqrt(fan_in)
@@ -35,13 +48,14 @@ def init_params(seed: int = 0, out_scale: float = 0.1) -> torch.Tensor:
         else:
             parts.append(np.zeros(shape))
     flat = np.concatenate(parts).astype(np.float32)
-    assert flat.size == NPARAM
+    assert flat.size == nparam(form)
     return torch.from_numpy(flat)
 
 
 def unflatten(p: torch.Tensor) -> dict:
+    form = "flux" if p.numel() == nparam("flux") else "state"
     out, o = {}, 0
-    for name, shape in LAYOUT:
+    for name, shape in layout(form):
         n = int(np.prod(shape))
         out[name] = p[o:o + n].reshape(shape)
         o += n
@@ -51,14 +65,17 @@ def unflatten(p: torch.Tensor) -> dict:
 class Network:
     """One dh_cnn for a grid of shape (nz, ny, nx) on the current CUDA stream."""
 
-    def __init__(self, shape, stream=None):
+    def __init__(self, shape, stream=None, form: str = "state"):
         self.lib = _lib.load()
-        assert self.lib.dh_cnn_param_count() == NPARAM
+        self.form = form
+        self.nparam = nparam(form)
+        assert self.lib.dh_cnn_param_count_form(FORMS[form]) == self.nparam
         self.shape = tuple(shape)
         nz, ny, nx = self.shape
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
-        check(self.lib.dh_cnn_create(nx, ny, nz, C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        check(self.lib.dh_cnn_create_form(nx, ny, nz, FORMS[form], C.c_void_p(self.stream.cuda_stream),
+                                          C.byref(h)))
         self.h = h
 
     def close(self):
@@ -81,10 +98,20 @@ class Network:
         check(self.lib.dh_cnn_set_params(self.h, C.c_void_p(p.data_ptr()), norm))
 
     def forward(self, U: torch.Tensor) -> torch.Tensor:
+        """The network outputs y (5 or 15 planes); keeps the activations for backward / vjp."""
         assert U.dtype == torch.float32 and U.is_cuda and U.is_contiguous()
-        y = torch.empty_like(U)
+        y = torch.empty((NOUT[self.form],) + self.shape, dtype=torch.float32, device=U.device)
         check(self.lib.dh_cnn_forward(self.h, C.c_void_p(U.data_ptr()), C.c_void_p(y.data_ptr())))
         return y
+
+    def vjp(self, dL_dcorr: torch.Tensor, grads: torch.Tensor, want_input: bool = True):
+        """For the last forward: parameter gradients into grads and (optionally) returns dL/dU
+        of the correction dU(U) for the upstream gradient dL_dcorr (5 planes, device)."""
+        assert dL_dcorr.dtype == torch.float32 and dL_dcorr.is_cuda and dL_dcorr.is_contiguous()
+        gU = torch.empty_like(dL_dcorr) if want_input else None
+        check(self.lib.dh_cnn_vjp(self.h, C.c_void_p(dL_dcorr.data_ptr()), C.c_void_p(grads.data_ptr()),
+                                  C.c_void_p(gU.data_ptr() if gU is not None else 0)))
+        return gU
 
     def backward(self, U_in: torch.Tensor, U_target: torch.Tensor, grads: torch.Tensor) -> float:
         """Gradient of mean((y - (U_target - U_in)/s)^2) for the last forward (on U_in)."""

@@ -680,9 +680,10 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
   return cudaSuccess;
 }
 
-extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLdU_final,
-                                        void* dLdU0, int on_device) {
+extern "C" dh_status dh_adjoint_advance_dt(dh_ctx* c, int n, int k, double dt,
+                                           const void* dLdU_final, void* dLdU0, int on_device) {
   if (!c || !dLdU_final || !dLdU0) return DH_ERR_ARG;
+  if (!(dt >= 0.0)) { c->err = "dt must be >= 0 (0: the CFL time step)"; return DH_ERR_ARG; }
   if (!c->initialized) { c->err = "state not initialised"; return DH_ERR_STATE; }
   if (n < 0 || k < 1) { c->err = "need n_steps >= 0 and ckpt_every >= 1"; return DH_ERR_ARG; }
   const cudaMemcpyKind h2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -704,7 +705,7 @@ extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLd
         e = cudaMemcpyAsync(a->ckPhi[m / k], mg_phi(c), (size_t)c->n3 * sizeof(double),
                             cudaMemcpyDeviceToDevice, c->stream);
     }
-    if (e == cudaSuccess) e = c->prec == DH_F64 ? dh_enqueue_step_f64(c) : dh_enqueue_step_f32(c);
+    if (e == cudaSuccess) e = c->prec == DH_F64 ? dh_enqueue_step_f64(c, dt) : dh_enqueue_step_f32(c, dt);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(a->dts + m, &c->rec->dt, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess && c->cfg.forcing) {
@@ -746,4 +747,9 @@ extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLd
     }
   }
   return DH_OK;
+}
+
+extern "C" dh_status dh_adjoint_advance(dh_ctx* c, int n, int k, const void* dLdU_final,
+                                        void* dLdU0, int on_device) {
+  return dh_adjoint_advance_dt(c, n, k, 0.0, dLdU_final, dLdU0, on_device);
 }

@@ -4,9 +4,14 @@
 //
 // Network: x0 = bf16((U - mu)/sigma) (5 channels, padded to 8); z1 = conv(x0, W1) + b1,
 // h1 = bf16(gelu(z1)); z2 = conv(h1, W2) + b2, h2 = bf16(gelu(z2)); y = conv(h2, W3) + b3.
-// Correction: U <- U + s * y (s the per-channel output scale), rho >= rho_floor, E raised so that the thermal energy is at
-// least rho T_floor / (gamma - 1).  Parameters, flat fp32: W1[32][5][27], b1[32],
-// W2[32][32][27], b2[32], W3[5][32][27], b3[5] (36357 values).
+// Two forms of the correction dU, then rho >= rho_floor and E raised so that the thermal energy
+// is at least rho T_floor / (gamma - 1):
+//   state form (5 outputs): dU_c = s_c y_c (s the per-channel output scale);
+//   flux form (15 outputs, y[5 a + c] the flux of field c through face i + 1/2 along axis a):
+//   dU_c(i) = -s_c sum_a (y_{a,c}(i) - y_{a,c}(i - e_a)), a divergence, so that every conserved
+//   total is unchanged (Sec. 7's flux corrector, applied after the step).
+// Parameters, flat fp32: W1[32][5][27], b1[32], W2[32][32][27], b2[32], W3[nout][32][27],
+// b3[nout] (36357 values for 5 outputs, 45007 for 15).
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -16,10 +21,12 @@
 #include "dh_internal.h"
 
 namespace {
-constexpr int NPARAM = 32 * 5 * 27 + 32 + 32 * 32 * 27 + 32 + 5 * 32 * 27 + 5;
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + 32 * 5 * 27, OFF_W2 = OFF_B1 + 32,
-              OFF_B2 = OFF_W2 + 32 * 32 * 27, OFF_W3 = OFF_B2 + 32, OFF_B3 = OFF_W3 + 5 * 32 * 27;
-static_assert(OFF_B3 + 5 == NPARAM, "parameter layout");
+              OFF_B2 = OFF_W2 + 32 * 32 * 27, OFF_W3 = OFF_B2 + 32;
+constexpr int off_b3(int nout) { return OFF_W3 + nout * 32 * 27; }
+constexpr int nparam(int nout) { return off_b3(nout) + nout; }
+constexpr int NPARAM = nparam(5);
+static_assert(NPARAM == 36357 && nparam(15) == 45007, "parameter layout");
 constexpr int RBLOCKS = 256;
 }  // namespace
 
@@ -33,15 +40,19 @@ extern "C" dh_status dh_conv3d_wgrad_bf16(const void*, int, int, const void*, in
 struct dh_cnn {
   int nx = 0, ny = 0, nz = 0;
   long long ncell = 0;
+  int form = 0;                             // 0 state, 1 flux
+  int nout = 5;                             // network outputs: 5 or 15
+  int dyc = 8;                              // channels of the padded output gradient: 8 or 32
   cudaStream_t stream = nullptr;
   float* params = nullptr;                  // device copy of the parameters
   float norm[15] = {0};                     // mu[5], sigma[5], output scale[5]
   float* norm_dev = nullptr;
   __nv_bfloat16 *pk_w1 = nullptr, *pk_w2 = nullptr, *pk_w3 = nullptr;   // forward operands
-  __nv_bfloat16 *pk_w2t = nullptr, *pk_w3t = nullptr;                  // data-gradient operands
+  __nv_bfloat16 *pk_w2t = nullptr, *pk_w3t = nullptr, *pk_w1t = nullptr;   // data-gradient operands
   // activations and their gradients, padded layout (conv_layout.cuh): 1 or 4 channel groups
   __nv_bfloat16 *x0 = nullptr, *h1 = nullptr, *h2 = nullptr;
-  float *z1 = nullptr, *z2 = nullptr, *y = nullptr;                     // [cell][32], [5][cell]
+  float *z1 = nullptr, *z2 = nullptr, *y = nullptr;                     // [cell][32], [nout][cell]
+  float* g5 = nullptr;                      // [5][cell]: gradient of the correction / input
   __nv_bfloat16 *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr;
   float* partial = nullptr;                 // weight-gradient partials
   int nctas = 148;
@@ -114,6 +125,101 @@ __global__ void mse_grad_kernel(const float* __restrict__ y, const float* __rest
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// Periodic neighbour cell index along axis a (0 x, 1 y, 2 z), offset d = +-1.
+__device__ __forceinline__ long long nb_cell(const ConvGeom& g, int x, int y, int z, int a, int d) {
+  if (a == 0) x = x + d < 0 ? g.nx - 1 : (x + d >= g.nx ? 0 : x + d);
+  else if (a == 1) y = y + d < 0 ? g.ny - 1 : (y + d >= g.ny ? 0 : y + d);
+  else z = z + d < 0 ? g.nz - 1 : (z + d >= g.nz ? 0 : z + d);
+  return ((long long)z * g.ny + y) * g.nx + x;
+}
+
+// Flux form: p_c(i) = -sum_a (y_{a,c}(i) - y_{a,c}(i - e_a)), the divergence of the 15 outputs.
+__device__ __forceinline__ float flux_div(const float* __restrict__ y, long long n, const ConvGeom& g,
+                                          long long q, int x, int yy, int z, int c) {
+  float p = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float* ya = y + (long long)(5 * a + c) * n;
+    p -= ya[q] - ya[nb_cell(g, x, yy, z, a, -1)];
+  }
+  return p;
+}
+
+// Flux form, one-step loss: t = (U_target - U_in) / s, loss = mean over 5 channels and cells of
+// (p - t)^2 with p the divergence above; g = d loss / d p (float [5][cell]) and loss partials.
+__global__ void flux_mse_kernel(const float* __restrict__ y, const float* __restrict__ Uin,
+                                const float* __restrict__ Utgt, const float* __restrict__ norm,
+                                ConvGeom geo, float* __restrict__ g, double* __restrict__ partial) {
+  const long long n = (long long)geo.nx * geo.ny * geo.nz;
+  __shared__ double red[256];
+  double s = 0.0;
+  const double scale = 2.0 / (5.0 * (double)n);
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long b0 = blockIdx.x * per, b1 = b0 + per < n ? b0 + per : n;
+  for (long long q = b0 + threadIdx.x; q < b1; q += blockDim.x) {
+    int x, yy, z;
+    cell_xyz(q, geo, x, yy, z);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const float t = (Utgt[c * n + q] - Uin[c * n + q]) / norm[10 + c];
+      const float d = flux_div(y, n, geo, q, x, yy, z, c) - t;
+      s += (double)d * (double)d;
+      g[c * n + q] = (float)scale * d;
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// Output gradient dy (bf16, padded layout) from g = d L / d p (state form: p = y; flux form:
+// p = the divergence of y), each channel c of g scaled by sc[c] (nullable: 1).
+//   state form: dy_c = sc_c g_c (8 channels);
+//   flux form:  dy_{a,c}(i) = sc_c (g_c(i + e_a) - g_c(i)), the transposed divergence (32 channels).
+__global__ void output_grad_kernel(const float* __restrict__ g, const float* __restrict__ sc,
+                                   int form, ConvGeom geo, __nv_bfloat16* __restrict__ dy) {
+  const long long n = (long long)geo.nx * geo.ny * geo.nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    int x, yy, z;
+    cell_xyz(q, geo, x, yy, z);
+    float f[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) f[k] = 0.f;
+    if (form == 0) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) f[c] = (sc ? sc[c] : 1.f) * g[c * n + q];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const float gc = g[c * n + q];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          f[5 * a + c] = (sc ? sc[c] : 1.f) * (g[c * n + nb_cell(geo, x, yy, z, a, +1)] - gc);
+      }
+    }
+    const int groups = form == 0 ? 1 : 4;
+    for (int gr = 0; gr < groups; ++gr) {
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn(f[8 * gr + e]);
+      store_with_images(reinterpret_cast<uint4*>(dy) + (long long)gr * geo.rows, geo, x, yy, z,
+                        *reinterpret_cast<const uint4*>(v));
+    }
+  }
+}
+
+// dL/dU = dL/dx0 / sigma per channel (the input normalisation transposed), in place.
+__global__ void input_grad_kernel(float* __restrict__ g, const float* __restrict__ norm, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 5 * n;
+       q += (long long)gridDim.x * blockDim.x)
+    g[q] = g[q] / norm[5 + (int)(q / n)];
+}
+
 // *out = scale * sum of partial[0..nb) in a fixed order: lane l sums entries l, l+32, ...,
 // then a fixed shuffle tree (one warp).
 __global__ void sum_blocks_kernel(const double* partial, int nb, double scale, double* out) {
@@ -181,14 +287,21 @@ constexpr unsigned CNN_ERR_WAIT = 1u, CNN_ERR_NONFINITE = 2u;
 __global__ void correct_kernel(const float* Uin, float* Uout, const float* __restrict__ y,
                                long long n, const float* __restrict__ norm, float rho_floor_c,
                                const double* __restrict__ totals, double floor_per_mass,
-                               float T_floor, float gm1, unsigned* err) {
+                               float T_floor, float gm1, unsigned* err, int form, ConvGeom geo) {
   const float rho_floor = totals ? (float)(floor_per_mass * totals[0]) : rho_floor_c;
   bool finite = true;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     float v[5];
+    if (form == 0) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) v[c] = Uin[c * n + q] + norm[10 + c] * y[c * n + q];
+      for (int c = 0; c < 5; ++c) v[c] = Uin[c * n + q] + norm[10 + c] * y[c * n + q];
+    } else {
+      int x, yy, z;
+      cell_xyz(q, geo, x, yy, z);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) v[c] = Uin[c * n + q] + norm[10 + c] * flux_div(y, n, geo, q, x, yy, z, c);
+    }
     const float rho = fmaxf(v[0], rho_floor);
     const float kin = 0.5f * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / rho;
     const float Emin = kin + rho * T_floor / gm1;
@@ -245,15 +358,20 @@ extern "C" void dh_cnn_destroy(dh_cnn* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   void* ps[] = {c->params, c->norm_dev, c->pk_w1, c->pk_w2, c->pk_w3, c->pk_w2t, c->pk_w3t,
-                c->x0, c->h1, c->h2, c->z1, c->z2, c->y, c->dy, c->dz2, c->dz1, c->partial,
-                c->red, c->bpart, c->err};
+                c->pk_w1t, c->x0, c->h1, c->h2, c->z1, c->z2, c->y, c->g5, c->dy, c->dz2, c->dz1,
+                c->partial, c->red, c->bpart, c->err};
   for (void* p : ps) cudaFree(p);
   delete c;
 }
 
-extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn** out) {
+extern "C" dh_status dh_cnn_create_form(int nx, int ny, int nz, int form, void* stream,
+                                        dh_cnn** out) {
   if (!out) return DH_ERR_ARG;
   *out = nullptr;
+  if (form != 0 && form != 1) {
+    dh_set_global_error("dh_cnn_create_form: form must be 0 (state) or 1 (flux)");
+    return DH_ERR_ARG;
+  }
   const long long n = (long long)nx * ny * nz;
   if (nx < 3 || ny < 3 || nz < 3 || n >= (1LL << 31)) {
     dh_set_global_error("dh_cnn_create: every dimension must be >= 3 and the grid below 2^31 cells");
@@ -262,26 +380,31 @@ extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn*
   const long long prow = conv_geom(nx, ny, nz).rows;   // 16-byte rows per channel group
   dh_cnn* c = new dh_cnn();
   c->nx = nx; c->ny = ny; c->nz = nz; c->ncell = n;
+  c->form = form;
+  c->nout = form == 0 ? 5 : 15;
+  c->dyc = form == 0 ? 8 : 32;
   c->stream = (cudaStream_t)stream;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&c->nctas, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t b) { if (e == cudaSuccess) e = cudaMalloc(p, b); };
-  A((void**)&c->params, NPARAM * sizeof(float));
+  A((void**)&c->params, nparam(c->nout) * sizeof(float));
   A((void**)&c->norm_dev, 15 * sizeof(float));
   A((void**)&c->pk_w1, 32 * 224 * 2);
   A((void**)&c->pk_w2, 32 * 864 * 2);
   A((void**)&c->pk_w3, 16 * 864 * 2);
   A((void**)&c->pk_w2t, 32 * 864 * 2);
-  A((void**)&c->pk_w3t, 32 * 224 * 2);
+  A((void**)&c->pk_w3t, 32 * (c->nout > 8 ? 864 : 224) * 2);
+  A((void**)&c->pk_w1t, 16 * 864 * 2);
   A((void**)&c->x0, prow * 16);
   A((void**)&c->h1, prow * 4 * 16);
   A((void**)&c->h2, prow * 4 * 16);
   A((void**)&c->z1, n * 32 * 4);
   A((void**)&c->z2, n * 32 * 4);
-  A((void**)&c->y, n * 5 * 4);
-  A((void**)&c->dy, prow * 16);
+  A((void**)&c->y, n * c->nout * 4);
+  A((void**)&c->g5, n * 5 * 4);
+  A((void**)&c->dy, prow * (c->dyc / 8) * 16);
   A((void**)&c->dz2, prow * 4 * 16);
   A((void**)&c->dz1, prow * 4 * 16);
   A((void**)&c->partial, (size_t)c->nctas * 7 * 128 * 32 * sizeof(float));
@@ -291,8 +414,8 @@ extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn*
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(unsigned));
   // the guard rows of the padded buffers must read as zero; every other row is rewritten by
   // the producer of the buffer (cell rows and their halo images)
-  for (__nv_bfloat16* b : {c->x0, c->dy})
-    if (e == cudaSuccess) e = cudaMemset(b, 0, prow * 16);
+  if (e == cudaSuccess) e = cudaMemset(c->x0, 0, prow * 16);
+  if (e == cudaSuccess) e = cudaMemset(c->dy, 0, prow * (c->dyc / 8) * 16);
   for (__nv_bfloat16* b : {c->h1, c->h2, c->dz2, c->dz1})
     if (e == cudaSuccess) e = cudaMemset(b, 0, prow * 4 * 16);
   if (e != cudaSuccess) {
@@ -304,19 +427,24 @@ extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn*
   return DH_OK;
 }
 
+extern "C" dh_status dh_cnn_create(int nx, int ny, int nz, void* stream, dh_cnn** out) {
+  return dh_cnn_create_form(nx, ny, nz, 0, stream, out);
+}
+
 extern "C" dh_status dh_cnn_set_params(dh_cnn* c, const float* params_dev, const float* norm15) {
   if (!c || !params_dev || !norm15) return DH_ERR_ARG;
   for (int k = 0; k < 5; ++k)
     if (!(norm15[5 + k] > 0.0f)) { dh_set_global_error("dh_cnn_set_params: sigma must be > 0"); return DH_ERR_ARG; }
   for (int k = 0; k < 15; ++k) c->norm[k] = norm15[k];
   cudaStream_t s = c->stream;
-  CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(c->params, params_dev, NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, s), "params"));
+  CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(c->params, params_dev, nparam(c->nout) * sizeof(float), cudaMemcpyDeviceToDevice, s), "params"));
   CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(c->norm_dev, c->norm, 15 * sizeof(float), cudaMemcpyHostToDevice, s), "norm"));
   CNN_TRY(dh_pack_conv_weights(c->params + OFF_W1, 32, 5, 0, c->pk_w1, s));
   CNN_TRY(dh_pack_conv_weights(c->params + OFF_W2, 32, 32, 0, c->pk_w2, s));
-  CNN_TRY(dh_pack_conv_weights(c->params + OFF_W3, 5, 32, 0, c->pk_w3, s));
+  CNN_TRY(dh_pack_conv_weights(c->params + OFF_W3, c->nout, 32, 0, c->pk_w3, s));
   CNN_TRY(dh_pack_conv_weights(c->params + OFF_W2, 32, 32, 1, c->pk_w2t, s));
-  CNN_TRY(dh_pack_conv_weights(c->params + OFF_W3, 5, 32, 1, c->pk_w3t, s));
+  CNN_TRY(dh_pack_conv_weights(c->params + OFF_W3, c->nout, 32, 1, c->pk_w3t, s));
+  CNN_TRY(dh_pack_conv_weights(c->params + OFF_W1, 32, 5, 1, c->pk_w1t, s));
   CNN_TRY(cnn_cuda(c, cudaStreamSynchronize(s), "set_params"));
   c->have_params = true;
   return DH_OK;
@@ -350,14 +478,45 @@ static dh_status cnn_forward(dh_cnn* c, const float* U, float* y_out, bool keep_
   CNN_TRY(cnn_cuda(c, cudaGetLastError(), "normalize"));
   CNN_TRY(dh_conv3d_bf16(c->x0, 8, c->pk_w1, 32, c->params + OFF_B1, 0, nullptr, c->h1, keep_z ? c->z1 : nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
   CNN_TRY(dh_conv3d_bf16(c->h1, 32, c->pk_w2, 32, c->params + OFF_B2, 0, nullptr, c->h2, keep_z ? c->z2 : nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
-  CNN_TRY(dh_conv3d_bf16(c->h2, 32, c->pk_w3, 16, c->params + OFF_B3, 1, nullptr, c->y, nullptr, 5, c->nx, c->ny, c->nz, c->err, s));
-  if (y_out) CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(y_out, c->y, n * 5 * sizeof(float), cudaMemcpyDeviceToDevice, s), "y"));
+  CNN_TRY(dh_conv3d_bf16(c->h2, 32, c->pk_w3, 16, c->params + off_b3(c->nout), 1, nullptr, c->y, nullptr, c->nout, c->nx, c->ny, c->nz, c->err, s));
+  if (y_out) CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(y_out, c->y, n * c->nout * sizeof(float), cudaMemcpyDeviceToDevice, s), "y"));
   c->have_forward = keep_z;
   return DH_OK;
 }
 
 extern "C" dh_status dh_cnn_forward(dh_cnn* c, const float* U, float* y_out) {
   return cnn_forward(c, U, y_out, true);
+}
+
+// Back-propagation from the output gradient already in c->dy, for the last forward: parameter
+// gradients into grads; with dLdU (nullable) also the gradient of the network input U.
+static dh_status backprop(dh_cnn* c, float* grads, float* dLdU) {
+  cudaStream_t s = c->stream;
+  const ConvGeom geo = conv_geom(c->nx, c->ny, c->nz);
+  const int nb3 = off_b3(c->nout);
+  // output layer
+  CNN_TRY(dh_conv3d_wgrad_bf16(c->h2, 32, 32, c->dy, c->dyc, c->nout, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W3, c->err, s));
+  if (c->form == 0) {
+    bias_grad(c->dy, c->dyc / 8, c->nout, geo, c->bpart, grads + nb3, s);
+  } else {
+    // a constant flux has no divergence: b3 does not enter the flux-form correction (its exact
+    // gradient is zero; summing the bf16 output gradient would only add rounding noise)
+    CNN_TRY(cnn_cuda(c, cudaMemsetAsync(grads + nb3, 0, c->nout * sizeof(float), s), "b3 grad"));
+  }
+  CNN_TRY(dh_conv3d_bf16(c->dy, c->dyc, c->pk_w3t, 32, nullptr, 2, c->z2, c->dz2, nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
+  // hidden layer
+  CNN_TRY(dh_conv3d_wgrad_bf16(c->h1, 32, 32, c->dz2, 32, 32, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W2, c->err, s));
+  bias_grad(c->dz2, 4, 32, geo, c->bpart, grads + OFF_B2, s);
+  CNN_TRY(dh_conv3d_bf16(c->dz2, 32, c->pk_w2t, 32, nullptr, 2, c->z1, c->dz1, nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
+  // first layer
+  CNN_TRY(dh_conv3d_wgrad_bf16(c->x0, 8, 5, c->dz1, 32, 32, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W1, c->err, s));
+  bias_grad(c->dz1, 4, 32, geo, c->bpart, grads + OFF_B1, s);
+  if (dLdU) {
+    // input: dL/dx0 = conv(dz1, W1 transposed), then the normalisation transposed
+    CNN_TRY(dh_conv3d_bf16(c->dz1, 32, c->pk_w1t, 16, nullptr, 1, nullptr, dLdU, nullptr, 5, c->nx, c->ny, c->nz, c->err, s));
+    input_grad_kernel<<<grid_for(5 * c->ncell), 256, 0, s>>>(dLdU, c->norm_dev, c->ncell);
+  }
+  return cnn_cuda(c, cudaGetLastError(), "backward");
 }
 
 extern "C" dh_status dh_cnn_backward(dh_cnn* c, const float* U_in, const float* U_target,
@@ -367,21 +526,25 @@ extern "C" dh_status dh_cnn_backward(dh_cnn* c, const float* U_in, const float* 
   const long long n = c->ncell;
   cudaStream_t s = c->stream;
   const ConvGeom geo = conv_geom(c->nx, c->ny, c->nz);
-  mse_grad_kernel<<<RBLOCKS, 256, 0, s>>>(c->y, U_in, U_target, c->norm_dev, geo, c->dy, c->red);
+  if (c->form == 0) {
+    mse_grad_kernel<<<RBLOCKS, 256, 0, s>>>(c->y, U_in, U_target, c->norm_dev, geo, c->dy, c->red);
+  } else {
+    flux_mse_kernel<<<RBLOCKS, 256, 0, s>>>(c->y, U_in, U_target, c->norm_dev, geo, c->g5, c->red);
+    output_grad_kernel<<<grid_for(n), 256, 0, s>>>(c->g5, nullptr, 1, geo, c->dy);
+  }
   sum_blocks_kernel<<<1, 32, 0, s>>>(c->red, RBLOCKS, 1.0 / (5.0 * (double)n), c->red + RBLOCKS);
-  // output layer
-  CNN_TRY(dh_conv3d_wgrad_bf16(c->h2, 32, 32, c->dy, 8, 5, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W3, c->err, s));
-  bias_grad(c->dy, 1, 5, geo, c->bpart, grads + OFF_B3, s);
-  CNN_TRY(dh_conv3d_bf16(c->dy, 8, c->pk_w3t, 32, nullptr, 2, c->z2, c->dz2, nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
-  // hidden layer
-  CNN_TRY(dh_conv3d_wgrad_bf16(c->h1, 32, 32, c->dz2, 32, 32, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W2, c->err, s));
-  bias_grad(c->dz2, 4, 32, geo, c->bpart, grads + OFF_B2, s);
-  CNN_TRY(dh_conv3d_bf16(c->dz2, 32, c->pk_w2t, 32, nullptr, 2, c->z1, c->dz1, nullptr, 32, c->nx, c->ny, c->nz, c->err, s));
-  // first layer
-  CNN_TRY(dh_conv3d_wgrad_bf16(c->x0, 8, 5, c->dz1, 32, 32, c->nx, c->ny, c->nz, c->partial, c->nctas, grads + OFF_W1, c->err, s));
-  bias_grad(c->dz1, 4, 32, geo, c->bpart, grads + OFF_B1, s);
-  CNN_TRY(cnn_cuda(c, cudaGetLastError(), "backward"));
+  CNN_TRY(backprop(c, grads, nullptr));
   if (loss) CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(loss, c->red + RBLOCKS, sizeof(double), cudaMemcpyDeviceToHost, s), "loss"));
+  return check_err(c);
+}
+
+extern "C" dh_status dh_cnn_vjp(dh_cnn* c, const float* dL_dcorr, float* grads, float* dL_dU) {
+  if (!c || !dL_dcorr || !grads) return DH_ERR_ARG;
+  if (!c->have_forward) { dh_set_global_error("dh_cnn_vjp: run dh_cnn_forward first"); return DH_ERR_STATE; }
+  const ConvGeom geo = conv_geom(c->nx, c->ny, c->nz);
+  output_grad_kernel<<<grid_for(c->ncell), 256, 0, c->stream>>>(dL_dcorr, c->norm_dev + 10, c->form,
+                                                                geo, c->dy);
+  CNN_TRY(backprop(c, grads, dL_dU));
   return check_err(c);
 }
 
@@ -393,7 +556,8 @@ static dh_status cnn_correct(dh_cnn* c, const float* Uin, float* Uout, double rh
   correct_kernel<<<grid_for(c->ncell), 256, 0, c->stream>>>(Uin, Uout, c->y, c->ncell, c->norm_dev,
                                                             (float)rho_floor, totals,
                                                             floor_per_mass, (float)T_floor,
-                                                            (float)(gamma - 1.0), c->err);
+                                                            (float)(gamma - 1.0), c->err, c->form,
+                                                            conv_geom(c->nx, c->ny, c->nz));
   CNN_TRY(cnn_cuda(c, cudaGetLastError(), "correct"));
   return check_err(c);
 }
@@ -417,18 +581,29 @@ extern "C" dh_status dh_adam_step(float* params, const float* grads, float* m, f
 }
 
 extern "C" long long dh_cnn_param_count(void) { return NPARAM; }
+extern "C" long long dh_cnn_param_count_form(int form) { return form == 1 ? nparam(15) : nparam(5); }
 
 // ---- the context's corrector -------------------------------------------------------------------
-extern "C" dh_status dh_set_corrector(dh_ctx* ctx, const float* params_dev, const float* norm15) {
+extern "C" dh_status dh_set_corrector_form(dh_ctx* ctx, int form, const float* params_dev,
+                                           const float* norm15) {
   if (!ctx || !params_dev || !norm15) return DH_ERR_ARG;
   if (ctx->prec != DH_F32) { ctx->err = "the corrector runs on float32 states"; return DH_ERR_ARG; }
+  if (form != 0 && form != 1) { ctx->err = "form must be 0 (state) or 1 (flux)"; return DH_ERR_ARG; }
+  if (ctx->cnn && ctx->cnn->form != form) {
+    dh_cnn_destroy(ctx->cnn);
+    ctx->cnn = nullptr;
+  }
   if (!ctx->cnn) {
-    dh_status st = dh_cnn_create(ctx->cfg.nx, ctx->cfg.ny, ctx->cfg.nz, ctx->stream, &ctx->cnn);
+    dh_status st = dh_cnn_create_form(ctx->cfg.nx, ctx->cfg.ny, ctx->cfg.nz, form, ctx->stream, &ctx->cnn);
     if (st != DH_OK) { ctx->err = dh_last_error(nullptr); return st; }
   }
   dh_status st = dh_cnn_set_params(ctx->cnn, params_dev, norm15);
   if (st != DH_OK) ctx->err = dh_last_error(nullptr);
   return st;
+}
+
+extern "C" dh_status dh_set_corrector(dh_ctx* ctx, const float* params_dev, const float* norm15) {
+  return dh_set_corrector_form(ctx, 0, params_dev, norm15);
 }
 
 extern "C" dh_status dh_correct(dh_ctx* ctx) {

@@ -379,8 +379,8 @@ dh_status dh_refresh_cfl(dh_ctx* c) {
   return DH_OK;
 }
 
-cudaError_t dh_enqueue_step_f32(dh_ctx* c) { return enqueue_step<float>(c, 0.0); }
-cudaError_t dh_enqueue_step_f64(dh_ctx* c) { return enqueue_step<double>(c, 0.0); }
+cudaError_t dh_enqueue_step_f32(dh_ctx* c, double dt) { return enqueue_step<float>(c, dt); }
+cudaError_t dh_enqueue_step_f64(dh_ctx* c, double dt) { return enqueue_step<double>(c, dt); }
 dh_status dh_finish_steps(dh_ctx* c) { return finish_steps(c, c->host_rec.nstep - c->pending_steps); }
 
 extern "C" dh_status dh_step(dh_ctx* c, double dt, double* dt_used) {

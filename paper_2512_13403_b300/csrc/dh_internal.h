@@ -70,8 +70,8 @@ void adjoint_free(dh_ctx* c);
 }  // namespace dh
 
 // dh_api.cu: step machinery shared with the adjoint driver
-cudaError_t dh_enqueue_step_f32(dh_ctx* c);
-cudaError_t dh_enqueue_step_f64(dh_ctx* c);
+cudaError_t dh_enqueue_step_f32(dh_ctx* c, double dt_fixed);   // dt_fixed <= 0: CFL
+cudaError_t dh_enqueue_step_f64(dh_ctx* c, double dt_fixed);
 dh_status dh_finish_steps(dh_ctx* c);
 // message returned by dh_last_error(NULL)
 void dh_set_global_error(const std::string& msg);

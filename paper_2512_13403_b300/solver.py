@@ -204,12 +204,14 @@ class Solver:
             return (None,) + tuple(self.mg_stats())
         return self.potential()
 
-    def adjoint_advance(self, n_steps: int, ckpt_every: int, dLdU_final):
+    def adjoint_advance(self, n_steps: int, ckpt_every: int, dLdU_final, dt: float = 0.0):
+        """dL/dU of the current state for n_steps steps (CFL steps, or each at dt > 0) and the
+        gradient dLdU_final of the state they reach; the state itself advances."""
         ptr, dev, keep = self._as_buffer(dLdU_final)
         out = torch.empty((5,) + self.shape, dtype=self.dtype, device="cuda" if dev else "cpu")
         optr, odev, okeep = self._as_buffer(out)
-        self._check(self.lib.dh_adjoint_advance(self.ctx, int(n_steps), int(ckpt_every),
-                                                C.c_void_p(ptr), C.c_void_p(optr), dev))
+        self._check(self.lib.dh_adjoint_advance_dt(self.ctx, int(n_steps), int(ckpt_every), float(dt),
+                                                   C.c_void_p(ptr), C.c_void_p(optr), dev))
         return out
 
     def save(self, path: str):
