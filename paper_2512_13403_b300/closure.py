@@ -373,14 +373,17 @@ def train_rollout(trajs: List[Trajectory], setup: ClosureSetup, params, norm, it
     params = params.clone()
     opt = Adam(params, lr=lr)
     losses = []
-    t0 = time.perf_counter()
+    t0 = None
     for it in range(iters):
+        if it == 1:                      # the first iteration loads kernels and allocates
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
         L, g = tr.loss_and_grad(trajs[it % len(trajs)], params, norm, weights)
         opt.step(g)
         losses.append(L)
         if log and (it + 1) % max(1, iters // 10) == 0:
             log(f"rollout training: iteration {it + 1}/{iters} loss {L:.4e}")
     torch.cuda.synchronize()
-    ms = 1e3 * (time.perf_counter() - t0) / max(iters, 1)
+    ms = 1e3 * (time.perf_counter() - t0) / max(iters - 1, 1) if t0 is not None else float("nan")
     tr.close()
     return params, losses, ms
