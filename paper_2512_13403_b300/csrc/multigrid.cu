@@ -32,7 +32,13 @@ constexpr int MG_LMAX = 16;
 // reductions: 8 CTAs per SM over 148 SMs (enough warps to cover the stencil loads), then one
 // warp adds the per-block partials in a fixed order
 constexpr int RED_BLOCKS = 148 * 8, RED_THREADS = 256;
-constexpr int RES_BLOCKS = 148 * 4;   // the residual's grid: one resident wave
+// the residual's z-march: 32 x 8 columns of RZ_ZC planes (one partial sum per CTA)
+constexpr int RZ_TX = 32, RZ_TY = 8, RZ_ZC = 64;
+constexpr int RZ_HX = RZ_TX + 2, RZ_HY = RZ_TY + 2, RZ_H = RZ_HX * RZ_HY;
+constexpr int RZ_D = 2, RZ_RING = 4 + RZ_D;
+inline long long residual_zm_blocks(int nx, int ny, int nz) {
+  return (long long)((nx + RZ_TX - 1) / RZ_TX) * ((ny + RZ_TY - 1) / RZ_TY) * ((nz + RZ_ZC - 1) / RZ_ZC);
+}
 }
 
 struct MG {
@@ -42,12 +48,13 @@ struct MG {
   long long cells[dh::MG_LMAX];
   // potential and source in float-float, planar: n hi floats then n lo floats (ff.cuh)
   float* phi = nullptr;
+  float* phi2 = nullptr;         // the other buffer of the residual's fused update
   float* F = nullptr;
   float* e[dh::MG_LMAX] = {nullptr};
   float* e2[dh::MG_LMAX] = {nullptr};   // the sweep's other buffer (a sweep writes e2, then swaps)
   float* r[dh::MG_LMAX] = {nullptr};
   double* G = nullptr;           // coarsest circulant pseudo-inverse
-  double* partials = nullptr;    // RED_BLOCKS doubles
+  double* partials = nullptr;    // max(RED_BLOCKS, residual CTAs) doubles
   double* scal = nullptr;        // [0] mean rho, [1] |F|^2, [2] |r|^2, [3] mean phi
   int last_cycles = 0;
   double last_res = 0.0;
@@ -91,6 +98,7 @@ cudaError_t mg_allocate(dh_ctx* c) {
   c->mg = m;
   level_dims(c->cfg, m);
   cudaError_t e = cudaMalloc(&m->phi, 2 * m->cells[0] * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->phi2, 2 * m->cells[0] * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->F, 2 * m->cells[0] * sizeof(float));
   for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
     e = cudaMalloc(&m->e[l], m->cells[l] * sizeof(float));
@@ -98,7 +106,11 @@ cudaError_t mg_allocate(dh_ctx* c) {
     if (e == cudaSuccess) e = cudaMalloc(&m->r[l], m->cells[l] * sizeof(float));
   }
   if (e == cudaSuccess) e = cudaMalloc(&m->G, m->cells[m->L - 1] * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&m->partials, RED_BLOCKS * sizeof(double));
+  {
+    const long long rb = residual_zm_blocks(m->n[0][0], m->n[0][1], m->n[0][2]);
+    if (e == cudaSuccess)
+      e = cudaMalloc(&m->partials, (rb > RED_BLOCKS ? rb : RED_BLOCKS) * sizeof(double));
+  }
   if (e == cudaSuccess) e = cudaMalloc(&m->scal, 8 * sizeof(double));
   // the potential is the warm start of the first solve: zero, not whatever the allocator held
   if (e == cudaSuccess) e = cudaMemset(m->phi, 0, 2 * m->cells[0] * sizeof(float));
@@ -145,6 +157,7 @@ void mg_free(dh_ctx* c) {
   MG* m = c->mg;
   if (!m) return;
   cudaFree(m->phi);
+  cudaFree(m->phi2);
   cudaFree(m->F);
   for (int l = 0; l < MG_LMAX; ++l) { cudaFree(m->e[l]); cudaFree(m->e2[l]); cudaFree(m->r[l]); }
   cudaFree(m->G);
@@ -238,65 +251,6 @@ __global__ void poisson_source_kernel(const T* __restrict__ rho, long long n, co
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// r = F - A phi: stores r as the float32 right-hand side of the correction, and partials of
-// |r / rms(F)|^2 with rms(F) = sqrt(fnorm2 / n).  h^2 A phi is the neighbour sum minus 6 phi:
-// the hi words go through a TwoSum chain (exact), the lo words, the chain's rounding errors and
-// the exact error of 6 phi_hi through float32, an absolute error of a few eps32^2 times
-// sum |phi| -- far below what a relative residual of 1e-6 needs at any N this part holds.
-// The grid strides through the cells together (cell q by thread q mod the grid's threads), so
-// the planes above and below a cell are read while they are still in L2; the grid is one wave.
-// Indices are 32-bit (grids below 2^31 cells) and a thread's (i, j, k) advance by the stride's
-// digits instead of being divided out per cell.
-__global__ void __launch_bounds__(RED_THREADS, 4)
-residual_ff_kernel(const float* __restrict__ phi, const float* __restrict__ F,
-                   float* __restrict__ r32, int nx, int ny, int nz, ff2 h2, float ih2,
-                   const double* fnorm2, double* partials) {
-  __shared__ double red[RED_THREADS];
-  const unsigned n = (unsigned)nx * (unsigned)ny * (unsigned)nz;
-  const unsigned plane = (unsigned)nx * (unsigned)ny;
-  const float* __restrict__ phl = phi + n;
-  const float* __restrict__ Fl = F + n;
-  const float sF = (float)(1.0 / sqrt(*fnorm2 / (double)n));
-  const unsigned stride = gridDim.x * RED_THREADS;
-  const int si = (int)(stride % (unsigned)nx), sj = (int)((stride / (unsigned)nx) % (unsigned)ny),
-            sk = (int)(stride / plane);
-  unsigned q = blockIdx.x * RED_THREADS + threadIdx.x;
-  int i = (int)(q % (unsigned)nx), j = (int)((q / (unsigned)nx) % (unsigned)ny), k = (int)(q / plane);
-  ff2 acc{0.0f, 0.0f};
-  for (; q < n; q += stride) {
-    const unsigned xm = i == 0 ? q + nx - 1 : q - 1, xp = i == nx - 1 ? q + 1 - nx : q + 1;
-    const unsigned ym = j == 0 ? q + plane - nx : q - nx, yp = j == ny - 1 ? q + nx - plane : q + nx;
-    const unsigned zm = k == 0 ? q + n - plane : q - plane, zp = k == nz - 1 ? q + plane - n : q + plane;
-    const unsigned nq[6] = {zm, zp, ym, yp, xm, xp};
-    const ff2 c{phi[q], phl[q]};
-    // -6 phi_c: exact product of the hi word
-    ff2 sum{__fmul_rn(-6.0f, c.hi), 0.0f};
-    const float err = __fmaf_rn(-6.0f, c.hi, -sum.hi);
-    float lo = __fmul_rn(-6.0f, c.lo);
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-      ff_acc(sum, phi[nq[a]]);
-      lo = __fadd_rn(lo, phl[nq[a]]);
-    }
-    const ff2 lap = ff_fast_two_sum(sum.hi, __fadd_rn(sum.lo, __fadd_rn(err, lo)));  // h^2 A phi
-    const ff2 fh = ff_mul(ff2{F[q], Fl[q]}, h2);                                      // h^2 F
-    const ff2 d = ff_two_sum(fh.hi, -lap.hi);
-    const float rr = __fmul_rn(__fadd_rn(d.hi, __fadd_rn(d.lo, __fsub_rn(fh.lo, lap.lo))), ih2);
-    r32[q] = rr;
-    const float rs = rr * sF;
-    ff_acc(acc, rs * rs);
-    // (i, j, k) of q + stride
-    i += si;
-    int cy = i >= nx;
-    if (cy) i -= nx;
-    j += sj + cy;
-    cy = j >= ny;
-    if (cy) j -= ny;
-    k += sk + cy;
-  }
-  const double s = block_sum(ff_to_double(acc), red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
 
 // Asynchronous 4-byte global -> shared copies (cp.async), grouped per plane.
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
@@ -640,58 +594,222 @@ __global__ void jacobi_zero_kernel(float* __restrict__ en, const float* __restri
     en[q] = s * r[q];
 }
 
-// rc[I] = mean over the 8 children of (r - A e), coarse dims (cx, cy, cz).
+// r = F - A phi as a z-march, with the correction of the previous cycle applied on the way
+// (UPDATE): phi' = phi + e (float-float), r = F - A phi' (stored as the float32 right-hand side
+// of the next correction), and partials of |r / rms(F)|^2 with rms(F) = sqrt(fnorm2 / n); phi'
+// goes to a second buffer (neighbouring CTAs still read phi).  A CTA owns a 32 x 8 column and
+// RZ_ZC planes; phi (both words) and e arrive by cp.async on the tile and a one-cell halo, two
+// planes ahead; each landed plane is updated in shared memory once.  h^2 A phi is the neighbour
+// sum minus 6 phi: the hi words go through a TwoSum chain (exact), the lo words, the chain's
+// rounding errors and the exact error of 6 phi_hi through float32, an absolute error of a few
+// eps32^2 times sum |phi| -- far below what a relative residual of 1e-6 needs at any N this
+// part holds.
+
+template <bool UPDATE>
+__global__ void __launch_bounds__(256)
+residual_zm_kernel(const float* __restrict__ phi, float* __restrict__ phi_out,
+                   const float* __restrict__ e, const float* __restrict__ F,
+                   float* __restrict__ r32, int nx, int ny, int nz, ff2 h2, float ih2,
+                   const double* fnorm2, double* partials) {
+  __shared__ float s_hi[RZ_RING][RZ_H];
+  __shared__ float s_lo[RZ_RING][RZ_H];
+  __shared__ float s_e[UPDATE ? RZ_RING : 1][RZ_H];
+  __shared__ double red[256];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * RZ_TX, y0 = blockIdx.y * RZ_TY, z0 = blockIdx.z * RZ_ZC;
+  const int z1 = z0 + RZ_ZC < nz ? z0 + RZ_ZC : nz;
+  const int nit = z1 - z0;
+  const long long plane = (long long)nx * ny;
+  const long long n = plane * nz;
+  const float* __restrict__ phl = phi + n;
+  const float sF = (float)(1.0 / sqrt(*fnorm2 / (double)n));
+  // this thread's (up to) two halo positions: offsets within a plane (cell 0 past the halo)
+  int hoff[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int pe = tid + 256 * u;
+    const int hx = x0 - 1 + pe % RZ_HX, hy = y0 - 1 + pe / RZ_HX;
+    hoff[u] = (pe < RZ_H && hx < nx + 1 && hy < ny + 1) ? wrap(hy, ny) * nx + wrap(hx, nx) : 0;
+  }
+  const bool h2nd = tid + 256 < RZ_H;
+  // plane z0 - 1 + m lives in slot m % RZ_RING
+  auto copy_plane = [&](int m) {
+    const long long b = (long long)wrap(z0 - 1 + m, nz) * plane;
+    const int sl = m % RZ_RING;
+    cp_async4(&s_hi[sl][tid], phi + b + hoff[0]);
+    cp_async4(&s_lo[sl][tid], phl + b + hoff[0]);
+    if (UPDATE) cp_async4(&s_e[UPDATE ? sl : 0][tid], e + b + hoff[0]);
+    if (h2nd) {
+      cp_async4(&s_hi[sl][tid + 256], phi + b + hoff[1]);
+      cp_async4(&s_lo[sl][tid + 256], phl + b + hoff[1]);
+      if (UPDATE) cp_async4(&s_e[UPDATE ? sl : 0][tid + 256], e + b + hoff[1]);
+    }
+  };
+  auto issue_group = [&](int g) {   // group g carries plane index g + 2
+    if (g < nit) copy_plane(g + 2);
+    cp_async_commit();
+  };
+  auto update_plane = [&](int m) {  // phi' = phi + e in place, this thread's positions
+    const int sl = m % RZ_RING;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int pe = tid + 256 * u;
+      if (pe < RZ_H) {
+        const ff2 v = ff_add_f(ff2{s_hi[sl][pe], s_lo[sl][pe]}, s_e[UPDATE ? sl : 0][pe]);
+        s_hi[sl][pe] = v.hi;
+        s_lo[sl][pe] = v.lo;
+      }
+    }
+  };
+  const int tx = tid % RZ_TX, ty = tid / RZ_TX;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < nx && y < ny;
+  const int c = (ty + 1) * RZ_HX + tx + 1;
+  copy_plane(0);
+  copy_plane(1);
+#pragma unroll
+  for (int g = 0; g < RZ_D; ++g) issue_group(g);
+  ff2 acc{0.0f, 0.0f};
+  for (int it = 0; it < nit; ++it) {
+    const long long q = (long long)(z0 + it) * plane + (long long)y * nx + x;
+    float fhi = 0.f, flo = 0.f;
+    if (active) { fhi = F[q]; flo = F[n + q]; }
+    issue_group(it + RZ_D);
+    cp_async_wait<RZ_D>();
+    __syncthreads();
+    if (UPDATE) {
+      if (it == 0) { update_plane(0); update_plane(1); }
+      update_plane(it + 2);
+      __syncthreads();
+    }
+    if (active) {
+      const int sm = it % RZ_RING, sc = (it + 1) % RZ_RING, sp = (it + 2) % RZ_RING;
+      const ff2 cv{s_hi[sc][c], s_lo[sc][c]};
+      ff2 sum{__fmul_rn(-6.0f, cv.hi), 0.0f};
+      const float err = __fmaf_rn(-6.0f, cv.hi, -sum.hi);
+      float lo = __fmul_rn(-6.0f, cv.lo);
+      ff_acc(sum, s_hi[sm][c]);      lo = __fadd_rn(lo, s_lo[sm][c]);
+      ff_acc(sum, s_hi[sp][c]);      lo = __fadd_rn(lo, s_lo[sp][c]);
+      ff_acc(sum, s_hi[sc][c - RZ_HX]); lo = __fadd_rn(lo, s_lo[sc][c - RZ_HX]);
+      ff_acc(sum, s_hi[sc][c + RZ_HX]); lo = __fadd_rn(lo, s_lo[sc][c + RZ_HX]);
+      ff_acc(sum, s_hi[sc][c - 1]);  lo = __fadd_rn(lo, s_lo[sc][c - 1]);
+      ff_acc(sum, s_hi[sc][c + 1]);  lo = __fadd_rn(lo, s_lo[sc][c + 1]);
+      const ff2 lap = ff_fast_two_sum(sum.hi, __fadd_rn(sum.lo, __fadd_rn(err, lo)));   // h^2 A phi
+      const ff2 fh = ff_mul(ff2{fhi, flo}, h2);                                          // h^2 F
+      const ff2 d = ff_two_sum(fh.hi, -lap.hi);
+      const float rr = __fmul_rn(__fadd_rn(d.hi, __fadd_rn(d.lo, __fsub_rn(fh.lo, lap.lo))), ih2);
+      r32[q] = rr;
+      const float rs = rr * sF;
+      ff_acc(acc, rs * rs);
+      if (UPDATE) {
+        phi_out[q] = cv.hi;
+        phi_out[n + q] = cv.lo;
+      }
+    }
+  }
+  cp_async_wait<0>();
+  red[tid] = ff_to_double(acc);
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) red[tid] += red[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0)
+    partials[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = red[0];
+}
+
+// rc[I] = mean over the 8 children of (r - A e), coarse dims (cx, cy, cz).  One thread per coarse
+// cell.  Over a 2x2x2 block the children's Laplacians sum to the 24 faces of the block:
+// sum_children h^2 (A e)_child = (sum of the 24 outside neighbours) - 3 (sum of the 8 children),
+// since every interior face cancels.  Rows of the fine grid are read as float2 pairs (x even).
 __global__ void resid_restrict_kernel(const float* __restrict__ e, const float* __restrict__ r,
                                       float* __restrict__ rc, int cx, int cy, int cz, float ih2) {
   const int nx = 2 * cx, ny = 2 * cy, nz = 2 * cz;
   const long long nc = (long long)cx * cy * cz;
+  const long long plane = (long long)nx * ny;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
        t += (long long)gridDim.x * blockDim.x) {
     const unsigned u = (unsigned)t / (unsigned)cx;
     const int I = (int)((unsigned)t - u * (unsigned)cx);
     const int K = (int)(u / (unsigned)cy);
     const int J = (int)(u - (unsigned)K * (unsigned)cy);
-    float s = 0.f;
+    const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+    const int im = wrap(i0 - 1, nx), ip = wrap(i0 + 2, nx);
+    const int jm = wrap(j0 - 1, ny), jp = wrap(j0 + 2, ny);
+    const int km = wrap(k0 - 1, nz), kp = wrap(k0 + 2, nz);
+    auto row = [&](int j, int k) { return (long long)k * plane + (long long)j * nx; };
+    float inside = 0.f, outside = 0.f, rs = 0.f;
+#pragma unroll
     for (int dk = 0; dk < 2; ++dk)
-      for (int dj = 0; dj < 2; ++dj)
-        for (int di = 0; di < 2; ++di) {
-          const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
-          const long long row = (long long)k * ny;
-          const long long q = (row + j) * nx + i;
-          const float nb = e[((long long)wrap(k - 1, nz) * ny + j) * nx + i] +
-                           e[((long long)wrap(k + 1, nz) * ny + j) * nx + i] +
-                           e[(row + wrap(j - 1, ny)) * nx + i] + e[(row + wrap(j + 1, ny)) * nx + i] +
-                           e[(row + j) * nx + wrap(i - 1, nx)] + e[(row + j) * nx + wrap(i + 1, nx)];
-          s += r[q] - (nb - 6.0f * e[q]) * ih2;
-        }
-    rc[t] = 0.125f * s;
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj) {
+        const long long rw = row(j0 + dj, k0 + dk);
+        const float2 ev = *reinterpret_cast<const float2*>(e + rw + i0);
+        const float2 rv = *reinterpret_cast<const float2*>(r + rw + i0);
+        inside += ev.x + ev.y;
+        rs += rv.x + rv.y;
+        outside += e[rw + im] + e[rw + ip];                              // x faces
+      }
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const float2 ym = *reinterpret_cast<const float2*>(e + row(jm, k0 + d) + i0);   // y faces
+      const float2 yp = *reinterpret_cast<const float2*>(e + row(jp, k0 + d) + i0);
+      const float2 zm = *reinterpret_cast<const float2*>(e + row(j0 + d, km) + i0);   // z faces
+      const float2 zp = *reinterpret_cast<const float2*>(e + row(j0 + d, kp) + i0);
+      outside += (ym.x + ym.y) + (yp.x + yp.y) + (zm.x + zm.y) + (zp.x + zp.y);
+    }
+    rc[t] = 0.125f * (rs - (outside - 3.0f * inside) * ih2);
   }
 }
 
 // e_fine += P e_coarse: per axis 3/4 of the parent and 1/4 of the parent's neighbour on the
-// fine cell's side (weights (27, 9, 9, 9, 3, 3, 3, 1)/64), periodic.
+// fine cell's side (weights (27, 9, 9, 9, 3, 3, 3, 1)/64), periodic.  One thread per coarse
+// cell: its 27-neighbourhood, combined axis by axis, gives its 8 children (stored as float2
+// pairs along x).
 __global__ void prolong_add_kernel(float* __restrict__ ef, const float* __restrict__ ec, int cx,
                                    int cy, int cz) {
-  const int nx = 2 * cx, ny = 2 * cy, nz = 2 * cz;
-  const long long nf = (long long)nx * ny * nz;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nf;
-       q += (long long)gridDim.x * blockDim.x) {
-    const unsigned u = (unsigned)q / (unsigned)nx;
-    const int i = (int)((unsigned)q - u * (unsigned)nx);
-    const int k = (int)(u / (unsigned)ny);
-    const int j = (int)(u - (unsigned)k * (unsigned)ny);
-    const int I = i >> 1, J = j >> 1, K = k >> 1;
-    const int I2 = wrap(I + ((i & 1) ? 1 : -1), cx);
-    const int J2 = wrap(J + ((j & 1) ? 1 : -1), cy);
-    const int K2 = wrap(K + ((k & 1) ? 1 : -1), cz);
-    const int Is[2] = {I, I2}, Js[2] = {J, J2}, Ks[2] = {K, K2};
-    const float w[2] = {0.75f, 0.25f};
-    float s = 0.f;
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b)
-        for (int c = 0; c < 2; ++c)
-          s += w[a] * w[b] * w[c] * ec[((long long)Ks[a] * cy + Js[b]) * cx + Is[c]];
-    ef[q] += s;
+  const int nx = 2 * cx, ny = 2 * cy;
+  const long long nc = (long long)cx * cy * cz;
+  const long long plane = (long long)nx * ny;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
+       t += (long long)gridDim.x * blockDim.x) {
+    const unsigned u = (unsigned)t / (unsigned)cx;
+    const int I = (int)((unsigned)t - u * (unsigned)cx);
+    const int K = (int)(u / (unsigned)cy);
+    const int J = (int)(u - (unsigned)K * (unsigned)cy);
+    const int Is[3] = {wrap(I - 1, cx), I, wrap(I + 1, cx)};
+    const int Js[3] = {wrap(J - 1, cy), J, wrap(J + 1, cy)};
+    const int Ks[3] = {wrap(K - 1, cz), K, wrap(K + 1, cz)};
+    // along x: X[d][b][c] = 3/4 parent + 1/4 neighbour on side d (d = 0: -1, d = 1: +1)
+    float X[2][3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float* rowp = ec + ((long long)Ks[c] * cy + Js[b]) * cx;
+        const float m0 = rowp[Is[0]], m1 = rowp[Is[1]], m2 = rowp[Is[2]];
+        X[0][b][c] = 0.75f * m1 + 0.25f * m0;
+        X[1][b][c] = 0.75f * m1 + 0.25f * m2;
+      }
+#pragma unroll
+    for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj) {
+        float v[2];
+#pragma unroll
+        for (int di = 0; di < 2; ++di) {
+          float Y[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Y[c] = 0.75f * X[di][1][c] + 0.25f * X[di][dj == 0 ? 0 : 2][c];
+          v[di] = 0.75f * Y[1] + 0.25f * Y[dk == 0 ? 0 : 2];
+        }
+        float2* dst = reinterpret_cast<float2*>(ef + (long long)(2 * K + dk) * plane +
+                                                (long long)(2 * J + dj) * nx + 2 * I);
+        float2 w = *dst;
+        w.x += v[0];
+        w.y += v[1];
+        *dst = w;
+      }
   }
 }
 
@@ -708,12 +826,6 @@ __global__ void coarse_solve_kernel(const float* __restrict__ r, float* __restri
     }
     e[p] = (float)s;
   }
-}
-
-__global__ void update_ff_kernel(float* __restrict__ phi, const float* __restrict__ e, long long n) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x)
-    ff_store(phi, n, q, ff_add_f(ff_load(phi, n, q), e[q]));
 }
 
 // Per-block float-float sums of the potential (the gauge's mean), in float64 partials.
@@ -827,11 +939,22 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
   int cycles = 0;
   double rel = 0.0;
   bool ok = false;
+  const dim3 rg((nx + RZ_TX - 1) / RZ_TX, (ny + RZ_TY - 1) / RZ_TY, (nz + RZ_ZC - 1) / RZ_ZC);
+  const int rblocks = (int)residual_zm_blocks(nx, ny, nz);
+  bool pending = false;   // a correction e[0] not yet added to phi
   while (true) {
     prof_begin(c, DH_KERNEL_MG);
-    residual_ff_kernel<<<RES_BLOCKS, RED_THREADS, 0, s>>>(m->phi, m->F, m->r[0], nx, ny, nz, h2,
-                                                          ih2, m->scal + 1, m->partials);
-    finalize_kernel<<<1, 32, 0, s>>>(m->partials, RES_BLOCKS, m->scal + 2, 1.0 / (double)n);
+    if (pending) {
+      // phi2 = phi + e and its residual in one pass, then phi2 becomes phi
+      residual_zm_kernel<true><<<rg, 256, 0, s>>>(m->phi, m->phi2, m->e[0], m->F, m->r[0], nx, ny,
+                                                  nz, h2, ih2, m->scal + 1, m->partials);
+      std::swap(m->phi, m->phi2);
+    } else {
+      residual_zm_kernel<false><<<rg, 256, 0, s>>>(m->phi, nullptr, nullptr, m->F, m->r[0], nx, ny,
+                                                   nz, h2, ih2, m->scal + 1, m->partials);
+    }
+    pending = false;
+    finalize_kernel<<<1, 32, 0, s>>>(m->partials, rblocks, m->scal + 2, 1.0 / (double)n);
     prof_end(c, 2);
     double h[3];
     cudaError_t e = cudaMemcpyAsync(h, m->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -850,8 +973,8 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
     if (cycles >= g.mg_max_cycles) break;
     prof_begin(c, DH_KERNEL_MG);
     cycle(c, 0, true);
-    update_ff_kernel<<<grid_for(n), 256, 0, s>>>(m->phi, m->e[0], n);
-    prof_end(c, 1);
+    prof_end(c, 0);
+    pending = true;   // the next residual adds e[0]
     ++cycles;
   }
   if (gauge) {
@@ -909,10 +1032,16 @@ cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, float* x) {
                                                                    m->F, m->partials);
   finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
   prof_end(c, 4);
+  // x stands in for the context's potential; the fused update alternates between the two
+  // buffers, so the result is copied into x if it ends in the other one
   float* keep = m->phi;
+  float* keep2 = m->phi2;
   m->phi = x;
   cudaError_t e = mg_iterate(c, true);
+  if (e == cudaSuccess && m->phi != x)
+    e = cudaMemcpyAsync(x, m->phi, 2 * n * sizeof(float), cudaMemcpyDeviceToDevice, s);
   m->phi = keep;
+  m->phi2 = keep2;
   return e;
 }
 
