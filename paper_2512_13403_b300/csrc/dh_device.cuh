@@ -213,7 +213,9 @@ __device__ __forceinline__ Flux<float> hllc_packed(float rL, float uL, float aL,
                                                    float gamma, float gm1) {
   const float2 r = f2(rL, rR), u = f2(uL, uR), pp = f2(pL, pR);
   const float2 gp = p_mul(pp, f2s(gamma));
-  const float2 c = f2(q_sqrt(q_div(gp.x, rL)), q_sqrt(q_div(gp.y, rR)));
+  // c = sqrt(gamma p / rho) = gamma p / sqrt(gamma p rho): one reciprocal square root per side
+  const float2 gpr = p_mul(gp, r);
+  const float2 c = p_mul(gp, f2(gpr.x > 0.0f ? rsqrtf(gpr.x) : 0.0f, gpr.y > 0.0f ? rsqrtf(gpr.y) : 0.0f));
   const float2 um = p_sub(u, c), upc = p_add(u, c);
   const float SL = fminf(um.x, um.y);
   const float SR = fmaxf(upc.x, upc.y);
@@ -229,14 +231,19 @@ __device__ __forceinline__ Flux<float> hllc_packed(float rL, float uL, float aL,
   const float pk = left ? pL : pR, S = left ? SL : SR, dk = left ? d.x : d.y;
 
   const float2 ua2 = p_mul(f2(uk, ak), f2(uk, ak));
-  const float E = q_div(pk, gm1) + 0.5f * rk * (ua2.x + ua2.y + bk * bk);
+  const float igm1 = 1.0f / gm1;   // uniform: hoisted out of the face loops
+  const float E = pk * igm1 + 0.5f * rk * (ua2.x + ua2.y + bk * bk);
   const float mass = rk * uk;
   const float2 fna = p_fma(f2s(mass), f2(uk, ak), f2(pk, 0.0f));   // (mass u + p, mass a)
   Flux<float> F{mass, fna.x, fna.y, mass * bk, uk * (E + pk)};
   if (star) {
+    // E* = rho d/(S - S*) (E/rho + (S* - u)(S* + p/(rho d))) with one reciprocal:
+    // = (d (E + rho S* (S* - u)) + (S* - u) p) / (S - S*)
+    const float inv = q_div(1.0f, S - Sstar);
     const float rdk = rk * dk;
-    const float coef = q_div(rdk, S - Sstar);
-    const float Es = coef * (q_div(E, rk) + (Sstar - uk) * (Sstar + q_div(pk, rdk)));
+    const float coef = rdk * inv;
+    const float sdu = Sstar - uk;
+    const float Es = (dk * (E + rk * Sstar * sdu) + sdu * pk) * inv;
     const float w = coef - rk;
     const float2 f0n = p_fma(f2s(S), f2(w, coef * Sstar - mass), f2(F.f0, F.fn));
     const float2 ft = p_fma(f2s(S * w), f2(ak, bk), f2(F.ft1, F.ft2));

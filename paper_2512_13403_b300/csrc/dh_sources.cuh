@@ -163,12 +163,12 @@ __device__ __forceinline__ real cooling_energy(real r, real mx, real my, real mz
   const real ir = q_div(real(1), r);
   const real kin = real(0.5) * (mx * mx + my * my + mz * mz) * ir;
   const real Eth = E - kin;
-  const real Efl = q_div(r * T_floor, gm1);
+  const real Efl = r * T_floor * (real(1) / gm1);
   if (!(Eth > Efl)) return E;
   const real r2 = r * r;
   const real Ed0 = -r2 * q_sqrt(gm1 * Eth * ir);
-  const real tcool = q_div(Eth, -Ed0);
-  const real raw = ceil(q_div(dt, frac * tcool));
+  // dt / (frac t_cool) with t_cool = Eth / (-Ed0), as one division
+  const real raw = ceil(q_div(dt * -Ed0, frac * Eth));
   // clamp to [1, nsub_max]; a NaN count also takes the cap, so the loop below is always bounded
   real nsub = raw;
   if (!(raw <= real(nsub_max))) {
@@ -207,7 +207,7 @@ __device__ __forceinline__ void cooling_tangents(real r, real mx, real my, real 
   const real ir = q_div(real(1), r);
   const real kin = real(0.5) * (mx * mx + my * my + mz * mz) * ir;
   const real Eth = E - kin;
-  const real Efl = q_div(r * T_floor, gm1);
+  const real Efl = r * T_floor * (real(1) / gm1);
   cR = real(0);
   cE = real(1);
   if (!(Eth > Efl)) return;
@@ -220,8 +220,7 @@ __device__ __forceinline__ void cooling_tangents(real r, real mx, real my, real 
     else { tr = real(0.5) * (xr + dfl); te = real(0.5) * xe; }
   };
   const real Ed0 = -r2 * q_sqrt(gm1 * Eth * ir);
-  const real tcool = q_div(Eth, -Ed0);
-  const real raw = ceil(q_div(dt, frac * tcool));
+  const real raw = ceil(q_div(dt * -Ed0, frac * Eth));   // the forward's substep count
   real nsub = raw;
   if (!(raw <= real(nsub_max))) nsub = real(nsub_max);
   if (!(nsub >= real(1))) nsub = real(1);
@@ -268,7 +267,13 @@ template <typename real>
 __device__ __forceinline__ real cfl_time(real r, real mx, real my, real mz, real E, real gamma,
                                          real gm1, real dx, real dy, real dz) {
   const Prim<real> w = cons_to_prim(r, mx, my, mz, E, gm1);
-  const real c = q_sqrt(q_div(gamma * w.p, w.r));
+  real c;
+  if constexpr (std::is_same<real, float>::value) {
+    const float gpr = gamma * w.p * w.r;    // c = gamma p / sqrt(gamma p rho)
+    c = gpr > 0.0f ? gamma * w.p * rsqrtf(gpr) : 0.0f;
+  } else {
+    c = q_sqrt(q_div(gamma * w.p, w.r));
+  }
   const real tx = q_div(dx, fabs(w.vx) + c);
   const real ty = q_div(dy, fabs(w.vy) + c);
   const real tz = q_div(dz, fabs(w.vz) + c);
