@@ -584,10 +584,10 @@ def main():
     ap.add_argument("--no-corrector", action="store_true")
     ap.add_argument("--no-selfgrav", action="store_true", help="skip the 1024^3 self-gravitating leg")
     ap.add_argument("--sg-grid", type=int, default=1024)
-    ap.add_argument("--rollout-trajs", type=int, default=4)
-    ap.add_argument("--rollout-unroll", type=int, default=8)
-    ap.add_argument("--rollout-iters", type=int, default=64)
-    ap.add_argument("--rollout-lr", type=float, default=3e-4)
+    ap.add_argument("--rollout-trajs", type=int, default=8)
+    ap.add_argument("--rollout-unroll", type=int, default=32)
+    ap.add_argument("--rollout-iters", type=int, default=80)
+    ap.add_argument("--rollout-lr", type=float, default=1e-4)
     ap.add_argument("--no-scheme-variants", action="store_true",
                     help="skip the forward step per limiter and integrator")
     ap.add_argument("--no-poisson-variants", action="store_true",
