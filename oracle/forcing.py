@@ -124,6 +124,21 @@ class OUForcing:
         """a(x) normalised to the prescribed rms amplitude (Sec. 3.1.1)."""
         return self.raw_field(shape) * (self.a_rms / math.sqrt(self.mean_square()))
 
+    def field_at(self, shape, k: torch.Tensor, j: torch.Tensor, i: torch.Tensor) -> torch.Tensor:
+        """The normalised a(x) of `field` at the cells (k, j, i) only (integer tensors of one
+        shape), shape (3,) + k.shape: the same sum over forced modes, for grids too large to
+        synthesise whole."""
+        nz, ny, nx = shape
+        x = (i.to(torch.float64) + 0.5) / nx
+        y = (j.to(torch.float64) + 0.5) / ny
+        z = (k.to(torch.float64) + 0.5) / nz
+        a = torch.zeros((3,) + tuple(k.shape), dtype=torch.float64)
+        for m, (mx, my, mz) in enumerate(forced_modes()):
+            e = torch.exp(1j * (2.0 * math.pi * (mx * x + my * y + mz * z)))
+            for c in range(3):
+                a[c] += 2.0 * (self.a_hat[m, c] * e).real
+        return a * (self.a_rms / math.sqrt(self.mean_square()))
+
 
 def apply_forcing(U: torch.Tensor, a: torch.Tensor, dt: float) -> torch.Tensor:
     """dm = rho a dt, dE = (m . a) dt, m before the kick (Sec. 3.1.1)."""

@@ -138,3 +138,16 @@ def test_cooling_floor_kinetic_and_cold_cells():
     assert float(Eth[0]) == pytest.approx(float(floor[0]), rel=1e-12)  # long step: reaches the floor
     assert torch.equal(out[4, 1], U[4, 1])  # below the floor: untouched
     assert torch.equal(out[:4], U[:4])
+
+
+def test_forcing_field_at_cells_equals_the_whole_field():
+    from oracle import forcing as of
+    ou = of.OUForcing(seed=3, tau=0.5, a_rms=1.0)
+    ou.update(0.01, 0)
+    shape = (6, 7, 8)
+    full = ou.field(shape)
+    g = torch.Generator().manual_seed(0)
+    k = torch.randint(0, 6, (50,), generator=g)
+    j = torch.randint(0, 7, (50,), generator=g)
+    i = torch.randint(0, 8, (50,), generator=g)
+    assert torch.allclose(ou.field_at(shape, k, j, i), full[:, k, j, i], rtol=0, atol=1e-14)
