@@ -13,6 +13,7 @@
 #include <math.h>
 #include "dh_kernels.h"
 #include "dh_sources.cuh"
+#include "ff.cuh"
 #include "../../include/dh.h"
 
 namespace dh {
@@ -555,9 +556,31 @@ __global__ void totals_partial_kernel(const real* __restrict__ U, long long n3,
   const long long per = (n3 + gridDim.x - 1) / gridDim.x;
   const long long b0 = blockIdx.x * per;
   const long long b1 = b0 + per < n3 ? b0 + per : n3;
-  for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+  if constexpr (std::is_same<real, float>::value) {
+    // float32 state: each thread adds 8 values per field in compensated float32 (TwoSum: the
+    // chunk's sum to a few eps32^2 of its magnitude), then the two words in float64 -- a
+    // quarter of the float64 operations, which bound this reduction on this part
+    constexpr int CH = 8;
+    for (long long i = b0 + threadIdx.x; i < b1; i += (long long)CH * blockDim.x) {
+      ff2 acc[5];
 #pragma unroll
-    for (int f = 0; f < 5; ++f) s[f] += (double)__ldg(U + f * n3 + i);
+      for (int f = 0; f < 5; ++f) acc[f] = ff2{0.0f, 0.0f};
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const long long idx = i + (long long)u * blockDim.x;
+        if (idx < b1) {
+#pragma unroll
+          for (int f = 0; f < 5; ++f) ff_acc(acc[f], __ldg(U + f * n3 + idx));
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 5; ++f) s[f] += (double)acc[f].hi + (double)acc[f].lo;
+    }
+  } else {
+    for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+#pragma unroll
+      for (int f = 0; f < 5; ++f) s[f] += (double)__ldg(U + f * n3 + i);
+    }
   }
 #pragma unroll
   for (int f = 0; f < 5; ++f) red[f][threadIdx.x] = s[f];

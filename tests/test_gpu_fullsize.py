@@ -142,3 +142,19 @@ def test_corrector_64_sampled_cells_vs_oracle():
         num += float((d ** 2).sum())
         den += float((yr[:, r, r, r] ** 2).sum())
     assert math.sqrt(num / den) < 1e-2
+
+
+def test_conserved_totals_256_float32():
+    """The float32 state's totals (compensated float32 chunks, float64 across them) against
+    float64 sums on the host, at the benchmark's size."""
+    n = 256
+    shape = (n, n, n)
+    U0 = torch.from_numpy(inputs.decaying_turbulence(shape, seed=3, sigma=0.5, mach=1.0, P0=0.6)).float()
+    s = solver(shape, "f32")
+    s.init_state(U0.cuda().contiguous())
+    tot = s.conserved_totals()
+    Uh = U0.numpy().astype(np.float64)
+    for f in range(5):
+        ref = float(Uh[f].sum())
+        scale = float(np.abs(Uh[f]).sum())
+        assert abs(tot[f] - ref) <= 1e-12 * scale, (f, tot[f], ref)
