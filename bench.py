@@ -182,6 +182,18 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_replicas(ms: float, e2e_s: float, ws: int, cells: int, steps: int, device):
+    """Whole-job numbers of N independent replicas: the slowest rank's device time (ms) and
+    end-to-end time (s) by a MAX all-reduce, and the cell-updates/s of all ranks together over
+    each.  Returns (ms_max, e2e_s_max, value, e2e_value)."""
+    import torch
+    t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=device)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max, e2e_max = (float(v) for v in t.tolist())
+    return ms_max, e2e_max, ws * cells * steps / (ms_max * 1e-3), ws * cells * steps / e2e_max
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -248,12 +260,8 @@ def run_ours(args):
         e2e_s = time.perf_counter() - t0
         s2.close()
 
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t)
     cells = n ** 3
-    value = ws * cells * args.steps / (ms_max * 1e-3)
+    ms_max, e2e_max, value, e2e_value = aggregate_replicas(ms, e2e_s, ws, cells, args.steps, "cuda")
 
     peak, peak_kind = _peaks()
     n2, t2 = prof["stage2"]
@@ -283,7 +291,7 @@ def run_ours(args):
                                "frac": ach2 / peak},
                     "prologue": {"launches": prof["prologue"][0],
                                  "avg_ms": prof["prologue"][1] / max(prof["prologue"][0], 1)}},
-        "e2e": {"value": cells * args.steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes / args.steps,
                 "d2h_bytes_per_step": 40 + state_bytes / args.steps},
         "gpu_launches": gpu_launches,
