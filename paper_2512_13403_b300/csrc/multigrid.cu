@@ -58,6 +58,15 @@ struct MG {
   double* scal = nullptr;        // [0] mean rho, [1] |F|^2, [2] |r|^2, [3] mean phi
   int last_cycles = 0;
   double last_res = 0.0;
+  // One cycle as a CUDA graph (captured on first use): its hundreds of small launches at the
+  // coarse levels (a W-cycle visits level l 2^l times) replay without per-launch host work.
+  // Valid while the e / e2 buffers are where they were at capture, which holds when every
+  // level swaps them an even number of times per cycle.
+  cudaGraphExec_t cycle_exec = nullptr;
+  float* cycle_e[dh::MG_LMAX] = {nullptr};
+  float* cycle_e2[dh::MG_LMAX] = {nullptr};
+  long long cycle_launches = 0;
+  bool cycle_graph_failed = false;
 };
 
 namespace dh {
@@ -163,6 +172,7 @@ void mg_free(dh_ctx* c) {
   cudaFree(m->G);
   cudaFree(m->partials);
   cudaFree(m->scal);
+  if (m->cycle_exec) cudaGraphExecDestroy(m->cycle_exec);
   delete m;
   c->mg = nullptr;
 }
@@ -922,6 +932,68 @@ static void cycle(dh_ctx* c, int l, bool zero_init) {
   c->launches += 2;
 }
 
+// Launches one cycle from the finest level: replays the captured graph when the buffers are
+// where they were at capture, else captures it (or, if capture fails, launches directly).
+static cudaError_t run_cycle(dh_ctx* c) {
+  MG* m = c->mg;
+  const dh_config& g = c->cfg;
+  // the buffer layout returns to its start after a cycle iff every level swaps an even number
+  // of times: each visit swaps (mg_pre + mg_post) times
+  const bool even = (g.mg_pre + g.mg_post) % 2 == 0;
+  auto same_layout = [&]() {
+    for (int l = 0; l < m->L; ++l)
+      if (m->cycle_e[l] != m->e[l]) return false;
+    return true;
+  };
+  if (m->cycle_exec && even && same_layout()) {
+    c->launches += m->cycle_launches;
+    return cudaGraphLaunch(m->cycle_exec, c->stream);
+  }
+  if (!even || m->cycle_graph_failed) {
+    cycle(c, 0, true);
+    return cudaGetLastError();
+  }
+  if (m->cycle_exec) {
+    cudaGraphExecDestroy(m->cycle_exec);
+    m->cycle_exec = nullptr;
+  }
+  for (int l = 0; l < m->L; ++l) {
+    m->cycle_e[l] = m->e[l];
+    m->cycle_e2[l] = m->e2[l];
+  }
+  cudaGraph_t graph = nullptr;
+  const long long before = c->launches;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cycle(c, 0, true);
+    e = cudaStreamEndCapture(c->stream, &graph);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&m->cycle_exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  m->cycle_launches = c->launches - before;
+  c->launches = before;
+  if (e != cudaSuccess || !m->cycle_exec) {
+    // no graph on this stream (for instance the caller is capturing it): direct launches, and
+    // the buffers as they were before the aborted capture
+    cudaGetLastError();
+    m->cycle_exec = nullptr;
+    m->cycle_graph_failed = true;
+    for (int l = 0; l < m->L; ++l) {
+      m->e[l] = m->cycle_e[l];
+      m->e2[l] = m->cycle_e2[l];
+    }
+    cycle(c, 0, true);
+    return cudaGetLastError();
+  }
+  // the capture swapped the buffers as the cycle does; the graph leaves them as at its start
+  for (int l = 0; l < m->L; ++l) {
+    m->e[l] = m->cycle_e[l];
+    m->e2[l] = m->cycle_e2[l];
+  }
+  c->launches += m->cycle_launches;
+  return cudaGraphLaunch(m->cycle_exec, c->stream);
+}
+
 // V-cycles on phi for the source in F (|F|^2 already in scal[1]) until the relative residual
 // reaches mg_tol, then (gauge) <phi> = 0.  Marks FLAG_MG_NOCONV on failure.  The solves inside
 // a step leave the gauge open: only differences of phi enter the step, and dh_get_potential
@@ -972,8 +1044,9 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
     if (!(rel == rel)) break;                 // non-finite residual
     if (cycles >= g.mg_max_cycles) break;
     prof_begin(c, DH_KERNEL_MG);
-    cycle(c, 0, true);
+    e = run_cycle(c);
     prof_end(c, 0);
+    if (e != cudaSuccess) return e;
     pending = true;   // the next residual adds e[0]
     ++cycles;
   }
