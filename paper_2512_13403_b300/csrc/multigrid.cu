@@ -195,15 +195,25 @@ __device__ __forceinline__ void block_range(long long n, long long& b0, long lon
   b1 = b0 + per < n ? b0 + per : n;
 }
 
-// out = scale * sum(partials): lane l adds entries l, l + 32, ..., then a fixed shuffle tree
-// (one warp; the order, and so the result, does not depend on scheduling)
-__global__ void finalize_kernel(const double* partials, int nb, double* out, double scale) {
-  const int l = threadIdx.x;
+// out = scale * sum(partials), launched as one block of FIN_THREADS: thread t adds entries
+// t, t + FIN_THREADS, ..., then a fixed shuffle tree per warp and a fixed sum of the warps (the
+// order, and so the result, does not depend on scheduling)
+constexpr int FIN_THREADS = 1024;
+__global__ void __launch_bounds__(FIN_THREADS)
+finalize_kernel(const double* partials, int nb, double* out, double scale) {
+  __shared__ double wsum[FIN_THREADS / 32];
+  const int t = threadIdx.x;
   double s = 0.0;
-  for (int b = l; b < nb; b += 32) s += partials[b];
+  for (int b = t; b < nb; b += FIN_THREADS) s += partials[b];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (l == 0) *out = scale * s;
+  if ((t & 31) == 0) wsum[t >> 5] = s;
+  __syncthreads();
+  if (t == 0) {
+    double a = 0.0;
+    for (int w = 0; w < FIN_THREADS / 32; ++w) a += wsum[w];
+    *out = scale * a;
+  }
 }
 
 template <typename T>
@@ -1026,7 +1036,7 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
                                                    nz, h2, ih2, m->scal + 1, m->partials);
     }
     pending = false;
-    finalize_kernel<<<1, 32, 0, s>>>(m->partials, rblocks, m->scal + 2, 1.0 / (double)n);
+    finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, rblocks, m->scal + 2, 1.0 / (double)n);
     prof_end(c, 2);
     double h[3];
     cudaError_t e = cudaMemcpyAsync(h, m->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1053,7 +1063,7 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
   if (gauge) {
     prof_begin(c, DH_KERNEL_MG);
     sum_ff_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->phi, n, m->partials);
-    finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 3, 1.0 / (double)n);
+    finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 3, 1.0 / (double)n);
     sub_mean_ff_kernel<<<grid_for(n), 256, 0, s>>>(m->phi, n, m->scal + 3);
     prof_end(c, 3);
   }
@@ -1083,10 +1093,10 @@ cudaError_t mg_solve(dh_ctx* c, const real* rho, bool in_step) {
   }
   prof_begin(c, DH_KERNEL_MG);
   sum_partial_kernel<real><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rho, n, m->partials);
-  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
+  finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
   poisson_source_kernel<real><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rho, n, m->scal + 0, g.four_pi_G,
                                                                  m->F, m->partials);
-  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
+  finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
   prof_end(c, 4);
   return mg_iterate(c, false);
 }
@@ -1100,10 +1110,10 @@ cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, float* x) {
   const long long n = m->cells[0];
   prof_begin(c, DH_KERNEL_MG);
   sum_partial_kernel<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rhs, n, m->partials);
-  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
+  finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
   poisson_source_kernel<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rhs, n, m->scal + 0, 1.0,
                                                                    m->F, m->partials);
-  finalize_kernel<<<1, 32, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
+  finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
   prof_end(c, 4);
   // x stands in for the context's potential; the fused update alternates between the two
   // buffers, so the result is copied into x if it ends in the other one
@@ -1270,7 +1280,7 @@ extern "C" dh_status dh_get_potential(dh_ctx* c, double* phi_out, int on_device,
     const long long n = m->cells[0];
     double* tmp = on_device ? phi_out : (double*)m->F;
     dh::sum_ff_kernel<<<dh::RED_BLOCKS, dh::RED_THREADS, 0, c->stream>>>(m->phi, n, m->partials);
-    dh::finalize_kernel<<<1, 32, 0, c->stream>>>(m->partials, dh::RED_BLOCKS, m->scal + 3,
+    dh::finalize_kernel<<<1, dh::FIN_THREADS, 0, c->stream>>>(m->partials, dh::RED_BLOCKS, m->scal + 3,
                                                  1.0 / (double)n);
     dh::ff_to_double_kernel<<<dh::grid_for(n), 256, 0, c->stream>>>(m->phi, n, m->scal + 3, tmp);
     cudaError_t e = cudaGetLastError();
