@@ -499,6 +499,21 @@ def poisson_variants_leg(args, stream):
             ms = sorted(times)[1]
             out["variants"][f"{smoother}-{cyc}"] = {"cycles": cycles, "relative_residual": res,
                                                     "ms_per_solve": ms, "ms_per_cycle": ms / max(cycles, 1)}
+            if smoother == "rbgs" and cyc == "V":
+                # the exact DFT solve of the same problem (float64 complex), for comparison
+                s.fft_poisson(rho)
+                torch.cuda.synchronize()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                phi_fft = s.fft_poisson(rho)
+                ev1.record(stream)
+                ev1.synchronize()
+                phi_mg, _, _ = s.potential()
+                out["fft"] = {"ms_per_solve": ev0.elapsed_time(ev1),
+                              "max_rel_diff_to_multigrid": float((phi_mg - phi_fft).abs().max()
+                                                                 / phi_fft.abs().max()),
+                              "note": "float64 complex radix-2 DFT; the multigrid stops at 1e-6"}
+                del phi_fft, phi_mg
             s.close()
             torch.cuda.empty_cache()
     return out

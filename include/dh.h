@@ -162,6 +162,17 @@ dh_status dh_downsample(const float* U_fine, int nx, int ny, int nz, int factor,
 dh_status dh_get_potential(dh_ctx* ctx, double* phi_out, int on_device, int* cycles,
                            double* rel_residual);
 
+/* The same Poisson problem solved exactly by the discrete Fourier transform (the FFT solver
+   named beside the multigrid one, Sec. 2.3 and 5): F = four_pi_G (rho - <rho>) from one density
+   plane `rho` (state index order, context precision; on_device as in dh_init_state), then
+   phi_hat = F_hat / lambda(k) with lambda(k) = -(4/h^2) sum_a sin^2(pi k_a / n_a) the
+   eigenvalues of the seven-point operator, phi_hat(0) = 0.  Float64 complex arithmetic; every
+   dimension a power of two in [2, 1024] (else DH_ERR_ARG).  phi_out: n float64 values, device
+   or host memory (out_on_device).  Needs gravity on (four_pi_G, cubic cells).  Leaves the
+   context's potential and state alone; synchronises.  A cross-check of the multigrid. */
+dh_status dh_fft_poisson(dh_ctx* ctx, const void* rho, int on_device, double* phi_out,
+                         int out_on_device);
+
 /* Sets the potential, the warm start of the next Poisson solve, to zero (the cold start of
    dh_init_state) without touching the state.  Needs gravity on.  Asynchronous on the stream. */
 dh_status dh_reset_potential(dh_ctx* ctx);

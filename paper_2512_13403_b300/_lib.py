@@ -53,6 +53,7 @@ _SIGNATURES = {
     "dh_get_potential": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "dh_solve_poisson": (C.c_int, [_P, _P, C.c_int]),
     "dh_reset_potential": (C.c_int, [_P]),
+    "dh_fft_poisson": (C.c_int, [_P, _P, C.c_int, _P, C.c_int]),
     "dh_adjoint_advance": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "dh_adjoint_advance_dt": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, _P, _P, C.c_int]),
     "dh_conserved_totals_static": (C.c_int, [_P, C.c_int, C.c_longlong, _P, _P]),

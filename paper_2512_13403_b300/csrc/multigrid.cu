@@ -1330,3 +1330,197 @@ extern "C" dh_status dh_solve_poisson(dh_ctx* c, const void* rho, int on_device)
   }
   return DH_OK;
 }
+
+// =============================================================================================
+// Exact periodic Poisson solve by the discrete Fourier transform (Sec. 2.3 and 5 name the FFT
+// solver beside the multigrid one): the DFT diagonalises the seven-point operator A, with
+// eigenvalue lambda(k) = -(4/h^2) sum_a sin^2(pi k_a / n_a), so phi_hat = F_hat / lambda for
+// k != 0 and 0 for k = 0 (<phi> = 0).  Float64 complex, power-of-two dimensions.  Each 1D
+// transform is an iterative radix-2 Cooley-Tukey pass of one CTA over one line in shared memory
+// (bit-reversed load, log2 n butterfly stages, twiddles from a per-axis table).
+namespace dh {
+
+constexpr int FFT_MAX = 1024;
+
+// F = four_pi_G (rho - <rho>) as complex float64
+template <typename T>
+__global__ void fft_load_kernel(const T* __restrict__ rho, long long n, const double* mean,
+                                double four_pi_G, double2* __restrict__ buf) {
+  const double m = *mean;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    buf[q] = make_double2(four_pi_G * ((double)rho[q] - m), 0.0);
+}
+
+// One line per CTA: lines `line` = 0 .. count-1 start at line_base(line) and step `stride`.
+// Axis layout: x lines (stride 1) are rows; y lines (stride nx) are indexed by (x, z); z lines
+// (stride nx ny) by (x, y).  tw[j] = exp(-2 pi i j / n), j < n/2; inverse uses the conjugate.
+__global__ void fft_lines_kernel(double2* __restrict__ buf, const double2* __restrict__ tw, int n,
+                                 int logn, int axis, int nx, int ny, int nz, int inverse) {
+  extern __shared__ double2 s_fft[];   // n values, then n/2 twiddles
+  double2* v = s_fft;
+  double2* w = s_fft + n;
+  const long long plane = (long long)nx * ny;
+  const long long count = axis == 0 ? (long long)ny * nz : (axis == 1 ? (long long)nx * nz : plane);
+  const long long stride = axis == 0 ? 1 : (axis == 1 ? nx : plane);
+  for (int j = threadIdx.x; j < n / 2; j += blockDim.x)
+    w[j] = inverse ? make_double2(tw[j].x, -tw[j].y) : tw[j];
+  for (long long line = blockIdx.x; line < count; line += gridDim.x) {
+    long long base;
+    if (axis == 0) base = line * nx;
+    else if (axis == 1) base = (line / nx) * plane + (line % nx);     // (x, z) -> z plane + x
+    else base = line;                                                  // (x, y) -> y row + x
+    __syncthreads();   // the previous line's values are no longer read
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int r = (int)(__brev((unsigned)i) >> (32 - logn));
+      v[r] = buf[base + (long long)i * stride];
+    }
+    __syncthreads();
+    for (int len = 2, s = 1; len <= n; len <<= 1, ++s) {
+      const int half = len >> 1, step = n >> s;   // twiddle index step for this stage
+      for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+        const int grp = b / half, k = b - grp * half;
+        const int i0 = grp * len + k, i1 = i0 + half;
+        const double2 t = w[k * step];
+        const double2 a = v[i0], c = v[i1];
+        const double2 tc = make_double2(t.x * c.x - t.y * c.y, t.x * c.y + t.y * c.x);
+        v[i0] = make_double2(a.x + tc.x, a.y + tc.y);
+        v[i1] = make_double2(a.x - tc.x, a.y - tc.y);
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) buf[base + (long long)i * stride] = v[i];
+  }
+}
+
+// phi_hat = F_hat / lambda(k), 0 at k = 0; s2x[k] = sin^2(pi k / nx) etc.
+__global__ void fft_divide_kernel(double2* __restrict__ buf, const double* __restrict__ s2x,
+                                  const double* __restrict__ s2y, const double* __restrict__ s2z,
+                                  int nx, int ny, int nz, double m4ih2) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long t = q / nx;
+    const int i = (int)(q - t * nx), j = (int)(t % ny), k = (int)(t / ny);
+    if (q == 0) {
+      buf[q] = make_double2(0.0, 0.0);
+    } else {
+      const double il = 1.0 / (m4ih2 * (s2x[i] + s2y[j] + s2z[k]));
+      buf[q] = make_double2(buf[q].x * il, buf[q].y * il);
+    }
+  }
+}
+
+__global__ void fft_store_kernel(const double2* __restrict__ buf, long long n, double scale,
+                                 double* __restrict__ phi) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    phi[q] = buf[q].x * scale;
+}
+
+}  // namespace dh
+
+namespace {
+int log2_exact(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return (1 << l) == n ? l : -1;
+}
+}  // namespace
+
+extern "C" dh_status dh_fft_poisson(dh_ctx* c, const void* rho, int on_device, double* phi_out,
+                                    int out_on_device) {
+  if (!c || !rho || !phi_out) return DH_ERR_ARG;
+  if (!c->cfg.gravity || !c->mg) { c->err = "gravity is off"; return DH_ERR_STATE; }
+  const int dims[3] = {c->cfg.nx, c->cfg.ny, c->cfg.nz};
+  int logs[3];
+  for (int a = 0; a < 3; ++a) {
+    logs[a] = log2_exact(dims[a]);
+    if (logs[a] < 1 || dims[a] > dh::FFT_MAX) {
+      c->err = "dh_fft_poisson: every dimension must be a power of two between 2 and 1024";
+      return DH_ERR_ARG;
+    }
+  }
+  MG* m = c->mg;
+  cudaStream_t s = c->stream;
+  const long long n = c->n3;
+  const size_t es = c->prec == DH_F64 ? 8 : 4;
+  // buffers: the complex field, twiddles and sin^2 tables of the three axes
+  double2* buf = nullptr;
+  double2* tw = nullptr;
+  double* s2 = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, n * sizeof(double2), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&tw, 3 * (dh::FFT_MAX / 2) * sizeof(double2), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&s2, 3 * dh::FFT_MAX * sizeof(double), s);
+  std::vector<double2> htw(3 * (dh::FFT_MAX / 2));
+  std::vector<double> hs2(3 * dh::FFT_MAX);
+  for (int a = 0; a < 3; ++a) {
+    for (int j = 0; j < dims[a] / 2; ++j) {
+      const double ang = -2.0 * M_PI * j / dims[a];
+      htw[a * (dh::FFT_MAX / 2) + j] = make_double2(std::cos(ang), std::sin(ang));
+    }
+    for (int k = 0; k < dims[a]; ++k) {
+      const double sn = std::sin(M_PI * k / dims[a]);
+      hs2[a * dh::FFT_MAX + k] = sn * sn;
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tw, htw.data(), htw.size() * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s2, hs2.data(), hs2.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  // the density in the stage scratch (free between steps), its mean, then F
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->U1, rho, (size_t)n * es,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    if (c->prec == DH_F64) {
+      dh::sum_partial_kernel<double><<<dh::RED_BLOCKS, dh::RED_THREADS, 0, s>>>((const double*)c->U1, n, m->partials);
+      dh::finalize_kernel<<<1, dh::FIN_THREADS, 0, s>>>(m->partials, dh::RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
+      dh::fft_load_kernel<double><<<dh::grid_for(n), 256, 0, s>>>((const double*)c->U1, n, m->scal + 0, c->cfg.four_pi_G, buf);
+    } else {
+      dh::sum_partial_kernel<float><<<dh::RED_BLOCKS, dh::RED_THREADS, 0, s>>>((const float*)c->U1, n, m->partials);
+      dh::finalize_kernel<<<1, dh::FIN_THREADS, 0, s>>>(m->partials, dh::RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
+      dh::fft_load_kernel<float><<<dh::grid_for(n), 256, 0, s>>>((const float*)c->U1, n, m->scal + 0, c->cfg.four_pi_G, buf);
+    }
+    e = cudaGetLastError();
+  }
+  auto pass = [&](int inverse) {
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+      const int len = dims[a];
+      const long long lines = n / len;
+      const int threads = len / 2 < 32 ? 32 : (len / 2 > 512 ? 512 : len / 2);
+      const size_t smem = (size_t)(len + len / 2) * sizeof(double2);
+      const int blocks = (int)(lines < 148LL * 16 ? lines : 148LL * 16);
+      if (smem > 48 * 1024)
+        e = cudaFuncSetAttribute(dh::fft_lines_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) break;
+      dh::fft_lines_kernel<<<blocks, threads, smem, s>>>(buf, tw + a * (dh::FFT_MAX / 2), len, logs[a], a,
+                                                         dims[0], dims[1], dims[2], inverse);
+      e = cudaGetLastError();
+    }
+  };
+  dh::prof_begin(c, DH_KERNEL_MG);
+  pass(0);
+  if (e == cudaSuccess) {
+    const double h = c->cfg.dx;
+    dh::fft_divide_kernel<<<dh::grid_for(n), 256, 0, s>>>(buf, s2, s2 + dh::FFT_MAX, s2 + 2 * dh::FFT_MAX,
+                                                          dims[0], dims[1], dims[2], -4.0 / (h * h));
+    e = cudaGetLastError();
+  }
+  pass(1);
+  // a host result is staged in the stage scratch (5 planes: at least 20 bytes per cell)
+  double* out = out_on_device ? phi_out : (double*)c->U1;
+  if (e == cudaSuccess) {
+    dh::fft_store_kernel<<<dh::grid_for(n), 256, 0, s>>>(buf, n, 1.0 / (double)n, out);
+    e = cudaGetLastError();
+  }
+  dh::prof_end(c, 11);
+  if (e == cudaSuccess && !out_on_device)
+    e = cudaMemcpyAsync(phi_out, out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(buf, s);
+  cudaFreeAsync(tw, s);
+  cudaFreeAsync(s2, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return DH_ERR_CUDA; }
+  return DH_OK;
+}

@@ -185,6 +185,17 @@ class Solver:
         self._check(self.lib.dh_get_potential(self.ctx, None, 1, C.byref(cyc), C.byref(res)))
         return cyc.value, res.value
 
+    def fft_poisson(self, rho):
+        """Exact Poisson solve by the DFT for one density plane (power-of-two grids); returns
+        phi (float64, on the device)."""
+        if not (isinstance(rho, torch.Tensor) and rho.is_cuda and rho.dtype == self.dtype
+                and tuple(rho.shape) == self.shape and rho.is_contiguous()):
+            raise ValueError("rho must be a contiguous device plane of the solver dtype")
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        self._check(self.lib.dh_fft_poisson(self.ctx, C.c_void_p(rho.data_ptr()), 1,
+                                            C.c_void_p(out.data_ptr()), 1))
+        return out
+
     def reset_potential(self):
         """Zero potential: the next solve starts cold."""
         self._check(self.lib.dh_reset_potential(self.ctx))

@@ -193,3 +193,35 @@ def test_cycle_graph_on_a_side_stream_matches_direct_launches(smoother, cycle_ty
     (a1, a2, ca1, ca2), (b1, b2, cb1, cb2) = out
     assert (ca1, ca2) == (cb1, cb2)
     assert torch.equal(a1, b1) and torch.equal(a2, b2)
+
+
+@pytest.mark.parametrize("shape,prec", [((16, 32, 64), "f64"), ((32, 32, 32), "f32"), ((16, 8, 4), "f64")])
+def test_fft_poisson_matches_oracle(shape, prec):
+    """dh_fft_poisson (exact DFT solve of the same operator) against the oracle's FFT solve."""
+    h = 1.0 / shape[2]
+    rho = inputs.lognormal_density(shape, 1.0, 4)
+    s = solver(shape, prec, gravity=True, dx=(h, h, h), four_pi_G=1.7)
+    r = to_gpu(rho[None], prec)[0].contiguous()
+    phi = s.fft_poisson(r).cpu()
+    F = omg.poisson_source(r.double().cpu(), 1.7)
+    exact = omg.fft_solve(F, h)
+    assert float((phi - exact).abs().max()) < 1e-12 * float(exact.abs().max())
+    s.close()
+
+
+def test_fft_poisson_agrees_with_multigrid_and_rejects_other_sizes():
+    from paper_2512_13403_b300._lib import DH_ERR_ARG, DhError
+    shape = (32, 32, 32)
+    rho = inputs.lognormal_density(shape, 1.0, 8)
+    s = solver(shape, "f64", gravity=True, mg_tol=1e-12, mg_max_cycles=80)
+    r = to_gpu(rho[None], "f64")[0].contiguous()
+    phi_mg, _, res = s.solve_poisson(r)
+    phi_fft = s.fft_poisson(r)
+    assert res <= 1e-12
+    assert float((phi_mg - phi_fft).abs().max()) < 1e-10 * float(phi_fft.abs().max())
+    s.close()
+    s = solver((12, 16, 16), "f64", gravity=True, dx=(1 / 16, 1 / 16, 1 / 16))
+    with pytest.raises(DhError) as e:
+        s.fft_poisson(torch.ones((12, 16, 16), dtype=torch.float64, device="cuda"))
+    assert e.value.status == DH_ERR_ARG
+    s.close()
