@@ -4,10 +4,12 @@
 //
 // stage_adjoint_kernel computes, for one RK2 stage out = alpha U0 + beta (U + dt L(U)),
 //   lam_in = c1 lam_out + c2 extra + (dL/dU)^T mu,   mu = beta dt lam_out,
-// as a gather per cell: every face VJP of HLLC o reconstruction is evaluated once per CTA tile
-// (x and y faces in shared memory, z faces in a per-thread register pipeline), the limiter's
-// transposed stencil is gathered from the neighbouring cells, and the primitive-recovery
-// Jacobian is applied last.  No atomics; each output cell is written by one thread.
+// as a gather per cell.  Per plane of a CTA tile: the limited slopes and face states of every
+// cell the tile's faces touch are computed once (x and y in shared memory, z in a per-thread
+// register pipeline); every face VJP of HLLC is evaluated once on those states; the limiter's
+// transposed stencil (slope VJPs) is evaluated once per cell and axis and gathered from the
+// neighbouring cells; the primitive-recovery Jacobian is applied last.  No atomics; each output
+// cell is written by one thread.
 //
 // Kink convention: the derivative of the branch the forward took; exact ties of min/max split
 // the derivative evenly between the tied arguments (the MC limiter and the Davis speeds).
@@ -24,18 +26,28 @@ constexpr int ABX = 32, ABY = 8;
 constexpr int ANT = ABX * ABY;
 constexpr int WX = ABX + 6, WY = ABY + 6;   // primitive planes, halo 3
 constexpr int MXH = ABX + 4, MYH = ABY + 4; // mu plane, halo 2
+constexpr int NSXA = ABX + 4;               // x slopes per row: cells -2 .. BX+1
+constexpr int NSYA = ABY + 4;               // y slopes per column: cells -2 .. BY+1
 constexpr int NFXA = ABX + 3;               // x faces per row: -3/2 .. BX+1/2
 constexpr int NFYA = ABY + 3;               // y faces per column
 constexpr int NCXA = ABX + 2;               // x cells per row for the slope terms: -1 .. BX
 constexpr int NCYA = ABY + 2;
+constexpr int NSX = NSXA * ABY, NSY = NSYA * ABX;   // x and y slopes of a plane tile
 constexpr int NFX = NFXA * ABY, NFY = NFYA * ABX;   // x and y faces of a plane tile
 constexpr int NCX = NCXA * ABY, NCY = NCYA * ABX;   // cells with x and y slope terms
+// the y items of each per-plane loop start on a warp boundary, so no warp takes both branches
+constexpr int warp_up(int n) { return (n + 31) / 32 * 32; }
+constexpr int NSXP = warp_up(NSX), NFXP = warp_up(NFX), NCXP = warp_up(NCX);
 
 template <typename real> struct AdjSmem {
   real w[4][5][WY][WX];
   real mu[5][MYH][MXH];
-  real face[10][NFX + NFY];    // (gL[5], gR[5]) per face: x faces, then y faces
-  real cell[10][NCX + NCY];    // (A[5], B[5]) per cell: x terms, then y terms
+  real face[10][NFXP + NFY];      // (gL[5], gR[5]) per face: x faces, then y faces
+  union {
+    real st[10][NSXP + NSY];      // (W - dW/2, W + dW/2) per cell and axis: x, then y
+    real cell[10][NCXP + NCY];    // (A[5], B[5]) per cell: x terms, then y terms
+  } u;
+  unsigned char zero[NSXP + NSY]; // the cell's limited slope along the axis is all zero
   int xs[WX], ys[WY];
 };
 
@@ -43,6 +55,12 @@ template <typename real>
 __device__ __forceinline__ Prim<real> ring_prim(const AdjSmem<real>& S, int slot, int sy, int sx) {
   return Prim<real>{S.w[slot][0][sy][sx], S.w[slot][1][sy][sx], S.w[slot][2][sy][sx],
                     S.w[slot][3][sy][sx], S.w[slot][4][sy][sx]};
+}
+
+template <typename real>
+__device__ __forceinline__ Prim<real> st_prim(const AdjSmem<real>& S, int half, int i) {
+  return Prim<real>{S.u.st[half][i], S.u.st[half + 1][i], S.u.st[half + 2][i],
+                    S.u.st[half + 3][i], S.u.st[half + 4][i]};
 }
 
 template <typename real>
@@ -119,26 +137,34 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
   gload5(p.lam_out, n3, (long long)wrap(z0 + 1, nz) * plane + col, sdt, mun);
   __syncthreads();
 
+  // z pipeline of the own column at the top of iteration k: the limited slope dz1 of cell k+1,
+  // the face gradients gLn, gRn of face k+1/2 and gRc of face k-1/2, and the slope terms
+  // A_{k-1}, A_k, B_k.
   real gLn[5], gRc[5], gRn[5], Ap[5], Ac[5], Bc[5];
+  Prim<real> dz1;
   {
     const Prim<real> w0 = ring_prim(S, 0, ty + 3, tx + 3);
     const Prim<real> w1 = ring_prim(S, 1, ty + 3, tx + 3);
     const Prim<real> w2 = ring_prim(S, 2, ty + 3, tx + 3);
+    const Prim<real> dm2 = limited_slope<LIM>(wm3, wm2, wm1);
+    const Prim<real> dm1 = limited_slope<LIM>(wm2, wm1, w0);
+    const Prim<real> d0 = limited_slope<LIM>(wm1, w0, w1);
+    dz1 = limited_slope<LIM>(w0, w1, w2);
     real g[5], gLa[5], gRa[5], gLb[5], gRb[5], D[5], Bt[5];
     // face z0-3/2
     for (int c = 0; c < 5; ++c) g[c] = (mum1[c] - mum2[c]) * p.idz;
-    face_vjp<LIM>(2, wm3, wm2, wm1, w0, g, gamma, gm1, gLa, gRa);
+    face_vjp(2, add_half(wm2, dm2, real(1)), add_half(wm1, dm1, real(-1)), g, gamma, gm1, gLa, gRa);
     // face z0-1/2
     for (int c = 0; c < 5; ++c) g[c] = (mu0[c] - mum1[c]) * p.idz;
-    face_vjp<LIM>(2, wm2, wm1, w0, w1, g, gamma, gm1, gLb, gRb);
+    face_vjp(2, add_half(wm1, dm1, real(1)), add_half(w0, d0, real(-1)), g, gamma, gm1, gLb, gRb);
     // A_{z0-1} from D = gL(z0-1/2)/2 - gR(z0-3/2)/2
     for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gLb[c] - real(0.5) * gRa[c];
-    slope_vjp<LIM>(wm2, wm1, w0, D, Ap, Bt);
+    slope_vjp<LIM>(wm2, wm1, w0, slope_is_zero(dm1), D, Ap, Bt);
     // face z0+1/2
     for (int c = 0; c < 5; ++c) g[c] = (mun[c] - mu0[c]) * p.idz;
-    face_vjp<LIM>(2, wm1, w0, w1, w2, g, gamma, gm1, gLn, gRn);
+    face_vjp(2, add_half(w0, d0, real(1)), add_half(w1, dz1, real(-1)), g, gamma, gm1, gLn, gRn);
     for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gLn[c] - real(0.5) * gRb[c];
-    slope_vjp<LIM>(wm1, w0, w1, D, Ac, Bc);
+    slope_vjp<LIM>(wm1, w0, w1, slope_is_zero(d0), D, Ac, Bc);
     for (int c = 0; c < 5; ++c) gRc[c] = gRb[c];
   }
 
@@ -148,20 +174,22 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
     load_mu(k);
     real mun2[5];
     gload5(p.lam_out, n3, (long long)wrap(k + 2, nz) * plane + col, sdt, mun2);
-    __syncthreads();
+    __syncthreads();  // ---- plane k+3 and mu of plane k in shared memory
 
     real gW[5];
-    // ---- z: face k+3/2, slope terms of k+1, gather for k ------------------------------------
+    Prim<real> wk;   // own cell of plane k, kept for the primitive-recovery step
+    // ---- z: slope of k+2, face k+3/2, slope terms of k+1, gather for k ------------------------
     {
-      const Prim<real> w0 = ring_prim(S, s0, ty + 3, tx + 3);
+      wk = ring_prim(S, s0, ty + 3, tx + 3);
       const Prim<real> w1 = ring_prim(S, s1, ty + 3, tx + 3);
       const Prim<real> w2 = ring_prim(S, s2, ty + 3, tx + 3);
       const Prim<real> w3 = ring_prim(S, s3, ty + 3, tx + 3);
+      const Prim<real> dz2 = limited_slope<LIM>(w1, w2, w3);
       real g[5], gL2[5], gR2[5], D[5], An[5], Bn[5];
       for (int c = 0; c < 5; ++c) g[c] = (mun2[c] - mun[c]) * p.idz;
-      face_vjp<LIM>(2, w0, w1, w2, w3, g, gamma, gm1, gL2, gR2);
+      face_vjp(2, add_half(w1, dz1, real(1)), add_half(w2, dz2, real(-1)), g, gamma, gm1, gL2, gR2);
       for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gL2[c] - real(0.5) * gRn[c];
-      slope_vjp<LIM>(w0, w1, w2, D, An, Bn);
+      slope_vjp<LIM>(wk, w1, w2, slope_is_zero(dz1), D, An, Bn);
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         gW[c] = (gLn[c] + gRc[c]) + Ap[c] - Ac[c] + Bc[c] - Bn[c];
@@ -173,71 +201,101 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
         Bc[c] = Bn[c];
         mun[c] = mun2[c];
       }
+      dz1 = dz2;
     }
 
-    // ---- x and y faces of plane k (one linear loop), then their slope terms, then the gather
-    for (int f = tid; f < NFX + NFY; f += ANT) {
+    // ---- limited slopes and face states of plane k along x and y, once per cell and axis -------
+    for (int t = tid; t < NSXP + NSY; t += ANT) {
+      Prim<real> wm, w0, wp;
+      if (t < NSXP) {
+        if (t >= NSX) continue;
+        const int ly = t / NSXA, r = t - ly * NSXA;          // cell lx = r - 2
+        wm = ring_prim(S, s0, ly + 3, r);
+        w0 = ring_prim(S, s0, ly + 3, r + 1);
+        wp = ring_prim(S, s0, ly + 3, r + 2);
+      } else {
+        const int u = t - NSXP;
+        const int r = u / ABX, lx = u - r * ABX;             // cell ly = r - 2
+        wm = ring_prim(S, s0, r, lx + 3);
+        w0 = ring_prim(S, s0, r + 1, lx + 3);
+        wp = ring_prim(S, s0, r + 2, lx + 3);
+      }
+      const Prim<real> d = limited_slope<LIM>(wm, w0, wp);
+      const Prim<real> lo = add_half(w0, d, real(-1)), hi = add_half(w0, d, real(1));
+      S.u.st[0][t] = lo.r; S.u.st[1][t] = lo.vx; S.u.st[2][t] = lo.vy; S.u.st[3][t] = lo.vz;
+      S.u.st[4][t] = lo.p;
+      S.u.st[5][t] = hi.r; S.u.st[6][t] = hi.vx; S.u.st[7][t] = hi.vy; S.u.st[8][t] = hi.vz;
+      S.u.st[9][t] = hi.p;
+      S.zero[t] = slope_is_zero(d) ? 1 : 0;
+    }
+    __syncthreads();  // ---- face states ready
+
+    // ---- x and y face VJPs of plane k ------------------------------------------------------------
+    for (int f = tid; f < NFXP + NFY; f += ANT) {
       real g[5], gL[5], gR[5];
-      if (f < NFX) {
-        const int ly = f / NFXA, q = f - ly * NFXA;
-        const int sy = ly + 3;
+      if (f < NFXP) {
+        if (f >= NFX) continue;
+        const int ly = f / NFXA, q = f - ly * NFXA;   // between cells lx = q-2 and q-1
 #pragma unroll
         for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][ly + 2][q + 1] - S.mu[c][ly + 2][q]) * p.idx;
-        face_vjp<LIM>(0, ring_prim(S, s0, sy, q), ring_prim(S, s0, sy, q + 1), ring_prim(S, s0, sy, q + 2),
-                 ring_prim(S, s0, sy, q + 3), g, gamma, gm1, gL, gR);
+        const int i = ly * NSXA + q;
+        face_vjp(0, st_prim(S, 5, i), st_prim(S, 0, i + 1), g, gamma, gm1, gL, gR);
       } else {
-        const int fy = f - NFX;
-        const int q = fy / ABX, lx = fy - q * ABX;
-        const int sx = lx + 3;
+        const int fy = f - NFXP;
+        const int q = fy / ABX, lx = fy - q * ABX;    // between cells ly = q-2 and q-1
 #pragma unroll
         for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][q + 1][lx + 2] - S.mu[c][q][lx + 2]) * p.idy;
-        face_vjp<LIM>(1, ring_prim(S, s0, q, sx), ring_prim(S, s0, q + 1, sx), ring_prim(S, s0, q + 2, sx),
-                 ring_prim(S, s0, q + 3, sx), g, gamma, gm1, gL, gR);
+        const int i = NSXP + q * ABX + lx;
+        face_vjp(1, st_prim(S, 5, i), st_prim(S, 0, i + ABX), g, gamma, gm1, gL, gR);
       }
 #pragma unroll
       for (int c = 0; c < 5; ++c) { S.face[c][f] = gL[c]; S.face[5 + c][f] = gR[c]; }
     }
-    __syncthreads();
-    for (int e = tid; e < NCX + NCY; e += ANT) {
+    __syncthreads();  // ---- face gradients ready; the face states are dead from here
+
+    // ---- slope terms (A, B) of the x and y slopes; they overwrite the face states --------------
+    for (int e = tid; e < NCXP + NCY; e += ANT) {
       real D[5], A[5], B[5];
-      if (e < NCX) {
-        const int ly = e / NCXA, r = e - ly * NCXA;
+      if (e < NCXP) {
+        if (e >= NCX) continue;
+        const int ly = e / NCXA, r = e - ly * NCXA;   // cell lx = r - 1
         const int sy = ly + 3;
 #pragma unroll
         for (int c = 0; c < 5; ++c)
           D[c] = real(0.5) * S.face[c][ly * NFXA + r + 1] - real(0.5) * S.face[5 + c][ly * NFXA + r];
         slope_vjp<LIM>(ring_prim(S, s0, sy, r + 1), ring_prim(S, s0, sy, r + 2),
-                  ring_prim(S, s0, sy, r + 3), D, A, B);
+                       ring_prim(S, s0, sy, r + 3), S.zero[ly * NSXA + r + 1] != 0, D, A, B);
       } else {
-        const int ey = e - NCX;
-        const int r = ey / ABX, lx = ey - r * ABX;
+        const int ey = e - NCXP;
+        const int r = ey / ABX, lx = ey - r * ABX;    // cell ly = r - 1
         const int sx = lx + 3;
 #pragma unroll
         for (int c = 0; c < 5; ++c)
-          D[c] = real(0.5) * S.face[c][NFX + (r + 1) * ABX + lx] -
-                 real(0.5) * S.face[5 + c][NFX + r * ABX + lx];
+          D[c] = real(0.5) * S.face[c][NFXP + (r + 1) * ABX + lx] -
+                 real(0.5) * S.face[5 + c][NFXP + r * ABX + lx];
         slope_vjp<LIM>(ring_prim(S, s0, r + 1, sx), ring_prim(S, s0, r + 2, sx),
-                  ring_prim(S, s0, r + 3, sx), D, A, B);
+                       ring_prim(S, s0, r + 3, sx), S.zero[NSXP + (r + 1) * ABX + lx] != 0, D, A, B);
       }
 #pragma unroll
-      for (int c = 0; c < 5; ++c) { S.cell[c][e] = A[c]; S.cell[5 + c][e] = B[c]; }
+      for (int c = 0; c < 5; ++c) { S.u.cell[c][e] = A[c]; S.u.cell[5 + c][e] = B[c]; }
     }
-    __syncthreads();
+    __syncthreads();  // ---- slope terms ready
     {
       const int fb = ty * NFXA, cb = ty * NCXA;
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        gW[c] += (S.face[c][fb + tx + 2] + S.face[5 + c][fb + tx + 1]) + S.cell[c][cb + tx] -
-                 S.cell[c][cb + tx + 1] + S.cell[5 + c][cb + tx + 1] - S.cell[5 + c][cb + tx + 2];
-        gW[c] += (S.face[c][NFX + (ty + 2) * ABX + tx] + S.face[5 + c][NFX + (ty + 1) * ABX + tx]) +
-                 S.cell[c][NCX + ty * ABX + tx] - S.cell[c][NCX + (ty + 1) * ABX + tx] +
-                 S.cell[5 + c][NCX + (ty + 1) * ABX + tx] - S.cell[5 + c][NCX + (ty + 2) * ABX + tx];
+        gW[c] += (S.face[c][fb + tx + 2] + S.face[5 + c][fb + tx + 1]) + S.u.cell[c][cb + tx] -
+                 S.u.cell[c][cb + tx + 1] + S.u.cell[5 + c][cb + tx + 1] - S.u.cell[5 + c][cb + tx + 2];
+        gW[c] += (S.face[c][NFXP + (ty + 2) * ABX + tx] + S.face[5 + c][NFXP + (ty + 1) * ABX + tx]) +
+                 S.u.cell[c][NCXP + ty * ABX + tx] - S.u.cell[c][NCXP + (ty + 1) * ABX + tx] +
+                 S.u.cell[5 + c][NCXP + (ty + 1) * ABX + tx] - S.u.cell[5 + c][NCXP + (ty + 2) * ABX + tx];
       }
     }
 
     // ---- primitive recovery transposed, stage combination, store ------------------------------
+    // (from registers only: the next plane's loads may already overwrite the ring slot of k)
     if (active) {
-      const Prim<real> w = ring_prim(S, s0, ty + 3, tx + 3);
+      const Prim<real> w = wk;
       const real ir = q_div(real(1), w.r);
       const real v2 = w.vx * w.vx + w.vy * w.vy + w.vz * w.vz;
       real gU[5];
@@ -255,7 +313,6 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
         p.lam_in[c * n3 + idx] = v;
       }
     }
-    __syncthreads();
   }
 }
 

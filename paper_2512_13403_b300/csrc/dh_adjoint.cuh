@@ -1,31 +1,28 @@
-// Per-face reverse-mode building blocks of the hand adjoint: the MC and van Leer slopes, the limited slope
-// with its positivity fallback, HLLC and the face VJP of reconstruction o HLLC (App. A.1-A.2
-// transposed).  Host and device: the same code is checked on the CPU against finite
-// differences of the forward face flux.
+// Per-face reverse-mode building blocks of the hand adjoint: the MC and van Leer slopes, the
+// limited slope with its positivity fallback, HLLC and the face VJP of HLLC on reconstructed
+// states (App. A.1-A.2 transposed).  Host and device code; the GPU kernels that use them are
+// checked against reverse-mode differentiation of the oracle step and against finite
+// differences.
 #pragma once
 #include "dh_device.cuh"
 
 namespace dh {
 
-// Reverse of mc_slope for one component: D = dL/d(slope) -> (dL/da, dL/db).
+// Reverse of mc_slope for one component: D = dL/d(slope) -> (dL/da, dL/db).  Where a b > 0 the
+// slope is sign(a) min(2|a|, 2|b|, |a+b|/2); its three branches have the derivatives (2, 0),
+// (0, 2) and (1/2, 1/2) in (a, b), and a tie splits the derivative evenly between the tied
+// branches.  Branch-free: the branch weights are 0, 1/2 or 1.
 template <typename real>
 __host__ __device__ __forceinline__ void mc_slope_vjp(real a, real b, real D, real& ga, real& gb) {
-  ga = real(0);
-  gb = real(0);
-  if (!(a * b > real(0))) return;
   const real X = real(2) * fabs(a), Y = real(2) * fabs(b), Z = real(0.5) * fabs(a + b);
   const real m1 = fmin(X, Y);
-  const real mg = D * copysign(real(1), a);  // d(sign(a) m)/dm
-  real m1g, Zg;
-  if (m1 < Z) { m1g = mg; Zg = real(0); }
-  else if (Z < m1) { m1g = real(0); Zg = mg; }
-  else { m1g = real(0.5) * mg; Zg = real(0.5) * mg; }
-  real Xg, Yg;
-  if (X < Y) { Xg = m1g; Yg = real(0); }
-  else if (Y < X) { Xg = real(0); Yg = m1g; }
-  else { Xg = real(0.5) * m1g; Yg = real(0.5) * m1g; }
-  ga = real(2) * copysign(real(1), a) * Xg + real(0.5) * copysign(real(1), a + b) * Zg;
-  gb = real(2) * copysign(real(1), b) * Yg + real(0.5) * copysign(real(1), a + b) * Zg;
+  const real wm = m1 < Z ? real(1) : (m1 == Z ? real(0.5) : real(0));   // weight of min(X, Y)
+  const real wx = X < Y ? real(1) : (X == Y ? real(0.5) : real(0));     // share of X in it
+  const real t = (a * b > real(0)) ? D : real(0);
+  const real tm = real(2) * wm * t;
+  const real tz = real(0.5) * (real(1) - wm) * t;
+  ga = tm * wx + tz;
+  gb = tm * (real(1) - wx) + tz;
 }
 
 // Reverse of vl_slope: d/da 2ab/(a+b) = 2b^2/(a+b)^2, d/db = 2a^2/(a+b)^2 where a*b > 0, else 0.
@@ -46,21 +43,21 @@ __host__ __device__ __forceinline__ void lim_slope_vjp(real a, real b, real D, r
   else mc_slope_vjp(a, b, D, ga, gb);
 }
 
-// A_i = dL/da_i, B_i = dL/db_i of a cell from D = dL/d(dW_i); zero when the positivity fallback
-// zeroed the cell's slopes.
+// True when every component of a limited slope is zero.  The positivity fallback zeroes all
+// of them; otherwise a zero component has a b <= 0 and a zero derivative, so "all zero" selects
+// exactly the cells whose slope derivative vanishes as a whole.
+template <typename real>
+__host__ __device__ __forceinline__ bool slope_is_zero(const Prim<real>& d) {
+  return d.r == real(0) && d.vx == real(0) && d.vy == real(0) && d.vz == real(0) && d.p == real(0);
+}
+
+// A_i = dL/da_i, B_i = dL/db_i of a cell (a = w_{+1} - w_0, b = w_0 - w_{-1}) from
+// D = dL/d(dW_i), given whether the forward's limited slope of the cell was all zero.
 template <int LIM = LIM_MC, typename real>
 __host__ __device__ __forceinline__ void slope_vjp(const Prim<real>& wm, const Prim<real>& w0,
-                                          const Prim<real>& wp, const real D[5], real A[5],
-                                          real B[5]) {
-  const Prim<real> d = limited_slope<LIM>(wm, w0, wp);
-  const bool zeroed = (d.r == real(0) && d.vx == real(0) && d.vy == real(0) && d.vz == real(0) &&
-                       d.p == real(0));
-  // recompute the unguarded slopes to tell the fallback apart from slopes that are all zero
-  const real hr = real(0.5) * lim_slope<LIM>(wp.r - w0.r, w0.r - wm.r);
-  const real hp = real(0.5) * lim_slope<LIM>(wp.p - w0.p, w0.p - wm.p);
-  const bool fallback = zeroed && ((w0.r + hr <= real(0)) || (w0.p + hp <= real(0)) ||
-                                   (w0.r - hr <= real(0)) || (w0.p - hp <= real(0)));
-  if (fallback) {
+                                                   const Prim<real>& wp, bool zero, const real D[5],
+                                                   real A[5], real B[5]) {
+  if (zero) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) { A[c] = real(0); B[c] = real(0); }
     return;
@@ -188,16 +185,13 @@ __host__ __device__ __forceinline__ void hllc_vjp(real rL, real uL, real aL, rea
   gR[0] = rR_; gR[1] = uR_; gR[2] = aR_; gR[3] = bR_; gR[4] = pR_;
 }
 
-// Face VJP along `axis` from the four primitive cells around the face and the flux gradient
-// g[5] in (rho, m_x, m_y, m_z, E) order; returns gradients of the two reconstructed states in
-// (rho, v_x, v_y, v_z, P) order.
-template <int LIM = LIM_MC, typename real>
-__host__ __device__ __forceinline__ void face_vjp(int axis, const Prim<real>& w0, const Prim<real>& w1,
-                                         const Prim<real>& w2, const Prim<real>& w3,
-                                         const real g[5], real gamma, real gm1, real gL[5],
-                                         real gR[5]) {
-  const Prim<real> L = add_half(w1, limited_slope<LIM>(w0, w1, w2), real(1));
-  const Prim<real> R = add_half(w2, limited_slope<LIM>(w1, w2, w3), real(-1));
+// Face VJP along `axis` from the reconstructed states L (upper face state of the lower cell) and
+// R, and the flux gradient g[5] in (rho, m_x, m_y, m_z, E) order; returns gradients of the two
+// states in (rho, v_x, v_y, v_z, P) order.
+template <typename real>
+__host__ __device__ __forceinline__ void face_vjp(int axis, const Prim<real>& L, const Prim<real>& R,
+                                                  const real g[5], real gamma, real gm1, real gL[5],
+                                                  real gR[5]) {
   real fL[5], fR[5];
   if (axis == 0) {
     hllc_vjp(L.r, L.vx, L.vy, L.vz, L.p, R.r, R.vx, R.vy, R.vz, R.p, gamma, gm1, g[0], g[1], g[2],
