@@ -336,7 +336,7 @@ def _adjoint_run(cfg, U0, steps, k, stream, lam_scale):
         lam = torch.zeros_like(U0)
         lam[0] = lam_scale  # gradient of a mean-squared density misfit (scale only)
         s.init_state(U0)
-        s.adjoint_advance(2, 1, lam)  # warm-up: allocations and first launches
+        s.adjoint_advance(steps, k, lam)  # warm-up: the same call allocates its buffers once
         s.init_state(U0)
         s.profile(True)
         torch.cuda.synchronize()

@@ -316,29 +316,26 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
   }
 }
 
-static int adj_zchunk(int nx, int ny, int nz) {
-  const long long tiles = (long long)((nx + ABX - 1) / ABX) * ((ny + ABY - 1) / ABY);
-  int chunks = (int)((148LL * 4 + tiles - 1) / tiles);
-  if (chunks < 1) chunks = 1;
-  int zc = (nz + chunks - 1) / chunks;
-  if (zc < 8) zc = 8;
-  if (zc > nz) zc = nz;
-  return zc;
-}
-
 template <typename real>
 cudaError_t launch_stage_adjoint(const AdjointArgs<real>& a, cudaStream_t s) {
-  const int zc = adj_zchunk(a.nx, a.ny, a.nz);
-  dim3 grid((a.nx + ABX - 1) / ABX, (a.ny + ABY - 1) / ABY, (a.nz + zc - 1) / zc);
   const size_t smem = sizeof(AdjSmem<real>);
-  auto run = [&](auto kernel) {
+  auto run = [&](auto kernel, int& resident) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (resident <= 0) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kernel, ANT, smem);
+      if (e != cudaSuccess) return e;
+      if (resident <= 0) resident = 1;
+    }
+    const long long tiles = (long long)((a.nx + ABX - 1) / ABX) * ((a.ny + ABY - 1) / ABY);
+    const int zc = wave_zchunk(tiles, a.nz, resident, 1.0);
+    dim3 grid((a.nx + ABX - 1) / ABX, (a.ny + ABY - 1) / ABY, (a.nz + zc - 1) / zc);
     kernel<<<grid, ANT, smem, s>>>(a, zc);
     return cudaGetLastError();
   };
-  return a.limiter == LIM_VL ? run(stage_adjoint_kernel<real, LIM_VL>)
-                             : run(stage_adjoint_kernel<real, LIM_MC>);
+  static int res_vl = 0, res_mc = 0;   // CTAs per SM of each instance
+  return a.limiter == LIM_VL ? run(stage_adjoint_kernel<real, LIM_VL>, res_vl)
+                             : run(stage_adjoint_kernel<real, LIM_MC>, res_mc);
 }
 template cudaError_t launch_stage_adjoint<float>(const AdjointArgs<float>&, cudaStream_t);
 template cudaError_t launch_stage_adjoint<double>(const AdjointArgs<double>&, cudaStream_t);
@@ -615,7 +612,7 @@ static cudaError_t adjoint_stage(dh_ctx* c, const void* U, const void* lam_out, 
 }
 
 template <typename real>
-static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev) {
+static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev, bool last_kept) {
   AdjointSpace* a = c->adj;
   cudaError_t e;
   void* lam = a->lam[0];
@@ -640,7 +637,9 @@ static cudaError_t adjoint_backward(dh_ctx* c, int n, int k, void* lam_final_dev
     }
     // final-stage weights: RK2 (1/2, 1/2); SSPRK3 (1/3, 2/3) after the middle stage (3/4, 1/4)
     const real fw0 = a->rk3 ? real(1.0 / 3.0) : real(0.5), fw1 = a->rk3 ? real(2.0 / 3.0) : real(0.5);
-    for (int j = 0; j < len; ++j) {
+    // the last segment was kept by the forward sweep
+    const bool kept = last_kept && m0 + k >= n;
+    for (int j = 0; j < len && !kept; ++j) {
       const double* dtp = a->dts + m0 + j;
       e = replay_stage<real>(c, 1, in(j), nullptr, a->seg1[j], dtp, real(1), real(1), false);
       if (e != cudaSuccess) return e;
@@ -754,7 +753,11 @@ extern "C" dh_status dh_adjoint_advance_dt(dh_ctx* c, int n, int k, double dt,
   cudaError_t e = adjoint_reserve(c, n, k);
   if (e != cudaSuccess) { c->err = std::string("adjoint allocation: ") + cudaGetErrorString(e); return DH_ERR_CUDA; }
   AdjointSpace* a = c->adj;
-  // forward sweep with checkpoints; the dt of every step is recorded on the device
+  // forward sweep with checkpoints; the dt of every step is recorded on the device.  Without
+  // gravity the steps of the last segment also keep their inputs and intermediate states (the
+  // segment buffers the backward sweep would otherwise fill by replaying them).
+  const bool keep_last = !a->gravity;
+  const int m_last = (n - 1) / k * k;
   for (int m = 0; m < n && e == cudaSuccess; ++m) {
     if (m % k == 0) {
       e = cudaMemcpyAsync(a->ckpt[m / k], c->U[c->cur], c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -762,7 +765,20 @@ extern "C" dh_status dh_adjoint_advance_dt(dh_ctx* c, int n, int k, double dt,
         e = cudaMemcpyAsync(a->ckPhi[m / k], mg_phi(c), (size_t)c->n3 * sizeof(double),
                             cudaMemcpyDeviceToDevice, c->stream);
     }
-    if (e == cudaSuccess) e = c->prec == DH_F64 ? dh_enqueue_step_f64(c, dt) : dh_enqueue_step_f32(c, dt);
+    StepCapture cap;
+    const bool keep = keep_last && m >= m_last;
+    if (keep) {
+      const int j = m - m_last;
+      if (j > 0 && e == cudaSuccess)
+        e = cudaMemcpyAsync(a->seg[j - 1], c->U[c->cur], c->state_bytes, cudaMemcpyDeviceToDevice,
+                            c->stream);
+      cap.u1 = a->seg1[j];
+      cap.u2 = a->rk3 ? a->seg2[j] : nullptr;
+      cap.pre_src = a->sources ? a->segH[j] : nullptr;
+    }
+    if (e == cudaSuccess)
+      e = c->prec == DH_F64 ? dh_enqueue_step_f64(c, dt, keep ? &cap : nullptr)
+                            : dh_enqueue_step_f32(c, dt, keep ? &cap : nullptr);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(a->dts + m, &c->rec->dt, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess && c->cfg.forcing) {
@@ -783,8 +799,8 @@ extern "C" dh_status dh_adjoint_advance_dt(dh_ctx* c, int n, int k, double dt,
   // backward sweep
   if (e == cudaSuccess) e = cudaMemcpyAsync(a->lam[1], dLdU_final, c->state_bytes, h2d, c->stream);
   if (e == cudaSuccess)
-    e = c->prec == DH_F64 ? adjoint_backward<double>(c, n, k, a->lam[1])
-                          : adjoint_backward<float>(c, n, k, a->lam[1]);
+    e = c->prec == DH_F64 ? adjoint_backward<double>(c, n, k, a->lam[1], keep_last)
+                          : adjoint_backward<float>(c, n, k, a->lam[1], keep_last);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dLdU0, a->lam[0], c->state_bytes, d2h, c->stream);
   if (e == cudaSuccess && a->gravity)
     e = cudaMemcpyAsync(mg_phi(c), a->phi_keep, pb, cudaMemcpyDeviceToDevice, c->stream);

@@ -185,6 +185,138 @@ __host__ __device__ __forceinline__ void hllc_vjp(real rL, real uL, real aL, rea
   gR[0] = rR_; gR[1] = uR_; gR[2] = aR_; gR[3] = bR_; gR[4] = pR_;
 }
 
+#if defined(__CUDA_ARCH__)
+// hllc_vjp for float32 with the left and right sides in the two lanes of packed operations.  The
+// forward quantities are recomputed as hllc_packed computes them (c = gamma p / sqrt(gamma p
+// rho), one reciprocal for S*), so the region taken is the forward kernel's.  With
+// s = 1/sqrt(gamma p rho): dc/dp = gamma s / 2 and dc/drho = -c^2 s / 2.
+__device__ __forceinline__ void hllc_vjp_packed(float rL, float uL, float aL, float bL, float pL,
+                                                float rR, float uR, float aR, float bR, float pR,
+                                                float gamma, float gm1, float g0, float gn,
+                                                float gt1, float gt2, float ge, float gL[5],
+                                                float gR[5]) {
+  const float2 r = f2(rL, rR), u = f2(uL, uR), pp = f2(pL, pR);
+  const float2 gp = p_mul(pp, f2s(gamma));
+  const float2 gpr = p_mul(gp, r);
+  const float2 rs = f2(gpr.x > 0.0f ? rsqrtf(gpr.x) : 0.0f, gpr.y > 0.0f ? rsqrtf(gpr.y) : 0.0f);
+  const float2 c = p_mul(gp, rs);
+  const float2 um = p_sub(u, c), upc = p_add(u, c);
+  const float SL = fminf(um.x, um.y), SR = fmaxf(upc.x, upc.y);
+  const float2 d = p_sub(f2(SL, SR), u);
+  const float2 rd = p_mul(r, d);
+  const float2 t = p_sub(p_mul(rd, u), pp);
+  const float Ss = q_div(t.x - t.y, rd.x - rd.y);
+  const bool left = (SL >= 0.0f) || (Ss >= 0.0f);
+  const bool star = !(SL >= 0.0f) && (Ss >= 0.0f || SR > 0.0f);
+  const float rk = left ? rL : rR, uk = left ? uL : uR, ak = left ? aL : aR, bk = left ? bL : bR;
+  const float pk = left ? pL : pR, S = left ? SL : SR, dk = left ? d.x : d.y;
+  const float igm1 = 1.0f / gm1;   // uniform: hoisted out of the face loops
+  const float2 ua2 = p_mul(f2(uk, ak), f2(uk, ak));
+  const float q2 = ua2.x + ua2.y + bk * bk;
+  const float E = pk * igm1 + 0.5f * rk * q2;
+  const float mass = rk * uk;
+
+  float mass_ = g0 + gn * uk + gt1 * ak + gt2 * bk;
+  float u_ = gn * mass + ge * (E + pk);
+  float2 ab_ = p_mul(f2(gt1, gt2), f2s(mass));
+  float p_ = gn + ge * uk;
+  float E_ = ge * uk;
+  float r_ = 0.0f, S_ = 0.0f, Ss_ = 0.0f, d_ = 0.0f;
+  if (star) {
+    const float ir = q_div(1.0f, rk);
+    const float rdk = rk * dk;
+    const float ird = q_div(1.0f, rdk);
+    const float iden2 = q_div(1.0f, S - Ss);
+    const float coef = rdk * iden2;
+    const float w = pk * ird;
+    const float sdu = Ss - uk;
+    const float Z = Ss + w;
+    const float Q = E * ir + sdu * Z;
+    const float Es = coef * Q;
+    const float cr = coef - rk;
+    const float G = g0 + gt1 * ak + gt2 * bk;
+    S_ = G * cr + gn * (coef * Ss - mass) + ge * (Es - E);
+    float coef_ = S * (G + gn * Ss);
+    Ss_ = S * gn * coef;
+    r_ = -S * G;
+    mass_ -= S * gn;
+    ab_ = p_fma(f2(gt1, gt2), f2s(S * cr), ab_);
+    const float Es_ = S * ge;
+    E_ -= Es_;
+    coef_ += Es_ * Q;
+    const float Q_ = Es_ * coef;
+    E_ += Q_ * ir;
+    r_ -= Q_ * E * ir * ir;
+    Ss_ += Q_ * (Z + sdu);
+    u_ -= Q_ * Z;
+    const float w_ = Q_ * sdu;
+    p_ += w_ * ird;
+    r_ -= w_ * w * ir;
+    d_ = -(w_ * w * rk * ird);
+    r_ += coef_ * dk * iden2;
+    d_ += coef_ * rk * iden2;
+    const float dc = coef_ * coef * iden2;
+    S_ -= dc;
+    Ss_ += dc;
+  }
+  p_ += E_ * igm1;
+  r_ += E_ * 0.5f * q2;
+  const float Er = E_ * rk;
+  u_ += Er * uk;
+  ab_ = p_fma(f2s(Er), f2(ak, bk), ab_);
+  r_ += mass_ * uk;
+  u_ += mass_ * rk;
+  S_ += d_;
+  u_ -= d_;
+
+  float2 rP = left ? f2(r_, 0.0f) : f2(0.0f, r_);
+  float2 uP = left ? f2(u_, 0.0f) : f2(0.0f, u_);
+  float2 pP = left ? f2(p_, 0.0f) : f2(0.0f, p_);
+  float2 SP = left ? f2(S_, 0.0f) : f2(0.0f, S_);
+  const float2 aP = left ? f2(ab_.x, 0.0f) : f2(0.0f, ab_.x);
+  const float2 bP = left ? f2(ab_.y, 0.0f) : f2(0.0f, ab_.y);
+  if (star) {
+    // S* = num / den, num = p_R - p_L + rho_L u_L d_L - rho_R u_R d_R, den = rho_L d_L - rho_R d_R
+    const float num_ = Ss_ * q_div(1.0f, rd.x - rd.y);
+    const float den_ = -num_ * Ss;
+    const float2 sn = f2(num_, -num_), sd = f2(den_, -den_);
+    pP = p_sub(pP, sn);
+    rP = p_fma(sn, p_mul(u, d), p_fma(sd, d, rP));
+    uP = p_fma(sn, rd, uP);
+    const float2 dP = p_fma(sn, p_mul(r, u), p_mul(sd, r));
+    SP = p_add(SP, dP);
+    uP = p_sub(uP, dP);
+  }
+  // S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R); ties split evenly
+  const float wx = um.x < um.y ? 1.0f : (um.x == um.y ? 0.5f : 0.0f);
+  const float wy = upc.x > upc.y ? 1.0f : (upc.x == upc.y ? 0.5f : 0.0f);
+  const float2 sx = p_mul(f2(wx, 1.0f - wx), f2s(SP.x));
+  const float2 sy = p_mul(f2(wy, 1.0f - wy), f2s(SP.y));
+  uP = p_add(uP, p_add(sx, sy));
+  const float2 c_ = p_sub(sy, sx);
+  pP = p_fma(c_, p_mul(f2s(0.5f * gamma), rs), pP);
+  rP = p_sub(rP, p_mul(c_, p_mul(p_mul(c, c), p_mul(rs, f2s(0.5f)))));
+  gL[0] = rP.x; gL[1] = uP.x; gL[2] = aP.x; gL[3] = bP.x; gL[4] = pP.x;
+  gR[0] = rP.y; gR[1] = uP.y; gR[2] = aP.y; gR[3] = bP.y; gR[4] = pP.y;
+}
+#endif
+
+// HLLC VJP in the face frame: hllc_vjp_packed for the float32 device build, hllc_vjp otherwise.
+template <typename real>
+__host__ __device__ __forceinline__ void hllc_vjp_any(real rL, real uL, real aL, real bL, real pL,
+                                                      real rR, real uR, real aR, real bR, real pR,
+                                                      real gamma, real gm1, real g0, real gn,
+                                                      real gt1, real gt2, real ge, real gL[5],
+                                                      real gR[5]) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (std::is_same<real, float>::value) {
+    hllc_vjp_packed(rL, uL, aL, bL, pL, rR, uR, aR, bR, pR, gamma, gm1, g0, gn, gt1, gt2, ge, gL, gR);
+    return;
+  }
+#endif
+  hllc_vjp(rL, uL, aL, bL, pL, rR, uR, aR, bR, pR, gamma, gm1, g0, gn, gt1, gt2, ge, gL, gR);
+}
+
 // Face VJP along `axis` from the reconstructed states L (upper face state of the lower cell) and
 // R, and the flux gradient g[5] in (rho, m_x, m_y, m_z, E) order; returns gradients of the two
 // states in (rho, v_x, v_y, v_z, P) order.
@@ -194,17 +326,17 @@ __host__ __device__ __forceinline__ void face_vjp(int axis, const Prim<real>& L,
                                                   real gR[5]) {
   real fL[5], fR[5];
   if (axis == 0) {
-    hllc_vjp(L.r, L.vx, L.vy, L.vz, L.p, R.r, R.vx, R.vy, R.vz, R.p, gamma, gm1, g[0], g[1], g[2],
+    hllc_vjp_any(L.r, L.vx, L.vy, L.vz, L.p, R.r, R.vx, R.vy, R.vz, R.p, gamma, gm1, g[0], g[1], g[2],
              g[3], g[4], fL, fR);
     gL[0] = fL[0]; gL[1] = fL[1]; gL[2] = fL[2]; gL[3] = fL[3]; gL[4] = fL[4];
     gR[0] = fR[0]; gR[1] = fR[1]; gR[2] = fR[2]; gR[3] = fR[3]; gR[4] = fR[4];
   } else if (axis == 1) {
-    hllc_vjp(L.r, L.vy, L.vx, L.vz, L.p, R.r, R.vy, R.vx, R.vz, R.p, gamma, gm1, g[0], g[2], g[1],
+    hllc_vjp_any(L.r, L.vy, L.vx, L.vz, L.p, R.r, R.vy, R.vx, R.vz, R.p, gamma, gm1, g[0], g[2], g[1],
              g[3], g[4], fL, fR);
     gL[0] = fL[0]; gL[1] = fL[2]; gL[2] = fL[1]; gL[3] = fL[3]; gL[4] = fL[4];
     gR[0] = fR[0]; gR[1] = fR[2]; gR[2] = fR[1]; gR[3] = fR[3]; gR[4] = fR[4];
   } else {
-    hllc_vjp(L.r, L.vz, L.vx, L.vy, L.p, R.r, R.vz, R.vx, R.vy, R.p, gamma, gm1, g[0], g[3], g[1],
+    hllc_vjp_any(L.r, L.vz, L.vx, L.vy, L.p, R.r, R.vz, R.vx, R.vy, R.p, gamma, gm1, g[0], g[3], g[1],
              g[2], g[4], fL, fR);
     gL[0] = fL[0]; gL[1] = fL[2]; gL[2] = fL[3]; gL[3] = fL[1]; gL[4] = fL[4];
     gR[0] = fR[0]; gR[1] = fR[2]; gR[2] = fR[3]; gR[3] = fR[1]; gR[4] = fR[4];

@@ -277,7 +277,7 @@ static StageArgs<real> stage_args(dh_ctx* c) {
 
 // Enqueues one full step reading U[cur] and writing U[1-cur]; no synchronisation.
 template <typename real>
-static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed) {
+static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed, const StepCapture* cap) {
   const dh_config& g = c->cfg;
   BeginArgs b;
   b.rec = c->rec; b.dt_fixed = dt_fixed; b.cfl = g.cfl; b.dt_max = g.dt_max;
@@ -296,7 +296,7 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed) {
   const bool rk3 = g.integrator == 3;
   // RK2: U^n -> U1 (scratch) -> U^{n+1}.  SSPRK3: U^n -> U1 (in the output buffer) -> U2
   // (scratch) -> U^{n+1}; U^n is never written, so it stays the last good state.
-  real* Ust1 = rk3 ? Unew : (real*)c->U1;
+  real* Ust1 = cap && cap->u1 ? (real*)cap->u1 : (rk3 ? Unew : (real*)c->U1);
   a.U = Un; a.U0 = nullptr; a.out = Ust1;
   prof_begin(c, DH_KERNEL_STAGE1);
   e = launch_stage<real>(1, a, c->stream);
@@ -305,14 +305,14 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed) {
   const real* Ulast = Ust1;
   if (rk3) {
     StageArgs<real> m = a;
-    m.U = Ust1; m.U0 = Un; m.out = (real*)c->U1;
+    m.U = Ust1; m.U0 = Un; m.out = cap && cap->u2 ? (real*)cap->u2 : (real*)c->U1;
     m.w0 = real(0.75); m.w1 = real(0.25);
     m.final_stage = 0;
     prof_begin(c, DH_KERNEL_STAGE1);
     e = launch_stage<real>(3, m, c->stream);
     prof_end(c, 1);
     if (e != cudaSuccess) return e;
-    Ulast = (const real*)c->U1;
+    Ulast = m.out;
     a.w0 = real(1.0 / 3.0); a.w1 = real(2.0 / 3.0);
   }
 
@@ -321,6 +321,7 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed) {
   a.forcing = fuse ? g.forcing : 0;
   a.cooling = fuse ? g.cooling : 0;
   a.reduce_cfl = fuse ? 1 : 0;
+  a.pre_src = fuse && cap ? (real*)cap->pre_src : nullptr;
   prof_begin(c, DH_KERNEL_STAGE2);
   e = launch_stage<real>(rk3 ? 3 : 2, a, c->stream);
   prof_end(c, 1);
@@ -379,15 +380,19 @@ dh_status dh_refresh_cfl(dh_ctx* c) {
   return DH_OK;
 }
 
-cudaError_t dh_enqueue_step_f32(dh_ctx* c, double dt) { return enqueue_step<float>(c, dt); }
-cudaError_t dh_enqueue_step_f64(dh_ctx* c, double dt) { return enqueue_step<double>(c, dt); }
+cudaError_t dh_enqueue_step_f32(dh_ctx* c, double dt, const StepCapture* cap) {
+  return enqueue_step<float>(c, dt, cap);
+}
+cudaError_t dh_enqueue_step_f64(dh_ctx* c, double dt, const StepCapture* cap) {
+  return enqueue_step<double>(c, dt, cap);
+}
 dh_status dh_finish_steps(dh_ctx* c) { return finish_steps(c, c->host_rec.nstep - c->pending_steps); }
 
 extern "C" dh_status dh_step(dh_ctx* c, double dt, double* dt_used) {
   if (!c) return fail(c, DH_ERR_ARG, "null context");
   if (!c->initialized) return fail(c, DH_ERR_STATE, "state not initialised");
   const long long before = c->host_rec.nstep - c->pending_steps;
-  cudaError_t e = c->prec == DH_F64 ? enqueue_step<double>(c, dt) : enqueue_step<float>(c, dt);
+  cudaError_t e = c->prec == DH_F64 ? enqueue_step<double>(c, dt, nullptr) : enqueue_step<float>(c, dt, nullptr);
   if (e != cudaSuccess) return cuda_fail(c, e, "enqueue_step");
   if (dt_used) {
     dh_status s = finish_steps(c, before);
@@ -404,7 +409,7 @@ extern "C" dh_status dh_advance(dh_ctx* c, int n, double* t_out) {
   if (n < 0) return fail(c, DH_ERR_ARG, "n_steps must be >= 0");
   const long long before = c->host_rec.nstep - c->pending_steps;
   for (int i = 0; i < n; ++i) {
-    cudaError_t e = c->prec == DH_F64 ? enqueue_step<double>(c, 0.0) : enqueue_step<float>(c, 0.0);
+    cudaError_t e = c->prec == DH_F64 ? enqueue_step<double>(c, 0.0, nullptr) : enqueue_step<float>(c, 0.0, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "enqueue_step");
   }
   dh_status s = finish_steps(c, before);

@@ -70,8 +70,17 @@ void adjoint_free(dh_ctx* c);
 }  // namespace dh
 
 // dh_api.cu: step machinery shared with the adjoint driver
-cudaError_t dh_enqueue_step_f32(dh_ctx* c, double dt_fixed);   // dt_fixed <= 0: CFL
-cudaError_t dh_enqueue_step_f64(dh_ctx* c, double dt_fixed);
+// Optional extra outputs of one step (each nullable): the stage-1 state, SSPRK3's second-stage
+// state and, with fused sources, the state before the sources.  The adjoint's forward sweep
+// keeps its last segment this way instead of replaying it.
+struct StepCapture {
+  void* u1 = nullptr;
+  void* u2 = nullptr;
+  void* pre_src = nullptr;
+};
+cudaError_t dh_enqueue_step_f32(dh_ctx* c, double dt_fixed,    // dt_fixed <= 0: CFL
+                                const StepCapture* cap = nullptr);
+cudaError_t dh_enqueue_step_f64(dh_ctx* c, double dt_fixed, const StepCapture* cap = nullptr);
 dh_status dh_finish_steps(dh_ctx* c);
 // message returned by dh_last_error(NULL)
 void dh_set_global_error(const std::string& msg);

@@ -319,40 +319,65 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
   }
 }
 
-static int stage_zchunk(int nx, int ny, int nz) {
-  const long long tiles = (long long)((nx + BX - 1) / BX) * ((ny + BY - 1) / BY);
-  // aim for >= ~8 CTAs per SM over 148 SMs, with chunks of at least 8 planes
-  int chunks = (int)((148LL * 8 + tiles - 1) / tiles);
-  if (chunks < 1) chunks = 1;
-  int zc = (nz + chunks - 1) / chunks;
-  if (zc < 8) zc = 8;
-  if (zc > nz) zc = nz;
-  return zc;
+int sm_count() {
+  static int n = 0;
+  if (n <= 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+  }
+  return n;
+}
+
+int wave_zchunk(long long tiles, int nz, int resident_per_sm, double prologue) {
+  const long long slots = (long long)sm_count() * (resident_per_sm > 0 ? resident_per_sm : 1);
+  int best = nz;
+  double bestv = -1.0;
+  const int cmax = nz / 8 > 1 ? nz / 8 : 1;
+  for (int c = 1; c <= cmax; ++c) {
+    const int zc = (nz + c - 1) / c;
+    const int chunks = (nz + zc - 1) / zc;
+    const long long waves = (tiles * chunks + slots - 1) / slots;
+    const double fill = (double)tiles * nz / ((double)waves * slots * zc);
+    const double v = fill * zc / (zc + prologue);
+    if (v > bestv + 1e-9) {
+      bestv = v;
+      best = zc;
+    }
+  }
+  return best;
 }
 
 template <typename real, int STAGE, int LIM>
-static cudaError_t launch_stage_t(const StageArgs<real>& a, dim3 grid, size_t smem, int zc,
-                                  cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(stage_kernel<real, STAGE, LIM>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static cudaError_t launch_stage_t(const StageArgs<real>& a, cudaStream_t s) {
+  auto kernel = stage_kernel<real, STAGE, LIM>;
+  const size_t smem = sizeof(StageSmem<real>);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  stage_kernel<real, STAGE, LIM><<<grid, NTHREADS, smem, s>>>(a, zc);
+  static int resident = 0;   // CTAs per SM of this instance
+  if (resident <= 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kernel, NTHREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (resident <= 0) resident = 1;
+  }
+  const long long tiles = (long long)((a.nx + BX - 1) / BX) * ((a.ny + BY - 1) / BY);
+  const int zc = wave_zchunk(tiles, a.nz, resident, 1.0);
+  dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + zc - 1) / zc);
+  kernel<<<grid, NTHREADS, smem, s>>>(a, zc);
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s) {
-  const int zc = stage_zchunk(a.nx, a.ny, a.nz);
-  dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + zc - 1) / zc);
-  const size_t smem = sizeof(StageSmem<real>);
   if (a.limiter == LIM_VL) {
-    if (stage == 1) return launch_stage_t<real, 1, LIM_VL>(a, grid, smem, zc, s);
-    if (stage == 2) return launch_stage_t<real, 2, LIM_VL>(a, grid, smem, zc, s);
-    return launch_stage_t<real, 3, LIM_VL>(a, grid, smem, zc, s);
+    if (stage == 1) return launch_stage_t<real, 1, LIM_VL>(a, s);
+    if (stage == 2) return launch_stage_t<real, 2, LIM_VL>(a, s);
+    return launch_stage_t<real, 3, LIM_VL>(a, s);
   }
-  if (stage == 1) return launch_stage_t<real, 1, LIM_MC>(a, grid, smem, zc, s);
-  if (stage == 2) return launch_stage_t<real, 2, LIM_MC>(a, grid, smem, zc, s);
-  return launch_stage_t<real, 3, LIM_MC>(a, grid, smem, zc, s);
+  if (stage == 1) return launch_stage_t<real, 1, LIM_MC>(a, s);
+  if (stage == 2) return launch_stage_t<real, 2, LIM_MC>(a, s);
+  return launch_stage_t<real, 3, LIM_MC>(a, s);
 }
 template cudaError_t launch_stage<float>(int, const StageArgs<float>&, cudaStream_t);
 template cudaError_t launch_stage<double>(int, const StageArgs<double>&, cudaStream_t);
