@@ -111,6 +111,7 @@ __device__ __forceinline__ void add_modes(const real* ah, const real* tx, const 
 
 // One task of the per-row forcing factors: for row (y, z) and n_x in {0,1,2}, component c:
 // B = sum over forced modes with that n_x of a_hat_{m,c} exp(2 pi i (n_y y~ + n_z z~)).
+// `ah` (the normalised table) may be in global or shared memory.
 template <typename real, int M>
 __device__ __forceinline__ void row_factor(const real* __restrict__ ah, int nxsel, int c,
                                            const real* ty, const real* tz, real& bre, real& bim) {
@@ -126,8 +127,8 @@ __device__ __forceinline__ void row_factor(const real* __restrict__ ah, int nxse
         const C2<real> f = axis_factor<real, NZ>(tz);
         e = first ? f : cmul(e, f);
       }
-      const real are = __ldg(ah + 2 * (3 * M + c));
-      const real aim = __ldg(ah + 2 * (3 * M + c) + 1);
+      const real are = ah[2 * (3 * M + c)];
+      const real aim = ah[2 * (3 * M + c) + 1];
       bre += are * e.re - aim * e.im;
       bim += are * e.im + aim * e.re;
     }

@@ -9,8 +9,11 @@
 // Blocking: a CTA owns a BX x BY column of cells and marches along z through a chunk of
 // planes.  Primitive planes (with a two-cell x/y halo) sit in a three-plane shared-memory ring
 // (k, k+1, k+2); every x and y face of plane k is evaluated exactly once per CTA by a linear
-// face loop, and the z faces come from a per-thread register pipeline (each z face once).
+// face loop, and the z faces come from a per-thread register pipeline (each z face once).  The
+// conserved variables of the next plane arrive by cp.async into a staging plane while the
+// current plane is computed, and are converted into the ring one plane later.
 #include <math.h>
+#include "async_copy.cuh"
 #include "dh_kernels.h"
 #include "dh_sources.cuh"
 #include "ff.cuh"
@@ -26,7 +29,22 @@ constexpr int NXF = (BX + 1) * BY;   // x faces of a plane tile
 constexpr int NYF = BX * (BY + 1);   // y faces of a plane tile
 constexpr int NFORCE = BY * 9;       // forcing row factors: row x (n_x = 0, 1, 2) x component
 
+// Staging plane: rows of conserved variables copied in 16-byte chunks of SCE elements, from
+// x0 - SHALO to x0 + BX + SHALO (SHALO >= 2, a multiple of SCE); prim column sx is staging
+// column sx + SOFF.
+template <typename real> struct Staging {
+  static constexpr int SCE = 16 / (int)sizeof(real);
+  static constexpr int SHALO = (2 + SCE - 1) / SCE * SCE;
+  static constexpr int SROW = BX + 2 * SHALO;
+  static constexpr int NCH = SROW / SCE;       // chunks per row
+  static constexpr int SOFF = SHALO - 2;
+};
+
 template <typename real> struct StageSmem {
+  real stg[5][HY][Staging<real>::SROW];   // conserved variables of the plane in flight
+  real tz[4];                // forcing: z twiddles of the plane in flight (staged with it)
+  real ah[96];               // forcing: normalised OU table
+  real tyt[BY][4];           // forcing: y twiddles of the tile's rows
   real w[3][5][HY][HX];      // primitive planes ring (k, k+1, k+2), two-cell x/y halo
   real xm[5][BY][BX + 2];    // x face states W - dW/2 of cells lx = -1..BX (index lx + 1)
   real xp[5][BY][BX + 2];    //                W + dW/2
@@ -37,6 +55,7 @@ template <typename real> struct StageSmem {
   real fB[BY][3][3][2];      // forcing: B[row][n_x][component] = sum over modes with that n_x
   int xs[HX];                // wrapped global x of each smem column
   int ys[HY];                // wrapped global y of each smem row
+  int cx[Staging<real>::NCH];  // wrapped global x of each staging chunk
   real red[NTHREADS / 32];   // CFL reduction scratch
 };
 
@@ -95,9 +114,62 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
   const real w0 = STAGE == 2 ? real(0.5) : p.w0, w1 = STAGE == 2 ? real(0.5) : p.w1;
   const bool forcing = final && p.forcing;
 
+  using ST = Staging<real>;
   if (tid < HX) S.xs[tid] = ((x0 + tid - 2) % nx + nx) % nx;
   if (tid >= 64 && tid < 64 + HY) S.ys[tid - 64] = ((y0 + tid - 64 - 2) % ny + ny) % ny;
+  if (tid >= 96 && tid < 96 + ST::NCH)
+    S.cx[tid - 96] = ((x0 - ST::SHALO + ST::SCE * (tid - 96)) % nx + nx) % nx;
+  if (forcing) {
+    if (tid < 96) S.ah[tid] = __ldg(p.ahat_norm + tid);
+    if (tid >= 128 && tid < 128 + 4 * BY) {
+      const int ly = (tid - 128) >> 2, i = (tid - 128) & 3;
+      S.tyt[ly][i] = __ldg(p.tw[1] + 4 * ((y0 + ly) % ny) + i);
+    }
+  }
+  // whole 16-byte chunks need rows of a multiple of SCE elements and an aligned state
+  const bool vec = (nx % ST::SCE == 0) && (((unsigned long long)p.U & 15ull) == 0);
   __syncthreads();
+
+  // cp.async of the conserved variables of plane k into the staging plane, with the forcing's z
+  // twiddles of plane k - 2 (the plane whose row factors the next iteration builds); one group
+  auto stage_plane = [&](int k) {
+    const long long zoff = (long long)wrap(k, nz) * plane;
+    if (forcing && tid == NTHREADS - 1) {
+      const real* t = p.tw[2] + 4 * wrap(k - 2, nz);
+#pragma unroll
+      for (int i = 0; i < 4; i += ST::SCE) cp_async16(&S.tz[i], t + i);
+    }
+    if (vec) {
+      for (int c = tid; c < 5 * HY * ST::NCH; c += NTHREADS) {
+        const int f = c / (HY * ST::NCH), r = c - f * (HY * ST::NCH);
+        const int sy = r / ST::NCH, j = r - sy * ST::NCH;
+        cp_async16(&S.stg[f][sy][ST::SCE * j], p.U + f * n3 + zoff + (long long)S.ys[sy] * nx + S.cx[j]);
+      }
+    } else {
+      for (int c = tid; c < 5 * HY * HX; c += NTHREADS) {
+        const int f = c / (HY * HX), r = c - f * (HY * HX);
+        const int sy = r / HX, sx = r - sy * HX;
+        const real* g = p.U + f * n3 + zoff + (long long)S.ys[sy] * nx + S.xs[sx];
+        if constexpr (sizeof(real) == 4) cp_async4(&S.stg[f][sy][sx + ST::SOFF], g);
+        else cp_async8(&S.stg[f][sy][sx + ST::SOFF], g);
+      }
+    }
+    cp_async_commit();
+  };
+  // primitive recovery of the staged plane into a ring slot
+  auto convert_plane = [&](int slot) {
+    for (int c = tid; c < HX * HY; c += NTHREADS) {
+      const int sy = c / HX, sx = c - sy * HX;
+      const int q = sx + ST::SOFF;
+      const Prim<real> w = cons_to_prim(S.stg[0][sy][q], S.stg[1][sy][q], S.stg[2][sy][q],
+                                        S.stg[3][sy][q], S.stg[4][sy][q], gm1);
+      S.w[slot][0][sy][sx] = w.r;
+      S.w[slot][1][sy][sx] = w.vx;
+      S.w[slot][2][sy][sx] = w.vy;
+      S.w[slot][3][sy][sx] = w.vz;
+      S.w[slot][4][sy][sx] = w.p;
+    }
+  };
 
   auto load_plane = [&](int k, int slot) {
     const long long zoff = (long long)wrap(k, nz) * plane;
@@ -136,15 +208,17 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
     dk = limited_slope<LIM>(wm1, w0, w1);
     face_flux(2, add_half(wm1, dm1, real(1)), add_half(w0, dk, real(-1)), gamma, gm1, fz_lo);
   }
+  stage_plane(z0 + 2);
 
   real tmin = real(INFINITY);
   unsigned flags = 0;
 
   for (int k = z0; k < z1; ++k) {
     const int s0 = (k - z0) % 3, s1 = (k - z0 + 1) % 3, s2 = (k - z0 + 2) % 3;
-    load_plane(k + 2, s2);
-    __syncthreads();  // ---- plane k+2 in the ring
+    cp_async_wait<0>();
+    __syncthreads();  // ---- plane k+2 staged; the update of plane k-1 is done
 
+    convert_plane(s2);
     // limited slopes and face states of plane k, once per cell and axis
     for (int t = tid; t < NXS + NYS; t += NTHREADS) {
       if (t < NXS) {
@@ -168,17 +242,27 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
       const int q = tid - (NTHREADS - NFORCE);
       const int ly = q / 9, rem = q - 9 * ly;
       const int nxsel = rem / 3, c = rem - 3 * nxsel;
-      const int yrow = (y0 + ly) % ny;
       real tyv[4], tzv[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        tyv[i] = __ldg(p.tw[1] + 4 * yrow + i);
-        tzv[i] = __ldg(p.tw[2] + 4 * k + i);
+        tyv[i] = S.tyt[ly][i];
+        tzv[i] = S.tz[i];
       }
       real bre = real(0), bim = real(0);
-      row_factor<real, 0>(p.ahat_norm, nxsel, c, tyv, tzv, bre, bim);
+      row_factor<real, 0>(S.ah, nxsel, c, tyv, tzv, bre, bim);
       S.fB[ly][nxsel][c][0] = bre;
       S.fB[ly][nxsel][c][1] = bim;
+    }
+    __syncthreads();  // ---- plane k+2 in the ring, face states ready, staging plane free
+
+    if (k + 1 < z1) stage_plane(k + 3);
+    // stage 1 loads the own cell's state for the update now and uses it after the face loop;
+    // the combination stages load U and U0 there (measured faster: fewer live registers)
+    const long long idx = (long long)k * plane + col;
+    real uin[5], un[5];
+    if (!COMB && active) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) uin[c] = __ldg(p.U + c * n3 + idx);
     }
     // z face k+1/2 of the own column
     real fz_hi[5];
@@ -190,7 +274,6 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
       dk1 = limited_slope<LIM>(w0, w1, w2);
       face_flux(2, add_half(w0, dk, real(1)), add_half(w1, dk1, real(-1)), gamma, gm1, fz_hi);
     }
-    __syncthreads();  // ---- face states ready
 
     // every x and y face of plane k, once
     for (int f = tid; f < NXF + NYF; f += NTHREADS) {
@@ -211,16 +294,16 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
     __syncthreads();  // ---- fluxes ready
 
     if (active) {
-      const long long idx = (long long)k * plane + col;
       real u[5];
-      if constexpr (std::is_same<real, float>::value) {
-        // components (0,1) and (2,3) as packed pairs, 4 alone
-        float uin[5], un[5];
+      if (COMB) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           uin[c] = __ldg(p.U + c * n3 + idx);
-          if (COMB) un[c] = __ldg(p.U0 + c * n3 + idx);
+          un[c] = __ldg(p.U0 + c * n3 + idx);
         }
+      }
+      if constexpr (std::is_same<real, float>::value) {
+        // components (0,1) and (2,3) as packed pairs, 4 alone
 #pragma unroll
         for (int c = 0; c < 4; c += 2) {
           const float2 dfx = p_sub(f2(S.fx[c][ty][tx + 1], S.fx[c + 1][ty][tx + 1]),
@@ -248,13 +331,8 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
           real L = -((S.fx[c][ty][tx + 1] - S.fx[c][ty][tx]) * p.idx);
           L -= (S.fy[c][ty + 1][tx] - S.fy[c][ty][tx]) * p.idy;
           L -= (fz_hi[c] - fz_lo[c]) * p.idz;
-          const real uin = __ldg(p.U + c * n3 + idx);
-          if (STAGE == 1) {
-            u[c] = uin + dt * L;
-          } else {
-            const real un = __ldg(p.U0 + c * n3 + idx);
-            u[c] = w0 * un + w1 * (uin + dt * L);
-          }
+          if (STAGE == 1) u[c] = uin[c] + dt * L;
+          else u[c] = w0 * un[c] + w1 * (uin[c] + dt * L);
         }
       }
       if (COMB && final) {

@@ -23,6 +23,7 @@
 #include <utility>
 #include <vector>
 
+#include "async_copy.cuh"
 #include "dh_internal.h"
 #include "dh_sources.cuh"
 #include "ff.cuh"
@@ -272,14 +273,6 @@ __global__ void poisson_source_kernel(const T* __restrict__ rho, long long n, co
 }
 
 
-// Asynchronous 4-byte global -> shared copies (cp.async), grouped per plane.
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // One red-black Gauss-Seidel sweep on A e = r in one pass, from e_old into e_new: first every
 // red cell (i + j + k even), then every black cell, each e_i = (sum of 6 neighbours - h^2 r_i)/6.
@@ -400,11 +393,6 @@ rbgs_sweep_kernel(const float* __restrict__ eo, float* __restrict__ en, const fl
   cp_async_wait<0>();
 }
 
-// 16-byte cp.async (both addresses 16-byte aligned).
-__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 
 // The same sweep for rows of a multiple of 4 cells, two cells per thread: a CTA owns a 64 x 8
 // column; thread (t, y) takes the pair x0 + 2t, x0 + 2t + 1 of row y, which holds one red and
