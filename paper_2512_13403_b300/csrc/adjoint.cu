@@ -16,6 +16,7 @@
 #include <math.h>
 #include <vector>
 
+#include "async_copy.cuh"
 #include "dh_internal.h"
 #include "dh_adjoint.cuh"
 #include "dh_sources.cuh"
@@ -39,22 +40,42 @@ constexpr int NCX = NCXA * ABY, NCY = NCYA * ABX;   // cells with x and y slope 
 constexpr int warp_up(int n) { return (n + 31) / 32 * 32; }
 constexpr int NSXP = warp_up(NSX), NFXP = warp_up(NFX), NCXP = warp_up(NCX);
 
+// Staging plane: rows of conserved variables copied in 16-byte chunks of SCE elements, from
+// x0 - SHALO to x0 + ABX + SHALO (SHALO >= 3, a multiple of SCE); ring column sx is staging
+// column sx + SOFF.
+template <typename real> struct AdjStaging {
+  static constexpr int SCE = 16 / (int)sizeof(real);
+  static constexpr int SHALO = (3 + SCE - 1) / SCE * SCE;
+  static constexpr int SROW = ABX + 2 * SHALO;
+  static constexpr int NCH = SROW / SCE;
+  static constexpr int SOFF = SHALO - 3;
+};
+
 template <typename real> struct AdjSmem {
+  real stg[5][WY][AdjStaging<real>::SROW];   // conserved variables of the plane in flight
   real w[4][5][WY][WX];
-  real mu[5][MYH][MXH];
+  real mu[5][MYH][MXH];           // lam_out of plane k (the stage's beta dt is applied at use)
   real face[10][NFXP + NFY];      // (gL[5], gR[5]) per face: x faces, then y faces
   union {
     real st[10][NSXP + NSY];      // (W - dW/2, W + dW/2) per cell and axis: x, then y
     real cell[10][NCXP + NCY];    // (A[5], B[5]) per cell: x terms, then y terms
   } u;
-  unsigned char zero[NSXP + NSY]; // the cell's limited slope along the axis is all zero
-  int xs[WX], ys[WY];
+  unsigned zero[(NSXP + NSY) / 32];   // bit t: the limited slope of slope item t is all zero
+  int xs[WX], ys[WY], cx[AdjStaging<real>::NCH];
 };
+static_assert(NSXP % 32 == 0 && NSY % 32 == 0, "slope items come in whole warps");
+// two CTAs per SM for the float32 instance: 2 x (size + 1 KB reserved) within 228 KB
+static_assert(2 * (sizeof(AdjSmem<float>) + 1024) <= 228 * 1024, "adjoint shared memory");
 
 template <typename real>
 __device__ __forceinline__ Prim<real> ring_prim(const AdjSmem<real>& S, int slot, int sy, int sx) {
   return Prim<real>{S.w[slot][0][sy][sx], S.w[slot][1][sy][sx], S.w[slot][2][sy][sx],
                     S.w[slot][3][sy][sx], S.w[slot][4][sy][sx]};
+}
+
+template <typename real>
+__device__ __forceinline__ bool zero_bit(const AdjSmem<real>& S, int i) {
+  return (S.zero[i >> 5] >> (i & 31)) & 1u;
 }
 
 template <typename real>
@@ -72,13 +93,17 @@ __device__ __forceinline__ Prim<real> gload_prim(const real* __restrict__ U, lon
 
 template <typename real>
 __device__ __forceinline__ void gload5(const real* __restrict__ p, long long n3, long long idx,
-                                       real s, real out[5]) {
+                                       real out[5]) {
 #pragma unroll
-  for (int c = 0; c < 5; ++c) out[c] = s * __ldg(p + c * n3 + idx);
+  for (int c = 0; c < 5; ++c) out[c] = __ldg(p + c * n3 + idx);
 }
 
+__device__ __forceinline__ void cp_async_elem(float* s, const float* g) { cp_async4(s, g); }
+__device__ __forceinline__ void cp_async_elem(double* s, const double* g) { cp_async8(s, g); }
+
+// float32: two CTAs per SM (its registers and shared memory are sized for it); float64: one
 template <typename real, int LIM>
-__global__ void __launch_bounds__(ANT)
+__global__ void __launch_bounds__(ANT, sizeof(real) == 4 ? 2 : 1)
 stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AdjSmem<real>& S = *reinterpret_cast<AdjSmem<real>*>(smem_raw);
@@ -93,12 +118,19 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
   const real gamma = p.gamma, gm1 = p.gm1;
   const real dt = (real)*p.dtp;
   const real sdt = p.beta * dt;
+  // flux gradients are beta dt times differences of lam_out
+  const real gfx = sdt * p.idx, gfy = sdt * p.idy, gfz = sdt * p.idz;
   const int gx = x0 + tx, gy = y0 + ty;
   const bool active = gx < nx && gy < ny;
   const long long col = (long long)(gy % ny) * nx + (gx % nx);
 
+  using ST = AdjStaging<real>;
   if (tid < WX) S.xs[tid] = ((x0 + tid - 3) % nx + nx) % nx;
   if (tid >= 64 && tid < 64 + WY) S.ys[tid - 64] = ((y0 + tid - 64 - 3) % ny + ny) % ny;
+  if (tid >= 96 && tid < 96 + ST::NCH)
+    S.cx[tid - 96] = ((x0 - ST::SHALO + ST::SCE * (tid - 96)) % nx + nx) % nx;
+  // whole 16-byte chunks need rows of a multiple of SCE elements and an aligned state
+  const bool vec = (nx % ST::SCE == 0) && (((unsigned long long)p.U & 15ull) == 0);
   __syncthreads();
 
   auto load_w = [&](int k, int slot) {
@@ -113,14 +145,52 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       S.w[slot][4][sy][sx] = w.p;
     }
   };
+  // cp.async of the conserved variables of plane k into the staging plane (one commit group)
+  auto stage_plane = [&](int k) {
+    const long long zoff = (long long)wrap(k, nz) * plane;
+    if (vec) {
+      for (int c = tid; c < 5 * WY * ST::NCH; c += ANT) {
+        const int f = c / (WY * ST::NCH), r = c - f * (WY * ST::NCH);
+        const int sy = r / ST::NCH, j = r - sy * ST::NCH;
+        cp_async16(&S.stg[f][sy][ST::SCE * j], p.U + f * n3 + zoff + (long long)S.ys[sy] * nx + S.cx[j]);
+      }
+    } else {
+      for (int c = tid; c < 5 * WY * WX; c += ANT) {
+        const int f = c / (WY * WX), r = c - f * (WY * WX);
+        const int sy = r / WX, sx = r - sy * WX;
+        cp_async_elem(&S.stg[f][sy][sx + ST::SOFF],
+                      p.U + f * n3 + zoff + (long long)S.ys[sy] * nx + S.xs[sx]);
+      }
+    }
+    cp_async_commit();
+  };
+  auto staged_prim = [&](int sy, int sx) {
+    const int q = sx + ST::SOFF;
+    return cons_to_prim(S.stg[0][sy][q], S.stg[1][sy][q], S.stg[2][sy][q], S.stg[3][sy][q],
+                        S.stg[4][sy][q], gm1);
+  };
+  // primitive recovery of the staged plane into a ring slot
+  auto convert_plane = [&](int slot) {
+    for (int c = tid; c < WX * WY; c += ANT) {
+      const int sy = c / WX, sx = c - sy * WX;
+      const Prim<real> w = staged_prim(sy, sx);
+      S.w[slot][0][sy][sx] = w.r;
+      S.w[slot][1][sy][sx] = w.vx;
+      S.w[slot][2][sy][sx] = w.vy;
+      S.w[slot][3][sy][sx] = w.vz;
+      S.w[slot][4][sy][sx] = w.p;
+    }
+  };
+  // cp.async of lam_out of plane k (x/y halo 2) into mu (one commit group)
   auto load_mu = [&](int k) {
     const long long zoff = (long long)wrap(k, nz) * plane;
-    for (int c = tid; c < MXH * MYH; c += ANT) {
-      const int sy = c / MXH, sx = c - sy * MXH;
-      const long long idx = zoff + (long long)S.ys[sy + 1] * nx + S.xs[sx + 1];
-#pragma unroll
-      for (int f = 0; f < 5; ++f) S.mu[f][sy][sx] = sdt * __ldg(p.lam_out + f * n3 + idx);
+    for (int c = tid; c < 5 * MXH * MYH; c += ANT) {
+      const int f = c / (MXH * MYH), r = c - f * (MXH * MYH);
+      const int sy = r / MXH, sx = r - sy * MXH;
+      cp_async_elem(&S.mu[f][sy][sx],
+                    p.lam_out + f * n3 + zoff + (long long)S.ys[sy + 1] * nx + S.xs[sx + 1]);
     }
+    cp_async_commit();
   };
 
   // ---- prologue: ring planes z0..z0+2, own-column history below z0 -------------------------
@@ -131,10 +201,10 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
   const Prim<real> wm2 = gload_prim(p.U, n3, (long long)wrap(z0 - 2, nz) * plane + col, gm1);
   const Prim<real> wm1 = gload_prim(p.U, n3, (long long)wrap(z0 - 1, nz) * plane + col, gm1);
   real mum2[5], mum1[5], mu0[5], mun[5];
-  gload5(p.lam_out, n3, (long long)wrap(z0 - 2, nz) * plane + col, sdt, mum2);
-  gload5(p.lam_out, n3, (long long)wrap(z0 - 1, nz) * plane + col, sdt, mum1);
-  gload5(p.lam_out, n3, (long long)wrap(z0, nz) * plane + col, sdt, mu0);
-  gload5(p.lam_out, n3, (long long)wrap(z0 + 1, nz) * plane + col, sdt, mun);
+  gload5(p.lam_out, n3, (long long)wrap(z0 - 2, nz) * plane + col, mum2);
+  gload5(p.lam_out, n3, (long long)wrap(z0 - 1, nz) * plane + col, mum1);
+  gload5(p.lam_out, n3, (long long)wrap(z0, nz) * plane + col, mu0);
+  gload5(p.lam_out, n3, (long long)wrap(z0 + 1, nz) * plane + col, mun);
   __syncthreads();
 
   // z pipeline of the own column at the top of iteration k: the limited slope dz1 of cell k+1,
@@ -152,29 +222,61 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
     dz1 = limited_slope<LIM>(w0, w1, w2);
     real g[5], gLa[5], gRa[5], gLb[5], gRb[5], D[5], Bt[5];
     // face z0-3/2
-    for (int c = 0; c < 5; ++c) g[c] = (mum1[c] - mum2[c]) * p.idz;
+    for (int c = 0; c < 5; ++c) g[c] = (mum1[c] - mum2[c]) * gfz;
     face_vjp(2, add_half(wm2, dm2, real(1)), add_half(wm1, dm1, real(-1)), g, gamma, gm1, gLa, gRa);
     // face z0-1/2
-    for (int c = 0; c < 5; ++c) g[c] = (mu0[c] - mum1[c]) * p.idz;
+    for (int c = 0; c < 5; ++c) g[c] = (mu0[c] - mum1[c]) * gfz;
     face_vjp(2, add_half(wm1, dm1, real(1)), add_half(w0, d0, real(-1)), g, gamma, gm1, gLb, gRb);
     // A_{z0-1} from D = gL(z0-1/2)/2 - gR(z0-3/2)/2
     for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gLb[c] - real(0.5) * gRa[c];
     slope_vjp<LIM>(wm2, wm1, w0, slope_is_zero(dm1), D, Ap, Bt);
     // face z0+1/2
-    for (int c = 0; c < 5; ++c) g[c] = (mun[c] - mu0[c]) * p.idz;
+    for (int c = 0; c < 5; ++c) g[c] = (mun[c] - mu0[c]) * gfz;
     face_vjp(2, add_half(w0, d0, real(1)), add_half(w1, dz1, real(-1)), g, gamma, gm1, gLn, gRn);
     for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gLn[c] - real(0.5) * gRb[c];
     slope_vjp<LIM>(wm1, w0, w1, slope_is_zero(d0), D, Ac, Bc);
     for (int c = 0; c < 5; ++c) gRc[c] = gRb[c];
   }
+  stage_plane(z0 + 3);
 
   for (int k = z0; k < z1; ++k) {
     const int s0 = (k - z0) & 3, s1 = (k - z0 + 1) & 3, s2 = (k - z0 + 2) & 3, s3 = (k - z0 + 3) & 3;
-    load_w(k + 3, s3);
+    cp_async_wait<0>();
+    __syncthreads();  // ---- plane k+3 staged; the gather of plane k-1 is done
+
     load_mu(k);
     real mun2[5];
-    gload5(p.lam_out, n3, (long long)wrap(k + 2, nz) * plane + col, sdt, mun2);
-    __syncthreads();  // ---- plane k+3 and mu of plane k in shared memory
+    gload5(p.lam_out, n3, (long long)wrap(k + 2, nz) * plane + col, mun2);
+
+    // ---- limited slopes and face states of plane k along x and y, once per cell and axis -------
+    for (int t = tid; t < NSXP + NSY; t += ANT) {
+      bool zero = false;
+      if (t < NSX || t >= NSXP) {
+        Prim<real> wm, w0, wp;
+        if (t < NSXP) {
+          const int ly = t / NSXA, r = t - ly * NSXA;          // cell lx = r - 2
+          wm = ring_prim(S, s0, ly + 3, r);
+          w0 = ring_prim(S, s0, ly + 3, r + 1);
+          wp = ring_prim(S, s0, ly + 3, r + 2);
+        } else {
+          const int u = t - NSXP;
+          const int r = u / ABX, lx = u - r * ABX;             // cell ly = r - 2
+          wm = ring_prim(S, s0, r, lx + 3);
+          w0 = ring_prim(S, s0, r + 1, lx + 3);
+          wp = ring_prim(S, s0, r + 2, lx + 3);
+        }
+        const Prim<real> d = limited_slope<LIM>(wm, w0, wp);
+        const Prim<real> lo = add_half(w0, d, real(-1)), hi = add_half(w0, d, real(1));
+        S.u.st[0][t] = lo.r; S.u.st[1][t] = lo.vx; S.u.st[2][t] = lo.vy; S.u.st[3][t] = lo.vz;
+        S.u.st[4][t] = lo.p;
+        S.u.st[5][t] = hi.r; S.u.st[6][t] = hi.vx; S.u.st[7][t] = hi.vy; S.u.st[8][t] = hi.vz;
+        S.u.st[9][t] = hi.p;
+        zero = slope_is_zero(d);
+      }
+      const unsigned bits = __ballot_sync(0xffffffffu, zero);
+      if ((t & 31) == 0) S.zero[t >> 5] = bits;
+    }
+    convert_plane(s3);
 
     real gW[5];
     Prim<real> wk;   // own cell of plane k, kept for the primitive-recovery step
@@ -183,10 +285,10 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       wk = ring_prim(S, s0, ty + 3, tx + 3);
       const Prim<real> w1 = ring_prim(S, s1, ty + 3, tx + 3);
       const Prim<real> w2 = ring_prim(S, s2, ty + 3, tx + 3);
-      const Prim<real> w3 = ring_prim(S, s3, ty + 3, tx + 3);
+      const Prim<real> w3 = staged_prim(ty + 3, tx + 3);   // this thread's cell of plane k+3
       const Prim<real> dz2 = limited_slope<LIM>(w1, w2, w3);
       real g[5], gL2[5], gR2[5], D[5], An[5], Bn[5];
-      for (int c = 0; c < 5; ++c) g[c] = (mun2[c] - mun[c]) * p.idz;
+      for (int c = 0; c < 5; ++c) g[c] = (mun2[c] - mun[c]) * gfz;
       face_vjp(2, add_half(w1, dz1, real(1)), add_half(w2, dz2, real(-1)), g, gamma, gm1, gL2, gR2);
       for (int c = 0; c < 5; ++c) D[c] = real(0.5) * gL2[c] - real(0.5) * gRn[c];
       slope_vjp<LIM>(wk, w1, w2, slope_is_zero(dz1), D, An, Bn);
@@ -203,33 +305,10 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       }
       dz1 = dz2;
     }
+    cp_async_wait<0>();
+    __syncthreads();  // ---- face states, mu of plane k and ring slot of plane k+3 ready
 
-    // ---- limited slopes and face states of plane k along x and y, once per cell and axis -------
-    for (int t = tid; t < NSXP + NSY; t += ANT) {
-      Prim<real> wm, w0, wp;
-      if (t < NSXP) {
-        if (t >= NSX) continue;
-        const int ly = t / NSXA, r = t - ly * NSXA;          // cell lx = r - 2
-        wm = ring_prim(S, s0, ly + 3, r);
-        w0 = ring_prim(S, s0, ly + 3, r + 1);
-        wp = ring_prim(S, s0, ly + 3, r + 2);
-      } else {
-        const int u = t - NSXP;
-        const int r = u / ABX, lx = u - r * ABX;             // cell ly = r - 2
-        wm = ring_prim(S, s0, r, lx + 3);
-        w0 = ring_prim(S, s0, r + 1, lx + 3);
-        wp = ring_prim(S, s0, r + 2, lx + 3);
-      }
-      const Prim<real> d = limited_slope<LIM>(wm, w0, wp);
-      const Prim<real> lo = add_half(w0, d, real(-1)), hi = add_half(w0, d, real(1));
-      S.u.st[0][t] = lo.r; S.u.st[1][t] = lo.vx; S.u.st[2][t] = lo.vy; S.u.st[3][t] = lo.vz;
-      S.u.st[4][t] = lo.p;
-      S.u.st[5][t] = hi.r; S.u.st[6][t] = hi.vx; S.u.st[7][t] = hi.vy; S.u.st[8][t] = hi.vz;
-      S.u.st[9][t] = hi.p;
-      S.zero[t] = slope_is_zero(d) ? 1 : 0;
-    }
-    __syncthreads();  // ---- face states ready
-
+    if (k + 1 < z1) stage_plane(k + 4);
     // ---- x and y face VJPs of plane k ------------------------------------------------------------
     for (int f = tid; f < NFXP + NFY; f += ANT) {
       real g[5], gL[5], gR[5];
@@ -237,14 +316,14 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
         if (f >= NFX) continue;
         const int ly = f / NFXA, q = f - ly * NFXA;   // between cells lx = q-2 and q-1
 #pragma unroll
-        for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][ly + 2][q + 1] - S.mu[c][ly + 2][q]) * p.idx;
+        for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][ly + 2][q + 1] - S.mu[c][ly + 2][q]) * gfx;
         const int i = ly * NSXA + q;
         face_vjp(0, st_prim(S, 5, i), st_prim(S, 0, i + 1), g, gamma, gm1, gL, gR);
       } else {
         const int fy = f - NFXP;
         const int q = fy / ABX, lx = fy - q * ABX;    // between cells ly = q-2 and q-1
 #pragma unroll
-        for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][q + 1][lx + 2] - S.mu[c][q][lx + 2]) * p.idy;
+        for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][q + 1][lx + 2] - S.mu[c][q][lx + 2]) * gfy;
         const int i = NSXP + q * ABX + lx;
         face_vjp(1, st_prim(S, 5, i), st_prim(S, 0, i + ABX), g, gamma, gm1, gL, gR);
       }
@@ -264,7 +343,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
         for (int c = 0; c < 5; ++c)
           D[c] = real(0.5) * S.face[c][ly * NFXA + r + 1] - real(0.5) * S.face[5 + c][ly * NFXA + r];
         slope_vjp<LIM>(ring_prim(S, s0, sy, r + 1), ring_prim(S, s0, sy, r + 2),
-                       ring_prim(S, s0, sy, r + 3), S.zero[ly * NSXA + r + 1] != 0, D, A, B);
+                       ring_prim(S, s0, sy, r + 3), zero_bit(S, ly * NSXA + r + 1), D, A, B);
       } else {
         const int ey = e - NCXP;
         const int r = ey / ABX, lx = ey - r * ABX;    // cell ly = r - 1
@@ -274,7 +353,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
           D[c] = real(0.5) * S.face[c][NFXP + (r + 1) * ABX + lx] -
                  real(0.5) * S.face[5 + c][NFXP + r * ABX + lx];
         slope_vjp<LIM>(ring_prim(S, s0, r + 1, sx), ring_prim(S, s0, r + 2, sx),
-                       ring_prim(S, s0, r + 3, sx), S.zero[NSXP + (r + 1) * ABX + lx] != 0, D, A, B);
+                       ring_prim(S, s0, r + 3, sx), zero_bit(S, NSXP + (r + 1) * ABX + lx), D, A, B);
       }
 #pragma unroll
       for (int c = 0; c < 5; ++c) { S.u.cell[c][e] = A[c]; S.u.cell[5 + c][e] = B[c]; }
@@ -307,7 +386,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       const long long idx = (long long)k * plane + col;
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        real v = p.c1 * __ldg(p.lam_out + c * n3 + idx) + gU[c];
+        real v = p.c1 * S.mu[c][ty + 2][tx + 2] + gU[c];
         if (p.extra) v += p.c2 * __ldg(p.extra + c * n3 + idx);
         if (p.extra2) v += p.c3 * __ldg(p.extra2 + c * n3 + idx);
         p.lam_in[c * n3 + idx] = v;
