@@ -28,6 +28,9 @@ constexpr int NYS = BX * (BY + 2);   // cells with a y slope: ly = -1 .. BY
 constexpr int NXF = (BX + 1) * BY;   // x faces of a plane tile
 constexpr int NYF = BX * (BY + 1);   // y faces of a plane tile
 constexpr int NFORCE = BY * 9;       // forcing row factors: row x (n_x = 0, 1, 2) x component
+// The y items of the per-plane slope and face loops start on a warp boundary, so that no warp
+// takes both branches of a loop step.
+constexpr int NXSP = (NXS + 31) / 32 * 32, NXFP = (NXF + 31) / 32 * 32;
 
 // Staging plane: rows of conserved variables copied in 16-byte chunks of SCE elements, from
 // x0 - SHALO to x0 + BX + SHALO (SHALO >= 2, a multiple of SCE); prim column sx is staging
@@ -40,18 +43,38 @@ template <typename real> struct Staging {
   static constexpr int SOFF = SHALO - 2;
 };
 
+// Four components of a primitive state or flux in one 16-byte-aligned word group, so that a
+// shared-memory access moves them with one 128-bit instruction (two for float64); the fifth
+// component sits in a separate array.
+template <typename real> struct alignas(16) Q4 { real a, b, c, d; };
+
+template <typename real>
+__device__ __forceinline__ Prim<real> qprim(const Q4<real>& q, real p) {
+  return Prim<real>{q.a, q.b, q.c, q.d, p};
+}
+template <typename real>
+__device__ __forceinline__ void qstore(Q4<real>& q, real& s, const Prim<real>& w) {
+  q = Q4<real>{w.r, w.vx, w.vy, w.vz};
+  s = w.p;
+}
+
 template <typename real> struct StageSmem {
   real stg[5][HY][Staging<real>::SROW];   // conserved variables of the plane in flight
   real tz[4];                // forcing: z twiddles of the plane in flight (staged with it)
+  Q4<real> w4[3][HY][HX];    // primitive planes ring (k, k+1, k+2), two-cell x/y halo: rho, v
+  Q4<real> xm4[BY][BX + 2];  // x face states W - dW/2 of cells lx = -1..BX (index lx + 1)
+  Q4<real> xp4[BY][BX + 2];  //                W + dW/2
+  Q4<real> ym4[BY + 2][BX];  // y face states of cells ly = -1..BY (index ly + 1)
+  Q4<real> yp4[BY + 2][BX];
+  Q4<real> fx4[BY][BX + 1];  // x-face fluxes of the current plane: mass and momentum
+  Q4<real> fy4[BY + 1][BX];  // y-face fluxes
+  real wp[3][HY][HX];        // pressure of the ring planes
+  real xmp[BY][BX + 2], xpp[BY][BX + 2];   // pressure of the face states
+  real ymp[BY + 2][BX], ypp[BY + 2][BX];
+  real fxe[BY][BX + 1];      // energy fluxes
+  real fye[BY + 1][BX];
   real ah[96];               // forcing: normalised OU table
   real tyt[BY][4];           // forcing: y twiddles of the tile's rows
-  real w[3][5][HY][HX];      // primitive planes ring (k, k+1, k+2), two-cell x/y halo
-  real xm[5][BY][BX + 2];    // x face states W - dW/2 of cells lx = -1..BX (index lx + 1)
-  real xp[5][BY][BX + 2];    //                W + dW/2
-  real ym[5][BY + 2][BX];    // y face states of cells ly = -1..BY (index ly + 1)
-  real yp[5][BY + 2][BX];
-  real fx[5][BY][BX + 1];    // x-face fluxes of the current plane
-  real fy[5][BY + 1][BX];    // y-face fluxes of the current plane
   real fB[BY][3][3][2];      // forcing: B[row][n_x][component] = sum over modes with that n_x
   int xs[HX];                // wrapped global x of each smem column
   int ys[HY];                // wrapped global y of each smem row
@@ -62,8 +85,7 @@ template <typename real> struct StageSmem {
 template <typename real>
 __device__ __forceinline__ Prim<real> smem_prim(const StageSmem<real>& S, int slot, int sy,
                                                 int sx) {
-  return Prim<real>{S.w[slot][0][sy][sx], S.w[slot][1][sy][sx], S.w[slot][2][sy][sx],
-                    S.w[slot][3][sy][sx], S.w[slot][4][sy][sx]};
+  return qprim(S.w4[slot][sy][sx], S.wp[slot][sy][sx]);
 }
 
 template <typename real>
@@ -73,16 +95,9 @@ __device__ __forceinline__ Prim<real> load_prim(const real* __restrict__ U, long
                       __ldg(U + 3 * n3 + idx), __ldg(U + 4 * n3 + idx), gm1);
 }
 
-#define DH_STORE_PRIM(arr, i0, i1, v)                                                   \
-  do {                                                                                  \
-    arr[0][i0][i1] = (v).r; arr[1][i0][i1] = (v).vx; arr[2][i0][i1] = (v).vy;           \
-    arr[3][i0][i1] = (v).vz; arr[4][i0][i1] = (v).p;                                    \
-  } while (0)
-#define DH_LOAD_PRIM(arr, i0, i1)                                                       \
-  Prim<real>{arr[0][i0][i1], arr[1][i0][i1], arr[2][i0][i1], arr[3][i0][i1], arr[4][i0][i1]}
-
+// float32: three CTAs per SM (shared memory allows three; registers are capped to match)
 template <typename real, int STAGE, int LIM>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(NTHREADS, sizeof(real) == 4 ? 3 : 1)
 stage_kernel(const StageArgs<real> p, const int zchunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageSmem<real>& S = *reinterpret_cast<StageSmem<real>*>(smem_raw);
@@ -156,18 +171,17 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
     }
     cp_async_commit();
   };
-  // primitive recovery of the staged plane into a ring slot
+  // primitive recovery of the staged plane into a ring slot.  Without forcing the cells are
+  // taken from the last thread down, so that the warps with a third slope item get one cell
+  // fewer; with forcing the last warps build the row factors and take the fewer cells instead.
+  const int conv0 = forcing ? tid : NTHREADS - 1 - tid;
   auto convert_plane = [&](int slot) {
-    for (int c = tid; c < HX * HY; c += NTHREADS) {
+    for (int c = conv0; c < HX * HY; c += NTHREADS) {
       const int sy = c / HX, sx = c - sy * HX;
       const int q = sx + ST::SOFF;
-      const Prim<real> w = cons_to_prim(S.stg[0][sy][q], S.stg[1][sy][q], S.stg[2][sy][q],
-                                        S.stg[3][sy][q], S.stg[4][sy][q], gm1);
-      S.w[slot][0][sy][sx] = w.r;
-      S.w[slot][1][sy][sx] = w.vx;
-      S.w[slot][2][sy][sx] = w.vy;
-      S.w[slot][3][sy][sx] = w.vz;
-      S.w[slot][4][sy][sx] = w.p;
+      qstore(S.w4[slot][sy][sx], S.wp[slot][sy][sx],
+             cons_to_prim(S.stg[0][sy][q], S.stg[1][sy][q], S.stg[2][sy][q], S.stg[3][sy][q],
+                          S.stg[4][sy][q], gm1));
     }
   };
 
@@ -176,12 +190,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
     for (int c = tid; c < HX * HY; c += NTHREADS) {
       const int sy = c / HX, sx = c - sy * HX;
       const long long idx = zoff + (long long)S.ys[sy] * nx + S.xs[sx];
-      const Prim<real> w = load_prim(p.U, n3, idx, gm1);
-      S.w[slot][0][sy][sx] = w.r;
-      S.w[slot][1][sy][sx] = w.vx;
-      S.w[slot][2][sy][sx] = w.vy;
-      S.w[slot][3][sy][sx] = w.vz;
-      S.w[slot][4][sy][sx] = w.p;
+      qstore(S.w4[slot][sy][sx], S.wp[slot][sy][sx], load_prim(p.U, n3, idx, gm1));
     }
   };
 
@@ -220,22 +229,23 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
 
     convert_plane(s2);
     // limited slopes and face states of plane k, once per cell and axis
-    for (int t = tid; t < NXS + NYS; t += NTHREADS) {
-      if (t < NXS) {
+    for (int t = tid; t < NXSP + NYS; t += NTHREADS) {
+      if (t < NXSP) {
+        if (t >= NXS) continue;
         const int ly = t / (BX + 2), r = t - ly * (BX + 2);
         const int sy = ly + 2;
         const Prim<real> w1 = smem_prim(S, s0, sy, r + 1);
         const Prim<real> d = limited_slope<LIM>(smem_prim(S, s0, sy, r), w1, smem_prim(S, s0, sy, r + 2));
-        DH_STORE_PRIM(S.xm, ly, r, add_half(w1, d, real(-1)));
-        DH_STORE_PRIM(S.xp, ly, r, add_half(w1, d, real(1)));
+        qstore(S.xm4[ly][r], S.xmp[ly][r], add_half(w1, d, real(-1)));
+        qstore(S.xp4[ly][r], S.xpp[ly][r], add_half(w1, d, real(1)));
       } else {
-        const int u = t - NXS;
+        const int u = t - NXSP;
         const int r = u / BX, lx = u - r * BX;
         const int sx = lx + 2;
         const Prim<real> w1 = smem_prim(S, s0, r + 1, sx);
         const Prim<real> d = limited_slope<LIM>(smem_prim(S, s0, r, sx), w1, smem_prim(S, s0, r + 2, sx));
-        DH_STORE_PRIM(S.ym, r, lx, add_half(w1, d, real(-1)));
-        DH_STORE_PRIM(S.yp, r, lx, add_half(w1, d, real(1)));
+        qstore(S.ym4[r][lx], S.ymp[r][lx], add_half(w1, d, real(-1)));
+        qstore(S.yp4[r][lx], S.ypp[r][lx], add_half(w1, d, real(1)));
       }
     }
     if (forcing && tid >= NTHREADS - NFORCE) {
@@ -276,19 +286,22 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
     }
 
     // every x and y face of plane k, once
-    for (int f = tid; f < NXF + NYF; f += NTHREADS) {
+    for (int f = tid; f < NXFP + NYF; f += NTHREADS) {
       real F[5];
-      if (f < NXF) {
+      if (f < NXFP) {
+        if (f >= NXF) continue;
         const int ly = f / (BX + 1), a = f - ly * (BX + 1);
-        face_flux(0, DH_LOAD_PRIM(S.xp, ly, a), DH_LOAD_PRIM(S.xm, ly, a + 1), gamma, gm1, F);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) S.fx[c][ly][a] = F[c];
+        face_flux(0, qprim(S.xp4[ly][a], S.xpp[ly][a]), qprim(S.xm4[ly][a + 1], S.xmp[ly][a + 1]),
+                  gamma, gm1, F);
+        S.fx4[ly][a] = Q4<real>{F[0], F[1], F[2], F[3]};
+        S.fxe[ly][a] = F[4];
       } else {
-        const int g = f - NXF;
+        const int g = f - NXFP;
         const int a = g / BX, lx = g - a * BX;
-        face_flux(1, DH_LOAD_PRIM(S.yp, a, lx), DH_LOAD_PRIM(S.ym, a + 1, lx), gamma, gm1, F);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) S.fy[c][a][lx] = F[c];
+        face_flux(1, qprim(S.yp4[a][lx], S.ypp[a][lx]), qprim(S.ym4[a + 1][lx], S.ymp[a + 1][lx]),
+                  gamma, gm1, F);
+        S.fy4[a][lx] = Q4<real>{F[0], F[1], F[2], F[3]};
+        S.fye[a][lx] = F[4];
       }
     }
     __syncthreads();  // ---- fluxes ready
@@ -302,14 +315,16 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
           un[c] = __ldg(p.U0 + c * n3 + idx);
         }
       }
+      const Q4<real> fxr = S.fx4[ty][tx + 1], fxl = S.fx4[ty][tx];
+      const Q4<real> fyr = S.fy4[ty + 1][tx], fyl = S.fy4[ty][tx];
+      const real fxh[4] = {fxr.a, fxr.b, fxr.c, fxr.d}, fxo[4] = {fxl.a, fxl.b, fxl.c, fxl.d};
+      const real fyh[4] = {fyr.a, fyr.b, fyr.c, fyr.d}, fyo[4] = {fyl.a, fyl.b, fyl.c, fyl.d};
       if constexpr (std::is_same<real, float>::value) {
         // components (0,1) and (2,3) as packed pairs, 4 alone
 #pragma unroll
         for (int c = 0; c < 4; c += 2) {
-          const float2 dfx = p_sub(f2(S.fx[c][ty][tx + 1], S.fx[c + 1][ty][tx + 1]),
-                                   f2(S.fx[c][ty][tx], S.fx[c + 1][ty][tx]));
-          const float2 dfy = p_sub(f2(S.fy[c][ty + 1][tx], S.fy[c + 1][ty + 1][tx]),
-                                   f2(S.fy[c][ty][tx], S.fy[c + 1][ty][tx]));
+          const float2 dfx = p_sub(f2(fxh[c], fxh[c + 1]), f2(fxo[c], fxo[c + 1]));
+          const float2 dfy = p_sub(f2(fyh[c], fyh[c + 1]), f2(fyo[c], fyo[c + 1]));
           const float2 dfz = p_sub(f2(fz_hi[c], fz_hi[c + 1]), f2(fz_lo[c], fz_lo[c + 1]));
           float2 L = p_mul(dfx, f2s(-p.idx));
           L = p_fma(dfy, f2s(-p.idy), L);
@@ -320,16 +335,18 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
           u[c + 1] = v.y;
         }
         {
-          float L = -((S.fx[4][ty][tx + 1] - S.fx[4][ty][tx]) * p.idx);
-          L -= (S.fy[4][ty + 1][tx] - S.fy[4][ty][tx]) * p.idy;
+          float L = -((S.fxe[ty][tx + 1] - S.fxe[ty][tx]) * p.idx);
+          L -= (S.fye[ty + 1][tx] - S.fye[ty][tx]) * p.idy;
           L -= (fz_hi[4] - fz_lo[4]) * p.idz;
           u[4] = STAGE == 1 ? uin[4] + dt * L : w0 * un[4] + w1 * (uin[4] + dt * L);
         }
       } else {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-          real L = -((S.fx[c][ty][tx + 1] - S.fx[c][ty][tx]) * p.idx);
-          L -= (S.fy[c][ty + 1][tx] - S.fy[c][ty][tx]) * p.idy;
+          const real fxd = c < 4 ? fxh[c < 4 ? c : 0] - fxo[c < 4 ? c : 0] : S.fxe[ty][tx + 1] - S.fxe[ty][tx];
+          const real fyd = c < 4 ? fyh[c < 4 ? c : 0] - fyo[c < 4 ? c : 0] : S.fye[ty + 1][tx] - S.fye[ty][tx];
+          real L = -(fxd * p.idx);
+          L -= fyd * p.idy;
           L -= (fz_hi[c] - fz_lo[c]) * p.idz;
           if (STAGE == 1) u[c] = uin[c] + dt * L;
           else u[c] = w0 * un[c] + w1 * (uin[c] + dt * L);
