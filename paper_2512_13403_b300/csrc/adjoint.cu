@@ -145,21 +145,23 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       S.w[slot][4][sy][sx] = w.p;
     }
   };
-  // cp.async of the conserved variables of plane k into the staging plane (one commit group)
+  // cp.async of the conserved variables of plane k into the staging plane (one commit group);
+  // each item is one chunk (or cell) position with its five fields
   auto stage_plane = [&](int k) {
     const long long zoff = (long long)wrap(k, nz) * plane;
     if (vec) {
-      for (int c = tid; c < 5 * WY * ST::NCH; c += ANT) {
-        const int f = c / (WY * ST::NCH), r = c - f * (WY * ST::NCH);
-        const int sy = r / ST::NCH, j = r - sy * ST::NCH;
-        cp_async16(&S.stg[f][sy][ST::SCE * j], p.U + f * n3 + zoff + (long long)S.ys[sy] * nx + S.cx[j]);
+      for (int c = tid; c < WY * ST::NCH; c += ANT) {
+        const int sy = c / ST::NCH, j = c - sy * ST::NCH;
+        const real* g = p.U + zoff + (long long)S.ys[sy] * nx + S.cx[j];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) cp_async16(&S.stg[f][sy][ST::SCE * j], g + f * n3);
       }
     } else {
-      for (int c = tid; c < 5 * WY * WX; c += ANT) {
-        const int f = c / (WY * WX), r = c - f * (WY * WX);
-        const int sy = r / WX, sx = r - sy * WX;
-        cp_async_elem(&S.stg[f][sy][sx + ST::SOFF],
-                      p.U + f * n3 + zoff + (long long)S.ys[sy] * nx + S.xs[sx]);
+      for (int c = tid; c < WY * WX; c += ANT) {
+        const int sy = c / WX, sx = c - sy * WX;
+        const real* g = p.U + zoff + (long long)S.ys[sy] * nx + S.xs[sx];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) cp_async_elem(&S.stg[f][sy][sx + ST::SOFF], g + f * n3);
       }
     }
     cp_async_commit();
@@ -184,11 +186,11 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
   // cp.async of lam_out of plane k (x/y halo 2) into mu (one commit group)
   auto load_mu = [&](int k) {
     const long long zoff = (long long)wrap(k, nz) * plane;
-    for (int c = tid; c < 5 * MXH * MYH; c += ANT) {
-      const int f = c / (MXH * MYH), r = c - f * (MXH * MYH);
-      const int sy = r / MXH, sx = r - sy * MXH;
-      cp_async_elem(&S.mu[f][sy][sx],
-                    p.lam_out + f * n3 + zoff + (long long)S.ys[sy + 1] * nx + S.xs[sx + 1]);
+    for (int c = tid; c < MXH * MYH; c += ANT) {
+      const int sy = c / MXH, sx = c - sy * MXH;
+      const real* g = p.lam_out + zoff + (long long)S.ys[sy + 1] * nx + S.xs[sx + 1];
+#pragma unroll
+      for (int f = 0; f < 5; ++f) cp_async_elem(&S.mu[f][sy][sx], g + f * n3);
     }
     cp_async_commit();
   };

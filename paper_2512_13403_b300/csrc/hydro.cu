@@ -154,19 +154,23 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
 #pragma unroll
       for (int i = 0; i < 4; i += ST::SCE) cp_async16(&S.tz[i], t + i);
     }
+    // each item is one chunk (or cell) position with its five fields
     if (vec) {
-      for (int c = tid; c < 5 * HY * ST::NCH; c += NTHREADS) {
-        const int f = c / (HY * ST::NCH), r = c - f * (HY * ST::NCH);
-        const int sy = r / ST::NCH, j = r - sy * ST::NCH;
-        cp_async16(&S.stg[f][sy][ST::SCE * j], p.U + f * n3 + zoff + (long long)S.ys[sy] * nx + S.cx[j]);
+      for (int c = tid; c < HY * ST::NCH; c += NTHREADS) {
+        const int sy = c / ST::NCH, j = c - sy * ST::NCH;
+        const real* g = p.U + zoff + (long long)S.ys[sy] * nx + S.cx[j];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) cp_async16(&S.stg[f][sy][ST::SCE * j], g + f * n3);
       }
     } else {
-      for (int c = tid; c < 5 * HY * HX; c += NTHREADS) {
-        const int f = c / (HY * HX), r = c - f * (HY * HX);
-        const int sy = r / HX, sx = r - sy * HX;
-        const real* g = p.U + f * n3 + zoff + (long long)S.ys[sy] * nx + S.xs[sx];
-        if constexpr (sizeof(real) == 4) cp_async4(&S.stg[f][sy][sx + ST::SOFF], g);
-        else cp_async8(&S.stg[f][sy][sx + ST::SOFF], g);
+      for (int c = tid; c < HY * HX; c += NTHREADS) {
+        const int sy = c / HX, sx = c - sy * HX;
+        const real* g = p.U + zoff + (long long)S.ys[sy] * nx + S.xs[sx];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+          if constexpr (sizeof(real) == 4) cp_async4(&S.stg[f][sy][sx + ST::SOFF], g + f * n3);
+          else cp_async8(&S.stg[f][sy][sx + ST::SOFF], g + f * n3);
+        }
       }
     }
     cp_async_commit();
