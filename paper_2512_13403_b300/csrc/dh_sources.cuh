@@ -14,28 +14,47 @@ namespace dh {
 // differenced separately: hi - hi is exact when the two lie within a factor 2 of each other
 // (Sterbenz) and otherwise rounds below an ulp of the result, so the float-float difference is
 // not needed.  For float64 the difference is taken in float-float.
-template <typename real>
-__device__ __forceinline__ void potential_gradient(const float* __restrict__ phi, int nx, int ny,
-                                                   int nz, int i, int j, int k, real i2h, real& g0,
-                                                   real& g1, real& g2) {
+//
+// The 12 float-float words of the potential that g = -grad phi at cell (i, j, k) needs:
+// (hi, lo) of the +x, -x, +y, -y, +z, -z neighbours (periodic).
+__device__ __forceinline__ void potential_gradient_load(const float* __restrict__ phi, int nx, int ny,
+                                                        int nz, int i, int j, int k, float v[12]) {
   const unsigned plane = (unsigned)nx * (unsigned)ny, n = plane * (unsigned)nz;
   const unsigned q = ((unsigned)k * (unsigned)ny + (unsigned)j) * (unsigned)nx + (unsigned)i;
   const unsigned xm = i == 0 ? q + nx - 1 : q - 1, xp = i == nx - 1 ? q + 1 - nx : q + 1;
   const unsigned ym = j == 0 ? q + plane - nx : q - nx, yp = j == ny - 1 ? q + nx - plane : q + nx;
   const unsigned zm = k == 0 ? q + n - plane : q - plane, zp = k == nz - 1 ? q + plane - n : q + plane;
   const float* __restrict__ lo = phi + n;
+  v[0] = phi[xp]; v[1] = lo[xp]; v[2] = phi[xm]; v[3] = lo[xm];
+  v[4] = phi[yp]; v[5] = lo[yp]; v[6] = phi[ym]; v[7] = lo[ym];
+  v[8] = phi[zp]; v[9] = lo[zp]; v[10] = phi[zm]; v[11] = lo[zm];
+}
+
+// g from the words of potential_gradient_load.
+template <typename real>
+__device__ __forceinline__ void potential_gradient_eval(const float v[12], real i2h, real& g0,
+                                                        real& g1, real& g2) {
   if constexpr (std::is_same<real, float>::value) {
-    g0 = -((phi[xp] - phi[xm]) + (lo[xp] - lo[xm])) * i2h;
-    g1 = -((phi[yp] - phi[ym]) + (lo[yp] - lo[ym])) * i2h;
-    g2 = -((phi[zp] - phi[zm]) + (lo[zp] - lo[zm])) * i2h;
+    g0 = -((v[0] - v[2]) + (v[1] - v[3])) * i2h;
+    g1 = -((v[4] - v[6]) + (v[5] - v[7])) * i2h;
+    g2 = -((v[8] - v[10]) + (v[9] - v[11])) * i2h;
   } else {
-    const ff2 dx = ff_sub(ff2{phi[xp], lo[xp]}, ff2{phi[xm], lo[xm]});
-    const ff2 dy = ff_sub(ff2{phi[yp], lo[yp]}, ff2{phi[ym], lo[ym]});
-    const ff2 dz = ff_sub(ff2{phi[zp], lo[zp]}, ff2{phi[zm], lo[zm]});
+    const ff2 dx = ff_sub(ff2{v[0], v[1]}, ff2{v[2], v[3]});
+    const ff2 dy = ff_sub(ff2{v[4], v[5]}, ff2{v[6], v[7]});
+    const ff2 dz = ff_sub(ff2{v[8], v[9]}, ff2{v[10], v[11]});
     g0 = -((real)dx.hi + (real)dx.lo) * i2h;
     g1 = -((real)dy.hi + (real)dy.lo) * i2h;
     g2 = -((real)dz.hi + (real)dz.lo) * i2h;
   }
+}
+
+template <typename real>
+__device__ __forceinline__ void potential_gradient(const float* __restrict__ phi, int nx, int ny,
+                                                   int nz, int i, int j, int k, real i2h, real& g0,
+                                                   real& g1, real& g2) {
+  float v[12];
+  potential_gradient_load(phi, nx, ny, nz, i, j, k, v);
+  potential_gradient_eval(v, i2h, g0, g1, g2);
 }
 
 // Forced-mode table of Sec. 3.1.1 as compile-time data: the half-space of integer n with

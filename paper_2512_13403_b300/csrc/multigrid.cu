@@ -1136,8 +1136,23 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
   __shared__ unsigned s_skip;
   __shared__ real red[8];
   __shared__ real fB[2][GS_TY][3][3][2];   // double-buffered by plane parity
+  // forcing tables of the CTA: the OU table, the y twiddles of its rows and the z twiddles of
+  // its planes, loaded once so that the per-plane row factors wait on no global load
+  __shared__ real s_ah[96], s_ty[GS_TY][4], s_tz[GS_ZC][4];
   const int tid = threadIdx.x;
+  const int z0 = blockIdx.z * GS_ZC, z1 = z0 + GS_ZC < nz ? z0 + GS_ZC : nz;
   if (tid == 0) s_skip = *((volatile unsigned*)&rec->flags) & FATAL_FLAGS;
+  if (forcing) {
+    if (tid < 96) s_ah[tid] = __ldg(ah + tid);
+    if (tid >= 96 && tid < 96 + 4 * GS_TY) {
+      const int ly = (tid - 96) >> 2, q = (tid - 96) & 3;
+      s_ty[ly][q] = __ldg(tw1 + 4 * ((blockIdx.y * GS_TY + ly) % ny) + q);
+    }
+    if (tid >= 128 && tid < 128 + 4 * GS_ZC) {
+      const int lz = (tid - 128) >> 2, q = (tid - 128) & 3;
+      if (z0 + lz < nz) s_tz[lz][q] = __ldg(tw2 + 4 * (z0 + lz) + q);
+    }
+  }
   __syncthreads();
   if (s_skip) return;
   const real dt = (real)*dtp;
@@ -1145,7 +1160,6 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
   const long long n3 = plane * nz;
   const int tx = tid % GS_TX, ty = tid / GS_TX;
   const int i = blockIdx.x * GS_TX + tx, j = blockIdx.y * GS_TY + ty;
-  const int z0 = blockIdx.z * GS_ZC, z1 = z0 + GS_ZC < nz ? z0 + GS_ZC : nz;
   const bool active = i < nx && j < ny;
   real twx[4] = {real(0), real(0), real(0), real(0)};
   if (forcing && active) {
@@ -1154,21 +1168,29 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
   }
   real tmin = real(INFINITY);
   unsigned flags = 0;
+  // the state and potential words of the next plane are loaded a plane ahead
+  real un[5];
+  float pv[12];
+  if (active) {
+    const long long q = (long long)z0 * plane + (long long)j * nx + i;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) un[c] = U[c * n3 + q];
+    potential_gradient_load(phi, nx, ny, nz, i, j, z0, pv);
+  }
   for (int k = z0; k < z1; ++k) {
     const int buf = (k - z0) & 1;
     if (forcing) {
       if (tid < GS_NF) {
         const int ly = tid / 9, rem = tid - 9 * ly;
         const int nxsel = rem / 3, c = rem - 3 * nxsel;
-        const int yrow = (blockIdx.y * GS_TY + ly) % ny;
         real tyv[4], tzv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          tyv[q] = __ldg(tw1 + 4 * yrow + q);
-          tzv[q] = __ldg(tw2 + 4 * k + q);
+          tyv[q] = s_ty[ly][q];
+          tzv[q] = s_tz[k - z0][q];
         }
         real bre = real(0), bim = real(0);
-        row_factor<real, 0>(ah, nxsel, c, tyv, tzv, bre, bim);
+        row_factor<real, 0>(s_ah, nxsel, c, tyv, tzv, bre, bim);
         fB[buf][ly][nxsel][c][0] = bre;
         fB[buf][ly][nxsel][c][1] = bim;
       }
@@ -1177,8 +1199,16 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
     if (!active) continue;
     const long long q = (long long)k * plane + (long long)j * nx + i;
     real u[5];
+    float pw[12];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) u[c] = U[c * n3 + q];
+    for (int c = 0; c < 5; ++c) u[c] = un[c];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) pw[c] = pv[c];
+    if (k + 1 < z1) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) un[c] = U[c * n3 + q + plane];
+      potential_gradient_load(phi, nx, ny, nz, i, j, k + 1, pv);
+    }
     if (forcing) {
       // a = 2 Re sum_{n_x} B_{n_x} exp(2 pi i n_x x~)  (Sec. 3.1.1)
       real a[3];
@@ -1196,7 +1226,7 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
     {
       // g = -grad phi by central differences (Sec. 5), momentum taken before the kick
       real g0, g1, g2;
-      potential_gradient(phi, nx, ny, nz, i, j, k, i2h, g0, g1, g2);
+      potential_gradient_eval(pw, i2h, g0, g1, g2);
       const real e = (u[1] * g0 + u[2] * g1 + u[3] * g2) * dt;
       u[1] = u[1] + u[0] * g0 * dt;
       u[2] = u[2] + u[0] * g1 * dt;
