@@ -669,71 +669,112 @@ template cudaError_t launch_cfl_reduce<double>(const double*, int, int, int, dou
 
 // ---------------------------------------------------------------------------------------------
 // Conserved totals in float64 with a fixed reduction order (two passes, no atomics).
-constexpr int TOTALS_BLOCKS = 296, TOTALS_THREADS = 256;
+// Conserved totals: a fixed grid of 8 CTAs per SM on 148 SMs, each thread summing a strided
+// share, then fixed-order reductions, so the result is the same on every call.
+constexpr int TOTALS_BLOCKS = 148 * 8, TOTALS_THREADS = 256;
 int totals_blocks() { return TOTALS_BLOCKS; }
 
+// Sum over the CTA of five doubles per thread (warp shuffles, then the warps in order);
+// thread 0 writes them to partials[blockIdx.x * 5 + f].
+__device__ __forceinline__ void totals_block_store(double s[5], double* __restrict__ partials) {
+  __shared__ double red[TOTALS_THREADS / 32][5];
+#pragma unroll
+  for (int f = 0; f < 5; ++f)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[f] += __shfl_xor_sync(0xffffffffu, s[f], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int f = 0; f < 5; ++f) red[threadIdx.x >> 5][f] = s[f];
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double t = 0.0;
+    for (int w = 0; w < TOTALS_THREADS / 32; ++w) t += red[w][threadIdx.x];
+    partials[blockIdx.x * 5 + threadIdx.x] = t;
+  }
+}
+
 template <typename real>
-__global__ void totals_partial_kernel(const real* __restrict__ U, long long n3,
-                                      double* __restrict__ partials) {
-  __shared__ double red[5][TOTALS_THREADS];
+__global__ void __launch_bounds__(TOTALS_THREADS)
+totals_partial_kernel(const real* __restrict__ U, long long n3, double* __restrict__ partials) {
   double s[5] = {0, 0, 0, 0, 0};
-  const long long per = (n3 + gridDim.x - 1) / gridDim.x;
-  const long long b0 = blockIdx.x * per;
-  const long long b1 = b0 + per < n3 ? b0 + per : n3;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if constexpr (std::is_same<real, float>::value) {
-    // float32 state: each thread adds 8 values per field in compensated float32 (TwoSum: the
-    // chunk's sum to a few eps32^2 of its magnitude), then the two words in float64 -- a
-    // quarter of the float64 operations, which bound this reduction on this part
+    // float32 state: 16-byte loads (when every field starts 16-byte aligned); each thread adds
+    // 8 values per field in compensated float32 (TwoSum: the chunk's sum to a few eps32^2 of
+    // its magnitude) and the chunks into a float-float running sum (accurate double-word
+    // addition, relative error a few eps32^2 per chunk); float64 only at the end, since
+    // float64 operations are scarce on this part
+    const bool vec = (n3 % 4 == 0) && (((unsigned long long)U & 15ull) == 0);
+    long long done = 0;   // elements covered by the vector loop
+    ff2 tot[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) tot[f] = ff2{0.0f, 0.0f};
+    if (vec) {
+      const long long n4 = n3 / 4;
+      const float4* __restrict__ U4 = reinterpret_cast<const float4*>(U);
+      for (long long i = t0; i < n4; i += 2 * stride) {
+        const bool two = i + stride < n4;
+        float4 a[5], b[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+          a[f] = __ldg(U4 + f * n4 + i);
+          b[f] = two ? __ldg(U4 + f * n4 + i + stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+          ff2 acc{0.0f, 0.0f};
+          ff_acc(acc, a[f].x); ff_acc(acc, a[f].y); ff_acc(acc, a[f].z); ff_acc(acc, a[f].w);
+          ff_acc(acc, b[f].x); ff_acc(acc, b[f].y); ff_acc(acc, b[f].z); ff_acc(acc, b[f].w);
+          tot[f] = ff_add(tot[f], ff_two_sum(acc.hi, acc.lo));
+        }
+      }
+      done = n3;
+    }
     constexpr int CH = 8;
-    for (long long i = b0 + threadIdx.x; i < b1; i += (long long)CH * blockDim.x) {
+    for (long long i = done + t0; i < n3; i += (long long)CH * stride) {
       ff2 acc[5];
 #pragma unroll
       for (int f = 0; f < 5; ++f) acc[f] = ff2{0.0f, 0.0f};
 #pragma unroll
       for (int u = 0; u < CH; ++u) {
-        const long long idx = i + (long long)u * blockDim.x;
-        if (idx < b1) {
+        const long long idx = i + (long long)u * stride;
+        if (idx < n3) {
 #pragma unroll
           for (int f = 0; f < 5; ++f) ff_acc(acc[f], __ldg(U + f * n3 + idx));
         }
       }
 #pragma unroll
-      for (int f = 0; f < 5; ++f) s[f] += (double)acc[f].hi + (double)acc[f].lo;
+      for (int f = 0; f < 5; ++f) tot[f] = ff_add(tot[f], ff_two_sum(acc[f].hi, acc[f].lo));
     }
+#pragma unroll
+    for (int f = 0; f < 5; ++f) s[f] = (double)tot[f].hi + (double)tot[f].lo;
   } else {
-    for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    for (long long i = t0; i < n3; i += stride) {
 #pragma unroll
       for (int f = 0; f < 5; ++f) s[f] += (double)__ldg(U + f * n3 + i);
     }
   }
-#pragma unroll
-  for (int f = 0; f < 5; ++f) red[f][threadIdx.x] = s[f];
-  __syncthreads();
-  for (int w = TOTALS_THREADS / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-#pragma unroll
-      for (int f = 0; f < 5; ++f) red[f][threadIdx.x] += red[f][threadIdx.x + w];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x < 5) partials[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+  totals_block_store(s, partials);
 }
 
+// One warp per field adds the CTA partials in a fixed order.
 __global__ void totals_final_kernel(const double* __restrict__ partials, int nblocks,
                                     double* __restrict__ out) {
-  const int f = threadIdx.x;
-  if (f < 5) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[b * 5 + f];
-    out[f] = s;
-  }
+  const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (f >= 5) return;
+  double t = 0.0;
+  for (int b = lane; b < nblocks; b += 32) t += partials[b * 5 + f];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) out[f] = t;
 }
 
 template <typename real>
 cudaError_t launch_totals(const real* U, long long n3, double* partials, int nblocks, double* out5,
                           cudaStream_t s) {
   totals_partial_kernel<real><<<nblocks, TOTALS_THREADS, 0, s>>>(U, n3, partials);
-  totals_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out5);
+  totals_final_kernel<<<1, 5 * 32, 0, s>>>(partials, nblocks, out5);
   return cudaGetLastError();
 }
 template cudaError_t launch_totals<float>(const float*, long long, double*, int, double*,
