@@ -171,9 +171,10 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
     return cons_to_prim(S.stg[0][sy][q], S.stg[1][sy][q], S.stg[2][sy][q], S.stg[3][sy][q],
                         S.stg[4][sy][q], gm1);
   };
-  // primitive recovery of the staged plane into a ring slot
+  // primitive recovery of the staged plane into a ring slot; cells are taken from the last
+  // thread down, so that the warps with a third slope item get no third cell
   auto convert_plane = [&](int slot) {
-    for (int c = tid; c < WX * WY; c += ANT) {
+    for (int c = ANT - 1 - tid; c < WX * WY; c += ANT) {
       const int sy = c / WX, sx = c - sy * WX;
       const Prim<real> w = staged_prim(sy, sx);
       S.w[slot][0][sy][sx] = w.r;
