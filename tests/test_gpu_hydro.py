@@ -127,8 +127,10 @@ def test_cooling_subcycling_branch_fp64():
     assert max(rel_linf(s.get_state(), sim.U)) <= 1e-11
 
 
-def test_conserved_totals_fp64_and_fp32():
-    shape = (12, 16, 20)
+@pytest.mark.parametrize("shape", [(12, 16, 20), (9, 11, 13), (33, 17, 35)])
+def test_conserved_totals_fp64_and_fp32(shape):
+    """Totals against math.fsum; cell counts that are multiples of 4 take the float32 path's
+    16-byte loads, odd ones its element loads."""
     U0 = inputs.kelvin_helmholtz(shape, seed=1)
     for prec in ("f64", "f32"):
         s = solver(shape, prec)
