@@ -9,7 +9,8 @@
 // register pipeline); every face VJP of HLLC is evaluated once on those states; the limiter's
 // transposed stencil (slope VJPs) is evaluated once per cell and axis and gathered from the
 // neighbouring cells; the primitive-recovery Jacobian is applied last.  No atomics; each output
-// cell is written by one thread.
+// cell is written by one thread.  The conserved variables of the plane three ahead and the
+// plane's lam_out arrive by cp.async while the previous phases compute.
 //
 // Kink convention: the derivative of the branch the forward took; exact ties of min/max split
 // the derivative evenly between the tied arguments (the MC limiter and the Davis speeds).
