@@ -270,13 +270,18 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
     __syncthreads();  // ---- plane k+2 in the ring, face states ready, staging plane free
 
     if (k + 1 < z1) stage_plane(k + 3);
-    // stage 1 loads the own cell's state for the update now and uses it after the face loop;
-    // the combination stages load U and U0 there (measured faster: fewer live registers)
+    // the own cell's values for the update, loaded now and used after the face loop: U in
+    // stage 1, U0 in the combination stages (which load U there: holding both measured
+    // slower, from more live registers)
     const long long idx = (long long)k * plane + col;
     real uin[5], un[5];
     if (!COMB && active) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) uin[c] = __ldg(p.U + c * n3 + idx);
+    }
+    if (COMB && active) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) un[c] = __ldg(p.U0 + c * n3 + idx);
     }
     // z face k+1/2 of the own column
     real fz_hi[5];
@@ -314,10 +319,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
       real u[5];
       if (COMB) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          uin[c] = __ldg(p.U + c * n3 + idx);
-          un[c] = __ldg(p.U0 + c * n3 + idx);
-        }
+        for (int c = 0; c < 5; ++c) uin[c] = __ldg(p.U + c * n3 + idx);
       }
       const Q4<real> fxr = S.fx4[ty][tx + 1], fxl = S.fx4[ty][tx];
       const Q4<real> fyr = S.fy4[ty + 1][tx], fyl = S.fy4[ty][tx];
