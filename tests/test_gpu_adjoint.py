@@ -41,7 +41,8 @@ def _rel(a, b):
     return float((a - b).norm() / b.norm())
 
 
-@pytest.mark.parametrize("shape,n,k", [((16, 16, 16), 6, 4), ((12, 10, 20), 5, 2), ((9, 12, 40), 3, 3)])
+@pytest.mark.parametrize("shape,n,k", [((16, 16, 16), 6, 4), ((12, 10, 20), 5, 2), ((9, 12, 40), 3, 3),
+                                       ((4, 6, 5), 3, 2), ((6, 5, 4), 2, 1)])
 def test_fp64_matches_oracle_vjp_smooth(shape, n, k):
     U0 = inputs.decaying_turbulence(shape, seed=5, sigma=0.3, mach=0.8, p_sigma=0.3)
     lam = np.random.default_rng(1).standard_normal((5,) + shape)

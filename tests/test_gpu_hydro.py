@@ -46,6 +46,22 @@ def test_ragged_tiles_fp64(shape):
     assert max(rel_linf(s.get_state(), U)) <= 1e-11
 
 
+@pytest.mark.parametrize("shape", [(4, 6, 5), (5, 4, 8), (6, 5, 4)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 2e-5)])
+def test_smallest_grids(shape, prec, tol):
+    """Grids of 4-8 cells per axis: every staged plane, halo row and face wraps around the
+    periodic box, and rows of 5 or 4 cells take the element or 16-byte staging copies."""
+    U0 = inputs.decaying_turbulence(shape, seed=4, sigma=0.4, mach=1.0)
+    s = solver(shape, prec)
+    s.init_state(to_gpu(U0, prec))
+    U = torch.from_numpy(to_gpu(U0, prec).double().cpu().numpy())
+    for _ in range(3):
+        dto = ohydro.cfl_dt(U, G, _dx(shape), 0.4)
+        s.step(dto)
+        U = ohydro.rk2_step(U, dto, G, _dx(shape))
+    assert max(rel_linf(s.get_state(), U)) <= tol
+
+
 def test_kh32_50_steps_fp64_and_fp32():
     shape = (32, 32, 32)
     U0 = inputs.kelvin_helmholtz(shape, seed=0)
