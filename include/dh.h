@@ -67,6 +67,7 @@ typedef struct dh_config {
   double t_floor;            /* temperature floor (default 0.05)                           */
   double cool_frac;          /* first-substep fractional change limit f (default 0.1)      */
   int nsub_max;              /* substep cap (default 1024)                                 */
+  /* (c_cool, the cooling time-step factor, is the last field below.) */
   /* Multigrid self-gravity, Sec. 5.2 and App. C: A phi = 4 pi G (rho - <rho>) by V- or
      W-cycles smoothed by red-black Gauss-Seidel or weighted Jacobi.  Needs dx == dy == dz;
      halving stops at dims < 8 or odd, coarsest <= 1024 cells. */
@@ -82,6 +83,10 @@ typedef struct dh_config {
   /* Scheme (App. A.1, A.3). */
   int limiter;               /* 0: MC (default); 1: van Leer 2ab/(a+b)                     */
   int integrator;            /* 2: RK2 / Heun (default); 3: SSPRK3 (Shu-Osher form)        */
+  /* Cooling time-step limit, Sec. 4.3: with cooling on and c_cool finite, the step is
+     min(CFL step, c_cool * min over cells of t_cool, dt_max), t_cool = E_th / |Edot| over the
+     cells above the floor energy.  Default +inf: off (cooling subcycles per cell instead). */
+  double c_cool;
 } dh_config;
 
 /* Fills *cfg with the defaults above for an nx*ny*nz grid. */

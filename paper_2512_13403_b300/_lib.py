@@ -31,6 +31,7 @@ class DhConfig(C.Structure):
         ("mg_max_cycles", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
         ("mg_smoother", C.c_int), ("mg_omega", C.c_double), ("mg_cycle", C.c_int),
         ("limiter", C.c_int), ("integrator", C.c_int),
+        ("c_cool", C.c_double),
     ]
 
 

@@ -49,6 +49,7 @@ extern "C" void dh_config_default(dh_config* cfg, int nx, int ny, int nz) {
   cfg->mg_pre = 2; cfg->mg_post = 2;
   cfg->mg_smoother = 0; cfg->mg_omega = 2.0 / 3.0; cfg->mg_cycle = 1;
   cfg->limiter = 0; cfg->integrator = 2;
+  cfg->c_cool = INFINITY;
 }
 
 static std::string validate(const dh_config& c) {
@@ -61,6 +62,7 @@ static std::string validate(const dh_config& c) {
   if (!(c.dt_max > 0.0)) return "dt_max must be positive";
   if (c.limiter != 0 && c.limiter != 1) return "limiter must be 0 (MC) or 1 (van Leer)";
   if (c.integrator != 2 && c.integrator != 3) return "integrator must be 2 (RK2) or 3 (SSPRK3)";
+  if (!(c.c_cool > 0.0)) return "c_cool must be positive (+inf: no cooling time-step limit)";
   if (c.forcing) {
     if (c.nx < 5 || c.ny < 5 || c.nz < 5) return "forcing needs every dimension >= 5";
     if (!(c.ou_tau > 0.0) || !(c.ou_arms >= 0.0)) return "ou_tau must be > 0 and ou_arms >= 0";
@@ -202,13 +204,20 @@ void dh::prof_fold(dh_ctx* c) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// c_cool / C: the reductions take min over cells of min(CFL time, (c_cool / C) t_cool), so that
+// C times the minimum is min(CFL step, c_cool min t_cool); 0 when the limit is off.
+template <typename real>
+static real cool_ratio(const dh_config& g) {
+  return g.cooling && std::isfinite(g.c_cool) ? (real)(g.c_cool / g.cfl) : real(0);
+}
+
 template <typename real>
 static cudaError_t cfl_reduce_current(dh_ctx* c) {
   const dh_config& g = c->cfg;
   prof_begin(c, DH_KERNEL_REDUCE);
   cudaError_t e = launch_cfl_reduce<real>((const real*)c->U[c->cur], g.nx, g.ny, g.nz,
                                           (real)g.gamma, (real)g.dx, (real)g.dy, (real)g.dz,
-                                          c->rec, c->stream);
+                                          cool_ratio<real>(g), (real)g.t_floor, c->rec, c->stream);
   prof_end(c, 1);
   return e;
 }
@@ -269,6 +278,7 @@ static StageArgs<real> stage_args(dh_ctx* c) {
   a.ahat_norm = (const real*)c->ahat_norm;
   for (int q = 0; q < 3; ++q) a.tw[q] = (const real*)c->tw[q];
   a.t_floor = (real)g.t_floor; a.cool_frac = (real)g.cool_frac; a.nsub_max = g.nsub_max;
+  a.cool_ratio = cool_ratio<real>(g);
   a.limiter = g.limiter;
   a.w0 = real(0.5); a.w1 = real(0.5);
   a.final_stage = 1;

@@ -23,6 +23,7 @@ template <typename real> struct StageArgs {
   real t_floor, cool_frac;
   int nsub_max;
   int reduce_cfl;         // accumulate the CFL minimum of the output state
+  real cool_ratio;        // > 0: also (c_cool / C) t_cool of each cell (cooling time-step limit)
   real* pre_src;          // stage 2 (nullable): also store the state before the sources
   int limiter;            // LIM_MC or LIM_VL
   // stage 3 (SSPRK3's combinations): out = w0 U0 + w1 (U + dt L(U)), (3/4, 1/4) then (1/3, 2/3);
@@ -53,7 +54,8 @@ cudaError_t launch_forcing_init(double* ahat, unsigned long long seed, cudaStrea
 
 template <typename real>
 cudaError_t launch_cfl_reduce(const real* U, int nx, int ny, int nz, real gamma, real dx, real dy,
-                              real dz, StepRecord* rec, cudaStream_t s);
+                              real dz, real cool_ratio, real t_floor, StepRecord* rec,
+                              cudaStream_t s);
 
 template <typename real>
 cudaError_t launch_totals(const real* U, long long n3, double* partials, int nblocks,

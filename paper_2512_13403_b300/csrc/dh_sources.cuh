@@ -283,6 +283,18 @@ __device__ __forceinline__ void cooling_tangents(real r, real mx, real my, real 
   }
 }
 
+// Cooling time t_cool = E_th / |Edot| = E_th / (rho^2 T^(1/2)) of a cell above the floor energy
+// (Sec. 4.3), +inf at or below it (where nothing cools).
+template <typename real>
+__device__ __forceinline__ real cooling_time(real r, real mx, real my, real mz, real E, real gm1,
+                                             real T_floor) {
+  const real ir = q_div(real(1), r);
+  const real Eth = E - real(0.5) * (mx * mx + my * my + mz * mz) * ir;
+  const real Efl = r * T_floor * (real(1) / gm1);
+  if (!(Eth > Efl)) return real(INFINITY);
+  return q_div(Eth, r * r * q_sqrt(gm1 * Eth * ir));
+}
+
 template <typename real>
 __device__ __forceinline__ real cfl_time(real r, real mx, real my, real mz, real E, real gamma,
                                          real gm1, real dx, real dy, real dz) {

@@ -388,8 +388,11 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
         } else {
           const real pr = gm1 * (u[4] - real(0.5) * q_div(u[1] * u[1] + u[2] * u[2] + u[3] * u[3], u[0]));
           if (!(u[0] > real(0)) || !(pr > real(0))) flags |= FLAG_POSITIVITY;
-          if (p.reduce_cfl)
+          if (p.reduce_cfl) {
             tmin = fmin(tmin, cfl_time(u[0], u[1], u[2], u[3], u[4], gamma, gm1, p.dx, p.dy, p.dz));
+            if (p.cool_ratio > real(0))
+              tmin = fmin(tmin, p.cool_ratio * cooling_time(u[0], u[1], u[2], u[3], u[4], gm1, p.t_floor));
+          }
         }
       }
 #pragma unroll
@@ -636,13 +639,15 @@ cudaError_t launch_step_begin(const BeginArgs& a, cudaStream_t s) {
 template <typename real>
 __global__ void cfl_reduce_kernel(const real* __restrict__ U, long long n3, int nx, int ny,
                                   real gamma, real gm1, real dx, real dy, real dz,
-                                  StepRecord* rec) {
+                                  real cool_ratio, real t_floor, StepRecord* rec) {
   __shared__ real red[8];
   real m = real(INFINITY);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
        i += (long long)gridDim.x * blockDim.x) {
-    m = fmin(m, cfl_time(__ldg(U + i), __ldg(U + n3 + i), __ldg(U + 2 * n3 + i),
-                         __ldg(U + 3 * n3 + i), __ldg(U + 4 * n3 + i), gamma, gm1, dx, dy, dz));
+    const real r = __ldg(U + i), mx = __ldg(U + n3 + i), my = __ldg(U + 2 * n3 + i);
+    const real mz = __ldg(U + 3 * n3 + i), E = __ldg(U + 4 * n3 + i);
+    m = fmin(m, cfl_time(r, mx, my, mz, E, gamma, gm1, dx, dy, dz));
+    if (cool_ratio > real(0)) m = fmin(m, cool_ratio * cooling_time(r, mx, my, mz, E, gm1, t_floor));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -656,18 +661,20 @@ __global__ void cfl_reduce_kernel(const real* __restrict__ U, long long n3, int 
 
 template <typename real>
 cudaError_t launch_cfl_reduce(const real* U, int nx, int ny, int nz, real gamma, real dx, real dy,
-                              real dz, StepRecord* rec, cudaStream_t s) {
+                              real dz, real cool_ratio, real t_floor, StepRecord* rec,
+                              cudaStream_t s) {
   const long long n3 = (long long)nx * ny * nz;
   long long blocks = (n3 + 255) / 256;
   if (blocks > 148 * 8) blocks = 148 * 8;
   cfl_reduce_kernel<real><<<(int)blocks, 256, 0, s>>>(U, n3, nx, ny, gamma, gamma - real(1), dx,
-                                                      dy, dz, rec);
+                                                      dy, dz, cool_ratio, t_floor, rec);
   return cudaGetLastError();
 }
 template cudaError_t launch_cfl_reduce<float>(const float*, int, int, int, float, float, float,
-                                              float, StepRecord*, cudaStream_t);
+                                              float, float, float, StepRecord*, cudaStream_t);
 template cudaError_t launch_cfl_reduce<double>(const double*, int, int, int, double, double,
-                                               double, double, StepRecord*, cudaStream_t);
+                                               double, double, double, double, StepRecord*,
+                                               cudaStream_t);
 
 // ---------------------------------------------------------------------------------------------
 // Conserved totals in float64 with a fixed reduction order (two passes, no atomics).

@@ -1132,7 +1132,7 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
                        int forcing,
                        const real* __restrict__ ah, const real* tw0, const real* tw1,
                        const real* tw2, int cooling, real gamma, real gm1, real t_floor,
-                       real frac, int nsub_max, real dx, real dy, real dz) {
+                       real frac, int nsub_max, real dx, real dy, real dz, real cool_ratio) {
   __shared__ unsigned s_skip;
   __shared__ real red[8];
   __shared__ real fB[2][GS_TY][3][3][2];   // double-buffered by plane parity
@@ -1244,6 +1244,8 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
       const real pr = gm1 * (u[4] - real(0.5) * q_div(u[1] * u[1] + u[2] * u[2] + u[3] * u[3], u[0]));
       if (!(u[0] > real(0)) || !(pr > real(0))) flags |= FLAG_POSITIVITY;
       tmin = fmin(tmin, cfl_time(u[0], u[1], u[2], u[3], u[4], gamma, gm1, dx, dy, dz));
+      if (cool_ratio > real(0))
+        tmin = fmin(tmin, cool_ratio * cooling_time(u[0], u[1], u[2], u[3], u[4], gm1, t_floor));
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) U[c * n3 + q] = u[c];
@@ -1279,7 +1281,8 @@ cudaError_t gravity_sources(dh_ctx* c, void* Ustar, const void* tab, const doubl
       g.forcing, (const real*)(tab ? tab : c->ahat_norm), (const real*)c->tw[0],
       (const real*)c->tw[1], (const real*)c->tw[2], g.cooling, (real)g.gamma,
       (real)(g.gamma - 1.0), (real)g.t_floor, (real)g.cool_frac, g.nsub_max, (real)g.dx,
-      (real)g.dy, (real)g.dz);
+      (real)g.dy, (real)g.dz,
+      g.cooling && std::isfinite(g.c_cool) ? (real)(g.c_cool / g.cfl) : real(0));
   prof_end(c, 1);
   return cudaGetLastError();
 }

@@ -44,6 +44,7 @@ class Config:
     mg_cycle: str = "V"           # "V" or "W"
     limiter: str = "mc"           # "mc" or "vanleer"
     integrator: str = "rk2"       # "rk2" or "ssprk3"
+    c_cool: float = math.inf      # cooling time-step factor (Sec. 4.3); inf: off
 
     def to_c(self) -> DhConfig:
         nz, ny, nx = self.shape
@@ -53,7 +54,7 @@ class Config:
         if self.dx is not None:
             c.dx, c.dy, c.dz = self.dx
         for f in ("gamma", "cfl", "dt_max", "ou_tau", "ou_arms", "t_floor", "cool_frac",
-                  "four_pi_G", "mg_tol"):
+                  "four_pi_G", "mg_tol", "c_cool"):
             setattr(c, f, float(getattr(self, f)))
         for f in ("nsub_max", "mg_max_cycles", "mg_pre", "mg_post"):
             setattr(c, f, int(getattr(self, f)))

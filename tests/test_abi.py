@@ -44,6 +44,7 @@ def test_config_struct_matches_header_layout():
     # the fields after the mg sweep counts (offsets follow the header's order)
     assert cfg.mg_smoother == 0 and abs(cfg.mg_omega - 2 / 3) < 1e-15 and cfg.mg_cycle == 1
     assert cfg.limiter == 0 and cfg.integrator == 2
+    assert cfg.c_cool == float("inf")   # the last field: the cooling time-step limit is off
 
 
 def test_create_rejects_bad_config_without_gpu_work():
@@ -59,7 +60,8 @@ def test_create_rejects_bad_config_without_gpu_work():
     assert lib.dh_status_string(_lib.DH_ERR_POSITIVITY) == b"DH_ERR_POSITIVITY"
     for field, bad, msg in (("mg_cycle", 3, b"mg_cycle"), ("mg_smoother", 2, b"mg_smoother"),
                             ("mg_omega", 1.5, b"mg_omega"), ("limiter", 2, b"limiter"),
-                            ("integrator", 4, b"integrator")):
+                            ("integrator", 4, b"integrator"), ("c_cool", 0.0, b"c_cool"),
+                            ("c_cool", -1.0, b"c_cool")):
         lib.dh_config_default(C.byref(cfg), 16, 16, 16)
         cfg.gravity = 1
         setattr(cfg, field, bad)

@@ -255,3 +255,22 @@ def test_scheme_variants_with_sources_fp64_and_fp32(integrator, limiter):
         assert dt == pytest.approx(dto, rel=1e-13)
     assert max(rel_linf(s.get_state(), sim.U)) <= 1e-11
     assert max(rel_linf(s32.get_state(), sim.U)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 2e-5)])
+def test_cooling_time_step_limit(prec, tol):
+    """dt = min(CFL step, c_cool min t_cool, dt_max) (Sec. 4.3), reduced in the stage-2 epilogue
+    (and after init_state) on the GPU, against the oracle's step; the limit binds here."""
+    shape = (16, 20, 24)
+    U0 = inputs.decaying_turbulence(shape, seed=9, sigma=0.5, mach=0.7, P0=0.6)
+    kw = dict(forcing=True, ou_seed=1, cooling=True, t_floor=0.05, c_cool=0.01)
+    sim = odrv.Simulation(odrv.Config(shape=shape, **kw), to_gpu(U0, prec).double().cpu())
+    s = solver(shape, prec, **kw)
+    s.init_state(to_gpu(U0, prec))
+    for _ in range(4):
+        cfl = ohydro.cfl_dt(sim.U, G, _dx(shape), 0.4)
+        dto = sim.step()
+        assert dto < 0.9 * cfl
+        dt = s.step(0.0)
+        assert dt == pytest.approx(dto, rel=1e-13 if prec == "f64" else 2e-6)
+    assert max(rel_linf(s.get_state(), sim.U)) <= tol

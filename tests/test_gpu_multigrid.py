@@ -225,3 +225,19 @@ def test_fft_poisson_agrees_with_multigrid_and_rejects_other_sizes():
         s.fft_poisson(torch.ones((12, 16, 16), dtype=torch.float64, device="cuda"))
     assert e.value.status == DH_ERR_ARG
     s.close()
+
+
+def test_cooling_time_step_limit_with_gravity_fp64():
+    """With gravity the sources run in their own kernel, which also reduces the next dt: the
+    cooling time-step limit there against the oracle."""
+    shape = (16, 16, 16)
+    U0 = inputs.self_gravitating_box(shape, seed=5, sigma=1.0)
+    kw = dict(gravity=True, mg_tol=1e-11, mg_max_cycles=60, cooling=True, t_floor=0.05, c_cool=0.02)
+    sim = odrv.Simulation(odrv.Config(shape=shape, **kw), U0)
+    s = solver(shape, "f64", **kw)
+    s.init_state(to_gpu(U0, "f64"))
+    for _ in range(3):
+        dt = s.step(0.0)
+        dto = sim.step()
+        assert dt == pytest.approx(dto, rel=1e-9)
+    assert max(rel_linf(s.get_state(), sim.U)) <= 1e-9

@@ -151,3 +151,30 @@ def test_forcing_field_at_cells_equals_the_whole_field():
     j = torch.randint(0, 7, (50,), generator=g)
     i = torch.randint(0, 8, (50,), generator=g)
     assert torch.allclose(ou.field_at(shape, k, j, i), full[:, k, j, i], rtol=0, atol=1e-14)
+
+
+def test_min_cooling_time_hand_values():
+    """t_cool = E_th / |Edot| with Edot = -rho^2 T^(1/2), T = (gamma - 1) E_th / rho (Sec. 4.3),
+    evaluated by hand; cells at or below the floor do not count, and with none cooling the
+    minimum is +inf.  The cooling limit of the step is then c_cool times that minimum."""
+    from oracle import driver, hydro
+    g = 5.0 / 3.0
+    shape = (4, 4, 4)
+    z = np.zeros(shape)
+    rho = np.ones(shape)
+    P = np.full(shape, 0.6)
+    rho[1, 2, 3] = 2.0                   # T = 0.3, E_th = 0.9: t = 0.9 / (4 sqrt(0.3))
+    vx = z.copy()
+    vx[1, 2, 3] = 0.5                    # kinetic energy does not enter E_th
+    U = torch.from_numpy(inputs.prim_to_state(rho, vx, z, z, P, g))
+    t = cooling.min_cooling_time(U, g, 0.05)
+    assert t == pytest.approx(0.9 / (4.0 * math.sqrt(0.3)), rel=1e-14)
+    assert 0.9 / math.sqrt(0.6) > t      # the uniform cells' time is the larger one
+    # at the floor (T = T_floor) nothing cools
+    U_cold = torch.from_numpy(inputs.prim_to_state(np.ones(shape), z, z, z, np.full(shape, 0.05), g))
+    assert cooling.min_cooling_time(U_cold, g, 0.05) == math.inf
+    # the step takes min(CFL step, c_cool min t_cool, dt_max)
+    sim = driver.Simulation(driver.Config(shape=shape, cooling=True, t_floor=0.05, c_cool=0.01), U)
+    cfl = hydro.cfl_dt(U, g, sim.cfg.dx, 0.4)
+    assert sim.compute_dt() == pytest.approx(min(cfl, 0.01 * t), rel=1e-15)
+    assert 0.01 * t < cfl                # the cooling limit binds here
