@@ -352,6 +352,52 @@ def _adjoint_run(cfg, U0, steps, k, stream, lam_scale):
     return ms, na, ta
 
 
+def _reconstruction_run(stream, n=128, steps=100, k=10):
+    """The differentiable-reconstruction configuration: 128^3 decaying turbulence, 100 float32
+    steps, loss L = mean over cells of (rho_final - rho_target)^2 with the target the final
+    density of the same setup from seed + 1, and its gradient with respect to the initial
+    state by the hand adjoint with a checkpoint every 10 steps.  Times the forward run that
+    yields the loss and, apart, the gradient call (its own forward sweep, recompute and
+    backward)."""
+    import torch
+    from paper_2512_13403_b300 import inputs
+    from paper_2512_13403_b300.solver import Config, Solver
+    shape = (n, n, n)
+    ic = lambda seed: torch.from_numpy(inputs.decaying_turbulence(shape, seed=seed, sigma=0.5,
+                                                                   mach=2.0)).float().cuda()
+    with torch.cuda.stream(stream):
+        s = Solver(Config(shape=shape, precision="f32"), stream=stream)
+        s.init_state(ic(3))
+        s.advance(steps)
+        target = s.get_state()[0].clone()
+        U0 = ic(2)
+        s.init_state(U0)
+        s.adjoint_advance(2, 1, torch.zeros_like(U0))      # warm-up of the adjoint buffers
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        s.init_state(U0)
+        s.advance(steps)
+        ev[1].record(stream)
+        rho = s.get_state()[0]
+        loss = torch.mean((rho.double() - target.double()) ** 2)
+        lam = torch.zeros_like(U0)
+        lam[0] = (2.0 / n ** 3) * (rho - target)
+        s.init_state(U0)
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        g = s.adjoint_advance(steps, k, lam)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        fwd_ms, adj_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+        gnorm = float(g.double().norm())
+        s.close()
+    return {"value": n ** 3 * steps / (adj_ms * 1e-3), "unit": UNIT, "steps": steps, "ckpt_every": k,
+            "loss": float(loss), "grad_norm": gnorm, "forward_ms": fwd_ms, "gradient_ms": adj_ms,
+            "workload": f"decaying turbulence {n}^3 float32, {steps} steps, MSE of the final density "
+                        "against the seed+1 run; gradient of the initial state by the hand adjoint"}
+
+
 def adjoint_leg(args, stream):
     """Hand adjoint through n steps at 256^3, checkpoints every k: cell-updates/s = N^3 n / wall
     time of dh_adjoint_advance (forward, recompute and backward).  Main line: decaying turbulence
@@ -375,6 +421,7 @@ def adjoint_leg(args, stream):
            "roofline": {"bound": "hbm", "kernel": "stage_adjoint_kernel<float>", "achieved": ach,
                         "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": kind,
                         "traffic": None, "avg_launch_ms": adj_ms, "launches": na}}
+    out["reconstruction_128"] = _reconstruction_run(stream)
     if not args.adj_sources:
         return out
     Ub = torch.from_numpy(inputs.cooling_box(shape)).float().cuda()
