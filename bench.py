@@ -36,8 +36,8 @@ ADJ_BYTES_STAGE = 70    # float32 per adjoint stage launch, average of stage-2^T
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp instructions
 # (smsp__inst_executed.sum) of one stage-2 launch at 256^3, from one ncu capture of the current
 # kernel source
-STAGE2_DRAM_BYTES_256 = 703019776 + 309364736
-STAGE2_WARP_INSTR_256 = 703772928
+STAGE2_DRAM_BYTES_256 = 702899456 + 308701184
+STAGE2_WARP_INSTR_256 = 693901568
 
 
 def _peaks():
