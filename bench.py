@@ -38,6 +38,10 @@ ADJ_BYTES_STAGE = 70    # float32 per adjoint stage launch, average of stage-2^T
 # kernel source
 STAGE2_DRAM_BYTES_256 = 702899456 + 308701184
 STAGE2_WARP_INSTR_256 = 693901568
+# the same for stage_adjoint_kernel<float> at 256^3, averaged over its two launches per RK2 step
+# (stage-2 transposed: 1029 MB, 1.411e9; stage-1 transposed with the extra term: 1378 MB, 1.412e9)
+ADJ_DRAM_BYTES_256 = (708688896 + 320567808 + 1055478272 + 322707456) // 2
+ADJ_WARP_INSTR_256 = (1410642007 + 1411619161) // 2
 
 
 def _peaks():
@@ -311,6 +315,15 @@ def run_ours(args):
                                         "issue slots x median SM clock sampled during the run"}
     if not args.no_adjoint:
         line["adjoint"] = adjoint_leg(args, stream)
+        if n == 256:
+            adj = line["adjoint"]
+            adj["roofline"]["traffic"] = ADJ_DRAM_BYTES_256
+            issue = ADJ_WARP_INSTR_256 / (adj["roofline"]["avg_launch_ms"] * 1e-3)
+            adj["roofline_alu"] = {"bound": "alu", "kernel": "stage_adjoint_kernel<float>",
+                                   "achieved": issue, "peak": 148 * 4 * clk * 1e6,
+                                   "unit": "warp-instr/s", "frac": issue / (148 * 4 * clk * 1e6),
+                                   "note": "warp instructions per launch from ncu (mean of the two "
+                                           "launches of a step); peak as for the forward"}
     if not args.no_selfgrav:
         line["self_gravitating"] = selfgrav_leg(args, stream)
     if not args.no_scheme_variants:
