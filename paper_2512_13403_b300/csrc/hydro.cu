@@ -678,9 +678,10 @@ template cudaError_t launch_cfl_reduce<double>(const double*, int, int, int, dou
 
 // ---------------------------------------------------------------------------------------------
 // Conserved totals in float64 with a fixed reduction order (two passes, no atomics).
-// Conserved totals: a fixed grid of 8 CTAs per SM on 148 SMs, each thread summing a strided
-// share, then fixed-order reductions, so the result is the same on every call.
-constexpr int TOTALS_BLOCKS = 148 * 8, TOTALS_THREADS = 256;
+// Conserved totals: a fixed grid of 6 CTAs per SM on 148 SMs, each CTA summing its own
+// contiguous range of every field, then fixed-order reductions, so the result is the same on
+// every call.
+constexpr int TOTALS_BLOCKS = 148 * 6, TOTALS_THREADS = 256;
 int totals_blocks() { return TOTALS_BLOCKS; }
 
 // Sum over the CTA of five doubles per thread (warp shuffles, then the warps in order);
@@ -703,7 +704,7 @@ __device__ __forceinline__ void totals_block_store(double s[5], double* __restri
 }
 
 template <typename real>
-__global__ void __launch_bounds__(TOTALS_THREADS)
+__global__ void __launch_bounds__(TOTALS_THREADS, TOTALS_BLOCKS / 148)
 totals_partial_kernel(const real* __restrict__ U, long long n3, double* __restrict__ partials) {
   double s[5] = {0, 0, 0, 0, 0};
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -720,23 +721,34 @@ totals_partial_kernel(const real* __restrict__ U, long long n3, double* __restri
 #pragma unroll
     for (int f = 0; f < 5; ++f) tot[f] = ff2{0.0f, 0.0f};
     if (vec) {
+      // each CTA streams its own contiguous range of every field, one field after the other
       const long long n4 = n3 / 4;
       const float4* __restrict__ U4 = reinterpret_cast<const float4*>(U);
-      for (long long i = t0; i < n4; i += 2 * stride) {
-        const bool two = i + stride < n4;
-        float4 a[5], b[5];
+      const long long per = (n4 + gridDim.x - 1) / gridDim.x;
+      const long long b0 = (long long)blockIdx.x * per, b1 = b0 + per < n4 ? b0 + per : n4;
+      const int bs = blockDim.x;
+#pragma unroll 1
+      for (int f = 0; f < 5; ++f) {
+        const float4* __restrict__ Uf = U4 + f * n4;
+        ff2 tf{0.0f, 0.0f};
+        for (long long i = b0 + threadIdx.x; i < b1; i += 4 * bs) {
+          float4 a[4];
 #pragma unroll
-        for (int f = 0; f < 5; ++f) {
-          a[f] = __ldg(U4 + f * n4 + i);
-          b[f] = two ? __ldg(U4 + f * n4 + i + stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int u = 0; u < 4; ++u)
+            a[u] = i + u * bs < b1 ? __ldg(Uf + i + u * bs) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            ff2 acc{0.0f, 0.0f};
+            ff_acc(acc, a[2 * h].x); ff_acc(acc, a[2 * h].y);
+            ff_acc(acc, a[2 * h].z); ff_acc(acc, a[2 * h].w);
+            ff_acc(acc, a[2 * h + 1].x); ff_acc(acc, a[2 * h + 1].y);
+            ff_acc(acc, a[2 * h + 1].z); ff_acc(acc, a[2 * h + 1].w);
+            tf = ff_add(tf, ff_two_sum(acc.hi, acc.lo));
+          }
         }
 #pragma unroll
-        for (int f = 0; f < 5; ++f) {
-          ff2 acc{0.0f, 0.0f};
-          ff_acc(acc, a[f].x); ff_acc(acc, a[f].y); ff_acc(acc, a[f].z); ff_acc(acc, a[f].w);
-          ff_acc(acc, b[f].x); ff_acc(acc, b[f].y); ff_acc(acc, b[f].z); ff_acc(acc, b[f].w);
-          tot[f] = ff_add(tot[f], ff_two_sum(acc.hi, acc.lo));
-        }
+        for (int q = 0; q < 5; ++q)
+          if (q == f) tot[q] = tf;
       }
       done = n3;
     }
