@@ -331,3 +331,26 @@ def test_gradient_independent_of_checkpoint_interval(prec, integrator, sources):
         grads.append(s.adjoint_advance(n, k, lam).clone())
         s.close()
     assert torch.equal(grads[0], grads[1]) and torch.equal(grads[0], grads[2])
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_adjoint_commutes_with_reflection_fp64(axis):
+    """The gradient of the reflected problem (state and lambda reflected, the momentum along the
+    axis negated in both) is the reflected gradient."""
+    shape = (12, 10, 20)
+    U0 = torch.from_numpy(inputs.decaying_turbulence(shape, seed=5, sigma=0.3, mach=0.8, p_sigma=0.3))
+    lam = torch.from_numpy(np.random.default_rng(3).standard_normal((5,) + shape))
+
+    def mirror(U):
+        d = 3 - axis
+        V = torch.flip(U, dims=[d]).clone()
+        V[1 + axis] = -V[1 + axis]
+        return V
+
+    grads = []
+    for U, L in ((U0, lam), (mirror(U0), mirror(lam))):
+        s = solver(shape, "f64")
+        s.init_state(to_gpu(U.numpy(), "f64"))
+        grads.append(s.adjoint_advance(3, 2, to_gpu(L.numpy(), "f64")).cpu())
+        s.close()
+    assert _rel(mirror(grads[1]), grads[0]) < 1e-11
