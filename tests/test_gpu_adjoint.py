@@ -354,3 +354,29 @@ def test_adjoint_commutes_with_reflection_fp64(axis):
         grads.append(s.adjoint_advance(3, 2, to_gpu(L.numpy(), "f64")).cpu())
         s.close()
     assert _rel(mirror(grads[1]), grads[0]) < 1e-11
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_adjoint_translation_equivariant(prec):
+    """The gradient of a periodically shifted problem is the shifted gradient: bit for bit for
+    shifts in x and y, to rounding for shifts in z (z-chunk starts take their first faces and
+    slope terms from the prologue's copy of the same formulas)."""
+    shape = (12, 10, 20)
+    U0 = torch.from_numpy(inputs.decaying_turbulence(shape, seed=5, sigma=0.3, mach=0.8, p_sigma=0.3))
+    lam = torch.from_numpy(np.random.default_rng(3).standard_normal((5,) + shape))
+
+    def grad(U, L):
+        s = solver(shape, prec)
+        s.init_state(to_gpu(U.numpy(), prec))
+        g = s.adjoint_advance(3, 2, to_gpu(L.numpy(), prec)).cpu()
+        s.close()
+        return g
+
+    ref = grad(U0, lam)
+    for shift, exact in (((0, 3, 11), True), ((5, 3, 11), False)):
+        got = grad(torch.roll(U0, shift, (1, 2, 3)), torch.roll(lam, shift, (1, 2, 3)))
+        want = torch.roll(ref, shift, (1, 2, 3))
+        if exact:
+            assert torch.equal(want, got), shift
+        else:
+            assert _rel(got, want) < (1e-13 if prec == "f64" else 1e-5), shift

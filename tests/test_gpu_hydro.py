@@ -303,3 +303,32 @@ def test_step_commutes_with_reflection(axis, prec, tol):
         out.append(s.get_state().cpu())
         s.close()
     assert max(rel_linf(_mirror(out[1], axis), out[0])) <= tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_step_translation_equivariant(prec):
+    """A periodically shifted state steps to the shifted result (cooling on; the forcing field
+    is position-dependent and is off here).  Shifts in x and y are bit for bit: every cell's
+    update is the same code wherever it sits in its tile or staging chunk.  Shifts in z move
+    cells across z-chunk starts, whose first z face and slope come from the prologue's copy of
+    the same formulas, which the compiler may contract differently: equal to rounding."""
+    shape = (20, 12, 40)
+    U0 = torch.from_numpy(inputs.decaying_turbulence(shape, seed=6, sigma=0.5, mach=1.2))
+
+    def run(U):
+        s = solver(shape, prec, cooling=True, t_floor=0.05)
+        s.init_state(to_gpu(U, prec))
+        for _ in range(2):
+            s.step(0.0)
+        out = s.get_state().cpu()
+        s.close()
+        return out
+
+    ref = run(U0)
+    for shift, exact in (((0, 5, 13), True), ((7, 5, 13), False)):
+        got = run(torch.roll(U0, shifts=shift, dims=(1, 2, 3)))
+        want = torch.roll(ref, shifts=shift, dims=(1, 2, 3))
+        if exact:
+            assert torch.equal(want, got), shift
+        else:
+            assert max(rel_linf(got, want)) <= (1e-14 if prec == "f64" else 1e-6), shift
