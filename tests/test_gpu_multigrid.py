@@ -266,3 +266,23 @@ def test_point_mass_force_multigrid_against_fft():
         err = float(torch.sqrt(sum((gm[d] - ref[0][d]) ** 2 for d in range(3))).max()) / ref[1]
         assert err < bound, (tol, err)
         s.close()
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_potential_commutes_with_reflection(axis):
+    """The converged potential of a reflected density is the reflected potential.  Reflection
+    swaps the red and black cells on even grids, so the Gauss-Seidel iterates differ and only
+    the converged solutions agree, to the tolerance."""
+    shape = (32, 16, 24)
+    d = 2 - axis
+    rho = torch.from_numpy(inputs.self_gravitating_box(shape, seed=3, sigma=1.0)[0]).cuda()
+    phis = []
+    for r in (rho, torch.flip(rho, dims=[d])):
+        s = solver(shape, "f64", gravity=True, mg_tol=1e-12, mg_max_cycles=80,
+                   dx=(1 / 32, 1 / 32, 1 / 32))
+        s.solve_poisson(r.contiguous(), fetch=False)
+        phi, _, _ = s.potential()
+        phis.append(phi.cpu())
+        s.close()
+    ref = phis[0]
+    assert float((torch.flip(phis[1], dims=[d]) - ref).abs().max()) < 1e-10 * float(ref.abs().max())
