@@ -192,7 +192,9 @@ dh_status dh_solve_poisson(dh_ctx* ctx, const void* rho, int on_device);
 /* Reverse-mode product through n_steps steps (hand adjoint, App. A.3 stages transposed; dt of
    every step frozen at the value the forward took, App. A.4): given the current state U^0,
    runs the forward n_steps CFL steps (storing U every `ckpt_every` steps, Sec. 2.3
-   checkpointing), then returns dL/dU^0 in dLdU0 for dL/dU^{n} = dLdU_final.  Both buffers use
+   checkpointing; an interval above n_steps is taken as n_steps), then returns dL/dU^0 in
+   dLdU0 for dL/dU^{n} = dLdU_final.  n_steps = 0 copies dLdU_final; n_steps < 0 or
+   ckpt_every < 1 is DH_ERR_ARG.  Both buffers use
    the state layout and precision; the context is left at U^{n} and steps on as if no adjoint
    had run.  The operator-split sources are differentiated too: the OU kick with each step's
    field held fixed (Sec. 3.1.1; the draws do not depend on U), self-gravity (Sec. 5: the kick

@@ -833,6 +833,7 @@ extern "C" dh_status dh_adjoint_advance_dt(dh_ctx* c, int n, int k, double dt,
     if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return DH_ERR_CUDA; }
     return DH_OK;
   }
+  if (k > n) k = n;   // one segment: a larger interval would only allocate unused buffers
   cudaError_t e = adjoint_reserve(c, n, k);
   if (e != cudaSuccess) { c->err = std::string("adjoint allocation: ") + cudaGetErrorString(e); return DH_ERR_CUDA; }
   AdjointSpace* a = c->adj;

@@ -380,3 +380,25 @@ def test_adjoint_translation_equivariant(prec):
             assert torch.equal(want, got), shift
         else:
             assert _rel(got, want) < (1e-13 if prec == "f64" else 1e-5), shift
+
+
+def test_adjoint_edge_cases():
+    """n = 0 returns lambda unchanged; a checkpoint interval larger than n is one kept segment
+    (same bits as k = n); bad arguments are rejected without touching the state."""
+    from paper_2512_13403_b300._lib import DH_ERR_ARG, DhError
+    shape = (8, 8, 8)
+    U0 = inputs.decaying_turbulence(shape, seed=2, sigma=0.3, mach=0.6, p_sigma=0.2)
+    lam = to_gpu(np.random.default_rng(2).standard_normal((5,) + shape), "f64")
+    s = solver(shape, "f64")
+    s.init_state(to_gpu(U0, "f64"))
+    assert torch.equal(s.adjoint_advance(0, 1, lam), lam)
+    g_big = s.adjoint_advance(3, 50, lam).clone()
+    s.init_state(to_gpu(U0, "f64"))
+    assert torch.equal(s.adjoint_advance(3, 3, lam), g_big)
+    t0 = s.time()
+    for n, k in ((-1, 1), (2, 0)):
+        with pytest.raises(DhError) as e:
+            s.adjoint_advance(n, k, lam)
+        assert e.value.status == DH_ERR_ARG
+    assert s.time() == t0
+    s.close()
