@@ -10,6 +10,7 @@ barrier + synchronize on both sides; state buffers (3 x 336 MB) exceed the 126 M
 is needed.  value = cell-updates/s (N^3 * K / device time, summed over ranks).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--grid 256]
+  python bench.py --profile-case stage|adjoint|corrector|selfgrav [--profile-grid n]   (for ncu)
 """
 from __future__ import annotations
 
@@ -709,6 +710,58 @@ def corrector_leg(args):
                        f"{sub} substeps per coarse step (measured cost ratio)"}
 
 
+def profile_case(case: str, n):
+    """Small fixed workloads for profiling one kernel family under ncu: a few seconds and a few
+    hundred MB on the device each, no timing.  stage: 3 forward steps of the driven cooling box;
+    adjoint: dh_adjoint_advance over 2 steps of decaying turbulence; corrector: 3 network
+    forwards and 1 backward; selfgrav: 4 self-gravitating steps (gravity, forcing, cooling)."""
+    import torch
+    from paper_2512_13403_b300 import build as _build
+    from paper_2512_13403_b300 import inputs
+    from paper_2512_13403_b300.solver import Config, Solver
+    _build.build()
+    n = n or {"stage": 128, "adjoint": 128, "corrector": 64, "selfgrav": 1024}[case]
+    shape = (n, n, n)
+    if case == "stage":
+        s = Solver(Config(shape=shape, precision="f32", forcing=True, cooling=True, t_floor=0.05))
+        s.init_state(torch.from_numpy(inputs.cooling_box(shape)).float().cuda().contiguous())
+        s.advance(3)
+        torch.cuda.synchronize()
+        print("stage", n, s.time())
+    elif case == "adjoint":
+        s = Solver(Config(shape=shape, precision="f32"))
+        s.init_state(torch.from_numpy(inputs.decaying_turbulence(shape, seed=2, sigma=0.5, mach=2.0))
+                     .float().cuda().contiguous())
+        lam = torch.randn((5,) + shape, generator=torch.Generator().manual_seed(0)).cuda()
+        out = s.adjoint_advance(2, 2, lam)
+        torch.cuda.synchronize()
+        print("adjoint", n, float(out.abs().sum()))
+    elif case == "corrector":
+        from paper_2512_13403_b300 import corrector as cr
+        U = torch.from_numpy(inputs.decaying_turbulence(shape, seed=1, sigma=0.5, mach=1.0, p_sigma=0.3)) \
+            .float().cuda().contiguous()
+        mu = [float(U[c].mean()) for c in range(5)]
+        sg = [float(U[c].std()) for c in range(5)]
+        net = cr.Network(shape)
+        net.set_params(cr.init_params(0, out_scale=1.0).cuda(), mu, sg)
+        grads = torch.zeros(cr.NPARAM, device="cuda")
+        for _ in range(3):
+            net.forward(U)
+        net.backward(U, U, grads)
+        torch.cuda.synchronize()
+        print("corrector", n, float(grads.abs().sum()))
+    elif case == "selfgrav":
+        s = Solver(Config(shape=shape, precision="f32", forcing=True, cooling=True, t_floor=0.05,
+                          gravity=True, four_pi_G=1.0, mg_tol=1e-6, mg_max_cycles=30))
+        U0 = inputs.self_gravitating_box_device(shape, seed=5, sigma=1.0)
+        s.init_state(U0)
+        del U0
+        torch.cuda.empty_cache()
+        s.advance(4)
+        torch.cuda.synchronize()
+        print("selfgrav", n, s.time(), s.mg_stats())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -741,7 +794,13 @@ def main():
     ap.add_argument("--corr-snapshots", type=int, default=100)
     ap.add_argument("--corr-epochs", type=int, default=4)
     ap.add_argument("--corr-eval-seeds", type=int, nargs="+", default=[200, 201, 202, 203, 204])
+    ap.add_argument("--profile-case", choices=["stage", "adjoint", "corrector", "selfgrav"],
+                    help="run one small untimed workload for a profiler, print nothing else")
+    ap.add_argument("--profile-grid", type=int, default=None)
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case, args.profile_grid)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -27,8 +27,11 @@ training follows.
 
 Pins: tests/test_oracle_corrector.py (brute-force convolution, delta-kernel translation,
 translation equivariance, gelu values and derivative, bf16 rounding of hand values, zero
-network = identity map, flux form: exact conservation and a single face moving mass between
-two cells, the transposed divergence, and the rollout gradient against finite differences).
+network = identity map, hand-evaluated layer composition of a centre-tap network (bf16
+roundings, GELU on layers 1-2 only, normalisation, output scale), hand-evaluated floors with
+each one binding alone and together, flux form: exact conservation and a single face moving
+mass between two cells, the transposed divergence, and the rollout gradient against finite
+differences).
 """
 from __future__ import annotations
 

@@ -169,3 +169,84 @@ def test_rollout_gradient_matches_finite_differences(form, monkeypatch):
                                         w, 1e-9, 1e-6, 5 / 3))
     fd = (f(eps) - f(-eps)) / (2 * eps)
     assert ad == pytest.approx(fd, rel=1e-6)
+
+
+def _centre_tap(M):
+    """3x3x3 kernels whose only nonzero tap is the centre one: the convolution is then the
+    per-cell linear map M."""
+    M = torch.tensor(M, dtype=torch.float64)
+    W = torch.zeros(M.shape + (3, 3, 3), dtype=torch.float64)
+    W[..., 1, 1, 1] = M
+    return W
+
+
+def _t(v):
+    return torch.tensor(v, dtype=torch.float64)
+
+
+def test_layer_composition_hand_values():
+    """A 5 -> 1 -> 1 -> 5 network with centre-tap kernels (a pointwise MLP), evaluated by hand
+    through normalise -> bf16 -> conv -> GELU -> bf16 -> conv -> GELU -> bf16 -> conv -> * s
+    (Sec. 7 corrector; the GELU values are the standard normal CDF tabulated at 1 and -1).
+
+    Cell A, U = (3, 1, 0, 0, 5), mu = (1, 0, 0, 0, 1), sigma = (2, 1, 1, 1, 4):
+      x0 = ((3-1)/2, 1, 0, 0, (5-1)/4) = (1, 1, 0, 0, 1)          (exact in bf16)
+      z1 = 1 * x0[0] + 0 = 1;  gelu(1) = Phi(1) = 0.8413447460685429
+      h1 = bf16(0.84134...) = 215/256 = 0.83984375   (215.38 ulps of 2^-8, rounded down)
+      z2 = 1 * h1 + 41/256 = 1;  h2 = 215/256 again
+      y  = (h2 + 0.5, 0, 0, 0, -2 h2) = (1.33984375, 0, 0, 0, -1.6796875)   (no GELU here)
+      U' = U + s y, s = (0.5, 1, 1, 1, 0.25): rho' = 3.669921875, E' = 4.580078125
+      (kinetic energy 0.5/3.67 is far below E', so the floors do not act).
+    Cell B, U = (-1, 1, 0, 0, 5): x0[0] = -1, z1 = -1, gelu(-1) = Phi(1) - 1 = -0.15865525393145707
+      h1 = bf16(.) = -162/1024 = -0.158203125   (162.46 ulps of 2^-10, rounded down)
+      z2 = -162/1024 + 164/1024 = 2^-9;  gelu(2^-9) = 2^-9 Phi(2^-9) = 2^-10 (1 + 1.6e-3)
+      h2 = bf16(.) = 2^-10   (below half an ulp, 2^-18, above 2^-10)
+      y  = (2^-10 + 0.5, 0, 0, 0, -2^-9) = (0.5009765625, 0, 0, 0, -0.001953125)
+      rho = -1 + 0.5 * 0.5009765625 < rho_floor = 1e-3  ->  rho' = 1e-3
+      E' = max(5 - 2^-9 / 4, 0.5 * 1^2 / 1e-3 + 1e-3 * 0.05 / (2/3)) = 500.000075.
+    A GELU after the last layer, a missing bf16 rounding, (U/sigma - mu) for the normalisation
+    or a missing output scale each changes one of these numbers."""
+    p = {"W1": _centre_tap([[1.0, 0, 0, 0, 0]]), "b1": _t([0.0]),
+         "W2": _centre_tap([[1.0]]), "b2": _t([41 / 256]),
+         "W3": _centre_tap([[1.0], [0], [0], [0], [-2.0]]), "b3": _t([0.5, 0, 0, 0, 0])}
+    U = torch.zeros(5, 1, 1, 2, dtype=torch.float64)
+    U[:, 0, 0, 0] = _t([3.0, 1.0, 0.0, 0.0, 5.0])
+    U[:, 0, 0, 1] = _t([-1.0, 1.0, 0.0, 0.0, 5.0])
+    mu, sg, s = [1.0, 0, 0, 0, 1.0], [2.0, 1, 1, 1, 4.0], [0.5, 1, 1, 1, 0.25]
+    y, t = oc.forward(U, p, mu, sg)
+    assert t["h1"][0, 0, 0].tolist() == [0.83984375, -0.158203125]
+    assert t["h2"][0, 0, 0].tolist() == [0.83984375, 2.0 ** -10]
+    assert y[:, 0, 0, 0].tolist() == [1.33984375, 0.0, 0.0, 0.0, -1.6796875]
+    assert y[:, 0, 0, 1].tolist() == [0.5009765625, 0.0, 0.0, 0.0, -0.001953125]
+    out = oc.correct(U, p, mu, sg, 1e-3, 0.05, 5 / 3, out_scale=s)
+    assert out[:, 0, 0, 0].tolist() == [3.669921875, 1.0, 0.0, 0.0, 4.580078125]
+    assert out[:, 0, 0, 1].tolist()[:4] == [1e-3, 1.0, 0.0, 0.0]
+    assert float(out[4, 0, 0, 1]) == pytest.approx(500.000075, rel=1e-15)
+
+
+def test_floors_hand_values():
+    """The floors after the correction (Sec. 7 with the temperature floor of Sec. 4.3): rho is
+    raised to rho_floor first, then E to |m|^2 / (2 rho') + rho' T_floor / (gamma - 1) with the
+    floored rho'.  All weights zero, so y = b3 and U' = U + b3 (s = 1).  rho_floor = 0.01,
+    T_floor = 0.05, gamma = 5/3, so the thermal floor is 0.075 rho'.  b3 = (-1, 0.1, 0, 0, -0.5).
+      A: U = (0.5, 0.2, -0.1, 0, 0.6) -> (-0.5, 0.3, -0.1, 0, 0.1); rho' = 0.01;
+         E' = 0.5 (0.09 + 0.01) / 0.01 + 0.01 * 0.075 = 5.00075        (both floors bind)
+      B: U = (2, 0.2, 0.2, 0.1, 0.6) -> (1, 0.3, 0.2, 0.1, 0.1);
+         E' = 0.5 (0.09 + 0.04 + 0.01) / 1 + 0.075 = 0.145             (only the energy floor)
+      C: U = (3, 0, 0, 0, 2) -> (2, 0.1, 0, 0, 1.5);
+         floor energy 0.005 / 2 + 0.15 = 0.1525 < 1.5, so E' = 1.5     (neither)
+    Kinetic energy taken from the unfloored rho, or E floored before rho, gives a negative
+    floor energy in A and leaves E' = 0.1 there."""
+    z = lambda *s: torch.zeros(s, dtype=torch.float64)
+    p = {"W1": z(32, 5, 3, 3, 3), "b1": z(32), "W2": z(32, 32, 3, 3, 3), "b2": z(32),
+         "W3": z(5, 32, 3, 3, 3), "b3": _t([-1.0, 0.1, 0.0, 0.0, -0.5])}
+    U = torch.zeros(5, 1, 1, 3, dtype=torch.float64)
+    U[:, 0, 0, 0] = _t([0.5, 0.2, -0.1, 0.0, 0.6])
+    U[:, 0, 0, 1] = _t([2.0, 0.2, 0.2, 0.1, 0.6])
+    U[:, 0, 0, 2] = _t([3.0, 0.0, 0.0, 0.0, 2.0])
+    out = oc.correct(U, p, [0.0] * 5, [1.0] * 5, 0.01, 0.05, 5 / 3, out_scale=[1.0] * 5)
+    expect = [[0.01, 0.3, -0.1, 0.0, 5.00075],
+              [1.0, 0.3, 0.2, 0.1, 0.145],
+              [2.0, 0.1, 0.0, 0.0, 1.5]]
+    for i, e in enumerate(expect):
+        assert out[:, 0, 0, i].tolist() == pytest.approx(e, rel=1e-14, abs=1e-15)
