@@ -35,14 +35,53 @@ ADJ_BYTES_STAGE = 70    # float32 per adjoint stage launch, average of stage-2^T
                         # write lambda_U1: 60 B) and stage-1^T (read U^n, lambda_U1, lambda;
                         # write lambda^n: 80 B)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp instructions
-# (smsp__inst_executed.sum) of one stage-2 launch at 256^3, from one ncu capture of the current
-# kernel source
-STAGE2_DRAM_BYTES_256 = 702899456 + 308701184
-STAGE2_WARP_INSTR_256 = 693901568
-# the same for stage_adjoint_kernel<float> at 256^3, averaged over its two launches per RK2 step
-# (stage-2 transposed: 1029 MB, 1.411e9; stage-1 transposed with the extra term: 1378 MB, 1.412e9)
-ADJ_DRAM_BYTES_256 = (708688896 + 320567808 + 1055478272 + 322707456) // 2
-ADJ_WARP_INSTR_256 = (1410642007 + 1411619161) // 2
+# (smsp__inst_executed.sum) of one launch at 256^3, from one ncu capture each, with the hash of
+# the kernel sources they were taken on (source_hash below).  A run whose sources hash
+# differently reports null for these fields: the counters describe another kernel.
+NCU_COUNTERS = {
+    "stage2": {"sources": ["hydro.cu", "dh_device.cuh", "dh_sources.cuh", "async_copy.cuh"],
+               "hash": None, "dram_bytes": None, "warp_instr": None,
+               "profile": "profiles/stage_kernels_driven_cooling_turbulence_256cubed.md"},
+    # averaged over the kernel's two launches per RK2 step
+    "adjoint": {"sources": ["adjoint.cu", "dh_adjoint.cuh", "dh_device.cuh", "async_copy.cuh"],
+                "hash": None, "dram_bytes": None, "warp_instr": None,
+                "profile": "profiles/stage_adjoint_kernel_decaying_turbulence_128cubed.md"},
+}
+
+
+def source_hash(files) -> str:
+    """sha256 (first 16 hex digits) of the named kernel sources, in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2512_13403_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_counters(kernel: str):
+    """(dram bytes, warp instructions, note) of `kernel` when they were taken on the current
+    sources, else (None, None, why)."""
+    k = NCU_COUNTERS[kernel]
+    cur = source_hash(k["sources"])
+    if k["hash"] is None or k["hash"] != cur:
+        return None, None, f"no ncu counters for the current sources (hash {cur})"
+    return k["dram_bytes"], k["warp_instr"], f"ncu capture of these sources ({k['profile']})"
+
+
+def _finite_or_null(x):
+    """The JSON line's numbers: inf / nan become null (strict JSON has neither)."""
+    if isinstance(x, float) and not math.isfinite(x):
+        return None
+    if isinstance(x, dict):
+        return {k: _finite_or_null(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_finite_or_null(v) for v in x]
+    return x
+
+
+def emit(line: dict):
+    print(json.dumps(_finite_or_null(line), allow_nan=False), flush=True)
 
 
 def _peaks():
@@ -184,7 +223,7 @@ def run_reference(args):
                              "cores": torch.get_num_threads(),
                              "sample": f"{grid}^3, {steps} steps after {args.warmup} warm-up"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 def aggregate_replicas(ms: float, e2e_s: float, ws: int, cells: int, steps: int, device):
@@ -229,7 +268,6 @@ def run_ours(args):
         stream.synchronize()
 
         launches0 = s.launch_count()
-        s.profile(True)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         if ws > 1:
@@ -243,9 +281,15 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
         gpu_launches = s.launch_count() - launches0
+        t_sim, nstep = s.time()
+        # per-kernel durations: a second timed pass of the same K steps with CUDA events around
+        # every launch on the solver's stream (kept out of the headline region above)
+        s.profile(True)
+        with ClockSampler(local) as clk_prof:
+            s.advance(args.steps)
+            stream.synchronize()
         prof = {k: s.profile_read(k) for k in ("stage1", "stage2", "prologue")}
         s.profile(False)
-        t_sim, nstep = s.time()
 
         # end to end through the public API with host buffers: upload the initial state from
         # pinned memory, K steps each followed by a host read of the conserved totals (the
@@ -289,7 +333,10 @@ def run_ours(args):
                      "achieved": ach2, "peak": peak, "unit": "GB/s", "frac": ach2 / peak,
                      "peak_source": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_launch": FWD_BYTES_STAGE2 * cells,
-                     "avg_launch_ms": stage2_ms},
+                     "avg_launch_ms": stage2_ms,
+                     "timing": "CUDA events around each launch, in a second timed pass of the "
+                               "same K steps (the headline region carries no per-launch events)",
+                     "pass_clocks": clk_prof.summary()},
         "kernels": {"stage1": {"launches": n1, "avg_ms": stage1_ms, "achieved_GBps": ach1,
                                "frac": ach1 / peak},
                     "stage2": {"launches": n2, "avg_ms": stage2_ms, "achieved_GBps": ach2,
@@ -306,25 +353,32 @@ def run_ours(args):
     # live launch time, against 4 issue slots per SM per cycle at the sampled SM clock
     clk = line["clocks"].get("sm_mhz") or 2032.0
     if n == 256:
-        line["roofline"]["traffic"] = STAGE2_DRAM_BYTES_256
-        issue_peak = 148 * 4 * clk * 1e6
-        issue = STAGE2_WARP_INSTR_256 / (stage2_ms * 1e-3)
-        line["roofline_alu"] = {"bound": "alu", "kernel": "stage2", "achieved": issue,
-                                "peak": issue_peak, "unit": "warp-instr/s",
-                                "frac": issue / issue_peak,
-                                "note": "warp instructions per launch from ncu; peak = 148 SMs x 4 "
-                                        "issue slots x median SM clock sampled during the run"}
+        dram, instr, note = ncu_counters("stage2")
+        line["roofline"]["traffic"] = dram
+        line["roofline"]["traffic_source"] = note
+        if instr is not None:
+            issue_peak = 148 * 4 * clk * 1e6
+            issue = instr / (stage2_ms * 1e-3)
+            line["roofline_alu"] = {"bound": "alu", "kernel": "stage2", "achieved": issue,
+                                    "peak": issue_peak, "unit": "warp-instr/s",
+                                    "frac": issue / issue_peak,
+                                    "note": "warp instructions per launch from " + note +
+                                            "; peak = 148 SMs x 4 issue slots x median SM clock "
+                                            "sampled during the run"}
     if not args.no_adjoint:
         line["adjoint"] = adjoint_leg(args, stream)
         if n == 256:
             adj = line["adjoint"]
-            adj["roofline"]["traffic"] = ADJ_DRAM_BYTES_256
-            issue = ADJ_WARP_INSTR_256 / (adj["roofline"]["avg_launch_ms"] * 1e-3)
-            adj["roofline_alu"] = {"bound": "alu", "kernel": "stage_adjoint_kernel<float>",
-                                   "achieved": issue, "peak": 148 * 4 * clk * 1e6,
-                                   "unit": "warp-instr/s", "frac": issue / (148 * 4 * clk * 1e6),
-                                   "note": "warp instructions per launch from ncu (mean of the two "
-                                           "launches of a step); peak as for the forward"}
+            dram, instr, note = ncu_counters("adjoint")
+            adj["roofline"]["traffic"] = dram
+            adj["roofline"]["traffic_source"] = note
+            if instr is not None:
+                issue = instr / (adj["roofline"]["avg_launch_ms"] * 1e-3)
+                adj["roofline_alu"] = {"bound": "alu", "kernel": "stage_adjoint_kernel<float>",
+                                       "achieved": issue, "peak": 148 * 4 * clk * 1e6,
+                                       "unit": "warp-instr/s", "frac": issue / (148 * 4 * clk * 1e6),
+                                       "note": "warp instructions per launch from " + note +
+                                               " (mean of the two launches of a step)"}
     if not args.no_selfgrav:
         line["self_gravitating"] = selfgrav_leg(args, stream)
     if not args.no_scheme_variants:
@@ -336,7 +390,7 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(budget_s=args.cpu_budget)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line)
     if ws > 1:
         torch.distributed.destroy_process_group()
 

@@ -123,12 +123,35 @@ dh_status dh_get_time(dh_ctx* ctx, double* t, long long* nstep);
    Sec. 2.1 implies: theta = time, step count, OU table, gravity warm start).  dh_save writes
    the current state, t, dt, the step count (which also numbers the OU draws), the OU tables
    and hold flag, and with gravity the potential that warm-starts the next solve (its float-float
-   words: n hi floats then n lo floats), with a checksum; it settles pending steps first.  dh_load reads such a file into a context created
-   with the same grid, precision, physics switches, OU seed, gamma and cell widths (else
-   DH_ERR_ARG, context unchanged), after which stepping continues bit for bit as in the saved
-   context.  DH_ERR_ARG for unreadable, truncated or corrupted files.  Both synchronise. */
+   words: n hi floats then n lo floats), with a checksum; it settles pending steps first.  dh_load
+   reads such a file into a context created with the same configuration in every dh_config
+   field (grid, precision, cell widths, gamma, CFL and dt_max, limiter and integrator, the
+   forcing, cooling and multigrid settings; else DH_ERR_ARG naming the first differing field,
+   context unchanged), after which stepping continues bit for bit as in the saved context.  DH_ERR_ARG for unreadable, truncated or corrupted files.  Both synchronise. */
 dh_status dh_save(dh_ctx* ctx, const char* path);
 dh_status dh_load(dh_ctx* ctx, const char* path);
+
+/* Diagnostics of the run so far (a metrics record per step when called after each step).
+   The paper keeps none beyond its figures; the record carries what the method's failure and
+   accuracy conditions depend on: the time and step, the status bits raised since the state was
+   set (DH_FLAG_*: DH_FLAG_COOL_CAP is informational, a cell reached the cooling substep cap of
+   Sec. 4.3), the largest cooling substep count of any cell since the previous dh_get_metrics
+   (1 when cooling ran without subcycling, 0 without cooling or steps), the last Poisson
+   solve's cycle count and relative residual (Sec. 5.2), the float64 conserved totals and the
+   minima over cells of rho and P of the current state.  Settles enqueued steps and returns
+   their status; synchronises. */
+enum { DH_FLAG_NONFINITE = 1, DH_FLAG_POSITIVITY = 2, DH_FLAG_MG_NOCONV = 4, DH_FLAG_COOL_CAP = 8 };
+typedef struct dh_metrics {
+  double t, dt;             /* time after the last completed step, and its dt            */
+  long long nstep;          /* completed steps                                           */
+  unsigned flags;           /* DH_FLAG_* bits                                            */
+  int cool_max_substeps;    /* largest cooling substep count since the previous read     */
+  int mg_cycles;            /* cycles of the last Poisson solve (0 without gravity)      */
+  double mg_residual;       /* its ||F - A phi||_2 / ||F||_2                             */
+  double totals[5];         /* sums over cells of rho, m_x, m_y, m_z, E (float64)        */
+  double rho_min, p_min;    /* minima over cells of rho and P                            */
+} dh_metrics;
+dh_status dh_get_metrics(dh_ctx* ctx, dh_metrics* out);
 
 /* CFL time step C * min_cells,axes dx_a / (|v_a| + c_s) of the current state (App. A.4). */
 dh_status dh_compute_dt(dh_ctx* ctx, double* dt);
@@ -312,6 +335,34 @@ dh_status dh_cnn_vjp(dh_cnn* cnn, const float* dL_dcorr, float* grads, float* dL
    DH_ERR_NONFINITE if a corrected value is not finite (U then holds the corrected values). */
 dh_status dh_cnn_correct_state(dh_cnn* cnn, float* U, double rho_floor, double T_floor,
                                double gamma);
+/* Solver-in-the-loop rollout training (Sec. 7: the loss of a rollout of solver steps, each
+   followed by the correction, differentiated through both).  One term of the rollout loss for
+   a state U and its reference T (float32, 5 planes of the network's grid, device):
+   coef * sum over fields c and cells of ((U - T) / w_c)^2, with w5 five positive per-field
+   weights (host).  With lam (nullable, device, same layout) also its gradient
+   2 coef (U - T) / w_c^2, written (accumulate = 0) or added (accumulate = 1).  With loss_acc
+   (nullable, one device double) the term is added to *loss_acc.  Asynchronous on the
+   network's stream; DH_ERR_ARG for a non-positive weight. */
+dh_status dh_cnn_rollout_misfit(dh_cnn* cnn, const float* U, const float* T, const float* w5,
+                                double coef, float* lam, int accumulate, double* loss_acc);
+/* The floors of the correction transposed (Sec. 7 corrector with the temperature floor of
+   Sec. 4.3).  The last dh_cnn_forward must have been on V (the state before the correction);
+   lam (device, 5 planes) holds dL/dU' for U' = floors(V + dU(V)) and is overwritten with
+   dL/d(V + dU).  rho' = max(rho, rho_floor) passes the gradient where rho >= rho_floor;
+   E' = max(E, |m|^2/(2 rho') + rho' T_floor/(gamma - 1)) gives it to the larger argument and
+   splits an exact tie evenly, the floor's share flowing on to m and rho'.  Asynchronous.
+   DH_ERR_STATE without a forward. */
+dh_status dh_cnn_floor_vjp(dh_cnn* cnn, const float* V, float* lam, double rho_floor,
+                           double T_floor, double gamma);
+/* Per-field mean and standard deviation (n - 1 normalisation) over `count` samples of A - B
+   (B nullable: A alone), each sample 5 planes of the network's grid (float32, device,
+   contiguous): the normalisation statistics of the corrector's training set (Sec. 7).  out10
+   (host): 5 means, then 5 standard deviations.  Float64 sums in a fixed order.  Synchronises. */
+dh_status dh_cnn_field_moments(dh_cnn* cnn, const float* A, const float* B, long long count,
+                               double* out10);
+/* y <- y + a x over n floats (device), on `stream`: the sums of gradient contributions in
+   rollout training. */
+dh_status dh_axpy(long long n, double a, const float* x, float* y, void* stream);
 /* Adam (Kingma & Ba) on n parameters: m, v are caller-owned moment buffers (device), step >= 1
    the 1-based step count for the bias corrections. */
 dh_status dh_adam_step(float* params, const float* grads, float* m, float* v, long long n,
@@ -339,9 +390,10 @@ dh_status dh_correct(dh_ctx* ctx);
                 DH_ERR_ARG with the limit in dh_last_error(NULL)
      totals_out device pointer to 5 doubles (rho, m_x, m_y, m_z, E), caller-owned
      cuda_stream cudaStream_t on which the work is ordered (NULL = legacy default stream)
-   Asynchronous: the result is ready when the stream reaches this point.  The first call on a
-   device looks the array's device address up once (cudaGetSymbolAddress) and caches it; make
-   that first call before capturing the stream into a graph.  All calls share the array, which
+   Asynchronous: the result is ready when the stream reaches this point.  A call on a stream
+   that is not being captured looks the array's device address up (cudaGetSymbolAddress) and
+   caches it per device; a call on a stream under capture uses the cached address, so make one
+   call on the device before capturing (and again after a cudaDeviceReset).  All calls share the array, which
    keeps the last call's contents (every slot a call reads is written earlier in the same call);
    calls whose kernels overlap on the GPU race on it and may return wrong sums. */
 dh_status dh_conserved_totals_static(const void* U, int precision, long long n_cells,

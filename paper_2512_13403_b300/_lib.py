@@ -35,6 +35,16 @@ class DhConfig(C.Structure):
     ]
 
 
+class DhMetrics(C.Structure):
+    _fields_ = [
+        ("t", C.c_double), ("dt", C.c_double), ("nstep", C.c_longlong), ("flags", C.c_uint),
+        ("cool_max_substeps", C.c_int), ("mg_cycles", C.c_int), ("mg_residual", C.c_double),
+        ("totals", C.c_double * 5), ("rho_min", C.c_double), ("p_min", C.c_double),
+    ]
+
+
+DH_FLAG_NONFINITE, DH_FLAG_POSITIVITY, DH_FLAG_MG_NOCONV, DH_FLAG_COOL_CAP = 1, 2, 4, 8
+
 _P = C.c_void_p
 _SIGNATURES = {
     "dh_config_default": (None, [C.POINTER(DhConfig), C.c_int, C.c_int, C.c_int]),
@@ -46,6 +56,7 @@ _SIGNATURES = {
     "dh_advance": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double)]),
     "dh_get_time": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "dh_compute_dt": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "dh_get_metrics": (C.c_int, [_P, C.POINTER(DhMetrics)]),
     "dh_conserved_totals": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "dh_forcing_field": (C.c_int, [_P, _P, C.c_int]),
     "dh_forcing_modes": (C.c_int, [_P, C.POINTER(C.c_double)]),
@@ -78,6 +89,10 @@ _SIGNATURES = {
     "dh_cnn_forward": (C.c_int, [_P, _P, _P]),
     "dh_cnn_backward": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_double)]),
     "dh_cnn_correct_state": (C.c_int, [_P, _P, C.c_double, C.c_double, C.c_double]),
+    "dh_cnn_rollout_misfit": (C.c_int, [_P, _P, _P, C.POINTER(C.c_float), C.c_double, _P, C.c_int, _P]),
+    "dh_cnn_floor_vjp": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.c_double]),
+    "dh_cnn_field_moments": (C.c_int, [_P, _P, _P, C.c_longlong, C.POINTER(C.c_double)]),
+    "dh_axpy": (C.c_int, [C.c_longlong, C.c_double, _P, _P, _P]),
     "dh_adam_step": (C.c_int, [_P, _P, _P, _P, C.c_longlong, C.c_double, C.c_double, C.c_double,
                                C.c_double, C.c_int, _P]),
     "dh_set_corrector": (C.c_int, [_P, _P, C.POINTER(C.c_float)]),

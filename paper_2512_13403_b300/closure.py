@@ -113,13 +113,12 @@ def make_pairs(setup: ClosureSetup, log=None):
     return X, Y
 
 
-def normalisation(X: torch.Tensor, Y: torch.Tensor):
-    """Per-channel input mean/std and residual std (the correction's output scale)."""
-    mu = [float(X[:, c].mean()) for c in range(5)]
-    sigma = [max(float(X[:, c].std()), 1e-12) for c in range(5)]
-    R = Y - X
-    out = [max(float(R[:, c].std()), 1e-12) for c in range(5)]
-    return mu, sigma, out
+def normalisation(X: torch.Tensor, Y: torch.Tensor, net: Network):
+    """Per-channel input mean/std and residual (Y - X) std, the correction's output scale
+    (dh_cnn_field_moments on the network's grid)."""
+    mu, sd = net.field_moments(X.contiguous())
+    _, rsd = net.field_moments(Y.contiguous(), X.contiguous())
+    return mu, [max(v, 1e-12) for v in sd], [max(v, 1e-12) for v in rsd]
 
 
 def train(X: torch.Tensor, Y: torch.Tensor, epochs: int = 4, lr0: float = 1e-3, lr1: float = 1e-4,
@@ -128,7 +127,7 @@ def train(X: torch.Tensor, Y: torch.Tensor, epochs: int = 4, lr0: float = 1e-3, 
     lr1.  Returns (params, (mu, sigma, out_scale), losses)."""
     shape = tuple(X.shape[2:])
     net = Network(shape, form=form)
-    mu, sigma, out = normalisation(X, Y)
+    mu, sigma, out = normalisation(X, Y, net)
     params = init_params(seed, out_scale=0.01, form=form).cuda()
     opt = Adam(params, lr=lr0)
     grads = torch.zeros(nparam(form), dtype=torch.float32, device="cuda")
@@ -329,36 +328,43 @@ class RolloutTrainer:
 
     def loss_and_grad(self, traj: Trajectory, params, norm, weights):
         """L = (1/S) sum_s mean(((U_s - T_s) / w)^2), U_s = C(H_s(U_{s-1})); returns (L, dL/dparams).
-        The floors of the correction are taken as inactive in the gradient."""
+        Every term and gradient is a library call: the loss terms and their gradients
+        (dh_cnn_rollout_misfit), the floors (dh_cnn_floor_vjp), the network (dh_cnn_vjp), the
+        solver step (dh_adjoint_advance_dt) and the sums (dh_axpy)."""
+        from .corrector import axpy
         mu, sigma, out = norm
         self.net.set_params(params, mu, sigma, out)
         S = len(traj.dts)
-        n5 = 5 * traj.U0[0].numel()
-        w2 = torch.tensor([float(v) ** 2 for v in weights], dtype=torch.float32, device="cuda").reshape(5, 1, 1, 1)
-        rho_floor = self.rho_floor_frac * float(traj.U0[0].mean())
+        coef = 1.0 / (5 * traj.U0[0].numel() * S)
+        rho_mean = self.net.field_moments(traj.U0.contiguous())[0][0]
+        rho_floor = self.rho_floor_frac * rho_mean
+        T_floor, gamma = self.cfg.t_floor, self.cfg.gamma
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
         Us, Vs = [traj.U0], []
-        loss = 0.0
         for k in range(S):
             self._start(Us[-1], traj.modes[k])
             self.solver.step(traj.dts[k])
             V = self.solver.get_state()
             Vs.append(V)
             Un = V.clone()
-            self.net.correct_state(Un, rho_floor, self.cfg.t_floor, self.cfg.gamma)
+            self.net.correct_state(Un, rho_floor, T_floor, gamma)
             Us.append(Un)
-            loss += float((((Un - traj.targets[k]) ** 2) / w2).sum()) / (n5 * S)
+            self.net.rollout_misfit(Un, traj.targets[k], weights, coef, loss_acc=loss)
         total = torch.zeros_like(self.grads)
-        lam = 2.0 * (Us[S] - traj.targets[S - 1]) / (w2 * n5 * S)
+        lam = torch.empty_like(Us[S])
+        self.net.rollout_misfit(Us[S], traj.targets[S - 1], weights, coef, lam=lam)
         for k in reversed(range(S)):
             self.net.forward(Vs[k])
+            self.net.floor_vjp(Vs[k], lam, rho_floor, T_floor, gamma)
             gU = self.net.vjp(lam.contiguous(), self.grads)
-            total += self.grads
-            lam_V = (lam + gU).contiguous()
+            axpy(1.0, self.grads, total)
+            axpy(1.0, lam, gU)                   # dL/dV = (I + J_dU)^T dL/dY
             self._start(Us[k], traj.modes[k])
-            lam = self.solver.adjoint_advance(1, 1, lam_V, dt=traj.dts[k])
+            lam = self.solver.adjoint_advance(1, 1, gU, dt=traj.dts[k])
             if k > 0:
-                lam = lam + 2.0 * (Us[k] - traj.targets[k - 1]) / (w2 * n5 * S)
-        return loss, total
+                self.net.rollout_misfit(Us[k], traj.targets[k - 1], weights, coef, lam=lam,
+                                        accumulate=True)
+        return float(loss.item()), total
 
 
 def train_rollout(trajs: List[Trajectory], setup: ClosureSetup, params, norm, iters: int,
@@ -366,10 +372,12 @@ def train_rollout(trajs: List[Trajectory], setup: ClosureSetup, params, norm, it
     """Adam on the rollout loss, one trajectory per iteration (cycling).  Returns
     (params, losses, ms per iteration)."""
     nc = setup.coarse
-    if weights is None:
-        weights = [max(float(torch.stack([t[c] for tr in trajs for t in tr.targets]).std()), 1e-12)
-                   for c in range(5)]
     tr = RolloutTrainer((nc, nc, nc), _cfg(nc, setup, 0), form)
+    if weights is None:
+        # the per-field spread of the targets (the paper weights fields to comparable ranges)
+        allt = torch.stack([t for trj in trajs for t in trj.targets]).contiguous()
+        weights = [max(v, 1e-12) for v in tr.net.field_moments(allt)[1]]
+        del allt
     params = params.clone()
     opt = Adam(params, lr=lr)
     losses = []

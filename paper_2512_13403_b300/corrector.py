@@ -125,6 +125,41 @@ class Network:
         check(self.lib.dh_cnn_correct_state(self.h, C.c_void_p(U.data_ptr()), float(rho_floor),
                                             float(T_floor), float(gamma)))
 
+    def rollout_misfit(self, U: torch.Tensor, T: torch.Tensor, weights, coef: float, lam=None,
+                       accumulate: bool = False, loss_acc=None):
+        """dh_cnn_rollout_misfit: adds coef * sum((U - T)/w)^2 to loss_acc (a device float64
+        tensor) and writes or adds its gradient into lam."""
+        w = (C.c_float * 5)(*[float(v) for v in weights])
+        check(self.lib.dh_cnn_rollout_misfit(
+            self.h, C.c_void_p(U.data_ptr()), C.c_void_p(T.data_ptr()), w, float(coef),
+            C.c_void_p(lam.data_ptr() if lam is not None else 0), int(accumulate),
+            C.c_void_p(loss_acc.data_ptr() if loss_acc is not None else 0)))
+
+    def floor_vjp(self, V: torch.Tensor, lam: torch.Tensor, rho_floor: float, T_floor: float,
+                  gamma: float):
+        """dh_cnn_floor_vjp: lam (dL/dU' after the floors) becomes dL/d(V + dU), for the last
+        forward, which must have been on V."""
+        check(self.lib.dh_cnn_floor_vjp(self.h, C.c_void_p(V.data_ptr()), C.c_void_p(lam.data_ptr()),
+                                        float(rho_floor), float(T_floor), float(gamma)))
+
+    def field_moments(self, A: torch.Tensor, B: torch.Tensor = None):
+        """dh_cnn_field_moments over the samples of A (or A - B): (means, standard deviations),
+        five each."""
+        assert A.dtype == torch.float32 and A.is_cuda and A.is_contiguous()
+        count = A.numel() // (5 * int(np.prod(self.shape)))
+        out = (C.c_double * 10)()
+        check(self.lib.dh_cnn_field_moments(self.h, C.c_void_p(A.data_ptr()),
+                                            C.c_void_p(B.data_ptr() if B is not None else 0),
+                                            count, out))
+        return list(out[:5]), list(out[5:])
+
+
+def axpy(a: float, x: torch.Tensor, y: torch.Tensor):
+    """y += a x on the current stream (dh_axpy)."""
+    assert x.numel() == y.numel() and x.dtype == y.dtype == torch.float32
+    check(_lib.load().dh_axpy(x.numel(), float(a), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                              C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
 
 class Adam:
     """Moment buffers for dh_adam_step."""

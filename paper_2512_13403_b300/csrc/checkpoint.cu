@@ -1,13 +1,16 @@
 // File checkpoints of a context (dh_save / dh_load): everything a continuation depends on, so
 // that a loaded context steps bit for bit like the one that was saved.
 //
-// Layout (native byte order): 8-byte magic "DHCKPT02", a fixed header (geometry, precision,
-// physics switches, OU seed and hold flag, gamma and cell widths, t, dt, step count, OU
-// normalisation), the OU tables a_hat and its pre-update copy (96 doubles each; forcing only),
-// the state (5 planes of the context precision), the potential that warm-starts the next
-// Poisson solve as its float-float words (n hi floats, then n lo floats; gravity only), and a
-// 64-bit FNV-1a checksum of everything before it.  Version 02 replaced version 01's float64
-// potential by the float-float words (same size, other meaning): 01 files are refused.
+// Layout (native byte order): 8-byte magic "DHCKPT03", a fixed header (every configuration
+// field that changes a step: geometry, precision, the scheme, CFL and dt bound, the forcing,
+// cooling and multigrid settings; then the OU hold flag, t, dt, step count, OU normalisation),
+// the OU tables a_hat and its pre-update copy (96 doubles each; forcing only), the state (5
+// planes of the context precision), the potential that warm-starts the next Poisson solve as
+// its float-float words (n hi floats, then n lo floats; gravity only), and a 64-bit FNV-1a
+// checksum of everything before it.  A file is loaded only into a context whose configuration
+// equals the saved one in every field, so that the continuation is the saved run's.  Version
+// 03 added the scheme, forcing, cooling and multigrid settings to the header; 01 and 02 files
+// are refused.
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -18,16 +21,54 @@
 
 namespace {
 
-constexpr char kMagic[8] = {'D', 'H', 'C', 'K', 'P', 'T', '0', '2'};
+constexpr char kMagic[8] = {'D', 'H', 'C', 'K', 'P', 'T', '0', '3'};
+
+// the configuration fields a step depends on, in a fixed layout
+struct CkptConfig {
+  int32_t nx, ny, nz, precision;
+  int32_t forcing, cooling, gravity, nsub_max;
+  int32_t mg_max_cycles, mg_pre, mg_post, mg_smoother;
+  int32_t mg_cycle, limiter, integrator, pad;
+  uint64_t ou_seed;
+  double dx, dy, dz, gamma, cfl, dt_max;
+  double ou_tau, ou_arms, t_floor, cool_frac, c_cool;
+  double four_pi_G, mg_tol, mg_omega;
+};
 
 struct CkptHeader {
-  int32_t nx, ny, nz, precision;
-  int32_t forcing, cooling, gravity, ou_hold;
-  uint64_t ou_seed;
-  double gamma, dx, dy, dz;
+  CkptConfig cfg;
+  int32_t ou_hold, pad;
   double t, dt, ou_norm;
   int64_t nstep;
 };
+
+CkptConfig pack_config(const dh_config& g, int prec) {
+  CkptConfig k;
+  std::memset(&k, 0, sizeof(k));
+  k.nx = g.nx; k.ny = g.ny; k.nz = g.nz; k.precision = prec;
+  k.forcing = g.forcing; k.cooling = g.cooling; k.gravity = g.gravity; k.nsub_max = g.nsub_max;
+  k.mg_max_cycles = g.mg_max_cycles; k.mg_pre = g.mg_pre; k.mg_post = g.mg_post;
+  k.mg_smoother = g.mg_smoother; k.mg_cycle = g.mg_cycle; k.limiter = g.limiter;
+  k.integrator = g.integrator;
+  k.ou_seed = g.ou_seed;
+  k.dx = g.dx; k.dy = g.dy; k.dz = g.dz; k.gamma = g.gamma; k.cfl = g.cfl; k.dt_max = g.dt_max;
+  k.ou_tau = g.ou_tau; k.ou_arms = g.ou_arms; k.t_floor = g.t_floor; k.cool_frac = g.cool_frac;
+  k.c_cool = g.c_cool; k.four_pi_G = g.four_pi_G; k.mg_tol = g.mg_tol; k.mg_omega = g.mg_omega;
+  return k;
+}
+
+// The first field in which two configurations differ, or "" (floating-point fields compare
+// bit for bit, so that +inf matches +inf).
+std::string config_mismatch(const CkptConfig& a, const CkptConfig& b) {
+#define DH_CK(f) if (std::memcmp(&a.f, &b.f, sizeof(a.f)) != 0) return #f;
+  DH_CK(nx) DH_CK(ny) DH_CK(nz) DH_CK(precision) DH_CK(forcing) DH_CK(cooling) DH_CK(gravity)
+  DH_CK(nsub_max) DH_CK(mg_max_cycles) DH_CK(mg_pre) DH_CK(mg_post) DH_CK(mg_smoother)
+  DH_CK(mg_cycle) DH_CK(limiter) DH_CK(integrator) DH_CK(ou_seed) DH_CK(dx) DH_CK(dy) DH_CK(dz)
+  DH_CK(gamma) DH_CK(cfl) DH_CK(dt_max) DH_CK(ou_tau) DH_CK(ou_arms) DH_CK(t_floor)
+  DH_CK(cool_frac) DH_CK(c_cool) DH_CK(four_pi_G) DH_CK(mg_tol) DH_CK(mg_omega)
+#undef DH_CK
+  return "";
+}
 
 struct Fnv {
   uint64_t h = 1469598103934665603ull;
@@ -55,10 +96,8 @@ extern "C" dh_status dh_save(dh_ctx* c, const char* path) {
   const dh_config& g = c->cfg;
   CkptHeader h;
   std::memset(&h, 0, sizeof(h));
-  h.nx = g.nx; h.ny = g.ny; h.nz = g.nz; h.precision = c->prec;
-  h.forcing = g.forcing; h.cooling = g.cooling; h.gravity = g.gravity; h.ou_hold = c->ou_hold;
-  h.ou_seed = g.ou_seed;
-  h.gamma = g.gamma; h.dx = g.dx; h.dy = g.dy; h.dz = g.dz;
+  h.cfg = pack_config(g, c->prec);
+  h.ou_hold = c->ou_hold;
   h.t = c->host_rec.t; h.dt = c->host_rec.dt; h.ou_norm = c->host_rec.ou_norm;
   h.nstep = c->host_rec.nstep;
   std::vector<double> ahat(96, 0.0), ahat_prev(96, 0.0);
@@ -124,11 +163,11 @@ extern "C" dh_status dh_load(dh_ctx* c, const char* path) {
     return fail(c, DH_ERR_ARG, "dh_load: not a checkpoint of this library");
   }
   const dh_config& g = c->cfg;
-  if (h.nx != g.nx || h.ny != g.ny || h.nz != g.nz || h.precision != c->prec ||
-      h.forcing != g.forcing || h.cooling != g.cooling || h.gravity != g.gravity ||
-      h.ou_seed != g.ou_seed || h.gamma != g.gamma || h.dx != g.dx || h.dy != g.dy || h.dz != g.dz) {
+  const std::string diff = config_mismatch(h.cfg, pack_config(g, c->prec));
+  if (!diff.empty()) {
     std::fclose(f);
-    return fail(c, DH_ERR_ARG, "dh_load: the checkpoint was written by a different configuration");
+    return fail(c, DH_ERR_ARG, "dh_load: the checkpoint was written by a different configuration (" +
+                                   diff + " differs)");
   }
   std::vector<double> ahat(96), ahat_prev(96);
   std::vector<unsigned char> state(c->state_bytes);

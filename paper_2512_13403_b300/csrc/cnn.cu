@@ -337,6 +337,128 @@ static int grid_for(long long n) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// ---- solver-in-the-loop rollout training (Sec. 7) ---------------------------------------------
+struct Weights5 {
+  float iw2[5];   // 1 / w_c^2
+};
+
+// One term of the rollout loss, coef * sum over fields c and cells of ((U - T) / w_c)^2, as
+// per-block partials; with lam, also its gradient 2 coef (U - T) / w_c^2, written or added.
+__global__ void misfit_kernel(const float* __restrict__ U, const float* __restrict__ T, long long n,
+                              Weights5 w, double coef, float* __restrict__ lam, int accumulate,
+                              double* __restrict__ partial) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long b0 = blockIdx.x * per, b1 = b0 + per < n ? b0 + per : n;
+  for (long long q = b0 + threadIdx.x; q < b1; q += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const float d = U[c * n + q] - T[c * n + q];
+      s += (double)d * (double)d * (double)w.iw2[c];
+      if (lam) {
+        const float g = (float)(2.0 * coef * (double)w.iw2[c]) * d;
+        lam[c * n + q] = accumulate ? lam[c * n + q] + g : g;
+      }
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = coef * red[0];
+}
+
+// *acc += sum of partial[0..nb) in a fixed order (one warp)
+__global__ void add_blocks_kernel(const double* partial, int nb, double* acc) {
+  const int l = threadIdx.x;
+  double s = 0.0;
+  for (int b = l; b < nb; b += 32) s += partial[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (l == 0) *acc += s;
+}
+
+// The floors of the correction transposed: lam holds dL/dU' for U' = floors(Y), Y = V + dU(V)
+// (recomputed from the network output y of the forward on V exactly as correct_kernel forms
+// it), and becomes dL/dY.  rho' = max(Y_rho, rho_floor) passes the gradient where
+// Y_rho >= rho_floor; E' = max(Y_E, E_min), E_min = |m|^2 / (2 rho') + rho' T_floor / (gamma - 1),
+// gives it to the larger argument and splits an exact tie evenly; the share of E_min flows to
+// m (m / rho') and to rho' (-|m|^2 / (2 rho'^2) + T_floor / (gamma - 1)).
+__global__ void floor_vjp_kernel(const float* __restrict__ V, const float* __restrict__ y,
+                                 float* __restrict__ lam, long long n, const float* __restrict__ norm,
+                                 float rho_floor, float T_floor, float gm1, int form, ConvGeom geo) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    float v[5];
+    if (form == 0) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) v[c] = V[c * n + q] + norm[10 + c] * y[c * n + q];
+    } else {
+      int x, yy, z;
+      cell_xyz(q, geo, x, yy, z);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) v[c] = V[c * n + q] + norm[10 + c] * flux_div(y, n, geo, q, x, yy, z, c);
+    }
+    const float rho = fmaxf(v[0], rho_floor);
+    const float kin = 0.5f * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / rho;
+    const float Emin = kin + rho * T_floor / gm1;
+    const float gE = lam[4 * n + q];
+    const float gEmin = v[4] > Emin ? 0.0f : (v[4] < Emin ? gE : 0.5f * gE);
+    const float grho = lam[q] + gEmin * (T_floor / gm1 - kin / rho);
+    lam[q] = v[0] >= rho_floor ? grho : 0.0f;
+#pragma unroll
+    for (int a = 1; a <= 3; ++a) lam[a * n + q] += gEmin * v[a] / rho;
+    lam[4 * n + q] = gE - gEmin;
+  }
+}
+
+// Per-channel sums over `count` samples of 5 planes of n cells of A - B (B nullable): pass 1
+// (mean == nullptr) sums the values, pass 2 the squared deviations from mean[c].  Block
+// partials; blockIdx.y is the channel.
+__global__ void moments_kernel(const float* __restrict__ A, const float* __restrict__ B,
+                               long long count, long long n, const double* __restrict__ mean,
+                               double* __restrict__ partial) {
+  __shared__ double red[256];
+  const int c = blockIdx.y;
+  const long long total = count * n;
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  const long long b0 = blockIdx.x * per, b1 = b0 + per < total ? b0 + per : total;
+  const double m = mean ? mean[c] : 0.0;
+  double s = 0.0;
+  for (long long t = b0 + threadIdx.x; t < b1; t += blockDim.x) {
+    const long long p = t / n, q = t - p * n;
+    const long long i = (p * 5 + c) * n + q;
+    const double x = (double)A[i] - (B ? (double)B[i] : 0.0);
+    s += mean ? (x - m) * (x - m) : x;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(long long)c * gridDim.x + blockIdx.x] = red[0];
+}
+
+// out[c] = scale * sum of partial[c][0..nb), one warp per channel
+__global__ void channel_sums_kernel(const double* partial, int nb, double scale, double* out) {
+  const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b = l; b < nb; b += 32) s += partial[(long long)c * nb + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (l == 0) out[c] = scale * s;
+}
+
+__global__ void axpy_kernel(long long n, float a, const float* __restrict__ x, float* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = fmaf(a, x[i], y[i]);
+}
+
 }  // namespace dh
 
 using namespace dh;
@@ -408,7 +530,7 @@ extern "C" dh_status dh_cnn_create_form(int nx, int ny, int nz, int form, void* 
   A((void**)&c->dz2, prow * 4 * 16);
   A((void**)&c->dz1, prow * 4 * 16);
   A((void**)&c->partial, (size_t)c->nctas * 7 * 128 * 32 * sizeof(float));
-  A((void**)&c->red, (RBLOCKS + 8) * sizeof(double));
+  A((void**)&c->red, (5 * RBLOCKS + 16) * sizeof(double));
   A((void**)&c->bpart, 32 * BG_BLOCKS * sizeof(double));
   A((void**)&c->err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(unsigned));
@@ -575,6 +697,56 @@ extern "C" dh_status dh_adam_step(float* params, const float* grads, float* m, f
   adam_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, n, (float)lr,
                                                              (float)beta1, (float)beta2,
                                                              (float)eps, c1, c2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
+  return DH_OK;
+}
+
+extern "C" dh_status dh_cnn_rollout_misfit(dh_cnn* c, const float* U, const float* T,
+                                           const float* w5, double coef, float* lam,
+                                           int accumulate, double* loss_acc) {
+  if (!c || !U || !T || !w5) return DH_ERR_ARG;
+  Weights5 w;
+  for (int k = 0; k < 5; ++k) {
+    if (!(w5[k] > 0.0f)) { dh_set_global_error("dh_cnn_rollout_misfit: weights must be positive"); return DH_ERR_ARG; }
+    w.iw2[k] = 1.0f / (w5[k] * w5[k]);
+  }
+  misfit_kernel<<<RBLOCKS, 256, 0, c->stream>>>(U, T, c->ncell, w, coef, lam, accumulate, c->red);
+  if (loss_acc) add_blocks_kernel<<<1, 32, 0, c->stream>>>(c->red, RBLOCKS, loss_acc);
+  return cnn_cuda(c, cudaGetLastError(), "rollout misfit");
+}
+
+extern "C" dh_status dh_cnn_floor_vjp(dh_cnn* c, const float* V, float* lam, double rho_floor,
+                                      double T_floor, double gamma) {
+  if (!c || !V || !lam) return DH_ERR_ARG;
+  if (!c->have_forward) { dh_set_global_error("dh_cnn_floor_vjp: run dh_cnn_forward on V first"); return DH_ERR_STATE; }
+  floor_vjp_kernel<<<grid_for(c->ncell), 256, 0, c->stream>>>(
+      V, c->y, lam, c->ncell, c->norm_dev, (float)rho_floor, (float)T_floor, (float)(gamma - 1.0),
+      c->form, conv_geom(c->nx, c->ny, c->nz));
+  return cnn_cuda(c, cudaGetLastError(), "floor vjp");
+}
+
+extern "C" dh_status dh_cnn_field_moments(dh_cnn* c, const float* A, const float* B, long long count,
+                                          double* out10) {
+  if (!c || !A || !out10 || count < 1) return DH_ERR_ARG;
+  const long long N = count * c->ncell;
+  if (N < 2) { dh_set_global_error("dh_cnn_field_moments: need at least two values per channel"); return DH_ERR_ARG; }
+  double* res = c->red + 5 * RBLOCKS;   // 5 means, then 5 standard deviations
+  cudaStream_t s = c->stream;
+  moments_kernel<<<dim3(RBLOCKS, 5), 256, 0, s>>>(A, B, count, c->ncell, nullptr, c->red);
+  channel_sums_kernel<<<1, 160, 0, s>>>(c->red, RBLOCKS, 1.0 / (double)N, res);
+  moments_kernel<<<dim3(RBLOCKS, 5), 256, 0, s>>>(A, B, count, c->ncell, res, c->red);
+  channel_sums_kernel<<<1, 160, 0, s>>>(c->red, RBLOCKS, 1.0 / (double)(N - 1), res + 5);
+  CNN_TRY(cnn_cuda(c, cudaMemcpyAsync(out10, res, 10 * sizeof(double), cudaMemcpyDeviceToHost, s), "moments"));
+  CNN_TRY(cnn_cuda(c, cudaStreamSynchronize(s), "moments"));
+  for (int k = 5; k < 10; ++k) out10[k] = sqrt(out10[k]);
+  return DH_OK;
+}
+
+extern "C" dh_status dh_axpy(long long n, double a, const float* x, float* y, void* stream) {
+  if (!x || !y || n < 0) return DH_ERR_ARG;
+  if (n == 0) return DH_OK;
+  axpy_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, (float)a, x, y);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
   return DH_OK;

@@ -471,6 +471,44 @@ extern "C" dh_status dh_conserved_totals(dh_ctx* c, double out[5]) {
   return DH_OK;
 }
 
+static_assert(DH_FLAG_NONFINITE == dh::FLAG_NONFINITE && DH_FLAG_POSITIVITY == dh::FLAG_POSITIVITY &&
+                  DH_FLAG_MG_NOCONV == dh::FLAG_MG_NOCONV && DH_FLAG_COOL_CAP == dh::FLAG_COOL_CAP,
+              "public and device status bits");
+
+extern "C" dh_status dh_get_metrics(dh_ctx* c, dh_metrics* out) {
+  if (!c || !out) return fail(c, DH_ERR_ARG, "null argument");
+  if (!c->initialized) return fail(c, DH_ERR_STATE, "state not initialised");
+  // settle enqueued steps (their status is this call's status), then read the record
+  dh_status st = finish_steps(c, c->host_rec.nstep - c->pending_steps);
+  std::memset(out, 0, sizeof(*out));
+  out->t = c->host_rec.t;
+  out->dt = c->host_rec.dt;
+  out->nstep = c->host_rec.nstep;
+  out->flags = c->host_rec.flags;
+  out->cool_max_substeps = c->host_rec.cool_nsub_max;
+  if (c->cfg.cooling && out->cool_max_substeps < 1 && out->nstep > 0) out->cool_max_substeps = 1;
+  dh::mg_last(c, &out->mg_cycles, &out->mg_residual);
+  double* mins = c->partials + 2 * totals_blocks();
+  cudaError_t e = c->prec == DH_F64
+      ? launch_totals<double>((const double*)c->U[c->cur], c->n3, c->partials, totals_blocks(), c->totals, c->stream)
+      : launch_totals<float>((const float*)c->U[c->cur], c->n3, c->partials, totals_blocks(), c->totals, c->stream);
+  if (e == cudaSuccess)
+    e = c->prec == DH_F64
+        ? launch_minima<double>((const double*)c->U[c->cur], c->n3, c->cfg.gamma, c->partials, totals_blocks(), mins, c->stream)
+        : launch_minima<float>((const float*)c->U[c->cur], c->n3, c->cfg.gamma, c->partials, totals_blocks(), mins, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "metrics");
+  double m2[2];
+  DH_CUDA(c, cudaMemcpyAsync(out->totals, c->totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  DH_CUDA(c, cudaMemcpyAsync(m2, mins, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  // the substep maximum covers the interval since the previous read
+  DH_CUDA(c, cudaMemsetAsync(&c->rec->cool_nsub_max, 0, sizeof(int), c->stream));
+  DH_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->host_rec.cool_nsub_max = 0;
+  out->rho_min = m2[0];
+  out->p_min = m2[1];
+  return st;
+}
+
 extern "C" dh_status dh_forcing_field(dh_ctx* c, void* a_out, int on_device) {
   if (!c || !a_out) return fail(c, DH_ERR_ARG, "null argument");
   if (!c->cfg.forcing) return fail(c, DH_ERR_STATE, "forcing is off");
@@ -489,13 +527,11 @@ extern "C" dh_status dh_forcing_field(dh_ctx* c, void* a_out, int on_device) {
                                     (float*)dst, c->stream);
   }
   prof_end(c, 1);
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(a_out, dst, bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (!on_device) cudaFree(dst);   // on every path: the staging buffer is this call's own
   if (e != cudaSuccess) return cuda_fail(c, e, "forcing_field");
-  if (!on_device) {
-    DH_CUDA(c, cudaMemcpyAsync(a_out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
-    DH_CUDA(c, cudaStreamSynchronize(c->stream));
-    cudaFree(dst);
-  }
-  DH_CUDA(c, cudaStreamSynchronize(c->stream));
   return DH_OK;
 }
 

@@ -27,6 +27,7 @@ struct StepRecord {
   int fail_step;         // step index of the first fatal failure, -1 if none
   unsigned long long cfl_min_bits;  // min over cells of dx_a/(|v_a|+c) as ordered bits
   double ou_norm;        // a_rms / sqrt(<|a|^2>) of the current forcing table
+  int cool_nsub_max;     // largest cooling substep count (> 1) since the last metrics read
 };
 
 __host__ __device__ inline int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }

@@ -54,6 +54,7 @@ std::string mg_validate(const dh_config& c);
 cudaError_t mg_allocate(dh_ctx* c);
 void mg_setup_host(dh_ctx* c);
 cudaError_t mg_reset(dh_ctx* c);
+void mg_last(const dh_ctx* c, int* cycles, double* rel_residual);   // the last solve's outcome
 void mg_free(dh_ctx* c);
 void* mg_phi(dh_ctx* c);   // the potential, float-float planar, 8 B per cell (warm start of the next solve)
 // Poisson solve on the density of Ustar, then forcing -> gravity -> cooling in place.  tab:

@@ -65,6 +65,11 @@ template <typename real>
 cudaError_t launch_forcing_field(const real* ahat_norm, const real* const tw[3], int nx, int ny,
                                  int nz, real* a_out, cudaStream_t s);
 
+// minima over cells of rho and P into out2 (device); partials holds 2 * nblocks doubles
+template <typename real>
+cudaError_t launch_minima(const real* U, long long n3, double gamma, double* partials, int nblocks,
+                          double* out2, cudaStream_t s);
+
 int totals_blocks();
 // Streaming multiprocessors of the current device.
 int sm_count();

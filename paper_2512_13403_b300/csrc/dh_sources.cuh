@@ -179,7 +179,7 @@ __device__ __forceinline__ void forcing_accel(const real* ah, const real* const 
 template <typename real>
 __device__ __forceinline__ real cooling_energy(real r, real mx, real my, real mz, real E, real dt,
                                                real gm1, real T_floor, real frac, int nsub_max,
-                                               unsigned& flags) {
+                                               unsigned& flags, int& nsub_seen) {
   const real ir = q_div(real(1), r);
   const real kin = real(0.5) * (mx * mx + my * my + mz * mz) * ir;
   const real Eth = E - kin;
@@ -204,6 +204,7 @@ __device__ __forceinline__ real cooling_energy(real r, real mx, real my, real mz
   } else {
     const real dts = q_div(dt, nsub);
     const int n = (int)nsub;
+    nsub_seen = n > nsub_seen ? n : nsub_seen;
     real Es = Eth;
     for (int q = 0; q < n; ++q) {
       const real ed = Es > Efl ? -r2 * q_sqrt(gm1 * Es * ir) : real(0);

@@ -225,6 +225,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
 
   real tmin = real(INFINITY);
   unsigned flags = 0;
+  int nsub_seen = 0;   // largest cooling substep count of this thread's cells
 
   for (int k = z0; k < z1; ++k) {
     const int s0 = (k - z0) % 3, s1 = (k - z0 + 1) % 3, s2 = (k - z0 + 2) % 3;
@@ -379,7 +380,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
         }
         if (p.cooling)
           u[4] = cooling_energy(u[0], u[1], u[2], u[3], u[4], dt, gm1, p.t_floor, p.cool_frac,
-                                p.nsub_max, flags);
+                                p.nsub_max, flags, nsub_seen);
         bool finite = true;
 #pragma unroll
         for (int c = 0; c < 5; ++c) finite = finite && isfinite(u[c]);
@@ -408,6 +409,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
       atomicOr(&p.rec->flags, flags);
       if (flags & FATAL_FLAGS) atomicCAS(&p.rec->fail_step, -1, (int)(p.rec->nstep - 1));
     }
+    if (nsub_seen > 1) atomicMax(&p.rec->cool_nsub_max, nsub_seen);
     if (p.reduce_cfl) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
@@ -798,6 +800,56 @@ cudaError_t launch_totals(const real* U, long long n3, double* partials, int nbl
   totals_final_kernel<<<1, 5 * 32, 0, s>>>(partials, nblocks, out5);
   return cudaGetLastError();
 }
+// Minima over cells of rho and P = (gamma - 1)(E - |m|^2 / (2 rho)) (the step diagnostics):
+// per-block minima into partials[2 b], [2 b + 1], then out2 = the minima over the blocks.
+template <typename real>
+__global__ void __launch_bounds__(TOTALS_THREADS)
+minima_partial_kernel(const real* __restrict__ U, long long n3, double gm1,
+                      double* __restrict__ partials) {
+  __shared__ double red[2][TOTALS_THREADS / 32];
+  double mr = INFINITY, mp = INFINITY;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n3;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double r = U[q], mx = U[n3 + q], my = U[2 * n3 + q], mz = U[3 * n3 + q], E = U[4 * n3 + q];
+    mr = fmin(mr, r);
+    mp = fmin(mp, gm1 * (E - 0.5 * (mx * mx + my * my + mz * mz) / r));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mr = fmin(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    mp = fmin(mp, __shfl_xor_sync(0xffffffffu, mp, o));
+  }
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = mr; red[1][threadIdx.x >> 5] = mp; }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double m = INFINITY;
+    for (int w = 0; w < TOTALS_THREADS / 32; ++w) m = fmin(m, red[threadIdx.x][w]);
+    partials[2 * blockIdx.x + threadIdx.x] = m;
+  }
+}
+
+__global__ void minima_final_kernel(const double* __restrict__ partials, int nblocks,
+                                    double* __restrict__ out2) {
+  const int f = threadIdx.x;
+  if (f < 2) {
+    double m = INFINITY;
+    for (int b = 0; b < nblocks; ++b) m = fmin(m, partials[2 * b + f]);
+    out2[f] = m;
+  }
+}
+
+template <typename real>
+cudaError_t launch_minima(const real* U, long long n3, double gamma, double* partials, int nblocks,
+                          double* out2, cudaStream_t s) {
+  minima_partial_kernel<real><<<nblocks, TOTALS_THREADS, 0, s>>>(U, n3, gamma - 1.0, partials);
+  minima_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out2);
+  return cudaGetLastError();
+}
+template cudaError_t launch_minima<float>(const float*, long long, double, double*, int, double*,
+                                          cudaStream_t);
+template cudaError_t launch_minima<double>(const double*, long long, double, double*, int, double*,
+                                           cudaStream_t);
+
 template cudaError_t launch_totals<float>(const float*, long long, double*, int, double*,
                                           cudaStream_t);
 template cudaError_t launch_totals<double>(const double*, long long, double*, int, double*,

@@ -54,6 +54,12 @@ struct MG {
   float* e[dh::MG_LMAX] = {nullptr};
   float* e2[dh::MG_LMAX] = {nullptr};   // the sweep's other buffer (a sweep writes e2, then swaps)
   float* r[dh::MG_LMAX] = {nullptr};
+  // float64 correction hierarchy of a float64 context (instead of e / e2 / r): its cycles are
+  // the oracle's float64 cycles, so its iterates match them to rounding
+  bool f64 = false;
+  double* de[dh::MG_LMAX] = {nullptr};
+  double* de2[dh::MG_LMAX] = {nullptr};  // Jacobi's other buffer
+  double* dr[dh::MG_LMAX] = {nullptr};
   double* G = nullptr;           // coarsest circulant pseudo-inverse
   double* partials = nullptr;    // max(RED_BLOCKS, residual CTAs) doubles
   double* scal = nullptr;        // [0] mean rho, [1] |F|^2, [2] |r|^2, [3] mean phi
@@ -110,7 +116,14 @@ cudaError_t mg_allocate(dh_ctx* c) {
   cudaError_t e = cudaMalloc(&m->phi, 2 * m->cells[0] * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->phi2, 2 * m->cells[0] * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->F, 2 * m->cells[0] * sizeof(float));
+  m->f64 = c->prec == DH_F64;
   for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
+    if (m->f64) {
+      e = cudaMalloc(&m->de[l], m->cells[l] * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&m->de2[l], m->cells[l] * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&m->dr[l], m->cells[l] * sizeof(double));
+      continue;
+    }
     e = cudaMalloc(&m->e[l], m->cells[l] * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&m->e2[l], m->cells[l] * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&m->r[l], m->cells[l] * sizeof(float));
@@ -163,13 +176,21 @@ cudaError_t mg_reset(dh_ctx* c) {
 
 void* mg_phi(dh_ctx* c) { return c->mg ? c->mg->phi : nullptr; }
 
+void mg_last(const dh_ctx* c, int* cycles, double* rel_residual) {
+  *cycles = c->mg ? c->mg->last_cycles : 0;
+  *rel_residual = c->mg ? c->mg->last_res : 0.0;
+}
+
 void mg_free(dh_ctx* c) {
   MG* m = c->mg;
   if (!m) return;
   cudaFree(m->phi);
   cudaFree(m->phi2);
   cudaFree(m->F);
-  for (int l = 0; l < MG_LMAX; ++l) { cudaFree(m->e[l]); cudaFree(m->e2[l]); cudaFree(m->r[l]); }
+  for (int l = 0; l < MG_LMAX; ++l) {
+    cudaFree(m->e[l]); cudaFree(m->e2[l]); cudaFree(m->r[l]);
+    cudaFree(m->de[l]); cudaFree(m->de2[l]); cudaFree(m->dr[l]);
+  }
   cudaFree(m->G);
   cudaFree(m->partials);
   cudaFree(m->scal);
@@ -836,6 +857,172 @@ __global__ void coarse_solve_kernel(const float* __restrict__ r, float* __restri
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// The float64 cycle of a float64 context.  Plain one-cell-per-thread kernels that take the
+// oracle's steps in its order (Sec. 5.2; App. C): a red-black sweep is a red pass then a black
+// pass in place, each cell (sum of its 6 neighbours - h^2 r) / 6 with the neighbours summed as
+// (z-, z+), then (y-, y+), then (x-, x+); the Jacobi sweep e + omega (-h^2/6)(r - A e); the
+// restriction the mean of the 8 children of r - A e; the prolongation interpolates along z,
+// then y, then x (3/4 of the parent, 1/4 of its neighbour on the fine cell's side).  Such a
+// context exists for parity (float64 arithmetic is scarce on this part), so these kernels are
+// written for clarity, not speed.
+
+__device__ __forceinline__ void cell_of(long long q, int nx, int ny, int& i, int& j, int& k) {
+  const long long t = q / nx;
+  i = (int)(q - t * nx);
+  k = (int)(t / ny);
+  j = (int)(t - (long long)k * ny);
+}
+
+// the oracle's neighbour sum: (z- + z+) + (y- + y+) + (x- + x+)
+__device__ __forceinline__ double nb_sum_d(const double* __restrict__ e, int i, int j, int k,
+                                           int nx, int ny, int nz) {
+  const long long row = (long long)k * ny;
+  const double z = e[((long long)wrap(k - 1, nz) * ny + j) * nx + i] +
+                   e[((long long)wrap(k + 1, nz) * ny + j) * nx + i];
+  const double y = e[(row + wrap(j - 1, ny)) * nx + i] + e[(row + wrap(j + 1, ny)) * nx + i];
+  const double x = e[(row + j) * nx + wrap(i - 1, nx)] + e[(row + j) * nx + wrap(i + 1, nx)];
+  return ((0.0 + z) + y) + x;
+}
+
+// A e at a cell as the oracle forms it: (-6 e + (z- + z+) + (y- + y+) + (x- + x+)) / h^2
+__device__ __forceinline__ double apply_A_d(const double* __restrict__ e, int i, int j, int k,
+                                            int nx, int ny, int nz, double hh) {
+  const long long row = (long long)k * ny;
+  double s = -6.0 * e[(row + j) * nx + i];
+  s = s + e[((long long)wrap(k - 1, nz) * ny + j) * nx + i] + e[((long long)wrap(k + 1, nz) * ny + j) * nx + i];
+  s = s + e[(row + wrap(j - 1, ny)) * nx + i] + e[(row + wrap(j + 1, ny)) * nx + i];
+  s = s + e[(row + j) * nx + wrap(i - 1, nx)] + e[(row + j) * nx + wrap(i + 1, nx)];
+  return s / hh;
+}
+
+// one colour pass in place: cells with (i + j + k) % 2 == colour
+__global__ void rbgs_colour_d_kernel(double* __restrict__ e, const double* __restrict__ r, int nx,
+                                     int ny, int nz, double hh, int colour) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    cell_of(q, nx, ny, i, j, k);
+    if (((i + j + k) & 1) != colour) continue;
+    e[q] = (nb_sum_d(e, i, j, k, nx, ny, nz) - hh * r[q]) / 6.0;
+  }
+}
+
+__global__ void jacobi_d_kernel(const double* __restrict__ eo, double* __restrict__ en,
+                                const double* __restrict__ r, int nx, int ny, int nz, double hh,
+                                double omega) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    cell_of(q, nx, ny, i, j, k);
+    en[q] = eo[q] + omega * (-hh / 6.0) * (r[q] - apply_A_d(eo, i, j, k, nx, ny, nz, hh));
+  }
+}
+
+// rc = mean over the 8 children of (r - A e); coarse dims (cx, cy, cz)
+__global__ void resid_restrict_d_kernel(const double* __restrict__ e, const double* __restrict__ r,
+                                        double* __restrict__ rc, int cx, int cy, int cz, double hh) {
+  const int nx = 2 * cx, ny = 2 * cy, nz = 2 * cz;
+  const long long nc = (long long)cx * cy * cz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
+       t += (long long)gridDim.x * blockDim.x) {
+    int I, J, K;
+    cell_of(t, cx, cy, I, J, K);
+    double s = 0.0;
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+          const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+          const long long q = ((long long)k * ny + j) * nx + i;
+          s += r[q] - apply_A_d(e, i, j, k, nx, ny, nz, hh);
+        }
+    rc[t] = s / 8.0;
+  }
+}
+
+// ef += P ec, one thread per fine cell
+__global__ void prolong_add_d_kernel(double* __restrict__ ef, const double* __restrict__ ec,
+                                     int cx, int cy, int cz) {
+  const int nx = 2 * cx, ny = 2 * cy, nz = 2 * cz;
+  const long long n = (long long)nx * ny * nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    cell_of(q, nx, ny, i, j, k);
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const int Is[2] = {I, wrap(I + ((i & 1) ? 1 : -1), cx)};
+    const int Js[2] = {J, wrap(J + ((j & 1) ? 1 : -1), cy)};
+    const int Ks[2] = {K, wrap(K + ((k & 1) ? 1 : -1), cz)};
+    auto at = [&](int kk, int jj, int ii) { return ec[((long long)kk * cy + jj) * cx + ii]; };
+    double Y[2];
+    for (int b = 0; b < 2; ++b) {            // the x index of the y pass: parent, neighbour
+      double Z[2];
+      for (int a = 0; a < 2; ++a)            // the y index of the z pass: parent, neighbour
+        Z[a] = 0.75 * at(Ks[0], Js[a], Is[b]) + 0.25 * at(Ks[1], Js[a], Is[b]);
+      Y[b] = 0.75 * Z[0] + 0.25 * Z[1];
+    }
+    ef[q] += 0.75 * Y[0] + 0.25 * Y[1];
+  }
+}
+
+__global__ void coarse_solve_d_kernel(const double* __restrict__ r, double* __restrict__ e,
+                                      const double* __restrict__ G, int n0, int n1, int n2) {
+  const int N = n0 * n1 * n2;
+  for (int p = threadIdx.x; p < N; p += blockDim.x) {
+    const int p0 = p % n0, p1 = (p / n0) % n1, p2 = p / (n0 * n1);
+    double s = 0.0;
+    for (int q = 0; q < N; ++q) {
+      const int q0 = q % n0, q1 = (q / n0) % n1, q2 = q / (n0 * n1);
+      const int d0 = wrap(p0 - q0, n0), d1 = wrap(p1 - q1, n1), d2 = wrap(p2 - q2, n2);
+      s += G[(d2 * n1 + d1) * n0 + d0] * r[q];
+    }
+    e[p] = s;
+  }
+}
+
+// The fine level of a float64 context: phi' = phi + e (UPDATE, float-float + float64), the
+// residual r = F - A phi' in float-float, stored in float64, and per-block partials of
+// |r / rms(F)|^2.  Each thread forms the updated neighbours itself (the same rounding as the
+// owner's), so phi' may go to a second buffer while other blocks read phi.
+template <bool UPDATE>
+__global__ void __launch_bounds__(RED_THREADS)
+residual_d_kernel(const float* __restrict__ phi, float* __restrict__ phi_out,
+                  const double* __restrict__ e, const float* __restrict__ F,
+                  double* __restrict__ r, int nx, int ny, int nz, ff2 h2, double ih2,
+                  const double* fnorm2, double* partials) {
+  __shared__ double red[RED_THREADS];
+  const long long n = (long long)nx * ny * nz;
+  const double sF = 1.0 / sqrt(*fnorm2 / (double)n);
+  auto val = [&](long long q) {
+    const ff2 v = ff_load(phi, n, q);
+    return UPDATE ? ff_add(v, ff_from_double(e[q])) : v;
+  };
+  double acc = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    cell_of(q, nx, ny, i, j, k);
+    const long long row = (long long)k * ny;
+    const ff2 cv = val(q);
+    ff2 lap = ff_mul_f(cv, -6.0f);
+    lap = ff_add(lap, val(((long long)wrap(k - 1, nz) * ny + j) * nx + i));
+    lap = ff_add(lap, val(((long long)wrap(k + 1, nz) * ny + j) * nx + i));
+    lap = ff_add(lap, val((row + wrap(j - 1, ny)) * nx + i));
+    lap = ff_add(lap, val((row + wrap(j + 1, ny)) * nx + i));
+    lap = ff_add(lap, val((row + j) * nx + wrap(i - 1, nx)));
+    lap = ff_add(lap, val((row + j) * nx + wrap(i + 1, nx)));
+    const ff2 d = ff_sub(ff_mul(ff_load(F, n, q), h2), lap);      // h^2 (F - A phi)
+    const double rr = ff_to_double(d) * ih2;
+    r[q] = rr;
+    acc += (rr * sF) * (rr * sF);
+    if (UPDATE) ff_store(phi_out, n, q, cv);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 // Per-block float-float sums of the potential (the gauge's mean), in float64 partials.
 __global__ void sum_ff_kernel(const float* __restrict__ phi, long long n, double* partials) {
   __shared__ double red[RED_THREADS];
@@ -930,11 +1117,52 @@ static void cycle(dh_ctx* c, int l, bool zero_init) {
   c->launches += 2;
 }
 
+// The float64 cycle of a float64 context for A e_l = r_l, in the oracle's order: e_l = 0 on a
+// first visit, mg_pre sweeps, restriction of r - A e, the coarser level once (V) or twice (W),
+// prolongation, mg_post sweeps; the coarsest level is solved exactly.
+static void cycle_d(dh_ctx* c, int l, bool zero_init) {
+  MG* m = c->mg;
+  const dh_config& g = c->cfg;
+  cudaStream_t s = c->stream;
+  const int nx = m->n[l][0], ny = m->n[l][1], nz = m->n[l][2];
+  const double hh = m->h[l] * m->h[l];
+  const int gb = grid_for(m->cells[l]);
+  if (l == m->L - 1) {
+    coarse_solve_d_kernel<<<1, 256, 0, s>>>(m->dr[l], m->de[l], m->G, nx, ny, nz);
+    c->launches += 1;
+    return;
+  }
+  auto smooth = [&]() {
+    if (g.mg_smoother == 1) {
+      jacobi_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->de2[l], m->dr[l], nx, ny, nz, hh, g.mg_omega);
+      std::swap(m->de[l], m->de2[l]);
+      c->launches += 1;
+    } else {
+      rbgs_colour_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->dr[l], nx, ny, nz, hh, 0);
+      rbgs_colour_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->dr[l], nx, ny, nz, hh, 1);
+      c->launches += 2;
+    }
+  };
+  if (zero_init) cudaMemsetAsync(m->de[l], 0, m->cells[l] * sizeof(double), s);
+  for (int it = 0; it < g.mg_pre; ++it) smooth();
+  resid_restrict_d_kernel<<<grid_for(m->cells[l + 1]), 256, 0, s>>>(m->de[l], m->dr[l], m->dr[l + 1],
+                                                                    nx / 2, ny / 2, nz / 2, hh);
+  const int visits = (g.mg_cycle == 2 && l + 1 < m->L - 1) ? 2 : 1;
+  for (int v = 0; v < visits; ++v) cycle_d(c, l + 1, v == 0);
+  prolong_add_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->de[l + 1], nx / 2, ny / 2, nz / 2);
+  for (int it = 0; it < g.mg_post; ++it) smooth();
+  c->launches += 2;
+}
+
 // Launches one cycle from the finest level: replays the captured graph when the buffers are
 // where they were at capture, else captures it (or, if capture fails, launches directly).
 static cudaError_t run_cycle(dh_ctx* c) {
   MG* m = c->mg;
   const dh_config& g = c->cfg;
+  if (m->f64) {
+    cycle_d(c, 0, true);
+    return cudaGetLastError();
+  }
   // the buffer layout returns to its start after a cycle iff every level swaps an even number
   // of times: each visit swaps (mg_pre + mg_post) times
   const bool even = (g.mg_pre + g.mg_post) % 2 == 0;
@@ -1014,7 +1242,17 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
   bool pending = false;   // a correction e[0] not yet added to phi
   while (true) {
     prof_begin(c, DH_KERNEL_MG);
-    if (pending) {
+    if (m->f64) {
+      if (pending)
+        residual_d_kernel<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(
+            m->phi, m->phi2, m->de[0], m->F, m->dr[0], nx, ny, nz, h2, 1.0 / hh, m->scal + 1,
+            m->partials);
+      else
+        residual_d_kernel<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(
+            m->phi, nullptr, nullptr, m->F, m->dr[0], nx, ny, nz, h2, 1.0 / hh, m->scal + 1,
+            m->partials);
+      if (pending) std::swap(m->phi, m->phi2);
+    } else if (pending) {
       // phi2 = phi + e and its residual in one pass, then phi2 becomes phi
       residual_zm_kernel<true><<<rg, 256, 0, s>>>(m->phi, m->phi2, m->e[0], m->F, m->r[0], nx, ny,
                                                   nz, h2, ih2, m->scal + 1, m->partials);
@@ -1024,7 +1262,8 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
                                                    nz, h2, ih2, m->scal + 1, m->partials);
     }
     pending = false;
-    finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, rblocks, m->scal + 2, 1.0 / (double)n);
+    finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, m->f64 ? RED_BLOCKS : rblocks, m->scal + 2,
+                                              1.0 / (double)n);
     prof_end(c, 2);
     double h[3];
     cudaError_t e = cudaMemcpyAsync(h, m->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1168,6 +1407,7 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
   }
   real tmin = real(INFINITY);
   unsigned flags = 0;
+  int nsub_seen = 0;
   // the state and potential words of the next plane are loaded a plane ahead
   real un[5];
   float pv[12];
@@ -1234,7 +1474,8 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
       u[4] = u[4] + e;
     }
     if (cooling)
-      u[4] = cooling_energy(u[0], u[1], u[2], u[3], u[4], dt, gm1, t_floor, frac, nsub_max, flags);
+      u[4] = cooling_energy(u[0], u[1], u[2], u[3], u[4], dt, gm1, t_floor, frac, nsub_max, flags,
+                            nsub_seen);
     bool finite = true;
 #pragma unroll
     for (int c = 0; c < 5; ++c) finite = finite && isfinite(u[c]);
@@ -1255,6 +1496,7 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
     atomicOr(&rec->flags, flags);
     if (flags & FATAL_FLAGS) atomicCAS(&rec->fail_step, -1, (int)(rec->nstep - 1));
   }
+  if (nsub_seen > 1) atomicMax(&rec->cool_nsub_max, nsub_seen);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
   if ((tid & 31) == 0) red[tid >> 5] = tmin;

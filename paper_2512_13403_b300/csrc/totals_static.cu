@@ -65,15 +65,23 @@ __global__ void static_totals_final(const double* __restrict__ scratch, int nblo
   }
 }
 
-// Device address of the file-scope array on the current device, looked up once per device.
-// In host code the array's name is only a host-side stand-in, never a device address.
-cudaError_t scratch_address(double** out) {
+// Device address of the file-scope array on the current device.  In host code the array's
+// name is only a host-side stand-in, never a device address.  Outside stream capture the
+// address is looked up on every call (so a cudaDeviceReset and a fresh context cannot leave a
+// stale address behind); while the stream is being captured the address cached by an earlier
+// call on this device is used.
+cudaError_t scratch_address(cudaStream_t s, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();                  // treat an undeterminable status as capturing
+    cap = cudaStreamCaptureStatusActive;
+  }
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_on_device[dev]) {
+  if (!g_scratch_on_device[dev] || cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_totals_scratch);
     if (e != cudaSuccess) return e;
@@ -101,7 +109,7 @@ extern "C" dh_status dh_conserved_totals_static(const void* U, int precision, lo
     return DH_ERR_ARG;
   }
   double* scratch = nullptr;
-  cudaError_t e = scratch_address(&scratch);
+  cudaError_t e = scratch_address((cudaStream_t)cuda_stream, &scratch);
   if (e != cudaSuccess) {
     dh_set_global_error(std::string("dh_conserved_totals_static: cudaGetSymbolAddress: ") +
                         cudaGetErrorString(e));

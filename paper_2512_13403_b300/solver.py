@@ -152,6 +152,16 @@ class Solver:
         self._check(self.lib.dh_conserved_totals(self.ctx, out))
         return list(out)
 
+    def metrics(self) -> dict:
+        """The diagnostics record (dh_get_metrics): t, dt, nstep, flags, cool_max_substeps,
+        mg_cycles, mg_residual, totals, rho_min, p_min."""
+        m = _lib.DhMetrics()
+        self._check(self.lib.dh_get_metrics(self.ctx, C.byref(m)))
+        return {"t": m.t, "dt": m.dt, "nstep": m.nstep, "flags": m.flags,
+                "cool_max_substeps": m.cool_max_substeps, "mg_cycles": m.mg_cycles,
+                "mg_residual": m.mg_residual, "totals": list(m.totals), "rho_min": m.rho_min,
+                "p_min": m.p_min}
+
     def forcing_field(self, device=True):
         out = torch.empty((3,) + self.shape, dtype=self.dtype, device="cuda" if device else "cpu")
         ptr, dev, keep = self._as_buffer(out, 3)

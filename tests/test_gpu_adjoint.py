@@ -194,8 +194,10 @@ def test_fp64_with_gravity_matches_oracle(forcing_cooling):
     g = s.adjoint_advance(n, k, to_gpu(lam, "f64"))
     ref = oadj.advance_vjp(torch.from_numpy(U0), dts, torch.from_numpy(lam), G, _dx(shape),
                            fields if forcing_cooling else None, cool, grav)
-    assert _rel(g, ref) < 1e-9
-    assert float((g.cpu() - ref).abs().max() / ref.abs().max()) < 1e-8
+    # the float64 context's multigrid runs float64 cycles: both Poisson solves are then exact to
+    # far below the float64 bar of 1e-11 (measured: 1e-15)
+    assert _rel(g, ref) < 1e-11
+    assert float((g.cpu() - ref).abs().max() / ref.abs().max()) < 1e-11
 
 
 def test_gravity_mass_invariant_fp32_and_state_kept():

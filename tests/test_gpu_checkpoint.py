@@ -54,3 +54,26 @@ def test_load_rejects_other_configuration_and_corruption(tmp_path):
         b.load(str(bad))
     with pytest.raises(_lib.DhError):
         b.load(str(tmp_path / "missing.bin"))
+
+
+@pytest.mark.parametrize("change", [dict(integrator="ssprk3"), dict(limiter="vanleer"), dict(cfl=0.3),
+                                    dict(t_floor=0.1), dict(ou_tau=0.4)])
+def test_load_rejects_other_scheme_and_settings(tmp_path, change):
+    """A checkpoint carries every setting a step depends on: a context with another integrator,
+    limiter, CFL number or source setting refuses it (its continuation would not be the saved
+    run's), and keeps its own state."""
+    shape = (16, 16, 16)
+    kw = dict(forcing=True, cooling=True)
+    a = solver(shape, "f32", **kw)
+    a.init_state(to_gpu(inputs.cooling_box(shape), "f32"))
+    a.advance(2)
+    path = tmp_path / "ck.bin"
+    a.save(str(path))
+    b = solver(shape, "f32", **{**kw, **change})
+    U = to_gpu(inputs.cooling_box(shape), "f32")
+    b.init_state(U)
+    with pytest.raises(_lib.DhError) as e:
+        b.load(str(path))
+    assert e.value.status == _lib.DH_ERR_ARG
+    assert "differs" in str(e.value)
+    assert torch.equal(b.get_state(), U)

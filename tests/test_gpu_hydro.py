@@ -332,3 +332,31 @@ def test_step_translation_equivariant(prec):
             assert torch.equal(want, got), shift
         else:
             assert max(rel_linf(got, want)) <= (1e-14 if prec == "f64" else 1e-6), shift
+
+
+def test_metrics_record_cooling_cap_and_minima():
+    """dh_get_metrics: a step whose cooling needs more substeps than nsub_max raises
+    DH_FLAG_COOL_CAP and reports nsub_max as the largest substep count; the totals equal
+    dh_conserved_totals, the minima those of the state, and the substep maximum covers the
+    interval since the previous read."""
+    from paper_2512_13403_b300 import _lib
+    shape = (16, 16, 16)
+    U0 = inputs.decaying_turbulence(shape, seed=3, sigma=0.5, mach=0.5)
+    # strong cooling: a large density contrast and a small substep cap
+    s = solver(shape, "f64", cooling=True, t_floor=0.01, cool_frac=0.01, nsub_max=4)
+    s.init_state(to_gpu(U0, "f64"))
+    m0 = s.metrics()
+    assert m0["nstep"] == 0 and m0["cool_max_substeps"] == 0 and m0["flags"] == 0
+    s.step(0.0)
+    m = s.metrics()
+    assert m["nstep"] == 1 and m["dt"] > 0
+    assert m["flags"] & _lib.DH_FLAG_COOL_CAP
+    assert m["cool_max_substeps"] == 4
+    assert m["totals"] == pytest.approx(s.conserved_totals(), rel=1e-14)
+    U = s.get_state().cpu()
+    P = (5.0 / 3.0 - 1.0) * (U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0])
+    assert m["rho_min"] == float(U[0].min())
+    assert m["p_min"] == pytest.approx(float(P.min()), rel=1e-12)
+    assert m["mg_cycles"] == 0
+    # the read reset the interval maximum: with no step since, cooling reports no subcycling
+    assert s.metrics()["cool_max_substeps"] == 1

@@ -135,10 +135,13 @@ def test_flux_form_one_step_backward_matches_oracle(monkeypatch):
     net.close()
 
 
-@pytest.mark.parametrize("form", ["state", "flux"])
-def test_rollout_gradient_matches_oracle(form, monkeypatch):
+@pytest.mark.parametrize("form,floors", [("state", False), ("flux", False), ("state", True),
+                                         ("flux", True)])
+def test_rollout_gradient_matches_oracle(form, floors, monkeypatch):
     """The rollout loss and its parameter gradient through two solver steps (hand adjoint,
-    imposed dt) and two corrections, against reverse mode of the oracle rollout."""
+    imposed dt) and two corrections, against reverse mode of the oracle rollout.  With
+    `floors`, rho_floor = 0.9 <rho> and T_floor = 0.6 bind in a large share of the cells (both
+    the density floor and the energy floor), and the gradient goes through them."""
     from paper_2512_13403_b300 import closure
     from paper_2512_13403_b300.solver import Config
     _straight_through(monkeypatch)
@@ -154,16 +157,25 @@ def test_rollout_gradient_matches_oracle(form, monkeypatch):
     sigma = [float(U0t[c].std()) for c in range(5)]
     out = [0.02 * s for s in sigma]
     w = [float(U0t[c].std()) for c in range(5)]
-    cfg = Config(shape=shape, precision="f32")
-    tr = closure.RolloutTrainer(shape, cfg, form, rho_floor_frac=1e-9)
+    frac = 0.9 if floors else 1e-9
+    cfg = Config(shape=shape, precision="f32", t_floor=0.6 if floors else 0.05)
+    tr = closure.RolloutTrainer(shape, cfg, form, rho_floor_frac=frac)
     traj = closure.Trajectory(to_gpu(U0, "f32"), dts, [None, None],
                               [t.float().cuda().contiguous() for t in targets])
     L, g = tr.loss_and_grad(traj, params.cuda(), (mu, sigma, out), w)
     tr.close()
     q = {k: v.clone().requires_grad_(True) for k, v in pd.items()}
     steps = [lambda U, dt=dt: ohydro.rk2_step(U, dt, G, dx) for dt in dts]
-    Lr = oc.rollout_loss(U0t, steps, targets, q, mu, sigma, out, w, 1e-9, cfg.t_floor, G)
+    rho_floor = frac * float(U0t[0].mean())
+    Lr = oc.rollout_loss(U0t, steps, targets, q, mu, sigma, out, w, rho_floor, cfg.t_floor, G)
     Lr.backward()
+    if floors:
+        # the floors do bind: the corrected state differs from the unfloored one in many cells
+        with torch.no_grad():
+            V = steps[0](U0t)
+            Y = V + oc.correction(V, pd, mu, sigma, out)
+            Z = oc.correct(V, pd, mu, sigma, rho_floor, cfg.t_floor, G, out)
+            assert int((Z[0] != Y[0]).sum()) > 100 and int((Z[4] != Y[4]).sum()) > 100
     assert L == pytest.approx(float(Lr.detach()), rel=1e-2)
     from paper_2512_13403_b300 import corrector as cr
     gg = cr.unflatten(g.double().cpu())
