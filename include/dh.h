@@ -140,7 +140,8 @@ dh_status dh_load(dh_ctx* ctx, const char* path);
    solve's cycle count and relative residual (Sec. 5.2), the float64 conserved totals and the
    minima over cells of rho and P of the current state.  Settles enqueued steps and returns
    their status; synchronises. */
-enum { DH_FLAG_NONFINITE = 1, DH_FLAG_POSITIVITY = 2, DH_FLAG_MG_NOCONV = 4, DH_FLAG_COOL_CAP = 8 };
+enum { DH_FLAG_NONFINITE = 1, DH_FLAG_POSITIVITY = 2, DH_FLAG_MG_NOCONV = 4, DH_FLAG_COOL_CAP = 8,
+       DH_FLAG_TIMEOUT = 16 /* a kernel's bounded wait for its own copies gave up (fatal) */ };
 typedef struct dh_metrics {
   double t, dt;             /* time after the last completed step, and its dt            */
   long long nstep;          /* completed steps                                           */

@@ -374,6 +374,9 @@ static dh_status finish_steps(dh_ctx* c, long long nstep_before) {
     reset_cfl_bits(c);
     if (c->prec == DH_F64) cfl_reduce_current<double>(c); else cfl_reduce_current<float>(c);
     cudaStreamSynchronize(c->stream);
+    if (fl & FLAG_TIMEOUT)
+      return fail(c, DH_ERR_CUDA, "a kernel's bounded wait for its own copies gave up in step " +
+                                      std::to_string(failed));
     if (fl & FLAG_MG_NOCONV)
       return fail(c, DH_ERR_MG_NOCONV, "multigrid did not converge in step " + std::to_string(failed));
     if (fl & FLAG_NONFINITE)
@@ -471,8 +474,11 @@ extern "C" dh_status dh_conserved_totals(dh_ctx* c, double out[5]) {
   return DH_OK;
 }
 
-static_assert(DH_FLAG_NONFINITE == dh::FLAG_NONFINITE && DH_FLAG_POSITIVITY == dh::FLAG_POSITIVITY &&
-                  DH_FLAG_MG_NOCONV == dh::FLAG_MG_NOCONV && DH_FLAG_COOL_CAP == dh::FLAG_COOL_CAP,
+static_assert((unsigned)DH_FLAG_NONFINITE == dh::FLAG_NONFINITE &&
+                  (unsigned)DH_FLAG_POSITIVITY == dh::FLAG_POSITIVITY &&
+                  (unsigned)DH_FLAG_MG_NOCONV == dh::FLAG_MG_NOCONV &&
+                  (unsigned)DH_FLAG_COOL_CAP == dh::FLAG_COOL_CAP &&
+                  (unsigned)DH_FLAG_TIMEOUT == dh::FLAG_TIMEOUT,
               "public and device status bits");
 
 extern "C" dh_status dh_get_metrics(dh_ctx* c, dh_metrics* out) {

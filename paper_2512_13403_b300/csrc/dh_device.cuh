@@ -15,8 +15,9 @@ enum : unsigned {
   FLAG_POSITIVITY = 2u,
   FLAG_MG_NOCONV = 4u,
   FLAG_COOL_CAP = 8u,   // informational: a cell hit the substep cap
+  FLAG_TIMEOUT = 16u,   // a bounded wait on the kernel's own copies gave up
 };
-constexpr unsigned FATAL_FLAGS = FLAG_NONFINITE | FLAG_POSITIVITY | FLAG_MG_NOCONV;
+constexpr unsigned FATAL_FLAGS = FLAG_NONFINITE | FLAG_POSITIVITY | FLAG_MG_NOCONV | FLAG_TIMEOUT;
 
 // Device-resident record of the time integration (one per context).
 struct StepRecord {

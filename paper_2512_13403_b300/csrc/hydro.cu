@@ -8,12 +8,24 @@
 //
 // Blocking: a CTA owns a BX x BY column of cells and marches along z through a chunk of
 // planes.  Primitive planes (with a two-cell x/y halo) sit in a three-plane shared-memory ring
-// (k, k+1, k+2); every x and y face of plane k is evaluated exactly once per CTA by a linear
-// face loop, and the z faces come from a per-thread register pipeline (each z face once).  The
-// conserved variables of the next plane arrive by cp.async into a staging plane while the
-// current plane is computed, and are converted into the ring one plane later.
+// (k, k+1, k+2); every x and y face of plane k is evaluated exactly once per CTA, each thread
+// taking its own cell's slopes and faces and a fixed tail of halo work, and the z faces come
+// from a per-thread register pipeline (each z face once).  The conserved variables of the next
+// plane arrive by TMA (five tensor-map boxes: the tile core and its four halo strips, wrapped
+// periodically) into staging buffers while the current plane is computed, and are converted
+// into the ring one plane later.
 #include <math.h>
+#include <string.h>
+#include <cstring>
+
+#include <mutex>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
 #include "async_copy.cuh"
+#include "tc_ptx.cuh"
+#include "tma.cuh"
 #include "dh_kernels.h"
 #include "dh_sources.cuh"
 #include "ff.cuh"
@@ -23,24 +35,18 @@ namespace dh {
 
 constexpr int BX = 32, BY = 8, HX = BX + 4, HY = BY + 4;
 constexpr int NTHREADS = BX * BY;
-constexpr int NXS = (BX + 2) * BY;   // cells with an x slope in a plane tile: lx = -1 .. BX
-constexpr int NYS = BX * (BY + 2);   // cells with a y slope: ly = -1 .. BY
-constexpr int NXF = (BX + 1) * BY;   // x faces of a plane tile
-constexpr int NYF = BX * (BY + 1);   // y faces of a plane tile
 constexpr int NFORCE = BY * 9;       // forcing row factors: row x (n_x = 0, 1, 2) x component
-// The y items of the per-plane slope and face loops start on a warp boundary, so that no warp
-// takes both branches of a loop step.
-constexpr int NXSP = (NXS + 31) / 32 * 32, NXFP = (NXF + 31) / 32 * 32;
 
-// Staging plane: rows of conserved variables copied in 16-byte chunks of SCE elements, from
-// x0 - SHALO to x0 + BX + SHALO (SHALO >= 2, a multiple of SCE); prim column sx is staging
-// column sx + SOFF.
+// Staged conserved variables of the plane in flight, one dense buffer per TMA box: the tile
+// core, the x halos (SCE cells = 16 bytes on each side, of which the two nearest the tile are
+// read) and the y halos (two rows above and below).  The four corner blocks of the halo are
+// never read by the stencil (x slopes read rows 0..BY-1, y slopes columns 0..BX-1) and are not
+// loaded.  Every box is contiguous in global memory at any tile position: x0 and y0 are
+// multiples of BX and BY, so a halo either lies inside the grid or is the whole wrapped strip
+// at the other side.
 template <typename real> struct Staging {
   static constexpr int SCE = 16 / (int)sizeof(real);
-  static constexpr int SHALO = (2 + SCE - 1) / SCE * SCE;
-  static constexpr int SROW = BX + 2 * SHALO;
-  static constexpr int NCH = SROW / SCE;       // chunks per row
-  static constexpr int SOFF = SHALO - 2;
+  static constexpr uint32_t BYTES = (uint32_t)sizeof(real) * 5u * (BX * BY + 2 * BY * SCE + 4 * BX);
 };
 
 // Four components of a primitive state or flux in one 16-byte-aligned word group, so that a
@@ -59,8 +65,12 @@ __device__ __forceinline__ void qstore(Q4<real>& q, real& s, const Prim<real>& w
 }
 
 template <typename real> struct StageSmem {
-  real stg[5][HY][Staging<real>::SROW];   // conserved variables of the plane in flight
-  real tz[4];                // forcing: z twiddles of the plane in flight (staged with it)
+  alignas(128) real core[5][BY][BX];                 // staged plane: tile core
+  alignas(128) real xl[5][BY][Staging<real>::SCE];   // x halo, x0 - SCE .. x0 - 1
+  alignas(128) real xr[5][BY][Staging<real>::SCE];   // x halo, x0 + BX .. x0 + BX + SCE - 1
+  alignas(128) real yt[5][2][BX];                    // y halo, y0 - 2, y0 - 1
+  alignas(128) real yb[5][2][BX];                    // y halo, y0 + BY, y0 + BY + 1
+  alignas(16) real tz[4];    // forcing: z twiddles of the plane in flight (staged with it)
   Q4<real> w4[3][HY][HX];    // primitive planes ring (k, k+1, k+2), two-cell x/y halo: rho, v
   Q4<real> xm4[BY][BX + 2];  // x face states W - dW/2 of cells lx = -1..BX (index lx + 1)
   Q4<real> xp4[BY][BX + 2];  //                W + dW/2
@@ -76,10 +86,10 @@ template <typename real> struct StageSmem {
   real ah[96];               // forcing: normalised OU table
   real tyt[BY][4];           // forcing: y twiddles of the tile's rows
   real fB[BY][3][3][2];      // forcing: B[row][n_x][component] = sum over modes with that n_x
-  int xs[HX];                // wrapped global x of each smem column
-  int ys[HY];                // wrapped global y of each smem row
-  int cx[Staging<real>::NCH];  // wrapped global x of each staging chunk
+  int xs[HX];                // wrapped global x of each ring column (prologue)
+  int ys[HY];                // wrapped global y of each ring row (prologue)
   real red[NTHREADS / 32];   // CFL reduction scratch
+  alignas(8) uint64_t bar;   // staging plane landed (TMA transaction bytes)
 };
 
 template <typename real>
@@ -95,21 +105,36 @@ __device__ __forceinline__ Prim<real> load_prim(const real* __restrict__ U, long
                       __ldg(U + 3 * n3 + idx), __ldg(U + 4 * n3 + idx), gm1);
 }
 
+// Bound on the probes of the staging mbarrier: a plane's copies land in microseconds; a wait
+// that reaches it sets FLAG_TIMEOUT and the CTA stops.
+constexpr uint32_t STAGE_WAIT_ITERS = 1u << 22;
+
+// Work of a plane.  Thread (tx, ty) = (tid % BX, tid / BX) owns tile cell (tx, ty): its
+// primitive conversion, x and y slopes, x face tx (its left face), y face ty (its lower face),
+// z faces and update.  The halo work is a fixed tail: the y slopes of rows -1 and BY (warps 0
+// and 1), the x slopes of columns -1 and BX (warp 2, lanes 0..15), the conversion of the 160
+// used halo cells (warps 3..7), the x face BX of each row (warp 6, lanes 0..7) and the y face
+// BY of each column (warp 7).  Every address is fixed for the whole march.
 // float32: three CTAs per SM (shared memory allows three; registers are capped to match)
 template <typename real, int STAGE, int LIM>
 __global__ void __launch_bounds__(NTHREADS, sizeof(real) == 4 ? 3 : 1)
-stage_kernel(const StageArgs<real> p, const int zchunk) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+stage_kernel(const StageArgs<real> p, const int zchunk, const __grid_constant__ StageTma tma,
+             const int use_tma) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   StageSmem<real>& S = *reinterpret_cast<StageSmem<real>*>(smem_raw);
   const int tid = threadIdx.x;
   // Skip the stage after a fatal failure.  One thread reads the flag and the CTA follows it, so
   // a flag raised by another CTA mid-launch cannot split this CTA across a barrier.
   __shared__ unsigned s_skip;
-  if (tid == 0) s_skip = *((volatile unsigned*)&p.rec->flags) & FATAL_FLAGS;
+  __shared__ int s_abort;
+  if (tid == 0) {
+    s_skip = *((volatile unsigned*)&p.rec->flags) & FATAL_FLAGS;
+    s_abort = 0;
+  }
   __syncthreads();
   if (s_skip) return;
 
-  const int tx = tid & (BX - 1), ty = tid / BX;
+  const int tx = tid & (BX - 1), ty = tid / BX, warp = tid >> 5;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const long long plane = (long long)nx * ny;
   const long long n3 = plane * nz;
@@ -130,10 +155,16 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
   const bool forcing = final && p.forcing;
 
   using ST = Staging<real>;
+  constexpr int SCE = ST::SCE;
+  const uint32_t bar = tc::smem_u32(&S.bar);
+  // box destinations must start on 128 bytes; the buffers are 128-byte multiples from S
+  const bool via_tma = use_tma != 0 && (tc::smem_u32(&S.core[0][0][0]) & 127u) == 0u;
   if (tid < HX) S.xs[tid] = ((x0 + tid - 2) % nx + nx) % nx;
   if (tid >= 64 && tid < 64 + HY) S.ys[tid - 64] = ((y0 + tid - 64 - 2) % ny + ny) % ny;
-  if (tid >= 96 && tid < 96 + ST::NCH)
-    S.cx[tid - 96] = ((x0 - ST::SHALO + ST::SCE * (tid - 96)) % nx + nx) % nx;
+  if (tid == 96) {
+    tc::mbar_init(&S.bar, 1u);
+    tc::mbar_fence_init();
+  }
   if (forcing) {
     if (tid < 96) S.ah[tid] = __ldg(p.ahat_norm + tid);
     if (tid >= 128 && tid < 128 + 4 * BY) {
@@ -141,52 +172,118 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
       S.tyt[ly][i] = __ldg(p.tw[1] + 4 * ((y0 + ly) % ny) + i);
     }
   }
-  // whole 16-byte chunks need rows of a multiple of SCE elements and an aligned state
-  const bool vec = (nx % ST::SCE == 0) && (((unsigned long long)p.U & 15ull) == 0);
+  // wrapped start coordinates of the halo boxes (TMA path: nx % BX == 0 and ny % BY == 0)
+  const int xl0 = x0 >= SCE ? x0 - SCE : nx - SCE, xr0 = x0 + BX < nx ? x0 + BX : 0;
+  const int yt0 = y0 >= 2 ? y0 - 2 : ny - 2, yb0 = y0 + BY < ny ? y0 + BY : 0;
   __syncthreads();
 
-  // cp.async of the conserved variables of plane k into the staging plane, with the forcing's z
-  // twiddles of plane k - 2 (the plane whose row factors the next iteration builds); one group
+  // The conserved variables of plane k into the staging buffers, with the forcing's z twiddles
+  // of plane k - 2 (the plane whose row factors the next iteration builds).  TMA: one thread
+  // issues five box loads (and the twiddles' bulk copy) on the staging barrier.  Otherwise
+  // every thread issues element copies of its share (wrapped coordinates of every position).
   auto stage_plane = [&](int k) {
-    const long long zoff = (long long)wrap(k, nz) * plane;
+    const int kz = wrap(k, nz);
+    if (via_tma) {
+      if (tid == 0) {
+        tc::mbar_arrive_expect_tx(&S.bar, ST::BYTES + (forcing ? 4u * (uint32_t)sizeof(real) : 0u));
+        tma_load_4d(tc::smem_u32(&S.core[0][0][0]), &tma.core, x0, y0, kz, 0, bar);
+        tma_load_4d(tc::smem_u32(&S.xl[0][0][0]), &tma.xh, xl0, y0, kz, 0, bar);
+        tma_load_4d(tc::smem_u32(&S.xr[0][0][0]), &tma.xh, xr0, y0, kz, 0, bar);
+        tma_load_4d(tc::smem_u32(&S.yt[0][0][0]), &tma.yh, x0, yt0, kz, 0, bar);
+        tma_load_4d(tc::smem_u32(&S.yb[0][0][0]), &tma.yh, x0, yb0, kz, 0, bar);
+        if (forcing)
+          tc::bulk_g2s(tc::smem_u32(&S.tz[0]), p.tw[2] + 4 * wrap(k - 2, nz),
+                       4u * (uint32_t)sizeof(real), &S.bar);
+      }
+      return;
+    }
+    const long long zoff = (long long)kz * plane;
     if (forcing && tid == NTHREADS - 1) {
       const real* t = p.tw[2] + 4 * wrap(k - 2, nz);
 #pragma unroll
-      for (int i = 0; i < 4; i += ST::SCE) cp_async16(&S.tz[i], t + i);
+      for (int i = 0; i < 4; i += SCE) cp_async16(&S.tz[i], t + i);
     }
-    // each item is one chunk (or cell) position with its five fields
-    if (vec) {
-      for (int c = tid; c < HY * ST::NCH; c += NTHREADS) {
-        const int sy = c / ST::NCH, j = c - sy * ST::NCH;
-        const real* g = p.U + zoff + (long long)S.ys[sy] * nx + S.cx[j];
-#pragma unroll
-        for (int f = 0; f < 5; ++f) cp_async16(&S.stg[f][sy][ST::SCE * j], g + f * n3);
+    constexpr int NC = BX * BY, NXH = BY * SCE, NYH = 2 * BX;
+    for (int c = tid; c < NC + 2 * NXH + 2 * NYH; c += NTHREADS) {
+      int lx, ly, fs;
+      real* dst;
+      if (c < NC) {
+        lx = c % BX; ly = c / BX; dst = &S.core[0][ly][lx]; fs = BY * BX;
+      } else if (c < NC + 2 * NXH) {
+        const int e = c - NC, side = e / NXH, r = e - side * NXH;
+        ly = r / SCE;
+        const int col = r - ly * SCE;
+        lx = side == 0 ? col - SCE : BX + col;
+        dst = side == 0 ? &S.xl[0][ly][col] : &S.xr[0][ly][col];
+        fs = BY * SCE;
+      } else {
+        const int e = c - NC - 2 * NXH, side = e / NYH, r = e - side * NYH;
+        const int row = r / BX;
+        lx = r - row * BX;
+        ly = side == 0 ? row - 2 : BY + row;
+        dst = side == 0 ? &S.yt[0][row][lx] : &S.yb[0][row][lx];
+        fs = 2 * BX;
       }
-    } else {
-      for (int c = tid; c < HY * HX; c += NTHREADS) {
-        const int sy = c / HX, sx = c - sy * HX;
-        const real* g = p.U + zoff + (long long)S.ys[sy] * nx + S.xs[sx];
+      const int gxc = ((x0 + lx) % nx + nx) % nx, gyc = ((y0 + ly) % ny + ny) % ny;
+      const real* g = p.U + zoff + (long long)gyc * nx + gxc;
 #pragma unroll
-        for (int f = 0; f < 5; ++f) {
-          if constexpr (sizeof(real) == 4) cp_async4(&S.stg[f][sy][sx + ST::SOFF], g + f * n3);
-          else cp_async8(&S.stg[f][sy][sx + ST::SOFF], g + f * n3);
-        }
+      for (int f = 0; f < 5; ++f) {
+        if constexpr (sizeof(real) == 4) cp_async4(dst + f * fs, g + f * n3);
+        else cp_async8(dst + f * fs, g + f * n3);
       }
     }
     cp_async_commit();
   };
-  // primitive recovery of the staged plane into a ring slot.  Without forcing the cells are
-  // taken from the last thread down, so that the warps with a third slope item get one cell
-  // fewer; with forcing the last warps build the row factors and take the fewer cells instead.
-  const int conv0 = forcing ? tid : NTHREADS - 1 - tid;
-  auto convert_plane = [&](int slot) {
-    for (int c = conv0; c < HX * HY; c += NTHREADS) {
-      const int sy = c / HX, sx = c - sy * HX;
-      const int q = sx + ST::SOFF;
-      qstore(S.w4[slot][sy][sx], S.wp[slot][sy][sx],
-             cons_to_prim(S.stg[0][sy][q], S.stg[1][sy][q], S.stg[2][sy][q], S.stg[3][sy][q],
-                          S.stg[4][sy][q], gm1));
+
+  // ---- fixed per-thread tasks -------------------------------------------------------------
+  // conversion: own cell from the core, and (warps 3..7) one halo cell
+  const int ring_own = (ty + 2) * HX + tx + 2;
+  const real* ext_src = nullptr;   // halo cell of the conversion tail, field stride ext_fs
+  int ext_fs = 0, ext_ring = -1;
+  if (tid >= 96) {
+    const int e = tid - 96;   // 0 .. 159
+    if (e < 64) {
+      const int row = e >> 5, lx = e & 31;
+      ext_src = &S.yt[0][row][lx]; ext_fs = 2 * BX; ext_ring = row * HX + lx + 2;
+    } else if (e < 128) {
+      const int row = (e - 64) >> 5, lx = e & 31;
+      ext_src = &S.yb[0][row][lx]; ext_fs = 2 * BX; ext_ring = (BY + 2 + row) * HX + lx + 2;
+    } else if (e < 144) {
+      const int ly = (e - 128) & 7, c = (e - 128) >> 3;
+      ext_src = &S.xl[0][ly][SCE - 2 + c]; ext_fs = BY * SCE; ext_ring = (ly + 2) * HX + c;
+    } else {
+      const int ly = (e - 144) & 7, c = (e - 144) >> 3;
+      ext_src = &S.xr[0][ly][c]; ext_fs = BY * SCE; ext_ring = (ly + 2) * HX + BX + 2 + c;
     }
+  }
+  // slope tail: y slopes of rows -1 (warp 0) and BY (warp 1), x slopes of columns -1 and BX
+  // (warp 2, lanes 0..15): the cell's ring position, its neighbour step and output slot
+  int sl_ring = -1, sl_step = 0, sl_out = 0;
+  bool sl_y = false;
+  if (tid < 64) {
+    const int ly = tid < 32 ? -1 : BY;
+    sl_ring = (ly + 2) * HX + tx + 2; sl_step = HX; sl_out = (ly + 1) * BX + tx; sl_y = true;
+  } else if (tid < 80) {
+    const int lx = tid - 64 < 8 ? -1 : BX, ly = (tid - 64) & 7;
+    sl_ring = (ly + 2) * HX + lx + 2; sl_step = 1; sl_out = ly * (BX + 2) + lx + 1;
+  }
+  // face tail: x face BX of row lane (warp 6, lanes 0..7), y face BY of column lane (warp 7)
+  const bool fx_tail = warp == 6 && (tid & 31) < BY, fy_tail = warp == 7;
+
+  // the conversion of a staged plane into ring slot `slot`
+  auto convert_plane = [&](int slot) {
+    const real* c0 = &S.core[0][ty][tx];
+    qstore(S.w4[slot][ty + 2][tx + 2], S.wp[slot][ty + 2][tx + 2],
+           cons_to_prim(c0[0], c0[BY * BX], c0[2 * BY * BX], c0[3 * BY * BX], c0[4 * BY * BX], gm1));
+    if (ext_ring >= 0) {
+      Q4<real>* q = &S.w4[slot][0][0] + ext_ring;
+      qstore(*q, (&S.wp[slot][0][0])[ext_ring],
+             cons_to_prim(ext_src[0], ext_src[ext_fs], ext_src[2 * ext_fs], ext_src[3 * ext_fs],
+                          ext_src[4 * ext_fs], gm1));
+    }
+  };
+  auto ring_prim = [&](int slot, int off) {
+    return qprim((&S.w4[slot][0][0])[off], (&S.wp[slot][0][0])[off]);
   };
 
   auto load_plane = [&](int k, int slot) {
@@ -229,28 +326,34 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
 
   for (int k = z0; k < z1; ++k) {
     const int s0 = (k - z0) % 3, s1 = (k - z0 + 1) % 3, s2 = (k - z0 + 2) % 3;
-    cp_async_wait<0>();
+    if (via_tma) {
+      if (!tc::mbar_wait(&S.bar, (uint32_t)(k - z0) & 1u, STAGE_WAIT_ITERS)) s_abort = 1;
+    } else {
+      cp_async_wait<0>();
+    }
     __syncthreads();  // ---- plane k+2 staged; the update of plane k-1 is done
+    if (s_abort) break;
 
     convert_plane(s2);
-    // limited slopes and face states of plane k, once per cell and axis
-    for (int t = tid; t < NXSP + NYS; t += NTHREADS) {
-      if (t < NXSP) {
-        if (t >= NXS) continue;
-        const int ly = t / (BX + 2), r = t - ly * (BX + 2);
-        const int sy = ly + 2;
-        const Prim<real> w1 = smem_prim(S, s0, sy, r + 1);
-        const Prim<real> d = limited_slope<LIM>(smem_prim(S, s0, sy, r), w1, smem_prim(S, s0, sy, r + 2));
-        qstore(S.xm4[ly][r], S.xmp[ly][r], add_half(w1, d, real(-1)));
-        qstore(S.xp4[ly][r], S.xpp[ly][r], add_half(w1, d, real(1)));
+    // limited slopes and face states of plane k: own cell on both axes, then the tail
+    {
+      const Prim<real> w1 = ring_prim(s0, ring_own);
+      const Prim<real> dx = limited_slope<LIM>(ring_prim(s0, ring_own - 1), w1, ring_prim(s0, ring_own + 1));
+      qstore(S.xm4[ty][tx + 1], S.xmp[ty][tx + 1], add_half(w1, dx, real(-1)));
+      qstore(S.xp4[ty][tx + 1], S.xpp[ty][tx + 1], add_half(w1, dx, real(1)));
+      const Prim<real> dy = limited_slope<LIM>(ring_prim(s0, ring_own - HX), w1, ring_prim(s0, ring_own + HX));
+      qstore(S.ym4[ty + 1][tx], S.ymp[ty + 1][tx], add_half(w1, dy, real(-1)));
+      qstore(S.yp4[ty + 1][tx], S.ypp[ty + 1][tx], add_half(w1, dy, real(1)));
+    }
+    if (sl_ring >= 0) {
+      const Prim<real> w1 = ring_prim(s0, sl_ring);
+      const Prim<real> d = limited_slope<LIM>(ring_prim(s0, sl_ring - sl_step), w1, ring_prim(s0, sl_ring + sl_step));
+      if (sl_y) {
+        qstore((&S.ym4[0][0])[sl_out], (&S.ymp[0][0])[sl_out], add_half(w1, d, real(-1)));
+        qstore((&S.yp4[0][0])[sl_out], (&S.ypp[0][0])[sl_out], add_half(w1, d, real(1)));
       } else {
-        const int u = t - NXSP;
-        const int r = u / BX, lx = u - r * BX;
-        const int sx = lx + 2;
-        const Prim<real> w1 = smem_prim(S, s0, r + 1, sx);
-        const Prim<real> d = limited_slope<LIM>(smem_prim(S, s0, r, sx), w1, smem_prim(S, s0, r + 2, sx));
-        qstore(S.ym4[r][lx], S.ymp[r][lx], add_half(w1, d, real(-1)));
-        qstore(S.yp4[r][lx], S.ypp[r][lx], add_half(w1, d, real(1)));
+        qstore((&S.xm4[0][0])[sl_out], (&S.xmp[0][0])[sl_out], add_half(w1, d, real(-1)));
+        qstore((&S.xp4[0][0])[sl_out], (&S.xpp[0][0])[sl_out], add_half(w1, d, real(1)));
       }
     }
     if (forcing && tid >= NTHREADS - NFORCE) {
@@ -268,7 +371,7 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
       S.fB[ly][nxsel][c][0] = bre;
       S.fB[ly][nxsel][c][1] = bim;
     }
-    __syncthreads();  // ---- plane k+2 in the ring, face states ready, staging plane free
+    __syncthreads();  // ---- plane k+2 in the ring, face states ready, staging buffers free
 
     if (k + 1 < z1) stage_plane(k + 3);
     // the own cell's values for the update, loaded now and used after the face loop: U in
@@ -295,24 +398,32 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
       face_flux(2, add_half(w0, dk, real(1)), add_half(w1, dk1, real(-1)), gamma, gm1, fz_hi);
     }
 
-    // every x and y face of plane k, once
-    for (int f = tid; f < NXFP + NYF; f += NTHREADS) {
+    // x face tx and y face ty of the own cell, then the tail faces
+    {
       real F[5];
-      if (f < NXFP) {
-        if (f >= NXF) continue;
-        const int ly = f / (BX + 1), a = f - ly * (BX + 1);
-        face_flux(0, qprim(S.xp4[ly][a], S.xpp[ly][a]), qprim(S.xm4[ly][a + 1], S.xmp[ly][a + 1]),
-                  gamma, gm1, F);
-        S.fx4[ly][a] = Q4<real>{F[0], F[1], F[2], F[3]};
-        S.fxe[ly][a] = F[4];
-      } else {
-        const int g = f - NXFP;
-        const int a = g / BX, lx = g - a * BX;
-        face_flux(1, qprim(S.yp4[a][lx], S.ypp[a][lx]), qprim(S.ym4[a + 1][lx], S.ymp[a + 1][lx]),
-                  gamma, gm1, F);
-        S.fy4[a][lx] = Q4<real>{F[0], F[1], F[2], F[3]};
-        S.fye[a][lx] = F[4];
-      }
+      face_flux(0, qprim(S.xp4[ty][tx], S.xpp[ty][tx]), qprim(S.xm4[ty][tx + 1], S.xmp[ty][tx + 1]),
+                gamma, gm1, F);
+      S.fx4[ty][tx] = Q4<real>{F[0], F[1], F[2], F[3]};
+      S.fxe[ty][tx] = F[4];
+      face_flux(1, qprim(S.yp4[ty][tx], S.ypp[ty][tx]), qprim(S.ym4[ty + 1][tx], S.ymp[ty + 1][tx]),
+                gamma, gm1, F);
+      S.fy4[ty][tx] = Q4<real>{F[0], F[1], F[2], F[3]};
+      S.fye[ty][tx] = F[4];
+    }
+    if (fx_tail) {
+      const int ly = tid & 31;
+      real F[5];
+      face_flux(0, qprim(S.xp4[ly][BX], S.xpp[ly][BX]), qprim(S.xm4[ly][BX + 1], S.xmp[ly][BX + 1]),
+                gamma, gm1, F);
+      S.fx4[ly][BX] = Q4<real>{F[0], F[1], F[2], F[3]};
+      S.fxe[ly][BX] = F[4];
+    }
+    if (fy_tail) {
+      real F[5];
+      face_flux(1, qprim(S.yp4[BY][tx], S.ypp[BY][tx]), qprim(S.ym4[BY + 1][tx], S.ymp[BY + 1][tx]),
+                gamma, gm1, F);
+      S.fy4[BY][tx] = Q4<real>{F[0], F[1], F[2], F[3]};
+      S.fye[BY][tx] = F[4];
     }
     __syncthreads();  // ---- fluxes ready
 
@@ -404,6 +515,15 @@ stage_kernel(const StageArgs<real> p, const int zchunk) {
     for (int c = 0; c < 5; ++c) fz_lo[c] = fz_hi[c];
   }
 
+  if (s_abort) {
+    // a staging wait gave up: nothing this CTA would write is valid; the step fails
+    if (tid == 0) {
+      atomicOr(&p.rec->flags, FLAG_TIMEOUT);
+      atomicCAS(&p.rec->fail_step, -1, (int)(p.rec->nstep - 1));
+    }
+    return;
+  }
+
   if (COMB) {
     if (flags) {
       atomicOr(&p.rec->flags, flags);
@@ -455,6 +575,63 @@ int wave_zchunk(long long tiles, int nz, int resident_per_sm, double prologue) {
   return best;
 }
 
+// ---- tensor maps of state buffers (cached per base address and shape) ----------------------
+namespace {
+struct TmaEntry {
+  const void* base;
+  int nx, ny, nz, esize;
+  StageTma maps;
+};
+std::mutex g_tma_mutex;
+std::vector<TmaEntry> g_tma_cache;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+bool g_encode_failed = false;
+
+bool encode_box(CUtensorMap* m, const void* base, int nx, int ny, int nz, int esize, int bx, int by) {
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 5};
+  const cuuint64_t strides[3] = {(cuuint64_t)nx * esize, (cuuint64_t)nx * ny * esize,
+                                 (cuuint64_t)nx * ny * nz * esize};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 5};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return g_encode(m, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                  4, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+bool stage_tma_maps(const void* base, int nx, int ny, int nz, int esize, int bx, int by,
+                    StageTma* out) {
+  std::lock_guard<std::mutex> lock(g_tma_mutex);
+  for (const TmaEntry& e : g_tma_cache)
+    if (e.base == base && e.nx == nx && e.ny == ny && e.nz == nz && e.esize == esize) {
+      *out = e.maps;
+      return true;
+    }
+  if (g_encode_failed) return false;
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      g_encode_failed = true;
+      return false;
+    }
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  TmaEntry e{base, nx, ny, nz, esize, {}};
+  const int sce = 16 / esize;
+  if (!encode_box(&e.maps.core, base, nx, ny, nz, esize, bx, by) ||
+      !encode_box(&e.maps.xh, base, nx, ny, nz, esize, sce, by) ||
+      !encode_box(&e.maps.yh, base, nx, ny, nz, esize, bx, 2))
+    return false;
+  if (g_tma_cache.size() >= 64) g_tma_cache.erase(g_tma_cache.begin());
+  g_tma_cache.push_back(e);
+  *out = e.maps;
+  return true;
+}
+
 template <typename real, int STAGE, int LIM>
 static cudaError_t launch_stage_t(const StageArgs<real>& a, cudaStream_t s) {
   auto kernel = stage_kernel<real, STAGE, LIM>;
@@ -470,7 +647,14 @@ static cudaError_t launch_stage_t(const StageArgs<real>& a, cudaStream_t s) {
   const long long tiles = (long long)((a.nx + BX - 1) / BX) * ((a.ny + BY - 1) / BY);
   const int zc = wave_zchunk(tiles, a.nz, resident, 1.0);
   dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + zc - 1) / zc);
-  kernel<<<grid, NTHREADS, smem, s>>>(a, zc);
+  // TMA boxes need whole tiles (so that every halo strip is contiguous), a 16-byte aligned base
+  // and rows of a multiple of 16 bytes
+  StageTma maps;
+  std::memset(&maps, 0, sizeof(maps));
+  const bool tma_ok = a.nx % BX == 0 && a.ny % BY == 0 && a.ny >= 2 &&
+                      ((unsigned long long)a.U & 15ull) == 0 &&
+                      stage_tma_maps(a.U, a.nx, a.ny, a.nz, (int)sizeof(real), BX, BY, &maps);
+  kernel<<<grid, NTHREADS, smem, s>>>(a, zc, maps, tma_ok ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -32,6 +32,24 @@ def test_single_step_fp64_kh32():
     assert max(rel_linf(s.get_state(), ref)) <= 1e-11
 
 
+@pytest.mark.parametrize("shape", [(12, 16, 64), (8, 8, 32), (6, 24, 96)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 2e-5)])
+def test_tensor_map_tiles_with_sources(shape, prec, tol):
+    """Grids of whole 32 x 8 tiles, whose planes arrive by tensor-map (TMA) boxes: the tile core
+    and four halo strips, each wrapped to the other side of the periodic box at the edges; with
+    one tile across an axis both of its halos wrap onto the tile itself.  Three steps with
+    forcing and cooling against the oracle."""
+    U0 = inputs.decaying_turbulence(shape, seed=7, sigma=0.4, mach=1.0, p_sigma=0.2)
+    kw = dict(forcing=True, cooling=True)
+    sim = odrv.Simulation(odrv.Config(shape=shape, **kw), U0)
+    s = solver(shape, prec, **kw)
+    s.init_state(to_gpu(U0, prec))
+    for _ in range(3):
+        dt = s.step(0.0 if prec == "f64" else sim.compute_dt())
+        sim.step(dt)
+    assert max(rel_linf(s.get_state(), sim.U)) <= tol
+
+
 @pytest.mark.parametrize("shape", [(20, 12, 40), (9, 17, 33), (8, 8, 70)])
 def test_ragged_tiles_fp64(shape):
     U0 = inputs.decaying_turbulence(shape, seed=3, sigma=0.4, mach=1.0)
