@@ -267,6 +267,77 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
     return ({k: v.tolist() for k, v in err.items()}, {k: v / nrun for k, v in gpu_ms.items()}, sub)
 
 
+def evaluate_coarsened(fine: Solver, coarse_cfg: Config, factor: int, params, norm, fine_steps: int = 20,
+                       form: str = "state"):
+    """A trained corrector applied to a coarsened copy of a running fine simulation (the
+    self-gravitating benchmark configuration: its 256^3-trained corrector at 4x coarsening).
+
+    From the fine solver's current state, runs on the coarse grid start from D(U_f): uncorrected,
+    corrected after every coarse step, and uncorrected with round(t_corrected / t_uncorrected)
+    substeps per coarse step (the corrected run's GPU time, from the first interval's timings).
+    Each coarse interval takes the uncorrected run's CFL step; the fine run covers the same time
+    (its first substep draws the OU update, the rest hold it, and the coarse runs take that
+    table), until it has taken `fine_steps` steps.  Returns per-interval relative L2 errors
+    (mean over fields) against D(U_f), the GPU ms per coarse interval of each run, and the
+    fine run's steps and GPU ms."""
+    lib = _lib.load()
+    U0 = downsample(fine.get_state(), factor)
+    runs = {k: Solver(coarse_cfg) for k in ("uncorrected", "corrected", "uncorrected_equal_gpu_time")}
+    for s in runs.values():
+        s.init_state(U0)
+    _set_corrector(runs["corrected"], params, norm, form)
+    # warm-up of the coarse kernels and the network on a scratch context (first launches load
+    # modules and set attributes), so that the first interval's timings are representative
+    scratch = Solver(coarse_cfg)
+    scratch.init_state(U0)
+    _set_corrector(scratch, params, norm, form)
+    for _ in range(2):
+        scratch.step(scratch.compute_dt())
+        _lib.check(lib.dh_correct(scratch.ctx), scratch.ctx)
+    scratch.close()
+    forcing = coarse_cfg.forcing
+    err = {k: [] for k in runs}
+    gpu_ms = {k: 0.0 for k in runs}
+    fine_ms, intervals, sub = 0.0, 0, None
+    n0 = fine.time()[1]
+    while fine.time()[1] - n0 < fine_steps:
+        dt_c = runs["uncorrected"].compute_dt()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        modes = fine_interval(fine, dt_c, forcing)
+        e1.record()
+        e1.synchronize()
+        fine_ms += e0.elapsed_time(e1)
+        for name, s in runs.items():
+            if modes is not None:
+                s.set_forcing_modes(modes, hold=True)
+            if name == "corrected":
+                def adv(s=s):
+                    s.step(dt_c, sync=False)
+                    _lib.check(lib.dh_correct(s.ctx), s.ctx)
+            elif name == "uncorrected_equal_gpu_time":
+                if sub is None:
+                    sub = max(1, int(round(gpu_ms["corrected"] / max(gpu_ms["uncorrected"], 1e-9))))
+                def adv(s=s):
+                    for _ in range(sub):
+                        s.step(dt_c / sub, sync=False)
+            else:
+                def adv(s=s):
+                    s.step(dt_c, sync=False)
+            gpu_ms[name] += _timed(adv)
+        ref = downsample(fine.get_state(), factor)
+        for name, s in runs.items():
+            err[name].append(_rel_l2(s.get_state(), ref))
+        intervals += 1
+    for s in runs.values():
+        s.close()
+    return {"errors": err, "mean_error": {k: sum(v) / len(v) for k, v in err.items()},
+            "gpu_ms_per_interval": {k: v / intervals for k, v in gpu_ms.items()},
+            "equal_time_substeps": sub, "intervals": intervals,
+            "fine_steps": fine.time()[1] - n0, "fine_gpu_ms": fine_ms}
+
+
 # ---- solver-in-the-loop training (Sec. 7) ------------------------------------------------------
 @dataclasses.dataclass
 class Trajectory:

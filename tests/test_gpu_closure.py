@@ -101,3 +101,29 @@ def test_non_finite_correction_is_reported_and_state_kept():
     assert lib.dh_correct(s.ctx) == 3   # DH_ERR_NONFINITE
     assert torch.equal(s.get_state(), before)
     s.step(s.compute_dt())              # the context stays usable
+
+
+def test_evaluate_coarsened_self_gravitating():
+    """The corrector applied at 4x coarsening of a running self-gravitating fine simulation
+    (closure.evaluate_coarsened): errors against the block mean of the fine run are finite and
+    positive, the fine run takes the requested steps, and a corrector whose output is zero
+    leaves the corrected run on the uncorrected one (up to the floor's float32 rounding where
+    cooling holds a cell at the floor energy), interval by interval."""
+    from paper_2512_13403_b300.solver import Config, Solver
+    n = 32
+    phys = dict(forcing=True, cooling=True, t_floor=0.05, gravity=True, mg_tol=1e-6, mg_max_cycles=30)
+    fine = Solver(Config(shape=(n, n, n), precision="f32", **phys))
+    fine.init_state(to_gpu(inputs.self_gravitating_box((n, n, n), seed=5, sigma=0.5), "f32"))
+    fine.advance(2)
+    params = torch.zeros(NPARAM)
+    params[:] = init_params(0, out_scale=0.0)     # output layer zero: the correction is zero
+    norm = ([1.0, 0.0, 0.0, 0.0, 1.0], [0.1, 0.1, 0.1, 0.1, 0.1], [1e-3] * 5)
+    ccfg = Config(shape=(n // 4,) * 3, precision="f32", **phys)
+    res = closure.evaluate_coarsened(fine, ccfg, 4, params, norm, fine_steps=6)
+    assert res["fine_steps"] >= 6 and res["intervals"] >= 1
+    e_u, e_c = res["errors"]["uncorrected"], res["errors"]["corrected"]
+    assert all(np.isfinite(e_u)) and all(e > 0 for e in e_u)
+    assert np.allclose(e_c, e_u, rtol=1e-4, atol=0)
+    assert res["equal_time_substeps"] >= 1
+    assert all(np.isfinite(res["errors"]["uncorrected_equal_gpu_time"]))
+    fine.close()
