@@ -266,8 +266,9 @@ dh_status dh_adjoint_advance_dt(dh_ctx* ctx, int n_steps, int ckpt_every, double
    1 = linear (out fp32 planar [n_real][cell] = acc + bias); 2 = GELU gradient (out bf16
    padded, 32 channels, = bf16(acc * gelu'(z_in)), z_in fp32 [cell][32]).  Supported
    (cin_pad, nout_pad, mode): (8,32,0), (8,32,2), (32,32,0), (32,32,2), (32,16,1), (32,32,1).
-   Two shared-memory windows of (130 + 2 (nx+2)) rows per tap plane must fit next to the
-   weights: DH_ERR_ARG for nx beyond about 150 with 32 input channels.  *err_flag (device
+   Shared-memory windows of (130 + 2 (nx+2)) rows per tap plane must fit next to the weights:
+   two or three of them (copies overlapping the MMAs) up to nx of about 160 with 32 input
+   channels, one beyond; DH_ERR_ARG for nx beyond about 330.  *err_flag (device
    unsigned) becomes nonzero if a bounded wait inside the kernel gave up. */
 long long dh_conv_padded_rows(int nx, int ny, int nz);
 dh_status dh_conv_pad(const void* src, int channels, int nx, int ny, int nz, void* dst,

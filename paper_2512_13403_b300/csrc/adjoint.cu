@@ -17,8 +17,12 @@
 #include <math.h>
 #include <vector>
 
+#include <string.h>
+
 #include "async_copy.cuh"
 #include "dh_internal.h"
+#include "tc_ptx.cuh"
+#include "tma.cuh"
 #include "dh_adjoint.cuh"
 #include "dh_sources.cuh"
 
@@ -41,19 +45,22 @@ constexpr int NCX = NCXA * ABY, NCY = NCYA * ABX;   // cells with x and y slope 
 constexpr int warp_up(int n) { return (n + 31) / 32 * 32; }
 constexpr int NSXP = warp_up(NSX), NFXP = warp_up(NFX), NCXP = warp_up(NCX);
 
-// Staging plane: rows of conserved variables copied in 16-byte chunks of SCE elements, from
-// x0 - SHALO to x0 + ABX + SHALO (SHALO >= 3, a multiple of SCE); ring column sx is staging
-// column sx + SOFF.
+// Staged conserved variables of the plane in flight, one dense buffer per TMA box: the tile
+// core, x halos of 4 cells on each side (3 are read) and y halos of 3 rows.  The corner blocks
+// are never read by the stencil (x slopes and terms read rows 0..ABY-1, y slopes and terms
+// columns 0..ABX-1).  Each box is contiguous in global memory at any tile position (x0, y0 are
+// multiples of ABX, ABY), so the periodic wrap is a start coordinate.
+constexpr int AXH = 4, AYH = 3;
 template <typename real> struct AdjStaging {
-  static constexpr int SCE = 16 / (int)sizeof(real);
-  static constexpr int SHALO = (3 + SCE - 1) / SCE * SCE;
-  static constexpr int SROW = ABX + 2 * SHALO;
-  static constexpr int NCH = SROW / SCE;
-  static constexpr int SOFF = SHALO - 3;
+  static constexpr uint32_t BYTES = (uint32_t)sizeof(real) * 5u * (ABX * ABY + 2 * ABY * AXH + 2 * AYH * ABX);
 };
 
 template <typename real> struct AdjSmem {
-  real stg[5][WY][AdjStaging<real>::SROW];   // conserved variables of the plane in flight
+  alignas(128) real core[5][ABY][ABX];   // staged plane: tile core
+  alignas(128) real xl[5][ABY][AXH];     // x0 - 4 .. x0 - 1
+  alignas(128) real xr[5][ABY][AXH];     // x0 + ABX .. x0 + ABX + 3
+  alignas(128) real yt[5][AYH][ABX];     // y0 - 3 .. y0 - 1
+  alignas(128) real yb[5][AYH][ABX];     // y0 + ABY .. y0 + ABY + 2
   real w[4][5][WY][WX];
   real mu[5][MYH][MXH];           // lam_out of plane k (the stage's beta dt is applied at use)
   real face[10][NFXP + NFY];      // (gL[5], gR[5]) per face: x faces, then y faces
@@ -61,10 +68,10 @@ template <typename real> struct AdjSmem {
     real st[10][NSXP + NSY];      // (W - dW/2, W + dW/2) per cell and axis: x, then y
     real cell[10][NCXP + NCY];    // (A[5], B[5]) per cell: x terms, then y terms
   } u;
-  unsigned zero[(NSXP + NSY) / 32];   // bit t: the limited slope of slope item t is all zero
-  int xs[WX], ys[WY], cx[AdjStaging<real>::NCH];
+  unsigned char zero[NSXP + NSY];  // 1: the limited slope of slope item t is all zero
+  int xs[WX], ys[WY];
+  alignas(8) uint64_t bar;         // staging plane landed (TMA transaction bytes)
 };
-static_assert(NSXP % 32 == 0 && NSY % 32 == 0, "slope items come in whole warps");
 // two CTAs per SM for the float32 instance: 2 x (size + 1 KB reserved) within 228 KB
 static_assert(2 * (sizeof(AdjSmem<float>) + 1024) <= 228 * 1024, "adjoint shared memory");
 
@@ -73,10 +80,17 @@ __device__ __forceinline__ Prim<real> ring_prim(const AdjSmem<real>& S, int slot
   return Prim<real>{S.w[slot][0][sy][sx], S.w[slot][1][sy][sx], S.w[slot][2][sy][sx],
                     S.w[slot][3][sy][sx], S.w[slot][4][sy][sx]};
 }
+// the same by flat ring offset (sy WX + sx)
+template <typename real>
+__device__ __forceinline__ Prim<real> ring_prim_at(const AdjSmem<real>& S, int slot, int off) {
+  const real* b = &S.w[slot][0][0][0] + off;
+  constexpr int FS = WX * WY;
+  return Prim<real>{b[0], b[FS], b[2 * FS], b[3 * FS], b[4 * FS]};
+}
 
 template <typename real>
 __device__ __forceinline__ bool zero_bit(const AdjSmem<real>& S, int i) {
-  return (S.zero[i >> 5] >> (i & 31)) & 1u;
+  return S.zero[i] != 0;
 }
 
 template <typename real>
@@ -102,12 +116,26 @@ __device__ __forceinline__ void gload5(const real* __restrict__ p, long long n3,
 __device__ __forceinline__ void cp_async_elem(float* s, const float* g) { cp_async4(s, g); }
 __device__ __forceinline__ void cp_async_elem(double* s, const double* g) { cp_async8(s, g); }
 
+// Bound on the probes of the staging mbarrier (a plane's copies land in microseconds); a wait
+// that reaches it sets FLAG_TIMEOUT and the CTA stops.
+constexpr uint32_t ADJ_WAIT_ITERS = 1u << 22;
+
+// Work of a plane.  Thread (tx, ty) owns tile cell (tx, ty): its x and y slopes, the x face
+// between cells tx - 1 and tx and the y face between ty - 1 and ty, its x and y slope terms,
+// its primitive conversion and its lam_out copy.  The halo work is a fixed tail per thread with
+// offsets computed once: slopes of cells -2, -1, ABX, ABX + 1 (x) and -2, -1, ABY, ABY + 1 (y)
+// (threads 96..255), the conversion of the 240 used halo cells (threads 0..239), the faces
+// -3/2, ABX + 1/2, ABX + 3/2 (x) and the like in y (threads 136..255), the slope terms of cells
+// -1 and ABX (x), -1 and ABY (y) (threads 0..79), and the 160 halo cells of lam_out (threads
+// 96..255).
 // float32: two CTAs per SM (its registers and shared memory are sized for it); float64: one
 template <typename real, int LIM>
 __global__ void __launch_bounds__(ANT, sizeof(real) == 4 ? 2 : 1)
-stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk,
+                     const __grid_constant__ StageTma tma, const int use_tma) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   AdjSmem<real>& S = *reinterpret_cast<AdjSmem<real>*>(smem_raw);
+  __shared__ int s_abort;
   const int tid = threadIdx.x;
   const int tx = tid & (ABX - 1), ty = tid / ABX;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -125,13 +153,18 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
   const bool active = gx < nx && gy < ny;
   const long long col = (long long)(gy % ny) * nx + (gx % nx);
 
-  using ST = AdjStaging<real>;
   if (tid < WX) S.xs[tid] = ((x0 + tid - 3) % nx + nx) % nx;
   if (tid >= 64 && tid < 64 + WY) S.ys[tid - 64] = ((y0 + tid - 64 - 3) % ny + ny) % ny;
-  if (tid >= 96 && tid < 96 + ST::NCH)
-    S.cx[tid - 96] = ((x0 - ST::SHALO + ST::SCE * (tid - 96)) % nx + nx) % nx;
-  // whole 16-byte chunks need rows of a multiple of SCE elements and an aligned state
-  const bool vec = (nx % ST::SCE == 0) && (((unsigned long long)p.U & 15ull) == 0);
+  if (tid == 96) {
+    tc::mbar_init(&S.bar, 1u);
+    tc::mbar_fence_init();
+    s_abort = 0;
+  }
+  // box destinations must start on 128 bytes; the buffers are 128-byte multiples from S
+  const bool via_tma = use_tma != 0 && (tc::smem_u32(&S.core[0][0][0]) & 127u) == 0u;
+  const uint32_t bar = tc::smem_u32(&S.bar);
+  const int xl0 = x0 >= AXH ? x0 - AXH : nx - AXH, xr0 = x0 + ABX < nx ? x0 + ABX : 0;
+  const int yt0 = y0 >= AYH ? y0 - AYH : ny - AYH, yb0 = y0 + ABY < ny ? y0 + ABY : 0;
   __syncthreads();
 
   auto load_w = [&](int k, int slot) {
@@ -146,55 +179,226 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       S.w[slot][4][sy][sx] = w.p;
     }
   };
-  // cp.async of the conserved variables of plane k into the staging plane (one commit group);
-  // each item is one chunk (or cell) position with its five fields
+  // The conserved variables of plane k into the staging buffers: TMA (one thread, five boxes
+  // on the staging barrier), or element copies of every position (wrapped coordinates).
   auto stage_plane = [&](int k) {
-    const long long zoff = (long long)wrap(k, nz) * plane;
-    if (vec) {
-      for (int c = tid; c < WY * ST::NCH; c += ANT) {
-        const int sy = c / ST::NCH, j = c - sy * ST::NCH;
-        const real* g = p.U + zoff + (long long)S.ys[sy] * nx + S.cx[j];
-#pragma unroll
-        for (int f = 0; f < 5; ++f) cp_async16(&S.stg[f][sy][ST::SCE * j], g + f * n3);
+    const int kz = wrap(k, nz);
+    if (via_tma) {
+      if (tid == 0) {
+        tc::mbar_arrive_expect_tx(&S.bar, AdjStaging<real>::BYTES);
+        tma_load_4d(tc::smem_u32(&S.core[0][0][0]), &tma.core, x0, y0, kz, 0, bar);
+        tma_load_4d(tc::smem_u32(&S.xl[0][0][0]), &tma.xh, xl0, y0, kz, 0, bar);
+        tma_load_4d(tc::smem_u32(&S.xr[0][0][0]), &tma.xh, xr0, y0, kz, 0, bar);
+        tma_load_4d(tc::smem_u32(&S.yt[0][0][0]), &tma.yh, x0, yt0, kz, 0, bar);
+        tma_load_4d(tc::smem_u32(&S.yb[0][0][0]), &tma.yh, x0, yb0, kz, 0, bar);
       }
-    } else {
-      for (int c = tid; c < WY * WX; c += ANT) {
-        const int sy = c / WX, sx = c - sy * WX;
-        const real* g = p.U + zoff + (long long)S.ys[sy] * nx + S.xs[sx];
-#pragma unroll
-        for (int f = 0; f < 5; ++f) cp_async_elem(&S.stg[f][sy][sx + ST::SOFF], g + f * n3);
+      return;
+    }
+    const long long zoff = (long long)kz * plane;
+    constexpr int NC = ABX * ABY, NXH = ABY * AXH, NYH = AYH * ABX;
+    for (int c = tid; c < NC + 2 * NXH + 2 * NYH; c += ANT) {
+      int lx, ly, fs;
+      real* dst;
+      if (c < NC) {
+        lx = c % ABX; ly = c / ABX; dst = &S.core[0][ly][lx]; fs = ABY * ABX;
+      } else if (c < NC + 2 * NXH) {
+        const int e = c - NC, side = e / NXH, r = e - side * NXH;
+        ly = r / AXH;
+        const int cl = r - ly * AXH;
+        lx = side == 0 ? cl - AXH : ABX + cl;
+        dst = side == 0 ? &S.xl[0][ly][cl] : &S.xr[0][ly][cl];
+        fs = ABY * AXH;
+      } else {
+        const int e = c - NC - 2 * NXH, side = e / NYH, r = e - side * NYH;
+        const int row = r / ABX;
+        lx = r - row * ABX;
+        ly = side == 0 ? row - AYH : ABY + row;
+        dst = side == 0 ? &S.yt[0][row][lx] : &S.yb[0][row][lx];
+        fs = AYH * ABX;
       }
+      const int gxc = ((x0 + lx) % nx + nx) % nx, gyc = ((y0 + ly) % ny + ny) % ny;
+      const real* g = p.U + zoff + (long long)gyc * nx + gxc;
+#pragma unroll
+      for (int f = 0; f < 5; ++f) cp_async_elem(dst + f * fs, g + f * n3);
     }
     cp_async_commit();
   };
-  auto staged_prim = [&](int sy, int sx) {
-    const int q = sx + ST::SOFF;
-    return cons_to_prim(S.stg[0][sy][q], S.stg[1][sy][q], S.stg[2][sy][q], S.stg[3][sy][q],
-                        S.stg[4][sy][q], gm1);
+  auto wait_staged = [&](int j) {   // the j-th staged plane of this CTA (0-based)
+    if (via_tma) {
+      if (!tc::mbar_wait(&S.bar, (uint32_t)j & 1u, ADJ_WAIT_ITERS)) s_abort = 1;
+    } else {
+      cp_async_wait<0>();
+    }
   };
-  // primitive recovery of the staged plane into a ring slot; cells are taken from the last
-  // thread down, so that the warps with a third slope item get no third cell
+
+  // ---- fixed per-thread tasks -------------------------------------------------------------
+  constexpr int RFS = WX * WY;                    // ring field stride
+  const int ring_own = (ty + 3) * WX + tx + 3;
+  // conversion tail: rows 3..10 x columns {0,1,2,35,36,37} (48), rows 0..2 and 11..13 x
+  // columns 3..34 (192)
+  // (packed to keep the march's live registers few: source offset from S.core and its field
+  // stride, ring offset)
+  int cv_src = -1, cv_ring_fs = 0;
+  if (tid < 240) {
+    const real* base = &S.core[0][0][0];
+    const int e = tid;
+    const real* src;
+    int ring, fs;
+    if (e < 48) {
+      const int ly = e % ABY, c = e / ABY;          // c 0..5: sx = 0,1,2,35,36,37
+      if (c < 3) { src = &S.xl[0][ly][1 + c]; ring = (ly + 3) * WX + c; }
+      else { src = &S.xr[0][ly][c - 3]; ring = (ly + 3) * WX + ABX + 3 + (c - 3); }
+      fs = ABY * AXH;
+    } else {
+      const int r = (e - 48) / ABX, lx = (e - 48) % ABX;   // r 0..5: sy = 0,1,2,11,12,13
+      if (r < 3) { src = &S.yt[0][r][lx]; ring = r * WX + lx + 3; }
+      else { src = &S.yb[0][r - 3][lx]; ring = (ABY + 3 + (r - 3)) * WX + lx + 3; }
+      fs = AYH * ABX;
+    }
+    cv_src = (int)(src - base);
+    cv_ring_fs = ring | (fs << 16);
+  }
+  // slope tail (threads 96..255): x slopes of cells -2, -1, ABX, ABX + 1 in each row (32),
+  // y slopes of cells -2, -1, ABY, ABY + 1 in each column (128)
+  // (packed: ring offset | item << 10 | y axis << 20; -1 none)
+  int sl_pack = -1;
+  if (tid >= 96) {
+    const int e = tid - 96;
+    if (e < 32) {
+      const int ly = e % ABY, c = e / ABY;
+      const int lx = c < 2 ? c - 2 : ABX + (c - 2);
+      sl_pack = ((ly + 3) * WX + lx + 3) | ((ly * NSXA + lx + 2) << 10);
+    } else {
+      const int r = (e - 32) / ABX, lx = (e - 32) % ABX;
+      const int ly = r < 2 ? r - 2 : ABY + (r - 2);
+      sl_pack = ((ly + 3) * WX + lx + 3) | ((NSXP + (ly + 2) * ABX + lx) << 10) | (1 << 20);
+    }
+  }
+  // face tail (threads 136..255): x faces q = 0, 33, 34 of each row (24), y faces q = 0, 9, 10
+  // of each column (96)
+  // (packed: q | l << 8 | y axis << 16; -1 none)
+  int fc_pack = -1;
+  if (tid >= 136) {
+    const int e = tid - 136;
+    if (e < 24) {
+      const int c = e / ABY;
+      fc_pack = (c == 0 ? 0 : ABX + c) | ((e % ABY) << 8);
+    } else {
+      const int c = (e - 24) / ABX;
+      fc_pack = (c == 0 ? 0 : ABY + c) | (((e - 24) % ABX) << 8) | (1 << 16);
+    }
+  }
+  // slope-term tail (threads 0..79): x terms of cells -1 and ABX in each row (16), y terms of
+  // cells -1 and ABY in each column (64)
+  // (packed: r | l << 8 | y axis << 16; -1 none)
+  int tm_pack = -1;
+  if (tid < 80) {
+    if (tid < 16) tm_pack = ((tid / ABY) == 0 ? 0 : ABX + 1) | ((tid % ABY) << 8);
+    else tm_pack = (((tid - 16) / ABX) == 0 ? 0 : ABY + 1) | (((tid - 16) % ABX) << 8) | (1 << 16);
+  }
+  // lam_out copy tail (threads 96..255): mu rows 2..9 x columns {0,1,34,35} (32), rows
+  // {0,1,10,11} x columns 2..33 (128); in-plane source offset and mu offset
+  int mu_goff = -1, mu_soff = 0;   // in-plane offsets (planes below 2^31 cells)
+  if (tid >= 96) {
+    const int e = tid - 96;
+    int my, mx;
+    if (e < 32) { my = 2 + e % ABY; const int c = e / ABY; mx = c < 2 ? c : ABX + c; }
+    else { const int r = (e - 32) / ABX; mx = 2 + (e - 32) % ABX; my = r < 2 ? r : ABY + r; }
+    mu_soff = my * MXH + mx;
+    mu_goff = S.ys[my + 1] * nx + S.xs[mx + 1];
+  }
+  const int mu_gown = S.ys[ty + 3] * nx + S.xs[tx + 3];
+  const int mu_sown = (ty + 2) * MXH + tx + 2;
+
   auto convert_plane = [&](int slot) {
-    for (int c = ANT - 1 - tid; c < WX * WY; c += ANT) {
-      const int sy = c / WX, sx = c - sy * WX;
-      const Prim<real> w = staged_prim(sy, sx);
-      S.w[slot][0][sy][sx] = w.r;
-      S.w[slot][1][sy][sx] = w.vx;
-      S.w[slot][2][sy][sx] = w.vy;
-      S.w[slot][3][sy][sx] = w.vz;
-      S.w[slot][4][sy][sx] = w.p;
+    {
+      const real* c0 = &S.core[0][ty][tx];
+      const Prim<real> w = cons_to_prim(c0[0], c0[ABY * ABX], c0[2 * ABY * ABX], c0[3 * ABY * ABX],
+                                        c0[4 * ABY * ABX], gm1);
+      real* d = &S.w[slot][0][0][0] + ring_own;
+      d[0] = w.r; d[RFS] = w.vx; d[2 * RFS] = w.vy; d[3 * RFS] = w.vz; d[4 * RFS] = w.p;
+    }
+    if (cv_src >= 0) {
+      const real* src = &S.core[0][0][0] + cv_src;
+      const int fs = cv_ring_fs >> 16;
+      const Prim<real> w = cons_to_prim(src[0], src[fs], src[2 * fs], src[3 * fs], src[4 * fs], gm1);
+      real* d = &S.w[slot][0][0][0] + (cv_ring_fs & 0xffff);
+      d[0] = w.r; d[RFS] = w.vx; d[2 * RFS] = w.vy; d[3 * RFS] = w.vz; d[4 * RFS] = w.p;
     }
   };
   // cp.async of lam_out of plane k (x/y halo 2) into mu (one commit group)
   auto load_mu = [&](int k) {
     const long long zoff = (long long)wrap(k, nz) * plane;
-    for (int c = tid; c < MXH * MYH; c += ANT) {
-      const int sy = c / MXH, sx = c - sy * MXH;
-      const real* g = p.lam_out + zoff + (long long)S.ys[sy + 1] * nx + S.xs[sx + 1];
 #pragma unroll
-      for (int f = 0; f < 5; ++f) cp_async_elem(&S.mu[f][sy][sx], g + f * n3);
+    for (int f = 0; f < 5; ++f)
+      cp_async_elem(&S.mu[f][0][0] + mu_sown, p.lam_out + f * n3 + zoff + mu_gown);
+    if (mu_goff >= 0) {
+#pragma unroll
+      for (int f = 0; f < 5; ++f)
+        cp_async_elem(&S.mu[f][0][0] + mu_soff, p.lam_out + f * n3 + zoff + mu_goff);
     }
     cp_async_commit();
+  };
+  // one slope item: the limited slope of the ring cell at `ring` along `step`, its face states
+  // into slot `item` of the st arrays, and its all-zero byte
+  auto slope_item = [&](int slot, int ring, int step, int item) {
+    const Prim<real> w0 = ring_prim_at(S, slot, ring);
+    const Prim<real> d = limited_slope<LIM>(ring_prim_at(S, slot, ring - step), w0,
+                                            ring_prim_at(S, slot, ring + step));
+    const Prim<real> lo = add_half(w0, d, real(-1)), hi = add_half(w0, d, real(1));
+    S.u.st[0][item] = lo.r; S.u.st[1][item] = lo.vx; S.u.st[2][item] = lo.vy; S.u.st[3][item] = lo.vz;
+    S.u.st[4][item] = lo.p;
+    S.u.st[5][item] = hi.r; S.u.st[6][item] = hi.vx; S.u.st[7][item] = hi.vy; S.u.st[8][item] = hi.vz;
+    S.u.st[9][item] = hi.p;
+    S.zero[item] = slope_is_zero(d) ? 1 : 0;
+  };
+  // x face q of row ly (between cells lx = q - 2 and q - 1) or y face q of column lx
+  auto face_item = [&](bool yaxis, int q, int l) {
+    real g[5], gL[5], gR[5];
+    if (!yaxis) {
+      const int ly = l;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][ly + 2][q + 1] - S.mu[c][ly + 2][q]) * gfx;
+      const int i = ly * NSXA + q;
+      face_vjp(0, st_prim(S, 5, i), st_prim(S, 0, i + 1), g, gamma, gm1, gL, gR);
+      const int f = ly * NFXA + q;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) { S.face[c][f] = gL[c]; S.face[5 + c][f] = gR[c]; }
+    } else {
+      const int lx = l;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][q + 1][lx + 2] - S.mu[c][q][lx + 2]) * gfy;
+      const int i = NSXP + q * ABX + lx;
+      face_vjp(1, st_prim(S, 5, i), st_prim(S, 0, i + ABX), g, gamma, gm1, gL, gR);
+      const int f = NFXP + q * ABX + lx;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) { S.face[c][f] = gL[c]; S.face[5 + c][f] = gR[c]; }
+    }
+  };
+  // slope terms (A, B) of cell lx = r - 1 in row ly (x) or ly = r - 1 in column lx (y)
+  auto term_item = [&](int slot, bool yaxis, int r, int l) {
+    real D[5], A[5], B[5];
+    int e;
+    if (!yaxis) {
+      const int ly = l, sy = ly + 3;
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        D[c] = real(0.5) * S.face[c][ly * NFXA + r + 1] - real(0.5) * S.face[5 + c][ly * NFXA + r];
+      slope_vjp<LIM>(ring_prim(S, slot, sy, r + 1), ring_prim(S, slot, sy, r + 2),
+                     ring_prim(S, slot, sy, r + 3), zero_bit(S, ly * NSXA + r + 1), D, A, B);
+      e = ly * NCXA + r;
+    } else {
+      const int lx = l, sx = lx + 3;
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        D[c] = real(0.5) * S.face[c][NFXP + (r + 1) * ABX + lx] -
+               real(0.5) * S.face[5 + c][NFXP + r * ABX + lx];
+      slope_vjp<LIM>(ring_prim(S, slot, r + 1, sx), ring_prim(S, slot, r + 2, sx),
+                     ring_prim(S, slot, r + 3, sx), zero_bit(S, NSXP + (r + 1) * ABX + lx), D, A, B);
+      e = NCXP + r * ABX + lx;
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) { S.u.cell[c][e] = A[c]; S.u.cell[5 + c][e] = B[c]; }
   };
 
   // ---- prologue: ring planes z0..z0+2, own-column history below z0 -------------------------
@@ -245,40 +449,24 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
 
   for (int k = z0; k < z1; ++k) {
     const int s0 = (k - z0) & 3, s1 = (k - z0 + 1) & 3, s2 = (k - z0 + 2) & 3, s3 = (k - z0 + 3) & 3;
-    cp_async_wait<0>();
+    wait_staged(k - z0);
     __syncthreads();  // ---- plane k+3 staged; the gather of plane k-1 is done
+    if (s_abort) break;
 
     load_mu(k);
     real mun2[5];
     gload5(p.lam_out, n3, (long long)wrap(k + 2, nz) * plane + col, mun2);
 
-    // ---- limited slopes and face states of plane k along x and y, once per cell and axis -------
-    for (int t = tid; t < NSXP + NSY; t += ANT) {
-      bool zero = false;
-      if (t < NSX || t >= NSXP) {
-        Prim<real> wm, w0, wp;
-        if (t < NSXP) {
-          const int ly = t / NSXA, r = t - ly * NSXA;          // cell lx = r - 2
-          wm = ring_prim(S, s0, ly + 3, r);
-          w0 = ring_prim(S, s0, ly + 3, r + 1);
-          wp = ring_prim(S, s0, ly + 3, r + 2);
-        } else {
-          const int u = t - NSXP;
-          const int r = u / ABX, lx = u - r * ABX;             // cell ly = r - 2
-          wm = ring_prim(S, s0, r, lx + 3);
-          w0 = ring_prim(S, s0, r + 1, lx + 3);
-          wp = ring_prim(S, s0, r + 2, lx + 3);
-        }
-        const Prim<real> d = limited_slope<LIM>(wm, w0, wp);
-        const Prim<real> lo = add_half(w0, d, real(-1)), hi = add_half(w0, d, real(1));
-        S.u.st[0][t] = lo.r; S.u.st[1][t] = lo.vx; S.u.st[2][t] = lo.vy; S.u.st[3][t] = lo.vz;
-        S.u.st[4][t] = lo.p;
-        S.u.st[5][t] = hi.r; S.u.st[6][t] = hi.vx; S.u.st[7][t] = hi.vy; S.u.st[8][t] = hi.vz;
-        S.u.st[9][t] = hi.p;
-        zero = slope_is_zero(d);
-      }
-      const unsigned bits = __ballot_sync(0xffffffffu, zero);
-      if ((t & 31) == 0) S.zero[t >> 5] = bits;
+    // ---- limited slopes and face states of plane k along x and y: own cell, then the tail ----
+    // (one call site: every item, own or tail, runs the same instructions, so a cell's result
+    // does not depend on where it falls in its tile)
+#pragma unroll 1
+    for (int it = 0; it < (sl_pack >= 0 ? 3 : 2); ++it) {
+      const int ring = it < 2 ? ring_own : sl_pack & 0x3ff;
+      const int step = it == 0 ? 1 : (it == 1 ? WX : ((sl_pack >> 20) ? WX : 1));
+      const int item = it == 0 ? ty * NSXA + tx + 2
+                               : (it == 1 ? NSXP + (ty + 2) * ABX + tx : (sl_pack >> 10) & 0x3ff);
+      slope_item(s0, ring, step, item);
     }
     convert_plane(s3);
 
@@ -289,7 +477,9 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       wk = ring_prim(S, s0, ty + 3, tx + 3);
       const Prim<real> w1 = ring_prim(S, s1, ty + 3, tx + 3);
       const Prim<real> w2 = ring_prim(S, s2, ty + 3, tx + 3);
-      const Prim<real> w3 = staged_prim(ty + 3, tx + 3);   // this thread's cell of plane k+3
+      const real* c3 = &S.core[0][ty][tx];   // this thread's cell of plane k+3
+      const Prim<real> w3 = cons_to_prim(c3[0], c3[ABY * ABX], c3[2 * ABY * ABX], c3[3 * ABY * ABX],
+                                         c3[4 * ABY * ABX], gm1);
       const Prim<real> dz2 = limited_slope<LIM>(w1, w2, w3);
       real g[5], gL2[5], gR2[5], D[5], An[5], Bn[5];
       for (int c = 0; c < 5; ++c) g[c] = (mun2[c] - mun[c]) * gfz;
@@ -313,54 +503,19 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
     __syncthreads();  // ---- face states, mu of plane k and ring slot of plane k+3 ready
 
     if (k + 1 < z1) stage_plane(k + 4);
-    // ---- x and y face VJPs of plane k ------------------------------------------------------------
-    for (int f = tid; f < NFXP + NFY; f += ANT) {
-      real g[5], gL[5], gR[5];
-      if (f < NFXP) {
-        if (f >= NFX) continue;
-        const int ly = f / NFXA, q = f - ly * NFXA;   // between cells lx = q-2 and q-1
-#pragma unroll
-        for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][ly + 2][q + 1] - S.mu[c][ly + 2][q]) * gfx;
-        const int i = ly * NSXA + q;
-        face_vjp(0, st_prim(S, 5, i), st_prim(S, 0, i + 1), g, gamma, gm1, gL, gR);
-      } else {
-        const int fy = f - NFXP;
-        const int q = fy / ABX, lx = fy - q * ABX;    // between cells ly = q-2 and q-1
-#pragma unroll
-        for (int c = 0; c < 5; ++c) g[c] = (S.mu[c][q + 1][lx + 2] - S.mu[c][q][lx + 2]) * gfy;
-        const int i = NSXP + q * ABX + lx;
-        face_vjp(1, st_prim(S, 5, i), st_prim(S, 0, i + ABX), g, gamma, gm1, gL, gR);
-      }
-#pragma unroll
-      for (int c = 0; c < 5; ++c) { S.face[c][f] = gL[c]; S.face[5 + c][f] = gR[c]; }
+    // ---- x and y face VJPs of plane k: own faces, then the tail ------------------------------
+#pragma unroll 1
+    for (int it = 0; it < (fc_pack >= 0 ? 3 : 2); ++it) {
+      const int pk = it == 0 ? (tx + 1) | (ty << 8) : (it == 1 ? (ty + 1) | (tx << 8) | (1 << 16) : fc_pack);
+      face_item((pk >> 16) != 0, pk & 0xff, (pk >> 8) & 0xff);
     }
     __syncthreads();  // ---- face gradients ready; the face states are dead from here
 
     // ---- slope terms (A, B) of the x and y slopes; they overwrite the face states --------------
-    for (int e = tid; e < NCXP + NCY; e += ANT) {
-      real D[5], A[5], B[5];
-      if (e < NCXP) {
-        if (e >= NCX) continue;
-        const int ly = e / NCXA, r = e - ly * NCXA;   // cell lx = r - 1
-        const int sy = ly + 3;
-#pragma unroll
-        for (int c = 0; c < 5; ++c)
-          D[c] = real(0.5) * S.face[c][ly * NFXA + r + 1] - real(0.5) * S.face[5 + c][ly * NFXA + r];
-        slope_vjp<LIM>(ring_prim(S, s0, sy, r + 1), ring_prim(S, s0, sy, r + 2),
-                       ring_prim(S, s0, sy, r + 3), zero_bit(S, ly * NSXA + r + 1), D, A, B);
-      } else {
-        const int ey = e - NCXP;
-        const int r = ey / ABX, lx = ey - r * ABX;    // cell ly = r - 1
-        const int sx = lx + 3;
-#pragma unroll
-        for (int c = 0; c < 5; ++c)
-          D[c] = real(0.5) * S.face[c][NFXP + (r + 1) * ABX + lx] -
-                 real(0.5) * S.face[5 + c][NFXP + r * ABX + lx];
-        slope_vjp<LIM>(ring_prim(S, s0, r + 1, sx), ring_prim(S, s0, r + 2, sx),
-                       ring_prim(S, s0, r + 3, sx), zero_bit(S, NSXP + (r + 1) * ABX + lx), D, A, B);
-      }
-#pragma unroll
-      for (int c = 0; c < 5; ++c) { S.u.cell[c][e] = A[c]; S.u.cell[5 + c][e] = B[c]; }
+#pragma unroll 1
+    for (int it = 0; it < (tm_pack >= 0 ? 3 : 2); ++it) {
+      const int pk = it == 0 ? (tx + 1) | (ty << 8) : (it == 1 ? (ty + 1) | (tx << 8) | (1 << 16) : tm_pack);
+      term_item(s0, (pk >> 16) != 0, pk & 0xff, (pk >> 8) & 0xff);
     }
     __syncthreads();  // ---- slope terms ready
     {
@@ -397,6 +552,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk) {
       }
     }
   }
+  if (s_abort && tid == 0) atomicOr(p.flags, FLAG_TIMEOUT);   // a staging wait gave up
 }
 
 template <typename real>
@@ -413,7 +569,12 @@ cudaError_t launch_stage_adjoint(const AdjointArgs<real>& a, cudaStream_t s) {
     const long long tiles = (long long)((a.nx + ABX - 1) / ABX) * ((a.ny + ABY - 1) / ABY);
     const int zc = wave_zchunk(tiles, a.nz, resident, 1.0);
     dim3 grid((a.nx + ABX - 1) / ABX, (a.ny + ABY - 1) / ABY, (a.nz + zc - 1) / zc);
-    kernel<<<grid, ANT, smem, s>>>(a, zc);
+    StageTma maps;
+    memset(&maps, 0, sizeof(maps));
+    const bool tma_ok = a.nx % ABX == 0 && a.ny % ABY == 0 && a.nx >= AXH && a.ny >= AYH &&
+                        ((unsigned long long)a.U & 15ull) == 0 &&
+                        stage_tma_maps(a.U, a.nx, a.ny, a.nz, (int)sizeof(real), ABX, ABY, AXH, AYH, &maps);
+    kernel<<<grid, ANT, smem, s>>>(a, zc, maps, tma_ok ? 1 : 0);
     return cudaGetLastError();
   };
   static int res_vl = 0, res_mc = 0;   // CTAs per SM of each instance
@@ -688,6 +849,7 @@ static cudaError_t adjoint_stage(dh_ctx* c, const void* U, const void* lam_out, 
   a.c1 = c1; a.c2 = c2; a.beta = beta; a.dtp = dtp;
   a.extra2 = (const real*)extra2; a.c3 = c3;
   a.limiter = g.limiter;
+  a.flags = &c->rec->flags;
   prof_begin(c, DH_KERNEL_ADJOINT);
   cudaError_t e = launch_stage_adjoint<real>(a, c->stream);
   prof_end(c, 1);
@@ -890,6 +1052,19 @@ extern "C" dh_status dh_adjoint_advance_dt(dh_ctx* c, int n, int k, double dt,
     e = cudaMemcpyAsync(mg_phi(c), a->phi_keep, pb, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) { c->err = std::string("adjoint backward: ") + cudaGetErrorString(e); return DH_ERR_CUDA; }
+  {
+    // a kernel whose bounded wait for its own copies gave up raised the flag in the step record
+    StepRecord r;
+    e = cudaMemcpy(&r, c->rec, sizeof(r), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return DH_ERR_CUDA; }
+    if (r.flags & FLAG_TIMEOUT) {
+      r.flags &= ~FLAG_TIMEOUT;
+      r.fail_step = -1;
+      cudaMemcpy(c->rec, &r, sizeof(r), cudaMemcpyHostToDevice);
+      c->err = "adjoint: a kernel's bounded wait for its own copies gave up";
+      return DH_ERR_CUDA;
+    }
+  }
   if (a->gravity) {
     // an adjoint Poisson solve that missed mg_tol raised the flag in the step record
     StepRecord r;

@@ -317,9 +317,11 @@ template <int CIN, int NOUT, int MODE>
 static cudaError_t launch_conv(const ConvArgs& a, const ConvGeom& g, cudaStream_t s) {
   using S = ConvShape<CIN, NOUT>;
   if (g.rows >= (1LL << 31)) return cudaErrorInvalidValue;   // padded rows are 32-bit indices
+  // as many window stages as fit (one stage: each tile's windows load after the previous
+  // tile's MMAs, without overlap, for long rows)
   int stages = CV_MAX_STAGES;
   while (stages >= 2 && S::smem_bytes(g, stages) > (size_t)CV_SMEM_MAX) --stages;
-  if (stages < 2) return cudaErrorInvalidValue;
+  if (S::smem_bytes(g, stages) > (size_t)CV_SMEM_MAX) return cudaErrorInvalidValue;
   const size_t smem = S::smem_bytes(g, stages);
   auto kern = conv3d_tc_kernel<CIN, NOUT, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

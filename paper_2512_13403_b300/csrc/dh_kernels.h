@@ -93,6 +93,7 @@ template <typename real> struct AdjointArgs {
   const real* extra2;    // added with weight c3 (nullable; SSPRK3's first stage)
   real c3;
   int limiter;           // LIM_MC or LIM_VL
+  unsigned* flags;       // step record flags: FLAG_TIMEOUT if a bounded copy wait gives up
 };
 // Adjoint of the operator-split sources of one step (forcing kick, gravity kick, cooling),
 // pointwise: lamH = (dF/dU)^T (dG/dU)^T (dC/dU)^T lam at the state UH the sources were applied

@@ -579,7 +579,7 @@ int wave_zchunk(long long tiles, int nz, int resident_per_sm, double prologue) {
 namespace {
 struct TmaEntry {
   const void* base;
-  int nx, ny, nz, esize;
+  int nx, ny, nz, esize, bx, by, xw, yh;
   StageTma maps;
 };
 std::mutex g_tma_mutex;
@@ -600,11 +600,12 @@ bool encode_box(CUtensorMap* m, const void* base, int nx, int ny, int nz, int es
 }
 }  // namespace
 
-bool stage_tma_maps(const void* base, int nx, int ny, int nz, int esize, int bx, int by,
-                    StageTma* out) {
+bool stage_tma_maps(const void* base, int nx, int ny, int nz, int esize, int bx, int by, int xw,
+                    int yh, StageTma* out) {
   std::lock_guard<std::mutex> lock(g_tma_mutex);
   for (const TmaEntry& e : g_tma_cache)
-    if (e.base == base && e.nx == nx && e.ny == ny && e.nz == nz && e.esize == esize) {
+    if (e.base == base && e.nx == nx && e.ny == ny && e.nz == nz && e.esize == esize && e.bx == bx &&
+        e.by == by && e.xw == xw && e.yh == yh) {
       *out = e.maps;
       return true;
     }
@@ -620,11 +621,10 @@ bool stage_tma_maps(const void* base, int nx, int ny, int nz, int esize, int bx,
     }
     g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  TmaEntry e{base, nx, ny, nz, esize, {}};
-  const int sce = 16 / esize;
+  TmaEntry e{base, nx, ny, nz, esize, bx, by, xw, yh, {}};
   if (!encode_box(&e.maps.core, base, nx, ny, nz, esize, bx, by) ||
-      !encode_box(&e.maps.xh, base, nx, ny, nz, esize, sce, by) ||
-      !encode_box(&e.maps.yh, base, nx, ny, nz, esize, bx, 2))
+      !encode_box(&e.maps.xh, base, nx, ny, nz, esize, xw, by) ||
+      !encode_box(&e.maps.yh, base, nx, ny, nz, esize, bx, yh))
     return false;
   if (g_tma_cache.size() >= 64) g_tma_cache.erase(g_tma_cache.begin());
   g_tma_cache.push_back(e);
@@ -653,7 +653,8 @@ static cudaError_t launch_stage_t(const StageArgs<real>& a, cudaStream_t s) {
   std::memset(&maps, 0, sizeof(maps));
   const bool tma_ok = a.nx % BX == 0 && a.ny % BY == 0 && a.ny >= 2 &&
                       ((unsigned long long)a.U & 15ull) == 0 &&
-                      stage_tma_maps(a.U, a.nx, a.ny, a.nz, (int)sizeof(real), BX, BY, &maps);
+                      stage_tma_maps(a.U, a.nx, a.ny, a.nz, (int)sizeof(real), BX, BY,
+                                     Staging<real>::SCE, 2, &maps);
   kernel<<<grid, NTHREADS, smem, s>>>(a, zc, maps, tma_ok ? 1 : 0);
   return cudaGetLastError();
 }

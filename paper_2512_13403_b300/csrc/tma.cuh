@@ -10,18 +10,18 @@
 
 namespace dh {
 
-// Box loads of a state plane used by the stage kernels: the tile core (BX x BY cells), the x
-// halos (16 bytes of cells on each side, BY rows) and the y halos (BX cells, 2 rows), all five
-// fields at once (the fourth dimension).
+// Box loads of a state plane used by the stage kernels: the tile core, the x halos on each side
+// and the y halos above and below, all five fields at once (the fourth dimension).
 struct StageTma {
   CUtensorMap core, xh, yh;
 };
 
-// Encodes the three maps for a state of nx * ny * nz cells of `esize` bytes (4 or 8) at `base`
-// (cached per base address and shape).  False if the driver refuses, in which case callers use
-// plain asynchronous copies.
-bool stage_tma_maps(const void* base, int nx, int ny, int nz, int esize, int bx, int by,
-                    StageTma* out);
+// Encodes the three maps for a state of nx * ny * nz cells of `esize` bytes (4 or 8) at `base`:
+// core boxes of bx x by cells, x-halo boxes of xw x by, y-halo boxes of bx x yh (cached per base
+// address, shape and box sizes).  False if the driver refuses, in which case callers use plain
+// asynchronous copies.
+bool stage_tma_maps(const void* base, int nx, int ny, int nz, int esize, int bx, int by, int xw,
+                    int yh, StageTma* out);
 
 #if defined(__CUDACC__)
 // Loads the box at coordinates (x, y, z, f) of `map` into shared memory at dst (128-byte

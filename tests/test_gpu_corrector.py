@@ -123,6 +123,20 @@ def test_hidden_layer_32_to_32_gelu(shape):
     assert float((zg - zr).abs().max() / zr.abs().max()) < 1e-5
 
 
+def test_long_rows_take_one_window_stage():
+    """Rows of 176 cells leave room for one shared-memory window stage only (the tile's windows
+    load after the previous tile's MMAs): the hidden layer still matches the oracle."""
+    shape = (4, 5, 176)
+    g = torch.Generator().manual_seed(13)
+    x = oc.bf16(torch.randn((32,) + shape, generator=g, dtype=torch.float64))
+    W = torch.randn(32, 32, 3, 3, 3, generator=g, dtype=torch.float64) * 0.05
+    b = torch.randn(32, generator=g, dtype=torch.float64) * 0.1
+    out, z = _conv(_act(x, 32), 32, _pack(W, 0), 32, b, 0, shape)
+    zr = oc.conv3d_periodic(x, oc.bf16(W), b)
+    zg = _planar(z, 32, shape)
+    assert float((zg - zr).abs().max() / zr.abs().max()) < 1e-5
+
+
 def test_padded_output_layout_images_and_guards():
     """The GELU output in the padded layout: every halo row equals the periodic image it
     stands for, and the guard rows stay zero."""
