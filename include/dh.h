@@ -147,6 +147,9 @@ typedef struct dh_metrics {
   long long nstep;          /* completed steps                                           */
   unsigned flags;           /* DH_FLAG_* bits                                            */
   int cool_max_substeps;    /* largest cooling substep count since the previous read     */
+  long long slope_fallbacks; /* positivity fallbacks of the PLM slopes since the previous
+                                read: (cell, axis, RK stage) triples whose slopes were zeroed
+                                because a face state had rho <= 0 or P <= 0 (App. A.2)     */
   int mg_cycles;            /* cycles of the last Poisson solve (0 without gravity)      */
   double mg_residual;       /* its ||F - A phi||_2 / ||F||_2                             */
   double totals[5];         /* sums over cells of rho, m_x, m_y, m_z, E (float64)        */

@@ -38,7 +38,8 @@ class DhConfig(C.Structure):
 class DhMetrics(C.Structure):
     _fields_ = [
         ("t", C.c_double), ("dt", C.c_double), ("nstep", C.c_longlong), ("flags", C.c_uint),
-        ("cool_max_substeps", C.c_int), ("mg_cycles", C.c_int), ("mg_residual", C.c_double),
+        ("cool_max_substeps", C.c_int), ("slope_fallbacks", C.c_longlong),
+        ("mg_cycles", C.c_int), ("mg_residual", C.c_double),
         ("totals", C.c_double * 5), ("rho_min", C.c_double), ("p_min", C.c_double),
     ]
 

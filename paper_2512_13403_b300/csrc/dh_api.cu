@@ -282,6 +282,7 @@ static StageArgs<real> stage_args(dh_ctx* c) {
   a.limiter = g.limiter;
   a.w0 = real(0.5); a.w1 = real(0.5);
   a.final_stage = 1;
+  a.count_fallbacks = 1;
   return a;
 }
 
@@ -492,6 +493,7 @@ extern "C" dh_status dh_get_metrics(dh_ctx* c, dh_metrics* out) {
   out->nstep = c->host_rec.nstep;
   out->flags = c->host_rec.flags;
   out->cool_max_substeps = c->host_rec.cool_nsub_max;
+  out->slope_fallbacks = (long long)c->host_rec.slope_fallbacks;
   if (c->cfg.cooling && out->cool_max_substeps < 1 && out->nstep > 0) out->cool_max_substeps = 1;
   dh::mg_last(c, &out->mg_cycles, &out->mg_residual);
   double* mins = c->partials + 2 * totals_blocks();
@@ -508,8 +510,10 @@ extern "C" dh_status dh_get_metrics(dh_ctx* c, dh_metrics* out) {
   DH_CUDA(c, cudaMemcpyAsync(m2, mins, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   // the substep maximum covers the interval since the previous read
   DH_CUDA(c, cudaMemsetAsync(&c->rec->cool_nsub_max, 0, sizeof(int), c->stream));
+  DH_CUDA(c, cudaMemsetAsync(&c->rec->slope_fallbacks, 0, sizeof(unsigned long long), c->stream));
   DH_CUDA(c, cudaStreamSynchronize(c->stream));
   c->host_rec.cool_nsub_max = 0;
+  c->host_rec.slope_fallbacks = 0;
   out->rho_min = m2[0];
   out->p_min = m2[1];
   return st;

@@ -29,6 +29,7 @@ struct StepRecord {
   unsigned long long cfl_min_bits;  // min over cells of dx_a/(|v_a|+c) as ordered bits
   double ou_norm;        // a_rms / sqrt(<|a|^2>) of the current forcing table
   int cool_nsub_max;     // largest cooling substep count (> 1) since the last metrics read
+  unsigned long long slope_fallbacks;  // positivity fallbacks (cell, axis, stage) since the last read
 };
 
 __host__ __device__ inline int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -126,10 +127,11 @@ __host__ __device__ __forceinline__ real lim_slope(real a, real b) {
 }
 
 // Limited slope of a cell from its two neighbours along one axis, with the positivity fallback:
-// if W +- dW/2 has rho <= 0 or P <= 0 every slope of the cell on that axis is zero.
+// if W +- dW/2 has rho <= 0 or P <= 0 every slope of the cell on that axis is zero, and
+// `fallbacks` is incremented.
 template <int LIM = LIM_MC, typename real>
 __host__ __device__ __forceinline__ Prim<real> limited_slope(const Prim<real>& wm, const Prim<real>& w0,
-                                                    const Prim<real>& wp) {
+                                                    const Prim<real>& wp, int& fallbacks) {
 #if defined(__CUDA_ARCH__)
   if constexpr (std::is_same<real, float>::value && LIM == LIM_MC) {
     const float2 c01 = f2(w0.r, w0.vx), c23 = f2(w0.vy, w0.vz);
@@ -140,7 +142,10 @@ __host__ __device__ __forceinline__ Prim<real> limited_slope(const Prim<real>& w
     const float2 rp = f2(w0.r, w0.p);
     const float2 up = p_add(rp, h), dn = p_sub(rp, h);
     const bool bad = (up.x <= 0.0f) || (up.y <= 0.0f) || (dn.x <= 0.0f) || (dn.y <= 0.0f);
-    if (bad) return Prim<float>{0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (bad) {
+      ++fallbacks;
+      return Prim<float>{0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    }
     return Prim<float>{d01.x, d01.y, d23.x, d23.y, dp};
   }
 #endif
@@ -153,8 +158,18 @@ __host__ __device__ __forceinline__ Prim<real> limited_slope(const Prim<real>& w
   const real hr = real(0.5) * d.r, hp = real(0.5) * d.p;
   const bool bad = (w0.r + hr <= real(0)) || (w0.p + hp <= real(0)) || (w0.r - hr <= real(0)) ||
                    (w0.p - hp <= real(0));
-  if (bad) d = Prim<real>{real(0), real(0), real(0), real(0), real(0)};
+  if (bad) {
+    ++fallbacks;
+    d = Prim<real>{real(0), real(0), real(0), real(0), real(0)};
+  }
   return d;
+}
+
+template <int LIM = LIM_MC, typename real>
+__host__ __device__ __forceinline__ Prim<real> limited_slope(const Prim<real>& wm, const Prim<real>& w0,
+                                                    const Prim<real>& wp) {
+  int unused = 0;
+  return limited_slope<LIM>(wm, w0, wp, unused);
 }
 
 template <typename real>

@@ -31,6 +31,7 @@ template <typename real> struct StageArgs {
   // positivity checks, CFL).  Stage 2 is RK2's final stage with weights (1/2, 1/2).
   real w0, w1;
   int final_stage;
+  int count_fallbacks;    // add the own cells' positivity fallbacks to rec->slope_fallbacks
 };
 
 // stage 1: U + dt L(U); 2: RK2's final stage; 3: the weighted combination of SSPRK3

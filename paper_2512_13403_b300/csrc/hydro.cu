@@ -311,11 +311,12 @@ stage_kernel(const StageArgs<real> p, const int zchunk, const __grid_constant__ 
   __syncthreads();
   Prim<real> dk;          // z slope of the own cell at plane k
   real fz_lo[5];          // z flux on face k - 1/2
+  int nfb = 0;            // positivity fallbacks of the own cell's slopes (x, y, z per plane)
   {
     const Prim<real> w0 = smem_prim(S, 0, ty + 2, tx + 2);
     const Prim<real> w1 = smem_prim(S, 1, ty + 2, tx + 2);
     const Prim<real> dm1 = limited_slope<LIM>(wm2, wm1, w0);
-    dk = limited_slope<LIM>(wm1, w0, w1);
+    dk = limited_slope<LIM>(wm1, w0, w1, nfb);
     face_flux(2, add_half(wm1, dm1, real(1)), add_half(w0, dk, real(-1)), gamma, gm1, fz_lo);
   }
   stage_plane(z0 + 2);
@@ -338,10 +339,10 @@ stage_kernel(const StageArgs<real> p, const int zchunk, const __grid_constant__ 
     // limited slopes and face states of plane k: own cell on both axes, then the tail
     {
       const Prim<real> w1 = ring_prim(s0, ring_own);
-      const Prim<real> dx = limited_slope<LIM>(ring_prim(s0, ring_own - 1), w1, ring_prim(s0, ring_own + 1));
+      const Prim<real> dx = limited_slope<LIM>(ring_prim(s0, ring_own - 1), w1, ring_prim(s0, ring_own + 1), nfb);
       qstore(S.xm4[ty][tx + 1], S.xmp[ty][tx + 1], add_half(w1, dx, real(-1)));
       qstore(S.xp4[ty][tx + 1], S.xpp[ty][tx + 1], add_half(w1, dx, real(1)));
-      const Prim<real> dy = limited_slope<LIM>(ring_prim(s0, ring_own - HX), w1, ring_prim(s0, ring_own + HX));
+      const Prim<real> dy = limited_slope<LIM>(ring_prim(s0, ring_own - HX), w1, ring_prim(s0, ring_own + HX), nfb);
       qstore(S.ym4[ty + 1][tx], S.ymp[ty + 1][tx], add_half(w1, dy, real(-1)));
       qstore(S.yp4[ty + 1][tx], S.ypp[ty + 1][tx], add_half(w1, dy, real(1)));
     }
@@ -394,7 +395,9 @@ stage_kernel(const StageArgs<real> p, const int zchunk, const __grid_constant__ 
       const Prim<real> w0 = smem_prim(S, s0, ty + 2, tx + 2);
       const Prim<real> w1 = smem_prim(S, s1, ty + 2, tx + 2);
       const Prim<real> w2 = smem_prim(S, s2, ty + 2, tx + 2);
-      dk1 = limited_slope<LIM>(w0, w1, w2);
+      int nfz = 0;  // plane k+1 is the own cell's only below the chunk's end (else the next chunk's)
+      dk1 = limited_slope<LIM>(w0, w1, w2, nfz);
+      if (k + 1 < z1) nfb += nfz;
       face_flux(2, add_half(w0, dk, real(1)), add_half(w1, dk1, real(-1)), gamma, gm1, fz_hi);
     }
 
@@ -522,6 +525,15 @@ stage_kernel(const StageArgs<real> p, const int zchunk, const __grid_constant__ 
       atomicCAS(&p.rec->fail_step, -1, (int)(p.rec->nstep - 1));
     }
     return;
+  }
+
+  if (p.count_fallbacks) {
+    unsigned long long n = active ? (unsigned long long)nfb : 0ull;
+    if (__any_sync(0xffffffffu, n != 0ull)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+      if ((tid & 31) == 0) atomicAdd(&p.rec->slope_fallbacks, n);
+    }
   }
 
   if (COMB) {

@@ -30,6 +30,18 @@
 
 namespace dh {
 constexpr int MG_LMAX = 16;
+// State of one solve on the device.  The residual of each iterate is judged by
+// mg_decide_kernel, so the host enqueues several cycles between reads of this block; once stop
+// is set, the kernels enqueued after it return at once.
+struct MGCtl {
+  int stop;      // the solve has finished (first word: the kernels' guard)
+  int cycles;    // cycles run
+  int ok;        // the residual reached mg_tol (or the source is zero)
+  int zero;      // zero source: phi = 0
+  int skipped;   // a fatal failure earlier in the step: nothing solved
+  int pad;
+  double rel;    // ||F - A phi||_2 / ||F||_2 of the last iterate
+};
 // reductions: 8 CTAs per SM over 148 SMs (enough warps to cover the stencil loads), then one
 // warp adds the per-block partials in a fixed order
 constexpr int RED_BLOCKS = 148 * 8, RED_THREADS = 256;
@@ -63,6 +75,10 @@ struct MG {
   double* G = nullptr;           // coarsest circulant pseudo-inverse
   double* partials = nullptr;    // max(RED_BLOCKS, residual CTAs) doubles
   double* scal = nullptr;        // [0] mean rho, [1] |F|^2, [2] |r|^2, [3] mean phi
+  // the solve's control block on the device (dh::MGCtl); stop points at its first word, which
+  // every kernel of a cycle and of the residual reads first
+  void* ctl = nullptr;
+  int* stop = nullptr;
   int last_cycles = 0;
   double last_res = 0.0;
   // One cycle as a CUDA graph (captured on first use): its hundreds of small launches at the
@@ -135,6 +151,9 @@ cudaError_t mg_allocate(dh_ctx* c) {
       e = cudaMalloc(&m->partials, (rb > RED_BLOCKS ? rb : RED_BLOCKS) * sizeof(double));
   }
   if (e == cudaSuccess) e = cudaMalloc(&m->scal, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&m->ctl, sizeof(MGCtl));
+  if (e == cudaSuccess) e = cudaMemset(m->ctl, 0, sizeof(MGCtl));
+  m->stop = (int*)m->ctl;
   // the potential is the warm start of the first solve: zero, not whatever the allocator held
   if (e == cudaSuccess) e = cudaMemset(m->phi, 0, 2 * m->cells[0] * sizeof(float));
   return e;
@@ -194,6 +213,7 @@ void mg_free(dh_ctx* c) {
   cudaFree(m->G);
   cudaFree(m->partials);
   cudaFree(m->scal);
+  cudaFree(m->ctl);
   if (m->cycle_exec) cudaGraphExecDestroy(m->cycle_exec);
   delete m;
   c->mg = nullptr;
@@ -222,7 +242,8 @@ __device__ __forceinline__ void block_range(long long n, long long& b0, long lon
 // order, and so the result, does not depend on scheduling)
 constexpr int FIN_THREADS = 1024;
 __global__ void __launch_bounds__(FIN_THREADS)
-finalize_kernel(const double* partials, int nb, double* out, double scale) {
+finalize_kernel(const double* partials, int nb, double* out, double scale, const int* stop = nullptr) {
+  if (stop && *stop) return;
   __shared__ double wsum[FIN_THREADS / 32];
   const int t = threadIdx.x;
   double s = 0.0;
@@ -316,7 +337,8 @@ constexpr int SW_RING = 6;                             // >= 3 + SW_D old-e and 
 template <bool ZERO>   // ZERO: e_old = 0 (the first sweep of a V-cycle level; e_old unread)
 __global__ void __launch_bounds__(256, 8)
 rbgs_sweep_kernel(const float* __restrict__ eo, float* __restrict__ en, const float* __restrict__ r,
-                  int nx, int ny, int nz, float h2) {
+                  int nx, int ny, int nz, float h2, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   __shared__ float s_eo[ZERO ? 1 : SW_RING][SW_E];
   __shared__ float s_r[SW_RING][SW_R];
   __shared__ float s_red[3][SW_R];
@@ -432,7 +454,8 @@ constexpr int S4_D = 2, S4_ERING = 3 + S4_D, S4_RRING = 3 + S4_D;
 template <bool ZERO>
 __global__ void __launch_bounds__(256)
 rbgs_sweep4_kernel(const float* __restrict__ eo, float* __restrict__ en, const float* __restrict__ r,
-                   int nx, int ny, int nz, float h2) {
+                   int nx, int ny, int nz, float h2, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   __shared__ __align__(16) float s_eo[ZERO ? 1 : S4_ERING][S4_EROWS * S4_W];
   __shared__ __align__(16) float s_r[S4_RRING][S4_RROWS * S4_W];
   __shared__ float s_red[3][S4_RROWS * S4_W];
@@ -532,7 +555,8 @@ constexpr int J4_D = 2, J4_ERING = 4 + J4_D, J4_RRING = 2 + J4_D;   // no slot a
 
 __global__ void __launch_bounds__(256)
 jacobi4_kernel(const float* __restrict__ eo, float* __restrict__ en, const float* __restrict__ r,
-               int nx, int ny, int nz, float h2, float omega) {
+               int nx, int ny, int nz, float h2, float omega, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   __shared__ __align__(16) float s_e[J4_ERING][J4_EROWS * S4_W];
   __shared__ __align__(16) float s_r[J4_RRING][S4_TY * S4_TX];
   const int tid = threadIdx.x;
@@ -597,7 +621,8 @@ jacobi4_kernel(const float* __restrict__ eo, float* __restrict__ en, const float
 // The same for any row length, one cell per thread from global memory.
 __global__ void jacobi_kernel(const float* __restrict__ eo, float* __restrict__ en,
                               const float* __restrict__ r, int nx, int ny, int nz, float h2,
-                              float omega) {
+                              float omega, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   const long long n = (long long)nx * ny * nz;
   const float cw = 1.0f - omega, cn = omega * (1.0f / 6.0f);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
@@ -617,7 +642,8 @@ __global__ void jacobi_kernel(const float* __restrict__ eo, float* __restrict__ 
 
 // The first Jacobi sweep of a level from e = 0: e_new = -(omega h^2 / 6) r.
 __global__ void jacobi_zero_kernel(float* __restrict__ en, const float* __restrict__ r,
-                                   long long n, float s) {
+                                   long long n, float s, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x)
     en[q] = s * r[q];
@@ -639,7 +665,8 @@ __global__ void __launch_bounds__(256)
 residual_zm_kernel(const float* __restrict__ phi, float* __restrict__ phi_out,
                    const float* __restrict__ e, const float* __restrict__ F,
                    float* __restrict__ r32, int nx, int ny, int nz, ff2 h2, float ih2,
-                   const double* fnorm2, double* partials) {
+                   const double* fnorm2, double* partials, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   __shared__ float s_hi[RZ_RING][RZ_H];
   __shared__ float s_lo[RZ_RING][RZ_H];
   __shared__ float s_e[UPDATE ? RZ_RING : 1][RZ_H];
@@ -752,7 +779,8 @@ residual_zm_kernel(const float* __restrict__ phi, float* __restrict__ phi_out,
 // sum_children h^2 (A e)_child = (sum of the 24 outside neighbours) - 3 (sum of the 8 children),
 // since every interior face cancels.  Rows of the fine grid are read as float2 pairs (x even).
 __global__ void resid_restrict_kernel(const float* __restrict__ e, const float* __restrict__ r,
-                                      float* __restrict__ rc, int cx, int cy, int cz, float ih2) {
+                                      float* __restrict__ rc, int cx, int cy, int cz, float ih2, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   const int nx = 2 * cx, ny = 2 * cy, nz = 2 * cz;
   const long long nc = (long long)cx * cy * cz;
   const long long plane = (long long)nx * ny;
@@ -796,7 +824,8 @@ __global__ void resid_restrict_kernel(const float* __restrict__ e, const float* 
 // cell: its 27-neighbourhood, combined axis by axis, gives its 8 children (stored as float2
 // pairs along x).
 __global__ void prolong_add_kernel(float* __restrict__ ef, const float* __restrict__ ec, int cx,
-                                   int cy, int cz) {
+                                   int cy, int cz, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   const int nx = 2 * cx, ny = 2 * cy;
   const long long nc = (long long)cx * cy * cz;
   const long long plane = (long long)nx * ny;
@@ -843,7 +872,8 @@ __global__ void prolong_add_kernel(float* __restrict__ ef, const float* __restri
 }
 
 __global__ void coarse_solve_kernel(const float* __restrict__ r, float* __restrict__ e,
-                                    const double* __restrict__ G, int n0, int n1, int n2) {
+                                    const double* __restrict__ G, int n0, int n1, int n2, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   const int N = n0 * n1 * n2;
   for (int p = threadIdx.x; p < N; p += blockDim.x) {
     const int p0 = p % n0, p1 = (p / n0) % n1, p2 = p / (n0 * n1);
@@ -898,7 +928,8 @@ __device__ __forceinline__ double apply_A_d(const double* __restrict__ e, int i,
 
 // one colour pass in place: cells with (i + j + k) % 2 == colour
 __global__ void rbgs_colour_d_kernel(double* __restrict__ e, const double* __restrict__ r, int nx,
-                                     int ny, int nz, double hh, int colour) {
+                                     int ny, int nz, double hh, int colour, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   const long long n = (long long)nx * ny * nz;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
@@ -911,7 +942,8 @@ __global__ void rbgs_colour_d_kernel(double* __restrict__ e, const double* __res
 
 __global__ void jacobi_d_kernel(const double* __restrict__ eo, double* __restrict__ en,
                                 const double* __restrict__ r, int nx, int ny, int nz, double hh,
-                                double omega) {
+                                double omega, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   const long long n = (long long)nx * ny * nz;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
@@ -923,7 +955,8 @@ __global__ void jacobi_d_kernel(const double* __restrict__ eo, double* __restric
 
 // rc = mean over the 8 children of (r - A e); coarse dims (cx, cy, cz)
 __global__ void resid_restrict_d_kernel(const double* __restrict__ e, const double* __restrict__ r,
-                                        double* __restrict__ rc, int cx, int cy, int cz, double hh) {
+                                        double* __restrict__ rc, int cx, int cy, int cz, double hh, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   const int nx = 2 * cx, ny = 2 * cy, nz = 2 * cz;
   const long long nc = (long long)cx * cy * cz;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
@@ -944,7 +977,8 @@ __global__ void resid_restrict_d_kernel(const double* __restrict__ e, const doub
 
 // ef += P ec, one thread per fine cell
 __global__ void prolong_add_d_kernel(double* __restrict__ ef, const double* __restrict__ ec,
-                                     int cx, int cy, int cz) {
+                                     int cx, int cy, int cz, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   const int nx = 2 * cx, ny = 2 * cy, nz = 2 * cz;
   const long long n = (long long)nx * ny * nz;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
@@ -968,7 +1002,8 @@ __global__ void prolong_add_d_kernel(double* __restrict__ ef, const double* __re
 }
 
 __global__ void coarse_solve_d_kernel(const double* __restrict__ r, double* __restrict__ e,
-                                      const double* __restrict__ G, int n0, int n1, int n2) {
+                                      const double* __restrict__ G, int n0, int n1, int n2, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   const int N = n0 * n1 * n2;
   for (int p = threadIdx.x; p < N; p += blockDim.x) {
     const int p0 = p % n0, p1 = (p / n0) % n1, p2 = p / (n0 * n1);
@@ -991,7 +1026,8 @@ __global__ void __launch_bounds__(RED_THREADS)
 residual_d_kernel(const float* __restrict__ phi, float* __restrict__ phi_out,
                   const double* __restrict__ e, const float* __restrict__ F,
                   double* __restrict__ r, int nx, int ny, int nz, ff2 h2, double ih2,
-                  const double* fnorm2, double* partials) {
+                  const double* fnorm2, double* partials, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
   __shared__ double red[RED_THREADS];
   const long long n = (long long)nx * ny * nz;
   const double sF = 1.0 / sqrt(*fnorm2 / (double)n);
@@ -1057,6 +1093,37 @@ __global__ void mark_fail_kernel(StepRecord* rec, unsigned flag) {
   }
 }
 
+// Judges the iterate whose residual finalize_kernel just reduced (scal[1] = |F|^2,
+// scal[2] = |r|^2 / |F|^2): stop at mg_tol, at a non-finite residual or after max_cycles
+// cycles, else count the cycle enqueued next.  rec (nullable): a step whose earlier kernels
+// failed fatally solves nothing.
+__global__ void mg_decide_kernel(MGCtl* ctl, const double* scal, double tol, int max_cycles,
+                                 const StepRecord* rec) {
+  if (threadIdx.x != 0 || ctl->stop) return;
+  if (rec && (rec->flags & FATAL_FLAGS)) {
+    ctl->skipped = 1;
+    ctl->stop = 1;
+    return;
+  }
+  if (!(scal[1] > 0.0)) {
+    ctl->zero = 1;
+    ctl->ok = 1;
+    ctl->rel = 0.0;
+    ctl->stop = 1;
+    return;
+  }
+  const double rel = sqrt(scal[2]);
+  ctl->rel = rel;
+  if (rel <= tol) {
+    ctl->ok = 1;
+    ctl->stop = 1;
+  } else if (!(rel == rel) || ctl->cycles >= max_cycles) {
+    ctl->stop = 1;
+  } else {
+    ctl->cycles += 1;
+  }
+}
+
 static int grid_for(long long n) {
   long long b = (n + 255) / 256;
   if (b > 148 * 16) b = 148 * 16;
@@ -1075,7 +1142,7 @@ static void cycle(dh_ctx* c, int l, bool zero_init) {
   const int nx = m->n[l][0], ny = m->n[l][1], nz = m->n[l][2];
   const float h2 = (float)(m->h[l] * m->h[l]);
   if (l == m->L - 1) {
-    coarse_solve_kernel<<<1, 256, 0, s>>>(m->r[l], m->e[l], m->G, nx, ny, nz);
+    coarse_solve_kernel<<<1, 256, 0, s>>>(m->r[l], m->e[l], m->G, nx, ny, nz, m->stop);
     c->launches += 1;
     return;
   }
@@ -1088,20 +1155,20 @@ static void cycle(dh_ctx* c, int l, bool zero_init) {
     if (g.mg_smoother == 1) {
       if (zero)
         jacobi_zero_kernel<<<grid_for(m->cells[l]), 256, 0, s>>>(m->e2[l], m->r[l], m->cells[l],
-                                                                 -omega * h2 * (1.0f / 6.0f));
+                                                                 -omega * h2 * (1.0f / 6.0f), m->stop);
       else if (vec)
-        jacobi4_kernel<<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2, omega);
+        jacobi4_kernel<<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2, omega, m->stop);
       else
         jacobi_kernel<<<grid_for(m->cells[l]), 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny,
-                                                            nz, h2, omega);
+                                                            nz, h2, omega, m->stop);
     } else if (vec && zero) {
-      rbgs_sweep4_kernel<true><<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
+      rbgs_sweep4_kernel<true><<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2, m->stop);
     } else if (vec) {
-      rbgs_sweep4_kernel<false><<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
+      rbgs_sweep4_kernel<false><<<sg4, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2, m->stop);
     } else if (zero) {
-      rbgs_sweep_kernel<true><<<sg, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
+      rbgs_sweep_kernel<true><<<sg, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2, m->stop);
     } else {
-      rbgs_sweep_kernel<false><<<sg, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2);
+      rbgs_sweep_kernel<false><<<sg, 256, 0, s>>>(m->e[l], m->e2[l], m->r[l], nx, ny, nz, h2, m->stop);
     }
     std::swap(m->e[l], m->e2[l]);
     c->launches += 1;
@@ -1109,10 +1176,11 @@ static void cycle(dh_ctx* c, int l, bool zero_init) {
   if (zero_init && g.mg_pre == 0) cudaMemsetAsync(m->e[l], 0, m->cells[l] * sizeof(float), s);
   for (int it = 0; it < g.mg_pre; ++it) smooth(zero_init && it == 0);
   resid_restrict_kernel<<<grid_for(m->cells[l + 1]), 256, 0, s>>>(
-      m->e[l], m->r[l], m->r[l + 1], nx / 2, ny / 2, nz / 2, 1.0f / h2);
+      m->e[l], m->r[l], m->r[l + 1], nx / 2, ny / 2, nz / 2, 1.0f / h2, m->stop);
   const int visits = (g.mg_cycle == 2 && l + 1 < m->L - 1) ? 2 : 1;
   for (int v = 0; v < visits; ++v) cycle(c, l + 1, v == 0);
-  prolong_add_kernel<<<grid_for(m->cells[l]), 256, 0, s>>>(m->e[l], m->e[l + 1], nx / 2, ny / 2, nz / 2);
+  prolong_add_kernel<<<grid_for(m->cells[l]), 256, 0, s>>>(m->e[l], m->e[l + 1], nx / 2, ny / 2, nz / 2,
+                                                           m->stop);
   for (int it = 0; it < g.mg_post; ++it) smooth(false);
   c->launches += 2;
 }
@@ -1128,28 +1196,28 @@ static void cycle_d(dh_ctx* c, int l, bool zero_init) {
   const double hh = m->h[l] * m->h[l];
   const int gb = grid_for(m->cells[l]);
   if (l == m->L - 1) {
-    coarse_solve_d_kernel<<<1, 256, 0, s>>>(m->dr[l], m->de[l], m->G, nx, ny, nz);
+    coarse_solve_d_kernel<<<1, 256, 0, s>>>(m->dr[l], m->de[l], m->G, nx, ny, nz, m->stop);
     c->launches += 1;
     return;
   }
   auto smooth = [&]() {
     if (g.mg_smoother == 1) {
-      jacobi_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->de2[l], m->dr[l], nx, ny, nz, hh, g.mg_omega);
+      jacobi_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->de2[l], m->dr[l], nx, ny, nz, hh, g.mg_omega, m->stop);
       std::swap(m->de[l], m->de2[l]);
       c->launches += 1;
     } else {
-      rbgs_colour_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->dr[l], nx, ny, nz, hh, 0);
-      rbgs_colour_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->dr[l], nx, ny, nz, hh, 1);
+      rbgs_colour_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->dr[l], nx, ny, nz, hh, 0, m->stop);
+      rbgs_colour_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->dr[l], nx, ny, nz, hh, 1, m->stop);
       c->launches += 2;
     }
   };
   if (zero_init) cudaMemsetAsync(m->de[l], 0, m->cells[l] * sizeof(double), s);
   for (int it = 0; it < g.mg_pre; ++it) smooth();
   resid_restrict_d_kernel<<<grid_for(m->cells[l + 1]), 256, 0, s>>>(m->de[l], m->dr[l], m->dr[l + 1],
-                                                                    nx / 2, ny / 2, nz / 2, hh);
+                                                                    nx / 2, ny / 2, nz / 2, hh, m->stop);
   const int visits = (g.mg_cycle == 2 && l + 1 < m->L - 1) ? 2 : 1;
   for (int v = 0; v < visits; ++v) cycle_d(c, l + 1, v == 0);
-  prolong_add_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->de[l + 1], nx / 2, ny / 2, nz / 2);
+  prolong_add_d_kernel<<<gb, 256, 0, s>>>(m->de[l], m->de[l + 1], nx / 2, ny / 2, nz / 2, m->stop);
   for (int it = 0; it < g.mg_post; ++it) smooth();
   c->launches += 2;
 }
@@ -1225,7 +1293,15 @@ static cudaError_t run_cycle(dh_ctx* c) {
 // a step leave the gauge open: only differences of phi enter the step, and dh_get_potential
 // removes the mean when it hands phi out (a constant is in A's null space, so the warm start and
 // the iterates are unaffected by it).
-static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
+//
+// The host does not read the residual after every cycle.  It enqueues a batch of items (a
+// cycle, the residual of the new iterate with the correction added, its reduction and
+// mg_decide_kernel), as many as the previous solve took cycles, then reads the control block
+// once; items after the decision to stop return at once.  A batch that ends before the
+// decision is followed by batches of 1, 2, 4, ... items.  The iterates and the cycle count are
+// those of a residual check after every cycle.  check_rec (nullable): the step record whose
+// fatal flags make the solve a no-op.
+static cudaError_t mg_iterate(dh_ctx* c, bool gauge, const StepRecord* check_rec) {
   MG* m = c->mg;
   const dh_config& g = c->cfg;
   cudaStream_t s = c->stream;
@@ -1234,58 +1310,71 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
   const double hh = m->h[0] * m->h[0];
   const ff2 h2 = ff_from_double(hh);
   const float ih2 = (float)(1.0 / hh);
-  int cycles = 0;
-  double rel = 0.0;
-  bool ok = false;
   const dim3 rg((nx + RZ_TX - 1) / RZ_TX, (ny + RZ_TY - 1) / RZ_TY, (nz + RZ_ZC - 1) / RZ_ZC);
   const int rblocks = (int)residual_zm_blocks(nx, ny, nz);
-  bool pending = false;   // a correction e[0] not yet added to phi
-  while (true) {
+  MGCtl* ctl = (MGCtl*)m->ctl;
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(MGCtl), s);
+  if (e != cudaSuccess) return e;
+  // one residual evaluation: of phi (first) or of phi + e[0] into phi2 (after a cycle), which
+  // then becomes phi
+  int swaps = 0;
+  auto evaluate = [&](bool add) {
     prof_begin(c, DH_KERNEL_MG);
     if (m->f64) {
-      if (pending)
+      if (add)
         residual_d_kernel<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(
             m->phi, m->phi2, m->de[0], m->F, m->dr[0], nx, ny, nz, h2, 1.0 / hh, m->scal + 1,
-            m->partials);
+            m->partials, m->stop);
       else
         residual_d_kernel<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(
             m->phi, nullptr, nullptr, m->F, m->dr[0], nx, ny, nz, h2, 1.0 / hh, m->scal + 1,
-            m->partials);
-      if (pending) std::swap(m->phi, m->phi2);
-    } else if (pending) {
-      // phi2 = phi + e and its residual in one pass, then phi2 becomes phi
+            m->partials, m->stop);
+    } else if (add) {
       residual_zm_kernel<true><<<rg, 256, 0, s>>>(m->phi, m->phi2, m->e[0], m->F, m->r[0], nx, ny,
-                                                  nz, h2, ih2, m->scal + 1, m->partials);
-      std::swap(m->phi, m->phi2);
+                                                  nz, h2, ih2, m->scal + 1, m->partials, m->stop);
     } else {
       residual_zm_kernel<false><<<rg, 256, 0, s>>>(m->phi, nullptr, nullptr, m->F, m->r[0], nx, ny,
-                                                   nz, h2, ih2, m->scal + 1, m->partials);
+                                                   nz, h2, ih2, m->scal + 1, m->partials, m->stop);
     }
-    pending = false;
+    if (add) {
+      std::swap(m->phi, m->phi2);
+      ++swaps;
+    }
     finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, m->f64 ? RED_BLOCKS : rblocks, m->scal + 2,
-                                              1.0 / (double)n);
+                                              1.0 / (double)n, m->stop);
+    mg_decide_kernel<<<1, 32, 0, s>>>(ctl, m->scal, g.mg_tol, g.mg_max_cycles, check_rec);
+    c->launches += 3;
     prof_end(c, 2);
-    double h[3];
-    cudaError_t e = cudaMemcpyAsync(h, m->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  };
+  const int max_items = g.mg_max_cycles + 1;   // residual evaluations of a solve at most
+  int items = m->last_cycles + 1;                // the previous solve's count
+  int enqueued = 0, next = 1;
+  MGCtl h;
+  while (true) {
+    if (items > max_items - enqueued) items = max_items - enqueued;
+    for (int i = 0; i < items; ++i, ++enqueued) {
+      if (enqueued > 0) {
+        prof_begin(c, DH_KERNEL_MG);
+        e = run_cycle(c);
+        prof_end(c, 0);
+        if (e != cudaSuccess) return e;
+      }
+      evaluate(enqueued > 0);
+    }
+    e = cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    if (!(h[1] > 0.0)) {  // zero source: phi = 0
-      e = cudaMemsetAsync(m->phi, 0, 2 * n * sizeof(float), s);
-      if (e != cudaSuccess) return e;
-      ok = true;
-      rel = 0.0;
-      break;
-    }
-    rel = std::sqrt(h[2]);   // scal[2] = |r|^2 / |F|^2
-    if (rel <= g.mg_tol) { ok = true; break; }
-    if (!(rel == rel)) break;                 // non-finite residual
-    if (cycles >= g.mg_max_cycles) break;
-    prof_begin(c, DH_KERNEL_MG);
-    e = run_cycle(c);
-    prof_end(c, 0);
+    if (h.stop || enqueued >= max_items) break;
+    items = next;
+    next *= 2;
+  }
+  // every cycle that ran was followed by the evaluation that added its correction; the swaps
+  // enqueued after the decision did not happen
+  if ((swaps - h.cycles) & 1) std::swap(m->phi, m->phi2);
+  if (h.skipped) return cudaGetLastError();
+  if (h.zero) {
+    e = cudaMemsetAsync(m->phi, 0, 2 * n * sizeof(float), s);
     if (e != cudaSuccess) return e;
-    pending = true;   // the next residual adds e[0]
-    ++cycles;
   }
   if (gauge) {
     prof_begin(c, DH_KERNEL_MG);
@@ -1294,9 +1383,9 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge) {
     sub_mean_ff_kernel<<<grid_for(n), 256, 0, s>>>(m->phi, n, m->scal + 3);
     prof_end(c, 3);
   }
-  m->last_cycles = cycles;
-  m->last_res = rel;
-  if (!ok) {
+  m->last_cycles = h.cycles;
+  m->last_res = h.rel;
+  if (!h.ok) {
     mark_fail_kernel<<<1, 32, 0, s>>>(c->rec, FLAG_MG_NOCONV);
     c->launches += 1;
   }
@@ -1310,14 +1399,6 @@ cudaError_t mg_solve(dh_ctx* c, const real* rho, bool in_step) {
   const dh_config& g = c->cfg;
   cudaStream_t s = c->stream;
   const long long n = m->cells[0];
-  if (in_step) {
-    // nothing to solve after a fatal failure earlier in this batch (the stages skipped)
-    unsigned fl = 0;
-    cudaError_t e = cudaMemcpyAsync(&fl, &c->rec->flags, sizeof(fl), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return e;
-    if (fl & FATAL_FLAGS) return cudaSuccess;
-  }
   prof_begin(c, DH_KERNEL_MG);
   sum_partial_kernel<real><<<RED_BLOCKS, RED_THREADS, 0, s>>>(rho, n, m->partials);
   finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 0, 1.0 / (double)n);
@@ -1325,7 +1406,8 @@ cudaError_t mg_solve(dh_ctx* c, const real* rho, bool in_step) {
                                                                  m->F, m->partials);
   finalize_kernel<<<1, FIN_THREADS, 0, s>>>(m->partials, RED_BLOCKS, m->scal + 1, 1.0);
   prof_end(c, 4);
-  return mg_iterate(c, false);
+  // in a step, nothing is solved after a fatal failure earlier in the batch (the stages skipped)
+  return mg_iterate(c, false, in_step ? c->rec : nullptr);
 }
 
 // A x = rhs - <rhs> for a float64 right-hand side; x (float-float, planar, n cells) is the warm
@@ -1347,7 +1429,7 @@ cudaError_t mg_solve_rhs(dh_ctx* c, const double* rhs, float* x) {
   float* keep = m->phi;
   float* keep2 = m->phi2;
   m->phi = x;
-  cudaError_t e = mg_iterate(c, true);
+  cudaError_t e = mg_iterate(c, true, nullptr);
   if (e == cudaSuccess && m->phi != x)
     e = cudaMemcpyAsync(x, m->phi, 2 * n * sizeof(float), cudaMemcpyDeviceToDevice, s);
   m->phi = keep;

@@ -154,11 +154,12 @@ class Solver:
 
     def metrics(self) -> dict:
         """The diagnostics record (dh_get_metrics): t, dt, nstep, flags, cool_max_substeps,
-        mg_cycles, mg_residual, totals, rho_min, p_min."""
+        slope_fallbacks, mg_cycles, mg_residual, totals, rho_min, p_min."""
         m = _lib.DhMetrics()
         self._check(self.lib.dh_get_metrics(self.ctx, C.byref(m)))
         return {"t": m.t, "dt": m.dt, "nstep": m.nstep, "flags": m.flags,
-                "cool_max_substeps": m.cool_max_substeps, "mg_cycles": m.mg_cycles,
+                "cool_max_substeps": m.cool_max_substeps, "slope_fallbacks": m.slope_fallbacks,
+                "mg_cycles": m.mg_cycles,
                 "mg_residual": m.mg_residual, "totals": list(m.totals), "rho_min": m.rho_min,
                 "p_min": m.p_min}
 

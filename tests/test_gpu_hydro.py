@@ -378,3 +378,37 @@ def test_metrics_record_cooling_cap_and_minima():
     assert m["mg_cycles"] == 0
     # the read reset the interval maximum: with no step since, cooling reports no subcycling
     assert s.metrics()["cool_max_substeps"] == 1
+    assert m["slope_fallbacks"] == 0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_metrics_count_slope_fallbacks(prec):
+    """The positivity fallback of the PLM slopes (App. A.2) is counted once per (cell, axis,
+    RK stage).  Density repeats (tiny, 1, 4) along x at rest under uniform pressure: the middle
+    cell's MC slope is 2 (the limit 2|b| with b = 1 - tiny, which rounds to 1), so its lower face
+    density 1 - 2/2 is exactly 0 and the fallback fires on the x axis; no other cell or axis
+    can fire (the slopes of the outer cells change sign, y and z are uniform).  A fixed time
+    step far below the rounding of the state leaves U1 = U^n, so both stages fire alike:
+    2 nz ny nx / 3 events per step.  x = 48 is not a multiple of the staging tile, so a partial
+    tile is covered as well."""
+    nz, ny, nx = 6, 10, 48
+    tiny = 1e-20 if prec == "f64" else 1e-9
+    U = np.zeros((5, nz, ny, nx))
+    U[0] = np.tile(np.array([tiny, 1.0, 4.0]), nx // 3)[None, None, :]
+    U[4] = 1.0 / (5.0 / 3.0 - 1.0)
+    s = solver((nz, ny, nx), prec)
+    s.init_state(to_gpu(U, prec))
+    s.step(1e-30)
+    m = s.metrics()
+    assert m["flags"] == 0
+    assert m["slope_fallbacks"] == 2 * nz * ny * nx // 3
+    s.step(1e-30)
+    s.step(1e-30)
+    assert s.metrics()["slope_fallbacks"] == 4 * nz * ny * nx // 3
+    assert s.metrics()["slope_fallbacks"] == 0
+    # a smooth state with positive neighbours never falls back
+    s2 = solver((8, 8, 32), prec)
+    s2.init_state(to_gpu(inputs.decaying_turbulence((8, 8, 32), seed=5, sigma=0.5, mach=0.5), prec))
+    for _ in range(3):
+        s2.step(0.0)
+    assert s2.metrics()["slope_fallbacks"] == 0
