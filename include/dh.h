@@ -382,6 +382,14 @@ dh_status dh_set_corrector(dh_ctx* ctx, const float* params, const float* norm15
    other form. */
 dh_status dh_set_corrector_form(dh_ctx* ctx, int form, const float* params, const float* norm15);
 dh_status dh_correct(dh_ctx* ctx);
+/* Sec. 7 (the corrector applied after each coarse step): with on = 1, every step that dh_step
+   and dh_advance enqueue applies the corrector in place after its sources, on the device and
+   without a host synchronisation (the same kernels and floors as dh_correct), and the next
+   step's CFL time step is that of the corrected state.  A non-finite corrected state fails the
+   step like a non-finite update: DH_ERR_NONFINITE, and the state holds the last good step.
+   DH_ERR_STATE for on = 1 without a corrector.  While it is on, dh_adjoint_advance and
+   dh_adjoint_advance_dt return DH_ERR_STATE (their adjoint covers the solver step only). */
+dh_status dh_set_correct_every_step(dh_ctx* ctx, int on);
 
 /* Conserved totals (as dh_conserved_totals) for callers that cannot allocate device memory,
    such as a host framework whose allocator owns the whole device-memory budget, or a

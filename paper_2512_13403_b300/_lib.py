@@ -99,6 +99,7 @@ _SIGNATURES = {
     "dh_set_corrector": (C.c_int, [_P, _P, C.POINTER(C.c_float)]),
     "dh_set_corrector_form": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_float)]),
     "dh_correct": (C.c_int, [_P]),
+    "dh_set_correct_every_step": (C.c_int, [_P, C.c_int]),
     "dh_profile_enable": (C.c_int, [_P, C.c_int]),
     "dh_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
     "dh_launch_count": (C.c_int, [_P, C.POINTER(C.c_longlong)]),

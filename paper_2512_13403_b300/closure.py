@@ -186,12 +186,12 @@ def equal_time_substeps(setup: ClosureSetup, params, norm, U0: torch.Tensor, pro
     plain.init_state(U0)
     corr.init_state(U0)
     _set_corrector(corr, params, norm)
-    lib = _lib.load()
+    corr.correct_every_step(True)
     tp = tc = 0.0
     for k in range(probes + 2):
         dt = plain.compute_dt()
         a = _timed(lambda: plain.step(dt, sync=False))
-        b = _timed(lambda: (corr.step(dt, sync=False), _lib.check(lib.dh_correct(corr.ctx), corr.ctx)))
+        b = _timed(lambda: corr.step(dt, sync=False))
         if k >= 2:            # the first steps warm up the kernels
             tp += a
             tc += b
@@ -214,7 +214,6 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
     maps such runs to (seed, coarse step).
     """
     n, nc = setup.fine, setup.coarse
-    lib = _lib.load()
     err = {"uncorrected": np.zeros(steps), "corrected": np.zeros(steps),
            "uncorrected_equal_gpu_time": np.zeros(steps)}
     gpu_ms = {k: 0.0 for k in err}
@@ -232,6 +231,7 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
             runs[name] = Solver(_cfg(nc, setup, seed))
             runs[name].init_state(U0)
         _set_corrector(runs["corrected"], params, norm, form)
+        runs["corrected"].correct_every_step(True)   # the step applies the corrector
         live = dict(runs)
         for k in range(steps):
             dt_c = runs["uncorrected"].compute_dt()
@@ -243,15 +243,12 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
                     def adv(s=s):
                         for _ in range(sub):
                             s.step(dt_c / sub, sync=False)
-                elif name == "corrected":
-                    def adv(s=s):
-                        s.step(dt_c, sync=False)
-                        _lib.check(lib.dh_correct(s.ctx), s.ctx)
                 else:
                     def adv(s=s):
                         s.step(dt_c, sync=False)
                 try:
                     gpu_ms[name] += _timed(adv)
+                    s.time()   # settles the enqueued steps: raises if one failed
                 except _lib.DhError:
                     # a non-finite state: the run stops and its error is infinite from here
                     diverged.setdefault(name, (seed, k))
@@ -280,20 +277,20 @@ def evaluate_coarsened(fine: Solver, coarse_cfg: Config, factor: int, params, no
     table), until it has taken `fine_steps` steps.  Returns per-interval relative L2 errors
     (mean over fields) against D(U_f), the GPU ms per coarse interval of each run, and the
     fine run's steps and GPU ms."""
-    lib = _lib.load()
     U0 = downsample(fine.get_state(), factor)
     runs = {k: Solver(coarse_cfg) for k in ("uncorrected", "corrected", "uncorrected_equal_gpu_time")}
     for s in runs.values():
         s.init_state(U0)
     _set_corrector(runs["corrected"], params, norm, form)
+    runs["corrected"].correct_every_step(True)
     # warm-up of the coarse kernels and the network on a scratch context (first launches load
     # modules and set attributes), so that the first interval's timings are representative
     scratch = Solver(coarse_cfg)
     scratch.init_state(U0)
     _set_corrector(scratch, params, norm, form)
+    scratch.correct_every_step(True)
     for _ in range(2):
         scratch.step(scratch.compute_dt())
-        _lib.check(lib.dh_correct(scratch.ctx), scratch.ctx)
     scratch.close()
     forcing = coarse_cfg.forcing
     err = {k: [] for k in runs}
@@ -312,11 +309,7 @@ def evaluate_coarsened(fine: Solver, coarse_cfg: Config, factor: int, params, no
         for name, s in runs.items():
             if modes is not None:
                 s.set_forcing_modes(modes, hold=True)
-            if name == "corrected":
-                def adv(s=s):
-                    s.step(dt_c, sync=False)
-                    _lib.check(lib.dh_correct(s.ctx), s.ctx)
-            elif name == "uncorrected_equal_gpu_time":
+            if name == "uncorrected_equal_gpu_time":
                 if sub is None:
                     sub = max(1, int(round(gpu_ms["corrected"] / max(gpu_ms["uncorrected"], 1e-9))))
                 def adv(s=s):

@@ -986,6 +986,10 @@ extern "C" dh_status dh_adjoint_advance_dt(dh_ctx* c, int n, int k, double dt,
   if (!c || !dLdU_final || !dLdU0) return DH_ERR_ARG;
   if (!(dt >= 0.0)) { c->err = "dt must be >= 0 (0: the CFL time step)"; return DH_ERR_ARG; }
   if (!c->initialized) { c->err = "state not initialised"; return DH_ERR_STATE; }
+  if (c->correct_each_step) {
+    c->err = "the adjoint covers the solver step only: turn the per-step corrector off";
+    return DH_ERR_STATE;
+  }
   if (n < 0 || k < 1) { c->err = "need n_steps >= 0 and ckpt_every >= 1"; return DH_ERR_ARG; }
   const cudaMemcpyKind h2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind d2h = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

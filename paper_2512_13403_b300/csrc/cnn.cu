@@ -284,10 +284,25 @@ static void bias_grad(const __nv_bfloat16* grad, int groups, int nch, const Conv
 // floor_per_mass * totals[0] when `totals` (the FP64 conserved totals of Uin, on the device) is
 // given.  A non-finite result sets bit 2 of *err.
 constexpr unsigned CNN_ERR_WAIT = 1u, CNN_ERR_NONFINITE = 2u;
+//
+// Inside a step (rec not null) the kernel writes nothing after a fatal failure earlier in the
+// batch or after a convolution's bounded wait gave up (which fails the step), and a non-finite
+// result fails the step instead of setting *err.
 __global__ void correct_kernel(const float* Uin, float* Uout, const float* __restrict__ y,
                                long long n, const float* __restrict__ norm, float rho_floor_c,
                                const double* __restrict__ totals, double floor_per_mass,
-                               float T_floor, float gm1, unsigned* err, int form, ConvGeom geo) {
+                               float T_floor, float gm1, unsigned* err, int form, ConvGeom geo,
+                               StepRecord* rec) {
+  if (rec) {
+    if (*(volatile unsigned*)&rec->flags & FATAL_FLAGS) return;
+    if (*(volatile unsigned*)err & CNN_ERR_WAIT) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicOr(&rec->flags, FLAG_TIMEOUT);
+        atomicCAS(&rec->fail_step, -1, (int)(rec->nstep - 1));
+      }
+      return;
+    }
+  }
   const float rho_floor = totals ? (float)(floor_per_mass * totals[0]) : rho_floor_c;
   bool finite = true;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
@@ -314,7 +329,14 @@ __global__ void correct_kernel(const float* Uin, float* Uout, const float* __res
     Uout[3 * n + q] = v[3];
     Uout[4 * n + q] = E;
   }
-  if (!__all_sync(0xffffffffu, finite) && (threadIdx.x & 31) == 0) atomicOr(err, CNN_ERR_NONFINITE);
+  if (!__all_sync(0xffffffffu, finite) && (threadIdx.x & 31) == 0) {
+    if (rec) {
+      atomicOr(&rec->flags, FLAG_NONFINITE);
+      atomicCAS(&rec->fail_step, -1, (int)(rec->nstep - 1));
+    } else {
+      atomicOr(err, CNN_ERR_NONFINITE);
+    }
+  }
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -679,9 +701,33 @@ static dh_status cnn_correct(dh_cnn* c, const float* Uin, float* Uout, double rh
                                                             (float)rho_floor, totals,
                                                             floor_per_mass, (float)T_floor,
                                                             (float)(gamma - 1.0), c->err, c->form,
-                                                            conv_geom(c->nx, c->ny, c->nz));
+                                                            conv_geom(c->nx, c->ny, c->nz), nullptr);
   CNN_TRY(cnn_cuda(c, cudaGetLastError(), "correct"));
   return check_err(c);
+}
+
+namespace dh {
+cudaError_t correct_in_step(dh_ctx* ctx, float* U) {
+  dh_cnn* c = ctx->cnn;
+  // rho floor: 1e-6 of the mean density of the uncorrected state (FP64 totals on the device)
+  cudaError_t e = launch_totals<float>(U, ctx->n3, ctx->partials, totals_blocks(), ctx->totals,
+                                       ctx->stream);
+  if (e != cudaSuccess) return e;
+  if (cnn_forward(c, U, nullptr, false) != DH_OK) return cudaErrorLaunchFailure;
+  correct_kernel<<<grid_for(c->ncell), 256, 0, c->stream>>>(
+      U, U, c->y, c->ncell, c->norm_dev, 0.0f, ctx->totals, 1e-6 / (double)ctx->n3,
+      (float)ctx->cfg.t_floor, (float)(ctx->cfg.gamma - 1.0), c->err, c->form,
+      conv_geom(c->nx, c->ny, c->nz), ctx->rec);
+  ctx->launches += 7;   // totals (2), normalise, three convolutions, correction
+  return cudaGetLastError();
+}
+}  // namespace dh
+
+extern "C" dh_status dh_set_correct_every_step(dh_ctx* ctx, int on) {
+  if (!ctx) return DH_ERR_ARG;
+  if (on && (!ctx->cnn || !ctx->cnn->have_params)) { ctx->err = "no corrector set"; return DH_ERR_STATE; }
+  ctx->correct_each_step = on != 0;
+  return DH_OK;
 }
 
 extern "C" dh_status dh_cnn_correct_state(dh_cnn* c, float* U, double rho_floor, double T_floor,

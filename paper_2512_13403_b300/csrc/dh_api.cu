@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dh.h"
@@ -222,6 +223,8 @@ static cudaError_t cfl_reduce_current(dh_ctx* c) {
   return e;
 }
 
+__global__ void set_u64_kernel(unsigned long long* p, unsigned long long v) { *p = v; }
+
 static cudaError_t reset_cfl_bits(dh_ctx* c) {
   const unsigned long long inf_bits =
       c->prec == DH_F32 ? (unsigned long long)0x7f800000u : 0x7ff0000000000000ull;
@@ -254,14 +257,18 @@ extern "C" dh_status dh_init_state(dh_ctx* c, const void* U, int on_device) {
   return DH_OK;
 }
 
+static dh_status finish_steps(dh_ctx* c, long long nstep_before);
+
 extern "C" dh_status dh_get_state(dh_ctx* c, void* U, int on_device) {
   if (!c || !U) return fail(c, DH_ERR_ARG, "null argument");
   if (!c->initialized) return fail(c, DH_ERR_STATE, "state not initialised");
+  // settle enqueued steps first: after a failed one the current state is the last good step
+  const dh_status st = c->pending_steps > 0 ? finish_steps(c, c->host_rec.nstep - c->pending_steps) : DH_OK;
   DH_CUDA(c, cudaMemcpyAsync(U, c->U[c->cur], c->state_bytes,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              c->stream));
   DH_CUDA(c, cudaStreamSynchronize(c->stream));
-  return DH_OK;
+  return st;
 }
 
 template <typename real>
@@ -329,9 +336,11 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed, const StepCapture* c
 
   a.U = Ulast; a.U0 = Un; a.out = Unew;
   const bool fuse = !g.gravity;
+  // with the corrector in the step, the next step's CFL minimum is the corrected state's
+  const bool correct = c->correct_each_step && std::is_same<real, float>::value;
   a.forcing = fuse ? g.forcing : 0;
   a.cooling = fuse ? g.cooling : 0;
-  a.reduce_cfl = fuse ? 1 : 0;
+  a.reduce_cfl = fuse && !correct ? 1 : 0;
   a.pre_src = fuse && cap ? (real*)cap->pre_src : nullptr;
   prof_begin(c, DH_KERNEL_STAGE2);
   e = launch_stage<real>(rk3 ? 3 : 2, a, c->stream);
@@ -339,6 +348,21 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed, const StepCapture* c
   if (e != cudaSuccess) return e;
   if (!fuse) {
     e = gravity_sources<real>(c, Unew, nullptr, &c->rec->dt, true);
+    if (e != cudaSuccess) return e;
+  }
+  if (correct) {
+    // Sec. 7: the corrector after the coarse step, in place on the new state, then the CFL
+    // minimum of the corrected state (the sources' reduction, if any, is discarded)
+    prof_begin(c, DH_KERNEL_CONV);
+    e = correct_in_step(c, (float*)Unew);
+    prof_end(c, 0);
+    if (e != cudaSuccess) return e;
+    set_u64_kernel<<<1, 1, 0, c->stream>>>(&c->rec->cfl_min_bits, (unsigned long long)0x7f800000u);
+    prof_begin(c, DH_KERNEL_REDUCE);
+    e = launch_cfl_reduce<real>((const real*)Unew, g.nx, g.ny, g.nz, (real)g.gamma, (real)g.dx,
+                                (real)g.dy, (real)g.dz, cool_ratio<real>(g), (real)g.t_floor,
+                                c->rec, c->stream);
+    prof_end(c, 2);
     if (e != cudaSuccess) return e;
   }
   c->cur = 1 - c->cur;

@@ -42,9 +42,14 @@ struct dh_ctx {
   struct AdjointSpace* adj = nullptr;
   // corrector network (dh_set_corrector)
   struct dh_cnn* cnn = nullptr;
+  bool correct_each_step = false;    // dh_set_correct_every_step: the step applies the corrector
 };
 
 namespace dh {
+// cnn.cu: enqueues the corrector on U (float32, in place) inside a step: no synchronisation;
+// after a fatal flag it changes nothing, and a non-finite result fails the step
+cudaError_t correct_in_step(dh_ctx* c, float* U);
+
 void prof_begin(dh_ctx* c, int kind);
 void prof_end(dh_ctx* c, int launches);
 void prof_fold(dh_ctx* c);

@@ -245,6 +245,14 @@ class Solver:
         """Restore a checkpoint written by a context of the same configuration."""
         self._check(self.lib.dh_load(self.ctx, str(path).encode()))
 
+    def correct(self):
+        """Applies the corrector set on this context to the current state (dh_correct)."""
+        self._check(self.lib.dh_correct(self.ctx))
+
+    def correct_every_step(self, on: bool):
+        """Every later step applies the corrector on the device (dh_set_correct_every_step)."""
+        self._check(self.lib.dh_set_correct_every_step(self.ctx, int(on)))
+
     def profile(self, enable: bool):
         self._check(self.lib.dh_profile_enable(self.ctx, int(enable)))
 

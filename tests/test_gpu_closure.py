@@ -127,3 +127,63 @@ def test_evaluate_coarsened_self_gravitating():
     assert res["equal_time_substeps"] >= 1
     assert all(np.isfinite(res["errors"]["uncorrected_equal_gpu_time"]))
     fine.close()
+
+
+def _closure_solver(shape, params, norm, **kw):
+    s = solver(shape, "f32", forcing=True, ou_seed=7, cooling=True, t_floor=0.05, **kw)
+    closure._set_corrector(s, params, norm)
+    return s
+
+
+@pytest.mark.parametrize("gravity", [False, True])
+def test_correct_every_step_matches_step_then_correct(gravity):
+    """The corrector inside the step (dh_set_correct_every_step) runs the kernels of a step
+    followed by dh_correct, on the device without a host synchronisation: the states, the time
+    steps and the CFL step after each corrected step are bit for bit those of the explicit
+    sequence."""
+    shape = (16, 16, 16) if gravity else (16, 16, 32)   # gravity needs cubic cells
+    U0 = to_gpu(inputs.decaying_turbulence(shape, seed=4, sigma=0.5, mach=0.8, p_sigma=0.2), "f32")
+    params = init_params(2, out_scale=1.0)
+    norm = ([1.0, 0.0, 0.0, 0.0, 1.5], [0.3, 0.5, 0.5, 0.5, 0.5], [2e-3] * 5)
+    kw = dict(gravity=True, mg_tol=1e-6, mg_max_cycles=30) if gravity else {}
+    a = _closure_solver(shape, params, norm, **kw)
+    b = _closure_solver(shape, params, norm, **kw)
+    a.init_state(U0)
+    b.init_state(U0)
+    b.correct_every_step(True)
+    for _ in range(4):
+        a.step(0.0)
+        a.correct()
+    b.advance(4)
+    assert a.time() == b.time()
+    assert torch.equal(a.get_state().cpu(), b.get_state().cpu())
+    assert a.compute_dt() == b.compute_dt()
+    # the correction did something
+    c = solver(shape, "f32", forcing=True, ou_seed=7, cooling=True, t_floor=0.05, **kw)
+    c.init_state(U0)
+    c.advance(4)
+    assert not torch.equal(c.get_state().cpu(), b.get_state().cpu())
+
+
+def test_non_finite_correction_in_step_fails_the_step():
+    """A corrected state that is not finite fails its step (DH_ERR_NONFINITE): the state, time
+    and step count stay at the last good step, and the context keeps working once the per-step
+    corrector is off.  The adjoint refuses to run while it is on."""
+    from paper_2512_13403_b300 import _lib
+    shape = (8, 16, 16)
+    U0 = to_gpu(inputs.decaying_turbulence(shape, seed=3, sigma=0.5, mach=1.0, p_sigma=0.2), "f32")
+    p = torch.zeros(NPARAM, dtype=torch.float32)
+    p[-5:] = 3.0e38            # output bias b3: s * y overflows to infinity
+    s = _closure_solver(shape, p, ([0.0] * 5, [1.0] * 5, [10.0] * 5))
+    s.init_state(U0)
+    s.advance(1)
+    before, (t0, n0) = s.get_state().clone(), s.time()
+    s.correct_every_step(True)
+    with pytest.raises(_lib.DhError):
+        s.advance(3)
+    assert torch.equal(s.get_state(), before) and s.time() == (t0, n0)
+    with pytest.raises(_lib.DhError):
+        s.adjoint_advance(1, 1, torch.zeros_like(before))
+    s.correct_every_step(False)
+    s.advance(1)
+    assert s.time()[1] == n0 + 1
