@@ -295,7 +295,7 @@ dh_status dh_conv3d_wgrad_bf16(const void* act, int cin_pad, int cin, const void
                                int grad_stride, int cout, int nx, int ny, int nz, float* partial,
                                int nctas, float* dW, unsigned* err_flag, void* stream);
 
-/* The corrector network (Sec. 7 closure, BASELINE's 3D CNN): x0 = bf16((U - mu)/sigma),
+/* The corrector network (Sec. 7 closure, a residual 3D CNN): x0 = bf16((U - mu)/sigma),
    z1 = conv(x0, W1) + b1, h1 = bf16(gelu(z1)), z2 = conv(h1, W2) + b2, h2 = bf16(gelu(z2)),
    y = conv(h2, W3) + b3, all 3x3x3 periodic, channels 5 -> 32 -> 32 -> 5.  Parameters are one
    flat fp32 device array of dh_cnn_param_count() = 36357 values: W1[32][5][27], b1[32],
