@@ -39,12 +39,15 @@ ADJ_BYTES_STAGE = 70    # float32 per adjoint stage launch, average of stage-2^T
 # the kernel sources they were taken on (source_hash below).  A run whose sources hash
 # differently reports null for these fields: the counters describe another kernel.
 NCU_COUNTERS = {
-    "stage2": {"sources": ["hydro.cu", "dh_device.cuh", "dh_sources.cuh", "async_copy.cuh"],
-               "hash": None, "dram_bytes": None, "warp_instr": None,
+    # one launch at 256^3: ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    # smsp__inst_executed.sum (the profile named here gives the command)
+    "stage2": {"sources": ['hydro.cu', 'dh_device.cuh', 'dh_sources.cuh', 'async_copy.cuh', 'tma.cuh', 'tc_ptx.cuh'],
+               "hash": "6f2dac0f7e7f527d", "dram_bytes": 1009837056, "warp_instr": 669825792,
                "profile": "profiles/stage_kernels_driven_cooling_turbulence_256cubed.md"},
     # averaged over the kernel's two launches per RK2 step
-    "adjoint": {"sources": ["adjoint.cu", "dh_adjoint.cuh", "dh_device.cuh", "async_copy.cuh"],
-                "hash": None, "dram_bytes": None, "warp_instr": None,
+    "adjoint": {"sources": ['adjoint.cu', 'dh_adjoint.cuh', 'dh_device.cuh', 'dh_sources.cuh', 'async_copy.cuh', 'tma.cuh', 'tc_ptx.cuh'],
+                "hash": "1e509db2fd19c89e", "dram_bytes": 1201327872,
+                "warp_instr": 1418086510,
                 "profile": "profiles/stage_adjoint_kernel_decaying_turbulence_128cubed.md"},
 }
 
