@@ -118,6 +118,7 @@ extern "C" dh_status dh_create(const dh_config* cfg, void* stream, dh_ctx** out)
   if (e == cudaSuccess) e = alloc((void**)&c->ahat, 96 * sizeof(double));
   if (e == cudaSuccess) e = alloc((void**)&c->ahat_prev, 96 * sizeof(double));
   if (e == cudaSuccess) e = alloc(&c->ahat_norm, 96 * esize(c));
+  if (e == cudaSuccess && cfg->forcing) e = alloc((void**)&c->ou_draws, OU_DRAW_BATCH * 96 * sizeof(double));
   if (e == cudaSuccess) e = alloc((void**)&c->partials, (size_t)totals_blocks() * 5 * sizeof(double));
   if (e == cudaSuccess) e = alloc((void**)&c->totals, 5 * sizeof(double));
   const int n[3] = {cfg->nx, cfg->ny, cfg->nz};
@@ -158,6 +159,7 @@ extern "C" void dh_destroy(dh_ctx* c) {
   cudaFree(c->rec);
   cudaFree(c->ahat);
   cudaFree(c->ahat_prev);
+  cudaFree(c->ou_draws);
   cudaFree(c->ahat_norm);
   cudaFree(c->partials);
   cudaFree(c->totals);
@@ -303,8 +305,28 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed, const StepCapture* c
   b.forcing = g.forcing; b.ahat = c->ahat; b.ahat_prev = c->ahat_prev; b.ahat_norm = c->ahat_norm;
   b.seed = g.ou_seed; b.tau = g.ou_tau; b.arms = g.ou_arms;
   b.hold = c->ou_hold;
+  b.draws = nullptr;
+  b.draw_first = 0;
+  b.draw_count = 0;
+  cudaError_t e = cudaSuccess;
+  if (g.forcing && !c->ou_hold && c->ou_draws) {
+    // the draw this step takes if every enqueued step succeeds (otherwise the kernel sees a
+    // different step count and draws itself); refill the table when it is not covered
+    const long long d = c->host_rec.nstep + c->pending_steps + 1;
+    if (c->ou_draw_count == 0 || d < c->ou_draw_first || d >= c->ou_draw_first + c->ou_draw_count) {
+      prof_begin(c, DH_KERNEL_PROLOGUE);
+      e = launch_ou_draws(g.ou_seed, d, OU_DRAW_BATCH, c->ou_draws, c->stream);
+      prof_end(c, 1);
+      if (e != cudaSuccess) return e;
+      c->ou_draw_first = d;
+      c->ou_draw_count = OU_DRAW_BATCH;
+    }
+    b.draws = c->ou_draws;
+    b.draw_first = c->ou_draw_first;
+    b.draw_count = c->ou_draw_count;
+  }
   prof_begin(c, DH_KERNEL_PROLOGUE);
-  cudaError_t e = launch_step_begin(b, c->stream);
+  e = launch_step_begin(b, c->stream);
   prof_end(c, 1);
   if (e != cudaSuccess) return e;
 

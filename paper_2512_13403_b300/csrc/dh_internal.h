@@ -25,6 +25,9 @@ struct dh_ctx {
   void* ahat_norm = nullptr;         // normalised table in the working precision
   void* tw[3] = {nullptr, nullptr, nullptr};  // per-axis forcing twiddles
   int ou_hold = 0;                   // 1: steps keep the forcing table as set (no OU update)
+  double* ou_draws = nullptr;        // projected draws of steps [ou_draw_first, + ou_draw_count)
+  long long ou_draw_first = 0;
+  int ou_draw_count = 0;
   double* partials = nullptr;        // totals: per-block partial sums
   double* totals = nullptr;          // totals: 5 doubles
   bool initialized = false;

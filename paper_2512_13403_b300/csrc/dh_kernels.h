@@ -49,8 +49,17 @@ struct BeginArgs {
   unsigned long long seed;
   double tau, arms;
   int hold;                 // keep the table (no draw, no update), only renormalise it
+  // projected draws made ahead (launch_ou_draws) for steps [draw_first, draw_first +
+  // draw_count): 96 doubles per step; a step outside the range draws in the kernel
+  const double* draws;
+  long long draw_first;
+  int draw_count;
 };
 cudaError_t launch_step_begin(const BeginArgs& a, cudaStream_t s);
+// The projected OU draws of steps first .. first + count - 1 (one CTA per step) into out.
+constexpr int OU_DRAW_BATCH = 128;
+cudaError_t launch_ou_draws(unsigned long long seed, long long first, int count, double* out,
+                            cudaStream_t s);
 cudaError_t launch_forcing_init(double* ahat, unsigned long long seed, cudaStream_t s);
 
 template <typename real>

@@ -756,6 +756,28 @@ cudaError_t launch_forcing_init(double* ahat, unsigned long long seed, cudaStrea
   return cudaGetLastError();
 }
 
+// The draws of a run of steps ahead of time: the float64 Box-Muller transform of one step is a
+// latency chain on one warp, so computing many steps' draws side by side takes it off the
+// steps' critical path.  Block b holds draw first + b; the values are those projected_draw
+// gives inside step_begin_kernel.
+__global__ void ou_draws_kernel(unsigned long long seed, long long first, double* out) {
+  __shared__ double sre[48], sim[48];
+  const int lane = threadIdx.x;
+  double ere, eim;
+  projected_draw(seed, first + blockIdx.x, lane, sre, sim, ere, eim);
+  if (lane < 48) {
+    out[96LL * blockIdx.x + 2 * lane] = ere;
+    out[96LL * blockIdx.x + 2 * lane + 1] = eim;
+  }
+}
+
+cudaError_t launch_ou_draws(unsigned long long seed, long long first, int count, double* out,
+                            cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  ou_draws_kernel<<<count, 64, 0, s>>>(seed, first, out);
+  return cudaGetLastError();
+}
+
 template <typename real>
 __device__ void store_norm(void* out, int i, double v) {
   reinterpret_cast<real*>(out)[i] = (real)v;
@@ -786,7 +808,17 @@ __global__ void step_begin_kernel(BeginArgs a) {
   const double dt = s_dt;
   if (a.forcing) {
     double ere = 0.0, eim = 0.0;
-    if (!a.hold) projected_draw(a.seed, rec->nstep + 1, lane, sre, sim, ere, eim);
+    if (!a.hold) {
+      const long long d = rec->nstep + 1;   // block-uniform: either branch is taken by all
+      if (a.draws && d >= a.draw_first && d < a.draw_first + a.draw_count) {
+        if (lane < 48) {
+          ere = a.draws[96 * (d - a.draw_first) + 2 * lane];
+          eim = a.draws[96 * (d - a.draw_first) + 2 * lane + 1];
+        }
+      } else {
+        projected_draw(a.seed, d, lane, sre, sim, ere, eim);
+      }
+    }
     const double f = a.hold ? 1.0 : exp(-dt / a.tau);
     const double g = a.hold ? 0.0 : sqrt(1.0 - f * f);
     double nre = 0.0, nim = 0.0;

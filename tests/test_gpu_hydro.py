@@ -122,6 +122,42 @@ def test_smooth_flow_50_steps_fp32_every_field():
     assert max(e) <= 1e-5, e
 
 
+def test_ou_table_over_many_steps_and_a_rollback():
+    """The OU draws of many steps are made ahead of the steps in batches of 128; the mode table
+    after 300 fixed-dt steps (three batches, plus a reload that rewinds the step count) is the
+    oracle's OU recurrence to rounding."""
+    from paper_2512_13403_b300 import _lib
+    shape = (8, 8, 8)
+    U0 = inputs.decaying_turbulence(shape, seed=2, sigma=0.3, mach=0.2, P0=1.0)
+    s = solver(shape, "f64", forcing=True, ou_tau=0.5, ou_arms=0.1, ou_seed=5)
+    s.init_state(to_gpu(U0, "f64"))
+    ou = oforce.OUForcing(5, 0.5, 0.1)
+    dt = 1e-3
+    for n in range(1, 301):
+        s.step(dt, sync=False)
+        ou.update(dt, n - 1)   # step n (1-based) takes draw n
+        if n == 150:
+            assert np.abs(s.forcing_modes() - ou.a_hat.numpy()).max() < 1e-12
+    assert np.abs(s.forcing_modes() - ou.a_hat.numpy()).max() < 1e-12
+    # a step count rewound by a reload: the next steps draw from the right place again
+    import os, tempfile
+    path = os.path.join(tempfile.mkdtemp(), "ck.bin")
+    s2 = solver(shape, "f64", forcing=True, ou_tau=0.5, ou_arms=0.1, ou_seed=5)
+    s2.init_state(to_gpu(U0, "f64"))
+    ou2 = oforce.OUForcing(5, 0.5, 0.1)
+    for n in range(1, 11):
+        s2.step(dt)
+        ou2.update(dt, n - 1)
+    s2.save(path)
+    for n in range(11, 141):
+        s2.step(dt, sync=False)
+    s2.load(path)
+    for n in range(11, 21):
+        s2.step(dt)
+        ou2.update(dt, n - 1)
+    assert np.abs(s2.forcing_modes() - ou2.a_hat.numpy()).max() < 1e-12
+
+
 def test_forcing_and_cooling_fp64():
     shape = (16, 20, 24)
     U0 = inputs.decaying_turbulence(shape, seed=9, sigma=0.5, mach=0.7, P0=0.6)
