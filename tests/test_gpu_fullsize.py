@@ -11,6 +11,10 @@ outputs the oracle computes one by one, or through properties that hold at any s
   computed by the oracle's operator at sampled cells from the GPU potential, against rms(F).
 - Corrector network at 64^3: the network at sampled cells against the oracle network on a
   13^3 block (three 3x3x3 layers reach 3 cells).
+- Self-gravitating step at 1024^3 (lognormal sigma = 1, forcing, cooling, multigrid gravity to
+  1e-6): one GPU step against the oracle's step of a 13^3 block around each sampled cell, with
+  the potential the GPU solved for (the kick needs it only at the cell's six neighbours; the
+  solve itself is checked by the multigrid test).
 """
 import math
 
@@ -158,3 +162,47 @@ def test_conserved_totals_256_float32():
         ref = float(Uh[f].sum())
         scale = float(np.abs(Uh[f]).sum())
         assert abs(tot[f] - ref) <= 1e-12 * scale, (f, tot[f], ref)
+
+
+def test_self_gravitating_step_1024_sampled_cells_vs_oracle():
+    from oracle import multigrid as omg
+    n = 1024
+    shape = (n, n, n)
+    h = 1.0 / n
+    dx = (h, h, h)
+    s = solver(shape, "f32", forcing=True, ou_seed=3, cooling=True, t_floor=0.05, gravity=True,
+               four_pi_G=1.0, mg_tol=1e-6, mg_max_cycles=30)
+    U0 = inputs.self_gravitating_box_device(shape, seed=5, sigma=1.0)
+    s.init_state(U0)
+    del U0
+    s.advance(2)                                  # a moving state, and a warm-started solve
+    Ub = s.get_state()                            # float32, on the device
+    ou = oforce.OUForcing(seed=4, tau=0.5, a_rms=1.0)
+    s.set_forcing_modes(ou.a_hat.numpy(), hold=True)   # the same table on both sides
+    dt = s.compute_dt()
+    s.step(dt)
+    out = s.get_state()
+    phi, cycles, res = s.potential()              # the solve of this step (float64, <phi> = 0)
+    assert res <= 1e-6
+    g = torch.Generator().manual_seed(9)
+    samples = torch.randint(0, n, (48, 3), generator=g).tolist() + [[0, 0, 0], [n - 1, n - 1, n - 1]]
+    r = 6
+    scale = torch.stack([Ub[c].abs().max() for c in range(5)]).double().cpu()
+    scale[1:4] = scale[1:4].max()
+    worst = 0.0
+    for k, j, i in samples:
+        ks = (torch.arange(k - r, k + r + 1) % n).cuda()
+        js = (torch.arange(j - r, j + r + 1) % n).cuda()
+        is_ = (torch.arange(i - r, i + r + 1) % n).cuda()
+        B = Ub[:, ks][:, :, js][:, :, :, is_].double().cpu()
+        P = phi[ks][:, js][:, :, is_].cpu()
+        kk, jj, ii = torch.meshgrid(ks.cpu(), js.cpu(), is_.cpu(), indexing="ij")
+        V = ohydro.rk2_step(B, dt, G, dx)
+        V = oforce.apply_forcing(V, ou.field_at(shape, kk, jj, ii), dt)
+        V = omg.gravity_source(V, P, dt, h)
+        V, _ = ocool.cool(V, dt, G, 0.05, 0.1, 1024)
+        ref = V[:, r, r, r]
+        got = out[:, k, j, i].double().cpu()
+        worst = max(worst, float(((got - ref).abs() / scale).max()))
+    assert worst < 4e-6, worst
+    s.close()
