@@ -522,6 +522,23 @@ def selfgrav_leg(args, stream):
     shape = (n, n, n)
     cfg = Config(shape=shape, precision="f32", forcing=True, cooling=True, t_floor=0.05,
                  gravity=True, four_pi_G=1.0, mg_tol=1e-6, mg_max_cycles=30)
+    sg_trained = None
+    if not args.no_corrector and n % 4 == 0 and n // 4 >= 16:
+        # a corrector for this physics: solver-made pairs of self-gravitating runs at n/4 (fine)
+        # -> n/16 (coarse), trained like the driven-cooling one (before the big context exists)
+        from paper_2512_13403_b300 import closure
+        gsetup = closure.ClosureSetup(fine=n // 4, factor=4, runs=args.sg_corr_runs,
+                                      snapshots=args.sg_corr_snapshots,
+                                      spinup_steps=args.sg_corr_spinup, seed0=500,
+                                      gravity=True, sigma=1.0)
+        tg0 = time.time()
+        Xg, Yg = closure.make_pairs(gsetup)
+        pg, ng, lg = closure.train(Xg, Yg, epochs=args.corr_epochs)
+        del Xg, Yg
+        torch.cuda.empty_cache()
+        sg_trained = (pg, ng, {"pairs": gsetup.runs * gsetup.snapshots, "epochs": args.corr_epochs,
+                               "train_loss": lg, "seconds": time.time() - tg0,
+                               "fine": n // 4, "spinup_steps": gsetup.spinup_steps})
     with torch.cuda.stream(stream):
         s = Solver(cfg, stream=stream)
         U0 = inputs.self_gravitating_box_device(shape, seed=5, sigma=1.0)
@@ -548,17 +565,26 @@ def selfgrav_leg(args, stream):
         nsrc, tsrc = s.profile_read("sources")
         s.profile(False)
         corr = None
+        corr_dc = None
+        from paper_2512_13403_b300 import closure
+        ccfg = Config(shape=(n // 4,) * 3, precision="f32", forcing=True, cooling=True, t_floor=0.05,
+                      gravity=True, four_pi_G=1.0, mg_tol=1e-6, mg_max_cycles=30)
+        if sg_trained is not None:
+            # the corrector trained on self-gravitating n/4 -> n/16 pairs, applied at 4x
+            # coarsening of this run: n -> n/4 with the same physics
+            corr = closure.evaluate_coarsened(s, ccfg, 4, sg_trained[0], sg_trained[1],
+                                              fine_steps=args.sg_steps)
+            corr["training"] = sg_trained[2]
+            corr["note"] = (f"corrector trained on self-gravitating {n // 4}^3 -> {n // 16}^3 pairs "
+                            "(same physics), applied at 4x coarsening: relative L2 (mean over fields) "
+                            f"of the {n // 4}^3 runs against the 4^3 block mean of the {n}^3 run after "
+                            "each coarse interval")
         trained = getattr(args, "_corrector", None)
         if trained is not None:
-            # the corrector trained on the 256^3 -> 64^3 pairs, applied at 4x coarsening of this
-            # run: 1024^3 -> 256^3 with the same physics
-            from paper_2512_13403_b300 import closure
-            ccfg = Config(shape=(n // 4,) * 3, precision="f32", forcing=True, cooling=True, t_floor=0.05,
-                          gravity=True, four_pi_G=1.0, mg_tol=1e-6, mg_max_cycles=30)
-            corr = closure.evaluate_coarsened(s, ccfg, 4, trained[0], trained[1], fine_steps=args.sg_steps)
-            corr["note"] = ("corrector trained on the driven-cooling 256^3 -> 64^3 pairs (no gravity), "
-                            "applied at 4x coarsening: relative L2 (mean over fields) of the 256^3 runs "
-                            "against the 4^3 block mean of the 1024^3 run after each coarse interval")
+            # the driven-cooling corrector (no gravity in its training data) on the same task
+            corr_dc = closure.evaluate_coarsened(s, ccfg, 4, trained[0], trained[1], fine_steps=args.sg_steps)
+            corr_dc["note"] = ("corrector trained on the driven-cooling 256^3 -> 64^3 pairs (no gravity), "
+                               "applied the same way (from the fine state after the first evaluation)")
         s.close()
     steps = args.sg_steps
     out = {"value": n ** 3 * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
@@ -572,6 +598,8 @@ def selfgrav_leg(args, stream):
                         "V-cycles to 1e-6 with FP64 norms; OU forcing + cooling)"}
     if corr is not None:
         out["corrector"] = corr
+    if corr_dc is not None:
+        out["corrector_driven_cooling_trained"] = corr_dc
     return out
 
 
@@ -867,6 +895,9 @@ def main():
                     help="skip the cold-start Poisson solves per smoother and cycle")
     ap.add_argument("--pv-grid", type=int, default=512)
     ap.add_argument("--sg-steps", type=int, default=20)
+    ap.add_argument("--sg-corr-runs", type=int, default=8)
+    ap.add_argument("--sg-corr-snapshots", type=int, default=100)
+    ap.add_argument("--sg-corr-spinup", type=int, default=40)
     ap.add_argument("--corr-runs", type=int, default=20)
     ap.add_argument("--corr-snapshots", type=int, default=100)
     ap.add_argument("--corr-epochs", type=int, default=4)

@@ -38,6 +38,10 @@ class ClosureSetup:
     forcing: bool = True
     cooling: bool = True
     t_floor: float = 0.05
+    # self-gravitating variant (Sec. 5.2): multigrid gravity, lognormal initial density of
+    # this sigma (seeded per run), fluid at rest
+    gravity: bool = False
+    sigma: float = 1.0
 
     @property
     def coarse(self) -> int:
@@ -45,8 +49,17 @@ class ClosureSetup:
 
 
 def _cfg(n, setup: ClosureSetup, seed):
+    grav = dict(gravity=True, four_pi_G=1.0, mg_tol=1e-6, mg_max_cycles=30) if setup.gravity else {}
     return Config(shape=(n, n, n), precision="f32", forcing=setup.forcing, ou_seed=seed,
-                  cooling=setup.cooling, t_floor=setup.t_floor)
+                  cooling=setup.cooling, t_floor=setup.t_floor, **grav)
+
+
+def _initial_state(setup: ClosureSetup, n: int, seed: int) -> torch.Tensor:
+    """The fine run's start: the driven cooling box (rho = 1, P = 0.6, at rest), or for the
+    self-gravitating variant a lognormal density of the run's seed."""
+    if setup.gravity:
+        return inputs.self_gravitating_box_device((n, n, n), seed=seed, sigma=setup.sigma)
+    return torch.from_numpy(inputs.cooling_box((n, n, n))).float().cuda().contiguous()
 
 
 def downsample(Uf: torch.Tensor, factor: int) -> torch.Tensor:
@@ -93,7 +106,7 @@ def make_pairs(setup: ClosureSetup, log=None):
     k = 0
     for r in range(setup.runs):
         fine = Solver(_cfg(n, setup, setup.seed0 + r))
-        fine.init_state(torch.from_numpy(inputs.cooling_box((n, n, n))).float().cuda().contiguous())
+        fine.init_state(_initial_state(setup, n, setup.seed0 + r))
         fine.advance(setup.spinup_steps)
         for s in range(setup.snapshots):
             Uc0 = downsample(fine.get_state(), setup.factor)
@@ -221,7 +234,7 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
     sub = equal_time_substeps_n
     for seed in seeds:
         fine = Solver(_cfg(n, setup, seed))
-        fine.init_state(torch.from_numpy(inputs.cooling_box((n, n, n))).float().cuda().contiguous())
+        fine.init_state(_initial_state(setup, n, seed))
         fine.advance(setup.spinup_steps)
         U0 = downsample(fine.get_state(), setup.factor)
         if sub == "auto":
@@ -350,7 +363,7 @@ def make_trajectories(setup: ClosureSetup, count: int, length: int, seed0: int =
     out = []
     for r in range(count):
         fine = Solver(_cfg(n, setup, seed0 + r))
-        fine.init_state(torch.from_numpy(inputs.cooling_box((n, n, n))).float().cuda().contiguous())
+        fine.init_state(_initial_state(setup, n, seed0 + r))
         fine.advance(setup.spinup_steps)
         U0 = downsample(fine.get_state(), setup.factor)
         dts, modes, targets = [], [], []

@@ -187,3 +187,16 @@ def test_non_finite_correction_in_step_fails_the_step():
     s.correct_every_step(False)
     s.advance(1)
     assert s.time()[1] == n0 + 1
+
+
+def test_self_gravitating_pairs():
+    """The self-gravitating closure set-up: solver-made pairs of runs with multigrid gravity
+    from seeded lognormal densities (one per run); each pair's coarse step stays close to the
+    downsampled fine run."""
+    setup = closure.ClosureSetup(fine=32, factor=4, runs=2, snapshots=3, spinup_steps=3,
+                                 gravity=True, sigma=0.5)
+    X, Y = closure.make_pairs(setup)
+    assert X.shape == (6, 5, 8, 8, 8) and torch.isfinite(X).all() and torch.isfinite(Y).all()
+    assert not torch.equal(X[0], X[3])            # the two runs start from different densities
+    rel = float((Y - X).norm() / Y.norm())
+    assert 0.0 < rel < 0.2
