@@ -82,16 +82,16 @@ __host__ __device__ __forceinline__ void hllc_vjp(real rL, real uL, real aL, rea
   const real SL = fmin(xL, xR);
   const real SR = fmax(yL, yR);
   const real dL = SL - uL, dR = SR - uR;
-  const real num = pR - pL + rL * uL * dL - rR * uR * dR;
-  const real den = rL * dL - rR * dR;
+  const real num = hllc_star_num(rL, uL, pL, dL, rR, uR, pR, dR);
+  const real den = hllc_star_den(rL, dL, rR, dR);
   const real Ss = q_div(num, den);
   const real iden = q_div(real(1), den);
   const bool left = (SL >= real(0)) || (Ss >= real(0));
   const bool star = !(SL >= real(0)) && (Ss >= real(0) || SR > real(0));
   const real r = left ? rL : rR, u = left ? uL : uR, a = left ? aL : aR, b = left ? bL : bR;
   const real p = left ? pL : pR, S = left ? SL : SR, d = left ? dL : dR;
-  const real E = q_div(p, gm1) + real(0.5) * r * (u * u + a * a + b * b);
-  const real mass = r * u;
+  const real E = rfma(rmul(real(0.5), r), rfma(b, b, rfma(a, a, rmul(u, u))), q_div(p, gm1));
+  const real mass = rmul(r, u);
 
   real r_ = 0, u_ = 0, a_ = 0, b_ = 0, p_ = 0, S_ = 0, Ss_ = 0, d_ = 0;
   real mass_ = g0 + gn * u + gt1 * a + gt2 * b;

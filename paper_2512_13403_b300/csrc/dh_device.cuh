@@ -69,6 +69,53 @@ __device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return _
 // a - b in one packed instruction: fma(b, -1, a) rounds the exact difference once.
 __device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, f2s(-1.0f), a); }
 
+// Scalar products, sums and fused multiply-adds with their rounding spelled out.  The compiler
+// never contracts these into other operations, so every inlined copy of a formula rounds the
+// same way wherever it is called (a cell's flux does not depend on which loop phase of the
+// stencil evaluates it).
+__host__ __device__ __forceinline__ float rmul(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ float radd(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ float rfma(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return fmaf(a, b, c);
+#endif
+}
+__host__ __device__ __forceinline__ double rmul(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ double radd(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ double rfma(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+  return __fma_rn(a, b, c);
+#else
+  return fma(a, b, c);
+#endif
+}
+
 // W = (rho, v, P) from U (Eq. 2).
 template <typename real>
 __host__ __device__ __forceinline__ Prim<real> cons_to_prim(real r, real mx, real my, real mz, real E,
@@ -80,8 +127,8 @@ __host__ __device__ __forceinline__ Prim<real> cons_to_prim(real r, real mx, rea
     const float2 vxy = p_mul(f2(mx, my), f2s(ir));
     const float vz = mz * ir;
     const float2 sq = p_mul(vxy, vxy);
-    const float v2 = sq.x + sq.y + vz * vz;
-    return Prim<float>{r, vxy.x, vxy.y, vz, gm1 * (E - 0.5f * r * v2)};
+    const float v2 = rfma(vz, vz, radd(sq.x, sq.y));
+    return Prim<float>{r, vxy.x, vxy.y, vz, rmul(gm1, rfma(rmul(-0.5f, r), v2, E))};
   }
 #endif
   Prim<real> w;
@@ -89,7 +136,8 @@ __host__ __device__ __forceinline__ Prim<real> cons_to_prim(real r, real mx, rea
   w.vx = q_div(mx, r);
   w.vy = q_div(my, r);
   w.vz = q_div(mz, r);
-  w.p = gm1 * (E - real(0.5) * r * (w.vx * w.vx + w.vy * w.vy + w.vz * w.vz));
+  const real v2 = rfma(w.vz, w.vz, rfma(w.vy, w.vy, rmul(w.vx, w.vx)));
+  w.p = rmul(gm1, rfma(rmul(real(-0.5), r), v2, E));
   return w;
 }
 
@@ -190,6 +238,19 @@ __host__ __device__ __forceinline__ Prim<real> add_half(const Prim<real>& w, con
 // Flux components in the face frame: (mass, normal momentum, tangential 1, tangential 2, energy).
 template <typename real> struct Flux { real f0, fn, ft1, ft2, fe; };
 
+// Numerator and denominator of the contact speed S* (App. A.2):
+// S* = (p_R - p_L + rho_L u_L d_L - rho_R u_R d_R) / (rho_L d_L - rho_R d_R), d_K = S_K - u_K.
+// The flux and its adjoint both take these, so that they choose the same HLLC region.
+template <typename real>
+__host__ __device__ __forceinline__ real hllc_star_num(real rL, real uL, real pL, real dL, real rR,
+                                                       real uR, real pR, real dR) {
+  return rfma(-rmul(rR, uR), dR, rfma(rmul(rL, uL), dL, radd(pR, -pL)));
+}
+template <typename real>
+__host__ __device__ __forceinline__ real hllc_star_den(real rL, real dL, real rR, real dR) {
+  return rfma(rL, dL, -rmul(rR, dR));
+}
+
 // HLLC flux (Toro, Spruce & Speares 1994) for face-frame states (rho, u_n, u_t1, u_t2, P).
 // Region choice: S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; otherwise F_R.
 template <typename real>
@@ -201,7 +262,7 @@ __host__ __device__ __forceinline__ Flux<real> hllc(real rL, real uL, real aL, r
   const real SL = fmin(uL - cL, uR - cR);
   const real SR = fmax(uL + cL, uR + cR);
   const real dL = SL - uL, dR = SR - uR;
-  const real Sstar = q_div(pR - pL + rL * uL * dL - rR * uR * dR, rL * dL - rR * dR);
+  const real Sstar = q_div(hllc_star_num(rL, uL, pL, dL, rR, uR, pR, dR), hllc_star_den(rL, dL, rR, dR));
 
   // Select the side K whose (star) flux is taken.
   const bool left = (SL >= real(0)) || (Sstar >= real(0));
@@ -209,17 +270,19 @@ __host__ __device__ __forceinline__ Flux<real> hllc(real rL, real uL, real aL, r
   const real r = left ? rL : rR, u = left ? uL : uR, a = left ? aL : aR, b = left ? bL : bR;
   const real p = left ? pL : pR, S = left ? SL : SR, d = left ? dL : dR;
 
-  const real E = q_div(p, gm1) + real(0.5) * r * (u * u + a * a + b * b);
-  const real mass = r * u;
-  Flux<real> F{mass, mass * u + p, mass * a, mass * b, u * (E + p)};
+  const real v2 = rfma(b, b, rfma(a, a, rmul(u, u)));
+  const real E = rfma(rmul(real(0.5), r), v2, q_div(p, gm1));
+  const real mass = rmul(r, u);
+  Flux<real> F{mass, rfma(mass, u, p), rmul(mass, a), rmul(mass, b), rmul(u, radd(E, p))};
   if (star) {
-    const real coef = q_div(r * d, S - Sstar);
-    const real Es = coef * (q_div(E, r) + (Sstar - u) * (Sstar + q_div(p, r * d)));
-    F.f0 += S * (coef - r);
-    F.fn += S * (coef * Sstar - mass);
-    F.ft1 += S * (coef * a - r * a);
-    F.ft2 += S * (coef * b - r * b);
-    F.fe += S * (Es - E);
+    const real coef = q_div(rmul(r, d), radd(S, -Sstar));
+    const real sdu = radd(Sstar, -u);
+    const real Es = rmul(coef, rfma(sdu, radd(Sstar, q_div(p, rmul(r, d))), q_div(E, r)));
+    F.f0 = rfma(S, radd(coef, -r), F.f0);
+    F.fn = rfma(S, rfma(coef, Sstar, -mass), F.fn);
+    F.ft1 = rfma(S, radd(rmul(coef, a), -rmul(r, a)), F.ft1);
+    F.ft2 = rfma(S, radd(rmul(coef, b), -rmul(r, b)), F.ft2);
+    F.fe = rfma(S, radd(Es, -E), F.fe);
   }
   return F;
 }
@@ -249,26 +312,26 @@ __device__ __forceinline__ Flux<float> hllc_packed(float rL, float uL, float aL,
 
   const float2 ua2 = p_mul(f2(uk, ak), f2(uk, ak));
   const float igm1 = 1.0f / gm1;   // uniform: hoisted out of the face loops
-  const float E = pk * igm1 + 0.5f * rk * (ua2.x + ua2.y + bk * bk);
-  const float mass = rk * uk;
+  const float E = rfma(pk, igm1, rmul(rmul(0.5f, rk), rfma(bk, bk, radd(ua2.x, ua2.y))));
+  const float mass = rmul(rk, uk);
   const float2 fna = p_fma(f2s(mass), f2(uk, ak), f2(pk, 0.0f));   // (mass u + p, mass a)
-  Flux<float> F{mass, fna.x, fna.y, mass * bk, uk * (E + pk)};
+  Flux<float> F{mass, fna.x, fna.y, rmul(mass, bk), rmul(uk, radd(E, pk))};
   if (star) {
     // E* = rho d/(S - S*) (E/rho + (S* - u)(S* + p/(rho d))) with one reciprocal:
     // = (d (E + rho S* (S* - u)) + (S* - u) p) / (S - S*)
-    const float inv = q_div(1.0f, S - Sstar);
-    const float rdk = rk * dk;
-    const float coef = rdk * inv;
-    const float sdu = Sstar - uk;
-    const float Es = (dk * (E + rk * Sstar * sdu) + sdu * pk) * inv;
-    const float w = coef - rk;
-    const float2 f0n = p_fma(f2s(S), f2(w, coef * Sstar - mass), f2(F.f0, F.fn));
-    const float2 ft = p_fma(f2s(S * w), f2(ak, bk), f2(F.ft1, F.ft2));
+    const float inv = q_div(1.0f, radd(S, -Sstar));
+    const float rdk = rmul(rk, dk);
+    const float coef = rmul(rdk, inv);
+    const float sdu = radd(Sstar, -uk);
+    const float Es = rmul(rfma(dk, rfma(rmul(rk, Sstar), sdu, E), rmul(sdu, pk)), inv);
+    const float w = radd(coef, -rk);
+    const float2 f0n = p_fma(f2s(S), f2(w, rfma(coef, Sstar, -mass)), f2(F.f0, F.fn));
+    const float2 ft = p_fma(f2s(rmul(S, w)), f2(ak, bk), f2(F.ft1, F.ft2));
     F.f0 = f0n.x;
     F.fn = f0n.y;
     F.ft1 = ft.x;
     F.ft2 = ft.y;
-    F.fe += S * (Es - E);
+    F.fe = rfma(S, radd(Es, -E), F.fe);
   }
   return F;
 }
