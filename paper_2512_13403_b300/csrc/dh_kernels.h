@@ -37,6 +37,11 @@ template <typename real> struct StageArgs {
 // stage 1: U + dt L(U); 2: RK2's final stage; 3: the weighted combination of SSPRK3
 template <typename real>
 cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s);
+// The same stage by the paired kernel (hydro_pair.cu) when the grid has whole 64 x 8 tiles and
+// the state takes tensor-map copies: returns false (nothing launched) otherwise; err is the
+// launch's status.
+template <typename real>
+bool launch_stage_pair(int stage, const StageArgs<real>& a, cudaStream_t s, cudaError_t& err);
 
 struct BeginArgs {
   StepRecord* rec;

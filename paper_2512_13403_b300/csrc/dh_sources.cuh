@@ -155,6 +155,30 @@ __device__ __forceinline__ void row_factor(const real* __restrict__ ah, int nxse
   }
 }
 
+// The row factors of all three n_x bins for row (y, z) and component c at once: bin b collects
+// the modes with n_x = b, in the mode order of row_factor.
+template <typename real, int M>
+__device__ __forceinline__ void row_factors3(const real* __restrict__ ah, int c, const real* ty,
+                                             const real* tz, real bre[3], real bim[3]) {
+  if constexpr (M < 16) {
+    constexpr int NX = forced_mode_component(M, 0);
+    constexpr int NY = forced_mode_component(M, 1);
+    constexpr int NZ = forced_mode_component(M, 2);
+    C2<real> e{real(1), real(0)};
+    bool first = true;
+    if constexpr (NY != 0) { e = axis_factor<real, NY>(ty); first = false; }
+    if constexpr (NZ != 0) {
+      const C2<real> f = axis_factor<real, NZ>(tz);
+      e = first ? f : cmul(e, f);
+    }
+    const real are = ah[2 * (3 * M + c)];
+    const real aim = ah[2 * (3 * M + c) + 1];
+    bre[NX] += are * e.re - aim * e.im;
+    bim[NX] += are * e.im + aim * e.re;
+    row_factors3<real, M + 1>(ah, c, ty, tz, bre, bim);
+  }
+}
+
 // a(x) = 2 Re sum_H a_hat_n exp(2 pi i n . x~), with the normalised table (Sec. 3.1.1).
 template <typename real>
 __device__ __forceinline__ void forcing_accel(const real* ah, const real* const tw[3], int i,
@@ -176,19 +200,26 @@ __device__ __forceinline__ void forcing_accel(const real* ah, const real* const 
 // Cooling of one cell (Sec. 4.3; Lambda = n^2 T^(1/2), T = P / rho, floor rho T_floor/(gamma-1)).
 // A cell cools only while its thermal energy is above the floor energy; the test compares
 // energies, so a state clamped to the floor is recognised exactly whatever the rounding of T.
+// Products, sums and fused multiply-adds have their rounding spelled out (never contracted by
+// the compiler), so the two-lane form (cooling_energy2) and the tangents (cooling_tangents)
+// take exactly this function's values and branches.
+template <typename real>
+__device__ __forceinline__ real cooling_rate(real r2, real gm1, real Eth, real ir) {
+  return -rmul(r2, q_sqrt(rmul(rmul(gm1, Eth), ir)));
+}
 template <typename real>
 __device__ __forceinline__ real cooling_energy(real r, real mx, real my, real mz, real E, real dt,
                                                real gm1, real T_floor, real frac, int nsub_max,
                                                unsigned& flags, int& nsub_seen) {
   const real ir = q_div(real(1), r);
-  const real kin = real(0.5) * (mx * mx + my * my + mz * mz) * ir;
-  const real Eth = E - kin;
-  const real Efl = r * T_floor * (real(1) / gm1);
+  const real kin = rmul(rmul(real(0.5), rfma(mz, mz, rfma(my, my, rmul(mx, mx)))), ir);
+  const real Eth = radd(E, -kin);
+  const real Efl = rmul(rmul(r, T_floor), real(1) / gm1);
   if (!(Eth > Efl)) return E;
-  const real r2 = r * r;
-  const real Ed0 = -r2 * q_sqrt(gm1 * Eth * ir);
+  const real r2 = rmul(r, r);
+  const real Ed0 = cooling_rate(r2, gm1, Eth, ir);
   // dt / (frac t_cool) with t_cool = Eth / (-Ed0), as one division
-  const real raw = ceil(q_div(dt * -Ed0, frac * Eth));
+  const real raw = ceil(q_div(rmul(dt, -Ed0), rmul(frac, Eth)));
   // clamp to [1, nsub_max]; a NaN count also takes the cap, so the loop below is always bounded
   real nsub = raw;
   if (!(raw <= real(nsub_max))) {
@@ -198,21 +229,21 @@ __device__ __forceinline__ real cooling_energy(real r, real mx, real my, real mz
   if (!(nsub >= real(1))) nsub = real(1);
   real Enew;
   if (nsub == real(1)) {
-    const real Ep = fmax(Efl, Eth + dt * Ed0);
-    const real Edp = Ep > Efl ? -r2 * q_sqrt(gm1 * Ep * ir) : real(0);
-    Enew = fmax(Efl, Eth + real(0.5) * dt * (Ed0 + Edp));
+    const real Ep = fmax(Efl, rfma(dt, Ed0, Eth));
+    const real Edp = Ep > Efl ? cooling_rate(r2, gm1, Ep, ir) : real(0);
+    Enew = fmax(Efl, rfma(real(0.5) * dt, radd(Ed0, Edp), Eth));
   } else {
     const real dts = q_div(dt, nsub);
     const int n = (int)nsub;
     nsub_seen = n > nsub_seen ? n : nsub_seen;
     real Es = Eth;
     for (int q = 0; q < n; ++q) {
-      const real ed = Es > Efl ? -r2 * q_sqrt(gm1 * Es * ir) : real(0);
-      Es = fmax(Efl, Es + ed * dts);
+      const real ed = Es > Efl ? cooling_rate(r2, gm1, Es, ir) : real(0);
+      Es = fmax(Efl, rfma(ed, dts, Es));
     }
     Enew = Es;
   }
-  return kin + Enew;
+  return radd(kin, Enew);
 }
 
 // Tangents of the cooling map of one cell, (rho, E_th) -> E_th', as cooling_energy computes it:
@@ -226,39 +257,39 @@ __device__ __forceinline__ void cooling_tangents(real r, real mx, real my, real 
                                                  real gm1, real T_floor, real frac, int nsub_max,
                                                  real& cR, real& cE) {
   const real ir = q_div(real(1), r);
-  const real kin = real(0.5) * (mx * mx + my * my + mz * mz) * ir;
-  const real Eth = E - kin;
-  const real Efl = r * T_floor * (real(1) / gm1);
+  const real kin = rmul(rmul(real(0.5), rfma(mz, mz, rfma(my, my, rmul(mx, mx)))), ir);
+  const real Eth = radd(E, -kin);
+  const real Efl = rmul(rmul(r, T_floor), real(1) / gm1);
   cR = real(0);
   cE = real(1);
   if (!(Eth > Efl)) return;
   const real dfl = q_div(T_floor, gm1);   // dE_floor/drho
-  const real r2 = r * r;
+  const real r2 = rmul(r, r);
   // clamp rule for max(E_floor, X) with tangent (xr, xe)
   auto clamp_t = [&](real X, real xr, real xe, real& tr, real& te) {
     if (X > Efl) { tr = xr; te = xe; }
     else if (X < Efl) { tr = dfl; te = real(0); }
     else { tr = real(0.5) * (xr + dfl); te = real(0.5) * xe; }
   };
-  const real Ed0 = -r2 * q_sqrt(gm1 * Eth * ir);
-  const real raw = ceil(q_div(dt * -Ed0, frac * Eth));   // the forward's substep count
+  const real Ed0 = cooling_rate(r2, gm1, Eth, ir);
+  const real raw = ceil(q_div(rmul(dt, -Ed0), rmul(frac, Eth)));   // the forward's substep count
   real nsub = raw;
   if (!(raw <= real(nsub_max))) nsub = real(nsub_max);
   if (!(nsub >= real(1))) nsub = real(1);
   if (nsub == real(1)) {
     const real d0r = real(1.5) * Ed0 * ir, d0e = real(0.5) * q_div(Ed0, Eth);
-    const real X = Eth + dt * Ed0;
+    const real X = rfma(dt, Ed0, Eth);
     real pr, pe;
     clamp_t(X, dt * d0r, real(1) + dt * d0e, pr, pe);
     const real Ep = fmax(Efl, X);
     real Edp = real(0), dpr = real(0), dpe = real(0);
     if (Ep > Efl) {
-      Edp = -r2 * q_sqrt(gm1 * Ep * ir);
+      Edp = cooling_rate(r2, gm1, Ep, ir);
       const real g = real(0.5) * q_div(Edp, Ep);
       dpr = real(1.5) * Edp * ir + g * pr;
       dpe = g * pe;
     }
-    const real Y = Eth + real(0.5) * dt * (Ed0 + Edp);
+    const real Y = rfma(real(0.5) * dt, radd(Ed0, Edp), Eth);
     clamp_t(Y, real(0.5) * dt * (d0r + dpr), real(1) + real(0.5) * dt * (d0e + dpe), cR, cE);
   } else {
     const real dts = q_div(dt, nsub);
@@ -267,12 +298,12 @@ __device__ __forceinline__ void cooling_tangents(real r, real mx, real my, real 
     for (int q = 0; q < n; ++q) {
       real ed = real(0), er = real(0), ee = real(0);
       if (Es > Efl) {
-        ed = -r2 * q_sqrt(gm1 * Es * ir);
+        ed = cooling_rate(r2, gm1, Es, ir);
         const real g = real(0.5) * q_div(ed, Es);
         er = real(1.5) * ed * ir + g * sr;
         ee = g * se;
       }
-      const real X = Es + ed * dts;
+      const real X = rfma(ed, dts, Es);
       real tr, te;
       clamp_t(X, sr + dts * er, se + dts * ee, tr, te);
       Es = fmax(Efl, X);

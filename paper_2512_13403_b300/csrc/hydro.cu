@@ -673,6 +673,8 @@ static cudaError_t launch_stage_t(const StageArgs<real>& a, cudaStream_t s) {
 
 template <typename real>
 cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s) {
+  cudaError_t pe = cudaSuccess;
+  if (launch_stage_pair<real>(stage, a, s, pe)) return pe;
   if (a.limiter == LIM_VL) {
     if (stage == 1) return launch_stage_t<real, 1, LIM_VL>(a, s);
     if (stage == 2) return launch_stage_t<real, 2, LIM_VL>(a, s);
