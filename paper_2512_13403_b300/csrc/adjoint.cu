@@ -824,14 +824,16 @@ static cudaError_t replay_stage(dh_ctx* c, int stage, const void* U, const void*
     a.forcing = g.forcing && tab;
     a.ahat_norm = (const real*)tab;
     for (int q = 0; q < 3; ++q) a.tw[q] = (const real*)c->tw[q];
+    a.frow = (real*)c->frow;
     a.cooling = g.cooling;
     a.t_floor = (real)g.t_floor; a.cool_frac = (real)g.cool_frac; a.nsub_max = g.nsub_max;
   }
   prof_begin(c, stage == 2 && final ? DH_KERNEL_STAGE2 : DH_KERNEL_STAGE1);
   // RK2's final stage is kernel stage 2; SSPRK3's weighted stages are kernel stage 3
   const bool rk2_final = stage == 2 && final && w0 == real(0.5) && w1 == real(0.5);
-  cudaError_t e = launch_stage<real>(stage == 1 ? 1 : (rk2_final ? 2 : 3), a, c->stream);
-  prof_end(c, 1);
+  int nl = 1;
+  cudaError_t e = launch_stage<real>(stage == 1 ? 1 : (rk2_final ? 2 : 3), a, c->stream, &nl);
+  prof_end(c, nl);
   return e;
 }
 

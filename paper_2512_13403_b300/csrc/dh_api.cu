@@ -119,6 +119,8 @@ extern "C" dh_status dh_create(const dh_config* cfg, void* stream, dh_ctx** out)
   if (e == cudaSuccess) e = alloc((void**)&c->ahat_prev, 96 * sizeof(double));
   if (e == cudaSuccess) e = alloc(&c->ahat_norm, 96 * esize(c));
   if (e == cudaSuccess && cfg->forcing) e = alloc((void**)&c->ou_draws, OU_DRAW_BATCH * 96 * sizeof(double));
+  if (e == cudaSuccess && cfg->forcing)
+    e = alloc(&c->frow, (size_t)cfg->ny * cfg->nz * 18 * esize(c));
   if (e == cudaSuccess) e = alloc((void**)&c->partials, (size_t)totals_blocks() * 5 * sizeof(double));
   if (e == cudaSuccess) e = alloc((void**)&c->totals, 5 * sizeof(double));
   const int n[3] = {cfg->nx, cfg->ny, cfg->nz};
@@ -161,6 +163,7 @@ extern "C" void dh_destroy(dh_ctx* c) {
   cudaFree(c->ahat_prev);
   cudaFree(c->ou_draws);
   cudaFree(c->ahat_norm);
+  cudaFree(c->frow);
   cudaFree(c->partials);
   cudaFree(c->totals);
   for (int a = 0; a < 3; ++a) cudaFree(c->tw[a]);
@@ -286,6 +289,7 @@ static StageArgs<real> stage_args(dh_ctx* c) {
   a.dtp = &c->rec->dt;
   a.ahat_norm = (const real*)c->ahat_norm;
   for (int q = 0; q < 3; ++q) a.tw[q] = (const real*)c->tw[q];
+  a.frow = (real*)c->frow;
   a.t_floor = (real)g.t_floor; a.cool_frac = (real)g.cool_frac; a.nsub_max = g.nsub_max;
   a.cool_ratio = cool_ratio<real>(g);
   a.limiter = g.limiter;
@@ -338,9 +342,10 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed, const StepCapture* c
   // (scratch) -> U^{n+1}; U^n is never written, so it stays the last good state.
   real* Ust1 = cap && cap->u1 ? (real*)cap->u1 : (rk3 ? Unew : (real*)c->U1);
   a.U = Un; a.U0 = nullptr; a.out = Ust1;
+  int nl = 1;
   prof_begin(c, DH_KERNEL_STAGE1);
-  e = launch_stage<real>(1, a, c->stream);
-  prof_end(c, 1);
+  e = launch_stage<real>(1, a, c->stream, &nl);
+  prof_end(c, nl);
   if (e != cudaSuccess) return e;
   const real* Ulast = Ust1;
   if (rk3) {
@@ -349,8 +354,8 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed, const StepCapture* c
     m.w0 = real(0.75); m.w1 = real(0.25);
     m.final_stage = 0;
     prof_begin(c, DH_KERNEL_STAGE1);
-    e = launch_stage<real>(3, m, c->stream);
-    prof_end(c, 1);
+    e = launch_stage<real>(3, m, c->stream, &nl);
+    prof_end(c, nl);
     if (e != cudaSuccess) return e;
     Ulast = m.out;
     a.w0 = real(1.0 / 3.0); a.w1 = real(2.0 / 3.0);
@@ -365,8 +370,8 @@ static cudaError_t enqueue_step(dh_ctx* c, double dt_fixed, const StepCapture* c
   a.reduce_cfl = fuse && !correct ? 1 : 0;
   a.pre_src = fuse && cap ? (real*)cap->pre_src : nullptr;
   prof_begin(c, DH_KERNEL_STAGE2);
-  e = launch_stage<real>(rk3 ? 3 : 2, a, c->stream);
-  prof_end(c, 1);
+  e = launch_stage<real>(rk3 ? 3 : 2, a, c->stream, &nl);
+  prof_end(c, nl);
   if (e != cudaSuccess) return e;
   if (!fuse) {
     e = gravity_sources<real>(c, Unew, nullptr, &c->rec->dt, true);

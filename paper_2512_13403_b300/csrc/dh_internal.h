@@ -23,6 +23,7 @@ struct dh_ctx {
   double* ahat = nullptr;            // OU mode table (96 doubles), unnormalised
   double* ahat_prev = nullptr;       // table before the last update (rollback)
   void* ahat_norm = nullptr;         // normalised table in the working precision
+  void* frow = nullptr;              // forcing row factors of the step (ny nz 18 reals)
   void* tw[3] = {nullptr, nullptr, nullptr};  // per-axis forcing twiddles
   int ou_hold = 0;                   // 1: steps keep the forcing table as set (no OU update)
   double* ou_draws = nullptr;        // projected draws of steps [ou_draw_first, + ou_draw_count)

@@ -20,6 +20,8 @@ template <typename real> struct StageArgs {
   int forcing, cooling;
   const real* ahat_norm;  // 16 modes x 3 comps x (re, im), normalised
   const real* tw[3];      // per-axis twiddles: for cell i, (cos t, sin t, cos 2t, sin 2t), t = 2 pi (i+1/2)/n
+  real* frow;             // scratch for the step's forcing row factors (ny nz 18 reals; the paired
+                          // kernel's final stage fills and reads it, nullable otherwise)
   real t_floor, cool_frac;
   int nsub_max;
   int reduce_cfl;         // accumulate the CFL minimum of the output state
@@ -34,14 +36,16 @@ template <typename real> struct StageArgs {
   int count_fallbacks;    // add the own cells' positivity fallbacks to rec->slope_fallbacks
 };
 
-// stage 1: U + dt L(U); 2: RK2's final stage; 3: the weighted combination of SSPRK3
+// stage 1: U + dt L(U); 2: RK2's final stage; 3: the weighted combination of SSPRK3.
+// `launched` (nullable) receives the number of kernels enqueued.
 template <typename real>
-cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s);
+cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s, int* launched = nullptr);
 // The same stage by the paired kernel (hydro_pair.cu) when the grid has whole 64 x 8 tiles and
 // the state takes tensor-map copies: returns false (nothing launched) otherwise; err is the
-// launch's status.
+// launches' status and launched their number (the final stage with forcing first fills the
+// forcing row-factor table).
 template <typename real>
-bool launch_stage_pair(int stage, const StageArgs<real>& a, cudaStream_t s, cudaError_t& err);
+bool launch_stage_pair(int stage, const StageArgs<real>& a, cudaStream_t s, cudaError_t& err, int& launched);
 
 struct BeginArgs {
   StepRecord* rec;

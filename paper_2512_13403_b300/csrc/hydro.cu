@@ -672,9 +672,14 @@ static cudaError_t launch_stage_t(const StageArgs<real>& a, cudaStream_t s) {
 }
 
 template <typename real>
-cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s) {
+cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s, int* launched) {
   cudaError_t pe = cudaSuccess;
-  if (launch_stage_pair<real>(stage, a, s, pe)) return pe;
+  int n = 0;
+  if (launch_stage_pair<real>(stage, a, s, pe, n)) {
+    if (launched) *launched = n;
+    return pe;
+  }
+  if (launched) *launched = 1;
   if (a.limiter == LIM_VL) {
     if (stage == 1) return launch_stage_t<real, 1, LIM_VL>(a, s);
     if (stage == 2) return launch_stage_t<real, 2, LIM_VL>(a, s);
@@ -684,8 +689,8 @@ cudaError_t launch_stage(int stage, const StageArgs<real>& a, cudaStream_t s) {
   if (stage == 2) return launch_stage_t<real, 2, LIM_MC>(a, s);
   return launch_stage_t<real, 3, LIM_MC>(a, s);
 }
-template cudaError_t launch_stage<float>(int, const StageArgs<float>&, cudaStream_t);
-template cudaError_t launch_stage<double>(int, const StageArgs<double>&, cudaStream_t);
+template cudaError_t launch_stage<float>(int, const StageArgs<float>&, cudaStream_t, int*);
+template cudaError_t launch_stage<double>(int, const StageArgs<double>&, cudaStream_t, int*);
 
 // ---------------------------------------------------------------------------------------------
 // OU forcing draws (Sec. 3.1.1): counter-based SplitMix64 stream, Box-Muller pairs.

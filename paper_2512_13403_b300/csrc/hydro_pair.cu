@@ -75,9 +75,8 @@ template <typename real> struct PairSmem {
   P fxe[QY][QX + 1];
   Q fy01[QY + 1][QX], fy23[QY + 1][QX];
   P fye[QY + 1][QX];
-  real ah[96];                  // forcing: normalised OU table
-  real tyt[QY][4];              // forcing: y twiddles of the tile's rows
-  real fB[2][QY][3][3][2];      // forcing row factors of planes (slot = plane & 1)
+  // forcing row factors B[row][n_x][component] (re, im) of plane j - 2, staged with plane j
+  alignas(16) real fB[2][QY][3][3][2];
   real red[QNT / 32];           // CFL reduction scratch
   alignas(8) uint64_t bar[2];   // staging slot landed (TMA transaction bytes; slot = plane & 1)
 };
@@ -205,22 +204,21 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
     tc::mbar_init(&S.bar[1], 1u);
     tc::mbar_fence_init();
   }
-  if (forcing) {
-    if (tid < 96) S.ah[tid] = __ldg(p.ahat_norm + tid);
-    if (tid >= 128 && tid < 128 + 4 * QY) {
-      const int ly = (tid - 128) >> 2, i = (tid - 128) & 3;
-      S.tyt[ly][i] = __ldg(p.tw[1] + 4 * (y0 + ly) + i);
-    }
-  }
   // wrapped start coordinates of the halo boxes
   const int xl0 = x0 >= SCE ? x0 - SCE : nx - SCE, xr0 = x0 + QCX < nx ? x0 + QCX : 0;
   const int yt0 = y0 >= 2 ? y0 - 2 : ny - 2, yb0 = y0 + QY < ny ? y0 + QY : 0;
   __syncthreads();
 
-  auto stage_plane = [&](int k) {   // thread 0: the five boxes of plane k on the staging barrier
+  // thread 0: the five boxes of plane k on the staging barrier, and with forcing the row factors
+  // of plane k - 2 (the plane whose update runs when plane k is converted)
+  constexpr uint32_t FB_BYTES = (uint32_t)sizeof(real) * QY * 18;
+  auto stage_plane = [&](int k) {
     const int kz = wrap(k, nz), b = k & 1;
     const uint32_t bar = tc::smem_u32(&S.bar[b]);
-    tc::mbar_arrive_expect_tx(&S.bar[b], ST::BYTES);
+    tc::mbar_arrive_expect_tx(&S.bar[b], ST::BYTES + (forcing ? FB_BYTES : 0u));
+    if (forcing)
+      tc::bulk_g2s(tc::smem_u32(&S.fB[b][0][0][0][0]), p.frow + ((long long)wrap(k - 2, nz) * ny + y0) * 18,
+                   FB_BYTES, &S.bar[b]);
     tma_load_4d(tc::smem_u32(&S.core[b][0][0][0]), &tma.core, x0, y0, kz, 0, bar);
     tma_load_4d(tc::smem_u32(&S.xl[b][0][0][0]), &tma.xh, xl0, y0, kz, 0, bar);
     tma_load_4d(tc::smem_u32(&S.xr[b][0][0][0]), &tma.xh, xr0, y0, kz, 0, bar);
@@ -233,12 +231,13 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
   // strides, the ring position, and the global coordinates (for the prologue's direct loads)
   // (slot 1 of each staging array lies a fixed number of elements after slot 0)
   constexpr int CORE_SLOT = 5 * QY * QCX, XH_SLOT = 5 * QY * SCE, YH_SLOT = 5 * 2 * QCX;
-  const bool halo = tid >= 96;
+  const int hbase = 96;
+  const bool halo = tid >= hbase;
   const real* hsa = nullptr;
   const real* hsb = nullptr;
   int hfa = 0, hfb = 0, hoa = 0, hob = 0, hr = 0, hp = 0, hgxa = 0, hgxb = 0, hgy = 0;
   if (halo) {
-    const int e = tid - 96;   // 0 .. 159
+    const int e = tid - hbase;   // 0 .. 159
     if (e < 128) {            // y halo rows -2, -1 (e < 64) and 8, 9
       const bool top = e < 64;
       const int row = (e >> 5) & 1, q = e & 31;
@@ -332,6 +331,16 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
     const int sk = k & 1, sk1 = sk ^ 1;
 
     // x/y divergence of plane k-1 from its face fluxes (written last iteration)
+    // the own cells' U (and U0) of plane k-1, loaded early for its update below
+    P uin_e[5], un_e[5];
+    if (k > z0) {
+      const long long ia = (long long)(k - 1) * plane + col, ib = ia + QX;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        uin_e[c] = pmk(__ldg(p.U + c * n3 + ia), __ldg(p.U + c * n3 + ib));
+        if (COMB) un_e[c] = pmk(__ldg(p.U0 + c * n3 + ia), __ldg(p.U0 + c * n3 + ib));
+      }
+    }
     P lxy[5];
     if (k > z0) {
       const Q ar = S.fx01[ty][tx + 1], al = S.fx01[ty][tx], br = S.fx23[ty][tx + 1], bl = S.fx23[ty][tx];
@@ -391,11 +400,11 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
       const P miz = pset(-p.idz), pdt = pset(dt);
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        const P uin = pmk(__ldg(p.U + c * n3 + ia), __ldg(p.U + c * n3 + ib));
+        const P uin = uin_e[c];
         const P L = pfma(psub(fz_hi[c], fz_lo[c]), miz, lxy[c]);
         P v = pfma(pdt, L, uin);
         if (COMB) {
-          const P un = pmk(__ldg(p.U0 + c * n3 + ia), __ldg(p.U0 + c * n3 + ib));
+          const P un = un_e[c];
           v = pfma(pset(w0c), un, pmul(pset(w1c), v));
         }
         u[c] = v;
@@ -410,7 +419,7 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
         }
         if (forcing) {
           // a = 2 Re sum_{n_x} B_{n_x} exp(2 pi i n_x x~)  (Sec. 3.1.1)
-          const real(*B)[3][2] = S.fB[(k - 1) & 1][ty];
+          const real(*B)[3][2] = S.fB[(k + 1) & 1][ty];   // staged with plane k + 1
           P a[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -458,25 +467,6 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
     }
     if (last) break;
 
-    // forcing row factors of plane k (its update runs next iteration): warp 7, lane = (row,
-    // component), the three n_x bins at once
-    if (forcing && ty == QY - 1 && tx < 3 * QY) {
-      const int ly = tx / 3, c = tx - 3 * ly;
-      real tyv[4], tzv[4];
-      const real* tzp = p.tw[2] + 4 * k;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        tyv[i] = S.tyt[ly][i];
-        tzv[i] = __ldg(tzp + i);
-      }
-      real bre[3] = {real(0), real(0), real(0)}, bim[3] = {real(0), real(0), real(0)};
-      row_factors3<real, 0>(S.ah, c, tyv, tzv, bre, bim);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        S.fB[sk][ly][b][c][0] = bre[b];
-        S.fB[sk][ly][b][c][1] = bim[b];
-      }
-    }
     __syncthreads();   // ---- half slopes of plane k ready; the staging buffers are free
 
     if (tid == 0 && k + 3 <= z1 + 1) stage_plane(k + 3);
@@ -559,6 +549,36 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
   }
 }
 
+// The forcing row factors of every (y, z) row of the step (Sec. 3.1.1): for n_x in {0, 1, 2} and
+// component c, B = sum over the forced modes with that n_x of a_hat_{m,c} exp(2 pi i (n_y y~ +
+// n_z z~)), stored [z][y][n_x][c][re, im].  One thread per (row, component).
+template <typename real>
+__global__ void forcing_rows_kernel(const real* __restrict__ ah, const real* __restrict__ tw1,
+                                    const real* __restrict__ tw2, int ny, int nz, real* __restrict__ out) {
+  __shared__ real s_ah[96];
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) s_ah[i] = ah[i];
+  __syncthreads();
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3ll * ny * nz) return;
+  const int c = (int)(t % 3);
+  const long long row = t / 3;
+  const int y = (int)(row % ny), z = (int)(row / ny);
+  real tyv[4], tzv[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    tyv[i] = tw1[4 * y + i];
+    tzv[i] = tw2[4 * z + i];
+  }
+  real bre[3] = {real(0), real(0), real(0)}, bim[3] = {real(0), real(0), real(0)};
+  row_factors3<real, 0>(s_ah, c, tyv, tzv, bre, bim);
+  real* o = out + row * 18;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    o[(b * 3 + c) * 2] = bre[b];
+    o[(b * 3 + c) * 2 + 1] = bim[b];
+  }
+}
+
 template <typename real, int STAGE, int LIM>
 static cudaError_t launch_pair_t(const StageArgs<real>& a, const StageTma& maps, cudaStream_t s) {
   auto kernel = stage_pair_kernel<real, STAGE, LIM>;
@@ -579,14 +599,26 @@ static cudaError_t launch_pair_t(const StageArgs<real>& a, const StageTma& maps,
 }
 
 template <typename real>
-bool launch_stage_pair(int stage, const StageArgs<real>& a, cudaStream_t s, cudaError_t& err) {
+bool launch_stage_pair(int stage, const StageArgs<real>& a, cudaStream_t s, cudaError_t& err, int& launched) {
+  launched = 0;
   // whole 64 x 8 tiles (every halo box contiguous), at least four planes, a 16-byte aligned base
   if (a.nx % QCX != 0 || a.ny % QY != 0 || a.nz < 4 || ((unsigned long long)a.U & 15ull) != 0)
     return false;
+  const bool final = stage == 2 || (stage == 3 && a.final_stage);
+  if (final && a.forcing && (!a.frow || ((unsigned long long)a.frow & 15ull) != 0)) return false;
   StageTma maps;
   std::memset(&maps, 0, sizeof(maps));
   if (!stage_tma_maps(a.U, a.nx, a.ny, a.nz, (int)sizeof(real), QCX, QY, PairStaging<real>::SCE, 2, &maps))
     return false;
+  if (final && a.forcing) {
+    const long long nt = 3ll * a.ny * a.nz;
+    forcing_rows_kernel<real><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(a.ahat_norm, a.tw[1], a.tw[2],
+                                                                           a.ny, a.nz, a.frow);
+    err = cudaGetLastError();
+    launched = 1;
+    if (err != cudaSuccess) return true;
+  }
+  ++launched;
   if (a.limiter == LIM_VL) {
     if (stage == 1) err = launch_pair_t<real, 1, LIM_VL>(a, maps, s);
     else if (stage == 2) err = launch_pair_t<real, 2, LIM_VL>(a, maps, s);
@@ -598,7 +630,7 @@ bool launch_stage_pair(int stage, const StageArgs<real>& a, cudaStream_t s, cuda
   }
   return true;
 }
-template bool launch_stage_pair<float>(int, const StageArgs<float>&, cudaStream_t, cudaError_t&);
-template bool launch_stage_pair<double>(int, const StageArgs<double>&, cudaStream_t, cudaError_t&);
+template bool launch_stage_pair<float>(int, const StageArgs<float>&, cudaStream_t, cudaError_t&, int&);
+template bool launch_stage_pair<double>(int, const StageArgs<double>&, cudaStream_t, cudaError_t&, int&);
 
 }  // namespace dh
