@@ -42,6 +42,10 @@ class ClosureSetup:
     # this sigma (seeded per run), fluid at rest
     gravity: bool = False
     sigma: float = 1.0
+    # coarse substeps per coarse interval: the coarse solver covers each interval with this many
+    # equal steps; the pair's input is the state after all of them (the corrector is applied
+    # once per interval, after the last)
+    substeps: int = 1
 
     @property
     def coarse(self) -> int:
@@ -115,7 +119,8 @@ def make_pairs(setup: ClosureSetup, log=None):
             modes = fine_interval(fine, dt_c, setup.forcing)
             if modes is not None:
                 coarse.set_forcing_modes(modes, hold=True)
-            coarse.step(dt_c)
+            for _ in range(setup.substeps):
+                coarse.step(dt_c / setup.substeps, sync=False)
             X[k] = coarse.get_state()
             Y[k] = downsample(fine.get_state(), setup.factor)
             k += 1
@@ -275,6 +280,68 @@ def evaluate(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
     nrun = steps * len(seeds)
     evaluate.diverged = diverged
     return ({k: v.tolist() for k, v in err.items()}, {k: v / nrun for k, v in gpu_ms.items()}, sub)
+
+
+def evaluate_substeps(setup: ClosureSetup, params, norm, steps: int = 100, seeds=(200,),
+                      frontier=(1, 2, 3, 4, 6, 8), form: str = "state"):
+    """The corrected coarse run with setup.substeps substeps per interval (the corrector applied
+    once, after the last) against uncorrected runs with each substep count of `frontier`, all
+    driven by the same fine run and forcing tables as evaluate().  The uncorrected runs trace the
+    plain solver's error against its GPU time; the equal-time comparison takes the frontier run
+    whose GPU time per interval is nearest the corrected run's, and the best frontier error at
+    any cost is reported beside it.  Returns a dict of mean and final errors and GPU ms per
+    interval of every run."""
+    n, nc = setup.fine, setup.coarse
+    names = [f"uncorrected_{m}" for m in frontier] + ["corrected"]
+    subs = {f"uncorrected_{m}": m for m in frontier}
+    subs["corrected"] = setup.substeps
+    err = {k: np.zeros(steps) for k in names}
+    gpu_ms = {k: 0.0 for k in names}
+    for seed in seeds:
+        fine = Solver(_cfg(n, setup, seed))
+        fine.init_state(_initial_state(setup, n, seed))
+        fine.advance(setup.spinup_steps)
+        U0 = downsample(fine.get_state(), setup.factor)
+        runs = {k: Solver(_cfg(nc, setup, seed)) for k in names}
+        for s in runs.values():
+            s.init_state(U0)
+        _set_corrector(runs["corrected"], params, norm, form)
+        clock = Solver(_cfg(nc, setup, seed))   # single-step run whose CFL step sets the interval
+        clock.init_state(U0)
+        for k in range(steps):
+            dt_c = clock.compute_dt()
+            modes = fine_interval(fine, dt_c, setup.forcing)
+            if modes is not None:
+                clock.set_forcing_modes(modes, hold=True)
+            clock.step(dt_c, sync=False)
+            for name, s in runs.items():
+                if modes is not None:
+                    s.set_forcing_modes(modes, hold=True)
+                m = subs[name]
+
+                def adv(s=s, m=m, corr=name == "corrected"):
+                    for j in range(m):
+                        if corr:
+                            s.correct_every_step(j == m - 1)
+                        s.step(dt_c / m, sync=False)
+                gpu_ms[name] += _timed(adv)
+                s.time()
+            ref = downsample(fine.get_state(), setup.factor)
+            for name, s in runs.items():
+                err[name][k] += _rel_l2(s.get_state(), ref) / len(seeds)
+        for s in list(runs.values()) + [fine, clock]:
+            s.close()
+    nrun = steps * len(seeds)
+    ms = {k: v / nrun for k, v in gpu_ms.items()}
+    mean = {k: float(v.mean()) for k, v in err.items()}
+    plain = [k for k in names if k != "corrected"]
+    eq = min(plain, key=lambda k: abs(ms[k] - ms["corrected"]))
+    best = min(plain, key=lambda k: mean[k])
+    return {"substeps": setup.substeps, "mean_error": mean,
+            "final_error": {k: float(v[-1]) for k, v in err.items()},
+            "gpu_ms_per_interval": ms, "equal_gpu_time_run": eq,
+            "uncorrected_equal_gpu_time": mean[eq], "corrected": mean["corrected"],
+            "best_uncorrected": {"run": best, "error": mean[best], "gpu_ms": ms[best]}}
 
 
 def evaluate_coarsened(fine: Solver, coarse_cfg: Config, factor: int, params, norm, fine_steps: int = 20,

@@ -83,6 +83,43 @@ def test_small_pair_train_evaluate_cycle():
     assert err2["uncorrected"] == err["uncorrected"] and err2["corrected"] == err["corrected"]
 
 
+def test_substep_pairs_and_frontier_evaluation():
+    """Coarse intervals covered by several substeps: the pair's input is the state after all of
+    them (equal to stepping by hand), and evaluate_substeps applies the corrector once per
+    interval (toggled on for the last substep only, which equals the substeps followed by
+    dh_correct) and reports the uncorrected frontier with its GPU times."""
+    setup = closure.ClosureSetup(fine=32, factor=4, runs=1, snapshots=3, spinup_steps=10, substeps=3)
+    X, Y = closure.make_pairs(setup)
+    assert X.shape == (3, 5, 8, 8, 8) and torch.isfinite(X).all()
+    one = closure.ClosureSetup(fine=32, factor=4, runs=1, snapshots=3, spinup_steps=10, substeps=1)
+    X1, Y1 = closure.make_pairs(one)
+    assert torch.equal(Y, Y1)                      # same fine run and targets
+    assert not torch.equal(X, X1)                  # a different coarse integration
+    params = init_params(2, out_scale=1.0)
+    norm = ([1.0, 0.0, 0.0, 0.0, 1.5], [0.3, 0.5, 0.5, 0.5, 0.5], [2e-3] * 5)
+    # the toggled in-step correction equals three plain substeps followed by dh_correct
+    shape = (16, 16, 32)
+    U0 = to_gpu(inputs.decaying_turbulence(shape, seed=4, sigma=0.5, mach=0.8, p_sigma=0.2), "f32")
+    a = _closure_solver(shape, params, norm)
+    b = _closure_solver(shape, params, norm)
+    a.init_state(U0)
+    b.init_state(U0)
+    for _ in range(2):
+        dt = a.compute_dt()
+        for j in range(3):
+            a.step(dt / 3)
+        a.correct()
+        for j in range(3):
+            b.correct_every_step(j == 2)
+            b.step(dt / 3)
+    assert torch.equal(a.get_state().cpu(), b.get_state().cpu())
+    r = closure.evaluate_substeps(setup, params.cuda(), norm, steps=3, seeds=(200,), frontier=(1, 3))
+    assert set(r["mean_error"]) == {"uncorrected_1", "uncorrected_3", "corrected"}
+    assert all(np.isfinite(v) and v > 0 for v in r["mean_error"].values())
+    assert r["gpu_ms_per_interval"]["uncorrected_3"] > r["gpu_ms_per_interval"]["uncorrected_1"] > 0
+    assert r["equal_gpu_time_run"] in ("uncorrected_1", "uncorrected_3")
+
+
 def test_non_finite_correction_is_reported_and_state_kept():
     import ctypes as C
     from paper_2512_13403_b300 import _lib
