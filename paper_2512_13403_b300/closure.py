@@ -452,7 +452,9 @@ class RolloutTrainer:
     """Loss and gradient of the rollout loss through the solver's hand adjoint and the network's
     VJP, for a coarse solver configuration and a network form."""
 
-    def __init__(self, shape, cfg: Config, form: str = "state", rho_floor_frac: float = 1e-6):
+    def __init__(self, shape, cfg: Config, form: str = "state", rho_floor_frac: float = 1e-6,
+                 substeps: int = 1):
+        self.substeps = int(substeps)    # equal solver steps per coarse interval
         self.shape = tuple(shape)
         self.cfg = cfg
         self.form = form
@@ -471,7 +473,8 @@ class RolloutTrainer:
             self.solver.set_forcing_modes(modes, hold=True)
 
     def loss_and_grad(self, traj: Trajectory, params, norm, weights):
-        """L = (1/S) sum_s mean(((U_s - T_s) / w)^2), U_s = C(H_s(U_{s-1})); returns (L, dL/dparams).
+        """L = (1/S) sum_s mean(((U_s - T_s) / w)^2), U_s = C(H_s(U_{s-1})), H_s the solver's
+        `substeps` equal steps over interval s; returns (L, dL/dparams).
         Every term and gradient is a library call: the loss terms and their gradients
         (dh_cnn_rollout_misfit), the floors (dh_cnn_floor_vjp), the network (dh_cnn_vjp), the
         solver step (dh_adjoint_advance_dt) and the sums (dh_axpy)."""
@@ -487,7 +490,8 @@ class RolloutTrainer:
         Us, Vs = [traj.U0], []
         for k in range(S):
             self._start(Us[-1], traj.modes[k])
-            self.solver.step(traj.dts[k])
+            for _ in range(self.substeps):
+                self.solver.step(traj.dts[k] / self.substeps, sync=False)
             V = self.solver.get_state()
             Vs.append(V)
             Un = V.clone()
@@ -504,7 +508,8 @@ class RolloutTrainer:
             axpy(1.0, self.grads, total)
             axpy(1.0, lam, gU)                   # dL/dV = (I + J_dU)^T dL/dY
             self._start(Us[k], traj.modes[k])
-            lam = self.solver.adjoint_advance(1, 1, gU, dt=traj.dts[k])
+            m = self.substeps
+            lam = self.solver.adjoint_advance(m, m, gU, dt=traj.dts[k] / m)
             if k > 0:
                 self.net.rollout_misfit(Us[k], traj.targets[k - 1], weights, coef, lam=lam,
                                         accumulate=True)
@@ -516,7 +521,7 @@ def train_rollout(trajs: List[Trajectory], setup: ClosureSetup, params, norm, it
     """Adam on the rollout loss, one trajectory per iteration (cycling).  Returns
     (params, losses, ms per iteration)."""
     nc = setup.coarse
-    tr = RolloutTrainer((nc, nc, nc), _cfg(nc, setup, 0), form)
+    tr = RolloutTrainer((nc, nc, nc), _cfg(nc, setup, 0), form, substeps=setup.substeps)
     if weights is None:
         # the per-field spread of the targets (the paper weights fields to comparable ranges)
         allt = torch.stack([t for trj in trajs for t in trj.targets]).contiguous()

@@ -135,11 +135,13 @@ def test_flux_form_one_step_backward_matches_oracle(monkeypatch):
     net.close()
 
 
-@pytest.mark.parametrize("form,floors", [("state", False), ("flux", False), ("state", True),
-                                         ("flux", True)])
-def test_rollout_gradient_matches_oracle(form, floors, monkeypatch):
-    """The rollout loss and its parameter gradient through two solver steps (hand adjoint,
-    imposed dt) and two corrections, against reverse mode of the oracle rollout.  With
+@pytest.mark.parametrize("form,floors,substeps", [("state", False, 1), ("flux", False, 1),
+                                                  ("state", True, 1), ("flux", True, 1),
+                                                  ("state", False, 2)])
+def test_rollout_gradient_matches_oracle(form, floors, substeps, monkeypatch):
+    """The rollout loss and its parameter gradient through two intervals of one or two solver
+    steps each (hand adjoint, imposed dt) and two corrections, against reverse mode of the oracle
+    rollout.  With
     `floors`, rho_floor = 0.9 <rho> and T_floor = 0.6 bind in a large share of the cells (both
     the density floor and the energy floor), and the gradient goes through them."""
     from paper_2512_13403_b300 import closure
@@ -159,13 +161,17 @@ def test_rollout_gradient_matches_oracle(form, floors, monkeypatch):
     w = [float(U0t[c].std()) for c in range(5)]
     frac = 0.9 if floors else 1e-9
     cfg = Config(shape=shape, precision="f32", t_floor=0.6 if floors else 0.05)
-    tr = closure.RolloutTrainer(shape, cfg, form, rho_floor_frac=frac)
+    tr = closure.RolloutTrainer(shape, cfg, form, rho_floor_frac=frac, substeps=substeps)
     traj = closure.Trajectory(to_gpu(U0, "f32"), dts, [None, None],
                               [t.float().cuda().contiguous() for t in targets])
     L, g = tr.loss_and_grad(traj, params.cuda(), (mu, sigma, out), w)
     tr.close()
     q = {k: v.clone().requires_grad_(True) for k, v in pd.items()}
-    steps = [lambda U, dt=dt: ohydro.rk2_step(U, dt, G, dx) for dt in dts]
+    def interval(U, dt):   # `substeps` equal solver steps per interval
+        for _ in range(substeps):
+            U = ohydro.rk2_step(U, dt / substeps, G, dx)
+        return U
+    steps = [lambda U, dt=dt: interval(U, dt) for dt in dts]
     rho_floor = frac * float(U0t[0].mean())
     Lr = oc.rollout_loss(U0t, steps, targets, q, mu, sigma, out, w, rho_floor, cfg.t_floor, G)
     Lr.backward()
