@@ -238,9 +238,11 @@ def _source_case(shape, steps, seed=3):
     return U0, dts, fields, dict(T_floor=0.05, frac=0.02, nsub_max=1024)
 
 
-@pytest.mark.parametrize("shape,n,k", [((16, 16, 16), 5, 2), ((12, 10, 20), 4, 4)])
+@pytest.mark.parametrize("shape,n,k", [((16, 16, 16), 5, 2), ((12, 10, 20), 4, 4), ((8, 8, 64), 4, 2)])
 def test_fp64_with_forcing_and_cooling_matches_oracle(shape, n, k):
-    """Adjoint through RK2, the forcing kick (field of each step fixed) and subcycled cooling."""
+    """Adjoint through RK2, the forcing kick (field of each step fixed) and subcycled cooling.
+    On the 64-wide grid the forward sweep and the replayed segment run the paired stage kernel
+    (with its staged forcing row factors and the pre-source capture)."""
     U0, dts, fields, cool = _source_case(shape, n)
     lam = np.random.default_rng(4).standard_normal((5,) + shape)
     s = solver(shape, "f64", forcing=True, ou_seed=11, cooling=True, t_floor=0.05, cool_frac=0.02)
