@@ -794,7 +794,11 @@ def corrector_leg(args):
         ps, ns, ls = closure.train(Xs, Ys, epochs=args.corr_epochs)
         del Xs, Ys
         ts1 = time.time()
-        sub_block = closure.evaluate_substeps(setup_s, ps, ns, steps=100, seeds=args.corr_eval_seeds)
+        sub_block = closure.evaluate_substeps(setup_s, ps, ns, steps=100, seeds=args.corr_substep_seeds)
+        pse = sub_block["per_seed_mean_error"]
+        sub_block["seeds_won"] = sum(1 for sd, v in pse["corrected"].items()
+                                     if v < pse[sub_block["equal_gpu_time_run"]][sd])
+        sub_block["seeds"] = len(pse["corrected"])
         sub_block.update({"train_loss": ls, "seconds": {"pairs_and_train": ts1 - ts0,
                                                         "eval": time.time() - ts1},
                           "reading": "each coarse interval (the single-step run's CFL step) is "
@@ -924,6 +928,7 @@ def main():
     ap.add_argument("--corr-runs", type=int, default=20)
     ap.add_argument("--corr-snapshots", type=int, default=100)
     ap.add_argument("--corr-epochs", type=int, default=4)
+    ap.add_argument("--corr-substep-seeds", type=int, nargs="+", default=list(range(200, 210)))
     ap.add_argument("--corr-substeps", type=int, default=3,
                     help="coarse substeps per interval of the substep closure block (1: skip it)")
     ap.add_argument("--corr-eval-seeds", type=int, nargs="+", default=[200, 201, 202, 203, 204])

@@ -296,6 +296,7 @@ def evaluate_substeps(setup: ClosureSetup, params, norm, steps: int = 100, seeds
     subs = {f"uncorrected_{m}": m for m in frontier}
     subs["corrected"] = setup.substeps
     err = {k: np.zeros(steps) for k in names}
+    per_seed = {k: {} for k in names}
     gpu_ms = {k: 0.0 for k in names}
     for seed in seeds:
         fine = Solver(_cfg(n, setup, seed))
@@ -328,7 +329,9 @@ def evaluate_substeps(setup: ClosureSetup, params, norm, steps: int = 100, seeds
                 s.time()
             ref = downsample(fine.get_state(), setup.factor)
             for name, s in runs.items():
-                err[name][k] += _rel_l2(s.get_state(), ref) / len(seeds)
+                e = _rel_l2(s.get_state(), ref)
+                err[name][k] += e / len(seeds)
+                per_seed[name][seed] = per_seed[name].get(seed, 0.0) + e / steps
         for s in list(runs.values()) + [fine, clock]:
             s.close()
     nrun = steps * len(seeds)
@@ -339,7 +342,7 @@ def evaluate_substeps(setup: ClosureSetup, params, norm, steps: int = 100, seeds
     best = min(plain, key=lambda k: mean[k])
     return {"substeps": setup.substeps, "mean_error": mean,
             "final_error": {k: float(v[-1]) for k, v in err.items()},
-            "gpu_ms_per_interval": ms, "equal_gpu_time_run": eq,
+            "per_seed_mean_error": per_seed, "gpu_ms_per_interval": ms, "equal_gpu_time_run": eq,
             "uncorrected_equal_gpu_time": mean[eq], "corrected": mean["corrected"],
             "best_uncorrected": {"run": best, "error": mean[best], "gpu_ms": ms[best]}}
 
