@@ -126,6 +126,41 @@ __device__ __forceinline__ pair_t<real> cooling_energy2(pair_t<real> r, pair_t<r
   return pmk(ca ? En.x : E.x, cb ? En.y : E.y);
 }
 
+// CFL time min_a dx_a / (|v_a| + c) of two cells (App. A.4) with cfl_time's arithmetic on both
+// lanes: the primitive recovery and the sound speed of the working precision, the same
+// operations in the same order, each lane rounded once, so each lane has cfl_time's bits (the
+// step's CFL minimum then equals that of cfl_reduce_kernel on the same state).  The pressure is
+// returned for the positivity check.
+template <typename real>
+__device__ __forceinline__ pair_t<real> cfl_time2(const pair_t<real> u[5], real gamma, real gm1, real dx,
+                                                  real dy, real dz, pair_t<real>& pres) {
+  using P = pair_t<real>;
+  P vx, vy, vz, v2;
+  if constexpr (std::is_same<real, float>::value) {
+    const P ir = pdiv(pset(1.0f), u[0]);
+    vx = pmul(u[1], ir); vy = pmul(u[2], ir); vz = pmul(u[3], ir);
+    v2 = pfma(vz, vz, padd(pmul(vx, vx), pmul(vy, vy)));
+  } else {
+    vx = pdiv(u[1], u[0]); vy = pdiv(u[2], u[0]); vz = pdiv(u[3], u[0]);
+    v2 = pfma(vz, vz, pfma(vy, vy, pmul(vx, vx)));
+  }
+  pres = pmul(pset(gm1), pfma(pmul(pset(real(-0.5)), u[0]), v2, u[4]));
+  P c;
+  const P gp = pmul(pset(gamma), pres);
+  if constexpr (std::is_same<real, float>::value) {
+    const P gpr = pmul(gp, u[0]);
+    c = pmul(gp, pmk(gpr.x > 0.0f ? rsqrtf(gpr.x) : 0.0f, gpr.y > 0.0f ? rsqrtf(gpr.y) : 0.0f));
+    c = pmk(gpr.x > 0.0f ? c.x : 0.0f, gpr.y > 0.0f ? c.y : 0.0f);
+  } else {
+    const P q = pdiv(gp, u[0]);
+    c = pmk(sqrt(q.x), sqrt(q.y));
+  }
+  const P tx = pdiv(pset(dx), padd(pmk(fabs(vx.x), fabs(vx.y)), c));
+  const P ty = pdiv(pset(dy), padd(pmk(fabs(vy.x), fabs(vy.y)), c));
+  const P tz = pdiv(pset(dz), padd(pmk(fabs(vz.x), fabs(vz.y)), c));
+  return pmin(pmin(tx, ty), tz);
+}
+
 // Bound on the probes of the staging mbarrier (a plane's copies land in microseconds); a wait
 // that reaches it sets FLAG_TIMEOUT and the CTA stops.
 constexpr uint32_t PAIR_WAIT_ITERS = 1u << 22;
@@ -436,28 +471,31 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
         if (p.cooling)
           u[4] = cooling_energy2<real>(u[0], u[1], u[2], u[3], u[4], dt, gm1, p.t_floor, p.cool_frac,
                                        p.nsub_max, flags, nsub_seen);
-        real ux[5] = {u[0].x, u[1].x, u[2].x, u[3].x, u[4].x};
-        real uy[5] = {u[0].y, u[1].y, u[2].y, u[3].y, u[4].y};
-        auto finish = [&](real* v) {
-          bool finite = true;
+        bool fa = true, fb = true;
 #pragma unroll
-          for (int c = 0; c < 5; ++c) finite = finite && isfinite(v[c]);
-          if (!finite) {
+        for (int c = 0; c < 5; ++c) {
+          fa = fa && isfinite(u[c].x);
+          fb = fb && isfinite(u[c].y);
+        }
+        P pres;
+        const P tc = cfl_time2<real>(u, gamma, gm1, p.dx, p.dy, p.dz, pres);
+        auto finish = [&](bool fin, real rho, real pr, real t, int lane) {
+          if (!fin) {
             flags |= FLAG_NONFINITE;
-          } else {
-            const real pr = gm1 * (v[4] - real(0.5) * q_div(v[1] * v[1] + v[2] * v[2] + v[3] * v[3], v[0]));
-            if (!(v[0] > real(0)) || !(pr > real(0))) flags |= FLAG_POSITIVITY;
-            if (p.reduce_cfl) {
-              tmin = fmin(tmin, cfl_time(v[0], v[1], v[2], v[3], v[4], gamma, gm1, p.dx, p.dy, p.dz));
-              if (p.cool_ratio > real(0))
-                tmin = fmin(tmin, p.cool_ratio * cooling_time(v[0], v[1], v[2], v[3], v[4], gm1, p.t_floor));
+            return;
+          }
+          if (!(rho > real(0)) || !(pr > real(0))) flags |= FLAG_POSITIVITY;
+          if (p.reduce_cfl) {
+            tmin = fmin(tmin, t);
+            if (p.cool_ratio > real(0)) {
+              const real v[5] = {lane ? u[0].y : u[0].x, lane ? u[1].y : u[1].x, lane ? u[2].y : u[2].x,
+                                 lane ? u[3].y : u[3].x, lane ? u[4].y : u[4].x};
+              tmin = fmin(tmin, p.cool_ratio * cooling_time(v[0], v[1], v[2], v[3], v[4], gm1, p.t_floor));
             }
           }
         };
-        finish(ux);
-        finish(uy);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) u[c] = pmk(ux[c], uy[c]);
+        finish(fa, u[0].x, pres.x, tc.x, 0);
+        finish(fb, u[0].y, pres.y, tc.y, 1);
       }
 #pragma unroll
       for (int c = 0; c < 5; ++c) {

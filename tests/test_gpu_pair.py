@@ -121,3 +121,20 @@ def test_paired_fallback_count(prec):
     m = s.metrics()
     assert m["flags"] == 0
     assert m["slope_fallbacks"] == 2 * nz * ny * nx // 3
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_paired_cfl_minimum_equals_cfl_reduce(prec):
+    """The CFL minimum that the paired kernel's final stage reduces (and the next step takes as
+    its dt) is bit for bit the one cfl_reduce_kernel computes from the same state: a step taken
+    after one step equals the CFL step recomputed on that state in a second context."""
+    shape = (12, 16, 64)
+    U0 = inputs.decaying_turbulence(shape, seed=8, sigma=0.5, mach=1.2, p_sigma=0.3)
+    kw = dict(forcing=True, cooling=True)
+    a = solver(shape, prec, **kw)
+    b = solver(shape, prec, **kw)
+    a.init_state(to_gpu(U0, prec))
+    b.init_state(to_gpu(U0, prec))
+    assert a.step(0.0) == b.step(0.0)
+    dt2 = a.step(0.0)               # from the first step's fused CFL reduction
+    assert b.compute_dt() == dt2    # recomputed by the stand-alone reduction on the same state
