@@ -95,8 +95,9 @@ int sm_count();
 // Planes per z chunk for a kernel whose CTAs each march one column tile through a chunk of
 // planes: the tiles x chunks CTAs run in waves of sm_count() x resident_per_sm, and the choice
 // maximises the filled fraction of the waves times zc / (zc + prologue), where `prologue` is the
-// cost of a chunk's start in planes.  Chunks hold at least 8 planes (all nz if nz < 16).
-int wave_zchunk(long long tiles, int nz, int resident_per_sm, double prologue);
+// cost of a chunk's start in planes.  Chunks hold at least `min_planes` planes (all nz if nz <
+// 2 min_planes).
+int wave_zchunk(long long tiles, int nz, int resident_per_sm, double prologue, int min_planes = 8);
 
 // Adjoint of one RK2 stage (adjoint.cu):
 //   lam_in = c1 * lam_out + c2 * extra + (dL/dU)^T (beta * dt * lam_out),  L the unsplit RHS at U.

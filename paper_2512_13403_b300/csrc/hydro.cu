@@ -568,11 +568,12 @@ int sm_count() {
   return n;
 }
 
-int wave_zchunk(long long tiles, int nz, int resident_per_sm, double prologue) {
+int wave_zchunk(long long tiles, int nz, int resident_per_sm, double prologue, int min_planes) {
   const long long slots = (long long)sm_count() * (resident_per_sm > 0 ? resident_per_sm : 1);
   int best = nz;
   double bestv = -1.0;
-  const int cmax = nz / 8 > 1 ? nz / 8 : 1;
+  const int mp = min_planes > 0 ? min_planes : 1;
+  const int cmax = nz / mp > 1 ? nz / mp : 1;
   for (int c = 1; c <= cmax; ++c) {
     const int zc = (nz + c - 1) / c;
     const int chunks = (nz + zc - 1) / zc;

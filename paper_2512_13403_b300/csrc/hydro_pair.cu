@@ -630,7 +630,9 @@ static cudaError_t launch_pair_t(const StageArgs<real>& a, const StageTma& maps,
     if (resident <= 0) resident = 1;
   }
   const long long tiles = (long long)(a.nx / QCX) * (a.ny / QY);
-  const int zc = wave_zchunk(tiles, a.nz, resident, 1.5);
+  // small grids fill the GPU with short chunks (down to two planes); a chunk's start costs
+  // about two planes (three planes loaded and converted, and the trailing half iteration)
+  const int zc = wave_zchunk(tiles, a.nz, resident, 2.0, 2);
   dim3 grid(a.nx / QCX, a.ny / QY, (a.nz + zc - 1) / zc);
   kernel<<<grid, QNT, smem, s>>>(a, zc, maps);
   return cudaGetLastError();
