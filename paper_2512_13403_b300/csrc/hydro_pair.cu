@@ -199,9 +199,19 @@ __device__ __forceinline__ Prim2<real> gload_pair(const real* __restrict__ U, lo
 // rows -1 and 8 (warps 0 and 1), the x slopes of positions -1 and 32 (warp 2, lanes 0..15), the
 // x face 32 of each row (warp 6, lanes 0..7) and the y face 8 of each position (warp 7).
 // float32: two CTAs per SM (shared memory and 128 registers); float64: one.
+// Per-field base pointers of the stage's state buffers, read from the parameter bank, so that a
+// cell's address is one 32-bit index scaled onto a constant base (grids below 2^31 cells per field).
+template <typename real> struct FieldPtrs {
+  const real* U[5];
+  const real* U0[5];
+  real* out[5];
+  real* pre[5];
+};
+
 template <typename real, int STAGE, int LIM>
 __global__ void __launch_bounds__(QNT, sizeof(real) == 4 ? 2 : 1)
-stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_constant__ StageTma tma) {
+stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_constant__ StageTma tma,
+                  const __grid_constant__ FieldPtrs<real> fp) {
   using P = pair_t<real>;
   using Q = Quad<real>;
   using ST = PairStaging<real>;
@@ -368,12 +378,12 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
     // x/y divergence of plane k-1 from its face fluxes (written last iteration)
     // the own cells' U (and U0) of plane k-1, loaded early for its update below
     P uin_e[5], un_e[5];
+    const int ia32 = (k - 1) * (int)plane + (int)col;
     if (k > z0) {
-      const long long ia = (long long)(k - 1) * plane + col, ib = ia + QX;
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        uin_e[c] = pmk(__ldg(p.U + c * n3 + ia), __ldg(p.U + c * n3 + ib));
-        if (COMB) un_e[c] = pmk(__ldg(p.U0 + c * n3 + ia), __ldg(p.U0 + c * n3 + ib));
+        uin_e[c] = pmk(__ldg(fp.U[c] + ia32), __ldg(fp.U[c] + ia32 + QX));
+        if (COMB) un_e[c] = pmk(__ldg(fp.U0[c] + ia32), __ldg(fp.U0[c] + ia32 + QX));
       }
     }
     P lxy[5];
@@ -430,7 +440,6 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
 
     // plane k-1 is complete: stage combination, epilogue, store
     if (k > z0) {
-      const long long ia = (long long)(k - 1) * plane + col, ib = ia + QX;
       P u[5];
       const P miz = pset(-p.idz), pdt = pset(dt);
 #pragma unroll
@@ -448,8 +457,8 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
         if (p.pre_src) {
 #pragma unroll
           for (int c = 0; c < 5; ++c) {
-            p.pre_src[c * n3 + ia] = u[c].x;
-            p.pre_src[c * n3 + ib] = u[c].y;
+            fp.pre[c][ia32] = u[c].x;
+            fp.pre[c][ia32 + QX] = u[c].y;
           }
         }
         if (forcing) {
@@ -499,8 +508,8 @@ stage_pair_kernel(const StageArgs<real> p, const int zchunk, const __grid_consta
       }
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        p.out[c * n3 + ia] = u[c].x;
-        p.out[c * n3 + ib] = u[c].y;
+        fp.out[c][ia32] = u[c].x;
+        fp.out[c][ia32 + QX] = u[c].y;
       }
     }
     if (last) break;
@@ -634,7 +643,15 @@ static cudaError_t launch_pair_t(const StageArgs<real>& a, const StageTma& maps,
   // about two planes (three planes loaded and converted, and the trailing half iteration)
   const int zc = wave_zchunk(tiles, a.nz, resident, 2.0, 2);
   dim3 grid(a.nx / QCX, a.ny / QY, (a.nz + zc - 1) / zc);
-  kernel<<<grid, QNT, smem, s>>>(a, zc, maps);
+  FieldPtrs<real> fp;
+  for (int c = 0; c < 5; ++c) {
+    const long long off = (long long)c * a.nx * a.ny * a.nz;
+    fp.U[c] = a.U + off;
+    fp.U0[c] = a.U0 ? a.U0 + off : nullptr;
+    fp.out[c] = a.out + off;
+    fp.pre[c] = a.pre_src ? a.pre_src + off : nullptr;
+  }
+  kernel<<<grid, QNT, smem, s>>>(a, zc, maps, fp);
   return cudaGetLastError();
 }
 
@@ -642,7 +659,8 @@ template <typename real>
 bool launch_stage_pair(int stage, const StageArgs<real>& a, cudaStream_t s, cudaError_t& err, int& launched) {
   launched = 0;
   // whole 64 x 8 tiles (every halo box contiguous), at least four planes, a 16-byte aligned base
-  if (a.nx % QCX != 0 || a.ny % QY != 0 || a.nz < 4 || ((unsigned long long)a.U & 15ull) != 0)
+  if (a.nx % QCX != 0 || a.ny % QY != 0 || a.nz < 4 || ((unsigned long long)a.U & 15ull) != 0 ||
+      (long long)a.nx * a.ny * a.nz >= (1ll << 31))
     return false;
   const bool final = stage == 2 || (stage == 3 && a.final_stage);
   if (final && a.forcing && (!a.frow || ((unsigned long long)a.frow & 15ull) != 0)) return false;
