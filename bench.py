@@ -42,7 +42,7 @@ NCU_COUNTERS = {
     # one launch at 256^3: ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
     # smsp__inst_executed.sum (the profile named here gives the command)
     "stage2": {"sources": ['hydro.cu', 'hydro_pair.cu', 'dh_device.cuh', 'dh_pair.cuh', 'dh_sources.cuh', 'tma.cuh', 'tc_ptx.cuh'],
-               "hash": "d1ce388b1af64095", "dram_bytes": 1037174016, "warp_instr": 445364864,
+               "hash": "48137736be689513", "dram_bytes": 1035561216, "warp_instr": 430815872,
                "profile": "profiles/stage_kernels_driven_cooling_turbulence_256cubed.md"},
     # averaged over the kernel's two launches per RK2 step
     "adjoint": {"sources": ['adjoint.cu', 'dh_adjoint.cuh', 'dh_device.cuh', 'dh_sources.cuh', 'async_copy.cuh', 'tma.cuh', 'tc_ptx.cuh'],
