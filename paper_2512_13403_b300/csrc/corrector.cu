@@ -707,29 +707,30 @@ conv3d_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ act, const __nv_bfloat1
   }
 }
 
-// dW[n][c][tap] (master layout) = sum over CTAs, in CTA order, of
-// partial[cta][tap * cin_pad + c][n].  Consecutive threads take consecutive n, so the reads of
-// one CTA's partials are contiguous.
-__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int nctas, int mt, int nout_pad,
-                                    int cin_pad, int cout, int cin, float* __restrict__ dW) {
-  const int total = cout * cin * 27;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const int n = idx % cout, mm = idx / cout;
-    const int c = mm % cin, tap = mm / cin;
-    const int m = tap * cin_pad + c;
-    const long long stride = (long long)mt * 128 * nout_pad;
-    const float* p = partial + (long long)m * nout_pad + n;
-    // four interleaved accumulators (CTA b into b % 4), combined in a fixed order
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int b = 0;
-    for (; b + 3 < nctas; b += 4) {
-      s0 += (double)p[b * stride];
-      s1 += (double)p[(b + 1) * stride];
-      s2 += (double)p[(b + 2) * stride];
-      s3 += (double)p[(b + 3) * stride];
-    }
-    for (; b < nctas; ++b) s0 += (double)p[b * stride];
-    dW[((long long)n * cin + c) * 27 + tap] = (float)((s0 + s1) + (s2 + s3));
+// dW[n][c][tap] (master layout) = sum over the CTAs b of partial[b][tap * cin_pad + c][n], in a
+// fixed order: warp w of the block adds b = w, w + 8, w + 16, ... in increasing b (float64), and
+// the eight warp sums are combined as ((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7)).  One
+// block per (c, tap); lane n reads element n of each CTA's row, so a warp's loads are contiguous,
+// and the CTAs' rows are read by eight warps at once.
+constexpr int WR_WARPS = 8;
+__global__ void __launch_bounds__(32 * WR_WARPS)
+wgrad_reduce_kernel(const float* __restrict__ partial, int nctas, long long stride, int nout_pad,
+                    int cin_pad, int cout, int cin, float* __restrict__ dW) {
+  __shared__ double red[WR_WARPS][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x % cin, tap = blockIdx.x / cin;
+  double s = 0.0;
+  if (lane < cout) {
+    const float* p = partial + (long long)(tap * cin_pad + c) * nout_pad + lane;
+#pragma unroll 4
+    for (int b = warp; b < nctas; b += WR_WARPS) s += (double)__ldg(p + b * stride);
+  }
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && lane < cout) {
+    const double r = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+                     ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
+    dW[((long long)lane * cin + c) * 27 + tap] = (float)r;
   }
 }
 
@@ -774,8 +775,8 @@ extern "C" dh_status dh_conv3d_wgrad_bf16(const void* act, int cin_pad, int cin,
   else if (cin_pad == 8 && nout_pad == 16) e = launch_wgrad<8, 16>(a, gg, grad_stride, nx, ny, nz, nctas, partial, err_flag, s);
   else return DH_ERR_ARG;
   if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
-  wgrad_reduce_kernel<<<(cout * cin * 27 + 255) / 256, 256, 0, s>>>(partial, nctas, mt, nout_pad,
-                                                                    cin_pad, cout, cin, dW);
+  wgrad_reduce_kernel<<<cin * 27, 32 * WR_WARPS, 0, s>>>(partial, nctas, (long long)mt * 128 * nout_pad,
+                                                         nout_pad, cin_pad, cout, cin, dW);
   e = cudaGetLastError();
   if (e != cudaSuccess) { dh_set_global_error(cudaGetErrorString(e)); return DH_ERR_CUDA; }
   return DH_OK;
