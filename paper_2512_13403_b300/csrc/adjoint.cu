@@ -310,13 +310,14 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk,
   const int mu_gown = S.ys[ty + 3] * nx + S.xs[tx + 3];
   const int mu_sown = (ty + 2) * MXH + tx + 2;
 
+  // (returns the own cell's primitives, which the z pipeline uses as well)
   auto convert_plane = [&](int slot) {
-    {
-      const real* c0 = &S.core[0][ty][tx];
-      const Prim<real> w = cons_to_prim(c0[0], c0[ABY * ABX], c0[2 * ABY * ABX], c0[3 * ABY * ABX],
+    const real* c0 = &S.core[0][ty][tx];
+    const Prim<real> own = cons_to_prim(c0[0], c0[ABY * ABX], c0[2 * ABY * ABX], c0[3 * ABY * ABX],
                                         c0[4 * ABY * ABX], gm1);
+    {
       real* d = &S.w[slot][0][0][0] + ring_own;
-      d[0] = w.r; d[RFS] = w.vx; d[2 * RFS] = w.vy; d[3 * RFS] = w.vz; d[4 * RFS] = w.p;
+      d[0] = own.r; d[RFS] = own.vx; d[2 * RFS] = own.vy; d[3 * RFS] = own.vz; d[4 * RFS] = own.p;
     }
     if (cv_src >= 0) {
       const real* src = &S.core[0][0][0] + cv_src;
@@ -325,6 +326,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk,
       real* d = &S.w[slot][0][0][0] + (cv_ring_fs & 0xffff);
       d[0] = w.r; d[RFS] = w.vx; d[2 * RFS] = w.vy; d[3 * RFS] = w.vz; d[4 * RFS] = w.p;
     }
+    return own;
   };
   // cp.async of lam_out of plane k (x/y halo 2) into mu (one commit group)
   auto load_mu = [&](int k) {
@@ -468,7 +470,7 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk,
                                : (it == 1 ? NSXP + (ty + 2) * ABX + tx : (sl_pack >> 10) & 0x3ff);
       slope_item(s0, ring, step, item);
     }
-    convert_plane(s3);
+    const Prim<real> w3 = convert_plane(s3);   // own cell of plane k+3
 
     real gW[5];
     Prim<real> wk;   // own cell of plane k, kept for the primitive-recovery step
@@ -477,9 +479,6 @@ stage_adjoint_kernel(const AdjointArgs<real> p, const int zchunk,
       wk = ring_prim(S, s0, ty + 3, tx + 3);
       const Prim<real> w1 = ring_prim(S, s1, ty + 3, tx + 3);
       const Prim<real> w2 = ring_prim(S, s2, ty + 3, tx + 3);
-      const real* c3 = &S.core[0][ty][tx];   // this thread's cell of plane k+3
-      const Prim<real> w3 = cons_to_prim(c3[0], c3[ABY * ABX], c3[2 * ABY * ABX], c3[3 * ABY * ABX],
-                                         c3[4 * ABY * ABX], gm1);
       const Prim<real> dz2 = limited_slope<LIM>(w1, w2, w3);
       real g[5], gL2[5], gR2[5], D[5], An[5], Bn[5];
       for (int c = 0; c < 5; ++c) g[c] = (mun2[c] - mun[c]) * gfz;
