@@ -244,6 +244,8 @@ __global__ void bias_grad_partial_kernel(const __nv_bfloat16* __restrict__ grad,
   const long long q0 = blockIdx.x * per, q1 = q0 + per < n ? q0 + per : n;
   const uint4* rows = reinterpret_cast<const uint4*>(grad) + (long long)grp * g.rows;
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // (unrolled so that several rows are in flight; the sums keep their order)
+#pragma unroll 4
   for (long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
     int x, y, z;
     cell_xyz(q, g, x, y, z);
@@ -269,6 +271,7 @@ __global__ void bias_grad_final_kernel(const double* __restrict__ part, int nb, 
   const int c = threadIdx.x;
   if (c < nch) {
     double s = 0.0;
+#pragma unroll 8
     for (int b = 0; b < nb; ++b) s += part[(long long)c * nb + b];
     db[c] = (float)s;
   }
