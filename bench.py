@@ -46,7 +46,7 @@ NCU_COUNTERS = {
                "profile": "profiles/stage_kernels_driven_cooling_turbulence_256cubed.md"},
     # averaged over the kernel's two launches per RK2 step
     "adjoint": {"sources": ['adjoint.cu', 'dh_adjoint.cuh', 'dh_device.cuh', 'dh_sources.cuh', 'async_copy.cuh', 'tma.cuh', 'tc_ptx.cuh'],
-                "hash": "6ea412ed56f026cd", "dram_bytes": 1201695872,
+                "hash": "854e44dff4a2dddf", "dram_bytes": 1201818880,
                 "warp_instr": 1418102895,
                 "profile": "profiles/stage_adjoint_kernel_decaying_turbulence_128cubed.md"},
 }
