@@ -249,6 +249,50 @@ def test_weight_gradient(cin, cout, shape):
     assert float((got - ref).norm() / ref.norm()) < 1e-5
 
 
+@pytest.mark.parametrize("cin,cout,nctas", [(32, 32, 148), (5, 32, 37), (32, 5, 9)])
+def test_weight_gradient_reduction_order(cin, cout, nctas):
+    """The per-CTA partials are added in the documented fixed order: warp w of a (channel, tap)
+    block sums the CTAs b = w, w + 8, ... in increasing b in float64, and the eight sums combine
+    as ((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7)); the float32 result is checked bit for bit
+    against that sum of the partials the kernel left in the scratch buffer."""
+    lib = _lib.load()
+    shape = (6, 8, 16)
+    nz, ny, nx = shape
+    cin_pad, g_stride = (8 if cin <= 8 else 32), (8 if cout <= 8 else 32)
+    g = torch.Generator().manual_seed(11)
+    x = oc.bf16(torch.randn((cin,) + shape, generator=g, dtype=torch.float64))
+    gr = oc.bf16(torch.randn((cout,) + shape, generator=g, dtype=torch.float64))
+    mt = (27 * cin_pad + 127) // 128
+    nout_pad = 32 if cout > 16 else 16
+    partial = torch.empty(nctas * mt * 128 * nout_pad, dtype=torch.float32, device="cuda")
+    dW = torch.empty(cout * cin * 27, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    a_dev, g_dev = _act(x, cin_pad), _act(gr, g_stride)
+    st = lib.dh_conv3d_wgrad_bf16(_ptr(a_dev), cin_pad, cin, _ptr(g_dev), g_stride, cout, nx, ny, nz,
+                                  _ptr(partial), nctas, _ptr(dW), _ptr(err), None)
+    assert st == 0, lib.dh_last_error(None)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    P = partial.cpu().numpy().astype(np.float64).reshape(nctas, mt * 128, nout_pad)
+    expect = np.empty((cout, cin, 27), dtype=np.float32)
+    for tap in range(27):
+        for c in range(cin):
+            row = P[:, tap * cin_pad + c, :cout]
+            s = []
+            for w in range(8):
+                acc = np.zeros(cout)
+                for b in range(w, nctas, 8):
+                    acc = acc + row[b]
+                s.append(acc)
+            r = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]))
+            expect[:, c, tap] = r.astype(np.float32)
+    got = dW.cpu().numpy().reshape(cout, cin, 27)
+    assert np.array_equal(got.view(np.uint32), expect.view(np.uint32))
+    # and the sum is the weight gradient
+    ref = oc.conv3d_weight_grad(x, gr, cout)
+    assert float((torch.from_numpy(got).double().reshape(ref.shape) - ref).norm() / ref.norm()) < 1e-5
+
+
 def _net_params(seed):
     from paper_2512_13403_b300 import corrector as cr
     p = cr.init_params(seed, out_scale=1.0)
