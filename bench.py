@@ -311,6 +311,20 @@ def run_ours(args):
         s2.get_state(host_out)
         e2e_s = time.perf_counter() - t0
         s2.close()
+        # the host link alone, outside the timed region: one pinned upload and one download of
+        # the state, by CUDA events on the same stream
+        link = {}
+        dev = torch.empty_like(Ud)
+        for name, dst, src in (("h2d", dev, host_in), ("d2h", host_out, dev)):
+            l0 = torch.cuda.Event(enable_timing=True)
+            l1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                l0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                l1.record(stream)
+            stream.synchronize()
+            link[name + "_GBps"] = src.numel() * src.element_size() / (l0.elapsed_time(l1) * 1e-3) / 1e9
+        del dev
 
     cells = n ** 3
     ms_max, e2e_max, value, e2e_value = aggregate_replicas(ms, e2e_s, ws, cells, args.steps, "cuda")
@@ -348,7 +362,8 @@ def run_ours(args):
                                  "avg_ms": prof["prologue"][1] / max(prof["prologue"][0], 1)}},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes / args.steps,
-                "d2h_bytes_per_step": 40 + state_bytes / args.steps},
+                "d2h_bytes_per_step": 40 + state_bytes / args.steps,
+                "host_link": link},
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
     }
