@@ -25,6 +25,7 @@
 
 #include "async_copy.cuh"
 #include "dh_internal.h"
+#include "dh_pair_sources.cuh"
 #include "dh_sources.cuh"
 #include "ff.cuh"
 
@@ -1590,6 +1591,180 @@ gravity_sources_kernel(real* __restrict__ U, const float* __restrict__ phi, int 
   }
 }
 
+// The same sources for two cells per thread, 32 apart in x (grids whose rows are whole multiples
+// of 64 cells): a CTA owns a 64 x 8 column and marches GS_ZC planes, and every quantity is a
+// two-lane pair, so the forcing and gravity kicks, the cooling and the CFL time run as packed
+// FP32x2 arithmetic.  The cooling and CFL time have the scalar functions' roundings per lane;
+// the checks are those of the paired stage kernel.  The potential gradient of the plane is
+// evaluated before the next plane's words are requested, so that only one plane of words is
+// held in registers.
+constexpr int GP_QX = 32, GP_TY = 8, GP_NF = GP_TY * 9;
+
+template <typename real>
+__global__ void __launch_bounds__(256)
+gravity_sources_pair_kernel(real* __restrict__ U, const float* __restrict__ phi, int nx, int ny,
+                            int nz, real i2h, StepRecord* rec, const double* dtp, int in_step,
+                            int forcing, const real* __restrict__ ah, const real* tw0,
+                            const real* tw1, const real* tw2, int cooling, real gamma, real gm1,
+                            real t_floor, real frac, int nsub_max, real dx, real dy, real dz,
+                            real cool_ratio) {
+  using P = pair_t<real>;
+  __shared__ unsigned s_skip;
+  __shared__ real red[8];
+  __shared__ real fB[2][GP_TY][3][3][2];   // double-buffered by plane parity
+  __shared__ real s_ah[96], s_ty[GP_TY][4], s_tz[GS_ZC][4];
+  const int tid = threadIdx.x;
+  const int z0 = blockIdx.z * GS_ZC, z1 = z0 + GS_ZC < nz ? z0 + GS_ZC : nz;
+  if (tid == 0) s_skip = *((volatile unsigned*)&rec->flags) & FATAL_FLAGS;
+  if (forcing) {
+    if (tid < 96) s_ah[tid] = __ldg(ah + tid);
+    if (tid >= 96 && tid < 96 + 4 * GP_TY) {
+      const int ly = (tid - 96) >> 2, q = (tid - 96) & 3;
+      s_ty[ly][q] = __ldg(tw1 + 4 * ((blockIdx.y * GP_TY + ly) % ny) + q);
+    }
+    if (tid >= 128 && tid < 128 + 4 * GS_ZC) {
+      const int lz = (tid - 128) >> 2, q = (tid - 128) & 3;
+      if (z0 + lz < nz) s_tz[lz][q] = __ldg(tw2 + 4 * (z0 + lz) + q);
+    }
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const real dt = (real)*dtp;
+  const long long plane = (long long)nx * ny;
+  const long long n3 = plane * nz;
+  const int tx = tid % GP_QX, ty = tid / GP_QX;
+  const int ia = blockIdx.x * (2 * GP_QX) + tx, ib = ia + GP_QX;
+  const int j = blockIdx.y * GP_TY + ty;
+  const bool active = j < ny;
+  P twx[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) twx[q] = pset(real(0));
+  if (forcing && active) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) twx[q] = pmk(__ldg(tw0 + 4 * ia + q), __ldg(tw0 + 4 * ib + q));
+  }
+  real tmin = real(INFINITY);
+  unsigned flags = 0;
+  int nsub_seen = 0;
+  const P pdt = pset(dt);
+  // the state and potential words of the next plane are loaded a plane ahead
+  P un[5];
+  float pva[12], pvb[12];
+  if (active) {
+    const long long q = (long long)z0 * plane + (long long)j * nx + ia;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) un[c] = pmk(U[c * n3 + q], U[c * n3 + q + GP_QX]);
+    potential_gradient_load(phi, nx, ny, nz, ia, j, z0, pva);
+    potential_gradient_load(phi, nx, ny, nz, ib, j, z0, pvb);
+  }
+  for (int k = z0; k < z1; ++k) {
+    const int buf = (k - z0) & 1;
+    if (forcing) {
+      if (tid < GP_NF) {
+        const int ly = tid / 9, rem = tid - 9 * ly;
+        const int nxsel = rem / 3, c = rem - 3 * nxsel;
+        real tyv[4], tzv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          tyv[q] = s_ty[ly][q];
+          tzv[q] = s_tz[k - z0][q];
+        }
+        real bre = real(0), bim = real(0);
+        row_factor<real, 0>(s_ah, nxsel, c, tyv, tzv, bre, bim);
+        fB[buf][ly][nxsel][c][0] = bre;
+        fB[buf][ly][nxsel][c][1] = bim;
+      }
+      __syncthreads();   // one barrier per plane: the other buffer is rewritten a plane later
+    }
+    if (!active) continue;
+    const long long q = (long long)k * plane + (long long)j * nx + ia;
+    // g = -grad phi by central differences (Sec. 5) of this plane, then the next plane's loads
+    real ga0, ga1, ga2, gb0, gb1, gb2;
+    potential_gradient_eval(pva, i2h, ga0, ga1, ga2);
+    potential_gradient_eval(pvb, i2h, gb0, gb1, gb2);
+    P u[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) u[c] = un[c];
+    if (k + 1 < z1) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) un[c] = pmk(U[c * n3 + q + plane], U[c * n3 + q + plane + GP_QX]);
+      potential_gradient_load(phi, nx, ny, nz, ia, j, k + 1, pva);
+      potential_gradient_load(phi, nx, ny, nz, ib, j, k + 1, pvb);
+    }
+    if (forcing) {
+      // a = 2 Re sum_{n_x} B_{n_x} exp(2 pi i n_x x~)  (Sec. 3.1.1)
+      const real(*B)[3][2] = fB[buf][ty];
+      P a[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const P t1 = pfma(pset(B[1][c][0]), twx[0], pmul(pset(-B[1][c][1]), twx[1]));
+        const P t2 = pfma(pset(B[2][c][0]), twx[2], pmul(pset(-B[2][c][1]), twx[3]));
+        a[c] = pmul(pset(real(2)), padd(padd(pset(B[0][c][0]), t1), t2));
+      }
+      const P e = pmul(pfma(u[3], a[2], pfma(u[2], a[1], pmul(u[1], a[0]))), pdt);
+      u[1] = pfma(pmul(u[0], a[0]), pdt, u[1]);
+      u[2] = pfma(pmul(u[0], a[1]), pdt, u[2]);
+      u[3] = pfma(pmul(u[0], a[2]), pdt, u[3]);
+      u[4] = padd(u[4], e);
+    }
+    {
+      // the gravity kick, momentum taken before the kick
+      const P g0 = pmk(ga0, gb0), g1 = pmk(ga1, gb1), g2 = pmk(ga2, gb2);
+      const P e = pmul(pfma(u[3], g2, pfma(u[2], g1, pmul(u[1], g0))), pdt);
+      u[1] = pfma(pmul(u[0], g0), pdt, u[1]);
+      u[2] = pfma(pmul(u[0], g1), pdt, u[2]);
+      u[3] = pfma(pmul(u[0], g2), pdt, u[3]);
+      u[4] = padd(u[4], e);
+    }
+    if (cooling)
+      u[4] = cooling_energy2<real>(u[0], u[1], u[2], u[3], u[4], dt, gm1, t_floor, frac, nsub_max,
+                                   flags, nsub_seen);
+    bool fa = true, fb = true;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      fa = fa && isfinite(u[c].x);
+      fb = fb && isfinite(u[c].y);
+    }
+    P pres;
+    const P tc = cfl_time2<real>(u, gamma, gm1, dx, dy, dz, pres);
+    auto finish = [&](bool fin, real rho, real pr, real t, int lane) {
+      if (!fin) {
+        flags |= FLAG_NONFINITE;
+        return;
+      }
+      if (!(rho > real(0)) || !(pr > real(0))) flags |= FLAG_POSITIVITY;
+      tmin = fmin(tmin, t);
+      if (cool_ratio > real(0)) {
+        const real v[5] = {lane ? u[0].y : u[0].x, lane ? u[1].y : u[1].x, lane ? u[2].y : u[2].x,
+                           lane ? u[3].y : u[3].x, lane ? u[4].y : u[4].x};
+        tmin = fmin(tmin, cool_ratio * cooling_time(v[0], v[1], v[2], v[3], v[4], gm1, t_floor));
+      }
+    };
+    finish(fa, u[0].x, pres.x, tc.x, 0);
+    finish(fb, u[0].y, pres.y, tc.y, 1);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      U[c * n3 + q] = u[c].x;
+      U[c * n3 + q + GP_QX] = u[c].y;
+    }
+  }
+  if (!in_step) return;   // a replay (adjoint) leaves the step record alone
+  if (flags) {
+    atomicOr(&rec->flags, flags);
+    if (flags & FATAL_FLAGS) atomicCAS(&rec->fail_step, -1, (int)(rec->nstep - 1));
+  }
+  if (nsub_seen > 1) atomicMax(&rec->cool_nsub_max, nsub_seen);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+  if ((tid & 31) == 0) red[tid >> 5] = tmin;
+  __syncthreads();
+  if (tid == 0) {
+    real m = red[0];
+    for (int w = 1; w < 8; ++w) m = fmin(m, red[w]);
+    if (m < real(INFINITY)) atomicMin(&rec->cfl_min_bits, ordered_bits(m));
+  }
+}
+
 template <typename real>
 cudaError_t gravity_sources(dh_ctx* c, void* Ustar, const void* tab, const double* dtp,
                             bool in_step) {
@@ -1599,14 +1774,26 @@ cudaError_t gravity_sources(dh_ctx* c, void* Ustar, const void* tab, const doubl
   cudaError_t e = mg_solve<real>(c, U, in_step);
   if (e != cudaSuccess) return e;
   prof_begin(c, DH_KERNEL_SOURCES);
+  const real cool_ratio = g.cooling && std::isfinite(g.c_cool) ? (real)(g.c_cool / g.cfl) : real(0);
+  if (std::is_same<real, float>::value && g.nx % (2 * GP_QX) == 0) {
+    // two cells per thread (float32, rows of whole 64-cell multiples)
+    const dim3 grid(g.nx / (2 * GP_QX), (g.ny + GP_TY - 1) / GP_TY, (g.nz + GS_ZC - 1) / GS_ZC);
+    gravity_sources_pair_kernel<real><<<grid, 256, 0, c->stream>>>(
+        U, c->mg->phi, g.nx, g.ny, g.nz, (real)(1.0 / (2.0 * g.dx)), c->rec, dtp, in_step ? 1 : 0,
+        g.forcing, (const real*)(tab ? tab : c->ahat_norm), (const real*)c->tw[0],
+        (const real*)c->tw[1], (const real*)c->tw[2], g.cooling, (real)g.gamma,
+        (real)(g.gamma - 1.0), (real)g.t_floor, (real)g.cool_frac, g.nsub_max, (real)g.dx,
+        (real)g.dy, (real)g.dz, cool_ratio);
+    prof_end(c, 1);
+    return cudaGetLastError();
+  }
   const dim3 grid((g.nx + GS_TX - 1) / GS_TX, (g.ny + GS_TY - 1) / GS_TY, (g.nz + GS_ZC - 1) / GS_ZC);
   gravity_sources_kernel<real><<<grid, 256, 0, c->stream>>>(
       U, c->mg->phi, g.nx, g.ny, g.nz, (real)(1.0 / (2.0 * g.dx)), c->rec, dtp, in_step ? 1 : 0,
       g.forcing, (const real*)(tab ? tab : c->ahat_norm), (const real*)c->tw[0],
       (const real*)c->tw[1], (const real*)c->tw[2], g.cooling, (real)g.gamma,
       (real)(g.gamma - 1.0), (real)g.t_floor, (real)g.cool_frac, g.nsub_max, (real)g.dx,
-      (real)g.dy, (real)g.dz,
-      g.cooling && std::isfinite(g.c_cool) ? (real)(g.c_cool / g.cfl) : real(0));
+      (real)g.dy, (real)g.dz, cool_ratio);
   prof_end(c, 1);
   return cudaGetLastError();
 }

@@ -93,13 +93,17 @@ def test_gravity_step_fp64_vs_oracle(smoother, cycle_type):
     assert max(rel_linf(s.get_state(), sim.U)) <= 1e-11
 
 
-def test_self_gravitating_cooling_turbulence_fp32_vs_oracle():
+@pytest.mark.parametrize("shape", [(32, 32, 32), (8, 12, 64)])
+def test_self_gravitating_cooling_turbulence_fp32_vs_oracle(shape):
     """All sources together (forcing, gravity, cooling).  Both sides solve the Poisson problem
     to 1e-10 so that the comparison sees float32 rounding, not two different 1e-6 iterates
-    (the default tolerance is covered by test_default_tolerance_fp32_residual_and_cycles)."""
-    shape = (32, 32, 32)
+    (the default tolerance is covered by test_default_tolerance_fp32_residual_and_cycles).
+    Rows of 64 cells take the two-cells-per-thread source kernel, with a ragged last row
+    block (12 rows in blocks of 8)."""
     U0 = inputs.self_gravitating_box(shape, seed=5, sigma=1.0)
-    kw = dict(forcing=True, cooling=True, gravity=True, mg_tol=1e-10, mg_max_cycles=60)
+    h = 1.0 / shape[2]   # cubic cells (gravity needs them) on non-cubic grids
+    kw = dict(forcing=True, cooling=True, gravity=True, mg_tol=1e-10, mg_max_cycles=60,
+              dx=(h, h, h))
     sim = odrv.Simulation(odrv.Config(shape=shape, **kw), U0)
     s = solver(shape, "f32", **kw)
     s.init_state(to_gpu(U0, "f32"))
@@ -110,15 +114,18 @@ def test_self_gravitating_cooling_turbulence_fp32_vs_oracle():
     assert max(err) < 1e-4, err
 
 
-def test_smooth_self_gravitating_fp32_50_steps_every_field():
+@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 16, 64)])
+def test_smooth_self_gravitating_fp32_50_steps_every_field(shape):
     """The float32 production path with every source (OU forcing, multigrid gravity, cooling)
     on a smooth self-gravitating state (lognormal density, sigma = 0.3) over 50 steps: each
     field within 1e-5 relative L1 of the float64 oracle on its own scale.  Both sides solve the
     Poisson problem to 1e-10, so the comparison sees float32 rounding, not two iterates that
-    each stop somewhere within a loose tolerance."""
-    shape = (32, 32, 32)
+    each stop somewhere within a loose tolerance.  Rows of 64 cells take the two-cells-per-thread
+    source kernel (and the paired stage kernel)."""
     U0 = inputs.self_gravitating_box(shape, seed=5, sigma=0.3)
-    kw = dict(forcing=True, cooling=True, gravity=True, mg_tol=1e-10, mg_max_cycles=60)
+    h = 1.0 / shape[2]   # cubic cells (gravity needs them) on non-cubic grids
+    kw = dict(forcing=True, cooling=True, gravity=True, mg_tol=1e-10, mg_max_cycles=60,
+              dx=(h, h, h))
     sim = odrv.Simulation(odrv.Config(shape=shape, **kw), U0)
     s = solver(shape, "f32", **kw)
     s.init_state(to_gpu(U0, "f32"))
