@@ -775,6 +775,166 @@ residual_zm_kernel(const float* __restrict__ phi, float* __restrict__ phi_out,
     partials[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = red[0];
 }
 
+// The same residual for two cells per thread, 32 apart in x, on rows of whole 64-cell
+// multiples: a CTA owns a 64 x 8 column, and the float-float Laplacian and residual run as packed
+// FP32x2 pairs with the scalar kernel's operations per lane (so r matches it cell for cell; the
+// norm's partial sums are grouped per CTA of this kernel, in a fixed order).
+constexpr int RP_QX = 32, RP_HX = 2 * RP_QX + 2, RP_H = RP_HX * RZ_HY;
+static_assert(RP_H <= 3 * 256, "three halo positions per thread");
+inline long long residual_pair_blocks(int nx, int ny, int nz) {
+  return (long long)(nx / (2 * RP_QX)) * ((ny + RZ_TY - 1) / RZ_TY) * ((nz + RZ_ZC - 1) / RZ_ZC);
+}
+
+struct ffp {
+  float2 hi, lo;
+};
+__device__ __forceinline__ ffp ffp_two_sum(float2 a, float2 b) {
+  const float2 s = padd(a, b);
+  const float2 bb = psub(s, a);
+  return ffp{s, padd(psub(a, psub(s, bb)), psub(b, bb))};
+}
+__device__ __forceinline__ ffp ffp_fast_two_sum(float2 a, float2 b) {   // |a| >= |b| per lane
+  const float2 s = padd(a, b);
+  return ffp{s, psub(b, psub(s, a))};
+}
+__device__ __forceinline__ void ffp_acc(ffp& acc, float2 x) {
+  const ffp t = ffp_two_sum(acc.hi, x);
+  acc.hi = t.hi;
+  acc.lo = padd(acc.lo, t.lo);
+}
+
+template <bool UPDATE>
+__global__ void __launch_bounds__(256)
+residual_zm_pair_kernel(const float* __restrict__ phi, float* __restrict__ phi_out,
+                        const float* __restrict__ e, const float* __restrict__ F,
+                        float* __restrict__ r32, int nx, int ny, int nz, ff2 h2, float ih2,
+                        const double* fnorm2, double* partials, const int* __restrict__ stop) {
+  if (*stop) return;  // the solve has finished: the rest of its batch does nothing
+  __shared__ float s_hi[RZ_RING][RP_H];
+  __shared__ float s_lo[RZ_RING][RP_H];
+  __shared__ float s_e[UPDATE ? RZ_RING : 1][RP_H];
+  __shared__ double red[8];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * (2 * RP_QX), y0 = blockIdx.y * RZ_TY, z0 = blockIdx.z * RZ_ZC;
+  const int z1 = z0 + RZ_ZC < nz ? z0 + RZ_ZC : nz;
+  const int nit = z1 - z0;
+  const long long plane = (long long)nx * ny;
+  const long long n = plane * nz;
+  const float* __restrict__ phl = phi + n;
+  const float sF = (float)(1.0 / sqrt(*fnorm2 / (double)n));
+  // this thread's (up to) three halo positions: offsets within a plane
+  int hoff[3];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    const int pe = tid + 256 * u;
+    const int hx = x0 - 1 + pe % RP_HX, hy = y0 - 1 + pe / RP_HX;
+    hoff[u] = (pe < RP_H && hy < ny + 1) ? wrap(hy, ny) * nx + wrap(hx, nx) : 0;
+  }
+  // plane z0 - 1 + m lives in slot m % RZ_RING
+  auto copy_plane = [&](int m) {
+    const long long b = (long long)wrap(z0 - 1 + m, nz) * plane;
+    const int sl = m % RZ_RING;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int pe = tid + 256 * u;
+      if (pe < RP_H) {
+        cp_async4(&s_hi[sl][pe], phi + b + hoff[u]);
+        cp_async4(&s_lo[sl][pe], phl + b + hoff[u]);
+        if (UPDATE) cp_async4(&s_e[UPDATE ? sl : 0][pe], e + b + hoff[u]);
+      }
+    }
+  };
+  auto issue_group = [&](int g) {   // group g carries plane index g + 2
+    if (g < nit) copy_plane(g + 2);
+    cp_async_commit();
+  };
+  auto update_plane = [&](int m) {  // phi' = phi + e in place, this thread's positions
+    const int sl = m % RZ_RING;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int pe = tid + 256 * u;
+      if (pe < RP_H) {
+        const ff2 v = ff_add_f(ff2{s_hi[sl][pe], s_lo[sl][pe]}, s_e[UPDATE ? sl : 0][pe]);
+        s_hi[sl][pe] = v.hi;
+        s_lo[sl][pe] = v.lo;
+      }
+    }
+  };
+  const int tx = tid % RP_QX, ty = tid / RP_QX;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = y < ny;
+  const int c = (ty + 1) * RP_HX + tx + 1, cb = c + RP_QX;
+  const float2 m6 = pset(-6.0f), h2hi = pset(h2.hi), h2lo = pset(h2.lo), pih2 = pset(ih2);
+  copy_plane(0);
+  copy_plane(1);
+#pragma unroll
+  for (int g = 0; g < RZ_D; ++g) issue_group(g);
+  ff2 acc{0.0f, 0.0f};
+  for (int it = 0; it < nit; ++it) {
+    const long long q = (long long)(z0 + it) * plane + (long long)y * nx + x;
+    float2 fhi = pset(0.f), flo = pset(0.f);
+    if (active) {
+      fhi = pmk(F[q], F[q + RP_QX]);
+      flo = pmk(F[n + q], F[n + q + RP_QX]);
+    }
+    issue_group(it + RZ_D);
+    cp_async_wait<RZ_D>();
+    __syncthreads();
+    if (UPDATE) {
+      if (it == 0) { update_plane(0); update_plane(1); }
+      update_plane(it + 2);
+      __syncthreads();
+    }
+    if (active) {
+      const int sm = it % RZ_RING, sc = (it + 1) % RZ_RING, sp = (it + 2) % RZ_RING;
+      auto hi2 = [&](int sl, int o) { return pmk(s_hi[sl][c + o], s_hi[sl][cb + o]); };
+      auto lo2 = [&](int sl, int o) { return pmk(s_lo[sl][c + o], s_lo[sl][cb + o]); };
+      const float2 cvh = hi2(sc, 0), cvl = lo2(sc, 0);
+      ffp sum{pmul(m6, cvh), pset(0.0f)};
+      const float2 err = pfma(m6, cvh, pneg(sum.hi));
+      float2 lo = pmul(m6, cvl);
+      ffp_acc(sum, hi2(sm, 0));      lo = padd(lo, lo2(sm, 0));
+      ffp_acc(sum, hi2(sp, 0));      lo = padd(lo, lo2(sp, 0));
+      ffp_acc(sum, hi2(sc, -RP_HX)); lo = padd(lo, lo2(sc, -RP_HX));
+      ffp_acc(sum, hi2(sc, RP_HX));  lo = padd(lo, lo2(sc, RP_HX));
+      ffp_acc(sum, hi2(sc, -1));     lo = padd(lo, lo2(sc, -1));
+      ffp_acc(sum, hi2(sc, 1));      lo = padd(lo, lo2(sc, 1));
+      const ffp lap = ffp_fast_two_sum(sum.hi, padd(sum.lo, padd(err, lo)));   // h^2 A phi
+      // h^2 F (ff_mul with both words)
+      const float2 pr = pmul(fhi, h2hi);
+      float2 pe = pfma(fhi, h2hi, pneg(pr));
+      pe = pfma(fhi, h2lo, pe);
+      pe = pfma(flo, h2hi, pe);
+      const ffp fh = ffp_fast_two_sum(pr, pe);
+      const ffp d = ffp_two_sum(fh.hi, pneg(lap.hi));
+      const float2 rr = pmul(padd(d.hi, padd(d.lo, psub(fh.lo, lap.lo))), pih2);
+      r32[q] = rr.x;
+      r32[q + RP_QX] = rr.y;
+      const float ra = rr.x * sF, rb = rr.y * sF;
+      ff_acc(acc, ra * ra);
+      ff_acc(acc, rb * rb);
+      if (UPDATE) {
+        phi_out[q] = cvh.x;
+        phi_out[q + RP_QX] = cvh.y;
+        phi_out[n + q] = cvl.x;
+        phi_out[n + q + RP_QX] = cvl.y;
+      }
+    }
+  }
+  cp_async_wait<0>();
+  // fixed-order block sum: each warp by shuffles, then the eight warp sums in order
+  double v = ff_to_double(acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double t = red[0];
+    for (int w = 1; w < 8; ++w) t += red[w];
+    partials[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 // rc[I] = mean over the 8 children of (r - A e), coarse dims (cx, cy, cz).  One thread per coarse
 // cell.  Over a 2x2x2 block the children's Laplacians sum to the 24 faces of the block:
 // sum_children h^2 (A e)_child = (sum of the 24 outside neighbours) - 3 (sum of the 8 children),
@@ -1312,7 +1472,10 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge, const StepRecord* check_rec
   const ff2 h2 = ff_from_double(hh);
   const float ih2 = (float)(1.0 / hh);
   const dim3 rg((nx + RZ_TX - 1) / RZ_TX, (ny + RZ_TY - 1) / RZ_TY, (nz + RZ_ZC - 1) / RZ_ZC);
-  const int rblocks = (int)residual_zm_blocks(nx, ny, nz);
+  // rows of whole 64-cell multiples take the two-cells-per-thread residual
+  const bool pair_res = nx % (2 * RP_QX) == 0;
+  const dim3 rpg(nx / (2 * RP_QX), (ny + RZ_TY - 1) / RZ_TY, (nz + RZ_ZC - 1) / RZ_ZC);
+  const int rblocks = (int)(pair_res ? residual_pair_blocks(nx, ny, nz) : residual_zm_blocks(nx, ny, nz));
   MGCtl* ctl = (MGCtl*)m->ctl;
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(MGCtl), s);
   if (e != cudaSuccess) return e;
@@ -1330,6 +1493,15 @@ static cudaError_t mg_iterate(dh_ctx* c, bool gauge, const StepRecord* check_rec
         residual_d_kernel<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(
             m->phi, nullptr, nullptr, m->F, m->dr[0], nx, ny, nz, h2, 1.0 / hh, m->scal + 1,
             m->partials, m->stop);
+    } else if (pair_res) {
+      if (add)
+        residual_zm_pair_kernel<true><<<rpg, 256, 0, s>>>(m->phi, m->phi2, m->e[0], m->F, m->r[0], nx,
+                                                          ny, nz, h2, ih2, m->scal + 1, m->partials,
+                                                          m->stop);
+      else
+        residual_zm_pair_kernel<false><<<rpg, 256, 0, s>>>(m->phi, nullptr, nullptr, m->F, m->r[0], nx,
+                                                           ny, nz, h2, ih2, m->scal + 1, m->partials,
+                                                           m->stop);
     } else if (add) {
       residual_zm_kernel<true><<<rg, 256, 0, s>>>(m->phi, m->phi2, m->e[0], m->F, m->r[0], nx, ny,
                                                   nz, h2, ih2, m->scal + 1, m->partials, m->stop);
