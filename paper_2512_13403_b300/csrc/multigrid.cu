@@ -945,6 +945,7 @@ __global__ void resid_restrict_kernel(const float* __restrict__ e, const float* 
   const int nx = 2 * cx, ny = 2 * cy, nz = 2 * cz;
   const long long nc = (long long)cx * cy * cz;
   const long long plane = (long long)nx * ny;
+#pragma unroll 2
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
        t += (long long)gridDim.x * blockDim.x) {
     const unsigned u = (unsigned)t / (unsigned)cx;
@@ -990,6 +991,7 @@ __global__ void prolong_add_kernel(float* __restrict__ ef, const float* __restri
   const int nx = 2 * cx, ny = 2 * cy;
   const long long nc = (long long)cx * cy * cz;
   const long long plane = (long long)nx * ny;
+#pragma unroll 2
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
        t += (long long)gridDim.x * blockDim.x) {
     const unsigned u = (unsigned)t / (unsigned)cx;
